@@ -1,0 +1,143 @@
+/*
+ * lpc.h -- C ABI of the B300 integer-only LiDAR geometry codec
+ * (arXiv 2603.25260, "Towards Practical Lossless Neural Compression for
+ * LiDAR Point Clouds").
+ *
+ * The codec turns integer voxel coordinates into a bitstream and back.  The
+ * GPU builds the octree (supplement, "Implementation of Octree Operations"),
+ * runs the integer network of Sec. 3 (GRED, Eq. 4-7; XFP, Eq. 8-11; integer
+ * linear / sparse conv / requantisation, Eq. 13-14) and the integer softmax
+ * (Eq. 15) that turns logits into 16-bit cumulative frequency tables; the
+ * host range coder consumes those tables.  All arithmetic that decides a
+ * bit of the stream is integer, so a stream written on one device decodes on
+ * any other (Sec. 3.3).
+ *
+ * Conventions for every entry point:
+ *  - Return value: an LPC_* status (0 = success, negative = failure).  On
+ *    failure `codec_last_error` gives a one-line message.  No entry point
+ *    aborts the process; kernels never trap, they record an error word that
+ *    the host turns into a status.
+ *  - "d_" arguments are device pointers (CUDA global memory on the device the
+ *    codec was created on); "h_" arguments are host pointers.  The caller
+ *    owns every buffer it passes; the codec owns its internal workspace.
+ *  - Coordinates are int32 triples (x, y, z), row-major [n][3], each in
+ *    [0, 2^L).  Duplicate points are allowed; the codec works on the set of
+ *    occupied voxels.
+ *  - All GPU work is issued on the stream given at creation.  Calls return
+ *    only after every host buffer they fill is complete; device outputs are
+ *    complete in stream order.  A codec is not thread-safe: use one codec per
+ *    host thread.
+ */
+#ifndef LPC_H
+#define LPC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LPC_OK 0
+#define LPC_INVALID_ARG (-1)      /* bad argument, out-of-range coordinate, bad blob */
+#define LPC_CAPACITY (-2)         /* an output buffer or the workspace is too small */
+#define LPC_HASH_FULL (-3)        /* voxel hash table probe limit reached */
+#define LPC_CORRUPT_STREAM (-4)   /* bitstream fails to parse or decode */
+#define LPC_WEIGHTS_MISMATCH (-5) /* bitstream written with a different weight blob */
+#define LPC_CUDA_ERROR (-6)       /* a CUDA runtime call failed */
+#define LPC_TIMEOUT (-7)          /* a bounded device wait gave up */
+
+typedef struct lpc_codec codec_t;
+
+typedef struct {
+  int L;              /* maximum octree depth handled (6..21); frames may use L' <= L */
+  int C;              /* network width; must equal the blob's (32) */
+  int b_off;          /* base level offset: b = L - b_off (5) */
+  int t_off;          /* threshold offset: t = L - t_off (4), Sec. 3.2 and supplement */
+  int64_t max_points; /* largest point count of one frame (sizes the workspace) */
+  int max_frames;     /* largest batch for encode_batch / decode_batch (>= 1) */
+  int chunk;          /* nodes per entropy-coded substream of a network level (16384) */
+  int host_threads;   /* host threads for range coding (0 = hardware concurrency) */
+  uint64_t cuda_stream; /* cudaStream_t as an integer (0 = legacy default stream) */
+} lpc_config;
+
+/* Create a codec.  `blob` is the integer weight blob (format in the Python
+ * package's synth module docstring: exp table, then per-layer INT8 weights,
+ * INT32 biases, multipliers, shifts, zero points and Q15 PReLU slopes).  The
+ * codec validates it, copies it to the device and keeps its 64-bit FNV-1a
+ * hash, which every bitstream header carries.  Allocates all device and
+ * pinned-host workspace once, sized by cfg->L and cfg->max_points.
+ * Errors: LPC_INVALID_ARG (config or blob), LPC_CUDA_ERROR (allocation). */
+int codec_create(const lpc_config* cfg, const void* blob, size_t blob_len, codec_t** out);
+
+/* Free every resource of the codec (NULL is allowed). */
+void codec_destroy(codec_t* codec);
+
+/* Message of the last failure on this codec ("" after success). */
+const char* codec_last_error(codec_t* codec);
+
+/* Encode one frame.  d_xyz: device int32 [n][3].  The bitstream goes to the
+ * caller's host buffer h_out of `cap` bytes; *out_len receives its length.
+ * If cap is too small, returns LPC_CAPACITY with the required length in
+ * *out_len.  n = 0 gives an empty-frame stream.
+ * Errors: LPC_INVALID_ARG (coordinate outside [0, 2^L)), LPC_CAPACITY
+ * (n > max_points or small h_out), LPC_HASH_FULL, LPC_CUDA_ERROR. */
+int encode_frame(codec_t* codec, const int32_t* d_xyz, int64_t n, uint8_t* h_out, size_t cap,
+                 size_t* out_len);
+
+/* Decode one bitstream (host bytes) into device int32 [n_out][3] voxel
+ * coordinates, unique and in Morton order (x the most significant bit of each
+ * 3-bit group).  cap = capacity of d_xyz_out in points; if too small,
+ * returns LPC_CAPACITY with the voxel count in *n_out.
+ * Errors: LPC_CORRUPT_STREAM, LPC_WEIGHTS_MISMATCH, LPC_CAPACITY,
+ * LPC_CUDA_ERROR. */
+int decode_frame(codec_t* codec, const uint8_t* h_in, size_t len, int32_t* d_xyz_out,
+                 int64_t cap, int64_t* n_out);
+
+/* Parity hook: the cumulative frequency table of network level d
+ * (b <= d <= L-1) for a frame, on the device.  d_cdf_out: u16 [N_d][256];
+ * row entry s = C_{s+1} = f_0 + ... + f_s for s = 0..253 (C_0 = 0 and
+ * C_255 = 65536 are implicit), entries 254 and 255 are 0xFFFF.  The f_s are
+ * the 16-bit integer softmax frequencies of Eq. 15 (every f_s >= 1, sum 2^16).
+ * cap_nodes: rows available; *n_nodes receives N_d (LPC_CAPACITY if larger).
+ * Only the network runs; nothing is entropy coded. */
+int probs_level(codec_t* codec, const int32_t* d_xyz, int64_t n, int d, uint16_t* d_cdf_out,
+                int64_t cap_nodes, int64_t* n_nodes);
+
+/* Batched encode: nf frames (nf <= max_frames), frame i has n[i] points at
+ * d_xyz[i] (device) and depth Ls[i] (6..cfg->L).  Frames are grouped by
+ * relative level so that every level of every frame goes through one launch
+ * sequence.  The output for frame i is byte-identical to encode_frame of that
+ * frame: h_out[i] (capacity caps[i]) receives out_lens[i] bytes.  Returns the
+ * first failing status (per-frame CAPACITY reports the needed length). */
+int encode_batch(codec_t* codec, int nf, const int32_t* const* d_xyz, const int64_t* n,
+                 const int* Ls, uint8_t* const* h_out, const size_t* caps, size_t* out_lens);
+
+/* Batched decode: the mirror of encode_batch.  Frame i's voxels go to
+ * d_xyz_out[i] (capacity caps[i] points), count in n_out[i]. */
+int decode_batch(codec_t* codec, int nf, const uint8_t* const* h_in, const size_t* lens,
+                 int32_t* const* d_xyz_out, const int64_t* caps, int64_t* n_out);
+
+/* Per-frame statistics of the last encode_frame / decode_frame call:
+ * counts[d] = N_d for d = 0..L (L+1 entries), and the time split in
+ * microseconds (GPU part, host coding part).  Returns the depth L. */
+int codec_last_stats(codec_t* codec, int64_t* counts, double* gpu_us, double* host_us);
+
+/* Kernel-family profiler.  codec_profile(mask) resets the counters and times
+ * every later launch of the families whose bit is set in `mask` with CUDA
+ * events on the codec's stream (0 turns it off).  Families: 0 sort (Morton +
+ * radix sort + unique), 1 levels (level build / decoder expansion), 2 hash_kmap,
+ * 3 embed, 4 up_prune, 5 down_s2, 6 conv333, 7 predictor_cdf.
+ * codec_profile_read returns, for one family, the summed launch time (ms),
+ * the launch count, and the algorithmic bytes and integer ops those launches
+ * must touch (counted from level sizes and neighbour pairs, not from the
+ * kernels' actual traffic).  codec_profile_name gives the family's name. */
+int codec_profile(codec_t* codec, unsigned family_mask);
+int codec_profile_read(codec_t* codec, int family, double* ms, int64_t* launches, double* bytes,
+                       double* ops);
+const char* codec_profile_name(int family);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LPC_H */

@@ -1,0 +1,77 @@
+/*
+ * lpc_ops.h -- op-level entry points of the B300 codec, for parity tests.
+ *
+ * Each function runs one step of the hot path on the device, exactly as the
+ * codec does inside encode_frame / decode_frame, on caller-provided data.
+ * Data arrays are device pointers ("d_"); layer parameters are host pointers
+ * ("h_") in the weight-blob layout.  Unlike the codec, these hooks allocate
+ * their temporaries (cudaMalloc) per call and synchronise the stream before
+ * returning.  Status codes are the LPC_* codes of lpc.h.
+ *
+ * Node arrays are Morton-sorted u64 keys of one depth (3 bits per level, x
+ * the most significant bit of each group).  Activations are int8 row-major
+ * [rows][channels].
+ */
+#ifndef LPC_OPS_H
+#define LPC_OPS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Octree levels (supplement, "Implementation of Octree Operations"): sort the
+ * Morton keys of d_xyz, drop duplicates, then repeatedly halve (key >> 3) and
+ * drop consecutive duplicates; the code of a parent ORs 1 << (child key & 7)
+ * (the kernel-2 stride-2 all-ones convolution).  Outputs, concatenated over
+ * depths: d_keys = V_0..V_L, d_codes = Y_0..Y_{L-1}; h_counts[d] = N_d
+ * (L+1 entries).  cap bounds both concatenations. */
+int lpc_build_levels(const int32_t* d_xyz, int64_t n, int L, uint64_t* d_keys, uint8_t* d_codes,
+                     int64_t* h_counts, int64_t cap, uint64_t stream);
+
+/* Voxel hash + 3x3x3 kernel map at one depth: d_nbr[N][27] = row of the
+ * neighbour at offset o = 9(dx+1) + 3(dy+1) + (dz+1), or -1 if absent or
+ * outside the cube (Sec. 3.3, sparse conv as indexed linear transforms).
+ * table_log2 = log2 of the hash capacity (0 = automatic, >= 2N slots).
+ * Errors: LPC_HASH_FULL when the bounded probe sequence finds no slot. */
+int lpc_kernel_map(const uint64_t* d_keys, int64_t N, int depth, int32_t* d_nbr, int table_log2,
+                   uint64_t stream);
+
+/* 3x3x3 sparse conv (Eq. 13-14): out[n] = requant(prelu(bias +
+ * sum_{o, present} W[o] (x[nb] - z_in))).  h_W: int8 [27][cout][cin];
+ * h_bias, h_mult: int32 [cout]; h_slope: int16 [cout] Q15 or NULL (no PReLU).
+ * cin in {32, 64}, cout = 32. */
+int lpc_conv333(const uint64_t* d_keys, int64_t N, int depth, const int8_t* d_x, int cin,
+                int z_in, const int8_t* h_W, const int32_t* h_bias, const int32_t* h_mult,
+                int shift, const int16_t* h_slope, int z_out, int cout, int8_t* d_out,
+                uint64_t stream);
+
+/* Kernel-2 stride-2 sparse conv from the children (depth k+1, d_ckeys[Nc])
+ * to the parents (depth k, d_pkeys[Np]), part of Downsampling (Eq. 4).
+ * h_W: int8 [8][cout][cin], slice = child index key & 7. */
+int lpc_down_s2(const uint64_t* d_ckeys, int64_t Nc, const uint64_t* d_pkeys, int64_t Np,
+                const int8_t* d_x, int cin, int z_in, const int8_t* h_W, const int32_t* h_bias,
+                const int32_t* h_mult, int shift, const int16_t* h_slope, int z_out, int cout,
+                int8_t* d_out, uint64_t stream);
+
+/* Upsampling + Pruning (Eq. 6): parent p with code d_codes[p]; each set bit c
+ * gives the child row (pkey << 3 | c) of d_ckeys with
+ * requant_c(prelu_c(bias[c] + W[c] (x[p] - z_in))).  h_W int8 [8][cout][cin];
+ * h_bias, h_mult int32 [8][cout]; h_slope int16 [8][cout] or NULL. */
+int lpc_up_prune(const uint64_t* d_pkeys, const uint8_t* d_codes, int64_t Np,
+                 const uint64_t* d_ckeys, int64_t Nc, const int8_t* d_x, int cin, int z_in,
+                 const int8_t* h_W, const int32_t* h_bias, const int32_t* h_mult, int shift,
+                 const int16_t* h_slope, int z_out, int cout, int8_t* d_out, uint64_t stream);
+
+/* Integer softmax to cumulative table (Eq. 15): d_logits int8 [N][255],
+ * h_lut u32 [256] (lut[0] = 2^16, non-increasing) -> d_cdf u16 [N][256] in
+ * the probs_level row format. */
+int lpc_softmax_cdf(const int8_t* d_logits, int64_t N, const uint32_t* h_lut, uint16_t* d_cdf,
+                    uint64_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LPC_OPS_H */

@@ -533,7 +533,7 @@ int or_rc_decode_adaptive(int64_t n, const uint8_t* in, size_t len, uint8_t* sym
 
 uint64_t or_fnv1a64(const void* data, size_t len) {
   const uint8_t* p = (const uint8_t*)data;
-  uint64_t h = 1469598103934665603ull;
+  uint64_t h = 14695981039346656037ull;
   for (size_t i = 0; i < len; i++) {
     h ^= p[i];
     h *= 1099511628211ull;

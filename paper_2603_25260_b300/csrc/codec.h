@@ -1,0 +1,166 @@
+// The codec object: workspace, level-by-level network schedule, host coding.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <condition_variable>
+#include <functional>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/lpc.h"
+#include "common.cuh"
+#include "kernels.h"
+#include "model.h"
+
+namespace lpc {
+
+// Minimal fork-join pool: run(n, fn) calls fn(0..n-1) on the workers and the
+// calling thread, and returns when all calls are done.
+class Pool {
+ public:
+  explicit Pool(int workers);
+  ~Pool();
+  void run(int ntasks, const std::function<void(int)>& fn);
+  int size() const { return (int)th_.size() + 1; }
+
+ private:
+  void loop();
+  std::vector<std::thread> th_;
+  std::mutex mu_;
+  std::condition_variable cv_, done_;
+  const std::function<void(int)>* fn_ = nullptr;
+  int ntasks_ = 0, busy_ = 0;
+  std::atomic<int> next_{0};
+  uint64_t gen_ = 0;
+  bool stop_ = false;
+};
+
+struct Levels {
+  uint64_t* key[kMaxDepth + 1] = {};
+  uint8_t* code[kMaxDepth + 1] = {};
+  uint32_t* off[kMaxDepth + 1] = {};  // child offsets (N_d + 1 entries)
+  uint32_t* par[kMaxDepth + 1] = {};  // parent row of every node
+  int64_t cap[kMaxDepth + 1] = {};
+};
+
+// Kernel families timed by the optional CUDA-event profiler.
+enum Family {
+  kFamSort = 0,  // Morton keys + radix sort + unique
+  kFamLevels,    // level build (encoder) / code expansion (decoder)
+  kFamHash,      // voxel hash + 27-neighbour map
+  kFamEmbed,     // occupancy-code embedding gathers
+  kFamUp,        // Upsampling + Pruning
+  kFamDown,      // stride-2 down conv
+  kFamConv,      // 3x3x3 sparse conv (+ fused residual merge)
+  kFamPred,      // predictor + integer softmax + cumulative table
+  kFamCount
+};
+
+// Per-family totals: summed launch durations (CUDA events on the codec's
+// stream), launches, and the algorithmic bytes / integer ops the launches
+// must touch (from the level sizes and the neighbour-pair counts).
+struct Profile {
+  unsigned mask = 0;  // families to time (0 = off)
+  double ms[kFamCount] = {};
+  int64_t launches[kFamCount] = {};
+  double bytes[kFamCount] = {};
+  double ops[kFamCount] = {};
+};
+
+struct Stats {
+  int L = 0;
+  int64_t N[kMaxDepth + 1] = {};
+  double gpu_us = 0, host_us = 0;
+};
+
+class Codec {
+ public:
+  Codec() = default;
+  ~Codec();
+  int create(const lpc_config& cfg, const void* blob, size_t len);
+  int encode(const int32_t* d_xyz, int64_t n, uint8_t* out, size_t cap, size_t* out_len);
+  int decode(const uint8_t* in, size_t len, int32_t* d_out, int64_t cap, int64_t* n_out);
+  int probs(const int32_t* d_xyz, int64_t n, int d, uint16_t* d_cdf, int64_t cap, int64_t* nn);
+  int encode_batch(int nf, const int32_t* const* xyz, const int64_t* n, const int* Ls,
+                   uint8_t* const* out, const size_t* caps, size_t* lens);
+  int decode_batch(int nf, const uint8_t* const* in, const size_t* lens, int32_t* const* out,
+                   const int64_t* caps, int64_t* n_out);
+
+  std::string err;
+  Stats stats;
+  Profile prof;
+  void profile_reset(unsigned mask);
+
+ private:
+  int fail(int st, const std::string& msg) {
+    err = msg;
+    return st;
+  }
+  int cuda_check(const char* what);
+  int check_device_error();
+  void build_octree(const int32_t* d_xyz, int64_t n, int L);
+  void begin_frame(int L);
+  void level_bytes(int L);
+  void embed(const DEmb& E, int d, int8_t* out, int stride, int col);
+  void up(const DLayer& W, int d, const int8_t* x, int xs, int8_t* out, int os);
+  void conv(const DLayer& W, int d, const int32_t* nbr, int slot, const int8_t* x, int xs,
+            int8_t* out, int os, int oc, const DRes* res);
+  void kmap(int d, int32_t* nbr, int slot);
+  void ensure_Fb();
+  void ensure_Ft();
+  void ensure_nbr_t();
+  void net_level(int d, int mode, uint16_t* cdf, uint32_t* enc, int8_t* logits);
+  int64_t hash_slots(int64_t n) const;
+  // profiler: bracket a launch of family f; ops/bytes are algorithmic work
+  // (pair_slot >= 0: ops/bytes are per neighbour pair, scaled at collection)
+  void pbeg(int f);
+  void pend(int f, double bytes, double ops, int pair_slot = -1, double per_pair_ops = 0,
+            double per_pair_bytes = 0);
+  void prof_collect();
+  struct Mark {
+    int f, e0, e1, pair_slot;
+    double bytes, ops, ppo, ppb;
+  };
+  std::vector<cudaEvent_t> pev_;
+  std::vector<Mark> marks_;
+  int pev_used_ = 0;
+  uint64_t* d_pairs_ = nullptr;  // [2]: present neighbour pairs at V_b, V_t
+
+  lpc_config cfg_{};
+  cudaStream_t st_ = nullptr;
+  Model M_;
+  Pool* pool_ = nullptr;
+  // per-frame state
+  int L_ = 0, b_ = 0, t_ = 0;
+  int64_t N_[kMaxDepth + 1] = {};  // host copies of the level sizes
+  bool have_Fb_ = false, have_Ft_ = false, have_nbr_t_ = false;
+  // device workspace
+  void* dmem_ = nullptr;
+  Levels lv_;
+  int64_t* d_N_ = nullptr;   // [kMaxDepth + 2]: level sizes, then the input count
+  int* d_err_ = nullptr;
+  uint64_t* d_keys0_ = nullptr;
+  SortScratch sort_;
+  ScanScratch scan_;
+  HashTable hash_;
+  int32_t *nbr_b_ = nullptr, *nbr_t_ = nullptr;
+  int8_t *fb_ = nullptr, *xb_ = nullptr, *xt_ = nullptr, *y1_ = nullptr, *xe_ = nullptr;
+  int8_t *g_[2] = {}, *hx_[2] = {}, *fo_ = nullptr;
+  uint16_t* d_cdf_ = nullptr;
+  uint32_t* d_enc_ = nullptr;
+  // pinned host workspace
+  void* hmem_ = nullptr;
+  int64_t* h_N_ = nullptr;
+  int* h_err_ = nullptr;
+  uint8_t* h_codes_ = nullptr;  // coarse codes / decoded codes (max_points * 2)
+  uint32_t* h_enc_ = nullptr;
+  uint16_t* h_cdf_ = nullptr;
+  std::vector<cudaEvent_t> ev_;
+};
+
+}  // namespace lpc

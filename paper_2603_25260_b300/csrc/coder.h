@@ -1,0 +1,96 @@
+// Host entropy coding: a range coder with a 32-bit range and byte-wise carry
+// propagation (low kept to 33 bits; a settled byte is held back in a cache
+// together with a count of pending 0xFF bytes until the carry is known).
+// Two probability sources: the device-made 16-bit cumulative tables of the
+// network levels, and an adaptive symbol-frequency model for the coarse
+// levels below b (supplement, "Detailed Model Structure").
+#pragma once
+
+#include <stddef.h>
+#include <stdint.h>
+
+#include <vector>
+
+namespace lpc {
+
+class RangeEncoder {
+ public:
+  explicit RangeEncoder(std::vector<uint8_t>* out) : out_(out) {}
+  // Code the interval [lo, lo + f) of a total 2^16.
+  inline void code16(uint32_t lo, uint32_t f) { code(range_ >> 16, lo, f); }
+  // Code the interval [lo, lo + f) of an arbitrary total (<= 2^16).
+  inline void code_total(uint32_t lo, uint32_t f, uint32_t total) { code(range_ / total, lo, f); }
+  void finish();
+
+ private:
+  inline void code(uint32_t r, uint32_t lo, uint32_t f) {
+    low_ += (uint64_t)r * lo;
+    range_ = r * f;
+    while (range_ < (1u << 24)) {
+      range_ <<= 8;
+      shift_low();
+    }
+  }
+  void shift_low();
+  std::vector<uint8_t>* out_;
+  uint64_t low_ = 0;
+  uint32_t range_ = 0xFFFFFFFFu;
+  uint8_t cache_ = 0;
+  uint64_t pending_ = 1;
+};
+
+class RangeDecoder {
+ public:
+  RangeDecoder(const uint8_t* p, size_t n);
+  // Decode with a table row (u16[256], entry s = C_{s+1}, s = 0..253).
+  int decode_row(const uint16_t* row);
+  // Range division and update for an arbitrary total (adaptive model).
+  inline uint32_t target(uint32_t total) {
+    r_ = range_ / total;
+    uint32_t v = code_ / r_;
+    return v < total ? v : total - 1;
+  }
+  void update(uint32_t lo, uint32_t f);
+  bool bad() const { return bad_; }
+
+ private:
+  inline uint8_t next() {
+    if (p_ < end_) return *p_++;
+    bad_ = true;
+    return 0;
+  }
+  const uint8_t* p_;
+  const uint8_t* end_;
+  uint32_t range_ = 0xFFFFFFFFu, code_ = 0, r_ = 0;
+  bool bad_ = false;
+};
+
+// Adaptive frequencies of the 255 symbols: start at 1, +32 per coded symbol,
+// every count halved (rounding up) once the total exceeds 2^16.  Kept in a
+// Fenwick tree so that cumulative lookups and the decoder's search are
+// logarithmic.
+class AdaptiveModel {
+ public:
+  AdaptiveModel();
+  void encode(RangeEncoder& e, int s);
+  int decode(RangeDecoder& d);
+
+ private:
+  uint32_t prefix(int s) const;  // sum of f[0..s)
+  void add(int s, int32_t v);
+  void rebuild();
+  void bump(int s);
+  uint32_t f_[256];
+  uint32_t tree_[257];
+  uint32_t total_;
+};
+
+// Encode symbols with per-node (lo, f) pairs packed as lo | f << 16.
+void encode_packed(const uint32_t* lofreq, size_t n, std::vector<uint8_t>* out);
+// Encode symbols with the adaptive model (one model per substream).
+void encode_adaptive(const uint8_t* syms, size_t n, std::vector<uint8_t>* out);
+// Decode n symbols with table rows; returns false on a corrupt stream.
+bool decode_rows(const uint16_t* rows, size_t n, const uint8_t* in, size_t len, uint8_t* syms);
+bool decode_adaptive(size_t n, const uint8_t* in, size_t len, uint8_t* syms);
+
+}  // namespace lpc

@@ -1,0 +1,68 @@
+// Shared device helpers of the B300 codec: status handling, Morton bit
+// spreading, and the integer primitives of Sec. 3.3 (Eq. 13-14).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/lpc.h"
+
+namespace lpc {
+
+constexpr int kMaxDepth = 21;
+constexpr int kNsym = 255;      // occupancy classes (codes 1..255)
+constexpr int kFreqBits = 16;   // cumulative tables sum to 2^16
+constexpr int kFreqTotal = 1 << kFreqBits;
+
+// Device error word values (first error wins).
+constexpr int kErrCoord = 1;    // coordinate outside [0, 2^L)
+constexpr int kErrHashFull = 2; // hash probe limit reached
+constexpr int kErrExpand = 3;   // decoded level is not strictly Morton-ordered
+
+__device__ __forceinline__ void set_error(int* err, int code) { atomicCAS(err, 0, code); }
+
+// Spread the low 21 bits of v to every third bit (bit i -> bit 3i).
+__host__ __device__ __forceinline__ uint64_t spread3(uint64_t v) {
+  v &= 0x1fffffull;
+  v = (v | (v << 32)) & 0x1f00000000ffffull;
+  v = (v | (v << 16)) & 0x1f0000ff0000ffull;
+  v = (v | (v << 8)) & 0x100f00f00f00f00full;
+  v = (v | (v << 4)) & 0x10c30c30c30c30c3ull;
+  v = (v | (v << 2)) & 0x1249249249249249ull;
+  return v;
+}
+
+// Inverse of spread3: gather every third bit.
+__host__ __device__ __forceinline__ uint32_t compact3(uint64_t v) {
+  v &= 0x1249249249249249ull;
+  v = (v ^ (v >> 2)) & 0x10c30c30c30c30c3ull;
+  v = (v ^ (v >> 4)) & 0x100f00f00f00f00full;
+  v = (v ^ (v >> 8)) & 0x1f0000ff0000ffull;
+  v = (v ^ (v >> 16)) & 0x1f00000000ffffull;
+  v = (v ^ (v >> 32)) & 0x1fffffull;
+  return (uint32_t)v;
+}
+
+// Morton key: x is the most significant bit of every 3-bit group, so the low
+// three bits of a key are the child index 4*xbit + 2*ybit + zbit.
+__host__ __device__ __forceinline__ uint64_t morton3(uint32_t x, uint32_t y, uint32_t z) {
+  return (spread3(x) << 2) | (spread3(y) << 1) | spread3(z);
+}
+
+// Eq. 14: clip(round_half_up(acc * m / 2^r) + z, -128, 127), int64 product,
+// arithmetic (floor) shift.
+__device__ __forceinline__ int requant(int32_t acc, int32_t m, int r, int z) {
+  long long p = (long long)acc * (long long)m;
+  long long q = ((p + (1ll << (r - 1))) >> r) + z;
+  q = q < -128 ? -128 : q;
+  q = q > 127 ? 127 : q;
+  return (int)q;
+}
+
+// PReLU on the INT32 accumulator with a Q15 slope, round half up.
+__device__ __forceinline__ int32_t prelu(int32_t acc, int a) {
+  if (acc >= 0) return acc;
+  return (int32_t)(((long long)acc * a + (1 << 14)) >> 15);
+}
+
+}  // namespace lpc

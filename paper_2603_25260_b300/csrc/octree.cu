@@ -1,0 +1,343 @@
+// Octree construction on the device (supplement, "Implementation of Octree
+// Operations"): Morton keys, an LSD radix sort, duplicate removal, the
+// level-by-level floor-halving with occupancy codes, and the decoder's
+// code -> child expansion.  Level sizes stay on the device, so a whole build
+// is queued without host round trips.
+#include <algorithm>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace lpc {
+
+// ------------------------------------------------------------ block scan --
+// Exclusive scan of one u32 per thread over a block of NT threads.
+template <int NT>
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* total, uint32_t* sm) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sm[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    uint32_t t = lane < NT / 32 ? sm[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    if (lane < NT / 32) sm[lane] = t;
+  }
+  __syncthreads();
+  uint32_t r = (w ? sm[w - 1] : 0) + x - v;
+  *total = sm[NT / 32 - 1];
+  __syncthreads();
+  return r;
+}
+
+// In-place exclusive scan of a[0..len) by one block of 1024 threads.
+__global__ void __launch_bounds__(1024) k_scan_single(uint32_t* a, int64_t len) {
+  __shared__ uint32_t sm[32];
+  const int64_t per = (len + 1023) / 1024;
+  const int64_t b = threadIdx.x * per, e = std::min(len, b + per);
+  uint32_t s = 0;
+  for (int64_t i = b; i < e; i++) s += a[i];
+  uint32_t tot;
+  uint32_t run = block_excl_scan<1024>(s, &tot, sm);
+  for (int64_t i = b; i < e; i++) {
+    uint32_t v = a[i];
+    a[i] = run;
+    run += v;
+  }
+}
+
+// ------------------------------------------------------------ radix sort --
+constexpr int kRsThreads = 256, kRsItems = 16, kRsTile = kRsThreads * kRsItems;
+
+int64_t sort_tiles(int64_t n) { return (n + kRsTile - 1) / kRsTile; }
+
+__global__ void __launch_bounds__(kRsThreads)
+k_rs_hist(const uint64_t* __restrict__ keys, int64_t n, int shift, uint32_t* hist, int64_t nt) {
+  __shared__ uint32_t h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * kRsTile;
+#pragma unroll 4
+  for (int i = 0; i < kRsItems; i++) {
+    int64_t idx = base + i * kRsThreads + threadIdx.x;
+    if (idx < n) atomicAdd(&h[(keys[idx] >> shift) & 255], 1u);
+  }
+  __syncthreads();
+  hist[(int64_t)threadIdx.x * nt + blockIdx.x] = h[threadIdx.x];
+}
+
+// Stable scatter: each warp ranks its 512 keys (warp-striped, so (item, lane)
+// order is the input order) with match.any, warps are ordered by a per-digit
+// prefix, tiles by the scanned histogram.
+__global__ void __launch_bounds__(kRsThreads)
+k_rs_scatter(const uint64_t* __restrict__ in, uint64_t* __restrict__ out, int64_t n, int shift,
+             const uint32_t* __restrict__ offs, int64_t nt) {
+  __shared__ uint32_t cnt[kRsThreads / 32][256];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < (kRsThreads / 32) * 256; i += kRsThreads) (&cnt[0][0])[i] = 0;
+  __syncthreads();
+  const int64_t seg = (int64_t)blockIdx.x * kRsTile + w * (kRsItems * 32);
+  const uint32_t lt = (1u << lane) - 1u;
+  uint64_t key[kRsItems];
+  uint32_t rank[kRsItems];
+  int dig[kRsItems];
+#pragma unroll
+  for (int i = 0; i < kRsItems; i++) {
+    const int64_t idx = seg + i * 32 + lane;
+    const bool valid = idx < n;
+    key[i] = valid ? in[idx] : 0;
+    const int d = valid ? (int)((key[i] >> shift) & 255) : 256;
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    uint32_t r = 0;
+    if (valid) r = cnt[w][d] + __popc(peers & lt);
+    __syncwarp();
+    if (valid && lane == __ffs(peers) - 1) cnt[w][d] += __popc(peers);
+    __syncwarp();
+    rank[i] = r;
+    dig[i] = d;
+  }
+  __syncthreads();
+  {
+    uint32_t run = 0;
+    for (int ww = 0; ww < kRsThreads / 32; ww++) {
+      uint32_t t = cnt[ww][threadIdx.x];
+      cnt[ww][threadIdx.x] = run;
+      run += t;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < kRsItems; i++) {
+    if (dig[i] < 256)
+      out[offs[(int64_t)dig[i] * nt + blockIdx.x] + cnt[w][dig[i]] + rank[i]] = key[i];
+  }
+}
+
+uint64_t* radix_sort(uint64_t* keys, int64_t n, int bits, const SortScratch& s, cudaStream_t st) {
+  if (n <= 1) return keys;
+  const int64_t nt = sort_tiles(n);
+  uint64_t* a = keys;
+  uint64_t* b = s.alt;
+  for (int shift = 0; shift < bits; shift += 8) {
+    k_rs_hist<<<(unsigned)nt, kRsThreads, 0, st>>>(a, n, shift, s.hist, nt);
+    k_scan_single<<<1, 1024, 0, st>>>(s.hist, 256 * nt);
+    k_rs_scatter<<<(unsigned)nt, kRsThreads, 0, st>>>(a, b, n, shift, s.hist, nt);
+    std::swap(a, b);
+  }
+  return a;
+}
+
+// ---------------------------------------------------------- Morton keys --
+__global__ void k_morton(const int32_t* __restrict__ xyz, int64_t n, int L, uint64_t* keys,
+                         int* err) {
+  const int32_t side = 1 << L;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int32_t x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
+    if (x < 0 || y < 0 || z < 0 || x >= side || y >= side || z >= side) {
+      set_error(err, kErrCoord);
+      x = y = z = 0;
+    }
+    keys[i] = morton3((uint32_t)x, (uint32_t)y, (uint32_t)z);
+  }
+}
+
+void launch_morton(const int32_t* xyz, int64_t n, int L, uint64_t* keys, int* err,
+                   cudaStream_t st) {
+  if (n <= 0) return;
+  int blocks = (int)std::min<int64_t>((n + 255) / 256, 148 * 8);
+  k_morton<<<blocks, 256, 0, st>>>(xyz, n, L, keys, err);
+}
+
+__global__ void k_keys_to_xyz(const uint64_t* __restrict__ keys, const int64_t* d_n,
+                              int32_t* xyz) {
+  const int64_t n = *d_n;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t k = keys[i];
+    xyz[3 * i] = (int32_t)compact3(k >> 2);
+    xyz[3 * i + 1] = (int32_t)compact3(k >> 1);
+    xyz[3 * i + 2] = (int32_t)compact3(k);
+  }
+}
+
+void launch_keys_to_xyz(const uint64_t* keys, const int64_t* d_n, int64_t cap, int L,
+                        int32_t* xyz, cudaStream_t st) {
+  (void)L;
+  if (cap <= 0) return;
+  int blocks = (int)std::min<int64_t>((cap + 255) / 256, 148 * 8);
+  k_keys_to_xyz<<<blocks, 256, 0, st>>>(keys, d_n, xyz);
+}
+
+// ------------------------------------------------- device-size scan pass --
+// Three kernels: per-tile sums, one-block scan of the tile sums, per-element
+// exclusive prefix handed to Op::emit.  Element count is read on the device.
+constexpr int kScThreads = 256, kScItems = 16, kScTile = kScThreads * kScItems;
+
+int64_t scan_tiles_for(int64_t cap) { return std::max<int64_t>(1, (cap + kScTile - 1) / kScTile); }
+
+template <class Op>
+__global__ void __launch_bounds__(kScThreads) k_sc_reduce(Op op, const int64_t* d_n,
+                                                          uint32_t* tiles) {
+  __shared__ uint32_t sm[32];
+  const int64_t n = *d_n;
+  const int64_t base = (int64_t)blockIdx.x * kScTile;
+  if (base >= n) return;
+  uint32_t s = 0;
+  for (int i = 0; i < kScItems; i++) {
+    int64_t idx = base + (int64_t)threadIdx.x * kScItems + i;
+    if (idx < n) s += op.value(idx);
+  }
+  uint32_t tot;
+  block_excl_scan<kScThreads>(s, &tot, sm);
+  if (threadIdx.x == 0) tiles[blockIdx.x] = tot;
+}
+
+template <class Op>
+__global__ void __launch_bounds__(1024) k_sc_top(Op op, const int64_t* d_n, uint32_t* tiles) {
+  __shared__ uint32_t sm[32];
+  const int64_t n = *d_n;
+  const int64_t len = (n + kScTile - 1) / kScTile;
+  const int64_t per = (len + 1023) / 1024;
+  const int64_t b = threadIdx.x * per, e = std::min(len, b + per);
+  uint32_t s = 0;
+  for (int64_t i = b; i < e; i++) s += tiles[i];
+  uint32_t tot;
+  uint32_t run = block_excl_scan<1024>(s, &tot, sm);
+  for (int64_t i = b; i < e; i++) {
+    uint32_t v = tiles[i];
+    tiles[i] = run;
+    run += v;
+  }
+  if (threadIdx.x == 0) op.finish(tot, n);
+}
+
+template <class Op>
+__global__ void __launch_bounds__(kScThreads) k_sc_emit(Op op, const int64_t* d_n,
+                                                        const uint32_t* tiles) {
+  __shared__ uint32_t sm[32];
+  const int64_t n = *d_n;
+  const int64_t base = (int64_t)blockIdx.x * kScTile;
+  if (base >= n) return;
+  const int64_t first = base + (int64_t)threadIdx.x * kScItems;
+  uint32_t v[kScItems];
+  uint32_t s = 0;
+#pragma unroll
+  for (int i = 0; i < kScItems; i++) {
+    v[i] = first + i < n ? op.value(first + i) : 0;
+    s += v[i];
+  }
+  uint32_t tot;
+  uint32_t run = tiles[blockIdx.x] + block_excl_scan<kScThreads>(s, &tot, sm);
+#pragma unroll
+  for (int i = 0; i < kScItems; i++) {
+    if (first + i < n) op.emit(first + i, run, n);
+    run += v[i];
+  }
+}
+
+template <class Op>
+static void run_scan(const Op& op, const int64_t* d_n, int64_t cap, const ScanScratch& s,
+                     cudaStream_t st) {
+  const int64_t nt = scan_tiles_for(cap);
+  k_sc_reduce<Op><<<(unsigned)nt, kScThreads, 0, st>>>(op, d_n, s.tiles);
+  k_sc_top<Op><<<1, 1024, 0, st>>>(op, d_n, s.tiles);
+  k_sc_emit<Op><<<(unsigned)nt, kScThreads, 0, st>>>(op, d_n, s.tiles);
+}
+
+struct UniqueOp {
+  const uint64_t* k;
+  uint64_t* out;
+  int64_t* nout;
+  __device__ uint32_t value(int64_t i) const { return i == 0 || k[i] != k[i - 1]; }
+  __device__ void emit(int64_t i, uint32_t ex, int64_t) const {
+    if (value(i)) out[ex] = k[i];
+  }
+  __device__ void finish(uint32_t total, int64_t) const { *nout = total; }
+};
+
+void launch_unique(const uint64_t* keys, const int64_t* d_n, int64_t cap, uint64_t* out,
+                   int64_t* d_nout, const ScanScratch& s, cudaStream_t st) {
+  run_scan(UniqueOp{keys, out, d_nout}, d_n, cap, s, st);
+}
+
+// Parent = key >> 3 (floor-halving of every coordinate); consecutive
+// duplicates removed; code = OR of 1 << (child key & 7) over the children.
+struct LevelOp {
+  const uint64_t* ck;
+  uint64_t* pk;
+  uint8_t* pc;
+  uint32_t* poff;
+  uint32_t* cpar;
+  int64_t* np;
+  __device__ uint32_t value(int64_t i) const { return i == 0 || (ck[i] >> 3) != (ck[i - 1] >> 3); }
+  __device__ void emit(int64_t i, uint32_t ex, int64_t n) const {
+    const uint32_t h = value(i);
+    cpar[i] = ex + h - 1;
+    if (h) {
+      const uint64_t p = ck[i] >> 3;
+      pk[ex] = p;
+      poff[ex] = (uint32_t)i;
+      uint32_t code = 0;
+      for (int64_t j = i; j < n && j < i + 8 && (ck[j] >> 3) == p; j++) code |= 1u << (ck[j] & 7);
+      pc[ex] = (uint8_t)code;
+    }
+  }
+  __device__ void finish(uint32_t total, int64_t n) const {
+    *np = total;
+    poff[total] = (uint32_t)n;
+  }
+};
+
+void launch_level_up(const uint64_t* ckeys, const int64_t* d_nc, int64_t cap_c, uint64_t* pkeys,
+                     uint8_t* pcodes, uint32_t* poff, uint32_t* cpar, int64_t* d_np,
+                     const ScanScratch& s, cudaStream_t st) {
+  run_scan(LevelOp{ckeys, pkeys, pcodes, poff, cpar, d_np}, d_nc, cap_c, s, st);
+}
+
+// Children (parent << 3 | c) for every set bit c in ascending order: parents
+// are Morton-sorted, so the children are too (no reordering).
+struct ExpandOp {
+  const uint64_t* pk;
+  const uint8_t* pc;
+  uint64_t* ck;
+  uint32_t* cpar;
+  uint32_t* poff;
+  int64_t* nc;
+  int* err;
+  __device__ uint32_t value(int64_t p) const { return __popc((uint32_t)pc[p]); }
+  __device__ void emit(int64_t p, uint32_t ex, int64_t) const {
+    poff[p] = ex;
+    const uint32_t code = pc[p];
+    if (code == 0) set_error(err, kErrExpand);
+    const uint64_t base = pk[p] << 3;
+    uint32_t r = ex;
+    for (int c = 0; c < 8; c++)
+      if (code >> c & 1) {
+        ck[r] = base | (uint64_t)c;
+        cpar[r] = (uint32_t)p;
+        r++;
+      }
+  }
+  __device__ void finish(uint32_t total, int64_t n) const {
+    *nc = total;
+    poff[n] = total;
+  }
+};
+
+void launch_expand(const uint64_t* pkeys, const uint8_t* pcodes, const int64_t* d_np,
+                   int64_t cap_p, uint64_t* ckeys, uint32_t* cpar, uint32_t* poff,
+                   int64_t* d_nc, const ScanScratch& s, int* err, cudaStream_t st) {
+  run_scan(ExpandOp{pkeys, pcodes, ckeys, cpar, poff, d_nc, err}, d_np, cap_p, s, st);
+}
+
+}  // namespace lpc

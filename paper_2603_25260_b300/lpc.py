@@ -1,0 +1,290 @@
+"""Python binding of the codec's C ABI (include/lpc.h, include/lpc_ops.h).
+
+Argument marshalling only: device tensors are passed as raw pointers
+(``tensor.data_ptr()``), every step runs inside ``liblpc.so``.  The binding
+refuses to run without the compiled library; there is no fallback path.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblpc.so")
+
+OK, INVALID_ARG, CAPACITY, HASH_FULL, CORRUPT_STREAM, WEIGHTS_MISMATCH, CUDA_ERROR, TIMEOUT = (
+    0, -1, -2, -3, -4, -5, -6, -7)
+STATUS = {0: "OK", -1: "INVALID_ARG", -2: "CAPACITY", -3: "HASH_FULL", -4: "CORRUPT_STREAM",
+          -5: "WEIGHTS_MISMATCH", -6: "CUDA_ERROR", -7: "TIMEOUT"}
+
+
+class LpcError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Config(C.Structure):
+    _fields_ = [("L", C.c_int), ("C", C.c_int), ("b_off", C.c_int), ("t_off", C.c_int),
+                ("max_points", C.c_int64), ("max_frames", C.c_int), ("chunk", C.c_int),
+                ("host_threads", C.c_int), ("cuda_stream", C.c_uint64)]
+
+
+_lib = None
+P, I64, SZ, I32 = C.c_void_p, C.c_int64, C.c_size_t, C.c_int
+
+
+def lib():
+    """Load liblpc.so (build it first with paper_2603_25260_b300.build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run paper_2603_25260_b300/build.py")
+        L = C.CDLL(LIB_PATH)
+        sig = {
+            "codec_create": (I32, [C.POINTER(Config), P, SZ, C.POINTER(P)]),
+            "codec_destroy": (None, [P]),
+            "codec_last_error": (C.c_char_p, [P]),
+            "encode_frame": (I32, [P, P, I64, P, SZ, C.POINTER(SZ)]),
+            "decode_frame": (I32, [P, P, SZ, P, I64, C.POINTER(I64)]),
+            "probs_level": (I32, [P, P, I64, I32, P, I64, C.POINTER(I64)]),
+            "encode_batch": (I32, [P, I32, P, P, P, P, P, P]),
+            "decode_batch": (I32, [P, I32, P, P, P, P, P]),
+            "codec_last_stats": (I32, [P, P, P, P]),
+            "lpc_build_levels": (I32, [P, I64, I32, P, P, P, I64, C.c_uint64]),
+            "lpc_kernel_map": (I32, [P, I64, I32, P, I32, C.c_uint64]),
+            "lpc_conv333": (I32, [P, I64, I32, P, I32, I32, P, P, P, I32, P, I32, I32, P,
+                                  C.c_uint64]),
+            "lpc_down_s2": (I32, [P, I64, P, I64, P, I32, I32, P, P, P, I32, P, I32, I32, P,
+                                  C.c_uint64]),
+            "lpc_up_prune": (I32, [P, P, I64, P, I64, P, I32, I32, P, P, P, I32, P, I32, I32, P,
+                                   C.c_uint64]),
+            "lpc_softmax_cdf": (I32, [P, I64, P, P, C.c_uint64]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _stream() -> int:
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _dev(t: torch.Tensor, dtype) -> torch.Tensor:
+    assert t.is_cuda and t.dtype == dtype and t.is_contiguous(), (t.device, t.dtype)
+    return t
+
+
+def _np(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _hp(a: np.ndarray | None):
+    return None if a is None else a.ctypes.data
+
+
+class Codec:
+    """One codec instance on the current CUDA device and stream."""
+
+    def __init__(self, blob: bytes, L: int, max_points: int, max_frames: int = 1,
+                 chunk: int = 16384, host_threads: int = 0, stream: int | None = None):
+        self._lib = lib()
+        self.blob = bytes(blob)
+        self.L = L
+        self.max_points = max_points
+        cfg = Config(L, 32, 5, 4, max_points, max_frames, chunk, host_threads,
+                     _stream() if stream is None else stream)
+        h = P()
+        st = self._lib.codec_create(C.byref(cfg), self.blob, len(self.blob), C.byref(h))
+        if st != OK:
+            raise LpcError(st, "codec_create failed")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.codec_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st: int):
+        if st != OK:
+            raise LpcError(st, self._lib.codec_last_error(self._h).decode())
+
+    def encode(self, xyz: torch.Tensor, cap: int | None = None) -> bytes:
+        xyz = _dev(xyz, torch.int32)
+        n = xyz.shape[0]
+        cap = cap if cap is not None else 1024 + 8 * n * 8
+        out = np.empty(max(cap, 1), dtype=np.uint8)
+        ln = C.c_size_t()
+        self._check(self._lib.encode_frame(self._h, xyz.data_ptr() if n else None, n,
+                                           out.ctypes.data, cap, C.byref(ln)))
+        return out[:ln.value].tobytes()
+
+    def encode_into(self, xyz: torch.Tensor, out: np.ndarray) -> int:
+        """Encode into a caller-owned host buffer; returns the length."""
+        n = xyz.shape[0]
+        ln = C.c_size_t()
+        self._check(self._lib.encode_frame(self._h, xyz.data_ptr() if n else None, n,
+                                           out.ctypes.data, out.nbytes, C.byref(ln)))
+        return ln.value
+
+    def decode(self, data: bytes, cap: int | None = None, out: torch.Tensor | None = None):
+        cap = cap if cap is not None else self.max_points
+        if out is None:
+            out = torch.empty((max(cap, 1), 3), dtype=torch.int32, device="cuda")
+        nn = C.c_int64()
+        buf = np.frombuffer(data, dtype=np.uint8) if len(data) else np.zeros(1, np.uint8)
+        self._check(self._lib.decode_frame(self._h, buf.ctypes.data, len(data), out.data_ptr(),
+                                           cap, C.byref(nn)))
+        return out[:nn.value]
+
+    def probs_level(self, xyz: torch.Tensor, d: int) -> torch.Tensor:
+        """CDF table [N_d, 256] of level d as int16 (reinterpret as uint16)."""
+        xyz = _dev(xyz, torch.int32)
+        n = xyz.shape[0]
+        cap = max(n, 1)
+        out = torch.empty((cap, 256), dtype=torch.int16, device="cuda")
+        nn = C.c_int64()
+        self._check(self._lib.probs_level(self._h, xyz.data_ptr() if n else None, n, d,
+                                          out.data_ptr(), cap, C.byref(nn)))
+        return out[:nn.value]
+
+    def encode_batch(self, frames: list[torch.Tensor], Ls: list[int]) -> list[bytes]:
+        nf = len(frames)
+        ptrs = (C.c_void_p * nf)(*[f.data_ptr() if f.shape[0] else 0 for f in frames])
+        ns = (C.c_int64 * nf)(*[f.shape[0] for f in frames])
+        ls = (C.c_int * nf)(*Ls)
+        caps = [1024 + 64 * f.shape[0] for f in frames]
+        bufs = [np.empty(c, dtype=np.uint8) for c in caps]
+        outs = (C.c_void_p * nf)(*[b.ctypes.data for b in bufs])
+        capa = (C.c_size_t * nf)(*caps)
+        lens = (C.c_size_t * nf)()
+        self._check(self._lib.encode_batch(self._h, nf, ptrs, ns, ls, outs, capa, lens))
+        return [bufs[i][:lens[i]].tobytes() for i in range(nf)]
+
+    def decode_batch(self, streams: list[bytes], caps: list[int]) -> list[torch.Tensor]:
+        nf = len(streams)
+        bufs = [np.frombuffer(s, dtype=np.uint8) for s in streams]
+        ins = (C.c_void_p * nf)(*[b.ctypes.data for b in bufs])
+        lens = (C.c_size_t * nf)(*[len(s) for s in streams])
+        outs_t = [torch.empty((max(c, 1), 3), dtype=torch.int32, device="cuda") for c in caps]
+        outs = (C.c_void_p * nf)(*[t.data_ptr() for t in outs_t])
+        capa = (C.c_int64 * nf)(*caps)
+        nout = (C.c_int64 * nf)()
+        self._check(self._lib.decode_batch(self._h, nf, ins, lens, outs, capa, nout))
+        return [outs_t[i][:nout[i]] for i in range(nf)]
+
+    def last_stats(self):
+        counts = (C.c_int64 * 32)()
+        g, h = C.c_double(), C.c_double()
+        L = self._lib.codec_last_stats(self._h, counts, C.byref(g), C.byref(h))
+        return [counts[d] for d in range(L + 1)], g.value, h.value
+
+
+# ------------------------------------------------------------------- ops --
+
+def _ops_check(st: int, what: str):
+    if st != OK:
+        raise LpcError(st, what)
+
+
+def build_levels(xyz: torch.Tensor, L: int):
+    """(keys per depth 0..L, codes per depth 0..L-1) as device tensors."""
+    xyz = _dev(xyz, torch.int32)
+    n = xyz.shape[0]
+    cap = max(1, n) * (L + 1)
+    keys = torch.empty(cap, dtype=torch.int64, device="cuda")
+    codes = torch.empty(cap, dtype=torch.uint8, device="cuda")
+    counts = np.zeros(L + 1, dtype=np.int64)
+    _ops_check(lib().lpc_build_levels(xyz.data_ptr() if n else None, n, L, keys.data_ptr(),
+                                      codes.data_ptr(), counts.ctypes.data, cap, _stream()),
+               "lpc_build_levels")
+    ks, cs, kp, cp = [], [], 0, 0
+    for d in range(L + 1):
+        N = int(counts[d])
+        ks.append(keys[kp:kp + N])
+        kp += N
+        if d < L:
+            cs.append(codes[cp:cp + N])
+            cp += N
+    return ks, cs
+
+
+def kernel_map(keys: torch.Tensor, depth: int, table_log2: int = 0) -> torch.Tensor:
+    keys = _dev(keys, torch.int64)
+    N = keys.shape[0]
+    nbr = torch.empty((max(N, 1), 27), dtype=torch.int32, device="cuda")
+    _ops_check(lib().lpc_kernel_map(keys.data_ptr() if N else None, N, depth, nbr.data_ptr(),
+                                    table_log2, _stream()), "lpc_kernel_map")
+    return nbr[:N]
+
+
+def conv333(keys, depth, x, z_in, W, bias, mult, shift, slope, z_out):
+    keys, x = _dev(keys, torch.int64), _dev(x, torch.int8)
+    N, cin = x.shape
+    W = _np(W, np.int8)
+    cout = W.shape[1]
+    out = torch.empty((max(N, 1), cout), dtype=torch.int8, device="cuda")
+    b, m = _np(bias, np.int32), _np(mult, np.int32)
+    s = None if slope is None else _np(slope, np.int16)
+    _ops_check(lib().lpc_conv333(keys.data_ptr(), N, depth, x.data_ptr(), cin, z_in, _hp(W),
+                                 _hp(b), _hp(m), shift, _hp(s), z_out, cout, out.data_ptr(),
+                                 _stream()), "lpc_conv333")
+    return out[:N]
+
+
+def down_s2(ckeys, pkeys, x, z_in, W, bias, mult, shift, slope, z_out):
+    ckeys, pkeys, x = _dev(ckeys, torch.int64), _dev(pkeys, torch.int64), _dev(x, torch.int8)
+    W = _np(W, np.int8)
+    cout = W.shape[1]
+    Np = pkeys.shape[0]
+    out = torch.empty((max(Np, 1), cout), dtype=torch.int8, device="cuda")
+    b, m = _np(bias, np.int32), _np(mult, np.int32)
+    s = None if slope is None else _np(slope, np.int16)
+    _ops_check(lib().lpc_down_s2(ckeys.data_ptr(), ckeys.shape[0], pkeys.data_ptr(), Np,
+                                 x.data_ptr(), x.shape[1], z_in, _hp(W), _hp(b), _hp(m), shift,
+                                 _hp(s), z_out, cout, out.data_ptr(), _stream()), "lpc_down_s2")
+    return out[:Np]
+
+
+def up_prune(pkeys, codes, ckeys, x, z_in, W, bias, mult, shift, slope, z_out):
+    pkeys, ckeys = _dev(pkeys, torch.int64), _dev(ckeys, torch.int64)
+    codes, x = _dev(codes, torch.uint8), _dev(x, torch.int8)
+    W = _np(W, np.int8)
+    cout = W.shape[1]
+    Nc = ckeys.shape[0]
+    out = torch.empty((max(Nc, 1), cout), dtype=torch.int8, device="cuda")
+    b, m = _np(bias, np.int32), _np(mult, np.int32)
+    s = None if slope is None else _np(slope, np.int16)
+    _ops_check(lib().lpc_up_prune(pkeys.data_ptr(), codes.data_ptr(), pkeys.shape[0],
+                                  ckeys.data_ptr(), Nc, x.data_ptr(), x.shape[1], z_in, _hp(W),
+                                  _hp(b), _hp(m), shift, _hp(s), z_out, cout, out.data_ptr(),
+                                  _stream()), "lpc_up_prune")
+    return out[:Nc]
+
+
+def softmax_cdf(logits: torch.Tensor, lut: np.ndarray) -> torch.Tensor:
+    logits = _dev(logits, torch.int8)
+    N = logits.shape[0]
+    out = torch.empty((max(N, 1), 256), dtype=torch.int16, device="cuda")
+    lut = _np(lut, np.uint32)
+    _ops_check(lib().lpc_softmax_cdf(logits.data_ptr(), N, _hp(lut), out.data_ptr(), _stream()),
+               "lpc_softmax_cdf")
+    return out[:N]
+
+
+def u16(t: torch.Tensor) -> np.ndarray:
+    """int16 device tensor -> uint16 numpy array (bit reinterpretation)."""
+    return t.cpu().numpy().view(np.uint16)

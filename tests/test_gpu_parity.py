@@ -1,0 +1,291 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Everything is integer, so every comparison is exact: level arrays, kernel
+maps (as sets of present neighbours), every layer's int8 outputs, cumulative
+tables, and whole bitstreams byte for byte.  Inputs are seeded synthetic
+frames and seeded weight blobs.
+"""
+
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2603_25260_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+O.set_threads(os.cpu_count() or 1)
+
+
+@pytest.fixture(scope="module")
+def lpc():
+    from paper_2603_25260_b300 import build, lpc as mod
+    build.build()
+    mod.lib()
+    return mod
+
+
+def _cuda(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def _params(S, cin, cout, seed, per_slice=False):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    W = rng.integers(-127, 128, size=(S, cout, cin)).astype(np.int8)
+    shape = (S, cout) if per_slice else (cout,)
+    bias = rng.integers(-(1 << 20), 1 << 20, size=shape).astype(np.int32)
+    mult = rng.integers(1, 1 << 16, size=shape).astype(np.int32)
+    slope = rng.integers(-32768, 32768, size=shape).astype(np.int16)
+    return W, bias, mult, slope
+
+
+# ------------------------------------------------------------------ levels --
+
+@pytest.mark.parametrize("n,L,seed", [(1, 6, 1), (5, 6, 2), (4097, 9, 3), (30000, 12, 4),
+                                      (20000, 21, 5), (9000, 16, 6)])
+def test_levels_match_oracle(lpc, n, L, seed):
+    xyz = synth.random_cloud(n, L, seed)
+    xyz = np.concatenate([xyz, xyz[: n // 2]])  # duplicates, out of order
+    ks, cs = lpc.build_levels(_cuda(xyz), L)
+    ok, oc = O.build_levels(xyz, L)
+    for d in range(L + 1):
+        assert np.array_equal(ks[d].cpu().numpy().view(np.uint64), ok[d])
+        if d < L:
+            assert np.array_equal(cs[d].cpu().numpy(), oc[d])
+
+
+def test_levels_config1(lpc):
+    xyz = synth.make_frame(synth.C1)
+    ks, cs = lpc.build_levels(_cuda(xyz), synth.C1.L)
+    ok, oc = O.build_levels(xyz, synth.C1.L)
+    for d in range(synth.C1.L):
+        assert np.array_equal(ks[d].cpu().numpy().view(np.uint64), ok[d])
+        assert np.array_equal(cs[d].cpu().numpy(), oc[d])
+
+
+def test_out_of_range_coordinate_is_rejected(lpc):
+    xyz = np.array([[0, 0, 0], [3, 64, 1]], dtype=np.int32)
+    with pytest.raises(lpc.LpcError) as e:
+        lpc.build_levels(_cuda(xyz), 6)
+    assert e.value.status == lpc.INVALID_ARG
+
+
+# -------------------------------------------------------------- kernel map --
+
+@pytest.mark.parametrize("n,depth,seed", [(1, 4, 1), (700, 5, 2), (5000, 7, 3), (40000, 12, 4)])
+def test_kernel_map(lpc, n, depth, seed):
+    xyz = synth.random_cloud(n, depth, seed)
+    keys = O.leaf_keys(xyz, depth)
+    nbr = lpc.kernel_map(_cuda(keys.view(np.int64)), depth).cpu().numpy()
+    pos = {int(k): i for i, k in enumerate(keys.tolist())}
+    side = 1 << depth
+    coords = np.stack([xyz[:, 0], xyz[:, 1], xyz[:, 2]], 1)
+    # brute force on the unique voxels
+    uniq = {}
+    for x, y, z in coords.tolist():
+        uniq[O.morton(x, y, z, depth)] = (x, y, z)
+    for i, k in enumerate(keys.tolist()[:3000]):
+        x, y, z = uniq[k]
+        for o in range(27):
+            qx, qy, qz = x + o // 9 - 1, y + (o // 3) % 3 - 1, z + o % 3 - 1
+            want = -1
+            if 0 <= qx < side and 0 <= qy < side and 0 <= qz < side:
+                want = pos.get(O.morton(qx, qy, qz, depth), -1)
+            assert nbr[i, o] == want
+
+
+def test_hash_full_is_reported(lpc):
+    keys = O.leaf_keys(synth.random_cloud(3000, 10, 7), 10)
+    with pytest.raises(lpc.LpcError) as e:
+        lpc.kernel_map(_cuda(keys.view(np.int64)), 10, table_log2=8)
+    assert e.value.status == lpc.HASH_FULL
+
+
+# ------------------------------------------------------------------ layers --
+
+@pytest.mark.parametrize("n,depth,cin,seed", [(1, 3, 32, 1), (333, 5, 32, 2), (4100, 8, 64, 3),
+                                              (20000, 12, 64, 4), (3000, 6, 64, 5)])
+def test_conv333(lpc, n, depth, cin, seed):
+    xyz = synth.random_cloud(n, depth, seed)
+    keys = O.leaf_keys(xyz, depth)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    x = rng.integers(-128, 128, size=(len(keys), cin)).astype(np.int8)
+    W, bias, mult, slope = _params(27, cin, 32, seed)
+    for sl, shift in ((slope, 24), (None, 20)):
+        want = O.conv333(keys, depth, x, 7, W, bias, mult, shift, sl, -5)
+        got = lpc.conv333(_cuda(keys.view(np.int64)), depth, _cuda(x), 7, W, bias, mult, shift,
+                          sl, -5).cpu().numpy()
+        assert np.array_equal(got, want)
+
+
+def test_conv333_extreme_accumulator(lpc):
+    """Worst-case magnitudes: every input at -128 with z = 127 and every
+    weight at +-127 over 27 present neighbours (|acc| near 27*64*255*127)."""
+    depth = 4
+    g = np.stack(np.meshgrid(np.arange(4), np.arange(4), np.arange(4), indexing="ij"), -1)
+    xyz = g.reshape(-1, 3).astype(np.int32) + 5
+    keys = O.leaf_keys(xyz, depth)
+    x = np.full((len(keys), 64), -128, np.int8)
+    for sign in (1, -1):
+        W = np.full((27, 32, 64), 127 * sign, np.int8)
+        bias = np.zeros(32, np.int32)
+        mult = np.full(32, 1 << 10, np.int32)
+        want = O.conv333(keys, depth, x, 127, W, bias, mult, 30, None, 0)
+        got = lpc.conv333(_cuda(keys.view(np.int64)), depth, _cuda(x), 127, W, bias, mult, 30,
+                          None, 0).cpu().numpy()
+        assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("n,depth,seed", [(1, 4, 1), (900, 6, 2), (20000, 11, 3)])
+def test_down_s2(lpc, n, depth, seed):
+    xyz = synth.random_cloud(n, depth, seed)
+    ck = O.leaf_keys(xyz, depth)
+    pk = np.unique(ck >> np.uint64(3))
+    rng = np.random.Generator(np.random.PCG64(seed))
+    x = rng.integers(-128, 128, size=(len(ck), 32)).astype(np.int8)
+    W, bias, mult, slope = _params(8, 32, 32, seed)
+    want = O.down_s2(ck, pk, x, -9, W, bias, mult, 22, slope, 4)
+    got = lpc.down_s2(_cuda(ck.view(np.int64)), _cuda(pk.view(np.int64)), _cuda(x), -9, W, bias,
+                      mult, 22, slope, 4).cpu().numpy()
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("n,depth,cin,seed", [(1, 4, 32, 1), (900, 6, 64, 2), (25000, 12, 64, 3),
+                                              (5000, 9, 32, 4)])
+def test_up_prune(lpc, n, depth, cin, seed):
+    xyz = synth.random_cloud(n, depth, seed)
+    keys, codes = O.build_levels(xyz, depth)
+    d = depth - 1
+    pk, cd, ck = keys[d], codes[d], keys[d + 1]
+    rng = np.random.Generator(np.random.PCG64(seed))
+    x = rng.integers(-128, 128, size=(len(pk), cin)).astype(np.int8)
+    W, bias, mult, slope = _params(8, cin, 32, seed, per_slice=True)
+    want = O.up_prune(pk, cd, ck, x, 3, W, bias, mult, 21, slope, -2)
+    got = lpc.up_prune(_cuda(pk.view(np.int64)), _cuda(cd), _cuda(ck.view(np.int64)), _cuda(x), 3,
+                       W, bias, mult, 21, slope, -2).cpu().numpy()
+    assert np.array_equal(got, want)
+
+
+def test_softmax_cdf(lpc):
+    rng = np.random.Generator(np.random.PCG64(3))
+    lut = synth.exp_lut()
+    lg = rng.integers(-128, 128, size=(5000, 255)).astype(np.int8)
+    lg[:1000] = np.clip(rng.normal(0, 20, size=(1000, 255)), -128, 127).astype(np.int8)
+    lg[1000] = 0
+    lg[1001] = -128
+    lg[1001, 254] = 127
+    lg[1002] = -128
+    lg[1002, [3, 200]] = 127
+    lg[1003] = 127
+    want = O.softmax_cdf(lg, lut)
+    got = lpc.u16(lpc.softmax_cdf(_cuda(lg), lut))
+    assert np.array_equal(got, want)
+
+
+# ------------------------------------------------------ whole path parity --
+
+@pytest.fixture(scope="module")
+def c1():
+    return synth.make_frame(synth.C1)
+
+
+def _codec(lpc, blob, L, n, **kw):
+    return lpc.Codec(blob, L, max(n, 16), **kw)
+
+
+def test_probs_level_config1(lpc, blob, c1):
+    L = synth.C1.L
+    cod = _codec(lpc, blob, L, c1.shape[0])
+    xyz = _cuda(c1)
+    for d in range(L - 5, L):
+        want = O.probs_level(blob, c1, L, d)
+        got = lpc.u16(cod.probs_level(xyz, d))
+        assert np.array_equal(got, want), d
+
+
+def test_encode_byte_identical_config1(lpc, blob, c1):
+    L = synth.C1.L
+    cod = _codec(lpc, blob, L, c1.shape[0])
+    assert cod.encode(_cuda(c1)) == O.encode(blob, c1, L)
+
+
+@pytest.mark.parametrize("n,L,seed,chunk", [(1, 6, 1, 16384), (2, 7, 2, 16384),
+                                            (3000, 10, 3, 100), (20000, 14, 4, 4096),
+                                            (5000, 21, 5, 16384), (12000, 12, 6, 999)])
+def test_encode_decode_random(lpc, blob, n, L, seed, chunk):
+    xyz = synth.random_cloud(n, L, seed)
+    cod = _codec(lpc, blob, L, n, chunk=chunk)
+    data = cod.encode(_cuda(xyz))
+    assert data == O.encode(blob, xyz, L, chunk)
+    dec = cod.decode(data).cpu().numpy()
+    assert np.array_equal(O.leaf_keys(dec, L), O.leaf_keys(xyz, L))
+    assert np.array_equal(dec, O.decode(blob, data, n))
+
+
+def test_cross_decode(lpc, blob, c1):
+    """Oracle stream decodes on the GPU and GPU stream decodes on the oracle."""
+    L = synth.C1.L
+    cod = _codec(lpc, blob, L, c1.shape[0])
+    so = O.encode(blob, c1, L)
+    assert np.array_equal(cod.decode(so).cpu().numpy(), O.decode(blob, so, c1.shape[0]))
+    sg = cod.encode(_cuda(c1))
+    assert np.array_equal(O.decode(blob, sg, c1.shape[0]), cod.decode(sg).cpu().numpy())
+
+
+def test_empty_and_failures(lpc, blob):
+    L = 12
+    cod = _codec(lpc, blob, L, 1000)
+    empty = cod.encode(torch.zeros((0, 3), dtype=torch.int32, device="cuda"))
+    assert empty == O.encode(blob, np.zeros((0, 3), np.int32), L)
+    assert cod.decode(empty).shape[0] == 0
+    xyz = synth.random_cloud(500, L, 3)
+    data = cod.encode(_cuda(xyz))
+    other = _codec(lpc, synth.make_blob(seed=8), L, 1000)
+    with pytest.raises(lpc.LpcError) as e:
+        other.decode(data)
+    assert e.value.status == lpc.WEIGHTS_MISMATCH
+    with pytest.raises(lpc.LpcError) as e:
+        cod.decode(data[:40])
+    assert e.value.status == lpc.CORRUPT_STREAM
+    with pytest.raises(lpc.LpcError) as e:
+        cod.decode(data, cap=10)
+    assert e.value.status == lpc.CAPACITY
+    bad = xyz.copy()
+    bad[7, 1] = 1 << L
+    with pytest.raises(lpc.LpcError) as e:
+        cod.encode(_cuda(bad))
+    assert e.value.status == lpc.INVALID_ARG
+    with pytest.raises(lpc.LpcError) as e:
+        cod.encode(_cuda(xyz), cap=10)
+    assert e.value.status == lpc.CAPACITY
+    # the codec stays usable after every failure
+    assert cod.encode(_cuda(xyz)) == data
+
+
+@pytest.mark.parametrize("spec", [synth.C2, synth.C3], ids=["kitti64_L16", "dense128_L18"])
+def test_full_size_frames_byte_identical(lpc, blob, spec):
+    xyz = synth.make_frame(spec)
+    cod = _codec(lpc, blob, spec.L, xyz.shape[0])
+    data = cod.encode(_cuda(xyz))
+    assert data == O.encode(blob, xyz, spec.L)
+    dec = cod.decode(data).cpu().numpy()
+    assert np.array_equal(O.leaf_keys(dec, spec.L), O.leaf_keys(xyz, spec.L))
+
+
+def test_batch_matches_per_frame_oracle(lpc, blob):
+    specs = synth.batch_specs(6)
+    frames = [synth.make_frame(s)[:20000] for s in specs]
+    Ls = [s.L for s in specs]
+    cod = lpc.Codec(blob, max(Ls), 20000, max_frames=len(frames))
+    outs = cod.encode_batch([_cuda(f) for f in frames], Ls)
+    for f, L, o in zip(frames, Ls, outs):
+        assert o == O.encode(blob, f, L)
+    decs = cod.decode_batch(outs, [f.shape[0] for f in frames])
+    for f, L, dcd in zip(frames, Ls, decs):
+        assert np.array_equal(O.leaf_keys(dcd.cpu().numpy(), L), O.leaf_keys(f, L))

@@ -468,3 +468,11 @@ def test_probs_level_rows_valid(blob):
         assert cdf.shape == (len(keys[d]), 256)
         C = cdf[:, :254].astype(np.int64)
         assert np.all(np.diff(C, axis=1) > 0) and np.all(C[:, 0] >= 1)
+
+
+def test_fnv1a64_published_vectors():
+    """The blob hash carried in every stream header is 64-bit FNV-1a; pinned
+    to the test vectors published with the FNV definition."""
+    assert O.fnv1a64(b"") == 0xcbf29ce484222325
+    assert O.fnv1a64(b"a") == 0xaf63dc4c8601ec8c
+    assert O.fnv1a64(b"foobar") == 0x85944171f73967e8
