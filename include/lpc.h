@@ -137,6 +137,10 @@ int codec_profile_read(codec_t* codec, int family, double* ms, int64_t* launches
                        double* ops);
 const char* codec_profile_name(int family);
 
+/* Number of CUDA kernels this library has launched in this process so far
+ * (all codecs and op entry points together). */
+int64_t lpc_kernel_launches(void);
+
 #ifdef __cplusplus
 }
 #endif

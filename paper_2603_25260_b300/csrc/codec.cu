@@ -780,6 +780,8 @@ const char* codec_profile_name(int family) {
   return family >= 0 && family < lpc::kFamCount ? names[family] : "";
 }
 
+int64_t lpc_kernel_launches(void) { return lpc::launches_total(); }
+
 int codec_last_stats(codec_t* codec, int64_t* counts, double* gpu_us, double* host_us) {
   if (!codec) return LPC_INVALID_ARG;
   const lpc::Stats& s = codec->c.stats;

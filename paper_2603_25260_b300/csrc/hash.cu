@@ -108,6 +108,7 @@ void launch_kernel_map(const uint64_t* keys, const int64_t* d_n, int64_t n_host,
   k_kernel_map<<<(int)std::min<int64_t>((n_host * 27 + 255) / 256, 148 * 16), 256, 0, st>>>(
       keys, d_n, depth, h.keys, h.vals, mask, nbr, err,
       reinterpret_cast<unsigned long long*>(pairs));
+  count_launches(3);
 }
 
 }  // namespace lpc

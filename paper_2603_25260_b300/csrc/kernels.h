@@ -9,6 +9,11 @@
 
 namespace lpc {
 
+// Process-wide count of kernel launches issued by this library (every
+// launcher adds the number of kernels it enqueues).
+void count_launches(int n);
+int64_t launches_total();
+
 // ---------------------------------------------------------------- octree --
 // Radix sort scratch for up to n_max keys.
 struct SortScratch {

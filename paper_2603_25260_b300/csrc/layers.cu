@@ -99,6 +99,7 @@ void launch_embed(const DEmb& E, const uint8_t* codes, const int64_t* d_n, int64
   if (n_host <= 0) return;
   int blocks = (int)std::min<int64_t>((2 * n_host + 255) / 256, 148 * 8);
   k_embed<<<blocks, 256, 0, st>>>(E.table, codes, d_n, out, stride, col);
+  count_launches(1);
 }
 
 // ------------------------------------------------------------- up-prune --
@@ -137,6 +138,7 @@ void launch_up_prune(const DLayer& W, const uint64_t* ckey, const uint32_t* cpar
   else
     k_up_prune<64><<<blocks, kWarps * 32, smem, st>>>(W, ckey, cpar, d_nc, x, x_stride, out,
                                                       out_stride, out_col);
+  count_launches(1);
 }
 
 // ------------------------------------------------------------ down (s2) --
@@ -177,6 +179,7 @@ void launch_down(const DLayer& W, const uint64_t* ckey, const uint32_t* poff, co
   else
     k_down<64><<<blocks, kWarps * 32, smem, st>>>(W, ckey, poff, d_np, x, x_stride, out,
                                                   out_stride, out_col);
+  count_launches(1);
 }
 
 // ------------------------------------------------------------- conv 333 --
@@ -238,6 +241,7 @@ void launch_conv333(const DLayer& W, const int32_t* nbr, const int64_t* d_n, int
     k_conv333<64><<<blocks, kWarps * 32, smem, st>>>(W, nbr, d_n, x, x_stride, out, out_stride,
                                                      out_col, r, res != nullptr, y1, y1_stride);
   }
+  count_launches(1);
 }
 
 // ------------------------------------------- integer softmax -> CDF row --
@@ -338,6 +342,7 @@ void launch_softmax_cdf(const int8_t* logits, int64_t n, const uint32_t* lut, ui
   if (n <= 0) return;
   const int blocks = (int)std::min<int64_t>((n + kWarps - 1) / kWarps, kBlocksRow);
   k_softmax_cdf<<<blocks, kWarps * 32, 0, st>>>(logits, n, lut, cdf);
+  count_launches(1);
 }
 
 // ------------------------------------------- predictor + softmax + CDF --
@@ -429,6 +434,7 @@ void launch_predictor(const DLayer& P1, const DPred2& P2, const uint32_t* lut, c
   const int blocks = (int)std::min<int64_t>((n_host + kWarps - 1) / kWarps, kBlocksRow);
   k_predictor<<<blocks, kWarps * 32, 0, st>>>(P1, P2, lut, F, f_stride, d_n, mode, codes, cdf,
                                               enc, logits);
+  count_launches(1);
 }
 
 }  // namespace lpc

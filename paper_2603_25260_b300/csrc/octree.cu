@@ -4,11 +4,16 @@
 // code -> child expansion.  Level sizes stay on the device, so a whole build
 // is queued without host round trips.
 #include <algorithm>
+#include <atomic>
 
 #include "common.cuh"
 #include "kernels.h"
 
 namespace lpc {
+
+static std::atomic<int64_t> g_launches{0};
+void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+int64_t launches_total() { return g_launches.load(std::memory_order_relaxed); }
 
 // ------------------------------------------------------------ block scan --
 // Exclusive scan of one u32 per thread over a block of NT threads.
@@ -131,6 +136,7 @@ uint64_t* radix_sort(uint64_t* keys, int64_t n, int bits, const SortScratch& s, 
     k_rs_hist<<<(unsigned)nt, kRsThreads, 0, st>>>(a, n, shift, s.hist, nt);
     k_scan_single<<<1, 1024, 0, st>>>(s.hist, 256 * nt);
     k_rs_scatter<<<(unsigned)nt, kRsThreads, 0, st>>>(a, b, n, shift, s.hist, nt);
+    count_launches(3);
     std::swap(a, b);
   }
   return a;
@@ -156,6 +162,7 @@ void launch_morton(const int32_t* xyz, int64_t n, int L, uint64_t* keys, int* er
   if (n <= 0) return;
   int blocks = (int)std::min<int64_t>((n + 255) / 256, 148 * 8);
   k_morton<<<blocks, 256, 0, st>>>(xyz, n, L, keys, err);
+  count_launches(1);
 }
 
 __global__ void k_keys_to_xyz(const uint64_t* __restrict__ keys, const int64_t* d_n,
@@ -176,6 +183,7 @@ void launch_keys_to_xyz(const uint64_t* keys, const int64_t* d_n, int64_t cap, i
   if (cap <= 0) return;
   int blocks = (int)std::min<int64_t>((cap + 255) / 256, 148 * 8);
   k_keys_to_xyz<<<blocks, 256, 0, st>>>(keys, d_n, xyz);
+  count_launches(1);
 }
 
 // ------------------------------------------------- device-size scan pass --
@@ -252,6 +260,7 @@ static void run_scan(const Op& op, const int64_t* d_n, int64_t cap, const ScanSc
   k_sc_reduce<Op><<<(unsigned)nt, kScThreads, 0, st>>>(op, d_n, s.tiles);
   k_sc_top<Op><<<1, 1024, 0, st>>>(op, d_n, s.tiles);
   k_sc_emit<Op><<<(unsigned)nt, kScThreads, 0, st>>>(op, d_n, s.tiles);
+  count_launches(3);
 }
 
 struct UniqueOp {

@@ -55,6 +55,10 @@ def lib():
             "encode_batch": (I32, [P, I32, P, P, P, P, P, P]),
             "decode_batch": (I32, [P, I32, P, P, P, P, P]),
             "codec_last_stats": (I32, [P, P, P, P]),
+            "codec_profile": (I32, [P, C.c_uint]),
+            "codec_profile_read": (I32, [P, I32, P, P, P, P]),
+            "codec_profile_name": (C.c_char_p, [I32]),
+            "lpc_kernel_launches": (I64, []),
             "lpc_build_levels": (I32, [P, I64, I32, P, P, P, I64, C.c_uint64]),
             "lpc_kernel_map": (I32, [P, I64, I32, P, I32, C.c_uint64]),
             "lpc_conv333": (I32, [P, I64, I32, P, I32, I32, P, P, P, I32, P, I32, I32, P,
@@ -186,11 +190,34 @@ class Codec:
         self._check(self._lib.decode_batch(self._h, nf, ins, lens, outs, capa, nout))
         return [outs_t[i][:nout[i]] for i in range(nf)]
 
+    FAMILIES = ("sort", "levels", "hash_kmap", "embed", "up_prune", "down_s2", "conv333",
+                "predictor_cdf")
+
+    def profile(self, mask: int):
+        """Time every launch of the kernel families in `mask` (bit i = FAMILIES[i])
+        with CUDA events on the codec's stream; resets the counters."""
+        self._check(self._lib.codec_profile(self._h, mask))
+
+    def profile_read(self) -> dict:
+        out = {}
+        for i, name in enumerate(self.FAMILIES):
+            ms, b, o = C.c_double(), C.c_double(), C.c_double()
+            n = C.c_int64()
+            self._check(self._lib.codec_profile_read(self._h, i, C.byref(ms), C.byref(n),
+                                                     C.byref(b), C.byref(o)))
+            out[name] = {"ms": ms.value, "launches": n.value, "bytes": b.value, "ops": o.value}
+        return out
+
     def last_stats(self):
         counts = (C.c_int64 * 32)()
         g, h = C.c_double(), C.c_double()
         L = self._lib.codec_last_stats(self._h, counts, C.byref(g), C.byref(h))
         return [counts[d] for d in range(L + 1)], g.value, h.value
+
+
+def kernel_launches() -> int:
+    """CUDA kernels launched by liblpc.so in this process so far."""
+    return int(lib().lpc_kernel_launches())
 
 
 # ------------------------------------------------------------------- ops --
