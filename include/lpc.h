@@ -137,6 +137,12 @@ int codec_profile_read(codec_t* codec, int family, double* ms, int64_t* launches
                        double* ops);
 const char* codec_profile_name(int family);
 
+/* Host timeline of the last encode / decode, microseconds (diagnostic):
+ * [0] octree ready, [1] launches issued, [2] coding done, [3] encode total;
+ * [4] coarse levels decoded, [5] network issue, [6] level decoding,
+ * [7] expansion issue (sums over levels), [8] decode total. */
+int codec_last_phases(codec_t* codec, double* us, int n);
+
 /* Number of CUDA kernels this library has launched in this process so far
  * (all codecs and op entry points together). */
 int64_t lpc_kernel_launches(void);

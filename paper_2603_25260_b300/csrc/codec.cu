@@ -361,7 +361,7 @@ void Codec::ensure_Fb() {
 void Codec::ensure_Ft() {
   if (have_Ft_) return;
   ensure_Fb();
-  const int b = b_, t = t_;
+  const int b = b_;
   kmap(b, nbr_b_, 0);
   conv(M_.RA[1], b, nbr_b_, 0, fb_, 32, y1_, 32, 0, nullptr);
   conv(M_.RB[1], b, nbr_b_, 0, y1_, 32, xb_, 64, 0, &M_.RM[1]);
@@ -446,6 +446,7 @@ int Codec::encode(const int32_t* d_xyz, int64_t n, uint8_t* out, size_t cap, siz
     cudaMemcpyAsync(h_err_, d_err_, 4, cudaMemcpyDeviceToHost, st_);
     if (cudaStreamSynchronize(st_) != cudaSuccess) return cuda_check("encode_frame: octree");
     if (int s = check_device_error()) return s;
+    stats.phase_us[0] = now_us() - t0;
     for (int d = 0; d <= L; d++) N_[d] = h_N_[d];
     level_bytes(L);
     // coarse codes to the host
@@ -478,6 +479,7 @@ int Codec::encode(const int32_t* d_xyz, int64_t n, uint8_t* out, size_t cap, siz
       for (int64_t s0 = 0; s0 < N_[d]; s0 += cfg_.chunk)
         tasks.push_back(Task{d, s0, std::min<int64_t>(cfg_.chunk, N_[d] - s0)});
     subs.resize(tasks.size());
+    stats.phase_us[1] = now_us() - t0;
     cudaEventSynchronize(ev_[0]);
     for (int d = 0; d < b_; d++)
       for (int64_t i = 0; i < N_[d]; i++) h_codes_[coff[d] + i] -= 1;
@@ -492,6 +494,7 @@ int Codec::encode(const int32_t* d_xyz, int64_t n, uint8_t* out, size_t cap, siz
       }
     });
     cudaEventSynchronize(ev_[1]);
+    stats.phase_us[2] = now_us() - t0;
     if (int s = check_device_error()) return s;
     prof_collect();
   }
@@ -512,6 +515,7 @@ int Codec::encode(const int32_t* d_xyz, int64_t n, uint8_t* out, size_t cap, siz
   stats.L = L;
   for (int d = 0; d <= L; d++) stats.N[d] = n > 0 ? N_[d] : 0;
   stats.host_us = now_us() - t0;
+  stats.phase_us[3] = stats.host_us;
   if (o.size() > cap) return fail(LPC_CAPACITY, "encode_frame: output buffer too small");
   memcpy(out, o.data(), o.size());
   return LPC_OK;
@@ -574,6 +578,8 @@ int Codec::decode(const uint8_t* in, size_t len, int32_t* d_out, int64_t cap, in
     if (nc > P) return fail(LPC_CAPACITY, "decode_frame: frame exceeds max_points");
     N_[d + 1] = nc;
   }
+  stats.phase_us[4] = now_us() - t0;
+  for (int i = 5; i < 9; i++) stats.phase_us[i] = 0;
   cudaMemsetAsync(d_err_, 0, 4, st_);
   cudaMemsetAsync(lv_.key[0], 0, 8, st_);
   h_N_[0] = 1;
@@ -588,6 +594,7 @@ int Codec::decode(const uint8_t* in, size_t len, int32_t* d_out, int64_t cap, in
   // network levels: full tables to the host in chunks, decoded in parallel
   for (int d = b; d < L; d++) {
     const int64_t N = N_[d];
+    double tl = now_us();
     net_level(d, kPredCdf, d_cdf_, nullptr, nullptr);
     const int64_t nch = (N + (int64_t)chunk - 1) / (int64_t)chunk;
     if ((int64_t)(si + nch) > (int64_t)nsub)
@@ -602,6 +609,8 @@ int Codec::decode(const uint8_t* in, size_t len, int32_t* d_out, int64_t cap, in
     if (int s = cuda_check("decode_frame: launch")) return s;
     coff[d] = cp;
     uint8_t* Y = h_codes_ + cp;
+    stats.phase_us[5] += now_us() - tl;
+    tl = now_us();
     std::atomic<bool> bad{false};
     const uint64_t s0 = si;
     pool_->run((int)nch, [&](int c) {
@@ -613,6 +622,8 @@ int Codec::decode(const uint8_t* in, size_t len, int32_t* d_out, int64_t cap, in
       for (int64_t i = 0; i < rows; i++) Y[r0 + i] += 1;
     });
     si += nch;
+    stats.phase_us[6] += now_us() - tl;
+    tl = now_us();
     if (bad) return fail(LPC_CORRUPT_STREAM, "decode_frame: corrupt level substream");
     int64_t nc = 0;
     for (int64_t i = 0; i < N; i++) nc += __builtin_popcount(Y[i]);
@@ -624,6 +635,7 @@ int Codec::decode(const uint8_t* in, size_t len, int32_t* d_out, int64_t cap, in
     launch_expand(lv_.key[d], lv_.code[d], d_N_ + d, lv_.cap[d], lv_.key[d + 1], lv_.par[d + 1],
                   lv_.off[d], d_N_ + d + 1, scan_, d_err_, st_);
     pend(kFamLevels, 13.0 * N + 12.0 * nc, 0);
+    stats.phase_us[7] += now_us() - tl;
   }
   if (si != nsub) return fail(LPC_CORRUPT_STREAM, "decode_frame: extra substreams");
   *n_out = N_[L];
@@ -637,6 +649,7 @@ int Codec::decode(const uint8_t* in, size_t len, int32_t* d_out, int64_t cap, in
   cudaMemcpyAsync(h_err_, d_err_, 4, cudaMemcpyDeviceToHost, st_);
   if (cudaStreamSynchronize(st_) != cudaSuccess) return cuda_check("decode_frame");
   stats.host_us = now_us() - t0;
+  stats.phase_us[8] = stats.host_us;
   prof_collect();
   return check_device_error();
 }
@@ -781,6 +794,12 @@ const char* codec_profile_name(int family) {
 }
 
 int64_t lpc_kernel_launches(void) { return lpc::launches_total(); }
+
+int codec_last_phases(codec_t* codec, double* us, int n) {
+  if (!codec || !us) return LPC_INVALID_ARG;
+  for (int i = 0; i < n && i < 16; i++) us[i] = codec->c.stats.phase_us[i];
+  return LPC_OK;
+}
 
 int codec_last_stats(codec_t* codec, int64_t* counts, double* gpu_us, double* host_us) {
   if (!codec) return LPC_INVALID_ARG;

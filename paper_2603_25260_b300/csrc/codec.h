@@ -76,6 +76,11 @@ struct Stats {
   int L = 0;
   int64_t N[kMaxDepth + 1] = {};
   double gpu_us = 0, host_us = 0;
+  // host timeline (us since the call started): encode 0 octree ready, 1 all
+  // launches issued, 2 coding done, 3 total; decode 4 coarse levels done,
+  // 5 network + copy issue (sum), 6 level decoding (sum), 7 expansion issue
+  // (sum), 8 total
+  double phase_us[16] = {};
 };
 
 class Codec {

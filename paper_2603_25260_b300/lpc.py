@@ -59,6 +59,7 @@ def lib():
             "codec_profile_read": (I32, [P, I32, P, P, P, P]),
             "codec_profile_name": (C.c_char_p, [I32]),
             "lpc_kernel_launches": (I64, []),
+            "codec_last_phases": (I32, [P, P, I32]),
             "lpc_build_levels": (I32, [P, I64, I32, P, P, P, I64, C.c_uint64]),
             "lpc_kernel_map": (I32, [P, I64, I32, P, I32, C.c_uint64]),
             "lpc_conv333": (I32, [P, I64, I32, P, I32, I32, P, P, P, I32, P, I32, I32, P,
@@ -207,6 +208,12 @@ class Codec:
                                                      C.byref(b), C.byref(o)))
             out[name] = {"ms": ms.value, "launches": n.value, "bytes": b.value, "ops": o.value}
         return out
+
+    def last_phases(self) -> list[float]:
+        """Host timeline of the last encode / decode in microseconds (see lpc.h)."""
+        us = (C.c_double * 16)()
+        self._check(self._lib.codec_last_phases(self._h, us, 16))
+        return list(us)
 
     def last_stats(self):
         counts = (C.c_int64 * 32)()
