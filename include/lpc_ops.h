@@ -39,6 +39,21 @@ int lpc_build_levels(const int32_t* d_xyz, int64_t n, int L, uint64_t* d_keys, u
 int lpc_kernel_map(const uint64_t* d_keys, int64_t N, int depth, int32_t* d_nbr, int table_log2,
                    uint64_t stream);
 
+/* Kernel map that allocates nothing (the paper has no counterpart; this is a
+ * deployment convenience).  Same inputs, output and statuses as
+ * lpc_kernel_map with automatic table size, for callers that may not call
+ * cudaMalloc at this point (a real-time loop whose memory is fixed at start-up,
+ * a component that does not own the CUDA allocator).  The voxel hash table is
+ * a file-scope device array of 2^19 slots that every GPU loading the library
+ * holds until exit; N above 262,144 nodes returns LPC_CAPACITY.  The first
+ * call on each device looks up the array's device address (make that first
+ * call before any stream capture).  All calls share the array, which keeps
+ * the previous call's contents (each call clears what it uses): calls whose
+ * GPU work overlaps race with each other and must be serialised by the
+ * caller.  Synchronises the stream before returning. */
+int lpc_kernel_map_noalloc(const uint64_t* d_keys, int64_t N, int depth, int32_t* d_nbr,
+                           uint64_t stream);
+
 /* 3x3x3 sparse conv (Eq. 13-14): out[n] = requant(prelu(bias +
  * sum_{o, present} W[o] (x[nb] - z_in))).  h_W: int8 [27][cout][cin];
  * h_bias, h_mult: int32 [cout]; h_slope: int16 [cout] Q15 or NULL (no PReLU).

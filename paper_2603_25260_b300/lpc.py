@@ -62,6 +62,7 @@ def lib():
             "codec_last_phases": (I32, [P, P, I32]),
             "lpc_build_levels": (I32, [P, I64, I32, P, P, P, I64, C.c_uint64]),
             "lpc_kernel_map": (I32, [P, I64, I32, P, I32, C.c_uint64]),
+            "lpc_kernel_map_noalloc": (I32, [P, I64, I32, P, C.c_uint64]),
             "lpc_conv333": (I32, [P, I64, I32, P, I32, I32, P, P, P, I32, P, I32, I32, P,
                                   C.c_uint64]),
             "lpc_down_s2": (I32, [P, I64, P, I64, P, I32, I32, P, P, P, I32, P, I32, I32, P,
@@ -263,6 +264,30 @@ def kernel_map(keys: torch.Tensor, depth: int, table_log2: int = 0) -> torch.Ten
     _ops_check(lib().lpc_kernel_map(keys.data_ptr() if N else None, N, depth, nbr.data_ptr(),
                                     table_log2, _stream()), "lpc_kernel_map")
     return nbr[:N]
+
+
+NOALLOC_MAX_NODES = 1 << 18
+
+
+def kernel_map_noalloc(keys: torch.Tensor, depth: int, out: torch.Tensor) -> torch.Tensor:
+    """Kernel map through the entry point that allocates no device memory.
+
+    For callers that must not allocate at this point (memory fixed at start-up,
+    allocator owned by another component).  `out` is the caller's int32
+    [N, 27] device buffer; the library's static table limits N to
+    NOALLOC_MAX_NODES.  Calls share that table, so do not overlap them on the
+    GPU."""
+    keys = _dev(keys, torch.int64)
+    out = _dev(out, torch.int32)
+    N = keys.shape[0]
+    assert out.shape[0] >= N and out.shape[1] == 27
+    st = lib().lpc_kernel_map_noalloc(keys.data_ptr() if N else None, N, depth,
+                                      out.data_ptr() if N else None, _stream())
+    if st == CAPACITY:
+        raise LpcError(st, f"lpc_kernel_map_noalloc: {N} nodes exceed the static table "
+                           f"limit of {NOALLOC_MAX_NODES}")
+    _ops_check(st, "lpc_kernel_map_noalloc")
+    return out[:N]
 
 
 def conv333(keys, depth, x, z_in, W, bias, mult, shift, slope, z_out):
