@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="kitti64_L16", choices=sorted(WORKLOADS))
-    ap.add_argument("--chunk", type=int, default=16384)
+    ap.add_argument("--chunk", type=int, default=4096)
     ap.add_argument("--batch-frames", type=int, default=64)
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -242,7 +242,7 @@ def run_ours(args):
         codec.decode(outbuf[:ln].tobytes(), out=out_dev)
         ev[k][2].record(stream)
     torch.cuda.synchronize()
-    launches = lpc.kernel_launches() - launches0
+    gpu_launches = lpc.kernel_launches() - launches0
     clk = clocks.stop()
     step_ms = [a.elapsed_time(c) for a, b, c in ev]
     enc_ms = [a.elapsed_time(b) for a, b, c in ev]
@@ -368,7 +368,7 @@ def run_ours(args):
         "batched": batched,
         "e2e": {"value": round(e2e_value, 4), "unit": "Mpoints/s",
                 "h2d_bytes_per_step": int(frame.nbytes), "d2h_bytes_per_step": int(12 * n_out)},
-        "gpu_launches": int(launches),
+        "gpu_launches": int(gpu_launches),
         "roofline": roof,
         "families": {k: {"ms": round(v["ms"], 4), "launches": v["launches"]}
                      for k, v in fams.items()},

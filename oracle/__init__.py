@@ -267,7 +267,7 @@ def logits_level(blob: bytes, xyz: np.ndarray, L: int, d: int) -> np.ndarray:
     return _level_call(lib().or_logits_level, blob, xyz, L, d, 255, np.int8, "logits_level")
 
 
-def encode(blob: bytes, xyz: np.ndarray, L: int, chunk: int = 16384) -> bytes:
+def encode(blob: bytes, xyz: np.ndarray, L: int, chunk: int = 4096) -> bytes:
     xyz = np.ascontiguousarray(xyz, dtype=np.int32)
     cap = 64 + xyz.shape[0] * 4 * 4 + 4096
     out = np.zeros(cap, dtype=np.uint8)

@@ -21,52 +21,53 @@ Pool::~Pool() {
   {
     std::lock_guard<std::mutex> g(mu_);
     stop_ = true;
-    gen_++;
   }
   cv_.notify_all();
   for (auto& t : th_) t.join();
 }
 
-void Pool::loop() {
-  uint64_t seen = 0;
-  for (;;) {
-    const std::function<void(int)>* fn;
-    int n;
-    {
-      std::unique_lock<std::mutex> lk(mu_);
-      cv_.wait(lk, [&] { return gen_ != seen; });
-      seen = gen_;
-      if (stop_) return;
-      fn = fn_;
-      n = ntasks_;
-      busy_++;
-    }
-    for (int i = next_.fetch_add(1); i < n; i = next_.fetch_add(1)) (*fn)(i);
-    {
-      std::lock_guard<std::mutex> g(mu_);
-      busy_--;
-    }
+// Runs the next queued task (lock held on entry and on return).
+bool Pool::run_one(std::unique_lock<std::mutex>& lk) {
+  if (head_ >= q_.size()) return false;
+  std::function<void()> f = std::move(q_[head_++]);
+  lk.unlock();
+  f();
+  lk.lock();
+  if (--pending_ == 0) {
+    q_.clear();
+    head_ = 0;
     done_.notify_all();
+  }
+  return true;
+}
+
+void Pool::loop() {
+  std::unique_lock<std::mutex> lk(mu_);
+  for (;;) {
+    cv_.wait(lk, [&] { return stop_ || head_ < q_.size(); });
+    if (stop_) return;
+    run_one(lk);
   }
 }
 
-void Pool::run(int ntasks, const std::function<void(int)>& fn) {
-  if (ntasks <= 0) return;
-  if (th_.empty() || ntasks == 1) {
-    for (int i = 0; i < ntasks; i++) fn(i);
+void Pool::submit(std::function<void()> task) {
+  if (th_.empty()) {
+    task();
     return;
   }
   {
     std::lock_guard<std::mutex> g(mu_);
-    fn_ = &fn;
-    ntasks_ = ntasks;
-    next_.store(0);
-    gen_++;
+    q_.push_back(std::move(task));
+    pending_++;
   }
-  cv_.notify_all();
-  for (int i = next_.fetch_add(1); i < ntasks; i = next_.fetch_add(1)) fn(i);
+  cv_.notify_one();
+}
+
+void Pool::wait() {
   std::unique_lock<std::mutex> lk(mu_);
-  done_.wait(lk, [&] { return busy_ == 0 && next_.load() >= ntasks; });
+  while (pending_ > 0) {
+    if (!run_one(lk)) done_.wait(lk, [&] { return pending_ == 0 || head_ < q_.size(); });
+  }
 }
 
 // ------------------------------------------------------------ bitstream --
@@ -195,9 +196,15 @@ int Codec::create(const lpc_config& cfg, const void* blob, size_t len) {
     off += (x.bytes + 255) / 256 * 256;
   }
   // ---- pinned host workspace ----
+  // The coded substreams of one frame fit in 2 bytes per symbol plus 8 per
+  // substream (coded_bound); the arena is pinned so that host threads write
+  // it without page faults.
+  const int64_t max_subs = L + (5 * P) / cfg.chunk + 5;
+  arena_cap_ = (size_t)2 * (L + 1) * P + (size_t)8 * max_subs + 1024;
   const size_t hN = 8 * (kMaxDepth + 2), hE = 16, hC = (size_t)(L + 1) * P + 64,
                hEnc = (size_t)4 * 5 * P, hCdf = (size_t)512 * P;
-  const size_t htotal = hN + hE + (hC + 255) / 256 * 256 + hEnc + hCdf + 1024;
+  const size_t hA = (arena_cap_ + 255) / 256 * 256;
+  const size_t htotal = hN + hE + (hC + 255) / 256 * 256 + hEnc + hCdf + hA + 1024;
   if (cudaMallocHost(&hmem_, htotal) != cudaSuccess) {
     cudaGetLastError();
     hmem_ = nullptr;
@@ -209,6 +216,7 @@ int Codec::create(const lpc_config& cfg, const void* blob, size_t len) {
   h_codes_ = h + hN + hE;
   h_enc_ = reinterpret_cast<uint32_t*>(h + hN + hE + (hC + 255) / 256 * 256);
   h_cdf_ = reinterpret_cast<uint16_t*>(reinterpret_cast<uint8_t*>(h_enc_) + hEnc);
+  h_arena_ = reinterpret_cast<uint8_t*>(h_cdf_) + hCdf;
   const int nev = (int)(P / cfg.chunk) + 8;
   ev_.resize(nev);
   for (auto& e : ev_) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
@@ -439,7 +447,6 @@ int Codec::encode(const int32_t* d_xyz, int64_t n, uint8_t* out, size_t cap, siz
   const int L = cfg_.L;
   begin_frame(L);
   const double t0 = now_us();
-  std::vector<std::vector<uint8_t>> subs;
   if (n > 0) {
     build_octree(d_xyz, n, L);
     cudaMemcpyAsync(h_N_, d_N_, 8 * (L + 1), cudaMemcpyDeviceToHost, st_);
@@ -457,67 +464,92 @@ int Codec::encode(const int32_t* d_xyz, int64_t n, uint8_t* out, size_t cap, siz
       pos += N_[d];
     }
     cudaEventRecord(ev_[0], st_);
-    // network levels: (C_s, f_s) of the true symbol of every node
+    // network levels: (C_s, f_s) of the true symbol of every node; each
+    // level's intervals go to the host as soon as that level is done, so the
+    // host codes level d while the device computes level d + 1
     int64_t eoff[kMaxDepth + 1], ep = 0;
     for (int d = b_; d < L; d++) {
       eoff[d] = ep;
       net_level(d, kPredEnc, nullptr, d_enc_ + ep, nullptr);
+      cudaMemcpyAsync(h_enc_ + ep, d_enc_ + ep, 4 * N_[d], cudaMemcpyDeviceToHost, st_);
+      cudaEventRecord(ev_[1 + d - b_], st_);
       ep += N_[d];
     }
-    cudaMemcpyAsync(h_enc_, d_enc_, 4 * ep, cudaMemcpyDeviceToHost, st_);
     cudaMemcpyAsync(h_err_, d_err_, 4, cudaMemcpyDeviceToHost, st_);
-    cudaEventRecord(ev_[1], st_);
+    cudaEventRecord(ev_[1 + L - b_], st_);
     if (int s = cuda_check("encode_frame: launch")) return s;
-    // substreams
-    struct Task {
-      int d;
-      int64_t start, count;
+    // substreams: coarse levels (one each), then chunks of the network levels
+    tasks_.clear();
+    size_t ao = 0;
+    auto add_task = [&](int d, int64_t s0, int64_t cnt) {
+      tasks_.push_back(SubTask{d, s0, cnt, ao, 0});
+      ao += coded_bound((size_t)cnt);
     };
-    std::vector<Task> tasks;
-    for (int d = 0; d < b_; d++) tasks.push_back(Task{d, 0, N_[d]});
+    for (int d = 0; d < b_; d++) add_task(d, 0, N_[d]);
     for (int d = b_; d < L; d++)
       for (int64_t s0 = 0; s0 < N_[d]; s0 += cfg_.chunk)
-        tasks.push_back(Task{d, s0, std::min<int64_t>(cfg_.chunk, N_[d] - s0)});
-    subs.resize(tasks.size());
+        add_task(d, s0, std::min<int64_t>(cfg_.chunk, N_[d] - s0));
+    if (ao > arena_cap_) return fail(LPC_CAPACITY, "encode_frame: coding arena too small");
     stats.phase_us[1] = now_us() - t0;
+    // coarse levels are coded while the device runs the network
     cudaEventSynchronize(ev_[0]);
     for (int d = 0; d < b_; d++)
       for (int64_t i = 0; i < N_[d]; i++) h_codes_[coff[d] + i] -= 1;
-    pool_->run((int)tasks.size(), [&](int i) {
-      const Task& T = tasks[i];
-      subs[i].reserve((size_t)T.count + 16);
-      if (T.d < b_) {
-        encode_adaptive(h_codes_ + coff[T.d], (size_t)T.count, &subs[i]);
-      } else {
-        cudaEventSynchronize(ev_[1]);
-        encode_packed(h_enc_ + eoff[T.d] + T.start, (size_t)T.count, &subs[i]);
+    for (int i = b_ - 1; i >= 0; i--) {  // largest level first
+      pool_->submit([this, i, &coff] {
+        SubTask& T = tasks_[i];
+        T.len = encode_adaptive(h_codes_ + coff[T.d], (size_t)T.count, h_arena_ + T.arena,
+                                coded_bound((size_t)T.count));
+      });
+    }
+    int level_done = b_ - 1;
+    for (size_t i = b_; i < tasks_.size(); i++) {
+      while (level_done < tasks_[i].d) {
+        level_done++;
+        cudaEventSynchronize(ev_[1 + level_done - b_]);
       }
-    });
-    cudaEventSynchronize(ev_[1]);
+      pool_->submit([this, i, &eoff] {
+        SubTask& T = tasks_[i];
+        T.len = encode_packed(h_enc_ + eoff[T.d] + T.start, (size_t)T.count, h_arena_ + T.arena,
+                              coded_bound((size_t)T.count));
+      });
+    }
+    cudaEventSynchronize(ev_[1 + L - b_]);
+    pool_->wait();
     stats.phase_us[2] = now_us() - t0;
     if (int s = check_device_error()) return s;
     prof_collect();
+  } else {
+    tasks_.clear();
   }
-  // assemble
-  std::vector<uint8_t> o;
-  size_t body = 0;
-  for (auto& s : subs) body += s.size();
-  o.reserve(kHdr + 16 + 5 * subs.size() + body);
+  // assemble straight into the caller's buffer
+  uint8_t head[kHdr + 32];
   const uint8_t hdr[10] = {'L', 'P', 'C', '1', 1, (uint8_t)L, (uint8_t)b_, (uint8_t)t_,
                            (uint8_t)M_.C, (uint8_t)(n > 0 ? 0 : 1)};
-  o.insert(o.end(), hdr, hdr + 10);
-  for (int i = 0; i < 8; i++) o.push_back((uint8_t)(M_.hash >> (8 * i)));
-  put_varint(o, (uint64_t)cfg_.chunk);
-  put_varint(o, subs.size());
-  for (auto& s : subs) put_varint(o, s.size());
-  for (auto& s : subs) o.insert(o.end(), s.begin(), s.end());
-  *out_len = o.size();
+  memcpy(head, hdr, 10);
+  for (int i = 0; i < 8; i++) head[10 + i] = (uint8_t)(M_.hash >> (8 * i));
+  std::vector<uint8_t> table;
+  put_varint(table, (uint64_t)cfg_.chunk);
+  put_varint(table, tasks_.size());
+  size_t body = 0;
+  for (const SubTask& T : tasks_) {
+    put_varint(table, T.len);
+    body += T.len;
+  }
+  const size_t total = kHdr + table.size() + body;
+  *out_len = total;
   stats.L = L;
   for (int d = 0; d <= L; d++) stats.N[d] = n > 0 ? N_[d] : 0;
+  if (total > cap) return fail(LPC_CAPACITY, "encode_frame: output buffer too small");
+  memcpy(out, head, kHdr);
+  memcpy(out + kHdr, table.data(), table.size());
+  uint8_t* p = out + kHdr + table.size();
+  for (const SubTask& T : tasks_) {
+    memcpy(p, h_arena_ + T.arena, T.len);
+    p += T.len;
+  }
   stats.host_us = now_us() - t0;
   stats.phase_us[3] = stats.host_us;
-  if (o.size() > cap) return fail(LPC_CAPACITY, "encode_frame: output buffer too small");
-  memcpy(out, o.data(), o.size());
   return LPC_OK;
 }
 
@@ -580,16 +612,30 @@ int Codec::decode(const uint8_t* in, size_t len, int32_t* d_out, int64_t cap, in
   }
   stats.phase_us[4] = now_us() - t0;
   for (int i = 5; i < 9; i++) stats.phase_us[i] = 0;
-  cudaMemsetAsync(d_err_, 0, 4, st_);
-  cudaMemsetAsync(lv_.key[0], 0, 8, st_);
-  h_N_[0] = 1;
-  cudaMemcpyAsync(d_N_, h_N_, 8, cudaMemcpyHostToDevice, st_);
-  for (int d = 0; d < b; d++) {
-    cudaMemcpyAsync(lv_.code[d], h_codes_ + coff[d], N_[d], cudaMemcpyHostToDevice, st_);
+  // the coarse levels are tiny: expand them on the host up to V_{b-1} and
+  // upload only V_{b-1} and Y_{b-1}; the device expands V_b from there
+  {
+    uint64_t* keys = reinterpret_cast<uint64_t*>(h_cdf_);  // pinned staging, free here
+    uint64_t* tmp = keys + P;
+    keys[0] = 0;
+    for (int d = 0; d + 1 < b; d++) {
+      const uint8_t* Y = h_codes_ + coff[d];
+      int64_t r = 0;
+      for (int64_t p = 0; p < N_[d]; p++)
+        for (int c = 0; c < 8; c++)
+          if (Y[p] >> c & 1) tmp[r++] = (keys[p] << 3) | (uint64_t)c;
+      std::swap(keys, tmp);
+    }
+    cudaMemsetAsync(d_err_, 0, 4, st_);
+    h_N_[b - 1] = N_[b - 1];
+    cudaMemcpyAsync(d_N_ + b - 1, h_N_ + b - 1, 8, cudaMemcpyHostToDevice, st_);
+    cudaMemcpyAsync(lv_.key[b - 1], keys, 8 * N_[b - 1], cudaMemcpyHostToDevice, st_);
+    cudaMemcpyAsync(lv_.code[b - 1], h_codes_ + coff[b - 1], N_[b - 1], cudaMemcpyHostToDevice,
+                    st_);
     pbeg(kFamLevels);
-    launch_expand(lv_.key[d], lv_.code[d], d_N_ + d, lv_.cap[d], lv_.key[d + 1], lv_.par[d + 1],
-                  lv_.off[d], d_N_ + d + 1, scan_, d_err_, st_);
-    pend(kFamLevels, 13.0 * N_[d] + 12.0 * N_[d + 1], 0);
+    launch_expand(lv_.key[b - 1], lv_.code[b - 1], d_N_ + b - 1, lv_.cap[b - 1], lv_.key[b],
+                  lv_.par[b], lv_.off[b - 1], d_N_ + b, scan_, d_err_, st_);
+    pend(kFamLevels, 13.0 * N_[b - 1] + 12.0 * N_[b], 0);
   }
   // network levels: full tables to the host in chunks, decoded in parallel
   for (int d = b; d < L; d++) {
@@ -613,14 +659,17 @@ int Codec::decode(const uint8_t* in, size_t len, int32_t* d_out, int64_t cap, in
     tl = now_us();
     std::atomic<bool> bad{false};
     const uint64_t s0 = si;
-    pool_->run((int)nch, [&](int c) {
-      const int64_t r0 = c * (int64_t)chunk, rows = std::min<int64_t>((int64_t)chunk, N - r0);
+    for (int64_t c = 0; c < nch; c++) {  // each chunk is decoded as soon as its table lands
       cudaEventSynchronize(ev_[c]);
-      if (!decode_rows(h_cdf_ + r0 * 256, (size_t)rows, in + soff[s0 + c], (size_t)slen[s0 + c],
-                       Y + r0))
-        bad = true;
-      for (int64_t i = 0; i < rows; i++) Y[r0 + i] += 1;
-    });
+      pool_->submit([&, c] {
+        const int64_t r0 = c * (int64_t)chunk, rows = std::min<int64_t>((int64_t)chunk, N - r0);
+        if (!decode_rows(h_cdf_ + r0 * 256, (size_t)rows, in + soff[s0 + c],
+                         (size_t)slen[s0 + c], Y + r0))
+          bad = true;
+        for (int64_t i = 0; i < rows; i++) Y[r0 + i] += 1;
+      });
+    }
+    pool_->wait();
     si += nch;
     stats.phase_us[6] += now_us() - tl;
     tl = now_us();

@@ -19,24 +19,26 @@
 
 namespace lpc {
 
-// Minimal fork-join pool: run(n, fn) calls fn(0..n-1) on the workers and the
-// calling thread, and returns when all calls are done.
+// Host task queue: the calling thread submits tasks as their inputs become
+// ready (it alone waits on CUDA events), workers run them; wait() helps run
+// queued tasks and returns when every submitted task has finished.
 class Pool {
  public:
   explicit Pool(int workers);
   ~Pool();
-  void run(int ntasks, const std::function<void(int)>& fn);
+  void submit(std::function<void()> task);
+  void wait();
   int size() const { return (int)th_.size() + 1; }
 
  private:
   void loop();
+  bool run_one(std::unique_lock<std::mutex>& lk);
   std::vector<std::thread> th_;
   std::mutex mu_;
   std::condition_variable cv_, done_;
-  const std::function<void(int)>* fn_ = nullptr;
-  int ntasks_ = 0, busy_ = 0;
-  std::atomic<int> next_{0};
-  uint64_t gen_ = 0;
+  std::vector<std::function<void()>> q_;
+  size_t head_ = 0;
+  int pending_ = 0;  // submitted and not finished
   bool stop_ = false;
 };
 
@@ -165,6 +167,14 @@ class Codec {
   uint8_t* h_codes_ = nullptr;  // coarse codes / decoded codes (max_points * 2)
   uint32_t* h_enc_ = nullptr;
   uint16_t* h_cdf_ = nullptr;
+  uint8_t* h_arena_ = nullptr;  // pinned, pre-faulted: coded substreams
+  size_t arena_cap_ = 0;
+  struct SubTask {
+    int d;
+    int64_t start, count;
+    size_t arena, len;
+  };
+  std::vector<SubTask> tasks_;
   std::vector<cudaEvent_t> ev_;
 };
 

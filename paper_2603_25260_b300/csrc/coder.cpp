@@ -7,7 +7,7 @@ void RangeEncoder::shift_low() {
     const uint8_t carry = (uint8_t)(low_ >> 32);
     uint8_t b = cache_;
     for (; pending_ > 0; pending_--) {
-      out_->push_back((uint8_t)(b + carry));
+      put((uint8_t)(b + carry));
       b = 0xFF;
     }
     cache_ = (uint8_t)(low_ >> 24);
@@ -111,22 +111,37 @@ int AdaptiveModel::decode(RangeDecoder& d) {
   return pos;
 }
 
-void encode_packed(const uint32_t* lofreq, size_t n, std::vector<uint8_t>* out) {
-  RangeEncoder e(out);
+size_t encode_packed(const uint32_t* lofreq, size_t n, uint8_t* out, size_t cap) {
+  RangeEncoder e(out, cap);
   for (size_t i = 0; i < n; i++) e.code16(lofreq[i] & 0xFFFFu, lofreq[i] >> 16);
   e.finish();
+  return e.size();
 }
 
-void encode_adaptive(const uint8_t* syms, size_t n, std::vector<uint8_t>* out) {
-  RangeEncoder e(out);
+size_t encode_adaptive(const uint8_t* syms, size_t n, uint8_t* out, size_t cap) {
+  RangeEncoder e(out, cap);
   AdaptiveModel m;
   for (size_t i = 0; i < n; i++) m.encode(e, syms[i]);
   e.finish();
+  return e.size();
+}
+
+// The tables were just written to host memory by DMA, so they are not in any
+// CPU cache: the eight 64-byte lines of a row are prefetched a few rows ahead
+// of the binary search.
+static inline void prefetch_row(const uint16_t* row) {
+  const char* p = reinterpret_cast<const char*>(row);
+  for (int k = 0; k < 512; k += 64) __builtin_prefetch(p + k, 0, 3);
 }
 
 bool decode_rows(const uint16_t* rows, size_t n, const uint8_t* in, size_t len, uint8_t* syms) {
+  constexpr size_t kAhead = 8;
   RangeDecoder d(in, len);
-  for (size_t i = 0; i < n; i++) syms[i] = (uint8_t)d.decode_row(rows + i * 256);
+  for (size_t i = 0; i < n && i < kAhead; i++) prefetch_row(rows + i * 256);
+  for (size_t i = 0; i < n; i++) {
+    if (i + kAhead < n) prefetch_row(rows + (i + kAhead) * 256);
+    syms[i] = (uint8_t)d.decode_row(rows + i * 256);
+  }
   return !d.bad();
 }
 

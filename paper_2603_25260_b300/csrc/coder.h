@@ -13,9 +13,13 @@
 
 namespace lpc {
 
+// Writes into a caller-provided byte range; bytes past `cap` are counted but
+// not stored (overflow() reports it).
 class RangeEncoder {
  public:
-  explicit RangeEncoder(std::vector<uint8_t>* out) : out_(out) {}
+  RangeEncoder(uint8_t* out, size_t cap) : out_(out), cap_(cap) {}
+  size_t size() const { return len_; }
+  bool overflow() const { return len_ > cap_; }
   // Code the interval [lo, lo + f) of a total 2^16.
   inline void code16(uint32_t lo, uint32_t f) { code(range_ >> 16, lo, f); }
   // Code the interval [lo, lo + f) of an arbitrary total (<= 2^16).
@@ -32,7 +36,12 @@ class RangeEncoder {
     }
   }
   void shift_low();
-  std::vector<uint8_t>* out_;
+  inline void put(uint8_t b) {
+    if (len_ < cap_) out_[len_] = b;
+    len_++;
+  }
+  uint8_t* out_;
+  size_t cap_, len_ = 0;
   uint64_t low_ = 0;
   uint32_t range_ = 0xFFFFFFFFu;
   uint8_t cache_ = 0;
@@ -85,10 +94,14 @@ class AdaptiveModel {
   uint32_t total_;
 };
 
-// Encode symbols with per-node (lo, f) pairs packed as lo | f << 16.
-void encode_packed(const uint32_t* lofreq, size_t n, std::vector<uint8_t>* out);
+// Upper bound of the coded size of n symbols: every coded interval is at
+// least 2^-16 of the range (at most 2 bytes per symbol) plus the flush.
+inline size_t coded_bound(size_t n) { return 2 * n + 8; }
+// Encode symbols with per-node (lo, f) pairs packed as lo | f << 16 into
+// out[0..cap); returns the byte count (> cap means overflow).
+size_t encode_packed(const uint32_t* lofreq, size_t n, uint8_t* out, size_t cap);
 // Encode symbols with the adaptive model (one model per substream).
-void encode_adaptive(const uint8_t* syms, size_t n, std::vector<uint8_t>* out);
+size_t encode_adaptive(const uint8_t* syms, size_t n, uint8_t* out, size_t cap);
 // Decode n symbols with table rows; returns false on a corrupt stream.
 bool decode_rows(const uint16_t* rows, size_t n, const uint8_t* in, size_t len, uint8_t* syms);
 bool decode_adaptive(size_t n, const uint8_t* in, size_t len, uint8_t* syms);

@@ -100,7 +100,7 @@ class Codec:
     """One codec instance on the current CUDA device and stream."""
 
     def __init__(self, blob: bytes, L: int, max_points: int, max_frames: int = 1,
-                 chunk: int = 16384, host_threads: int = 0, stream: int | None = None):
+                 chunk: int = 4096, host_threads: int = 0, stream: int | None = None):
         self._lib = lib()
         self.blob = bytes(blob)
         self.L = L
