@@ -175,6 +175,8 @@ int Codec::create(const lpc_config& cfg, const void* blob, size_t len) {
   add((void**)&xb_, 64 * P);
   add((void**)&xt_, 64 * P);
   add((void**)&y1_, 32 * P);
+  add((void**)&xb16_, 2 * 64 * P);
+  add((void**)&y1b16_, 2 * 32 * P);
   add((void**)&xe_, 32 * P);
   add((void**)&g_[0], 32 * P);
   add((void**)&g_[1], 32 * P);
@@ -246,6 +248,7 @@ void Codec::level_bytes(int L) {
 }
 
 int Codec::check_device_error() {
+  if (conv_tc_error(true)) return fail(LPC_TIMEOUT, "tensor-core conv gave up on a bounded wait");
   const int e = *h_err_;
   if (e == 0) return LPC_OK;
   if (e == kErrCoord) return fail(LPC_INVALID_ARG, "coordinate outside [0, 2^L)");
@@ -340,12 +343,53 @@ void Codec::up(const DLayer& W, int d, const int8_t* x, int xs, int8_t* out, int
        2.0 * N_[d + 1] * W.cin * 32);
 }
 
-void Codec::conv(const DLayer& W, int d, const int32_t* nbr, int slot, const int8_t* x, int xs,
-                 int8_t* out, int os, int oc, const DRes* res) {
+// int8 activations -> bf16 (q - z) rows, the tensor-core conv's input
+void Codec::to_bf16(const int8_t* x, int xs, int cols, int z, int d) {
+  pbeg(kFamEmbed);
+  launch_to_bf16(x, xs, cols, z, d_N_ + d, N_[d], xb16_, st_);
+  pend(kFamEmbed, 3.0 * cols * N_[d], 0);
+}
+
+// 3x3x3 conv on V_d: bf16 input rows xb (stride xbs elements); with res the
+// residual merge reads y1_; outb (optional) gets the next conv's bf16 input.
+void Codec::conv(const DLayer& W, int d, const int32_t* nbr, int slot, const void* xb, int xbs,
+                 int8_t* out, int os, int oc, const DRes* res, void* outb, int outb_z) {
+  ConvTcArgs a{};
+  a.wimg = W.Wtc;
+  a.bias = W.bias;
+  a.mult = W.mult;
+  a.slope = W.slope;
+  a.prelu = W.prelu;
+  a.shift = W.shift;
+  a.z_out = W.z_out;
+  a.nbr = nbr;
+  a.d_n = d_N_ + d;
+  a.xb = xb;
+  a.x_stride = xbs;
+  a.out = out;
+  a.out_stride = os;
+  a.out_col = oc;
+  a.outb = outb;
+  a.outb_stride = 32;
+  a.outb_z = outb_z;
+  if (res) {
+    a.has_res = 1;
+    a.y1 = y1_;
+    a.y1_stride = 32;
+    a.res_mab = res->mab;
+    a.res_slope = res->slope;
+    a.res_z1 = res->z1;
+    a.res_z2 = res->z2;
+    a.res_z_out = res->z_out;
+    a.res_shift = res->shift;
+  }
   pbeg(kFamConv);
-  launch_conv333(W, nbr, d_N_ + d, N_[d], x, xs, out, os, oc, res, res ? y1_ : nullptr, 32, st_);
-  pend(kFamConv, 32.0 * N_[d] * (res ? 2 : 1) + 27.0 * W.cin * 32, 0, slot, 2.0 * W.cin * 32,
-       (double)W.cin + 4.0);
+  launch_conv333_tc(a, W.cin, N_[d], st_);
+  // per neighbour pair: 2 Cin C ops and 2 Cin bytes gathered; per node: the
+  // int8 output (+ the residual's y1 and the bf16 copy when present)
+  pend(kFamConv,
+       N_[d] * (32.0 + (res ? 32.0 : 0.0) + (outb ? 64.0 : 0.0)) + 27.0 * W.cin * 32 * 2, 0,
+       slot, 2.0 * W.cin * 32, 2.0 * W.cin + 4.0);
 }
 
 void Codec::kmap(int d, int32_t* nbr, int slot) {
@@ -371,8 +415,9 @@ void Codec::ensure_Ft() {
   ensure_Fb();
   const int b = b_;
   kmap(b, nbr_b_, 0);
-  conv(M_.RA[1], b, nbr_b_, 0, fb_, 32, y1_, 32, 0, nullptr);
-  conv(M_.RB[1], b, nbr_b_, 0, y1_, 32, xb_, 64, 0, &M_.RM[1]);
+  to_bf16(fb_, 32, 32, M_.RA[1].z_in, b);
+  conv(M_.RA[1], b, nbr_b_, 0, xb16_, 32, y1_, 32, 0, nullptr, y1b16_, M_.RB[1].z_in);
+  conv(M_.RB[1], b, nbr_b_, 0, y1b16_, 32, xb_, 64, 0, &M_.RM[1], nullptr, 0);
   embed(M_.E1, b, xb_, 64, 32);
   up(M_.UP1, b, xb_, 64, xt_, 64);
   have_Ft_ = true;
@@ -424,8 +469,9 @@ void Codec::net_level(int d, int mode, uint16_t* cdf, uint32_t* enc, int8_t* log
     }
   }
   // H^t = ResBlock(Concat(F^t, G^t)) (Eq. 10)
-  conv(M_.RA[j], t_, nbr_t_, 1, xt_, 64, y1_, 32, 0, nullptr);
-  conv(M_.RB[j], t_, nbr_t_, 1, y1_, 32, hx_[0], 64, 0, &M_.RM[j]);
+  to_bf16(xt_, 64, 64, M_.RA[j].z_in, t_);
+  conv(M_.RA[j], t_, nbr_t_, 1, xb16_, 64, y1_, 32, 0, nullptr, y1b16_, M_.RB[j].z_in);
+  conv(M_.RB[j], t_, nbr_t_, 1, y1b16_, 32, hx_[0], 64, 0, &M_.RM[j], nullptr, 0);
   // F^{k+1} = Pruning(Upsampling(Concat(H^k, Y_k)), Y_k), k = t..d-1 (Eq. 11)
   int cur = 0;
   for (int k = t_; k < d; k++) {

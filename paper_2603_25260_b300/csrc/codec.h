@@ -115,8 +115,9 @@ class Codec {
   void level_bytes(int L);
   void embed(const DEmb& E, int d, int8_t* out, int stride, int col);
   void up(const DLayer& W, int d, const int8_t* x, int xs, int8_t* out, int os);
-  void conv(const DLayer& W, int d, const int32_t* nbr, int slot, const int8_t* x, int xs,
-            int8_t* out, int os, int oc, const DRes* res);
+  void to_bf16(const int8_t* x, int xs, int cols, int z, int d);
+  void conv(const DLayer& W, int d, const int32_t* nbr, int slot, const void* xb, int xbs,
+            int8_t* out, int os, int oc, const DRes* res, void* outb, int outb_z);
   void kmap(int d, int32_t* nbr, int slot);
   void ensure_Fb();
   void ensure_Ft();
@@ -158,6 +159,7 @@ class Codec {
   int32_t *nbr_b_ = nullptr, *nbr_t_ = nullptr;
   int8_t *fb_ = nullptr, *xb_ = nullptr, *xt_ = nullptr, *y1_ = nullptr, *xe_ = nullptr;
   int8_t *g_[2] = {}, *hx_[2] = {}, *fo_ = nullptr;
+  void *xb16_ = nullptr, *y1b16_ = nullptr;  // bf16 (q - z) inputs of the convs
   uint16_t* d_cdf_ = nullptr;
   uint32_t* d_enc_ = nullptr;
   // pinned host workspace

@@ -76,6 +76,7 @@ struct DLayer {
   const int32_t* bias;   // [P][cout], P = S if per_slice else 1
   const int32_t* mult;   // [P][cout]
   const int16_t* slope;  // [P][cout]
+  const uint16_t* Wtc;   // 27-slice layers: packed bf16 weights for the tensor cores
 };
 struct DEmb {
   int cout, z_out;
@@ -111,11 +112,40 @@ void launch_down(const DLayer& W, const uint64_t* ckey, const uint32_t* poff, co
                  int64_t np_host, const int8_t* x, int x_stride, int8_t* out, int out_stride,
                  int out_col, cudaStream_t st);
 
-// 3x3x3 conv over the kernel map; with res != nullptr the residual merge of
-// the ResBlock is fused into the epilogue (y1 = the first conv's output).
-void launch_conv333(const DLayer& W, const int32_t* nbr, const int64_t* d_n, int64_t n_host,
-                    const int8_t* x, int x_stride, int8_t* out, int out_stride, int out_col,
-                    const DRes* res, const int8_t* y1, int y1_stride, cudaStream_t st);
+// 3x3x3 conv on the tcgen05 tensor cores (conv_tc.cu).  Inputs are bf16 rows
+// holding (q - z_in); absent neighbours contribute zero.  With has_res the
+// ResBlock's residual merge is fused into the epilogue (y1 = the first conv's
+// int8 output).  outb (optional) receives bf16 (q - outb_z) rows for the next
+// conv.
+struct ConvTcArgs {
+  const uint16_t* wimg;  // packed weights, conv_tc_weight_bytes(cin)
+  const int32_t* bias;
+  const int32_t* mult;
+  const int16_t* slope;
+  int prelu, shift, z_out;
+  const int32_t* nbr;
+  const int64_t* d_n;
+  const void* xb;
+  int x_stride;  // elements
+  int8_t* out;
+  int out_stride, out_col;
+  void* outb;
+  int outb_stride, outb_z;
+  int has_res;
+  const int8_t* y1;
+  int y1_stride;
+  const int32_t* res_mab;
+  const int16_t* res_slope;
+  int res_z1, res_z2, res_z_out, res_shift;
+};
+size_t conv_tc_weight_bytes(int cin);
+void pack_conv_tc_weights(const int8_t* W, int cin, uint16_t* img);
+void launch_conv333_tc(const ConvTcArgs& a, int cin, int64_t n_host, cudaStream_t st);
+// int8 rows (stride x_stride) -> bf16 (q - z) rows of `cols` elements.
+void launch_to_bf16(const int8_t* x, int x_stride, int cols, int z, const int64_t* d_n,
+                    int64_t n_host, void* out, cudaStream_t st);
+// Non-zero if a tensor-core conv gave up on a bounded wait (optionally reset).
+int conv_tc_error(bool reset);
 
 // Predictor + integer softmax + cumulative table.
 enum PredMode { kPredCdf = 0, kPredEnc = 1, kPredLogits = 2 };

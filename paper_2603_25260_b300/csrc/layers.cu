@@ -1,9 +1,8 @@
 // Integer layers of the network (Sec. 3.1-3.3): occupancy-code embedding,
 // Upsampling + Pruning (Eq. 6, 9, 11), the stride-2 sparse conv of
-// Downsampling (Eq. 4), the 3x3x3 sparse conv of the ResBlock with the
-// residual merge fused into the second conv's epilogue (Eq. 5, 8, 10), and
-// the Predictor (Eq. 7) fused with the integer softmax and the cumulative
-// frequency table (Eq. 15).
+// Downsampling (Eq. 4), and the Predictor (Eq. 7) fused with the integer
+// softmax and the cumulative frequency table (Eq. 15).  The 3x3x3 sparse conv
+// of the ResBlock runs on the tensor cores (conv_tc.cu).
 //
 // Layout: one warp per output row, lane = output channel (C = 32).  Input
 // rows are int8, read as 16-byte vectors (every lane reads the same row, a
@@ -179,68 +178,6 @@ void launch_down(const DLayer& W, const uint64_t* ckey, const uint32_t* poff, co
   else
     k_down<64><<<blocks, kWarps * 32, smem, st>>>(W, ckey, poff, d_np, x, x_stride, out,
                                                   out_stride, out_col);
-  count_launches(1);
-}
-
-// ------------------------------------------------------------- conv 333 --
-template <int CIN>
-__global__ void __launch_bounds__(kWarps * 32)
-k_conv333(DLayer L, const int32_t* __restrict__ nbr, const int64_t* d_n,
-          const int8_t* __restrict__ x, int x_stride, int8_t* out, int out_stride, int out_col,
-          DRes res, int has_res, const int8_t* __restrict__ y1, int y1_stride) {
-  extern __shared__ int32_t sm[];
-  const SmemLayer s = stage_layer(L, sm);
-  __syncthreads();
-  const int lane = threadIdx.x & 31;
-  const int64_t n = *d_n;
-  int32_t ma = 0, mb = 0, rs = 0;
-  if (has_res) {
-    ma = res.mab[lane];
-    mb = res.mab[32 + lane];
-    rs = res.slope[lane];
-  }
-  for (int64_t i = warp_id_global(); i < n; i += warps_total()) {
-    const int32_t nb_lane = lane < 27 ? __ldg(nbr + i * 27 + lane) : -1;
-    unsigned present = __ballot_sync(0xffffffffu, nb_lane >= 0);
-    int32_t acc = s.bias[lane];
-    while (present) {
-      const int o = __ffs(present) - 1;
-      present &= present - 1;
-      const int32_t nb = __shfl_sync(0xffffffffu, nb_lane, o);
-      int32_t xv[CIN / 4];
-      load_row<CIN>(x + (int64_t)nb * x_stride, xv);
-      acc -= L.z_in * s.wsum[o * 32 + lane];
-      acc = dot_slice<CIN>(xv, s.W, o, lane, acc);
-    }
-    if (L.prelu) acc = prelu(acc, s.slope[lane]);
-    int q = requant(acc, s.mult[lane], L.shift, L.z_out);
-    if (has_res) {
-      const int a = y1[i * y1_stride + lane];
-      int32_t v = (a - res.z1) * ma + (q - res.z2) * mb;
-      v = prelu(v, rs);
-      q = requant(v, 1, res.shift, res.z_out);
-    }
-    out[i * out_stride + out_col + lane] = (int8_t)q;
-  }
-}
-
-void launch_conv333(const DLayer& W, const int32_t* nbr, const int64_t* d_n, int64_t n_host,
-                    const int8_t* x, int x_stride, int8_t* out, int out_stride, int out_col,
-                    const DRes* res, const int8_t* y1, int y1_stride, cudaStream_t st) {
-  if (n_host <= 0) return;
-  const size_t smem = smem_layer_bytes(W);
-  const int blocks = (int)std::min<int64_t>((n_host + kWarps - 1) / kWarps, kBlocksRow);
-  DRes r{};
-  if (res) r = *res;
-  if (W.cin == 32) {
-    cudaFuncSetAttribute(k_conv333<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_conv333<32><<<blocks, kWarps * 32, smem, st>>>(W, nbr, d_n, x, x_stride, out, out_stride,
-                                                     out_col, r, res != nullptr, y1, y1_stride);
-  } else {
-    cudaFuncSetAttribute(k_conv333<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_conv333<64><<<blocks, kWarps * 32, smem, st>>>(W, nbr, d_n, x, x_stride, out, out_stride,
-                                                     out_col, r, res != nullptr, y1, y1_stride);
-  }
   count_launches(1);
 }
 

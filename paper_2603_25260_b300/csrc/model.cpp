@@ -43,7 +43,7 @@ struct Image {
 };
 
 struct LayerOffs {
-  size_t W, wsum, bias, mult, slope;
+  size_t W, wsum, bias, mult, slope, tc;
 };
 
 LayerOffs pack_layer(Image& img, const BlobRecord& r) {
@@ -69,6 +69,12 @@ LayerOffs pack_layer(Image& img, const BlobRecord& r) {
   o.bias = img.add(r.bias, (size_t)P * cout * 4);
   o.mult = img.add(r.mult, (size_t)P * cout * 4);
   o.slope = img.add(r.slope, (size_t)P * cout * 2);
+  o.tc = 0;
+  if (r.S == 27 && r.kind == kSum && cout == 32 && (cin == 32 || cin == 64)) {
+    std::vector<uint16_t> tcimg(conv_tc_weight_bytes(cin) / 2);
+    pack_conv_tc_weights(r.W, cin, tcimg.data());
+    o.tc = img.add(tcimg.data(), tcimg.size() * 2);
+  }
   return o;
 }
 
@@ -201,7 +207,7 @@ int model_load(const void* blob, size_t len, Model& M, std::string& err) {
   struct Fix {
     void* slot;
     int what;  // 0 emb, 1 layer, 2 res, 3 pred2
-    size_t o[5];
+    size_t o[6];
   };
   std::vector<Fix> fixes;
   size_t ri = 0;
@@ -234,7 +240,7 @@ int model_load(const void* blob, size_t len, Model& M, std::string& err) {
     d.prelu = r->prelu;
     d.per_slice = kind == kSel;
     LayerOffs o = pack_layer(img, *r);
-    fixes.push_back({&d, 1, {o.W, o.wsum, o.bias, o.mult, o.slope}});
+    fixes.push_back({&d, 1, {o.W, o.wsum, o.bias, o.mult, o.slope, o.tc}});
   };
   auto resm = [&](DRes& d) {
     const BlobRecord* r = next(kRes, 2, C, C, 1);
@@ -322,6 +328,7 @@ int model_load(const void* blob, size_t len, Model& M, std::string& err) {
       d->bias = reinterpret_cast<const int32_t*>(base + f.o[2]);
       d->mult = reinterpret_cast<const int32_t*>(base + f.o[3]);
       d->slope = reinterpret_cast<const int16_t*>(base + f.o[4]);
+      d->Wtc = f.o[5] ? reinterpret_cast<const uint16_t*>(base + f.o[5]) : nullptr;
     } else if (f.what == 2) {
       DRes* d = static_cast<DRes*>(f.slot);
       d->mab = reinterpret_cast<const int32_t*>(base + f.o[0]);
@@ -358,6 +365,7 @@ int upload_layer(const BlobRecord& r, DLayer& d, void** dmem) {
   d.bias = reinterpret_cast<const int32_t*>(base + o.bias);
   d.mult = reinterpret_cast<const int32_t*>(base + o.mult);
   d.slope = reinterpret_cast<const int16_t*>(base + o.slope);
+  d.Wtc = o.tc ? reinterpret_cast<const uint16_t*>(base + o.tc) : nullptr;
   return LPC_OK;
 }
 

@@ -179,8 +179,27 @@ int lpc_conv333(const uint64_t* d_keys, int64_t N, int depth, const int8_t* d_x,
   if (s) return s;
   t.ptrs.push_back(mem);
   int64_t* d_n = dev_count(t, N, st);
-  launch_conv333(L, nbr, d_n, N, d_x, cin, d_out, cout, 0, nullptr, nullptr, 0, st);
-  return finish(st, nullptr);
+  uint16_t* xb = t.get<uint16_t>((size_t)N * cin);
+  if (!d_n || !xb || !L.Wtc) return LPC_CUDA_ERROR;
+  launch_to_bf16(d_x, cin, cin, z_in, d_n, N, xb, st);
+  ConvTcArgs a{};
+  a.wimg = L.Wtc;
+  a.bias = L.bias;
+  a.mult = L.mult;
+  a.slope = L.slope;
+  a.prelu = L.prelu;
+  a.shift = L.shift;
+  a.z_out = L.z_out;
+  a.nbr = nbr;
+  a.d_n = d_n;
+  a.xb = xb;
+  a.x_stride = cin;
+  a.out = d_out;
+  a.out_stride = cout;
+  launch_conv333_tc(a, cin, N, st);
+  s = finish(st, nullptr);
+  if (conv_tc_error(true)) return LPC_TIMEOUT;
+  return s;
 }
 
 int lpc_down_s2(const uint64_t* d_ckeys, int64_t Nc, const uint64_t* d_pkeys, int64_t Np,
