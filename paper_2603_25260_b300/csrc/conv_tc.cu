@@ -52,7 +52,9 @@ struct ConvCfg {
   static constexpr int kBBlocks = (27 * CIN + 63) / 64;
   static constexpr int kBBytes = kBBlocks * 4096;
   static constexpr int kChunks = RB / 16;            // 16-byte chunks per row
-  static constexpr size_t kSmem = 1024 + kBBytes + (size_t)kStages * kStageBytes;
+  static constexpr int kNbrBytes = kTileM * 27 * 4;  // the tile's neighbour rows
+  static constexpr size_t kSmem =
+      1024 + kBBytes + (size_t)kStages * kStageBytes + kNbrBytes;
 };
 
 __device__ int g_conv_error = 0;
@@ -66,6 +68,7 @@ k_conv333_tc(ConvTcArgs a) {
       (reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
   unsigned char* sB = sm;
   unsigned char* sA = sm + Cfg::kBBytes;
+  int32_t* sNbr = reinterpret_cast<int32_t*>(sA + (size_t)Cfg::kStages * Cfg::kStageBytes);
   __shared__ uint64_t bar[Cfg::kStages];
   __shared__ uint64_t done_bar;
   __shared__ uint32_t tslot;
@@ -114,16 +117,19 @@ k_conv333_tc(ConvTcArgs a) {
   uint32_t tiles_done = 0;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t r0 = tile * kTileM;
+    // the tile's neighbour rows into shared memory (coalesced), then the
     // offsets present in the tile (OR of the rows' neighbour masks)
     if (t == 0) tile_mask = 0;
+    {
+      const int64_t base = r0 * 27, lim = n * 27;
+      for (int i = t; i < kTileM * 27; i += kThreads)
+        sNbr[i] = base + i < lim ? __ldg(a.nbr + base + i) : -1;
+    }
     __syncthreads();
     if (t < kTileM) {
       uint32_t m = 0;
-      if (r0 + t < n) {
-        const int32_t* nb = a.nbr + (r0 + t) * 27;
 #pragma unroll
-        for (int o = 0; o < 27; o++) m |= (uint32_t)(__ldg(nb + o) >= 0) << o;
-      }
+      for (int o = 0; o < 27; o++) m |= (uint32_t)(sNbr[t * 27 + o] >= 0) << o;
       m = __reduce_or_sync(0xffffffffu, m);
       if (lane == 0) atomicOr(&tile_mask, m);
     }
@@ -152,9 +158,7 @@ k_conv333_tc(ConvTcArgs a) {
         const uint32_t sbase = tc::smem_u32(sA + (size_t)s * Cfg::kStageBytes);
         for (int q = t; q < kTileM * Cfg::kChunks; q += kThreads) {
           const int row = q / Cfg::kChunks, c = q % Cfg::kChunks;
-          const int64_t r = r0 + row;
-          int32_t nb = -1;
-          if (r < n) nb = __ldg(a.nbr + r * 27 + o);
+          const int32_t nb = sNbr[row * 27 + o];
           const bool present = nb >= 0;
           const unsigned char* src =
               reinterpret_cast<const unsigned char*>(a.xb) +
