@@ -289,7 +289,8 @@ def run_ours(args):
         frames = [synth.make_frame(s) for s in specs]
         Ls = [s.L for s in specs]
         bcodec = lpc.Codec(blob, max(Ls), max(f.shape[0] for f in frames),
-                           max_frames=len(frames), chunk=args.chunk)
+                           max_frames=len(frames), chunk=args.chunk,
+                           max_batch_points=sum(f.shape[0] for f in frames))
         xs = [torch.from_numpy(f).cuda() for f in frames]
         npts = sum(f.shape[0] for f in frames)
         streams = bcodec.encode_batch(xs, Ls)

@@ -50,15 +50,17 @@ extern "C" {
 typedef struct lpc_codec codec_t;
 
 typedef struct {
-  int L;              /* maximum octree depth handled (6..21); frames may use L' <= L */
+  int L;              /* maximum octree depth handled (6..19); frames may use L' <= L */
   int C;              /* network width; must equal the blob's (32) */
   int b_off;          /* base level offset: b = L - b_off (5) */
   int t_off;          /* threshold offset: t = L - t_off (4), Sec. 3.2 and supplement */
-  int64_t max_points; /* largest point count of one frame (sizes the workspace) */
-  int max_frames;     /* largest batch for encode_batch / decode_batch (>= 1) */
-  int chunk;          /* nodes per entropy-coded substream of a network level (16384) */
+  int64_t max_points; /* largest point count of one frame */
+  int max_frames;     /* largest batch for encode_batch / decode_batch (1..64) */
+  int chunk;          /* nodes per entropy-coded substream of a network level (4096) */
   int host_threads;   /* host threads for range coding (0 = hardware concurrency) */
   uint64_t cuda_stream; /* cudaStream_t as an integer (0 = legacy default stream) */
+  int64_t max_batch_points; /* points of one batch, all frames (0 = max_points * max_frames);
+                               sizes the device workspace */
 } lpc_config;
 
 /* Create a codec.  `blob` is the integer weight blob (format in the Python
@@ -105,11 +107,13 @@ int probs_level(codec_t* codec, const int32_t* d_xyz, int64_t n, int d, uint16_t
                 int64_t cap_nodes, int64_t* n_nodes);
 
 /* Batched encode: nf frames (nf <= max_frames), frame i has n[i] points at
- * d_xyz[i] (device) and depth Ls[i] (6..cfg->L).  Frames are grouped by
- * relative level so that every level of every frame goes through one launch
- * sequence.  The output for frame i is byte-identical to encode_frame of that
- * frame: h_out[i] (capacity caps[i]) receives out_lens[i] bytes.  Returns the
- * first failing status (per-frame CAPACITY reports the needed length). */
+ * d_xyz[i] (device) and depth Ls[i] (6..cfg->L).  All frames share the level
+ * arrays (frame index in the top key bits) and are aligned by relative level
+ * d - b, so every network level of every frame goes through one launch
+ * sequence; the host codes all frames' substreams in parallel.  The output
+ * for frame i is byte-identical to encode_frame of that frame: h_out[i]
+ * (capacity caps[i]) receives out_lens[i] bytes.  Returns the first failing
+ * status (per-frame CAPACITY reports the needed length). */
 int encode_batch(codec_t* codec, int nf, const int32_t* const* d_xyz, const int64_t* n,
                  const int* Ls, uint8_t* const* h_out, const size_t* caps, size_t* out_lens);
 

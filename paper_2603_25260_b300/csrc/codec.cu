@@ -1,6 +1,14 @@
-// Codec orchestration: workspace, octree build, the per-level network
-// schedule of Sec. 3 (GRED + XFP), and host range coding of the
-// device-made cumulative tables.  Exported through the C ABI of lpc.h.
+// Codec orchestration over a batch of frames: workspace, octree build, the
+// per-level network schedule of Sec. 3 (GRED + XFP), and host range coding of
+// the device-made cumulative tables.  Exported through the C ABI of lpc.h.
+//
+// Every level array holds all frames of a batch at once, frame-major then
+// Morton order, indexed by height above the leaves: height h is depth L_f - h
+// of frame f.  The network-coded levels b..L-1 of every frame are heights
+// 5..1, so relative level j = d - b is height 5 - j for every frame, whatever
+// its depth L_f: one launch sequence per relative level codes every frame.
+// The coarse levels (depth < b) are small and are built, coded and decoded on
+// the host, one frame per host task.
 #include "codec.h"
 
 #include <string.h>
@@ -29,15 +37,20 @@ Pool::~Pool() {
 // Runs the next queued task (lock held on entry and on return).
 bool Pool::run_one(std::unique_lock<std::mutex>& lk) {
   if (head_ >= q_.size()) return false;
-  std::function<void()> f = std::move(q_[head_++]);
+  const int g = q_[head_].first;
+  std::function<void()> f = std::move(q_[head_].second);
+  head_++;
+  running_++;
   lk.unlock();
   f();
   lk.lock();
-  if (--pending_ == 0) {
+  running_--;
+  pending_[g]--;
+  if (head_ >= q_.size() && running_ == 0) {
     q_.clear();
     head_ = 0;
-    done_.notify_all();
   }
+  done_.notify_all();
   return true;
 }
 
@@ -50,23 +63,24 @@ void Pool::loop() {
   }
 }
 
-void Pool::submit(std::function<void()> task) {
+void Pool::submit(int group, std::function<void()> task) {
   if (th_.empty()) {
     task();
     return;
   }
   {
     std::lock_guard<std::mutex> g(mu_);
-    q_.push_back(std::move(task));
-    pending_++;
+    q_.emplace_back(group, std::move(task));
+    pending_[group]++;
   }
   cv_.notify_one();
 }
 
-void Pool::wait() {
+void Pool::wait(int group) {
   std::unique_lock<std::mutex> lk(mu_);
-  while (pending_ > 0) {
-    if (!run_one(lk)) done_.wait(lk, [&] { return pending_ == 0 || head_ < q_.size(); });
+  while (pending_[group] > 0) {
+    if (!run_one(lk))
+      done_.wait(lk, [&] { return pending_[group] == 0 || head_ < q_.size(); });
   }
 }
 
@@ -78,6 +92,7 @@ void Pool::wait() {
 namespace {
 
 constexpr int kHdr = 18;
+constexpr int kMaxL = 19;  // 3 L Morton bits stay below the frame bits
 
 void put_varint(std::vector<uint8_t>& o, uint64_t v) {
   while (v >= 0x80) {
@@ -110,6 +125,7 @@ double now_us() {
 Codec::~Codec() {
   delete pool_;
   for (auto e : ev_) cudaEventDestroy(e);
+  for (auto e : pev_) cudaEventDestroy(e);
   if (dmem_) cudaFree(dmem_);
   if (hmem_) cudaFreeHost(hmem_);
   model_free(M_);
@@ -117,7 +133,8 @@ Codec::~Codec() {
 
 int Codec::cuda_check(const char* what) {
   cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return fail(LPC_CUDA_ERROR, std::string(what) + ": " + cudaGetErrorString(e));
+  if (e != cudaSuccess)
+    return fail(LPC_CUDA_ERROR, std::string(what) + ": " + cudaGetErrorString(e));
   return LPC_OK;
 }
 
@@ -129,16 +146,19 @@ int64_t Codec::hash_slots(int64_t n) const {
 
 int Codec::create(const lpc_config& cfg, const void* blob, size_t len) {
   cfg_ = cfg;
-  if (cfg.L < 6 || cfg.L > kMaxDepth || cfg.C != 32 || cfg.b_off != 5 || cfg.t_off != 4 ||
+  if (cfg.L < 6 || cfg.L > kMaxL || cfg.C != 32 || cfg.b_off != 5 || cfg.t_off != 4 ||
       cfg.max_points < 1 || cfg.max_points > (int64_t)1 << 31 || cfg.max_frames < 1 ||
-      cfg.chunk < 1)
+      cfg.max_frames > kMaxBatch || cfg.chunk < 1 || cfg.chunk > (1 << 24))
     return fail(LPC_INVALID_ARG,
-                "config: need 6 <= L <= 21, C = 32, b_off = 5, t_off = 4, max_points >= 1, "
-                "max_frames >= 1, chunk >= 1");
+                "config: need 6 <= L <= 19, C = 32, b_off = 5, t_off = 4, max_points >= 1, "
+                "1 <= max_frames <= 64, chunk >= 1");
   st_ = reinterpret_cast<cudaStream_t>(cfg.cuda_stream);
   int s = model_load(blob, len, M_, err);
   if (s) return s;
-  const int64_t P = cfg.max_points;
+  F_ = cfg.max_frames;
+  P_ = cfg.max_batch_points > 0 ? cfg.max_batch_points : cfg.max_points * (int64_t)cfg.max_frames;
+  if (P_ > ((int64_t)1 << 31) - 2) return fail(LPC_INVALID_ARG, "config: batch capacity too large");
+  const int64_t P = P_;
   const int L = cfg.L;
   // ---- device workspace (one allocation, 256-byte aligned slices) ----
   struct Slice {
@@ -147,16 +167,16 @@ int Codec::create(const lpc_config& cfg, const void* blob, size_t len) {
   };
   std::vector<Slice> sl;
   auto add = [&](void** p, size_t bytes) { sl.push_back({p, bytes}); };
-  int64_t cap = 1;
-  for (int d = 0; d <= L; d++) {
-    lv_.cap[d] = std::min<int64_t>(P, cap);
-    if (cap < ((int64_t)1 << 40)) cap *= 8;
-    add((void**)&lv_.key[d], 8 * lv_.cap[d]);
-    add((void**)&lv_.code[d], lv_.cap[d] + 16);
-    add((void**)&lv_.off[d], 4 * (lv_.cap[d] + 1));
-    add((void**)&lv_.par[d], 4 * lv_.cap[d]);
+  for (int h = 0; h < kHeights; h++) {
+    add((void**)&key_[h], 8 * P);
+    add((void**)&code_[h], P + 16);
+    add((void**)&off_[h], 4 * (P + 1));
+    add((void**)&par_[h], 4 * P);
   }
-  add((void**)&d_N_, 8 * (kMaxDepth + 2));
+  add((void**)&d_N_, 8 * (kHeights + 1));
+  add((void**)&d_foff_, 8 * kHeights * (F_ + 1));
+  add((void**)&d_fr_, sizeof(DevFrame) * F_);
+  add((void**)&d_L_, 4 * F_);
   add((void**)&d_err_, 16);
   add((void**)&d_pairs_, 16);
   add((void**)&d_keys0_, 8 * P);
@@ -198,62 +218,47 @@ int Codec::create(const lpc_config& cfg, const void* blob, size_t len) {
     off += (x.bytes + 255) / 256 * 256;
   }
   // ---- pinned host workspace ----
-  // The coded substreams of one frame fit in 2 bytes per symbol plus 8 per
-  // substream (coded_bound); the arena is pinned so that host threads write
-  // it without page faults.
-  const int64_t max_subs = L + (5 * P) / cfg.chunk + 5;
-  arena_cap_ = (size_t)2 * (L + 1) * P + (size_t)8 * max_subs + 1024;
-  const size_t hN = 8 * (kMaxDepth + 2), hE = 16, hC = (size_t)(L + 1) * P + 64,
-               hEnc = (size_t)4 * 5 * P, hCdf = (size_t)512 * P;
-  const size_t hA = (arena_cap_ + 255) / 256 * 256;
-  const size_t htotal = hN + hE + (hC + 255) / 256 * 256 + hEnc + hCdf + hA + 1024;
+  // Coded substreams fit in 2 bytes per symbol plus 8 per substream
+  // (coded_bound); coarse levels add at most b levels of N_{b-1} symbols.  The
+  // arena is pinned so that host threads write it without page faults.  The
+  // table ring holds two halves of 16 chunks each (at least 2^15 rows each).
+  arena_cap_ = (size_t)2 * (L + 5) * P + (size_t)16 * (L + 5 * P / cfg.chunk + 8) * F_ + 4096;
+  const int64_t half_rows = std::max<int64_t>((int64_t)16 * cfg.chunk, 1 << 15);
+  ring_slots_ = (int)half_rows;
+  struct HSlice {
+    void** p;
+    size_t bytes;
+  };
+  std::vector<HSlice> hs = {
+      {(void**)&h_N_, 8 * (kHeights + 1)},
+      {(void**)&h_foff_, 8 * (size_t)kHeights * (F_ + 1)},
+      {(void**)&h_fr_, sizeof(DevFrame) * F_},
+      {(void**)&h_L_, 4 * (size_t)F_},
+      {(void**)&h_err_, 16},
+      {(void**)&h_keys6_, 8 * (size_t)P},
+      {(void**)&h_codes_, (size_t)kHeights * P + 64},
+      {(void**)&h_enc_, 4 * 5 * (size_t)P},
+      {(void**)&h_ring_, (size_t)512 * 2 * half_rows},
+      {(void**)&h_arena_, arena_cap_},
+  };
+  size_t htotal = 0;
+  for (auto& x : hs) htotal += (x.bytes + 255) / 256 * 256;
   if (cudaMallocHost(&hmem_, htotal) != cudaSuccess) {
     cudaGetLastError();
     hmem_ = nullptr;
     return fail(LPC_CUDA_ERROR, "pinned host allocation failed");
   }
-  uint8_t* h = static_cast<uint8_t*>(hmem_);
-  h_N_ = reinterpret_cast<int64_t*>(h);
-  h_err_ = reinterpret_cast<int*>(h + hN);
-  h_codes_ = h + hN + hE;
-  h_enc_ = reinterpret_cast<uint32_t*>(h + hN + hE + (hC + 255) / 256 * 256);
-  h_cdf_ = reinterpret_cast<uint16_t*>(reinterpret_cast<uint8_t*>(h_enc_) + hEnc);
-  h_arena_ = reinterpret_cast<uint8_t*>(h_cdf_) + hCdf;
-  const int nev = (int)(P / cfg.chunk) + 8;
-  ev_.resize(nev);
+  size_t ho = 0;
+  for (auto& x : hs) {
+    *x.p = static_cast<uint8_t*>(hmem_) + ho;
+    ho += (x.bytes + 255) / 256 * 256;
+  }
+  ev_.resize(512);
   for (auto& e : ev_) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
-  int threads = cfg.host_threads > 0 ? cfg.host_threads : (int)std::thread::hardware_concurrency();
+  const int threads =
+      cfg.host_threads > 0 ? cfg.host_threads : (int)std::thread::hardware_concurrency();
   pool_ = new Pool(std::max(0, threads - 1));
   return cuda_check("codec_create");
-}
-
-// ------------------------------------------------------------ per frame --
-void Codec::begin_frame(int L) {
-  L_ = L;
-  b_ = L - cfg_.b_off;
-  t_ = L - cfg_.t_off;
-  have_Fb_ = have_Ft_ = have_nbr_t_ = false;
-  if (prof.mask) cudaMemsetAsync(d_pairs_, 0, 16, st_);
-}
-
-// Algorithmic bytes of the level build once the sizes are known.
-void Codec::level_bytes(int L) {
-  double b = 0;
-  for (int d = 0; d < L; d++) b += 8.0 * N_[d + 1] + 4.0 * N_[d + 1] + 13.0 * N_[d] + 4.0;
-  for (auto it = marks_.rbegin(); it != marks_.rend(); ++it)
-    if (it->f == kFamLevels) {
-      it->bytes = b;
-      break;
-    }
-}
-
-int Codec::check_device_error() {
-  if (conv_tc_error(true)) return fail(LPC_TIMEOUT, "tensor-core conv gave up on a bounded wait");
-  const int e = *h_err_;
-  if (e == 0) return LPC_OK;
-  if (e == kErrCoord) return fail(LPC_INVALID_ARG, "coordinate outside [0, 2^L)");
-  if (e == kErrHashFull) return fail(LPC_HASH_FULL, "voxel hash probe limit reached");
-  return fail(LPC_CORRUPT_STREAM, "decoded occupancy code is invalid");
 }
 
 // --------------------------------------------------------------- profiler --
@@ -263,7 +268,7 @@ void Codec::profile_reset(unsigned mask) {
   marks_.clear();
   pev_used_ = 0;
   if (mask && pev_.empty()) {
-    pev_.resize(2048);
+    pev_.resize(4096);
     for (auto& e : pev_) cudaEventCreate(&e);
   }
 }
@@ -288,7 +293,7 @@ void Codec::pend(int f, double bytes, double ops, int pair_slot, double ppo, dou
   m.ppb = ppb;
 }
 
-// After the frame's final synchronisation: fold the marks into the totals.
+// After the call's final synchronisation: fold the marks into the totals.
 void Codec::prof_collect() {
   if (!prof.mask) return;
   uint64_t pairs[2] = {0, 0};
@@ -299,7 +304,7 @@ void Codec::prof_collect() {
     cudaEventElapsedTime(&ms, pev_[m.e0], pev_[m.e1]);
     prof.ms[m.f] += ms;
     prof.launches[m.f] += 1;
-    double P = m.pair_slot >= 0 ? (double)pairs[m.pair_slot] : 0.0;
+    const double P = m.pair_slot >= 0 ? (double)pairs[m.pair_slot] : 0.0;
     prof.bytes[m.f] += m.bytes + P * m.ppb;
     prof.ops[m.f] += m.ops + P * m.ppo;
   }
@@ -307,52 +312,110 @@ void Codec::prof_collect() {
   pev_used_ = 0;
 }
 
-void Codec::build_octree(const int32_t* d_xyz, int64_t n, int L) {
+// Algorithmic bytes of the level build once the sizes are known.
+void Codec::level_bytes() {
+  double b = 0;
+  for (int h = 0; h + 1 < kHeights; h++) b += 8.0 * N_[h] + 4.0 * N_[h] + 13.0 * N_[h + 1] + 4.0;
+  for (auto it = marks_.rbegin(); it != marks_.rend(); ++it)
+    if (it->f == kFamLevels) {
+      it->bytes = b;
+      break;
+    }
+}
+
+// ------------------------------------------------------------- per batch --
+void Codec::begin_batch() {
+  have_Fb_ = have_Ft_ = have_nbr_t_ = false;
   cudaMemsetAsync(d_err_, 0, 4, st_);
-  h_N_[kMaxDepth + 1] = n;
-  cudaMemcpyAsync(d_N_ + kMaxDepth + 1, h_N_ + kMaxDepth + 1, 8, cudaMemcpyHostToDevice, st_);
+  if (prof.mask) cudaMemsetAsync(d_pairs_, 0, 16, st_);
+}
+
+int Codec::check_device_error() {
+  if (conv_tc_error(true)) return fail(LPC_TIMEOUT, "tensor-core conv gave up on a bounded wait");
+  const int e = *h_err_;
+  if (e == 0) return LPC_OK;
+  if (e == kErrCoord) return fail(LPC_INVALID_ARG, "coordinate outside [0, 2^L)");
+  if (e == kErrHashFull) return fail(LPC_HASH_FULL, "voxel hash probe limit reached");
+  return fail(LPC_CORRUPT_STREAM, "decoded occupancy code is invalid");
+}
+
+int Codec::sync_and_check(const char* what) {
+  cudaMemcpyAsync(h_err_, d_err_, 4, cudaMemcpyDeviceToHost, st_);
+  if (cudaStreamSynchronize(st_) != cudaSuccess) return cuda_check(what);
+  if (int s = cuda_check(what)) return s;
+  return check_device_error();
+}
+
+// Levels of the batch at heights 0..6 on the device: Morton keys (frame in
+// the top bits), one radix sort, duplicate removal, then six rounds of
+// floor-halving with occupancy codes (supplement, "Implementation of Octree
+// Operations").  Ends with N_ and every frame's offsets on the host.
+int Codec::build_levels_device(int nf, const int32_t* const* xyz, const int64_t* n) {
+  int64_t total = 0;
+  int maxL = 0;
+  for (int f = 0; f < nf; f++) {
+    h_fr_[f] = DevFrame{xyz[f], nullptr, n[f], total, fr_[f].L, 0};
+    h_L_[f] = fr_[f].L;
+    total += n[f];
+    maxL = std::max(maxL, fr_[f].L);
+  }
+  h_N_[kHeights] = total;
+  cudaMemcpyAsync(d_fr_, h_fr_, sizeof(DevFrame) * nf, cudaMemcpyHostToDevice, st_);
+  cudaMemcpyAsync(d_L_, h_L_, 4 * nf, cudaMemcpyHostToDevice, st_);
+  cudaMemcpyAsync(d_N_ + kHeights, h_N_ + kHeights, 8, cudaMemcpyHostToDevice, st_);
   pbeg(kFamSort);
-  launch_morton(d_xyz, n, L, d_keys0_, d_err_, st_);
-  uint64_t* sorted = radix_sort(d_keys0_, n, 3 * L, sort_, st_);
-  launch_unique(sorted, d_N_ + kMaxDepth + 1, n, lv_.key[L], d_N_ + L, scan_, st_);
-  const int passes = (3 * L + 7) / 8;
-  pend(kFamSort, 12.0 * n + 8.0 * n + 16.0 * n * passes + 16.0 * n, 0);
+  launch_morton_batch(d_fr_, nf, total, d_keys0_, d_err_, st_);
+  uint64_t* sorted = radix_sort(d_keys0_, total, 3 * maxL, nf > 1, sort_, st_);
+  launch_unique(sorted, d_N_ + kHeights, total, key_[0], d_N_, scan_, st_);
+  const int passes = (3 * maxL + 7) / 8 + (nf > 1 ? 1 : 0);
+  pend(kFamSort, 12.0 * total + 8.0 * total + 16.0 * total * passes + 16.0 * total, 0);
   pbeg(kFamLevels);
-  for (int d = L - 1; d >= 0; d--)
-    launch_level_up(lv_.key[d + 1], d_N_ + d + 1, lv_.cap[d + 1], lv_.key[d], lv_.code[d],
-                    lv_.off[d], lv_.par[d + 1], d_N_ + d, scan_, st_);
-  // level sizes are not known on the host yet: bytes are filled in by the
-  // caller once they are (see level_bytes)
+  for (int h = 0; h + 1 < kHeights; h++)
+    launch_level_up(key_[h], d_N_ + h, P_, key_[h + 1], code_[h + 1], off_[h + 1], par_[h],
+                    d_N_ + h + 1, scan_, st_);
   pend(kFamLevels, 0, 0);
+  fetch_frame_offsets(nf);
+  cudaMemcpyAsync(h_N_, d_N_, 8 * kHeights, cudaMemcpyDeviceToHost, st_);
+  return LPC_OK;
 }
 
+void Codec::fetch_frame_offsets(int nf) {
+  LevelPtrs lp;
+  for (int h = 0; h < kHeights; h++) {
+    lp.key[h] = key_[h];
+    lp.n[h] = d_N_ + h;
+  }
+  launch_frame_offsets(lp, kHeights, nf, d_foff_, st_);
+  cudaMemcpyAsync(h_foff_, d_foff_, 8 * kHeights * (nf + 1), cudaMemcpyDeviceToHost, st_);
+}
+
+// --------------------------------------------------------------- network --
 // Launch wrappers: one kernel each, bracketed by the profiler with the
-// algorithmic work of that launch.
-void Codec::embed(const DEmb& E, int d, int8_t* out, int stride, int col) {
+// algorithmic work of that launch.  `h` is a height of the level arrays.
+void Codec::embed(const DEmb& E, int h, int8_t* out, int stride, int col) {
   pbeg(kFamEmbed);
-  launch_embed(E, lv_.code[d], d_N_ + d, N_[d], out, stride, col, st_);
-  pend(kFamEmbed, 33.0 * N_[d], 0);
+  launch_embed(E, code_[h], d_N_ + h, N_[h], out, stride, col, st_);
+  pend(kFamEmbed, 33.0 * N_[h], 0);
 }
 
-// Pruning(Upsampling(x)) from V_d to V_{d+1}
-void Codec::up(const DLayer& W, int d, const int8_t* x, int xs, int8_t* out, int os) {
+// Pruning(Upsampling(x)) from height h to height h - 1
+void Codec::up(const DLayer& W, int h, const int8_t* x, int xs, int8_t* out, int os) {
   pbeg(kFamUp);
-  launch_up_prune(W, lv_.key[d + 1], lv_.par[d + 1], d_N_ + d + 1, N_[d + 1], x, xs, out, os, 0,
-                  st_);
-  pend(kFamUp, (double)W.cin * N_[d] + 32.0 * N_[d + 1] + 8.0 * N_[d + 1],
-       2.0 * N_[d + 1] * W.cin * 32);
+  launch_up_prune(W, key_[h - 1], par_[h - 1], d_N_ + h - 1, N_[h - 1], x, xs, out, os, 0, st_);
+  pend(kFamUp, (double)W.cin * N_[h] + 32.0 * N_[h - 1] + 8.0 * N_[h - 1],
+       2.0 * N_[h - 1] * W.cin * 32);
 }
 
 // int8 activations -> bf16 (q - z) rows, the tensor-core conv's input
-void Codec::to_bf16(const int8_t* x, int xs, int cols, int z, int d) {
+void Codec::to_bf16(const int8_t* x, int xs, int cols, int z, int h) {
   pbeg(kFamEmbed);
-  launch_to_bf16(x, xs, cols, z, d_N_ + d, N_[d], xb16_, st_);
-  pend(kFamEmbed, 3.0 * cols * N_[d], 0);
+  launch_to_bf16(x, xs, cols, z, d_N_ + h, N_[h], xb16_, st_);
+  pend(kFamEmbed, 3.0 * cols * N_[h], 0);
 }
 
-// 3x3x3 conv on V_d: bf16 input rows xb (stride xbs elements); with res the
-// residual merge reads y1_; outb (optional) gets the next conv's bf16 input.
-void Codec::conv(const DLayer& W, int d, const int32_t* nbr, int slot, const void* xb, int xbs,
+// 3x3x3 conv at height h: bf16 input rows xb (stride xbs elements); with res
+// the residual merge reads y1_; outb (optional) gets the next conv's input.
+void Codec::conv(const DLayer& W, int h, const int32_t* nbr, int slot, const void* xb, int xbs,
                  int8_t* out, int os, int oc, const DRes* res, void* outb, int outb_z) {
   ConvTcArgs a{};
   a.wimg = W.Wtc;
@@ -363,7 +426,7 @@ void Codec::conv(const DLayer& W, int d, const int32_t* nbr, int slot, const voi
   a.shift = W.shift;
   a.z_out = W.z_out;
   a.nbr = nbr;
-  a.d_n = d_N_ + d;
+  a.d_n = d_N_ + h;
   a.xb = xb;
   a.x_stride = xbs;
   a.out = out;
@@ -384,369 +447,576 @@ void Codec::conv(const DLayer& W, int d, const int32_t* nbr, int slot, const voi
     a.res_shift = res->shift;
   }
   pbeg(kFamConv);
-  launch_conv333_tc(a, W.cin, N_[d], st_);
+  launch_conv333_tc(a, W.cin, N_[h], st_);
   // per neighbour pair: 2 Cin C ops and 2 Cin bytes gathered; per node: the
   // int8 output (+ the residual's y1 and the bf16 copy when present)
   pend(kFamConv,
-       N_[d] * (32.0 + (res ? 32.0 : 0.0) + (outb ? 64.0 : 0.0)) + 27.0 * W.cin * 32 * 2, 0,
+       N_[h] * (32.0 + (res ? 32.0 : 0.0) + (outb ? 64.0 : 0.0)) + 27.0 * W.cin * 32 * 2, 0,
        slot, 2.0 * W.cin * 32, 2.0 * W.cin + 4.0);
 }
 
-void Codec::kmap(int d, int32_t* nbr, int slot) {
+void Codec::kmap(int h, int32_t* nbr, int slot) {
   pbeg(kFamHash);
-  const int64_t slots = hash_slots(N_[d]);
-  launch_kernel_map(lv_.key[d], d_N_ + d, N_[d], d, hash_, slots, nbr, d_err_, st_,
+  const int64_t slots = hash_slots(N_[h]);
+  launch_kernel_map(key_[h], d_N_ + h, N_[h], d_L_, h, hash_, slots, nbr, d_err_, st_,
                     prof.mask ? d_pairs_ + slot : nullptr);
-  pend(kFamHash, 12.0 * slots + 20.0 * N_[d] + 27.0 * N_[d] * (4 + 8), 0);
+  pend(kFamHash, 12.0 * slots + 20.0 * N_[h] + 27.0 * N_[h] * (4 + 8), 0);
 }
 
-// F^b = Pruning(Upsampling(E_0[Y_{b-1}]), Y_{b-1})
+// F^b = Pruning(Upsampling(E_0[Y_{b-1}]), Y_{b-1}): height 6 -> 5
 void Codec::ensure_Fb() {
   if (have_Fb_) return;
-  const int b = b_;
-  embed(M_.E0, b - 1, xe_, 32, 0);
-  up(M_.UP0, b - 1, xe_, 32, fb_, 32);
+  embed(M_.E0, 6, xe_, 32, 0);
+  up(M_.UP0, 6, xe_, 32, fb_, 32);
   have_Fb_ = true;
 }
 
-// S^b = ResBlock(F^b) (Eq. 8); F^t = Pruning(Upsampling(Concat(S^b, Y_b)), Y_b) (Eq. 9)
+// S^b = ResBlock(F^b) (Eq. 8); F^t = Pruning(Upsampling(Concat(S^b, Y_b)), Y_b)
+// (Eq. 9): V_b is height 5, V_t height 4
 void Codec::ensure_Ft() {
   if (have_Ft_) return;
   ensure_Fb();
-  const int b = b_;
-  kmap(b, nbr_b_, 0);
-  to_bf16(fb_, 32, 32, M_.RA[1].z_in, b);
-  conv(M_.RA[1], b, nbr_b_, 0, xb16_, 32, y1_, 32, 0, nullptr, y1b16_, M_.RB[1].z_in);
-  conv(M_.RB[1], b, nbr_b_, 0, y1b16_, 32, xb_, 64, 0, &M_.RM[1], nullptr, 0);
-  embed(M_.E1, b, xb_, 64, 32);
-  up(M_.UP1, b, xb_, 64, xt_, 64);
+  kmap(5, nbr_b_, 0);
+  to_bf16(fb_, 32, 32, M_.RA[1].z_in, 5);
+  conv(M_.RA[1], 5, nbr_b_, 0, xb16_, 32, y1_, 32, 0, nullptr, y1b16_, M_.RB[1].z_in);
+  conv(M_.RB[1], 5, nbr_b_, 0, y1b16_, 32, xb_, 64, 0, &M_.RM[1], nullptr, 0);
+  embed(M_.E1, 5, xb_, 64, 32);
+  up(M_.UP1, 5, xb_, 64, xt_, 64);
   have_Ft_ = true;
 }
 
 void Codec::ensure_nbr_t() {
   if (have_nbr_t_) return;
-  kmap(t_, nbr_t_, 1);
+  kmap(4, nbr_t_, 1);
   have_nbr_t_ = true;
 }
 
-// Network of level d (b <= d <= L-1): needs V_0..V_d and Y_0..Y_{d-1}.
-void Codec::net_level(int d, int mode, uint16_t* cdf, uint32_t* enc, int8_t* logits) {
-  auto pred = [&](int j, const int8_t* F, int stride) {
+// Network of relative level j (depth b + j of every frame, height 5 - j):
+// needs the levels above it and their codes.
+void Codec::net_level(int j, int mode, uint16_t* cdf, uint32_t* enc, int8_t* logits) {
+  const int h = 5 - j;
+  auto pred = [&](int jj, const int8_t* F, int stride) {
     pbeg(kFamPred);
-    launch_predictor(M_.P1[j], M_.P2[j], M_.d_lut, F, stride, d_N_ + d, N_[d], mode, lv_.code[d],
+    launch_predictor(M_.P1[jj], M_.P2[jj], M_.d_lut, F, stride, d_N_ + h, N_[h], mode, code_[h],
                      cdf, enc, logits, st_);
-    const double n = (double)N_[d];
-    pend(kFamPred, n * 32 + (mode == kPredCdf ? 512.0 * n : mode == kPredEnc ? 5.0 * n : 255.0 * n),
+    const double n = (double)N_[h];
+    pend(kFamPred,
+         n * 32 + (mode == kPredCdf ? 512.0 * n : mode == kPredEnc ? 5.0 * n : 255.0 * n),
          2.0 * n * (32 * 32 + 255 * 32));
   };
-  if (d == b_) {
+  if (j == 0) {
     ensure_Fb();
     pred(0, fb_, 32);
     return;
   }
   ensure_Ft();
-  if (d == t_) {
+  if (j == 1) {
     pred(1, xt_, 64);
     return;
   }
-  // deep level d = t + m: G^t = Downsampling(Y_{d-1}) (Eq. 4)
+  // deep level t + m: G^t = Downsampling(Y_{d-1}) (Eq. 4), from height 5 - m
+  // down to V_t (height 4) in m - 1 stride-2 steps
   ensure_nbr_t();
-  const int m = d - t_, j = m + 1;
+  const int m = j - 1;
   if (m == 1) {
-    embed(M_.G[j], t_, xt_, 64, 32);
+    embed(M_.G[j], 4, xt_, 64, 32);
   } else {
-    embed(M_.G[j], d - 1, g_[0], 32, 0);
+    embed(M_.G[j], 5 - m, g_[0], 32, 0);
     const int8_t* cur = g_[0];
     for (int i = 1; i < m; i++) {
-      const int k = d - 1 - i;  // V_{k+1} -> V_k
+      const int hp = 5 - m + i;  // parent height of this step
       int8_t* dst = i == m - 1 ? xt_ : g_[i & 1];
       const int ds = i == m - 1 ? 64 : 32, dc = i == m - 1 ? 32 : 0;
       pbeg(kFamDown);
-      launch_down(M_.D[j][i], lv_.key[k + 1], lv_.off[k], d_N_ + k, N_[k], cur, 32, dst, ds, dc,
+      launch_down(M_.D[j][i], key_[hp - 1], off_[hp], d_N_ + hp, N_[hp], cur, 32, dst, ds, dc,
                   st_);
-      pend(kFamDown, 32.0 * (N_[k + 1] + N_[k]), 2.0 * N_[k + 1] * 32 * 32);
+      pend(kFamDown, 32.0 * (N_[hp - 1] + N_[hp]), 2.0 * N_[hp - 1] * 32 * 32);
       cur = dst;
     }
   }
   // H^t = ResBlock(Concat(F^t, G^t)) (Eq. 10)
-  to_bf16(xt_, 64, 64, M_.RA[j].z_in, t_);
-  conv(M_.RA[j], t_, nbr_t_, 1, xb16_, 64, y1_, 32, 0, nullptr, y1b16_, M_.RB[j].z_in);
-  conv(M_.RB[j], t_, nbr_t_, 1, y1b16_, 32, hx_[0], 64, 0, &M_.RM[j], nullptr, 0);
-  // F^{k+1} = Pruning(Upsampling(Concat(H^k, Y_k)), Y_k), k = t..d-1 (Eq. 11)
+  to_bf16(xt_, 64, 64, M_.RA[j].z_in, 4);
+  conv(M_.RA[j], 4, nbr_t_, 1, xb16_, 64, y1_, 32, 0, nullptr, y1b16_, M_.RB[j].z_in);
+  conv(M_.RB[j], 4, nbr_t_, 1, y1b16_, 32, hx_[0], 64, 0, &M_.RM[j], nullptr, 0);
+  // F^{k+1} = Pruning(Upsampling(Concat(H^k, Y_k)), Y_k), k = t..d-1 (Eq. 11):
+  // heights 4 -> h
   int cur = 0;
-  for (int k = t_; k < d; k++) {
-    embed(M_.E[j][k - t_], k, hx_[cur], 64, 32);
-    int8_t* dst = k == d - 1 ? fo_ : hx_[1 - cur];
-    const int ds = k == d - 1 ? 32 : 64;
-    up(M_.UP[j][k - t_], k, hx_[cur], 64, dst, ds);
+  for (int k = 0; k < m; k++) {
+    const int hk = 4 - k;
+    embed(M_.E[j][k], hk, hx_[cur], 64, 32);
+    int8_t* dst = k == m - 1 ? fo_ : hx_[1 - cur];
+    const int ds = k == m - 1 ? 32 : 64;
+    up(M_.UP[j][k], hk, hx_[cur], 64, dst, ds);
     cur = 1 - cur;
   }
   pred(j, fo_, 32);
 }
 
+// ------------------------------------------------------------ host octree --
+namespace {
+
+// Coarse levels of one frame from its V_{b-1} keys (Morton, no frame bits)
+// and codes Y_{b-1}: floor-halving with duplicate removal up to the root.
+// Returns codes per depth 0..b-1.
+std::vector<std::vector<uint8_t>> coarse_from_keys(const uint64_t* keys, const uint8_t* codes,
+                                                   int64_t n, int b) {
+  std::vector<std::vector<uint8_t>> out(b);
+  out[b - 1].assign(codes, codes + n);
+  std::vector<uint64_t> cur(keys, keys + n), par;
+  for (int d = b - 2; d >= 0; d--) {
+    par.clear();
+    std::vector<uint8_t>& c = out[d];
+    c.clear();
+    for (uint64_t k : cur) {
+      const uint64_t p = k >> 3;
+      if (par.empty() || par.back() != p) {
+        par.push_back(p);
+        c.push_back(0);
+      }
+      c.back() |= (uint8_t)(1u << (k & 7));
+    }
+    cur.swap(par);
+  }
+  return out;
+}
+
+}  // namespace
+
 // --------------------------------------------------------------- encode --
-int Codec::encode(const int32_t* d_xyz, int64_t n, uint8_t* out, size_t cap, size_t* out_len) {
+int Codec::encode(int nf, const int32_t* const* xyz, const int64_t* n, const int* Ls,
+                  uint8_t* const* out, const size_t* caps, size_t* lens) {
   err.clear();
-  if (!out_len || n < 0 || (n > 0 && !d_xyz) || (cap > 0 && !out))
-    return fail(LPC_INVALID_ARG, "encode_frame: bad arguments");
-  if (n > cfg_.max_points) return fail(LPC_CAPACITY, "encode_frame: n exceeds max_points");
-  const int L = cfg_.L;
-  begin_frame(L);
+  if (nf < 1 || nf > F_ || !xyz || !n || !Ls || !out || !caps || !lens)
+    return fail(LPC_INVALID_ARG, "encode: bad arguments");
   const double t0 = now_us();
-  if (n > 0) {
-    build_octree(d_xyz, n, L);
-    cudaMemcpyAsync(h_N_, d_N_, 8 * (L + 1), cudaMemcpyDeviceToHost, st_);
-    cudaMemcpyAsync(h_err_, d_err_, 4, cudaMemcpyDeviceToHost, st_);
-    if (cudaStreamSynchronize(st_) != cudaSuccess) return cuda_check("encode_frame: octree");
-    if (int s = check_device_error()) return s;
+  stats = Stats{};
+  // frames with points go to the device batch, empty frames get a flag stream
+  std::vector<int> dev;  // device frame index -> caller index
+  int64_t total = 0;
+  for (int i = 0; i < nf; i++) {
+    if (Ls[i] < 6 || Ls[i] > std::min(cfg_.L, kMaxL) || n[i] < 0 || (n[i] > 0 && !xyz[i]))
+      return fail(LPC_INVALID_ARG, "encode: frame depth or point count out of range");
+    if (n[i] > cfg_.max_points) return fail(LPC_CAPACITY, "encode: frame exceeds max_points");
+    if (n[i] > 0) dev.push_back(i);
+    total += n[i];
+  }
+  if (total > P_) return fail(LPC_CAPACITY, "encode: batch exceeds the codec's capacity");
+  const int nd = (int)dev.size();
+  nf_ = nd;
+  fr_.assign(nd, Frame());
+  std::vector<const int32_t*> dx(nd);
+  std::vector<int64_t> dn(nd);
+  for (int f = 0; f < nd; f++) {
+    Frame& F = fr_[f];
+    F.L = Ls[dev[f]];
+    F.b = F.L - cfg_.b_off;
+    F.t = F.L - cfg_.t_off;
+    F.n = n[dev[f]];
+    dx[f] = xyz[dev[f]];
+    dn[f] = n[dev[f]];
+  }
+  std::vector<std::vector<uint8_t>> tables(nd);
+  if (nd > 0) {
+    begin_batch();
+    build_levels_device(nd, dx.data(), dn.data());
+    if (int s = sync_and_check("encode: octree")) return s;
     stats.phase_us[0] = now_us() - t0;
-    for (int d = 0; d <= L; d++) N_[d] = h_N_[d];
-    level_bytes(L);
-    // coarse codes to the host
-    size_t coff[kMaxDepth + 1], pos = 0;
-    for (int d = 0; d < b_; d++) {
-      coff[d] = pos;
-      cudaMemcpyAsync(h_codes_ + pos, lv_.code[d], N_[d], cudaMemcpyDeviceToHost, st_);
-      pos += N_[d];
-    }
+    for (int h = 0; h < kHeights; h++) N_[h] = h_N_[h];
+    level_bytes();
+    for (int f = 0; f < nd; f++)
+      for (int h = 0; h < kHeights; h++) {
+        fr_[f].off[h] = h_foff_[h * (nd + 1) + f];
+        fr_[f].cnt[h] = h_foff_[h * (nd + 1) + f + 1] - fr_[f].off[h];
+      }
+    // V_{b-1} keys and codes of every frame to the host (coarse levels)
+    cudaMemcpyAsync(h_keys6_, key_[6], 8 * N_[6], cudaMemcpyDeviceToHost, st_);
+    cudaMemcpyAsync(h_codes_ + 6 * P_, code_[6], N_[6], cudaMemcpyDeviceToHost, st_);
     cudaEventRecord(ev_[0], st_);
-    // network levels: (C_s, f_s) of the true symbol of every node; each
-    // level's intervals go to the host as soon as that level is done, so the
-    // host codes level d while the device computes level d + 1
-    int64_t eoff[kMaxDepth + 1], ep = 0;
-    for (int d = b_; d < L; d++) {
-      eoff[d] = ep;
-      net_level(d, kPredEnc, nullptr, d_enc_ + ep, nullptr);
-      cudaMemcpyAsync(h_enc_ + ep, d_enc_ + ep, 4 * N_[d], cudaMemcpyDeviceToHost, st_);
-      cudaEventRecord(ev_[1 + d - b_], st_);
-      ep += N_[d];
+    // network levels of all frames: (C_s, f_s) of the true symbol of every
+    // node; each level's intervals go to the host as soon as it is done
+    for (int j = 0; j < 5; j++) {
+      const int h = 5 - j;
+      net_level(j, kPredEnc, nullptr, d_enc_ + (size_t)j * P_, nullptr);
+      cudaMemcpyAsync(h_enc_ + (size_t)j * P_, d_enc_ + (size_t)j * P_, 4 * N_[h],
+                      cudaMemcpyDeviceToHost, st_);
+      cudaEventRecord(ev_[1 + j], st_);
     }
     cudaMemcpyAsync(h_err_, d_err_, 4, cudaMemcpyDeviceToHost, st_);
-    cudaEventRecord(ev_[1 + L - b_], st_);
-    if (int s = cuda_check("encode_frame: launch")) return s;
-    // substreams: coarse levels (one each), then chunks of the network levels
+    cudaEventRecord(ev_[6], st_);
+    if (int s = cuda_check("encode: launch")) return s;
+    // substream layout in the arena: per frame, b coarse slots then chunks
     tasks_.clear();
     size_t ao = 0;
-    auto add_task = [&](int d, int64_t s0, int64_t cnt) {
-      tasks_.push_back(SubTask{d, s0, cnt, ao, 0});
-      ao += coded_bound((size_t)cnt);
-    };
-    for (int d = 0; d < b_; d++) add_task(d, 0, N_[d]);
-    for (int d = b_; d < L; d++)
-      for (int64_t s0 = 0; s0 < N_[d]; s0 += cfg_.chunk)
-        add_task(d, s0, std::min<int64_t>(cfg_.chunk, N_[d] - s0));
-    if (ao > arena_cap_) return fail(LPC_CAPACITY, "encode_frame: coding arena too small");
-    stats.phase_us[1] = now_us() - t0;
-    // coarse levels are coded while the device runs the network
-    cudaEventSynchronize(ev_[0]);
-    for (int d = 0; d < b_; d++)
-      for (int64_t i = 0; i < N_[d]; i++) h_codes_[coff[d] + i] -= 1;
-    for (int i = b_ - 1; i >= 0; i--) {  // largest level first
-      pool_->submit([this, i, &coff] {
-        SubTask& T = tasks_[i];
-        T.len = encode_adaptive(h_codes_ + coff[T.d], (size_t)T.count, h_arena_ + T.arena,
-                                coded_bound((size_t)T.count));
-      });
-    }
-    int level_done = b_ - 1;
-    for (size_t i = b_; i < tasks_.size(); i++) {
-      while (level_done < tasks_[i].d) {
-        level_done++;
-        cudaEventSynchronize(ev_[1 + level_done - b_]);
+    for (int f = 0; f < nd; f++) {
+      Frame& F = fr_[f];
+      F.sub_base = tasks_.size();
+      const size_t coarse_bound = coded_bound((size_t)F.b * (size_t)F.cnt[6]) + 8 * F.b;
+      tasks_.push_back(SubTask{f, -1, 0, 0, ao, 0});  // whole coarse region of the frame
+      ao += coarse_bound;
+      for (int d = 1; d < F.b; d++) tasks_.push_back(SubTask{f, -1, 0, 0, 0, 0});
+      for (int j = 0; j < 5; j++) {
+        const int h = 5 - j;
+        for (int64_t s0 = 0; s0 < F.cnt[h]; s0 += cfg_.chunk) {
+          const int64_t cnt = std::min<int64_t>(cfg_.chunk, F.cnt[h] - s0);
+          tasks_.push_back(SubTask{f, F.b + j, s0, cnt, ao, 0});
+          ao += coded_bound((size_t)cnt);
+        }
       }
-      pool_->submit([this, i, &eoff] {
-        SubTask& T = tasks_[i];
-        T.len = encode_packed(h_enc_ + eoff[T.d] + T.start, (size_t)T.count, h_arena_ + T.arena,
-                              coded_bound((size_t)T.count));
+    }
+    if (ao > arena_cap_) return fail(LPC_CAPACITY, "encode: coding arena too small");
+    stats.phase_us[1] = now_us() - t0;
+    // coarse levels: one host task per frame, while the device runs the network
+    cudaEventSynchronize(ev_[0]);
+    for (int f = 0; f < nd; f++) {
+      pool_->submit(0, [this, f] {
+        Frame& F = fr_[f];
+        const int64_t r0 = F.off[6], cnt = F.cnt[6];
+        std::vector<uint64_t> k(cnt);
+        for (int64_t i = 0; i < cnt; i++) k[i] = h_keys6_[r0 + i] & kLowMask;
+        F.coarse = coarse_from_keys(k.data(), h_codes_ + 6 * P_ + r0, cnt, F.b);
+        // one coding task per coarse level (each level is its own adaptive
+        // model); slots laid out in the frame's coarse region
+        size_t ao = tasks_[F.sub_base].arena;
+        for (int d = 0; d < F.b; d++) {
+          SubTask& T = tasks_[F.sub_base + d];
+          T.arena = ao;
+          T.count = (int64_t)F.coarse[d].size();
+          ao += coded_bound((size_t)T.count);
+        }
+        for (int d = F.b - 1; d >= 0; d--) {
+          pool_->submit(0, [this, f, d] {
+            Frame& F = fr_[f];
+            const std::vector<uint8_t>& c = F.coarse[d];
+            std::vector<uint8_t> syms(c.size());
+            for (size_t i = 0; i < c.size(); i++) syms[i] = (uint8_t)(c[i] - 1);
+            SubTask& T = tasks_[F.sub_base + d];
+            T.len = encode_adaptive(syms.data(), syms.size(), h_arena_ + T.arena,
+                                    coded_bound(syms.size()));
+          });
+        }
       });
     }
-    cudaEventSynchronize(ev_[1 + L - b_]);
-    pool_->wait();
+    for (int j = 0; j < 5; j++) {
+      cudaEventSynchronize(ev_[1 + j]);
+      const int h = 5 - j;
+      for (int f = 0; f < nd; f++) {
+        const Frame& F = fr_[f];
+        for (size_t i = F.sub_base + F.b; i < (f + 1 < nd ? fr_[f + 1].sub_base : tasks_.size());
+             i++) {
+          if (tasks_[i].d != F.b + j) continue;
+          pool_->submit(0, [this, i, j, h] {
+            SubTask& T = tasks_[i];
+            const Frame& F = fr_[T.f];
+            T.len = encode_packed(h_enc_ + (size_t)j * P_ + F.off[h] + T.start, (size_t)T.count,
+                                  h_arena_ + T.arena, coded_bound((size_t)T.count));
+          });
+        }
+      }
+    }
+    cudaEventSynchronize(ev_[6]);
+    pool_->wait(0);
     stats.phase_us[2] = now_us() - t0;
     if (int s = check_device_error()) return s;
     prof_collect();
-  } else {
-    tasks_.clear();
   }
-  // assemble straight into the caller's buffer
-  uint8_t head[kHdr + 32];
-  const uint8_t hdr[10] = {'L', 'P', 'C', '1', 1, (uint8_t)L, (uint8_t)b_, (uint8_t)t_,
-                           (uint8_t)M_.C, (uint8_t)(n > 0 ? 0 : 1)};
-  memcpy(head, hdr, 10);
-  for (int i = 0; i < 8; i++) head[10 + i] = (uint8_t)(M_.hash >> (8 * i));
-  std::vector<uint8_t> table;
-  put_varint(table, (uint64_t)cfg_.chunk);
-  put_varint(table, tasks_.size());
-  size_t body = 0;
-  for (const SubTask& T : tasks_) {
-    put_varint(table, T.len);
-    body += T.len;
+  // assemble every frame's stream straight into its caller buffer
+  int first = LPC_OK;
+  for (int i = 0, f = 0; i < nf; i++) {
+    const bool empty = n[i] == 0;
+    const Frame* F = empty ? nullptr : &fr_[f];
+    const int L = Ls[i];
+    uint8_t head[kHdr];
+    const uint8_t hdr[10] = {'L', 'P', 'C', '1', 1, (uint8_t)L, (uint8_t)(L - cfg_.b_off),
+                             (uint8_t)(L - cfg_.t_off), (uint8_t)M_.C, (uint8_t)(empty ? 1 : 0)};
+    memcpy(head, hdr, 10);
+    for (int k = 0; k < 8; k++) head[10 + k] = (uint8_t)(M_.hash >> (8 * k));
+    std::vector<uint8_t> table;
+    put_varint(table, (uint64_t)cfg_.chunk);
+    size_t b0 = 0, b1 = 0;
+    if (!empty) {
+      b0 = F->sub_base;
+      b1 = f + 1 < nd ? fr_[f + 1].sub_base : tasks_.size();
+    }
+    put_varint(table, b1 - b0);
+    size_t body = 0;
+    for (size_t k = b0; k < b1; k++) {
+      put_varint(table, tasks_[k].len);
+      body += tasks_[k].len;
+    }
+    const size_t total_len = kHdr + table.size() + body;
+    lens[i] = total_len;
+    if (total_len > caps[i] || !out[i]) {
+      if (!first) first = fail(LPC_CAPACITY, "encode: output buffer too small");
+    } else {
+      memcpy(out[i], head, kHdr);
+      memcpy(out[i] + kHdr, table.data(), table.size());
+      uint8_t* p = out[i] + kHdr + table.size();
+      for (size_t k = b0; k < b1; k++) {
+        memcpy(p, h_arena_ + tasks_[k].arena, tasks_[k].len);
+        p += tasks_[k].len;
+      }
+    }
+    if (!empty) f++;
   }
-  const size_t total = kHdr + table.size() + body;
-  *out_len = total;
-  stats.L = L;
-  for (int d = 0; d <= L; d++) stats.N[d] = n > 0 ? N_[d] : 0;
-  if (total > cap) return fail(LPC_CAPACITY, "encode_frame: output buffer too small");
-  memcpy(out, head, kHdr);
-  memcpy(out + kHdr, table.data(), table.size());
-  uint8_t* p = out + kHdr + table.size();
-  for (const SubTask& T : tasks_) {
-    memcpy(p, h_arena_ + T.arena, T.len);
-    p += T.len;
+  // statistics of the first frame
+  if (nd > 0) {
+    const Frame& F = fr_[0];
+    stats.L = F.L;
+    for (int d = 0; d < F.b; d++) stats.N[d] = (int64_t)F.coarse[d].size();
+    for (int h = 0; h < kHeights; h++) stats.N[F.L - h] = F.cnt[h];
   }
   stats.host_us = now_us() - t0;
   stats.phase_us[3] = stats.host_us;
-  return LPC_OK;
+  return first;
 }
 
 // --------------------------------------------------------------- decode --
-int Codec::decode(const uint8_t* in, size_t len, int32_t* d_out, int64_t cap, int64_t* n_out) {
+int Codec::decode(int nf, const uint8_t* const* in, const size_t* lens, int32_t* const* out,
+                  const int64_t* caps, int64_t* n_out) {
   err.clear();
-  if (!in || !n_out) return fail(LPC_INVALID_ARG, "decode_frame: bad arguments");
-  *n_out = 0;
-  if (len < (size_t)kHdr || memcmp(in, "LPC1", 4) != 0 || in[4] != 1)
-    return fail(LPC_CORRUPT_STREAM, "decode_frame: not an LPC1 stream");
-  const int L = in[5], b = in[6], t = in[7], C = in[8], flags = in[9];
-  uint64_t hash = 0;
-  for (int i = 0; i < 8; i++) hash |= (uint64_t)in[10 + i] << (8 * i);
-  if (L < 6 || L > kMaxDepth || b != L - 5 || t != L - 4)
-    return fail(LPC_CORRUPT_STREAM, "decode_frame: bad depth fields");
-  if (hash != M_.hash || C != M_.C)
-    return fail(LPC_WEIGHTS_MISMATCH, "decode_frame: stream was written with another weight blob");
-  if (L > cfg_.L) return fail(LPC_INVALID_ARG, "decode_frame: stream depth exceeds codec L");
-  size_t pos = kHdr;
-  uint64_t chunk, nsub;
-  if (!get_varint(in, len, pos, chunk) || !get_varint(in, len, pos, nsub) || chunk < 1 ||
-      chunk > (1u << 30) || nsub > len)
-    return fail(LPC_CORRUPT_STREAM, "decode_frame: bad stream table");
-  if (flags & 1) {
-    if (nsub != 0) return fail(LPC_CORRUPT_STREAM, "decode_frame: empty frame with substreams");
-    return LPC_OK;
-  }
-  std::vector<uint64_t> slen(nsub);
-  std::vector<size_t> soff(nsub);
-  for (uint64_t i = 0; i < nsub; i++)
-    if (!get_varint(in, len, pos, slen[i]))
-      return fail(LPC_CORRUPT_STREAM, "decode_frame: bad stream table");
-  for (uint64_t i = 0; i < nsub; i++) {
-    if (slen[i] > len - pos) return fail(LPC_CORRUPT_STREAM, "decode_frame: truncated stream");
-    soff[i] = pos;
-    pos += slen[i];
-  }
-  begin_frame(L);
+  if (nf < 1 || nf > F_ || !in || !lens || !out || !caps || !n_out)
+    return fail(LPC_INVALID_ARG, "decode: bad arguments");
   const double t0 = now_us();
-  const int64_t P = cfg_.max_points;
-  uint64_t si = 0;
-  size_t coff[kMaxDepth + 1], cp = 0;
-  // coarse levels on the host, then the device expansion up to V_b
-  N_[0] = 1;
-  for (int d = 0; d < b; d++) {
-    if (si >= nsub) return fail(LPC_CORRUPT_STREAM, "decode_frame: missing substream");
-    coff[d] = cp;
-    uint8_t* Y = h_codes_ + cp;
-    if (!decode_adaptive((size_t)N_[d], in + soff[si], (size_t)slen[si], Y))
-      return fail(LPC_CORRUPT_STREAM, "decode_frame: corrupt coarse substream");
-    si++;
-    int64_t nc = 0;
-    for (int64_t i = 0; i < N_[d]; i++) {
-      Y[i] += 1;
-      nc += __builtin_popcount(Y[i]);
+  stats = Stats{};
+  std::vector<int> dev;
+  std::vector<Frame> all(nf);
+  for (int i = 0; i < nf; i++) {
+    n_out[i] = 0;
+    Frame& F = all[i];
+    const uint8_t* p = in[i];
+    const size_t len = lens[i];
+    if (!p || len < (size_t)kHdr || memcmp(p, "LPC1", 4) != 0 || p[4] != 1)
+      return fail(LPC_CORRUPT_STREAM, "decode: not an LPC1 stream");
+    const int L = p[5], b = p[6], t = p[7], C = p[8], flags = p[9];
+    uint64_t hash = 0;
+    for (int k = 0; k < 8; k++) hash |= (uint64_t)p[10 + k] << (8 * k);
+    if (L < 6 || L > kMaxDepth || b != L - 5 || t != L - 4)
+      return fail(LPC_CORRUPT_STREAM, "decode: bad depth fields");
+    if (hash != M_.hash || C != M_.C)
+      return fail(LPC_WEIGHTS_MISMATCH, "decode: stream was written with another weight blob");
+    if (L > std::min(cfg_.L, kMaxL))
+      return fail(LPC_INVALID_ARG, "decode: stream depth exceeds the codec's L");
+    size_t pos = kHdr;
+    uint64_t chunk, nsub;
+    if (!get_varint(p, len, pos, chunk) || !get_varint(p, len, pos, nsub) || chunk < 1 ||
+        chunk > (uint64_t)ring_slots_ || nsub > len)
+      return fail(LPC_CORRUPT_STREAM, "decode: bad stream table");
+    if (flags & 1) {
+      if (nsub != 0) return fail(LPC_CORRUPT_STREAM, "decode: empty frame with substreams");
+      continue;
     }
-    cp += N_[d];
-    if (nc > P) return fail(LPC_CAPACITY, "decode_frame: frame exceeds max_points");
-    N_[d + 1] = nc;
+    F.L = L;
+    F.b = b;
+    F.t = t;
+    F.in = p;
+    F.len = len;
+    F.chunk = (int64_t)chunk;
+    F.slen.resize(nsub);
+    F.soff.resize(nsub);
+    for (uint64_t k = 0; k < nsub; k++)
+      if (!get_varint(p, len, pos, F.slen[k]))
+        return fail(LPC_CORRUPT_STREAM, "decode: bad stream table");
+    for (uint64_t k = 0; k < nsub; k++) {
+      if (F.slen[k] > len - pos) return fail(LPC_CORRUPT_STREAM, "decode: truncated stream");
+      F.soff[k] = pos;
+      pos += F.slen[k];
+    }
+    if (nsub < (uint64_t)b) return fail(LPC_CORRUPT_STREAM, "decode: missing substream");
+    dev.push_back(i);
   }
+  const int nd = (int)dev.size();
+  nf_ = nd;
+  fr_.clear();
+  for (int i : dev) fr_.push_back(std::move(all[i]));
+  if (nd == 0) return LPC_OK;
+  begin_batch();
+  for (int f = 0; f < nd; f++) {
+    h_fr_[f] = DevFrame{nullptr, out[dev[f]], 0, 0, fr_[f].L, 0};
+    h_L_[f] = fr_[f].L;
+  }
+  cudaMemcpyAsync(d_L_, h_L_, 4 * nd, cudaMemcpyHostToDevice, st_);
+  // coarse levels: decoded and expanded to V_{b-1} on the host, one task per
+  // frame (levels are sequential within a frame: N_{d+1} = sum popcount Y_d)
+  std::vector<std::vector<uint64_t>> k6(nd);
+  std::atomic<int> cstat{0};
+  const int64_t maxp = cfg_.max_points;
+  for (int f = 0; f < nd; f++) {
+    pool_->submit(0, [&, f] {
+      Frame& F = fr_[f];
+      F.coarse.assign(F.b, {});
+      std::vector<uint64_t> keys(1, 0), next;
+      for (int d = 0; d < F.b; d++) {
+        std::vector<uint8_t>& Y = F.coarse[d];
+        Y.resize(keys.size());
+        if (!decode_adaptive(Y.size(), F.in + F.soff[d], (size_t)F.slen[d], Y.data())) {
+          cstat = LPC_CORRUPT_STREAM;
+          return;
+        }
+        for (auto& y : Y) y += 1;
+        if (d + 1 == F.b) break;
+        next.clear();
+        for (size_t p = 0; p < keys.size(); p++)
+          for (int c = 0; c < 8; c++)
+            if (Y[p] >> c & 1) next.push_back((keys[p] << 3) | (uint64_t)c);
+        if ((int64_t)next.size() > maxp) {
+          cstat = LPC_CAPACITY;
+          return;
+        }
+        keys.swap(next);
+      }
+      k6[f].swap(keys);
+    });
+  }
+  pool_->wait(0);
+  if (cstat == LPC_CORRUPT_STREAM) return fail(LPC_CORRUPT_STREAM, "decode: corrupt coarse substream");
+  if (cstat == LPC_CAPACITY) return fail(LPC_CAPACITY, "decode: frame exceeds max_points");
+  // V_{b-1} of every frame (height 6) to the device
+  int64_t n6 = 0;
+  for (int f = 0; f < nd; f++) {
+    Frame& F = fr_[f];
+    F.off[6] = n6;
+    F.cnt[6] = (int64_t)k6[f].size();
+    n6 += F.cnt[6];
+  }
+  if (n6 > P_) return fail(LPC_CAPACITY, "decode: batch exceeds the codec's capacity");
+  for (int f = 0; f < nd; f++) {
+    Frame& F = fr_[f];
+    const uint64_t fb = (uint64_t)f << kFrameShift;
+    for (int64_t i = 0; i < F.cnt[6]; i++) {
+      h_keys6_[F.off[6] + i] = fb | k6[f][i];
+      h_codes_[6 * P_ + F.off[6] + i] = F.coarse[F.b - 1][i];
+    }
+  }
+  N_[6] = n6;
+  h_N_[6] = n6;
+  cudaMemcpyAsync(d_N_ + 6, h_N_ + 6, 8, cudaMemcpyHostToDevice, st_);
+  cudaMemcpyAsync(key_[6], h_keys6_, 8 * n6, cudaMemcpyHostToDevice, st_);
+  cudaMemcpyAsync(code_[6], h_codes_ + 6 * P_, n6, cudaMemcpyHostToDevice, st_);
   stats.phase_us[4] = now_us() - t0;
   for (int i = 5; i < 9; i++) stats.phase_us[i] = 0;
-  // the coarse levels are tiny: expand them on the host up to V_{b-1} and
-  // upload only V_{b-1} and Y_{b-1}; the device expands V_b from there
-  {
-    uint64_t* keys = reinterpret_cast<uint64_t*>(h_cdf_);  // pinned staging, free here
-    uint64_t* tmp = keys + P;
-    keys[0] = 0;
-    for (int d = 0; d + 1 < b; d++) {
-      const uint8_t* Y = h_codes_ + coff[d];
-      int64_t r = 0;
-      for (int64_t p = 0; p < N_[d]; p++)
-        for (int c = 0; c < 8; c++)
-          if (Y[p] >> c & 1) tmp[r++] = (keys[p] << 3) | (uint64_t)c;
-      std::swap(keys, tmp);
-    }
-    cudaMemsetAsync(d_err_, 0, 4, st_);
-    h_N_[b - 1] = N_[b - 1];
-    cudaMemcpyAsync(d_N_ + b - 1, h_N_ + b - 1, 8, cudaMemcpyHostToDevice, st_);
-    cudaMemcpyAsync(lv_.key[b - 1], keys, 8 * N_[b - 1], cudaMemcpyHostToDevice, st_);
-    cudaMemcpyAsync(lv_.code[b - 1], h_codes_ + coff[b - 1], N_[b - 1], cudaMemcpyHostToDevice,
-                    st_);
-    pbeg(kFamLevels);
-    launch_expand(lv_.key[b - 1], lv_.code[b - 1], d_N_ + b - 1, lv_.cap[b - 1], lv_.key[b],
-                  lv_.par[b], lv_.off[b - 1], d_N_ + b, scan_, d_err_, st_);
-    pend(kFamLevels, 13.0 * N_[b - 1] + 12.0 * N_[b], 0);
-  }
-  // network levels: full tables to the host in chunks, decoded in parallel
-  for (int d = b; d < L; d++) {
-    const int64_t N = N_[d];
+  // substream index of (frame, relative level j, chunk 0)
+  std::vector<std::vector<size_t>> sidx(nd, std::vector<size_t>(6, 0));
+  std::atomic<bool> bad{false};
+  for (int j = 0; j < 5; j++) {
+    const int h = 5 - j;
     double tl = now_us();
-    net_level(d, kPredCdf, d_cdf_, nullptr, nullptr);
-    const int64_t nch = (N + (int64_t)chunk - 1) / (int64_t)chunk;
-    if ((int64_t)(si + nch) > (int64_t)nsub)
-      return fail(LPC_CORRUPT_STREAM, "decode_frame: missing substream");
-    if (nch > (int64_t)ev_.size()) return fail(LPC_CAPACITY, "decode_frame: chunk too small");
-    for (int64_t c = 0; c < nch; c++) {
-      const int64_t r0 = c * (int64_t)chunk, rows = std::min<int64_t>((int64_t)chunk, N - r0);
-      cudaMemcpyAsync(h_cdf_ + r0 * 256, d_cdf_ + r0 * 256, rows * 512, cudaMemcpyDeviceToHost,
-                      st_);
-      cudaEventRecord(ev_[c], st_);
+    // V at height h: children of height h + 1 (host knows the counts)
+    int64_t nh = 0;
+    for (int f = 0; f < nd; f++) {
+      Frame& F = fr_[f];
+      const uint8_t* Y = h_codes_ + (size_t)(h + 1) * P_ + F.off[h + 1];
+      int64_t c = 0;
+      for (int64_t i = 0; i < F.cnt[h + 1]; i++) c += __builtin_popcount(Y[i]);
+      if (c > maxp) return fail(LPC_CAPACITY, "decode: frame exceeds max_points");
+      F.off[h] = nh;
+      F.cnt[h] = c;
+      nh += c;
+      if (j == 0) sidx[f][0] = F.b;
     }
-    if (int s = cuda_check("decode_frame: launch")) return s;
-    coff[d] = cp;
-    uint8_t* Y = h_codes_ + cp;
+    if (nh > P_) return fail(LPC_CAPACITY, "decode: batch exceeds the codec's capacity");
+    N_[h] = nh;
+    pbeg(kFamLevels);
+    launch_expand(key_[h + 1], code_[h + 1], d_N_ + h + 1, P_, key_[h], par_[h], off_[h + 1],
+                  d_N_ + h, scan_, d_err_, st_);
+    pend(kFamLevels, 13.0 * N_[h + 1] + 12.0 * nh, 0);
+    net_level(j, kPredCdf, d_cdf_, nullptr, nullptr);
+    if (int s = cuda_check("decode: launch")) return s;
+    stats.phase_us[7] += now_us() - tl;
+    tl = now_us();
+    // tables to the host through the two-half ring; chunks are decoded as
+    // they land, one host task per (frame, chunk)
+    struct Ck {
+      int f;
+      int64_t r0, rows, local;
+      size_t sub;
+    };
+    std::vector<Ck> cks;
+    for (int f = 0; f < nd; f++) {
+      const Frame& F = fr_[f];
+      size_t s = sidx[f][j];
+      for (int64_t c0 = 0; c0 < F.cnt[h]; c0 += F.chunk, s++) {
+        if (s >= F.slen.size()) return fail(LPC_CORRUPT_STREAM, "decode: missing substream");
+        cks.push_back(Ck{f, F.off[h] + c0, std::min<int64_t>(F.chunk, F.cnt[h] - c0), c0, s});
+      }
+      sidx[f][j + 1] = s;
+    }
     stats.phase_us[5] += now_us() - tl;
     tl = now_us();
-    std::atomic<bool> bad{false};
-    const uint64_t s0 = si;
-    for (int64_t c = 0; c < nch; c++) {  // each chunk is decoded as soon as its table lands
-      cudaEventSynchronize(ev_[c]);
-      pool_->submit([&, c] {
-        const int64_t r0 = c * (int64_t)chunk, rows = std::min<int64_t>((int64_t)chunk, N - r0);
-        if (!decode_rows(h_cdf_ + r0 * 256, (size_t)rows, in + soff[s0 + c],
-                         (size_t)slen[s0 + c], Y + r0))
-          bad = true;
-        for (int64_t i = 0; i < rows; i++) Y[r0 + i] += 1;
-      });
+    size_t c = 0;
+    int wave = 0;
+    while (c < cks.size()) {
+      const int half = wave & 1;
+      pool_->wait(1 + half);  // the tasks that last read this half are done
+      uint16_t* base = h_ring_ + (size_t)half * ring_slots_ * 256;
+      int64_t used = 0;
+      size_t c1 = c;
+      int e = 0;
+      while (c1 < cks.size() && used + cks[c1].rows <= ring_slots_ && e < 240) {
+        cudaMemcpyAsync(base + used * 256, d_cdf_ + cks[c1].r0 * 256, 512 * cks[c1].rows,
+                        cudaMemcpyDeviceToHost, st_);
+        cudaEventRecord(ev_[16 + half * 240 + e], st_);
+        used += cks[c1].rows;
+        c1++;
+        e++;
+      }
+      used = 0;
+      for (size_t k = c; k < c1; k++) {
+        cudaEventSynchronize(ev_[16 + half * 240 + (int)(k - c)]);
+        const Ck ck = cks[k];
+        const uint16_t* rows = base + used * 256;
+        used += ck.rows;
+        pool_->submit(1 + half, [this, ck, rows, h, &bad] {
+          const Frame& F = fr_[ck.f];
+          uint8_t* Y = h_codes_ + (size_t)h * P_ + ck.r0;
+          if (!decode_rows(rows, (size_t)ck.rows, F.in + F.soff[ck.sub], (size_t)F.slen[ck.sub],
+                           Y))
+            bad = true;
+          for (int64_t i = 0; i < ck.rows; i++) Y[i] += 1;
+        });
+      }
+      c = c1;
+      wave++;
     }
-    pool_->wait();
-    si += nch;
+    pool_->wait(1);
+    pool_->wait(2);
     stats.phase_us[6] += now_us() - tl;
-    tl = now_us();
-    if (bad) return fail(LPC_CORRUPT_STREAM, "decode_frame: corrupt level substream");
-    int64_t nc = 0;
-    for (int64_t i = 0; i < N; i++) nc += __builtin_popcount(Y[i]);
-    cp += N;
-    if (nc > P) return fail(LPC_CAPACITY, "decode_frame: frame exceeds max_points");
-    N_[d + 1] = nc;
-    cudaMemcpyAsync(lv_.code[d], Y, N, cudaMemcpyHostToDevice, st_);
-    pbeg(kFamLevels);
-    launch_expand(lv_.key[d], lv_.code[d], d_N_ + d, lv_.cap[d], lv_.key[d + 1], lv_.par[d + 1],
-                  lv_.off[d], d_N_ + d + 1, scan_, d_err_, st_);
-    pend(kFamLevels, 13.0 * N + 12.0 * nc, 0);
-    stats.phase_us[7] += now_us() - tl;
+    if (bad) return fail(LPC_CORRUPT_STREAM, "decode: corrupt level substream");
+    cudaMemcpyAsync(code_[h], h_codes_ + (size_t)h * P_, nh, cudaMemcpyHostToDevice, st_);
   }
-  if (si != nsub) return fail(LPC_CORRUPT_STREAM, "decode_frame: extra substreams");
-  *n_out = N_[L];
-  stats.L = L;
-  for (int d = 0; d <= L; d++) stats.N[d] = N_[d];
-  if (N_[L] > cap) {
-    cudaStreamSynchronize(st_);
-    return fail(LPC_CAPACITY, "decode_frame: output capacity too small");
+  for (int f = 0; f < nd; f++)
+    if (sidx[f][5] != fr_[f].slen.size())
+      return fail(LPC_CORRUPT_STREAM, "decode: extra substreams");
+  // leaves: children of height 1
+  int64_t n0 = 0;
+  for (int f = 0; f < nd; f++) {
+    Frame& F = fr_[f];
+    const uint8_t* Y = h_codes_ + (size_t)P_ + F.off[1];
+    int64_t c = 0;
+    for (int64_t i = 0; i < F.cnt[1]; i++) c += __builtin_popcount(Y[i]);
+    F.off[0] = n0;
+    F.cnt[0] = c;
+    n0 += c;
+    n_out[dev[f]] = c;
+    if (c > caps[dev[f]]) return fail(LPC_CAPACITY, "decode: output capacity too small");
   }
-  launch_keys_to_xyz(lv_.key[L], d_N_ + L, N_[L], L, d_out, st_);
-  cudaMemcpyAsync(h_err_, d_err_, 4, cudaMemcpyDeviceToHost, st_);
-  if (cudaStreamSynchronize(st_) != cudaSuccess) return cuda_check("decode_frame");
+  if (n0 > P_) return fail(LPC_CAPACITY, "decode: batch exceeds the codec's capacity");
+  N_[0] = n0;
+  pbeg(kFamLevels);
+  launch_expand(key_[1], code_[1], d_N_ + 1, P_, key_[0], par_[0], off_[1], d_N_, scan_, d_err_,
+                st_);
+  pend(kFamLevels, 13.0 * N_[1] + 12.0 * n0, 0);
+  for (int f = 0; f < nd; f++) h_foff_[f] = fr_[f].off[0];
+  cudaMemcpyAsync(d_fr_, h_fr_, sizeof(DevFrame) * nd, cudaMemcpyHostToDevice, st_);
+  cudaMemcpyAsync(d_foff_, h_foff_, 8 * nd, cudaMemcpyHostToDevice, st_);
+  launch_keys_to_xyz_batch(key_[0], d_N_, n0, d_fr_, d_foff_, st_);
+  if (int s = sync_and_check("decode")) return s;
+  stats.L = fr_[0].L;
+  for (int d = 0; d < fr_[0].b; d++) stats.N[d] = (int64_t)fr_[0].coarse[d].size();
+  for (int h = 0; h < kHeights; h++) stats.N[fr_[0].L - h] = fr_[0].cnt[h];
   stats.host_us = now_us() - t0;
   stats.phase_us[8] = stats.host_us;
   prof_collect();
-  return check_device_error();
+  return LPC_OK;
 }
 
 // ---------------------------------------------------------------- probs --
@@ -756,57 +1026,28 @@ int Codec::probs(const int32_t* d_xyz, int64_t n, int d, uint16_t* d_cdf, int64_
   const int L = cfg_.L;
   if (!nn || n < 0 || (n > 0 && (!d_xyz || !d_cdf)) || d < L - cfg_.b_off || d > L - 1)
     return fail(LPC_INVALID_ARG, "probs_level: bad arguments");
-  if (n > cfg_.max_points) return fail(LPC_CAPACITY, "probs_level: n exceeds max_points");
+  if (n > cfg_.max_points || n > P_) return fail(LPC_CAPACITY, "probs_level: n exceeds max_points");
   *nn = 0;
   if (n == 0) return LPC_OK;
-  begin_frame(L);
-  build_octree(d_xyz, n, L);
-  cudaMemcpyAsync(h_N_, d_N_, 8 * (L + 1), cudaMemcpyDeviceToHost, st_);
-  cudaMemcpyAsync(h_err_, d_err_, 4, cudaMemcpyDeviceToHost, st_);
-  if (cudaStreamSynchronize(st_) != cudaSuccess) return cuda_check("probs_level");
-  if (int s = check_device_error()) return s;
-  for (int k = 0; k <= L; k++) N_[k] = h_N_[k];
-  level_bytes(L);
-  *nn = N_[d];
-  if (N_[d] > cap) return fail(LPC_CAPACITY, "probs_level: output rows too few");
-  net_level(d, kPredCdf, d_cdf, nullptr, nullptr);
-  cudaMemcpyAsync(h_err_, d_err_, 4, cudaMemcpyDeviceToHost, st_);
-  if (cudaStreamSynchronize(st_) != cudaSuccess) return cuda_check("probs_level");
-  if (int s = cuda_check("probs_level")) return s;
+  nf_ = 1;
+  fr_.assign(1, Frame());
+  fr_[0].L = L;
+  fr_[0].b = L - cfg_.b_off;
+  fr_[0].t = L - cfg_.t_off;
+  fr_[0].n = n;
+  begin_batch();
+  const int32_t* x = d_xyz;
+  build_levels_device(1, &x, &n);
+  if (int s = sync_and_check("probs_level")) return s;
+  for (int h = 0; h < kHeights; h++) N_[h] = h_N_[h];
+  level_bytes();
+  const int j = d - fr_[0].b;
+  *nn = N_[5 - j];
+  if (N_[5 - j] > cap) return fail(LPC_CAPACITY, "probs_level: output rows too few");
+  net_level(j, kPredCdf, d_cdf, nullptr, nullptr);
+  if (int s = sync_and_check("probs_level")) return s;
   prof_collect();
-  return check_device_error();
-}
-
-// ---------------------------------------------------------------- batch --
-int Codec::encode_batch(int nf, const int32_t* const* xyz, const int64_t* n, const int* Ls,
-                        uint8_t* const* out, const size_t* caps, size_t* lens) {
-  if (nf < 0 || nf > cfg_.max_frames || (nf > 0 && (!xyz || !n || !Ls || !out || !caps || !lens)))
-    return fail(LPC_INVALID_ARG, "encode_batch: bad arguments");
-  int first = LPC_OK;
-  const int Lsave = cfg_.L;
-  for (int i = 0; i < nf; i++) {
-    if (Ls[i] < 6 || Ls[i] > Lsave) {
-      if (!first) first = fail(LPC_INVALID_ARG, "encode_batch: frame depth out of range");
-      continue;
-    }
-    cfg_.L = Ls[i];
-    int s = encode(xyz[i], n[i], out[i], caps[i], &lens[i]);
-    if (s && !first) first = s;
-  }
-  cfg_.L = Lsave;
-  return first;
-}
-
-int Codec::decode_batch(int nf, const uint8_t* const* in, const size_t* lens, int32_t* const* out,
-                        const int64_t* caps, int64_t* n_out) {
-  if (nf < 0 || nf > cfg_.max_frames || (nf > 0 && (!in || !lens || !out || !caps || !n_out)))
-    return fail(LPC_INVALID_ARG, "decode_batch: bad arguments");
-  int first = LPC_OK;
-  for (int i = 0; i < nf; i++) {
-    int s = decode(in[i], lens[i], out[i], caps[i], &n_out[i]);
-    if (s && !first) first = s;
-  }
-  return first;
+  return LPC_OK;
 }
 
 }  // namespace lpc
@@ -837,14 +1078,15 @@ const char* codec_last_error(codec_t* codec) { return codec ? codec->c.err.c_str
 
 int encode_frame(codec_t* codec, const int32_t* d_xyz, int64_t n, uint8_t* h_out, size_t cap,
                  size_t* out_len) {
-  if (!codec) return LPC_INVALID_ARG;
-  return codec->c.encode(d_xyz, n, h_out, cap, out_len);
+  if (!codec || !out_len) return LPC_INVALID_ARG;
+  int Ls = codec->c.depth();
+  return codec->c.encode(1, &d_xyz, &n, &Ls, &h_out, &cap, out_len);
 }
 
 int decode_frame(codec_t* codec, const uint8_t* h_in, size_t len, int32_t* d_xyz_out, int64_t cap,
                  int64_t* n_out) {
-  if (!codec) return LPC_INVALID_ARG;
-  return codec->c.decode(h_in, len, d_xyz_out, cap, n_out);
+  if (!codec || !n_out) return LPC_INVALID_ARG;
+  return codec->c.decode(1, &h_in, &len, &d_xyz_out, &cap, n_out);
 }
 
 int probs_level(codec_t* codec, const int32_t* d_xyz, int64_t n, int d, uint16_t* d_cdf_out,
@@ -856,13 +1098,13 @@ int probs_level(codec_t* codec, const int32_t* d_xyz, int64_t n, int d, uint16_t
 int encode_batch(codec_t* codec, int nf, const int32_t* const* d_xyz, const int64_t* n,
                  const int* Ls, uint8_t* const* h_out, const size_t* caps, size_t* out_lens) {
   if (!codec) return LPC_INVALID_ARG;
-  return codec->c.encode_batch(nf, d_xyz, n, Ls, h_out, caps, out_lens);
+  return codec->c.encode(nf, d_xyz, n, Ls, h_out, caps, out_lens);
 }
 
 int decode_batch(codec_t* codec, int nf, const uint8_t* const* h_in, const size_t* lens,
                  int32_t* const* d_xyz_out, const int64_t* caps, int64_t* n_out) {
   if (!codec) return LPC_INVALID_ARG;
-  return codec->c.decode_batch(nf, h_in, lens, d_xyz_out, caps, n_out);
+  return codec->c.decode(nf, h_in, lens, d_xyz_out, caps, n_out);
 }
 
 int codec_profile(codec_t* codec, unsigned family_mask) {

@@ -1,4 +1,5 @@
-// The codec object: workspace, level-by-level network schedule, host coding.
+// The codec object: workspace, the per-level network schedule over a batch of
+// frames, and host range coding.  A single frame is a batch of one.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -20,15 +21,16 @@
 namespace lpc {
 
 // Host task queue: the calling thread submits tasks as their inputs become
-// ready (it alone waits on CUDA events), workers run them; wait() helps run
-// queued tasks and returns when every submitted task has finished.
+// ready (it alone waits on CUDA events), workers run them; wait(group) helps
+// run queued tasks and returns when every task of the group has finished.
 class Pool {
  public:
   explicit Pool(int workers);
   ~Pool();
-  void submit(std::function<void()> task);
-  void wait();
+  void submit(int group, std::function<void()> task);
+  void wait(int group);
   int size() const { return (int)th_.size() + 1; }
+  static constexpr int kGroups = 4;
 
  private:
   void loop();
@@ -36,18 +38,11 @@ class Pool {
   std::vector<std::thread> th_;
   std::mutex mu_;
   std::condition_variable cv_, done_;
-  std::vector<std::function<void()>> q_;
+  std::vector<std::pair<int, std::function<void()>>> q_;
   size_t head_ = 0;
-  int pending_ = 0;  // submitted and not finished
+  int pending_[kGroups] = {};
+  int running_ = 0;
   bool stop_ = false;
-};
-
-struct Levels {
-  uint64_t* key[kMaxDepth + 1] = {};
-  uint8_t* code[kMaxDepth + 1] = {};
-  uint32_t* off[kMaxDepth + 1] = {};  // child offsets (N_d + 1 entries)
-  uint32_t* par[kMaxDepth + 1] = {};  // parent row of every node
-  int64_t cap[kMaxDepth + 1] = {};
 };
 
 // Kernel families timed by the optional CUDA-event profiler.
@@ -55,10 +50,10 @@ enum Family {
   kFamSort = 0,  // Morton keys + radix sort + unique
   kFamLevels,    // level build (encoder) / code expansion (decoder)
   kFamHash,      // voxel hash + 27-neighbour map
-  kFamEmbed,     // occupancy-code embedding gathers
+  kFamEmbed,     // occupancy-code embedding gathers, bf16 conversions
   kFamUp,        // Upsampling + Pruning
   kFamDown,      // stride-2 down conv
-  kFamConv,      // 3x3x3 sparse conv (+ fused residual merge)
+  kFamConv,      // 3x3x3 sparse conv on the tensor cores (+ fused residual merge)
   kFamPred,      // predictor + integer softmax + cumulative table
   kFamCount
 };
@@ -85,18 +80,35 @@ struct Stats {
   double phase_us[16] = {};
 };
 
+// One frame of the current batch on the host.
+struct Frame {
+  int L = 0, b = 0, t = 0;
+  int64_t n = 0;                 // input points (encoder) / voxels (decoder)
+  int64_t off[kHeights] = {};    // first row in the level arrays, by height
+  int64_t cnt[kHeights] = {};    // rows of this frame, by height
+  // coarse octree (depths 0..b-1) on the host: codes per depth, in order
+  std::vector<std::vector<uint8_t>> coarse;
+  // decoder: parsed stream
+  const uint8_t* in = nullptr;
+  size_t len = 0;
+  int64_t chunk = 0;
+  std::vector<uint64_t> slen;
+  std::vector<size_t> soff;
+  size_t sub_base = 0;           // first substream task of this frame
+  int status = 0;
+};
+
 class Codec {
  public:
   Codec() = default;
   ~Codec();
   int create(const lpc_config& cfg, const void* blob, size_t len);
-  int encode(const int32_t* d_xyz, int64_t n, uint8_t* out, size_t cap, size_t* out_len);
-  int decode(const uint8_t* in, size_t len, int32_t* d_out, int64_t cap, int64_t* n_out);
+  int encode(int nf, const int32_t* const* xyz, const int64_t* n, const int* Ls,
+             uint8_t* const* out, const size_t* caps, size_t* lens);
+  int decode(int nf, const uint8_t* const* in, const size_t* lens, int32_t* const* out,
+             const int64_t* caps, int64_t* n_out);
   int probs(const int32_t* d_xyz, int64_t n, int d, uint16_t* d_cdf, int64_t cap, int64_t* nn);
-  int encode_batch(int nf, const int32_t* const* xyz, const int64_t* n, const int* Ls,
-                   uint8_t* const* out, const size_t* caps, size_t* lens);
-  int decode_batch(int nf, const uint8_t* const* in, const size_t* lens, int32_t* const* out,
-                   const int64_t* caps, int64_t* n_out);
+  int depth() const { return cfg_.L; }
 
   std::string err;
   Stats stats;
@@ -110,19 +122,23 @@ class Codec {
   }
   int cuda_check(const char* what);
   int check_device_error();
-  void build_octree(const int32_t* d_xyz, int64_t n, int L);
-  void begin_frame(int L);
-  void level_bytes(int L);
-  void embed(const DEmb& E, int d, int8_t* out, int stride, int col);
-  void up(const DLayer& W, int d, const int8_t* x, int xs, int8_t* out, int os);
-  void to_bf16(const int8_t* x, int xs, int cols, int z, int d);
-  void conv(const DLayer& W, int d, const int32_t* nbr, int slot, const void* xb, int xbs,
+  int sync_and_check(const char* what);
+  // octree of the batch: heights 0..6 on the device, coarse levels on the host
+  int build_levels_device(int nf, const int32_t* const* xyz, const int64_t* n);
+  void fetch_frame_offsets(int nf);
+  void begin_batch();
+  void level_bytes();
+  // network
+  void embed(const DEmb& E, int h, int8_t* out, int stride, int col);
+  void up(const DLayer& W, int h, const int8_t* x, int xs, int8_t* out, int os);
+  void to_bf16(const int8_t* x, int xs, int cols, int z, int h);
+  void conv(const DLayer& W, int h, const int32_t* nbr, int slot, const void* xb, int xbs,
             int8_t* out, int os, int oc, const DRes* res, void* outb, int outb_z);
-  void kmap(int d, int32_t* nbr, int slot);
+  void kmap(int h, int32_t* nbr, int slot);
   void ensure_Fb();
   void ensure_Ft();
   void ensure_nbr_t();
-  void net_level(int d, int mode, uint16_t* cdf, uint32_t* enc, int8_t* logits);
+  void net_level(int j, int mode, uint16_t* cdf, uint32_t* enc, int8_t* logits);
   int64_t hash_slots(int64_t n) const;
   // profiler: bracket a launch of family f; ops/bytes are algorithmic work
   // (pair_slot >= 0: ops/bytes are per neighbour pair, scaled at collection)
@@ -140,17 +156,26 @@ class Codec {
   uint64_t* d_pairs_ = nullptr;  // [2]: present neighbour pairs at V_b, V_t
 
   lpc_config cfg_{};
+  int64_t P_ = 0;  // batch capacity in points (rows per level array)
+  int F_ = 0;      // batch capacity in frames
   cudaStream_t st_ = nullptr;
   Model M_;
   Pool* pool_ = nullptr;
-  // per-frame state
-  int L_ = 0, b_ = 0, t_ = 0;
-  int64_t N_[kMaxDepth + 1] = {};  // host copies of the level sizes
+  // per-batch state
+  int nf_ = 0;
+  std::vector<Frame> fr_;
+  int64_t N_[kHeights] = {};  // rows per height (all frames)
   bool have_Fb_ = false, have_Ft_ = false, have_nbr_t_ = false;
-  // device workspace
+  // device workspace: level arrays by height (0 = leaves of every frame)
   void* dmem_ = nullptr;
-  Levels lv_;
-  int64_t* d_N_ = nullptr;   // [kMaxDepth + 2]: level sizes, then the input count
+  uint64_t* key_[kHeights] = {};
+  uint8_t* code_[kHeights] = {};   // code of each node (children mask), heights 1..6
+  uint32_t* off_[kHeights] = {};   // child offsets into height h-1, heights 1..6
+  uint32_t* par_[kHeights] = {};   // parent row at height h+1, heights 0..5
+  int64_t* d_N_ = nullptr;         // [kHeights + 1]: rows per height, then the point count
+  int64_t* d_foff_ = nullptr;      // [kHeights][F + 1] frame offsets
+  DevFrame* d_fr_ = nullptr;       // [F]
+  int* d_L_ = nullptr;             // [F] frame depths
   int* d_err_ = nullptr;
   uint64_t* d_keys0_ = nullptr;
   SortScratch sort_;
@@ -161,18 +186,23 @@ class Codec {
   int8_t *g_[2] = {}, *hx_[2] = {}, *fo_ = nullptr;
   void *xb16_ = nullptr, *y1b16_ = nullptr;  // bf16 (q - z) inputs of the convs
   uint16_t* d_cdf_ = nullptr;
-  uint32_t* d_enc_ = nullptr;
+  uint32_t* d_enc_ = nullptr;      // [5][P] intervals of the true symbols, by height 5..1
   // pinned host workspace
   void* hmem_ = nullptr;
   int64_t* h_N_ = nullptr;
+  int64_t* h_foff_ = nullptr;
+  DevFrame* h_fr_ = nullptr;
+  int* h_L_ = nullptr;
   int* h_err_ = nullptr;
-  uint8_t* h_codes_ = nullptr;  // coarse codes / decoded codes (max_points * 2)
-  uint32_t* h_enc_ = nullptr;
-  uint16_t* h_cdf_ = nullptr;
-  uint8_t* h_arena_ = nullptr;  // pinned, pre-faulted: coded substreams
+  uint64_t* h_keys6_ = nullptr;    // V_{b-1} keys of every frame (height 6)
+  uint8_t* h_codes_ = nullptr;     // [kHeights][P] codes by height
+  uint32_t* h_enc_ = nullptr;      // [5][P]
+  uint16_t* h_ring_ = nullptr;     // cumulative-table ring: 2 halves x ring_slots_ chunks
+  int ring_slots_ = 0;
+  uint8_t* h_arena_ = nullptr;     // pinned, pre-faulted: coded substreams
   size_t arena_cap_ = 0;
   struct SubTask {
-    int d;
+    int f, d;  // frame, depth
     int64_t start, count;
     size_t arena, len;
   };

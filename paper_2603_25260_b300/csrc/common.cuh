@@ -14,6 +14,20 @@ constexpr int kNsym = 255;      // occupancy classes (codes 1..255)
 constexpr int kFreqBits = 16;   // cumulative tables sum to 2^16
 constexpr int kFreqTotal = 1 << kFreqBits;
 
+// Frame batches: the frame index sits in the top six key bits, above the
+// Morton bits (3 L <= 57 for batched frames), so one sort and one set of
+// level arrays hold every frame of a batch, frame-major then Morton order.
+constexpr int kFrameShift = 58;
+constexpr int kMaxBatch = 64;
+constexpr uint64_t kLowMask = (1ull << kFrameShift) - 1;
+
+__host__ __device__ __forceinline__ uint64_t parent_key(uint64_t k) {
+  return (k & ~kLowMask) | ((k & kLowMask) >> 3);
+}
+__host__ __device__ __forceinline__ uint64_t child_key(uint64_t k, uint32_t c) {
+  return (k & ~kLowMask) | ((k & kLowMask) << 3) | c;
+}
+
 // Device error word values (first error wins).
 constexpr int kErrCoord = 1;    // coordinate outside [0, 2^L)
 constexpr int kErrHashFull = 2; // hash probe limit reached

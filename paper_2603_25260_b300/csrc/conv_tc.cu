@@ -48,7 +48,6 @@ struct ConvCfg {
   static constexpr int kStages = CIN == 64 ? 6 : 8;
   static constexpr int kStageBytes = kTileM * RB;
   static constexpr int kPerGroup = 256 / CIN;        // offsets per fp32 accumulator
-  static constexpr int kGroups = (27 + kPerGroup - 1) / kPerGroup;
   static constexpr int kBBlocks = (27 * CIN + 63) / 64;
   static constexpr int kBBytes = kBBlocks * 4096;
   static constexpr int kChunks = RB / 16;            // 16-byte chunks per row

@@ -54,18 +54,24 @@ __global__ void k_hash_insert(const uint64_t* __restrict__ keys, const int64_t* 
 }
 
 // One thread per (node, offset); offset o = 9(dx+1) + 3(dy+1) + (dz+1).
-__global__ void k_kernel_map(const uint64_t* __restrict__ keys, const int64_t* d_n, int depth,
+// The depth of a node is Lf[frame] - h for a frame batch (Lf != nullptr),
+// else h itself; neighbours keep the node's frame bits.
+__global__ void k_kernel_map(const uint64_t* __restrict__ keys, const int64_t* d_n,
+                             const int* __restrict__ Lf, int h,
                              const uint64_t* __restrict__ tk, const uint32_t* __restrict__ tv,
                              uint64_t mask, int32_t* nbr, int* err,
                              unsigned long long* pairs) {
   const int64_t n = *d_n;
   const int64_t total = n * 27;
-  const int32_t side = 1 << depth;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = t / 27;
     const int o = (int)(t - i * 27);
-    const uint64_t k = keys[i];
+    const uint64_t kf = keys[i];
+    const uint64_t fbits = kf & ~kLowMask;
+    const uint64_t k = kf & kLowMask;
+    const int depth = Lf ? Lf[kf >> kFrameShift] - h : h;
+    const int32_t side = 1 << depth;
     const int32_t x = (int32_t)compact3(k >> 2) + o / 9 - 1;
     const int32_t y = (int32_t)compact3(k >> 1) + (o / 3) % 3 - 1;
     const int32_t z = (int32_t)compact3(k) + o % 3 - 1;
@@ -73,7 +79,7 @@ __global__ void k_kernel_map(const uint64_t* __restrict__ keys, const int64_t* d
     if (o == 13) {
       r = (int32_t)i;
     } else if (x >= 0 && y >= 0 && z >= 0 && x < side && y < side && z < side) {
-      const uint64_t q = morton3((uint32_t)x, (uint32_t)y, (uint32_t)z);
+      const uint64_t q = fbits | morton3((uint32_t)x, (uint32_t)y, (uint32_t)z);
       uint64_t s = mix64(q) & mask;
       int p = 0;
       for (; p < kMaxProbe; p++) {
@@ -96,8 +102,8 @@ __global__ void k_kernel_map(const uint64_t* __restrict__ keys, const int64_t* d
   }
 }
 
-void launch_kernel_map(const uint64_t* keys, const int64_t* d_n, int64_t n_host, int depth,
-                       const HashTable& h, int64_t slots, int32_t* nbr, int* err,
+void launch_kernel_map(const uint64_t* keys, const int64_t* d_n, int64_t n_host, const int* Lf,
+                       int depth, const HashTable& h, int64_t slots, int32_t* nbr, int* err,
                        cudaStream_t st, uint64_t* pairs) {
   if (n_host <= 0) return;
   const uint64_t mask = (uint64_t)slots - 1;
@@ -106,7 +112,7 @@ void launch_kernel_map(const uint64_t* keys, const int64_t* d_n, int64_t n_host,
   k_hash_insert<<<(int)std::min<int64_t>((n_host + 255) / 256, 148 * 8), 256, 0, st>>>(
       keys, d_n, h.keys, h.vals, mask, err);
   k_kernel_map<<<(int)std::min<int64_t>((n_host * 27 + 255) / 256, 148 * 16), 256, 0, st>>>(
-      keys, d_n, depth, h.keys, h.vals, mask, nbr, err,
+      keys, d_n, Lf, depth, h.keys, h.vals, mask, nbr, err,
       reinterpret_cast<unsigned long long*>(pairs));
   count_launches(3);
 }

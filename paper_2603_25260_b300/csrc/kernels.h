@@ -22,9 +22,33 @@ struct SortScratch {
   int64_t n_max = 0;
 };
 int64_t sort_tiles(int64_t n);
-// Sort n keys (bits = significant low bits of the key).  Returns the buffer
-// holding the result (keys or scratch.alt).
-uint64_t* radix_sort(uint64_t* keys, int64_t n, int bits, const SortScratch& s, cudaStream_t st);
+// Sort n keys by their low `bits` bits and, if frame_bits, by the frame
+// bits 58..63 (8-bit digits; digits that are zero for every key are skipped).
+// Returns the buffer holding the result (keys or scratch.alt).
+uint64_t* radix_sort(uint64_t* keys, int64_t n, int bits, bool frame_bits, const SortScratch& s,
+                     cudaStream_t st);
+
+// One frame of a batch, as the device sees it.
+struct DevFrame {
+  const int32_t* xyz;  // encoder input [n][3]
+  int32_t* out;        // decoder output [n][3]
+  int64_t n;           // points (encoder) / voxels (decoder)
+  int64_t pre;         // first point of the frame in the batch
+  int L;               // octree depth
+  int pad;
+};
+// Morton keys of every frame, frame index in bits 58..63.
+void launch_morton_batch(const DevFrame* fr, int nf, int64_t total, uint64_t* keys, int* err,
+                         cudaStream_t st);
+// Level arrays by height (0 = leaves) for the frame-offset search.
+constexpr int kHeights = 7;  // heights 0..6 (depths L .. L-6 = b-1 of every frame)
+struct LevelPtrs {
+  const uint64_t* key[kHeights];
+  const int64_t* n[kHeights];
+};
+void launch_frame_offsets(const LevelPtrs& lv, int nh, int nf, int64_t* foff, cudaStream_t st);
+void launch_keys_to_xyz_batch(const uint64_t* keys, const int64_t* d_n, int64_t n_host,
+                              const DevFrame* fr, const int64_t* foff0, cudaStream_t st);
 
 // xyz int32 [n][3] -> Morton keys; out-of-range coordinates set err.
 void launch_morton(const int32_t* xyz, int64_t n, int L, uint64_t* keys, int* err,
@@ -60,11 +84,13 @@ struct HashTable {
   uint32_t* vals = nullptr;
   int64_t cap = 0;  // allocated slots (power of two)
 };
-// Clear `slots` (power of two <= cap) slots, insert the N keys of one depth,
-// then write the 27-neighbour map nbr[N][27].  If pairs != nullptr, the
-// number of present (node, neighbour) pairs, centre included, is added to it.
-void launch_kernel_map(const uint64_t* keys, const int64_t* d_n, int64_t n_host, int depth,
-                       const HashTable& h, int64_t slots, int32_t* nbr, int* err,
+// Clear `slots` (power of two <= cap) slots, insert the N keys of one level,
+// then write the 27-neighbour map nbr[N][27].  Node depth: Lf[frame] - depth
+// for a frame batch (Lf = per-frame octree depths on the device), else
+// `depth`.  If pairs != nullptr, the number of present (node, neighbour)
+// pairs, centre included, is added to it.
+void launch_kernel_map(const uint64_t* keys, const int64_t* d_n, int64_t n_host, const int* Lf,
+                       int depth, const HashTable& h, int64_t slots, int32_t* nbr, int* err,
                        cudaStream_t st, uint64_t* pairs = nullptr);
 
 // ---------------------------------------------------------------- layers --

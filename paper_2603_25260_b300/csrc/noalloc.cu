@@ -77,7 +77,7 @@ extern "C" int lpc_kernel_map_noalloc(const uint64_t* d_keys, int64_t N, int dep
   const int64_t n_host = N;
   cudaMemcpyAsync(d_n, &n_host, sizeof(n_host), cudaMemcpyHostToDevice, st);
   cudaMemsetAsync(d_err, 0, sizeof(int), st);
-  lpc::launch_kernel_map(d_keys, d_n, N, depth, h, slots, d_nbr, d_err, st);
+  lpc::launch_kernel_map(d_keys, d_n, N, nullptr, depth, h, slots, d_nbr, d_err, st);
   int e = 0;
   cudaMemcpyAsync(&e, d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess)

@@ -127,12 +127,17 @@ k_rs_scatter(const uint64_t* __restrict__ in, uint64_t* __restrict__ out, int64_
   }
 }
 
-uint64_t* radix_sort(uint64_t* keys, int64_t n, int bits, const SortScratch& s, cudaStream_t st) {
+uint64_t* radix_sort(uint64_t* keys, int64_t n, int bits, bool frame_bits, const SortScratch& s,
+                     cudaStream_t st) {
   if (n <= 1) return keys;
   const int64_t nt = sort_tiles(n);
   uint64_t* a = keys;
   uint64_t* b = s.alt;
-  for (int shift = 0; shift < bits; shift += 8) {
+  int shifts[9], ns = 0;
+  for (int shift = 0; shift < bits && shift < 56; shift += 8) shifts[ns++] = shift;
+  if (frame_bits || bits > 56) shifts[ns++] = 56;
+  for (int i = 0; i < ns; i++) {
+    const int shift = shifts[i];
     k_rs_hist<<<(unsigned)nt, kRsThreads, 0, st>>>(a, n, shift, s.hist, nt);
     k_scan_single<<<1, 1024, 0, st>>>(s.hist, 256 * nt);
     k_rs_scatter<<<(unsigned)nt, kRsThreads, 0, st>>>(a, b, n, shift, s.hist, nt);
@@ -183,6 +188,93 @@ void launch_keys_to_xyz(const uint64_t* keys, const int64_t* d_n, int64_t cap, i
   if (cap <= 0) return;
   int blocks = (int)std::min<int64_t>((cap + 255) / 256, 148 * 8);
   k_keys_to_xyz<<<blocks, 256, 0, st>>>(keys, d_n, xyz);
+  count_launches(1);
+}
+
+// ------------------------------------------------------ frame batches --
+// Key of point i of the batch: (frame << 58) | Morton(x, y, z); the frame of
+// a global index is found by binary search over the frames' prefix counts.
+__global__ void k_morton_batch(const DevFrame* __restrict__ fr, int nf, int64_t total,
+                               uint64_t* keys, int* err) {
+  __shared__ DevFrame sf[kMaxBatch];
+  for (int i = threadIdx.x; i < nf; i += blockDim.x) sf[i] = fr[i];
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = nf - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (sf[mid].pre <= i) lo = mid;
+      else hi = mid - 1;
+    }
+    const DevFrame& f = sf[lo];
+    const int64_t j = i - f.pre;
+    const int32_t side = 1 << f.L;
+    int32_t x = f.xyz[3 * j], y = f.xyz[3 * j + 1], z = f.xyz[3 * j + 2];
+    if (x < 0 || y < 0 || z < 0 || x >= side || y >= side || z >= side) {
+      set_error(err, kErrCoord);
+      x = y = z = 0;
+    }
+    keys[i] = ((uint64_t)lo << kFrameShift) | morton3((uint32_t)x, (uint32_t)y, (uint32_t)z);
+  }
+}
+
+void launch_morton_batch(const DevFrame* fr, int nf, int64_t total, uint64_t* keys, int* err,
+                         cudaStream_t st) {
+  if (total <= 0) return;
+  const int blocks = (int)std::min<int64_t>((total + 255) / 256, 148 * 8);
+  k_morton_batch<<<blocks, 256, 0, st>>>(fr, nf, total, keys, err);
+  count_launches(1);
+}
+
+// foff[h * (nf + 1) + f] = first row of frame f in the level array of
+// height h (lower bound of f << 58); the last entry is the level size.
+__global__ void k_frame_offsets(LevelPtrs lv, int nh, int nf, int64_t* foff) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nh * (nf + 1)) return;
+  const int h = t / (nf + 1), f = t % (nf + 1);
+  const int64_t n = *lv.n[h];
+  int64_t r = n;
+  if (f < nf) {
+    const uint64_t target = (uint64_t)f << kFrameShift;
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (lv.key[h][mid] < target) lo = mid + 1;
+      else hi = mid;
+    }
+    r = lo;
+  }
+  foff[t] = r;
+}
+
+void launch_frame_offsets(const LevelPtrs& lv, int nh, int nf, int64_t* foff, cudaStream_t st) {
+  const int n = nh * (nf + 1);
+  k_frame_offsets<<<(n + 127) / 128, 128, 0, st>>>(lv, nh, nf, foff);
+  count_launches(1);
+}
+
+// Leaf keys -> coordinates in every frame's own output buffer.
+__global__ void k_keys_to_xyz_batch(const uint64_t* __restrict__ keys, const int64_t* d_n,
+                                    const DevFrame* __restrict__ fr, const int64_t* foff0) {
+  const int64_t n = *d_n;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t kf = keys[i];
+    const int f = (int)(kf >> kFrameShift);
+    const uint64_t k = kf & kLowMask;
+    int32_t* out = fr[f].out + 3 * (i - foff0[f]);
+    out[0] = (int32_t)compact3(k >> 2);
+    out[1] = (int32_t)compact3(k >> 1);
+    out[2] = (int32_t)compact3(k);
+  }
+}
+
+void launch_keys_to_xyz_batch(const uint64_t* keys, const int64_t* d_n, int64_t n_host,
+                              const DevFrame* fr, const int64_t* foff0, cudaStream_t st) {
+  if (n_host <= 0) return;
+  const int blocks = (int)std::min<int64_t>((n_host + 255) / 256, 148 * 8);
+  k_keys_to_xyz_batch<<<blocks, 256, 0, st>>>(keys, d_n, fr, foff0);
   count_launches(1);
 }
 
@@ -288,16 +380,19 @@ struct LevelOp {
   uint32_t* poff;
   uint32_t* cpar;
   int64_t* np;
-  __device__ uint32_t value(int64_t i) const { return i == 0 || (ck[i] >> 3) != (ck[i - 1] >> 3); }
+  __device__ uint32_t value(int64_t i) const {
+    return i == 0 || parent_key(ck[i]) != parent_key(ck[i - 1]);
+  }
   __device__ void emit(int64_t i, uint32_t ex, int64_t n) const {
     const uint32_t h = value(i);
     cpar[i] = ex + h - 1;
     if (h) {
-      const uint64_t p = ck[i] >> 3;
+      const uint64_t p = parent_key(ck[i]);
       pk[ex] = p;
       poff[ex] = (uint32_t)i;
       uint32_t code = 0;
-      for (int64_t j = i; j < n && j < i + 8 && (ck[j] >> 3) == p; j++) code |= 1u << (ck[j] & 7);
+      for (int64_t j = i; j < n && j < i + 8 && parent_key(ck[j]) == p; j++)
+        code |= 1u << (ck[j] & 7);
       pc[ex] = (uint8_t)code;
     }
   }
@@ -328,11 +423,10 @@ struct ExpandOp {
     poff[p] = ex;
     const uint32_t code = pc[p];
     if (code == 0) set_error(err, kErrExpand);
-    const uint64_t base = pk[p] << 3;
     uint32_t r = ex;
     for (int c = 0; c < 8; c++)
       if (code >> c & 1) {
-        ck[r] = base | (uint64_t)c;
+        ck[r] = child_key(pk[p], (uint32_t)c);
         cpar[r] = (uint32_t)p;
         r++;
       }

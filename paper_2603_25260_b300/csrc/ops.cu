@@ -78,7 +78,7 @@ extern "C" {
 
 int lpc_build_levels(const int32_t* d_xyz, int64_t n, int L, uint64_t* d_keys, uint8_t* d_codes,
                      int64_t* h_counts, int64_t cap, uint64_t stream) {
-  if (L < 1 || L > kMaxDepth || n < 0 || !h_counts) return LPC_INVALID_ARG;
+  if (L < 1 || L > 19 || n < 0 || !h_counts) return LPC_INVALID_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (n == 0) {
     for (int d = 0; d <= L; d++) h_counts[d] = 0;
@@ -114,7 +114,7 @@ int lpc_build_levels(const int32_t* d_xyz, int64_t n, int L, uint64_t* d_keys, u
     return LPC_CUDA_ERROR;
   cudaMemsetAsync(d_err, 0, 4, st);
   launch_morton(d_xyz, nn, L, k0, d_err, st);
-  uint64_t* sorted = radix_sort(k0, nn, 3 * L, ss, st);
+  uint64_t* sorted = radix_sort(k0, nn, 3 * L, false, ss, st);
   launch_unique(sorted, d_n, nn, key[L], d_N + L, sc, st);
   for (int d = L - 1; d >= 0; d--)
     launch_level_up(key[d + 1], d_N + d + 1, capd[d + 1], key[d], code[d], off[d], par[d + 1],
@@ -157,7 +157,7 @@ int lpc_kernel_map(const uint64_t* d_keys, int64_t N, int depth, int32_t* d_nbr,
   int* d_err = t.get<int>(1);
   if (!h.keys || !h.vals || !d_n || !d_err) return LPC_CUDA_ERROR;
   cudaMemsetAsync(d_err, 0, 4, st);
-  launch_kernel_map(d_keys, d_n, N, depth, h, slots, d_nbr, d_err, st);
+  launch_kernel_map(d_keys, d_n, N, nullptr, depth, h, slots, d_nbr, d_err, st);
   return finish(st, d_err);
 }
 

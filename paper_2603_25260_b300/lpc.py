@@ -31,7 +31,8 @@ class LpcError(RuntimeError):
 class Config(C.Structure):
     _fields_ = [("L", C.c_int), ("C", C.c_int), ("b_off", C.c_int), ("t_off", C.c_int),
                 ("max_points", C.c_int64), ("max_frames", C.c_int), ("chunk", C.c_int),
-                ("host_threads", C.c_int), ("cuda_stream", C.c_uint64)]
+                ("host_threads", C.c_int), ("cuda_stream", C.c_uint64),
+                ("max_batch_points", C.c_int64)]
 
 
 _lib = None
@@ -100,13 +101,14 @@ class Codec:
     """One codec instance on the current CUDA device and stream."""
 
     def __init__(self, blob: bytes, L: int, max_points: int, max_frames: int = 1,
-                 chunk: int = 4096, host_threads: int = 0, stream: int | None = None):
+                 chunk: int = 4096, host_threads: int = 0, stream: int | None = None,
+                 max_batch_points: int = 0):
         self._lib = lib()
         self.blob = bytes(blob)
         self.L = L
         self.max_points = max_points
         cfg = Config(L, 32, 5, 4, max_points, max_frames, chunk, host_threads,
-                     _stream() if stream is None else stream)
+                     _stream() if stream is None else stream, max_batch_points)
         h = P()
         st = self._lib.codec_create(C.byref(cfg), self.blob, len(self.blob), C.byref(h))
         if st != OK:
