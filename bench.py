@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--batch-frames", type=int, default=64)
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-train", action="store_true")
+    ap.add_argument("--train-steps", type=int, default=3)
     return ap.parse_args()
 
 
@@ -189,6 +191,44 @@ def run_reference(args):
 
 # ------------------------------------------------------------------ ours --
 
+def train_leg(args, flush, stream):
+    """Training throughput of the differentiable twin: one step = forward and
+    backward over the 8-frame training batch (64-beam frames), gradient
+    clipping and the AdamW update; fake quantisers on, bf16 operands.  Index
+    structures are built once before timing, as a data loader would."""
+    import torch
+    from paper_2603_25260_b300 import train as TR
+
+    specs = synth.training_specs()
+    xyz = [synth.make_frame(s) for s in specs]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    frames = [TR.Frame(torch.from_numpy(f).cuda(), s.L) for f, s in zip(xyz, specs)]
+    torch.cuda.synchronize()
+    build_ms = 1e3 * (time.perf_counter() - t0) / len(frames)
+    model = TR.QATModel(synth.twin_params(0), qat=True, bf16=True)
+    opt = TR.make_optimizer(model)
+    for _ in range(2):
+        TR.train_step(model, opt, frames)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(args.train_steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        loss = TR.train_step(model, opt, frames)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    npts = sum(f.n for f in frames)
+    step = statistics.median(ms)
+    return {"frames_per_step": len(frames), "points_per_step": npts,
+            "ms_per_step": round(step, 3), "steps_per_s": round(1e3 / step, 4),
+            "mpoints_per_s": round(npts / step / 1e3, 4), "bits_per_point": round(loss, 4),
+            "mode": "fake-quant on, bf16 operands, fp32 accumulation",
+            "structure_ms_per_frame": round(build_ms, 3)}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -316,6 +356,8 @@ def run_ours(args):
                    "bits_per_point": round(8 * sum(len(s) for s in streams) / npts, 4)}
         bcodec.close()
 
+    train = None if args.no_train else train_leg(args, flush, stream)
+
     if rank != 0:
         return
     hbm, sm_max, src = peaks()
@@ -367,6 +409,7 @@ def run_ours(args):
         "decode_mpts": round(n / (statistics.median(dec_ms) / 1e3) / 1e6, 4),
         "bits_per_point": round(8 * nbytes / n, 4),
         "batched": batched,
+        "train": train,
         "e2e": {"value": round(e2e_value, 4), "unit": "Mpoints/s",
                 "h2d_bytes_per_step": int(frame.nbytes), "d2h_bytes_per_step": int(12 * n_out)},
         "gpu_launches": int(gpu_launches),

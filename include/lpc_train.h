@@ -1,0 +1,85 @@
+/*
+ * lpc_train.h -- differentiable (quantisation-aware) twin of the codec's
+ * network ops, for training on the rate loss (the occupancy cross-entropy of
+ * the supplement's training section, in bits).
+ *
+ * Every op has a forward and a hand-written backward kernel.  Tensors are
+ * device float32, row-major [rows][channels]; "bf16" = 1 rounds the operands
+ * of every product to bf16 before multiplying (accumulation stays float32).
+ * Weight layouts follow the integer blob: W[slices][cout][cin].  Backward
+ * calls ADD into dW / db / dE / da (zero them first); dx is overwritten and
+ * may be NULL when not needed.  All calls return LPC_* statuses (lpc.h) and
+ * are asynchronous on `stream`.
+ *
+ * Index structures (integer, not differentiated) come from the codec's octree
+ * and kernel-map builders: nbr[N][27] neighbour rows (-1 absent); par[r] the
+ * parent row of child r; off[p]..off[p+1] the child rows of parent p;
+ * ckey[r] & 7 the child slot of r.
+ */
+#ifndef LPC_TRAIN_H
+#define LPC_TRAIN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Sparse 3x3x3 conv (Eq. 5): y[i] = b + sum_o W[o] x[nbr[i][o]]. */
+int lpc_t_conv_fwd(const float* x, int64_t N, int cin, const int32_t* nbr, const float* W,
+                   const float* b, int cout, float* y, int bf16, uint64_t stream);
+/* dx[i] = sum_o W[o]^T dy[nbr[i][26 - o]] (mirror offset); dW[o] += sum_i
+ * dy[i] x[nbr[i][o]]^T; db += sum_i dy[i]. */
+int lpc_t_conv_bwd(const float* x, const float* dy, int64_t N, int cin, const int32_t* nbr,
+                   const float* W, int cout, float* dx, float* dW, float* db, int bf16,
+                   uint64_t stream);
+
+/* Upsampling + Pruning (Eq. 6): y[r] = b[c] + W[c] x[par[r]], c = ckey[r] & 7. */
+int lpc_t_up_fwd(const float* x, int cin, const uint32_t* par, const uint64_t* ckey, int64_t Nc,
+                 const float* W, const float* b, int cout, float* y, int bf16, uint64_t stream);
+/* dx[p] = sum over children r of W[c_r]^T dy[r]; dW[c] += sum_{c_r = c} dy[r]
+ * x[par r]^T; db[c] += sum_{c_r = c} dy[r]. */
+int lpc_t_up_bwd(const float* x, const float* dy, int64_t Np, int cin, const uint32_t* off,
+                 const uint32_t* par, const uint64_t* ckey, int64_t Nc, const float* W, int cout,
+                 float* dx, float* dW, float* db, int bf16, uint64_t stream);
+
+/* Stride-2 down conv (Eq. 4): y[p] = b + sum_{r child of p} W[c_r] x[r]. */
+int lpc_t_down_fwd(const float* x, int cin, const uint32_t* off, const uint64_t* ckey, int64_t Np,
+                   const float* W, const float* b, int cout, float* y, int bf16,
+                   uint64_t stream);
+/* dx[r] = W[c_r]^T dy[par r]; dW[c] += sum_{c_r = c} dy[par r] x[r]^T;
+ * db += sum_p dy[p]. */
+int lpc_t_down_bwd(const float* x, const float* dy, int64_t Nc, int cin, const uint32_t* par,
+                   const uint64_t* ckey, int64_t Np, const float* W, int cout, float* dx,
+                   float* dW, float* db, int bf16, uint64_t stream);
+
+/* Occupancy-code embedding: y[i] = E[codes[i]]; dE[codes[i]] += dy[i]. */
+int lpc_t_embed_fwd(const uint8_t* codes, int64_t N, const float* E, int C, float* y,
+                    uint64_t stream);
+int lpc_t_embed_bwd(const uint8_t* codes, int64_t N, const float* dy, int C, float* dE,
+                    uint64_t stream);
+
+/* PReLU with a per-channel slope a[C]. */
+int lpc_t_prelu_fwd(const float* x, int64_t N, int C, const float* a, float* y, uint64_t stream);
+int lpc_t_prelu_bwd(const float* x, const float* dy, int64_t N, int C, const float* a, float* dx,
+                    float* da, uint64_t stream);
+
+/* Fake quantisation of Eq. 12 with a straight-through gradient:
+ * y = (clip(round(x / s) + z, -128, 127) - z) s; mask[i] = 1 where the clip
+ * is inactive; dx = dy * mask. */
+int lpc_t_fq_fwd(const float* x, int64_t n, float s, int z, float* y, uint8_t* mask,
+                 uint64_t stream);
+int lpc_t_fq_bwd(const float* dy, const uint8_t* mask, int64_t n, float* dx, uint64_t stream);
+
+/* Octree levels with parent rows and child offsets, for the index
+ * structures above: concatenations over depths 0..L (keys, par) and
+ * 0..L-1 (codes, off with N_d + 1 entries each); counts[d] = N_d. */
+int lpc_t_levels(const int32_t* d_xyz, int64_t n, int L, uint64_t* d_keys, uint8_t* d_codes,
+                 uint32_t* d_par, uint32_t* d_off, int64_t* h_counts, int64_t cap,
+                 uint64_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LPC_TRAIN_H */

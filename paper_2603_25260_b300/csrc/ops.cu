@@ -6,6 +6,7 @@
 #include <vector>
 
 #include "../../include/lpc_ops.h"
+#include "../../include/lpc_train.h"
 #include "common.cuh"
 #include "kernels.h"
 #include "model.h"
@@ -78,6 +79,12 @@ extern "C" {
 
 int lpc_build_levels(const int32_t* d_xyz, int64_t n, int L, uint64_t* d_keys, uint8_t* d_codes,
                      int64_t* h_counts, int64_t cap, uint64_t stream) {
+  return lpc_t_levels(d_xyz, n, L, d_keys, d_codes, nullptr, nullptr, h_counts, cap, stream);
+}
+
+int lpc_t_levels(const int32_t* d_xyz, int64_t n, int L, uint64_t* d_keys, uint8_t* d_codes,
+                 uint32_t* d_par, uint32_t* d_off, int64_t* h_counts, int64_t cap,
+                 uint64_t stream) {
   if (L < 1 || L > 19 || n < 0 || !h_counts) return LPC_INVALID_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (n == 0) {
@@ -125,14 +132,19 @@ int lpc_build_levels(const int32_t* d_xyz, int64_t n, int L, uint64_t* d_keys, u
   int64_t tot = 0;
   for (int d = 0; d <= L; d++) tot += h_counts[d];
   if (tot > cap) return LPC_CAPACITY;
-  int64_t kp = 0, cp = 0;
+  int64_t kp = 0, cp = 0, op = 0;
   for (int d = 0; d <= L; d++) {
     if (d_keys)
       cudaMemcpyAsync(d_keys + kp, key[d], 8 * h_counts[d], cudaMemcpyDeviceToDevice, st);
+    if (d_par && d > 0)
+      cudaMemcpyAsync(d_par + kp, par[d], 4 * h_counts[d], cudaMemcpyDeviceToDevice, st);
     kp += h_counts[d];
     if (d < L) {
       if (d_codes) cudaMemcpyAsync(d_codes + cp, code[d], h_counts[d], cudaMemcpyDeviceToDevice, st);
+      if (d_off)
+        cudaMemcpyAsync(d_off + op, off[d], 4 * (h_counts[d] + 1), cudaMemcpyDeviceToDevice, st);
       cp += h_counts[d];
+      op += h_counts[d] + 1;
     }
   }
   return finish(st, nullptr);

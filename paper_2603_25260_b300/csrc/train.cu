@@ -1,0 +1,413 @@
+// Differentiable (quantisation-aware) twin of the network ops, forward and
+// hand-written backward, float32 with an optional bf16 rounding of every
+// product operand (fp32 accumulation).  Two generic kernels cover the sparse
+// ops:
+//  - k_gmv: out[row] = (bias) + sum over the row's items (slice s, source
+//    row r) of Wsl[s] in[r], one warp per output row, the weight tensor in
+//    shared memory laid out [slice][k][j] so that lane j reads consecutive
+//    words.  Forward of conv / up / down and their input gradients (through
+//    the mirrored index structure) are instances.
+//  - k_outer: dW[s] += sum over rows of dy[a(row)] x[b(row)]^T for the rows
+//    whose item belongs to slice s: the weight gradients.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "../../include/lpc.h"
+#include "../../include/lpc_train.h"
+#include "common.cuh"
+#include "kernels.h"
+
+namespace lpc {
+namespace {
+
+__device__ __forceinline__ float rnd(float v, int bf16) {
+  return bf16 ? __bfloat162float(__float2bfloat16_rn(v)) : v;
+}
+
+constexpr int kWarpsT = 8;
+
+// ---- index structures as item visitors --------------------------------------
+// conv forward: row i, items (o, nbr[i][o]); backward dx: (o, nbr[i][26 - o])
+struct ConvItems {
+  const int32_t* nbr;
+  int mirror;
+  template <class F>
+  __device__ void visit(int64_t i, F f) const {
+    for (int o = 0; o < 27; o++) {
+      const int32_t r = nbr[i * 27 + (mirror ? 26 - o : o)];
+      if (r >= 0) f(o, (int64_t)r);
+    }
+  }
+};
+// up forward: child row r, one item (c_r, par[r])
+struct UpFwdItems {
+  const uint32_t* par;
+  const uint64_t* ckey;
+  template <class F>
+  __device__ void visit(int64_t r, F f) const {
+    f((int)(ckey[r] & 7), (int64_t)par[r]);
+  }
+};
+// up backward dx / down forward: parent row p, items (c_r, r) over children
+struct ChildItems {
+  const uint32_t* off;
+  const uint64_t* ckey;
+  template <class F>
+  __device__ void visit(int64_t p, F f) const {
+    for (uint32_t r = off[p]; r < off[p + 1]; r++) f((int)(ckey[r] & 7), (int64_t)r);
+  }
+};
+
+template <int OUT, int IN, class Items>
+__global__ void __launch_bounds__(kWarpsT * 32)
+k_gmv(Items items, const float* __restrict__ W, int S, int transpose,
+      const float* __restrict__ bias, int bias_mode, const float* __restrict__ in, int64_t rows,
+      float* __restrict__ out, int bf16) {
+  extern __shared__ float sW[];  // [S][IN][OUT]
+  const int n = S * IN * OUT;
+  for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
+    const int s = idx / (IN * OUT), rem = idx % (IN * OUT), k = rem / OUT, j = rem % OUT;
+    // W is [S][cout][cin]; forward: k = cin, j = cout; transpose: k = cout, j = cin
+    const float w = transpose ? W[((size_t)s * IN + k) * OUT + j] : W[((size_t)s * OUT + j) * IN + k];
+    sW[idx] = rnd(w, bf16);
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * kWarpsT;
+  for (int64_t row = (int64_t)blockIdx.x * kWarpsT + (threadIdx.x >> 5); row < rows;
+       row += warps) {
+    float acc[OUT / 32];
+#pragma unroll
+    for (int q = 0; q < OUT / 32; q++) acc[q] = bias_mode == 1 ? bias[lane + 32 * q] : 0.f;
+    items.visit(row, [&](int s, int64_t src) {
+      const float* w = sW + (size_t)s * IN * OUT + lane;
+      const float* x = in + src * IN;
+      if (bias_mode == 2) {
+#pragma unroll
+        for (int q = 0; q < OUT / 32; q++) acc[q] += bias[s * OUT + lane + 32 * q];
+      }
+      for (int k = 0; k < IN; k++) {
+        const float v = rnd(__ldg(x + k), bf16);
+#pragma unroll
+        for (int q = 0; q < OUT / 32; q++) acc[q] += w[k * OUT + 32 * q] * v;
+      }
+    });
+#pragma unroll
+    for (int q = 0; q < OUT / 32; q++) out[row * OUT + lane + 32 * q] = acc[q];
+  }
+}
+
+// ---- weight gradients ---------------------------------------------------------
+// pair(s, row) -> (a, b): dW[s][i][j] += dy[a][i] * x[b][j]; a < 0 skips.
+struct ConvPairs {
+  const int32_t* nbr;
+  __device__ void pair(int s, int64_t row, int64_t& a, int64_t& b) const {
+    const int32_t r = nbr[row * 27 + s];
+    a = r >= 0 ? row : -1;
+    b = r;
+  }
+};
+struct UpPairs {  // rows = children; dy row = child, x row = parent
+  const uint32_t* par;
+  const uint64_t* ckey;
+  __device__ void pair(int s, int64_t row, int64_t& a, int64_t& b) const {
+    a = (int)(ckey[row] & 7) == s ? row : -1;
+    b = par[row];
+  }
+};
+struct DownPairs {  // rows = children; dy row = parent, x row = child
+  const uint32_t* par;
+  const uint64_t* ckey;
+  __device__ void pair(int s, int64_t row, int64_t& a, int64_t& b) const {
+    a = (int)(ckey[row] & 7) == s ? (int64_t)par[row] : -1;
+    b = row;
+  }
+};
+
+constexpr int kOuterRows = 512;  // rows per block
+constexpr int kStage = 32;       // rows staged in shared memory at a time
+
+template <int A, int B, class Pairs>
+__global__ void __launch_bounds__(256)
+k_outer(Pairs pairs, const float* __restrict__ dy, const float* __restrict__ x, int64_t rows,
+        float* dW, int bf16) {
+  __shared__ float sy[kStage][A];
+  __shared__ float sx[kStage][B];
+  constexpr int kPer = A * B / 256;
+  const int s = blockIdx.y;
+  float acc[kPer];
+#pragma unroll
+  for (int u = 0; u < kPer; u++) acc[u] = 0.f;
+  const int64_t r0 = (int64_t)blockIdx.x * kOuterRows;
+  const int64_t r1 = std::min<int64_t>(rows, r0 + kOuterRows);
+  for (int64_t base = r0; base < r1; base += kStage) {
+    for (int idx = threadIdx.x; idx < kStage * (A + B); idx += 256) {
+      const int r = idx / (A + B), c = idx % (A + B);
+      const int64_t row = base + r;
+      int64_t a = -1, b = -1;
+      if (row < r1) pairs.pair(s, row, a, b);
+      float v = 0.f;
+      if (a >= 0) v = c < A ? dy[a * A + c] : x[b * B + (c - A)];
+      if (c < A) sy[r][c] = rnd(v, bf16);
+      else sx[r][c - A] = rnd(v, bf16);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < kPer; u++) {
+      const int q = threadIdx.x + 256 * u, i = q / B, j = q % B;
+      float t = 0.f;
+#pragma unroll 8
+      for (int r = 0; r < kStage; r++) t += sy[r][i] * sx[r][j];
+      acc[u] += t;
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < kPer; u++) {
+    const int q = threadIdx.x + 256 * u;
+    atomicAdd(dW + (size_t)s * A * B + q, acc[u]);
+  }
+}
+
+// db[slice(row)][j] += dy[row][j]; slice_key = nullptr: one slice.
+__global__ void k_bias_grad(const float* __restrict__ dy, int64_t rows, int C,
+                            const uint64_t* __restrict__ slice_key, float* db) {
+  __shared__ float part[8 * 64];
+  for (int i = threadIdx.x; i < 8 * C; i += blockDim.x) part[i] = 0.f;
+  __syncthreads();
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < rows * C;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = q / C;
+    const int j = (int)(q - r * C);
+    const int s = slice_key ? (int)(slice_key[r] & 7) : 0;
+    atomicAdd(&part[s * C + j], dy[q]);
+  }
+  __syncthreads();
+  const int ns = slice_key ? 8 : 1;
+  for (int i = threadIdx.x; i < ns * C; i += blockDim.x)
+    if (part[i] != 0.f) atomicAdd(db + i, part[i]);
+}
+
+// ---- embedding, PReLU, fake quantisation -----------------------------------
+__global__ void k_embed_f(const uint8_t* codes, int64_t N, const float* E, int C, float* y) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < N * C;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = q / C;
+    y[q] = E[codes[r] * C + (q - r * C)];
+  }
+}
+__global__ void k_embed_b(const uint8_t* codes, int64_t N, const float* dy, int C, float* dE) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < N * C;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = q / C;
+    atomicAdd(dE + codes[r] * C + (q - r * C), dy[q]);
+  }
+}
+__global__ void k_prelu_f(const float* x, int64_t N, int C, const float* a, float* y) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < N * C;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const float v = x[q];
+    y[q] = v >= 0.f ? v : a[q % C] * v;
+  }
+}
+__global__ void k_prelu_b(const float* x, const float* dy, int64_t N, int C, const float* a,
+                          float* dx, float* da) {
+  __shared__ float part[256];
+  for (int i = threadIdx.x; i < C; i += blockDim.x) part[i] = 0.f;
+  __syncthreads();
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < N * C;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(q % C);
+    const float v = x[q], g = dy[q];
+    if (dx) dx[q] = v >= 0.f ? g : a[c] * g;
+    if (v < 0.f) atomicAdd(&part[c], g * v);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < C; i += blockDim.x)
+    if (part[i] != 0.f) atomicAdd(da + i, part[i]);
+}
+__global__ void k_fq_f(const float* x, int64_t n, float s, int z, float* y, uint8_t* mask) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const float r = rintf(x[q] / s) + (float)z;
+    const float c = fminf(fmaxf(r, -128.f), 127.f);
+    y[q] = (c - (float)z) * s;
+    mask[q] = r >= -128.f && r <= 127.f;
+  }
+}
+__global__ void k_fq_b(const float* dy, const uint8_t* mask, int64_t n, float* dx) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
+       q += (int64_t)gridDim.x * blockDim.x)
+    dx[q] = mask[q] ? dy[q] : 0.f;
+}
+
+int grid_for(int64_t work, int threads = 256) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>((work + threads - 1) / threads, 148 * 8));
+}
+
+template <class Items>
+int gmv(Items it, const float* W, int S, int out, int in, int transpose, const float* bias,
+        int bias_mode, const float* x, int64_t rows, float* y, int bf16, cudaStream_t st) {
+  if (rows <= 0) return LPC_OK;
+  const size_t smem = sizeof(float) * (size_t)S * in * out;
+  const int blocks = (int)std::min<int64_t>((rows + kWarpsT - 1) / kWarpsT, 148 * 2);
+#define LPC_GMV(O, I)                                                                       \
+  do {                                                                                      \
+    cudaFuncSetAttribute(k_gmv<O, I, Items>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+                         (int)smem);                                                        \
+    k_gmv<O, I, Items><<<blocks, kWarpsT * 32, smem, st>>>(it, W, S, transpose, bias,       \
+                                                           bias_mode, x, rows, y, bf16);    \
+  } while (0)
+  if (out == 32 && in == 32) LPC_GMV(32, 32);
+  else if (out == 32 && in == 64) LPC_GMV(32, 64);
+  else if (out == 64 && in == 32) LPC_GMV(64, 32);
+  else return LPC_INVALID_ARG;
+#undef LPC_GMV
+  count_launches(1);
+  return cudaGetLastError() == cudaSuccess ? LPC_OK : LPC_CUDA_ERROR;
+}
+
+template <class Pairs>
+int outer(Pairs p, int S, int A, int B, const float* dy, const float* x, int64_t rows,
+          float* dW, int bf16, cudaStream_t st) {
+  if (rows <= 0 || !dW) return LPC_OK;
+  dim3 grid((unsigned)((rows + kOuterRows - 1) / kOuterRows), (unsigned)S);
+  if (A == 32 && B == 32) k_outer<32, 32, Pairs><<<grid, 256, 0, st>>>(p, dy, x, rows, dW, bf16);
+  else if (A == 32 && B == 64) k_outer<32, 64, Pairs><<<grid, 256, 0, st>>>(p, dy, x, rows, dW, bf16);
+  else return LPC_INVALID_ARG;
+  count_launches(1);
+  return cudaGetLastError() == cudaSuccess ? LPC_OK : LPC_CUDA_ERROR;
+}
+
+int bias_grad(const float* dy, int64_t rows, int C, const uint64_t* slice_key, float* db,
+              cudaStream_t st) {
+  if (rows <= 0 || !db) return LPC_OK;
+  k_bias_grad<<<grid_for(rows * C), 256, 0, st>>>(dy, rows, C, slice_key, db);
+  count_launches(1);
+  return cudaGetLastError() == cudaSuccess ? LPC_OK : LPC_CUDA_ERROR;
+}
+
+bool ok_dims(int cin, int cout) { return cout == 32 && (cin == 32 || cin == 64); }
+
+}  // namespace
+}  // namespace lpc
+
+using namespace lpc;
+
+extern "C" {
+
+int lpc_t_conv_fwd(const float* x, int64_t N, int cin, const int32_t* nbr, const float* W,
+                   const float* b, int cout, float* y, int bf16, uint64_t stream) {
+  if (N < 0 || !ok_dims(cin, cout)) return LPC_INVALID_ARG;
+  return gmv(ConvItems{nbr, 0}, W, 27, cout, cin, 0, b, b ? 1 : 0, x, N, y, bf16,
+             reinterpret_cast<cudaStream_t>(stream));
+}
+
+int lpc_t_conv_bwd(const float* x, const float* dy, int64_t N, int cin, const int32_t* nbr,
+                   const float* W, int cout, float* dx, float* dW, float* db, int bf16,
+                   uint64_t stream) {
+  if (N < 0 || !ok_dims(cin, cout)) return LPC_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  int s = LPC_OK;
+  if (dx) s = gmv(ConvItems{nbr, 1}, W, 27, cin, cout, 1, nullptr, 0, dy, N, dx, bf16, st);
+  if (!s) s = outer(ConvPairs{nbr}, 27, cout, cin, dy, x, N, dW, bf16, st);
+  if (!s) s = bias_grad(dy, N, cout, nullptr, db, st);
+  return s;
+}
+
+int lpc_t_up_fwd(const float* x, int cin, const uint32_t* par, const uint64_t* ckey, int64_t Nc,
+                 const float* W, const float* b, int cout, float* y, int bf16, uint64_t stream) {
+  if (Nc < 0 || !ok_dims(cin, cout)) return LPC_INVALID_ARG;
+  return gmv(UpFwdItems{par, ckey}, W, 8, cout, cin, 0, b, b ? 2 : 0, x, Nc, y, bf16,
+             reinterpret_cast<cudaStream_t>(stream));
+}
+
+int lpc_t_up_bwd(const float* x, const float* dy, int64_t Np, int cin, const uint32_t* off,
+                 const uint32_t* par, const uint64_t* ckey, int64_t Nc, const float* W, int cout,
+                 float* dx, float* dW, float* db, int bf16, uint64_t stream) {
+  if (Nc < 0 || Np < 0 || !ok_dims(cin, cout)) return LPC_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  int s = LPC_OK;
+  if (dx) s = gmv(ChildItems{off, ckey}, W, 8, cin, cout, 1, nullptr, 0, dy, Np, dx, bf16, st);
+  if (!s) s = outer(UpPairs{par, ckey}, 8, cout, cin, dy, x, Nc, dW, bf16, st);
+  if (!s) s = bias_grad(dy, Nc, cout, ckey, db, st);
+  return s;
+}
+
+int lpc_t_down_fwd(const float* x, int cin, const uint32_t* off, const uint64_t* ckey, int64_t Np,
+                   const float* W, const float* b, int cout, float* y, int bf16,
+                   uint64_t stream) {
+  if (Np < 0 || !ok_dims(cin, cout)) return LPC_INVALID_ARG;
+  return gmv(ChildItems{off, ckey}, W, 8, cout, cin, 0, b, b ? 1 : 0, x, Np, y, bf16,
+             reinterpret_cast<cudaStream_t>(stream));
+}
+
+int lpc_t_down_bwd(const float* x, const float* dy, int64_t Nc, int cin, const uint32_t* par,
+                   const uint64_t* ckey, int64_t Np, const float* W, int cout, float* dx,
+                   float* dW, float* db, int bf16, uint64_t stream) {
+  if (Nc < 0 || Np < 0 || !ok_dims(cin, cout)) return LPC_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  int s = LPC_OK;
+  if (dx) s = gmv(UpFwdItems{par, ckey}, W, 8, cin, cout, 1, nullptr, 0, dy, Nc, dx, bf16, st);
+  if (!s) s = outer(DownPairs{par, ckey}, 8, cout, cin, dy, x, Nc, dW, bf16, st);
+  if (!s) s = bias_grad(dy, Np, cout, nullptr, db, st);
+  return s;
+}
+
+int lpc_t_embed_fwd(const uint8_t* codes, int64_t N, const float* E, int C, float* y,
+                    uint64_t stream) {
+  if (N < 0 || C < 1) return LPC_INVALID_ARG;
+  if (N == 0) return LPC_OK;
+  k_embed_f<<<grid_for(N * C), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(codes, N, E, C,
+                                                                                 y);
+  count_launches(1);
+  return cudaGetLastError() == cudaSuccess ? LPC_OK : LPC_CUDA_ERROR;
+}
+
+int lpc_t_embed_bwd(const uint8_t* codes, int64_t N, const float* dy, int C, float* dE,
+                    uint64_t stream) {
+  if (N < 0 || C < 1) return LPC_INVALID_ARG;
+  if (N == 0) return LPC_OK;
+  k_embed_b<<<grid_for(N * C), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(codes, N, dy,
+                                                                                 C, dE);
+  count_launches(1);
+  return cudaGetLastError() == cudaSuccess ? LPC_OK : LPC_CUDA_ERROR;
+}
+
+int lpc_t_prelu_fwd(const float* x, int64_t N, int C, const float* a, float* y, uint64_t stream) {
+  if (N < 0 || C < 1 || C > 256) return LPC_INVALID_ARG;
+  if (N == 0) return LPC_OK;
+  k_prelu_f<<<grid_for(N * C), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(x, N, C, a, y);
+  count_launches(1);
+  return cudaGetLastError() == cudaSuccess ? LPC_OK : LPC_CUDA_ERROR;
+}
+
+int lpc_t_prelu_bwd(const float* x, const float* dy, int64_t N, int C, const float* a, float* dx,
+                    float* da, uint64_t stream) {
+  if (N < 0 || C < 1 || C > 256 || !da) return LPC_INVALID_ARG;
+  if (N == 0) return LPC_OK;
+  k_prelu_b<<<grid_for(N * C), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(x, dy, N, C, a,
+                                                                                  dx, da);
+  count_launches(1);
+  return cudaGetLastError() == cudaSuccess ? LPC_OK : LPC_CUDA_ERROR;
+}
+
+int lpc_t_fq_fwd(const float* x, int64_t n, float s, int z, float* y, uint8_t* mask,
+                 uint64_t stream) {
+  if (n < 0 || !(s > 0.f) || z < -128 || z > 127) return LPC_INVALID_ARG;
+  if (n == 0) return LPC_OK;
+  k_fq_f<<<grid_for(n), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(x, n, s, z, y, mask);
+  count_launches(1);
+  return cudaGetLastError() == cudaSuccess ? LPC_OK : LPC_CUDA_ERROR;
+}
+
+int lpc_t_fq_bwd(const float* dy, const uint8_t* mask, int64_t n, float* dx, uint64_t stream) {
+  if (n < 0) return LPC_INVALID_ARG;
+  if (n == 0) return LPC_OK;
+  k_fq_b<<<grid_for(n), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(dy, mask, n, dx);
+  count_launches(1);
+  return cudaGetLastError() == cudaSuccess ? LPC_OK : LPC_CUDA_ERROR;
+}
+
+}  // extern "C"

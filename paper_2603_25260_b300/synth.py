@@ -371,3 +371,70 @@ def make_blob(C: int = 32, seed: int = 7) -> bytes:
     """The seeded weight blob (default: C = 32, seed 7)."""
     recs, lut = make_blob_records(C, seed)
     return pack_blob(recs, lut, C)
+
+
+# ----------------------------------------------------------------------------
+# Parameters of the differentiable twin (names, shapes, seeded initial values)
+# ----------------------------------------------------------------------------
+
+def twin_param_shapes(C: int = 32) -> dict:
+    """Parameter names and shapes of the twin (float counterparts of the
+    blob records; PReLU slopes are per output channel)."""
+    s = {}
+
+    def emb(n):
+        s[n] = (256, C)
+
+    def lin(n, S, cin, prelu_=True, per_slice_bias=False):
+        s[n + ".W"] = (S, C, cin) if S > 1 else (C, cin)
+        s[n + ".b"] = (S, C) if per_slice_bias else (C,)
+        if prelu_:
+            s[n + ".a"] = (C,)
+
+    def res(j, cin):
+        lin(f"RA_{j}", 27, cin)
+        lin(f"RB_{j}", 27, C, prelu_=False)
+        s[f"RM_{j}.ma"] = (C,)
+        s[f"RM_{j}.mb"] = (C,)
+        s[f"RM_{j}.a"] = (C,)
+
+    def pred(j):
+        lin(f"P1_{j}", 1, C)
+        s[f"P2_{j}.W"] = (255, C)
+        s[f"P2_{j}.b"] = (255,)
+
+    emb("E_0"); lin("UP_0", 8, C, per_slice_bias=True); pred(0)
+    res(1, C); emb("E_1"); lin("UP_1", 8, 2 * C, per_slice_bias=True); pred(1)
+    for j in range(2, 5):
+        m = j - 1
+        emb(f"G_{j}")
+        for i in range(1, m):
+            lin(f"D_{j}_{i}", 8, C)
+        res(j, 2 * C)
+        for k in range(m):
+            emb(f"E_{j}_{k}")
+            lin(f"UP_{j}_{k}", 8, 2 * C, per_slice_bias=True)
+        pred(j)
+    return s
+
+
+def twin_params(seed: int = 0, C: int = 32) -> dict:
+    """Seeded float parameters (numpy float32) for both implementations."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = {}
+    for name, shape in twin_param_shapes(C).items():
+        if name.endswith(".W"):
+            fan = shape[-1] * (shape[0] if len(shape) == 3 and shape[0] == 27 else 1)
+            if len(shape) == 3 and shape[0] == 8 and name.startswith("D_"):
+                fan = shape[-1] * 3
+            v = rng.normal(0.0, 1.0 / math.sqrt(fan), size=shape)
+        elif name.endswith(".a"):
+            v = rng.uniform(0.05, 0.35, size=shape)
+        elif name.endswith(".ma") or name.endswith(".mb"):
+            v = rng.uniform(0.5, 0.9, size=shape)
+        elif name.endswith(".b"):
+            v = rng.normal(0.0, 0.05, size=shape)
+        else:  # embeddings
+            v = rng.normal(0.0, 0.5, size=shape)
+        out[name] = v.astype(np.float32)
+    return out

@@ -1,0 +1,369 @@
+"""Differentiable (quantisation-aware) twin of the codec's network on B300.
+
+The sparse ops -- 3x3x3 conv, Upsampling + Pruning (densify), stride-2 down
+conv (sparsify), occupancy-code embedding, PReLU and the fake quantiser --
+run forward and backward in the hand-written kernels of ``csrc/train.cu``
+(C ABI in ``include/lpc_train.h``), exposed as ``torch.autograd.Function``s.
+The predictor's two dense linear layers and the cross-entropy are plain
+PyTorch.  The loss is the occupancy cross-entropy in bits (supplement,
+training section) over the five network-coded levels; training follows the
+paper's settings: AdamW, lr 1e-4, weight decay 1e-4, gradient clipping at 1.0.
+
+Index structures (levels, parent rows, child offsets, kernel maps) come from
+the codec's own octree and kernel-map kernels.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import math
+
+import numpy as np
+import torch
+
+from . import lpc
+
+P_, I64, I32 = C.c_void_p, C.c_int64, C.c_int
+_done = False
+
+
+def _lib():
+    global _done
+    L = lpc.lib()
+    if not _done:
+        sig = {
+            "lpc_t_conv_fwd": [P_, I64, I32, P_, P_, P_, I32, P_, I32, C.c_uint64],
+            "lpc_t_conv_bwd": [P_, P_, I64, I32, P_, P_, I32, P_, P_, P_, I32, C.c_uint64],
+            "lpc_t_up_fwd": [P_, I32, P_, P_, I64, P_, P_, I32, P_, I32, C.c_uint64],
+            "lpc_t_up_bwd": [P_, P_, I64, I32, P_, P_, P_, I64, P_, I32, P_, P_, P_, I32,
+                             C.c_uint64],
+            "lpc_t_down_fwd": [P_, I32, P_, P_, I64, P_, P_, I32, P_, I32, C.c_uint64],
+            "lpc_t_down_bwd": [P_, P_, I64, I32, P_, P_, I64, P_, I32, P_, P_, P_, I32,
+                               C.c_uint64],
+            "lpc_t_embed_fwd": [P_, I64, P_, I32, P_, C.c_uint64],
+            "lpc_t_embed_bwd": [P_, I64, P_, I32, P_, C.c_uint64],
+            "lpc_t_prelu_fwd": [P_, I64, I32, P_, P_, C.c_uint64],
+            "lpc_t_prelu_bwd": [P_, P_, I64, I32, P_, P_, P_, C.c_uint64],
+            "lpc_t_fq_fwd": [P_, I64, C.c_float, I32, P_, P_, C.c_uint64],
+            "lpc_t_fq_bwd": [P_, P_, I64, P_, C.c_uint64],
+            "lpc_t_levels": [P_, I64, I32, P_, P_, P_, P_, P_, I64, C.c_uint64],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.restype = I32
+            f.argtypes = args
+        _done = True
+    return L
+
+
+def _p(t):
+    return None if t is None else t.data_ptr()
+
+
+def _st():
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _ck(s, what):
+    if s != 0:
+        raise lpc.LpcError(s, what)
+
+
+# ------------------------------------------------------------- autograd ops --
+
+class ConvFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, x, nbr, W, b, bf16):
+        x, W, b = x.contiguous(), W.contiguous(), b.contiguous()
+        N, cin = x.shape
+        y = torch.empty(N, W.shape[1], device=x.device, dtype=torch.float32)
+        _ck(_lib().lpc_t_conv_fwd(_p(x), N, cin, _p(nbr), _p(W), _p(b), W.shape[1], _p(y),
+                                  bf16, _st()), "conv fwd")
+        ctx.save_for_backward(x, nbr, W)
+        ctx.bf16 = bf16
+        return y
+
+    @staticmethod
+    def backward(ctx, dy):
+        x, nbr, W = ctx.saved_tensors
+        dy = dy.contiguous()
+        N, cin = x.shape
+        dx = torch.empty_like(x) if ctx.needs_input_grad[0] else None
+        dW = torch.zeros_like(W)
+        db = torch.zeros(W.shape[1], device=x.device, dtype=torch.float32)
+        _ck(_lib().lpc_t_conv_bwd(_p(x), _p(dy), N, cin, _p(nbr), _p(W), W.shape[1], _p(dx),
+                                  _p(dW), _p(db), ctx.bf16, _st()), "conv bwd")
+        return dx, None, dW, db, None
+
+
+class UpFn(torch.autograd.Function):
+    """y[r] = W[c_r] x[par r] + b[c_r] over the children r of the next level."""
+
+    @staticmethod
+    def forward(ctx, x, par, ckey, off, W, b, bf16):
+        x, W, b = x.contiguous(), W.contiguous(), b.contiguous()
+        Nc = par.shape[0]
+        y = torch.empty(Nc, W.shape[1], device=x.device, dtype=torch.float32)
+        _ck(_lib().lpc_t_up_fwd(_p(x), x.shape[1], _p(par), _p(ckey), Nc, _p(W), _p(b),
+                                W.shape[1], _p(y), bf16, _st()), "up fwd")
+        ctx.save_for_backward(x, par, ckey, off, W)
+        ctx.bf16 = bf16
+        return y
+
+    @staticmethod
+    def backward(ctx, dy):
+        x, par, ckey, off, W = ctx.saved_tensors
+        dy = dy.contiguous()
+        dx = torch.empty_like(x) if ctx.needs_input_grad[0] else None
+        dW = torch.zeros_like(W)
+        db = torch.zeros(8, W.shape[1], device=x.device, dtype=torch.float32)
+        _ck(_lib().lpc_t_up_bwd(_p(x), _p(dy), x.shape[0], x.shape[1], _p(off), _p(par),
+                                _p(ckey), par.shape[0], _p(W), W.shape[1], _p(dx), _p(dW),
+                                _p(db), ctx.bf16, _st()), "up bwd")
+        return dx, None, None, None, dW, db, None
+
+
+class DownFn(torch.autograd.Function):
+    """y[p] = b + sum over the children r of p of W[c_r] x[r]."""
+
+    @staticmethod
+    def forward(ctx, x, par, ckey, off, W, b, bf16):
+        x, W, b = x.contiguous(), W.contiguous(), b.contiguous()
+        Np = off.shape[0] - 1
+        y = torch.empty(Np, W.shape[1], device=x.device, dtype=torch.float32)
+        _ck(_lib().lpc_t_down_fwd(_p(x), x.shape[1], _p(off), _p(ckey), Np, _p(W), _p(b),
+                                  W.shape[1], _p(y), bf16, _st()), "down fwd")
+        ctx.save_for_backward(x, par, ckey, off, W)
+        ctx.bf16 = bf16
+        return y
+
+    @staticmethod
+    def backward(ctx, dy):
+        x, par, ckey, off, W = ctx.saved_tensors
+        dy = dy.contiguous()
+        dx = torch.empty_like(x) if ctx.needs_input_grad[0] else None
+        dW = torch.zeros_like(W)
+        db = torch.zeros(W.shape[1], device=x.device, dtype=torch.float32)
+        _ck(_lib().lpc_t_down_bwd(_p(x), _p(dy), x.shape[0], x.shape[1], _p(par), _p(ckey),
+                                  off.shape[0] - 1, _p(W), W.shape[1], _p(dx), _p(dW), _p(db),
+                                  ctx.bf16, _st()), "down bwd")
+        return dx, None, None, None, dW, db, None
+
+
+class EmbedFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, codes, E):
+        E = E.contiguous()
+        y = torch.empty(codes.shape[0], E.shape[1], device=E.device, dtype=torch.float32)
+        _ck(_lib().lpc_t_embed_fwd(_p(codes), codes.shape[0], _p(E), E.shape[1], _p(y), _st()),
+            "embed fwd")
+        ctx.save_for_backward(codes)
+        ctx.shape = E.shape
+        return y
+
+    @staticmethod
+    def backward(ctx, dy):
+        (codes,) = ctx.saved_tensors
+        dE = torch.zeros(ctx.shape, device=dy.device, dtype=torch.float32)
+        _ck(_lib().lpc_t_embed_bwd(_p(codes), codes.shape[0], _p(dy.contiguous()), ctx.shape[1],
+                                   _p(dE), _st()), "embed bwd")
+        return None, dE
+
+
+class PReLUFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, x, a):
+        x, a = x.contiguous(), a.contiguous()
+        y = torch.empty_like(x)
+        _ck(_lib().lpc_t_prelu_fwd(_p(x), x.shape[0], x.shape[1], _p(a), _p(y), _st()),
+            "prelu fwd")
+        ctx.save_for_backward(x, a)
+        return y
+
+    @staticmethod
+    def backward(ctx, dy):
+        x, a = ctx.saved_tensors
+        dx = torch.empty_like(x)
+        da = torch.zeros_like(a)
+        _ck(_lib().lpc_t_prelu_bwd(_p(x), _p(dy.contiguous()), x.shape[0], x.shape[1], _p(a),
+                                   _p(dx), _p(da), _st()), "prelu bwd")
+        return dx, da
+
+
+class FakeQuantFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, x, s, z):
+        x = x.contiguous()
+        y = torch.empty_like(x)
+        mask = torch.empty(x.shape, dtype=torch.uint8, device=x.device)
+        _ck(_lib().lpc_t_fq_fwd(_p(x), x.numel(), float(s), int(z), _p(y), _p(mask), _st()),
+            "fq fwd")
+        ctx.save_for_backward(mask)
+        return y
+
+    @staticmethod
+    def backward(ctx, dy):
+        (mask,) = ctx.saved_tensors
+        dx = torch.empty_like(dy)
+        _ck(_lib().lpc_t_fq_bwd(_p(dy.contiguous()), _p(mask), dy.numel(), _p(dx), _st()),
+            "fq bwd")
+        return dx, None, None
+
+
+class RoundBF16(torch.autograd.Function):
+    """bf16 rounding of a float32 operand with an identity gradient."""
+
+    @staticmethod
+    def forward(ctx, x):
+        return x.bfloat16().float()
+
+    @staticmethod
+    def backward(ctx, g):
+        return g
+
+
+def fq_w(w):
+    s = float(w.detach().abs().max().clamp_min(1e-12)) / 127.0
+    return FakeQuantFn.apply(w, s, 0)
+
+
+# ------------------------------------------------------------ structures --
+
+class Frame:
+    """Device index structures of one frame: levels with parent rows, child
+    offsets and child slots, kernel maps at V_b and V_t, codes."""
+
+    def __init__(self, xyz: torch.Tensor, L: int):
+        _lib()
+        self.L, self.b, self.t = L, L - 5, L - 4
+        n = xyz.shape[0]
+        self.n = n
+        cap = max(1, n) * (L + 1)
+        keys = torch.empty(cap, dtype=torch.int64, device="cuda")
+        codes = torch.empty(cap, dtype=torch.uint8, device="cuda")
+        par = torch.empty(cap, dtype=torch.int32, device="cuda")
+        off = torch.empty(cap + L + 1, dtype=torch.int32, device="cuda")
+        counts = np.zeros(L + 1, dtype=np.int64)
+        _ck(_lib().lpc_t_levels(_p(xyz), n, L, _p(keys), _p(codes), _p(par), _p(off),
+                                counts.ctypes.data, cap, _st()), "levels")
+        self.N = counts.tolist()
+        self.keys, self.codes, self.par, self.off, self.Y = {}, {}, {}, {}, {}
+        kp = cp = op = 0
+        for d in range(L + 1):
+            N = self.N[d]
+            self.keys[d] = keys[kp:kp + N]
+            if d > 0:
+                self.par[d] = par[kp:kp + N]
+            kp += N
+            if d < L:
+                self.codes[d] = codes[cp:cp + N]
+                self.off[d] = off[op:op + N + 1]
+                cp += N
+                op += N + 1
+        for d in range(L):
+            self.Y[d] = self.codes[d].long()
+        self.nbr = {d: lpc.kernel_map(self.keys[d], d) for d in (self.b, self.t)}
+
+
+# ------------------------------------------------------------------ model --
+
+ACT_SCALE = 1.0 / 32.0
+
+
+class QATModel(torch.nn.Module):
+    """The float twin of the integer network with optional fake quantisation."""
+
+    def __init__(self, params: dict, qat: bool = False, bf16: bool = False):
+        super().__init__()
+        self.names = sorted(params)
+        self.p = torch.nn.ParameterDict(
+            {k.replace(".", "__"): torch.nn.Parameter(torch.tensor(v, device="cuda"))
+             for k, v in params.items()})
+        self.qat, self.bf16 = qat, int(bf16)
+
+    def P(self, name):
+        return self.p[name.replace(".", "__")]
+
+    def w(self, name):
+        return fq_w(self.P(name)) if self.qat else self.P(name)
+
+    def q(self, x):
+        return FakeQuantFn.apply(x, ACT_SCALE, 0) if self.qat else x
+
+    def linear(self, x, W, b):
+        if self.bf16:  # operands rounded to bf16, products accumulated in fp32
+            x, W = RoundBF16.apply(x), RoundBF16.apply(W)
+        return torch.nn.functional.linear(x, W, b)
+
+    def bits(self, fr: Frame) -> torch.Tensor:
+        b, t, P, q, w, bf = fr.b, fr.t, self.P, self.q, self.w, self.bf16
+
+        def prelu(x, name):
+            return PReLUFn.apply(x, P(name))
+
+        def pred(j, F):
+            h = prelu(self.linear(q(F), w(f"P1_{j}.W"), P(f"P1_{j}.b")), f"P1_{j}.a")
+            return self.linear(q(h), w(f"P2_{j}.W"), P(f"P2_{j}.b"))
+
+        def upl(name, d, x):  # V_{d-1} -> V_d
+            y = UpFn.apply(q(x), fr.par[d], fr.keys[d], fr.off[d - 1], w(name + ".W"),
+                           P(name + ".b"), bf)
+            return prelu(y, name + ".a")
+
+        def conv(x, d, name):
+            return ConvFn.apply(q(x), fr.nbr[d], w(name + ".W"), P(name + ".b"), bf)
+
+        def resblock(j, d, x):
+            y1 = prelu(conv(x, d, f"RA_{j}"), f"RA_{j}.a")
+            y2 = conv(y1, d, f"RB_{j}")
+            return prelu(P(f"RM_{j}.ma") * y1 + P(f"RM_{j}.mb") * y2, f"RM_{j}.a")
+
+        def emb(name, d):
+            return EmbedFn.apply(fr.codes[d], P(name))
+
+        def ce(logits, d):
+            return torch.nn.functional.cross_entropy(logits, fr.Y[d] - 1,
+                                                     reduction="sum") / math.log(2.0)
+
+        Fb = upl("UP_0", b, emb("E_0", b - 1))
+        bits = ce(pred(0, Fb), b)
+        Sb = resblock(1, b, Fb)
+        Ft = upl("UP_1", t, torch.cat([Sb, emb("E_1", b)], 1))
+        bits = bits + ce(pred(1, Ft), t)
+        for j in range(2, 5):
+            m = j - 1
+            d = t + m
+            g = emb(f"G_{j}", d - 1)
+            for i in range(1, m):
+                k = d - 1 - i
+                name = f"D_{j}_{i}"
+                g = DownFn.apply(q(g), fr.par[k + 1], fr.keys[k + 1], fr.off[k], w(name + ".W"),
+                                 P(name + ".b"), bf)
+                g = prelu(g, name + ".a")
+            H = resblock(j, t, torch.cat([Ft, g], 1))
+            for k in range(m):
+                H = upl(f"UP_{j}_{k}", t + k + 1, torch.cat([H, emb(f"E_{j}_{k}", t + k)], 1))
+            bits = bits + ce(pred(j, H), d)
+        return bits
+
+    def grads(self) -> dict:
+        return {k: self.P(k).grad.detach().cpu().double().numpy() for k in self.names}
+
+
+def train_step(model: QATModel, opt, frames: list[Frame]) -> float:
+    """One step on a batch of frames: bits per point of the batch, AdamW,
+    gradient norm clipped at 1.0 (supplement, training settings)."""
+    opt.zero_grad(set_to_none=True)
+    npts = sum(f.n for f in frames)
+    total = 0.0
+    for f in frames:
+        loss = model.bits(f) / npts
+        loss.backward()
+        total += float(loss.detach())
+    torch.nn.utils.clip_grad_norm_(model.parameters(), 1.0)
+    opt.step()
+    return total
+
+
+def make_optimizer(model: QATModel):
+    return torch.optim.AdamW(model.parameters(), lr=1e-4, weight_decay=1e-4)

@@ -12,7 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def _declared():
     names = set()
-    for h in ("lpc.h", "lpc_ops.h"):
+    for h in ("lpc.h", "lpc_ops.h", "lpc_train.h"):
         src = open(os.path.join(ROOT, "include", h)).read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
         for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b([a-z_][a-z0-9_]*)\s*\(",
@@ -27,7 +27,11 @@ def test_headers_declare_the_boundary():
     for want in ("codec_create", "codec_destroy", "codec_last_error", "encode_frame",
                  "decode_frame", "probs_level", "encode_batch", "decode_batch",
                  "lpc_build_levels", "lpc_kernel_map", "lpc_conv333", "lpc_down_s2",
-                 "lpc_up_prune", "lpc_softmax_cdf"):
+                 "lpc_up_prune", "lpc_softmax_cdf", "lpc_kernel_map_noalloc",
+                 "lpc_t_conv_fwd", "lpc_t_conv_bwd", "lpc_t_up_fwd", "lpc_t_up_bwd",
+                 "lpc_t_down_fwd", "lpc_t_down_bwd", "lpc_t_embed_fwd", "lpc_t_embed_bwd",
+                 "lpc_t_prelu_fwd", "lpc_t_prelu_bwd", "lpc_t_fq_fwd", "lpc_t_fq_bwd",
+                 "lpc_t_levels"):
         assert want in names
 
 
