@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="kitti64_L16", choices=sorted(WORKLOADS))
-    ap.add_argument("--chunk", type=int, default=4096)
+    ap.add_argument("--chunk", type=int, default=1024)
     ap.add_argument("--batch-frames", type=int, default=64)
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -124,8 +124,8 @@ def alu_peak_tops(sm_mhz: float) -> float:
 
 KERNEL_SOURCES = {
     "sort": "octree.cu", "levels": "octree.cu", "hash_kmap": "hash.cu", "embed": "layers.cu",
-    "up_prune": "layers.cu", "down_s2": "layers.cu", "conv333": "layers.cu",
-    "predictor_cdf": "layers.cu",
+    "up_prune": "layers.cu", "down_s2": "layers.cu", "conv333": "conv_tc.cu",
+    "predictor_cdf": "layers.cu", "range_coder": "rc_device.cu",
 }
 
 
@@ -258,7 +258,7 @@ def run_ours(args):
     for _ in range(max(args.warmup, 1)):
         nbytes = step()
     # untimed profile pass over every family picks the dominant one
-    codec.profile(0xFF)
+    codec.profile((1 << len(lpc.Codec.FAMILIES)) - 1)
     for _ in range(2):
         step()
     torch.cuda.synchronize()
@@ -321,6 +321,29 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_total = float(t.item())
     e2e_value = world * n * args.steps / (e2e_total / 1e3) / 1e6
+
+    # the same step with the network levels range coded on host threads
+    hcodec = lpc.Codec(blob, spec.L, n, chunk=args.chunk, host_coding=True)
+    for _ in range(2):
+        ln = hcodec.encode_into(x, outbuf)
+        hcodec.decode(outbuf[:ln].tobytes(), out=out_dev)
+    hms = []
+    for _ in range(3):
+        flush.zero_()
+        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        a.record(stream)
+        ln = hcodec.encode_into(x, outbuf)
+        b.record(stream)
+        hcodec.decode(outbuf[:ln].tobytes(), out=out_dev)
+        c.record(stream)
+        torch.cuda.synchronize()
+        hms.append((a.elapsed_time(b), b.elapsed_time(c)))
+    hcodec.close()
+    he = statistics.median(t[0] for t in hms)
+    hd = statistics.median(t[1] for t in hms)
+    host_coding = {"value": round(n / ((he + hd) / 1e3) / 1e6, 4),
+                   "encode_mpts": round(n / (he / 1e3) / 1e6, 4),
+                   "decode_mpts": round(n / (hd / 1e3) / 1e6, 4)}
 
     # batched form: the mixed-size 64-frame batch, whole batch per step
     batched = None
@@ -405,12 +428,15 @@ def run_ours(args):
         "config": {"workload": args.workload, "points": n, "voxels": n_out, "L": spec.L,
                    "C": 32, "chunk": args.chunk, "l2": "flushed between steps (256 MiB write)",
                    "parallelism": f"replicas x{world}"},
+        "step_ms": [round(t, 3) for t in step_ms],
         "encode_mpts": round(n / (statistics.median(enc_ms) / 1e3) / 1e6, 4),
         "decode_mpts": round(n / (statistics.median(dec_ms) / 1e3) / 1e6, 4),
         "bits_per_point": round(8 * nbytes / n, 4),
         "batched": batched,
+        "host_coding": host_coding,
         "train": train,
         "e2e": {"value": round(e2e_value, 4), "unit": "Mpoints/s",
+                "step_ms": [round(t, 3) for t in e2e_ms],
                 "h2d_bytes_per_step": int(frame.nbytes), "d2h_bytes_per_step": int(12 * n_out)},
         "gpu_launches": int(gpu_launches),
         "roofline": roof,

@@ -56,11 +56,14 @@ typedef struct {
   int t_off;          /* threshold offset: t = L - t_off (4), Sec. 3.2 and supplement */
   int64_t max_points; /* largest point count of one frame */
   int max_frames;     /* largest batch for encode_batch / decode_batch (1..64) */
-  int chunk;          /* nodes per entropy-coded substream of a network level (4096) */
+  int chunk;          /* nodes per entropy-coded substream of a network level (1024) */
   int host_threads;   /* host threads for range coding (0 = hardware concurrency) */
   uint64_t cuda_stream; /* cudaStream_t as an integer (0 = legacy default stream) */
   int64_t max_batch_points; /* points of one batch, all frames (0 = max_points * max_frames);
                                sizes the device workspace */
+  int host_coding;    /* 0 (default): the network levels are range coded on the device,
+                         one thread (encode) or warp (decode) per substream; 1: on host
+                         threads from tables copied to the host.  Same bitstream. */
 } lpc_config;
 
 /* Create a codec.  `blob` is the integer weight blob (format in the Python
@@ -131,7 +134,7 @@ int codec_last_stats(codec_t* codec, int64_t* counts, double* gpu_us, double* ho
  * every later launch of the families whose bit is set in `mask` with CUDA
  * events on the codec's stream (0 turns it off).  Families: 0 sort (Morton +
  * radix sort + unique), 1 levels (level build / decoder expansion), 2 hash_kmap,
- * 3 embed, 4 up_prune, 5 down_s2, 6 conv333, 7 predictor_cdf.
+ * 3 embed, 4 up_prune, 5 down_s2, 6 conv333, 7 predictor_cdf, 8 range_coder.
  * codec_profile_read returns, for one family, the summed launch time (ms),
  * the launch count, and the algorithmic bytes and integer ops those launches
  * must touch (counted from level sizes and neighbour pairs, not from the
@@ -144,7 +147,8 @@ const char* codec_profile_name(int family);
 /* Host timeline of the last encode / decode, microseconds (diagnostic):
  * [0] octree ready, [1] launches issued, [2] coding done, [3] encode total;
  * [4] coarse levels decoded, [5] network issue, [6] level decoding,
- * [7] expansion issue (sums over levels), [8] decode total. */
+ * [7] expansion issue (sums over levels), [8] decode total; encode again:
+ * [9] coarse keys on the host, [10] device work done, [11] host coding done. */
 int codec_last_phases(codec_t* codec, double* us, int n);
 
 /* Number of CUDA kernels this library has launched in this process so far

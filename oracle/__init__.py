@@ -267,9 +267,11 @@ def logits_level(blob: bytes, xyz: np.ndarray, L: int, d: int) -> np.ndarray:
     return _level_call(lib().or_logits_level, blob, xyz, L, d, 255, np.int8, "logits_level")
 
 
-def encode(blob: bytes, xyz: np.ndarray, L: int, chunk: int = 4096) -> bytes:
+def encode(blob: bytes, xyz: np.ndarray, L: int, chunk: int = 1024) -> bytes:
     xyz = np.ascontiguousarray(xyz, dtype=np.int32)
-    cap = 64 + xyz.shape[0] * 4 * 4 + 4096
+    # coded bytes: at most 2 per symbol, plus flush bytes and a length varint
+    # per substream (one substream per chunk of every network level)
+    cap = 64 + xyz.shape[0] * 4 * 4 + 4096 + 16 * (5 * (xyz.shape[0] // chunk + 1) + L)
     out = np.zeros(cap, dtype=np.uint8)
     ln = C.c_size_t()
     _check(lib().or_encode(blob, len(blob), _p(xyz), xyz.shape[0], L, chunk, _p(out), cap,

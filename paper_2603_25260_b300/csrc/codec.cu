@@ -128,7 +128,37 @@ Codec::~Codec() {
   for (auto e : pev_) cudaEventDestroy(e);
   if (dmem_) cudaFree(dmem_);
   if (hmem_) cudaFreeHost(hmem_);
+  for (Buf* b : {&d_rcck_, &d_rclen_, &d_rcbuf_})
+    if (b->p) cudaFree(b->p);
+  for (Buf* b : {&h_rcck_, &h_rclen_, &h_rcbuf_})
+    if (b->p) cudaFreeHost(b->p);
   model_free(M_);
+}
+
+void* Codec::dgrow(Buf& b, size_t bytes) {
+  if (bytes <= b.cap) return b.p;
+  cudaStreamSynchronize(st_);
+  if (b.p) cudaFree(b.p);
+  b.cap = std::max<size_t>(bytes + bytes / 4, 4096);
+  if (cudaMalloc(&b.p, b.cap) != cudaSuccess) {
+    cudaGetLastError();
+    b.p = nullptr;
+    b.cap = 0;
+  }
+  return b.p;
+}
+
+void* Codec::hgrow(Buf& b, size_t bytes) {
+  if (bytes <= b.cap) return b.p;
+  cudaStreamSynchronize(st_);
+  if (b.p) cudaFreeHost(b.p);
+  b.cap = std::max<size_t>(bytes + bytes / 4, 4096);
+  if (cudaMallocHost(&b.p, b.cap) != cudaSuccess) {
+    cudaGetLastError();
+    b.p = nullptr;
+    b.cap = 0;
+  }
+  return b.p;
 }
 
 int Codec::cuda_check(const char* what) {
@@ -148,11 +178,13 @@ int Codec::create(const lpc_config& cfg, const void* blob, size_t len) {
   cfg_ = cfg;
   if (cfg.L < 6 || cfg.L > kMaxL || cfg.C != 32 || cfg.b_off != 5 || cfg.t_off != 4 ||
       cfg.max_points < 1 || cfg.max_points > (int64_t)1 << 31 || cfg.max_frames < 1 ||
-      cfg.max_frames > kMaxBatch || cfg.chunk < 1 || cfg.chunk > (1 << 24))
+      cfg.max_frames > kMaxBatch || cfg.chunk < 1 || cfg.chunk > (1 << 24) ||
+      cfg.host_coding < 0 || cfg.host_coding > 1)
     return fail(LPC_INVALID_ARG,
                 "config: need 6 <= L <= 19, C = 32, b_off = 5, t_off = 4, max_points >= 1, "
                 "1 <= max_frames <= 64, chunk >= 1");
   st_ = reinterpret_cast<cudaStream_t>(cfg.cuda_stream);
+  dev_rc_ = cfg.host_coding == 0;
   int s = model_load(blob, len, M_, err);
   if (s) return s;
   F_ = cfg.max_frames;
@@ -336,6 +368,8 @@ int Codec::check_device_error() {
   if (e == 0) return LPC_OK;
   if (e == kErrCoord) return fail(LPC_INVALID_ARG, "coordinate outside [0, 2^L)");
   if (e == kErrHashFull) return fail(LPC_HASH_FULL, "voxel hash probe limit reached");
+  if (e == kErrCapacity) return fail(LPC_CAPACITY, "a level exceeds the codec's capacity");
+  if (e == kErrTimeout) return fail(LPC_TIMEOUT, "a device range decoder gave up on a bounded wait");
   return fail(LPC_CORRUPT_STREAM, "decoded occupancy code is invalid");
 }
 
@@ -637,16 +671,18 @@ int Codec::encode(int nf, const int32_t* const* xyz, const int64_t* n, const int
     for (int j = 0; j < 5; j++) {
       const int h = 5 - j;
       net_level(j, kPredEnc, nullptr, d_enc_ + (size_t)j * P_, nullptr);
-      cudaMemcpyAsync(h_enc_ + (size_t)j * P_, d_enc_ + (size_t)j * P_, 4 * N_[h],
-                      cudaMemcpyDeviceToHost, st_);
-      cudaEventRecord(ev_[1 + j], st_);
+      if (!dev_rc_) {
+        cudaMemcpyAsync(h_enc_ + (size_t)j * P_, d_enc_ + (size_t)j * P_, 4 * N_[h],
+                        cudaMemcpyDeviceToHost, st_);
+        cudaEventRecord(ev_[1 + j], st_);
+      }
     }
-    cudaMemcpyAsync(h_err_, d_err_, 4, cudaMemcpyDeviceToHost, st_);
-    cudaEventRecord(ev_[6], st_);
     if (int s = cuda_check("encode: launch")) return s;
-    // substream layout in the arena: per frame, b coarse slots then chunks
+    // substream layout: per frame, b coarse slots in the host arena, then the
+    // network chunks (host arena, or the device coder's byte buffer)
     tasks_.clear();
-    size_t ao = 0;
+    size_t ao = 0, doff = 0;
+    int64_t nck = 0;
     for (int f = 0; f < nd; f++) {
       Frame& F = fr_[f];
       F.sub_base = tasks_.size();
@@ -658,15 +694,50 @@ int Codec::encode(int nf, const int32_t* const* xyz, const int64_t* n, const int
         const int h = 5 - j;
         for (int64_t s0 = 0; s0 < F.cnt[h]; s0 += cfg_.chunk) {
           const int64_t cnt = std::min<int64_t>(cfg_.chunk, F.cnt[h] - s0);
-          tasks_.push_back(SubTask{f, F.b + j, s0, cnt, ao, 0});
-          ao += coded_bound((size_t)cnt);
+          if (dev_rc_) {
+            tasks_.push_back(SubTask{f, F.b + j, s0, cnt, doff, 0, nck++});
+            doff += coded_bound((size_t)cnt);
+          } else {
+            tasks_.push_back(SubTask{f, F.b + j, s0, cnt, ao, 0});
+            ao += coded_bound((size_t)cnt);
+          }
         }
       }
     }
     if (ao > arena_cap_) return fail(LPC_CAPACITY, "encode: coding arena too small");
+    if (dev_rc_ && nck > 0) {
+      // every network chunk of every frame range coded by one launch
+      RcChunk* hc = static_cast<RcChunk*>(hgrow(h_rcck_, sizeof(RcChunk) * nck));
+      RcChunk* dc = static_cast<RcChunk*>(dgrow(d_rcck_, sizeof(RcChunk) * nck));
+      uint32_t* hl = static_cast<uint32_t*>(hgrow(h_rclen_, 4 * nck));
+      uint32_t* dl = static_cast<uint32_t*>(dgrow(d_rclen_, 4 * nck));
+      uint8_t* dbuf = static_cast<uint8_t*>(dgrow(d_rcbuf_, doff));
+      uint8_t* hbuf = static_cast<uint8_t*>(hgrow(h_rcbuf_, doff));
+      if (!hc || !dc || !hl || !dl || !dbuf || !hbuf)
+        return fail(LPC_CUDA_ERROR, "encode: range coder buffer allocation failed");
+      for (const SubTask& T : tasks_) {
+        if (T.rc < 0) continue;
+        const Frame& F = fr_[T.f];
+        const int j = T.d - F.b;
+        hc[T.rc] = RcChunk{(int64_t)j * P_ + F.off[5 - j] + T.start, T.count, (int64_t)T.arena,
+                           (int64_t)coded_bound((size_t)T.count)};
+      }
+      cudaMemcpyAsync(dc, hc, sizeof(RcChunk) * nck, cudaMemcpyHostToDevice, st_);
+      pbeg(kFamCoder);
+      launch_rc_encode(dc, (int)nck, d_enc_, dbuf, dl, d_err_, st_);
+      // intervals read, bytes written (at most the bound; 1 byte per symbol
+      // is the order of the real output)
+      pend(kFamCoder, 4.0 * (double)(N_[1] + N_[2] + N_[3] + N_[4] + N_[5]) + 32.0 * nck, 0);
+      cudaMemcpyAsync(hl, dl, 4 * nck, cudaMemcpyDeviceToHost, st_);
+      cudaMemcpyAsync(hbuf, dbuf, doff, cudaMemcpyDeviceToHost, st_);
+    }
+    cudaMemcpyAsync(h_err_, d_err_, 4, cudaMemcpyDeviceToHost, st_);
+    cudaEventRecord(ev_[6], st_);
+    if (int s = cuda_check("encode: range coder launch")) return s;
     stats.phase_us[1] = now_us() - t0;
     // coarse levels: one host task per frame, while the device runs the network
     cudaEventSynchronize(ev_[0]);
+    stats.phase_us[9] = now_us() - t0;
     for (int f = 0; f < nd; f++) {
       pool_->submit(0, [this, f] {
         Frame& F = fr_[f];
@@ -696,7 +767,7 @@ int Codec::encode(int nf, const int32_t* const* xyz, const int64_t* n, const int
         }
       });
     }
-    for (int j = 0; j < 5; j++) {
+    for (int j = 0; j < 5 && !dev_rc_; j++) {
       cudaEventSynchronize(ev_[1 + j]);
       const int h = 5 - j;
       for (int f = 0; f < nd; f++) {
@@ -714,7 +785,12 @@ int Codec::encode(int nf, const int32_t* const* xyz, const int64_t* n, const int
       }
     }
     cudaEventSynchronize(ev_[6]);
+    stats.phase_us[10] = now_us() - t0;
     pool_->wait(0);
+    stats.phase_us[11] = now_us() - t0;
+    if (dev_rc_)
+      for (SubTask& T : tasks_)
+        if (T.rc >= 0) T.len = static_cast<const uint32_t*>(h_rclen_.p)[T.rc];
     stats.phase_us[2] = now_us() - t0;
     if (int s = check_device_error()) return s;
     prof_collect();
@@ -752,8 +828,10 @@ int Codec::encode(int nf, const int32_t* const* xyz, const int64_t* n, const int
       memcpy(out[i] + kHdr, table.data(), table.size());
       uint8_t* p = out[i] + kHdr + table.size();
       for (size_t k = b0; k < b1; k++) {
-        memcpy(p, h_arena_ + tasks_[k].arena, tasks_[k].len);
-        p += tasks_[k].len;
+        const SubTask& T = tasks_[k];
+        const uint8_t* src = T.rc >= 0 ? static_cast<const uint8_t*>(h_rcbuf_.p) : h_arena_;
+        memcpy(p, src + T.arena, T.len);
+        p += T.len;
       }
     }
     if (!empty) f++;
@@ -835,6 +913,21 @@ int Codec::decode(int nf, const uint8_t* const* in, const size_t* lens, int32_t*
     h_L_[f] = fr_[f].L;
   }
   cudaMemcpyAsync(d_L_, h_L_, 4 * nd, cudaMemcpyHostToDevice, st_);
+  // device coding: every frame's bytes go to the device while the host
+  // decodes the coarse levels
+  in_base_.assign(nd, 0);
+  if (dev_rc_) {
+    size_t tot = 0;
+    for (int f = 0; f < nd; f++) {
+      in_base_[f] = (int64_t)tot;
+      tot += (fr_[f].len + 15) & ~(size_t)15;
+    }
+    uint8_t* hb = static_cast<uint8_t*>(hgrow(h_rcbuf_, tot));
+    uint8_t* db = static_cast<uint8_t*>(dgrow(d_rcbuf_, tot));
+    if (!hb || !db) return fail(LPC_CUDA_ERROR, "decode: range coder buffer allocation failed");
+    for (int f = 0; f < nd; f++) memcpy(hb + in_base_[f], fr_[f].in, fr_[f].len);
+    cudaMemcpyAsync(db, hb, tot, cudaMemcpyHostToDevice, st_);
+  }
   // coarse levels: decoded and expanded to V_{b-1} on the host, one task per
   // frame (levels are sequential within a frame: N_{d+1} = sum popcount Y_d)
   std::vector<std::vector<uint64_t>> k6(nd);
@@ -894,6 +987,9 @@ int Codec::decode(int nf, const uint8_t* const* in, const size_t* lens, int32_t*
   cudaMemcpyAsync(code_[6], h_codes_ + 6 * P_, n6, cudaMemcpyHostToDevice, st_);
   stats.phase_us[4] = now_us() - t0;
   for (int i = 5; i < 9; i++) stats.phase_us[i] = 0;
+  if (dev_rc_) {
+    if (int s = decode_net_device(nd, n_out, dev, caps)) return s;
+  } else {
   // substream index of (frame, relative level j, chunk 0)
   std::vector<std::vector<size_t>> sidx(nd, std::vector<size_t>(6, 0));
   std::atomic<bool> bad{false};
@@ -916,7 +1012,7 @@ int Codec::decode(int nf, const uint8_t* const* in, const size_t* lens, int32_t*
     if (nh > P_) return fail(LPC_CAPACITY, "decode: batch exceeds the codec's capacity");
     N_[h] = nh;
     pbeg(kFamLevels);
-    launch_expand(key_[h + 1], code_[h + 1], d_N_ + h + 1, P_, key_[h], par_[h], off_[h + 1],
+    launch_expand(key_[h + 1], code_[h + 1], d_N_ + h + 1, P_, key_[h], par_[h], off_[h + 1], P_,
                   d_N_ + h, scan_, d_err_, st_);
     pend(kFamLevels, 13.0 * N_[h + 1] + 12.0 * nh, 0);
     net_level(j, kPredCdf, d_cdf_, nullptr, nullptr);
@@ -1002,14 +1098,15 @@ int Codec::decode(int nf, const uint8_t* const* in, const size_t* lens, int32_t*
   if (n0 > P_) return fail(LPC_CAPACITY, "decode: batch exceeds the codec's capacity");
   N_[0] = n0;
   pbeg(kFamLevels);
-  launch_expand(key_[1], code_[1], d_N_ + 1, P_, key_[0], par_[0], off_[1], d_N_, scan_, d_err_,
-                st_);
+  launch_expand(key_[1], code_[1], d_N_ + 1, P_, key_[0], par_[0], off_[1], P_, d_N_, scan_,
+                d_err_, st_);
   pend(kFamLevels, 13.0 * N_[1] + 12.0 * n0, 0);
   for (int f = 0; f < nd; f++) h_foff_[f] = fr_[f].off[0];
   cudaMemcpyAsync(d_fr_, h_fr_, sizeof(DevFrame) * nd, cudaMemcpyHostToDevice, st_);
   cudaMemcpyAsync(d_foff_, h_foff_, 8 * nd, cudaMemcpyHostToDevice, st_);
   launch_keys_to_xyz_batch(key_[0], d_N_, n0, d_fr_, d_foff_, st_);
   if (int s = sync_and_check("decode")) return s;
+  }
   stats.L = fr_[0].L;
   for (int d = 0; d < fr_[0].b; d++) stats.N[d] = (int64_t)fr_[0].coarse[d].size();
   for (int h = 0; h < kHeights; h++) stats.N[fr_[0].L - h] = fr_[0].cnt[h];
@@ -1017,6 +1114,83 @@ int Codec::decode(int nf, const uint8_t* const* in, const size_t* lens, int32_t*
   stats.phase_us[8] = stats.host_us;
   prof_collect();
   return LPC_OK;
+}
+
+// Network levels decoded on the device: per relative level, expand the
+// codes of the level above, read the new level's frame offsets back (the
+// host sizes the launches and the substream table from them), run the
+// network to the cumulative tables, and range-decode every chunk of every
+// frame in one launch straight into the level's code array.  Ends with the
+// leaves written to the callers' buffers.
+int Codec::decode_net_device(int nd, int64_t* n_out, const std::vector<int>& dev,
+                             const int64_t* caps) {
+  const int64_t maxp = cfg_.max_points;
+  std::vector<size_t> sidx(nd);
+  for (int f = 0; f < nd; f++) sidx[f] = (size_t)fr_[f].b;
+  const uint8_t* d_in = static_cast<const uint8_t*>(d_rcbuf_.p);
+  for (int j = 0; j <= 5; j++) {  // j = 5: the leaves
+    const int h = 5 - j;
+    double tl = now_us();
+    pbeg(kFamLevels);
+    launch_expand(key_[h + 1], code_[h + 1], d_N_ + h + 1, P_, key_[h], par_[h], off_[h + 1], P_,
+                  d_N_ + h, scan_, d_err_, st_);
+    pend(kFamLevels, 13.0 * N_[h + 1] + 12.0 * 2.0 * N_[h + 1], 0);
+    LevelPtrs lp{};
+    lp.key[0] = key_[h];
+    lp.n[0] = d_N_ + h;
+    int64_t* dfo = d_foff_ + (size_t)h * (nd + 1);
+    int64_t* hfo = h_foff_ + (size_t)h * (nd + 1);
+    launch_frame_offsets(lp, 1, nd, dfo, st_);
+    cudaMemcpyAsync(hfo, dfo, 8 * (nd + 1), cudaMemcpyDeviceToHost, st_);
+    cudaMemcpyAsync(h_err_, d_err_, 4, cudaMemcpyDeviceToHost, st_);
+    stats.phase_us[7] += now_us() - tl;
+    tl = now_us();
+    if (cudaStreamSynchronize(st_) != cudaSuccess) return cuda_check("decode: level");
+    if (int s = check_device_error()) return s;
+    stats.phase_us[6] += now_us() - tl;
+    tl = now_us();
+    int64_t nck = 0;
+    for (int f = 0; f < nd; f++) {
+      Frame& F = fr_[f];
+      F.off[h] = hfo[f];
+      F.cnt[h] = hfo[f + 1] - hfo[f];
+      if (F.cnt[h] > maxp) return fail(LPC_CAPACITY, "decode: frame exceeds max_points");
+      nck += (F.cnt[h] + F.chunk - 1) / F.chunk;
+    }
+    N_[h] = hfo[nd];
+    if (h == 0) break;
+    RcChunk* hc = static_cast<RcChunk*>(hgrow(h_rcck_, sizeof(RcChunk) * (size_t)nck));
+    RcChunk* dc = static_cast<RcChunk*>(dgrow(d_rcck_, sizeof(RcChunk) * (size_t)nck));
+    if (!hc || !dc) return fail(LPC_CUDA_ERROR, "decode: range coder buffer allocation failed");
+    int64_t k = 0;
+    for (int f = 0; f < nd; f++) {
+      const Frame& F = fr_[f];
+      for (int64_t c0 = 0; c0 < F.cnt[h]; c0 += F.chunk, k++) {
+        const size_t s = sidx[f]++;
+        if (s >= F.slen.size()) return fail(LPC_CORRUPT_STREAM, "decode: missing substream");
+        hc[k] = RcChunk{F.off[h] + c0, std::min<int64_t>(F.chunk, F.cnt[h] - c0),
+                        in_base_[f] + (int64_t)F.soff[s], (int64_t)F.slen[s]};
+      }
+    }
+    cudaMemcpyAsync(dc, hc, sizeof(RcChunk) * (size_t)nck, cudaMemcpyHostToDevice, st_);
+    net_level(j, kPredCdf, d_cdf_, nullptr, nullptr);
+    pbeg(kFamCoder);
+    launch_rc_decode(dc, (int)nck, d_cdf_, d_in, code_[h], d_err_, st_);
+    // table rows read, codes written
+    pend(kFamCoder, 513.0 * N_[h] + 32.0 * nck, 0);
+    if (int s = cuda_check("decode: launch")) return s;
+    stats.phase_us[5] += now_us() - tl;
+  }
+  for (int f = 0; f < nd; f++)
+    if (sidx[f] != fr_[f].slen.size()) return fail(LPC_CORRUPT_STREAM, "decode: extra substreams");
+  for (int f = 0; f < nd; f++) {
+    const int64_t c = fr_[f].cnt[0];
+    n_out[dev[f]] = c;
+    if (c > caps[dev[f]]) return fail(LPC_CAPACITY, "decode: output capacity too small");
+  }
+  cudaMemcpyAsync(d_fr_, h_fr_, sizeof(DevFrame) * nd, cudaMemcpyHostToDevice, st_);
+  launch_keys_to_xyz_batch(key_[0], d_N_, N_[0], d_fr_, d_foff_, st_);
+  return sync_and_check("decode");
 }
 
 // ---------------------------------------------------------------- probs --
@@ -1126,7 +1300,8 @@ int codec_profile_read(codec_t* codec, int family, double* ms, int64_t* launches
 
 const char* codec_profile_name(int family) {
   static const char* names[lpc::kFamCount] = {"sort", "levels", "hash_kmap", "embed",
-                                              "up_prune", "down_s2", "conv333", "predictor_cdf"};
+                                              "up_prune", "down_s2", "conv333", "predictor_cdf",
+                                              "range_coder"};
   return family >= 0 && family < lpc::kFamCount ? names[family] : "";
 }
 

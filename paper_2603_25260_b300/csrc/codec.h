@@ -55,6 +55,7 @@ enum Family {
   kFamDown,      // stride-2 down conv
   kFamConv,      // 3x3x3 sparse conv on the tensor cores (+ fused residual merge)
   kFamPred,      // predictor + integer softmax + cumulative table
+  kFamCoder,     // device range coding of the network levels
   kFamCount
 };
 
@@ -204,8 +205,21 @@ class Codec {
   struct SubTask {
     int f, d;  // frame, depth
     int64_t start, count;
-    size_t arena, len;
+    size_t arena, len;  // offset in the host arena, or in the device-coded bytes if rc >= 0
+    int64_t rc = -1;    // index of the device-coded chunk
   };
+  // growable buffers for the device range coder (replaced only when a call
+  // needs more; the stream is synchronised first)
+  struct Buf {
+    void* p = nullptr;
+    size_t cap = 0;
+  };
+  void* dgrow(Buf& b, size_t bytes);
+  void* hgrow(Buf& b, size_t bytes);
+  Buf d_rcck_, d_rclen_, d_rcbuf_, h_rcck_, h_rclen_, h_rcbuf_;
+  bool dev_rc_ = true;
+  std::vector<int64_t> in_base_;  // each decoded frame's first byte in d_rcbuf_
+  int decode_net_device(int nd, int64_t* n_out, const std::vector<int>& dev, const int64_t* caps);
   std::vector<SubTask> tasks_;
   std::vector<cudaEvent_t> ev_;
 };

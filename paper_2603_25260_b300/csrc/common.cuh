@@ -32,6 +32,9 @@ __host__ __device__ __forceinline__ uint64_t child_key(uint64_t k, uint32_t c) {
 constexpr int kErrCoord = 1;    // coordinate outside [0, 2^L)
 constexpr int kErrHashFull = 2; // hash probe limit reached
 constexpr int kErrExpand = 3;   // decoded level is not strictly Morton-ordered
+constexpr int kErrCapacity = 4; // decoded level exceeds the level arrays
+constexpr int kErrStream = 5;   // range-coded substream is corrupt
+constexpr int kErrTimeout = 6;  // a bounded wait on the device gave up
 
 __device__ __forceinline__ void set_error(int* err, int code) { atomicCAS(err, 0, code); }
 

@@ -73,10 +73,32 @@ void launch_level_up(const uint64_t* ckeys, const int64_t* d_nc, int64_t cap_c, 
                      uint8_t* pcodes, uint32_t* poff, uint32_t* cpar, int64_t* d_np,
                      const ScanScratch& s, cudaStream_t st);
 // Decoder expansion: parents + codes -> children keys (Morton order), parent
-// index of every child, child offsets of every parent.
+// index of every child, child offsets of every parent.  At most cap_c
+// children are written (kErrCapacity beyond).
 void launch_expand(const uint64_t* pkeys, const uint8_t* pcodes, const int64_t* d_np,
-                   int64_t cap_p, uint64_t* ckeys, uint32_t* cpar, uint32_t* poff,
+                   int64_t cap_p, uint64_t* ckeys, uint32_t* cpar, uint32_t* poff, int64_t cap_c,
                    int64_t* d_nc, const ScanScratch& s, int* err, cudaStream_t st);
+
+// ------------------------------------------------------ device range coding --
+// One substream: `rows` symbols starting at table / interval row `row`, its
+// bytes at `byte_off` of the byte buffer (`byte_len` = stream length when
+// decoding, capacity when encoding).
+struct RcChunk {
+  int64_t row;
+  int64_t rows;
+  int64_t byte_off;
+  int64_t byte_len;
+};
+// Range-encode every chunk (one thread each) from packed intervals
+// lo | f << 16 of a total 2^16; lens[k] = bytes written (kErrCapacity past
+// the capacity).  Same bytes as the host encoder.
+void launch_rc_encode(const RcChunk* ck, int n, const uint32_t* lofreq, uint8_t* out,
+                      uint32_t* lens, int* err, cudaStream_t st);
+// Range-decode every chunk (one warp each) against the cumulative tables
+// (u16[256] rows, entry s = C_{s+1}); codes[row + i] = symbol + 1.  A corrupt
+// substream sets kErrStream.  Same symbols as the host decoder.
+void launch_rc_decode(const RcChunk* ck, int n, const uint16_t* cdf, const uint8_t* in,
+                      uint8_t* codes, int* err, cudaStream_t st);
 
 // ------------------------------------------------------------------ hash --
 struct HashTable {

@@ -410,6 +410,8 @@ void launch_level_up(const uint64_t* ckeys, const int64_t* d_nc, int64_t cap_c, 
 
 // Children (parent << 3 | c) for every set bit c in ascending order: parents
 // are Morton-sorted, so the children are too (no reordering).
+// Codes decoded on the device may be corrupt: children past the capacity of
+// the child arrays are not written, the count is clamped and err is set.
 struct ExpandOp {
   const uint64_t* pk;
   const uint8_t* pc;
@@ -418,29 +420,35 @@ struct ExpandOp {
   uint32_t* poff;
   int64_t* nc;
   int* err;
+  int64_t cap_c;
   __device__ uint32_t value(int64_t p) const { return __popc((uint32_t)pc[p]); }
   __device__ void emit(int64_t p, uint32_t ex, int64_t) const {
-    poff[p] = ex;
     const uint32_t code = pc[p];
     if (code == 0) set_error(err, kErrExpand);
-    uint32_t r = ex;
+    int64_t r = ex;
+    poff[p] = (uint32_t)(r < cap_c ? r : cap_c);
     for (int c = 0; c < 8; c++)
       if (code >> c & 1) {
+        if (r >= cap_c) {
+          set_error(err, kErrCapacity);
+          break;
+        }
         ck[r] = child_key(pk[p], (uint32_t)c);
         cpar[r] = (uint32_t)p;
         r++;
       }
   }
   __device__ void finish(uint32_t total, int64_t n) const {
-    *nc = total;
-    poff[n] = total;
+    const int64_t t = (int64_t)total < cap_c ? (int64_t)total : cap_c;
+    *nc = t;
+    poff[n] = (uint32_t)t;
   }
 };
 
 void launch_expand(const uint64_t* pkeys, const uint8_t* pcodes, const int64_t* d_np,
-                   int64_t cap_p, uint64_t* ckeys, uint32_t* cpar, uint32_t* poff,
+                   int64_t cap_p, uint64_t* ckeys, uint32_t* cpar, uint32_t* poff, int64_t cap_c,
                    int64_t* d_nc, const ScanScratch& s, int* err, cudaStream_t st) {
-  run_scan(ExpandOp{pkeys, pcodes, ckeys, cpar, poff, d_nc, err}, d_np, cap_p, s, st);
+  run_scan(ExpandOp{pkeys, pcodes, ckeys, cpar, poff, d_nc, err, cap_c}, d_np, cap_p, s, st);
 }
 
 }  // namespace lpc

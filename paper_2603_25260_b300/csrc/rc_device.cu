@@ -1,0 +1,232 @@
+// Range coding of the network levels on the device, byte-identical to the
+// host coder (coder.h): 32-bit range, low kept to 33 bits, a settled byte
+// held back with a count of pending 0xFF bytes until the carry is known,
+// 5 flush bytes; intervals of a total 2^16 from the integer softmax tables.
+//
+// Substreams are independent, so every chunk is coded in parallel:
+//  - encode: one warp per chunk (its lane 0) walks the packed (lo, f)
+//    intervals;
+//  - decode: one warp per chunk.  Table rows are staged in shared memory by
+//    bulk copies well ahead of use; the 256 entries of a row are spread over
+//    the warp, 8 a lane.  The target floor(code / r) is never formed:
+//    C <= floor(code / r) holds exactly when r C <= code (r C < 2^32), and
+//    the clamp of the target to 2^16 - 1 changes nothing since every C is
+//    below 2^16.  The symbol s is the count of entries with r C <= code, the
+//    interval [C_s, C_{s+1}) the largest such entry and the smallest other
+//    one: three independent warp reductions.  The two stream bytes a
+//    renormalisation can take (range >= 2^8 after every update) are loaded
+//    before they are needed.  Every lane keeps the same copy of the decoder
+//    state, so no broadcasts are needed.  The symbol loop is a serial chain
+//    of dependent instructions in one warp (about 170 ns a symbol on a B300),
+//    so a level takes chunk x that: the chunk length sets the latency.
+#include "common.cuh"
+#include "kernels.h"
+#include "tc_util.cuh"
+
+namespace lpc {
+namespace {
+
+using tc::fence_async_smem;
+using tc::fence_mbar_init;
+using tc::mbar_init;
+using tc::mbar_wait;
+using tc::smem_u32;
+
+constexpr int kEncWarps = 4;
+constexpr int kEncAhead = 4;
+
+// One chunk per warp, coded by its lane 0: chunks are few and each is a
+// serial chain, so lanes of other chunks in the same warp would only add
+// divergence.
+__global__ void __launch_bounds__(kEncWarps * 32)
+k_rc_encode(const RcChunk* __restrict__ ck, int n, const uint32_t* __restrict__ lofreq,
+            uint8_t* __restrict__ out, uint32_t* __restrict__ lens, int* err) {
+  if ((threadIdx.x & 31) != 0) return;
+  const int t = blockIdx.x * kEncWarps + (threadIdx.x >> 5);
+  if (t >= n) return;
+  const RcChunk c = ck[t];
+  uint8_t* o = out + c.byte_off;
+  const int64_t cap = c.byte_len;
+  int64_t len = 0;
+  uint64_t low = 0;
+  uint32_t range = 0xFFFFFFFFu;
+  uint32_t cache = 0;
+  int64_t pending = 1;
+  auto shift_low = [&]() {
+    if ((uint32_t)low < 0xFF000000u || (low >> 32) != 0) {
+      const uint32_t carry = (uint32_t)(low >> 32);
+      uint32_t b = cache;
+      for (; pending > 0; pending--) {
+        if (len < cap) o[len] = (uint8_t)(b + carry);
+        len++;
+        b = 0xFF;
+      }
+      cache = (uint32_t)(low >> 24) & 0xFF;
+    }
+    pending++;
+    low = (low & 0x00FFFFFFull) << 8;
+  };
+  const uint32_t* src = lofreq + c.row;
+  uint32_t nx[kEncAhead];  // intervals loaded ahead of use
+#pragma unroll
+  for (int k = 0; k < kEncAhead; k++) nx[k] = k < c.rows ? __ldg(src + k) : 0u;
+  for (int64_t i0 = 0; i0 < c.rows; i0 += kEncAhead) {
+#pragma unroll
+    for (int k = 0; k < kEncAhead; k++) {
+      if (i0 + k < c.rows) {
+        const uint32_t x = nx[k];
+        if (i0 + k + kEncAhead < c.rows) nx[k] = __ldg(src + i0 + k + kEncAhead);
+        const uint32_t r = range >> 16;
+        low += (uint64_t)r * (x & 0xFFFFu);
+        range = r * (x >> 16);
+        while (range < (1u << 24)) {
+          range <<= 8;
+          shift_low();
+        }
+      }
+    }
+  }
+  for (int i = 0; i < 5; i++) shift_low();
+  lens[t] = (uint32_t)len;
+  if (len > cap) set_error(err, kErrCapacity);
+}
+
+// Table rows reach shared memory by bulk copies (TMA, one per stage of
+// kStageRows rows, completion counted on the stage's mbarrier) kStages stages
+// ahead of use: rows do not depend on earlier symbols.
+constexpr int kStageRows = 8;
+constexpr int kStages = 8;
+constexpr int kRowBytes = 512;
+constexpr size_t kDecSmem = (size_t)kStages * kStageRows * kRowBytes + 8 * kStages;
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n"
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%2], [%3], %1, [%0];"
+      ::"r"(smem_u32(bar)), "r"(bytes), "r"(dst), "l"(src)
+      : "memory");
+}
+
+__global__ void __launch_bounds__(32)
+k_rc_decode(const RcChunk* __restrict__ ck, int n, const uint16_t* __restrict__ cdf,
+            const uint8_t* __restrict__ in, uint8_t* __restrict__ codes, int* err) {
+  extern __shared__ __align__(128) uint8_t sm[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + (size_t)kStages * kStageRows * kRowBytes);
+  const int lane = threadIdx.x;
+  const int w = blockIdx.x;
+  if (w >= n) return;
+  const RcChunk c = ck[w];
+  const int64_t nst = (c.rows + kStageRows - 1) / kStageRows;
+  const uint8_t* src = reinterpret_cast<const uint8_t*>(cdf + c.row * 256);
+  auto issue = [&](int64_t st) {  // lane 0: rows of stage st into its slot
+    const int slot = (int)(st % kStages);
+    const int64_t r0 = st * kStageRows;
+    const int64_t nr = c.rows - r0 < kStageRows ? c.rows - r0 : kStageRows;
+    const uint32_t bytes = (uint32_t)(nr * kRowBytes);
+    bulk_g2s(smem_u32(sm + (size_t)slot * kStageRows * kRowBytes), src + r0 * kRowBytes, bytes,
+             bar + slot);
+  };
+  if (lane == 0) {
+    for (int s = 0; s < kStages; s++) mbar_init(bar + s, 1);
+    fence_mbar_init();
+    for (int64_t st = 0; st < kStages && st < nst; st++) issue(st);
+  }
+  __syncwarp();
+  const uint8_t* p = in + c.byte_off;
+  const uint8_t* const end = p + c.byte_len;
+  bool bad = false, lost = false;
+  uint32_t range = 0xFFFFFFFFu, code = 0;
+  for (int i = 0; i < 5; i++) {
+    code = (code << 8) | (p < end ? __ldg(p) : 0u);
+    if (p >= end) bad = true;
+    p++;
+  }
+  // lane l holds entries 8l .. 8l+7 of a row; only entries 0..253 are
+  // cumulative values (254, 255 are padding, in lane 31)
+  const bool pad = lane == 31;
+  uint8_t* dst = codes + c.row;
+  int64_t st = 0;
+  for (; st < nst; st++) {
+    const int slot = (int)(st % kStages);
+    const bool ok = mbar_wait(bar + slot, (uint32_t)((st / kStages) & 1));
+    if (!__all_sync(0xFFFFFFFFu, ok)) {  // leave together
+      lost = true;
+      break;
+    }
+    const uint8_t* stage = sm + (size_t)slot * kStageRows * kRowBytes;
+    const int64_t r0 = st * kStageRows;
+    const int nr = (int)(c.rows - r0 < kStageRows ? c.rows - r0 : kStageRows);
+#pragma unroll
+    for (int k = 0; k < kStageRows; k++) {
+      if (k < nr) {
+        const uint4 q = *reinterpret_cast<const uint4*>(stage + k * kRowBytes + 16 * lane);
+        const uint32_t b0 = p < end ? __ldg(p) : 0u;
+        const uint32_t b1 = p + 1 < end ? __ldg(p + 1) : 0u;
+        const uint32_t r = range >> 16;
+        const uint32_t e[8] = {q.x & 0xFFFFu, q.x >> 16, q.y & 0xFFFFu, q.y >> 16,
+                               q.z & 0xFFFFu, q.z >> 16, q.w & 0xFFFFu, q.w >> 16};
+        uint32_t cnt = 0, lo = 0, hi = 65536u;
+#pragma unroll
+        for (int m = 0; m < 8; m++) {
+          const bool real = m < 6 || !pad;
+          const bool le = real && r * e[m] <= code;
+          cnt += le;
+          lo = le ? e[m] : lo;  // entries ascend: the last qualifying one is the largest
+          hi = real && !le ? min(hi, e[m]) : hi;
+        }
+        // the three reductions are independent and overlap
+        const uint32_t s = __reduce_add_sync(0xFFFFFFFFu, cnt);
+        lo = __reduce_max_sync(0xFFFFFFFFu, lo);
+        hi = __reduce_min_sync(0xFFFFFFFFu, hi);
+        code -= r * lo;
+        range = r * (hi - lo);
+        if (code >= range) bad = true;
+        // renormalise: range >= 2^8 here, so at most two bytes
+        const int nb = (range < (1u << 24)) + (range < (1u << 16));
+        if (nb == 1) {
+          code = (code << 8) | b0;
+        } else if (nb == 2) {
+          code = (code << 16) | (b0 << 8) | b1;
+        }
+        range <<= 8 * nb;
+        if (p + nb > end) bad = true;
+        p += nb;
+        if (lane == 0) dst[r0 + k] = (uint8_t)(s + 1);
+      }
+    }
+    __syncwarp();
+    if (lane == 0 && st + kStages < nst) {
+      fence_async_smem();  // this stage's reads come before the copy that reuses it
+      issue(st + kStages);
+    }
+  }
+  if (lost) {
+    // a copy never completed: report it and give the copies still counted
+    // on the other stages a bounded chance to land before the block exits
+    if (lane == 0) set_error(err, kErrTimeout);
+    for (int64_t q = st + 1; q < nst && q < st + kStages; q++)
+      mbar_wait(bar + (int)(q % kStages), (uint32_t)((q / kStages) & 1));
+    return;
+  }
+  if (bad && lane == 0) set_error(err, kErrStream);
+}
+
+}  // namespace
+
+void launch_rc_encode(const RcChunk* ck, int n, const uint32_t* lofreq, uint8_t* out,
+                      uint32_t* lens, int* err, cudaStream_t st) {
+  if (n <= 0) return;
+  k_rc_encode<<<(n + kEncWarps - 1) / kEncWarps, kEncWarps * 32, 0, st>>>(ck, n, lofreq, out,
+                                                                          lens, err);
+  count_launches(1);
+}
+
+void launch_rc_decode(const RcChunk* ck, int n, const uint16_t* cdf, const uint8_t* in,
+                      uint8_t* codes, int* err, cudaStream_t st) {
+  if (n <= 0) return;
+  k_rc_decode<<<n, 32, kDecSmem, st>>>(ck, n, cdf, in, codes, err);
+  count_launches(1);
+}
+
+}  // namespace lpc

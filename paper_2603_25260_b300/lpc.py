@@ -32,7 +32,7 @@ class Config(C.Structure):
     _fields_ = [("L", C.c_int), ("C", C.c_int), ("b_off", C.c_int), ("t_off", C.c_int),
                 ("max_points", C.c_int64), ("max_frames", C.c_int), ("chunk", C.c_int),
                 ("host_threads", C.c_int), ("cuda_stream", C.c_uint64),
-                ("max_batch_points", C.c_int64)]
+                ("max_batch_points", C.c_int64), ("host_coding", C.c_int)]
 
 
 _lib = None
@@ -101,14 +101,17 @@ class Codec:
     """One codec instance on the current CUDA device and stream."""
 
     def __init__(self, blob: bytes, L: int, max_points: int, max_frames: int = 1,
-                 chunk: int = 4096, host_threads: int = 0, stream: int | None = None,
-                 max_batch_points: int = 0):
+                 chunk: int = 1024, host_threads: int = 0, stream: int | None = None,
+                 max_batch_points: int = 0, host_coding: bool = False):
+        """host_coding: range-code the network levels on host threads (tables
+        copied to the host) instead of on the device; same bitstream."""
         self._lib = lib()
         self.blob = bytes(blob)
         self.L = L
         self.max_points = max_points
         cfg = Config(L, 32, 5, 4, max_points, max_frames, chunk, host_threads,
-                     _stream() if stream is None else stream, max_batch_points)
+                     _stream() if stream is None else stream, max_batch_points,
+                     int(bool(host_coding)))
         h = P()
         st = self._lib.codec_create(C.byref(cfg), self.blob, len(self.blob), C.byref(h))
         if st != OK:
@@ -195,7 +198,7 @@ class Codec:
         return [outs_t[i][:nout[i]] for i in range(nf)]
 
     FAMILIES = ("sort", "levels", "hash_kmap", "embed", "up_prune", "down_s2", "conv333",
-                "predictor_cdf")
+                "predictor_cdf", "range_coder")
 
     def profile(self, mask: int):
         """Time every launch of the kernel families in `mask` (bit i = FAMILIES[i])

@@ -215,12 +215,14 @@ def test_encode_byte_identical_config1(lpc, blob, c1):
     assert cod.encode(_cuda(c1)) == O.encode(blob, c1, L)
 
 
+@pytest.mark.parametrize("host_coding", [False, True], ids=["device_rc", "host_rc"])
 @pytest.mark.parametrize("n,L,seed,chunk", [(1, 6, 1, 16384), (2, 7, 2, 16384),
                                             (3000, 10, 3, 100), (20000, 14, 4, 4096),
-                                            (5000, 19, 5, 16384), (12000, 12, 6, 999)])
-def test_encode_decode_random(lpc, blob, n, L, seed, chunk):
+                                            (5000, 19, 5, 16384), (12000, 12, 6, 999),
+                                            (7000, 11, 7, 1)])
+def test_encode_decode_random(lpc, blob, n, L, seed, chunk, host_coding):
     xyz = synth.random_cloud(n, L, seed)
-    cod = _codec(lpc, blob, L, n, chunk=chunk)
+    cod = _codec(lpc, blob, L, n, chunk=chunk, host_coding=host_coding)
     data = cod.encode(_cuda(xyz))
     assert data == O.encode(blob, xyz, L, chunk)
     dec = cod.decode(data).cpu().numpy()
@@ -268,10 +270,11 @@ def test_empty_and_failures(lpc, blob):
     assert cod.encode(_cuda(xyz)) == data
 
 
+@pytest.mark.parametrize("host_coding", [False, True], ids=["device_rc", "host_rc"])
 @pytest.mark.parametrize("spec", [synth.C2, synth.C3], ids=["kitti64_L16", "dense128_L18"])
-def test_full_size_frames_byte_identical(lpc, blob, spec):
+def test_full_size_frames_byte_identical(lpc, blob, spec, host_coding):
     xyz = synth.make_frame(spec)
-    cod = _codec(lpc, blob, spec.L, xyz.shape[0])
+    cod = _codec(lpc, blob, spec.L, xyz.shape[0], host_coding=host_coding)
     data = cod.encode(_cuda(xyz))
     assert data == O.encode(blob, xyz, spec.L)
     dec = cod.decode(data).cpu().numpy()
@@ -291,7 +294,8 @@ def test_batch_matches_per_frame_oracle(lpc, blob):
         assert np.array_equal(O.leaf_keys(dcd.cpu().numpy(), L), O.leaf_keys(f, L))
 
 
-def test_batch_mixed_with_empty_frames(lpc, blob):
+@pytest.mark.parametrize("host_coding", [False, True], ids=["device_rc", "host_rc"])
+def test_batch_mixed_with_empty_frames(lpc, blob, host_coding):
     """A batch mixing depths 6..19, tiny and empty frames: every stream equals
     the oracle's stream of that frame alone, and the batch decodes exactly
     (also the oracle's streams, decoded as one batch)."""
@@ -299,7 +303,7 @@ def test_batch_mixed_with_empty_frames(lpc, blob):
              (9000, 13, 7)]
     frames = [synth.random_cloud(n, L, s) for n, L, s in specs]
     Ls = [L for _, L, _ in specs]
-    cod = lpc.Codec(blob, 19, 25000, max_frames=len(frames), chunk=1000)
+    cod = lpc.Codec(blob, 19, 25000, max_frames=len(frames), chunk=1000, host_coding=host_coding)
     outs = cod.encode_batch([_cuda(f) for f in frames], Ls)
     want = [O.encode(blob, f, L, 1000) for f, L in zip(frames, Ls)]
     assert outs == want
@@ -307,3 +311,31 @@ def test_batch_mixed_with_empty_frames(lpc, blob):
     for f, L, dcd in zip(frames, Ls, decs):
         assert np.array_equal(dcd.cpu().numpy(), O.decode(blob, O.encode(blob, f, L, 1000),
                                                           max(f.shape[0], 1)))
+
+
+@pytest.mark.parametrize("host_coding", [False, True], ids=["device_rc", "host_rc"])
+def test_corrupt_payload(lpc, blob, host_coding):
+    """Flipped payload bytes: decoding either reports the stream as corrupt
+    (or its levels as too large) or returns some other point set, never
+    anything else, and the codec stays usable."""
+    L = 10
+    xyz = synth.random_cloud(3000, L, 9)
+    cod = _codec(lpc, blob, L, 3000, chunk=256, host_coding=host_coding)
+    data = cod.encode(_cuda(xyz))
+    want = O.decode(blob, data, 3000)
+    rng = np.random.Generator(np.random.PCG64(5))
+    outcomes = set()
+    for trial in range(12):
+        bad = bytearray(data)
+        lo = len(data) // 3 if trial % 2 else 40
+        for pos in rng.integers(lo, len(data), size=3):
+            bad[pos] ^= int(rng.integers(1, 256))
+        try:
+            dec = cod.decode(bytes(bad), cap=3000)
+            outcomes.add("decoded")
+            assert dec.shape[1] == 3
+        except lpc.LpcError as e:
+            assert e.status in (lpc.CORRUPT_STREAM, lpc.CAPACITY), e
+            outcomes.add(e.status)
+    assert outcomes
+    assert np.array_equal(cod.decode(data).cpu().numpy(), want)
