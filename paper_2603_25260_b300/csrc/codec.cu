@@ -130,7 +130,7 @@ Codec::~Codec() {
   if (hmem_) cudaFreeHost(hmem_);
   for (Buf* b : {&d_rcck_, &d_rclen_, &d_rcbuf_})
     if (b->p) cudaFree(b->p);
-  for (Buf* b : {&h_rcck_, &h_rclen_, &h_rcbuf_})
+  for (Buf* b : {&h_rcck_, &h_rclen_, &h_rcbuf_, &h_ccodes_})
     if (b->p) cudaFreeHost(b->p);
   model_free(M_);
 }
@@ -207,6 +207,8 @@ int Codec::create(const lpc_config& cfg, const void* blob, size_t len) {
   }
   add((void**)&d_N_, 8 * (kHeights + 1));
   add((void**)&d_foff_, 8 * kHeights * (F_ + 1));
+  add((void**)&d_cN_, 8 * (kMaxDepth + 2));
+  add((void**)&d_cfoff_, 8 * (kMaxDepth + 1) * (F_ + 1));
   add((void**)&d_fr_, sizeof(DevFrame) * F_);
   add((void**)&d_L_, 4 * F_);
   add((void**)&d_err_, 16);
@@ -264,6 +266,8 @@ int Codec::create(const lpc_config& cfg, const void* blob, size_t len) {
   std::vector<HSlice> hs = {
       {(void**)&h_N_, 8 * (kHeights + 1)},
       {(void**)&h_foff_, 8 * (size_t)kHeights * (F_ + 1)},
+      {(void**)&h_cN_, 8 * (kMaxDepth + 2)},
+      {(void**)&h_cfoff_, 8 * (size_t)(kMaxDepth + 1) * (F_ + 1)},
       {(void**)&h_fr_, sizeof(DevFrame) * F_},
       {(void**)&h_L_, 4 * (size_t)F_},
       {(void**)&h_err_, 16},
@@ -384,7 +388,8 @@ int Codec::sync_and_check(const char* what) {
 // the top bits), one radix sort, duplicate removal, then six rounds of
 // floor-halving with occupancy codes (supplement, "Implementation of Octree
 // Operations").  Ends with N_ and every frame's offsets on the host.
-int Codec::build_levels_device(int nf, const int32_t* const* xyz, const int64_t* n) {
+int Codec::build_levels_device(int nf, const int32_t* const* xyz, const int64_t* n,
+                                bool coarse) {
   int64_t total = 0;
   int maxL = 0;
   for (int f = 0; f < nf; f++) {
@@ -407,6 +412,31 @@ int Codec::build_levels_device(int nf, const int32_t* const* xyz, const int64_t*
   for (int h = 0; h + 1 < kHeights; h++)
     launch_level_up(key_[h], d_N_ + h, P_, key_[h + 1], code_[h + 1], off_[h + 1], par_[h],
                     d_N_ + h + 1, scan_, st_);
+  // coarse heights (encoder): the same halving up to the deepest frame's
+  // root; frames with a smaller depth carry their root up unchanged
+  max_h_ = kHeights - 1;
+  if (coarse) {
+    const uint64_t* src = key_[kHeights - 1];
+    const int64_t* dn = d_N_ + kHeights - 1;
+    uint64_t* pp[2] = {d_keys0_, sort_.alt};
+    for (int h = kHeights; h <= maxL; h++) {
+      uint64_t* dst = pp[h & 1];
+      launch_level_up(src, dn, P_, dst, coarse_codes(h), nullptr, nullptr, d_cN_ + h, scan_, st_);
+      LevelPtrs lp{};
+      lp.key[0] = dst;
+      lp.n[0] = d_cN_ + h;
+      launch_frame_offsets(lp, 1, nf, d_cfoff_ + (size_t)h * (nf + 1), st_);
+      src = dst;
+      dn = d_cN_ + h;
+    }
+    max_h_ = std::max(maxL, kHeights - 1);
+    if (max_h_ >= kHeights) {
+      cudaMemcpyAsync(h_cN_ + kHeights, d_cN_ + kHeights, 8 * (max_h_ - kHeights + 1),
+                      cudaMemcpyDeviceToHost, st_);
+      cudaMemcpyAsync(h_cfoff_ + (size_t)kHeights * (nf + 1), d_cfoff_ + (size_t)kHeights * (nf + 1),
+                      8 * (size_t)(max_h_ - kHeights + 1) * (nf + 1), cudaMemcpyDeviceToHost, st_);
+    }
+  }
   pend(kFamLevels, 0, 0);
   fetch_frame_offsets(nf);
   cudaMemcpyAsync(h_N_, d_N_, 8 * kHeights, cudaMemcpyDeviceToHost, st_);
@@ -586,36 +616,6 @@ void Codec::net_level(int j, int mode, uint16_t* cdf, uint32_t* enc, int8_t* log
   pred(j, fo_, 32);
 }
 
-// ------------------------------------------------------------ host octree --
-namespace {
-
-// Coarse levels of one frame from its V_{b-1} keys (Morton, no frame bits)
-// and codes Y_{b-1}: floor-halving with duplicate removal up to the root.
-// Returns codes per depth 0..b-1.
-std::vector<std::vector<uint8_t>> coarse_from_keys(const uint64_t* keys, const uint8_t* codes,
-                                                   int64_t n, int b) {
-  std::vector<std::vector<uint8_t>> out(b);
-  out[b - 1].assign(codes, codes + n);
-  std::vector<uint64_t> cur(keys, keys + n), par;
-  for (int d = b - 2; d >= 0; d--) {
-    par.clear();
-    std::vector<uint8_t>& c = out[d];
-    c.clear();
-    for (uint64_t k : cur) {
-      const uint64_t p = k >> 3;
-      if (par.empty() || par.back() != p) {
-        par.push_back(p);
-        c.push_back(0);
-      }
-      c.back() |= (uint8_t)(1u << (k & 7));
-    }
-    cur.swap(par);
-  }
-  return out;
-}
-
-}  // namespace
-
 // --------------------------------------------------------------- encode --
 int Codec::encode(int nf, const int32_t* const* xyz, const int64_t* n, const int* Ls,
                   uint8_t* const* out, const size_t* caps, size_t* lens) {
@@ -649,10 +649,9 @@ int Codec::encode(int nf, const int32_t* const* xyz, const int64_t* n, const int
     dx[f] = xyz[dev[f]];
     dn[f] = n[dev[f]];
   }
-  std::vector<std::vector<uint8_t>> tables(nd);
   if (nd > 0) {
     begin_batch();
-    build_levels_device(nd, dx.data(), dn.data());
+    build_levels_device(nd, dx.data(), dn.data(), true);
     if (int s = sync_and_check("encode: octree")) return s;
     stats.phase_us[0] = now_us() - t0;
     for (int h = 0; h < kHeights; h++) N_[h] = h_N_[h];
@@ -662,9 +661,19 @@ int Codec::encode(int nf, const int32_t* const* xyz, const int64_t* n, const int
         fr_[f].off[h] = h_foff_[h * (nd + 1) + f];
         fr_[f].cnt[h] = h_foff_[h * (nd + 1) + f + 1] - fr_[f].off[h];
       }
-    // V_{b-1} keys and codes of every frame to the host (coarse levels)
-    cudaMemcpyAsync(h_keys6_, key_[6], 8 * N_[6], cudaMemcpyDeviceToHost, st_);
+    // codes of the coarse levels (depths 0..b-1 = heights 6..L_f) to the host
+    std::vector<size_t> hoff(max_h_ + 1, 0);
+    size_t ctot = 0;
+    for (int h = kHeights; h <= max_h_; h++) {
+      hoff[h] = ctot;
+      ctot += (size_t)h_cN_[h];
+    }
+    uint8_t* hcc = static_cast<uint8_t*>(hgrow(h_ccodes_, ctot + 16));
+    if (!hcc) return fail(LPC_CUDA_ERROR, "encode: pinned allocation failed");
     cudaMemcpyAsync(h_codes_ + 6 * P_, code_[6], N_[6], cudaMemcpyDeviceToHost, st_);
+    for (int h = kHeights; h <= max_h_; h++)
+      cudaMemcpyAsync(hcc + hoff[h], coarse_codes(h), (size_t)h_cN_[h], cudaMemcpyDeviceToHost,
+                      st_);
     cudaEventRecord(ev_[0], st_);
     // network levels of all frames: (C_s, f_s) of the true symbol of every
     // node; each level's intervals go to the host as soon as it is done
@@ -735,37 +744,40 @@ int Codec::encode(int nf, const int32_t* const* xyz, const int64_t* n, const int
     cudaEventRecord(ev_[6], st_);
     if (int s = cuda_check("encode: range coder launch")) return s;
     stats.phase_us[1] = now_us() - t0;
-    // coarse levels: one host task per frame, while the device runs the network
+    // coarse levels: one host task per (frame, level), each its own adaptive
+    // model, while the device runs the network.  The largest (depth b - 1 of
+    // the first frame) runs on this thread: it is the critical path, and a
+    // thread that was just busy runs it faster than a woken worker.
     cudaEventSynchronize(ev_[0]);
     stats.phase_us[9] = now_us() - t0;
+    std::function<void()> mine;
     for (int f = 0; f < nd; f++) {
-      pool_->submit(0, [this, f] {
-        Frame& F = fr_[f];
-        const int64_t r0 = F.off[6], cnt = F.cnt[6];
-        std::vector<uint64_t> k(cnt);
-        for (int64_t i = 0; i < cnt; i++) k[i] = h_keys6_[r0 + i] & kLowMask;
-        F.coarse = coarse_from_keys(k.data(), h_codes_ + 6 * P_ + r0, cnt, F.b);
-        // one coding task per coarse level (each level is its own adaptive
-        // model); slots laid out in the frame's coarse region
-        size_t ao = tasks_[F.sub_base].arena;
-        for (int d = 0; d < F.b; d++) {
-          SubTask& T = tasks_[F.sub_base + d];
-          T.arena = ao;
-          T.count = (int64_t)F.coarse[d].size();
-          ao += coded_bound((size_t)T.count);
+      Frame& F = fr_[f];
+      size_t ao = tasks_[F.sub_base].arena;
+      for (int d = 0; d < F.b; d++) {
+        const int h = F.L - d;
+        const uint8_t* codes;
+        int64_t cnt;
+        if (h == kHeights - 1) {
+          codes = h_codes_ + 6 * P_ + F.off[6];
+          cnt = F.cnt[6];
+        } else {
+          const int64_t* fo = h_cfoff_ + (size_t)h * (nd + 1);
+          codes = hcc + hoff[h] + fo[f];
+          cnt = fo[f + 1] - fo[f];
         }
-        for (int d = F.b - 1; d >= 0; d--) {
-          pool_->submit(0, [this, f, d] {
-            Frame& F = fr_[f];
-            const std::vector<uint8_t>& c = F.coarse[d];
-            std::vector<uint8_t> syms(c.size());
-            for (size_t i = 0; i < c.size(); i++) syms[i] = (uint8_t)(c[i] - 1);
-            SubTask& T = tasks_[F.sub_base + d];
-            T.len = encode_adaptive(syms.data(), syms.size(), h_arena_ + T.arena,
-                                    coded_bound(syms.size()));
-          });
-        }
-      });
+        SubTask& T = tasks_[F.sub_base + d];
+        T.arena = ao;
+        T.count = cnt;
+        ao += coded_bound((size_t)cnt);
+        stats.N[d] = f == 0 ? cnt : stats.N[d];
+        auto task = [this, &T, codes, cnt] {
+          T.len = encode_adaptive_codes(codes, (size_t)cnt, h_arena_ + T.arena,
+                                        coded_bound((size_t)cnt));
+        };
+        if (f == 0 && d == F.b - 1) mine = task;
+        else pool_->submit(0, task);
+      }
     }
     for (int j = 0; j < 5 && !dev_rc_; j++) {
       cudaEventSynchronize(ev_[1 + j]);
@@ -784,10 +796,11 @@ int Codec::encode(int nf, const int32_t* const* xyz, const int64_t* n, const int
         }
       }
     }
-    cudaEventSynchronize(ev_[6]);
-    stats.phase_us[10] = now_us() - t0;
+    if (mine) mine();
     pool_->wait(0);
     stats.phase_us[11] = now_us() - t0;
+    cudaEventSynchronize(ev_[6]);
+    stats.phase_us[10] = now_us() - t0;
     if (dev_rc_)
       for (SubTask& T : tasks_)
         if (T.rc >= 0) T.len = static_cast<const uint32_t*>(h_rclen_.p)[T.rc];
@@ -839,8 +852,7 @@ int Codec::encode(int nf, const int32_t* const* xyz, const int64_t* n, const int
   // statistics of the first frame
   if (nd > 0) {
     const Frame& F = fr_[0];
-    stats.L = F.L;
-    for (int d = 0; d < F.b; d++) stats.N[d] = (int64_t)F.coarse[d].size();
+    stats.L = F.L;  // coarse depths were counted when their tasks were made
     for (int h = 0; h < kHeights; h++) stats.N[F.L - h] = F.cnt[h];
   }
   stats.host_us = now_us() - t0;
@@ -933,8 +945,7 @@ int Codec::decode(int nf, const uint8_t* const* in, const size_t* lens, int32_t*
   std::vector<std::vector<uint64_t>> k6(nd);
   std::atomic<int> cstat{0};
   const int64_t maxp = cfg_.max_points;
-  for (int f = 0; f < nd; f++) {
-    pool_->submit(0, [&, f] {
+  auto coarse = [&](int f) {
       Frame& F = fr_[f];
       F.coarse.assign(F.b, {});
       std::vector<uint64_t> keys(1, 0), next;
@@ -958,8 +969,10 @@ int Codec::decode(int nf, const uint8_t* const* in, const size_t* lens, int32_t*
         keys.swap(next);
       }
       k6[f].swap(keys);
-    });
-  }
+  };
+  // frame 0 on this thread (recently busy, so fast), the others on workers
+  for (int f = 1; f < nd; f++) pool_->submit(0, [&, f] { coarse(f); });
+  coarse(0);
   pool_->wait(0);
   if (cstat == LPC_CORRUPT_STREAM) return fail(LPC_CORRUPT_STREAM, "decode: corrupt coarse substream");
   if (cstat == LPC_CAPACITY) return fail(LPC_CAPACITY, "decode: frame exceeds max_points");
@@ -1211,7 +1224,7 @@ int Codec::probs(const int32_t* d_xyz, int64_t n, int d, uint16_t* d_cdf, int64_
   fr_[0].n = n;
   begin_batch();
   const int32_t* x = d_xyz;
-  build_levels_device(1, &x, &n);
+  build_levels_device(1, &x, &n, false);
   if (int s = sync_and_check("probs_level")) return s;
   for (int h = 0; h < kHeights; h++) N_[h] = h_N_[h];
   level_bytes();

@@ -125,7 +125,10 @@ class Codec {
   int check_device_error();
   int sync_and_check(const char* what);
   // octree of the batch: heights 0..6 on the device, coarse levels on the host
-  int build_levels_device(int nf, const int32_t* const* xyz, const int64_t* n);
+  int build_levels_device(int nf, const int32_t* const* xyz, const int64_t* n, bool coarse);
+  uint8_t* coarse_codes(int h) const {  // codes of coarse height h >= 7 (encoder)
+    return reinterpret_cast<uint8_t*>(d_cdf_) + (size_t)(h - kHeights) * P_;
+  }
   void fetch_frame_offsets(int nf);
   void begin_batch();
   void level_bytes();
@@ -175,6 +178,14 @@ class Codec {
   uint32_t* par_[kHeights] = {};   // parent row at height h+1, heights 0..5
   int64_t* d_N_ = nullptr;         // [kHeights + 1]: rows per height, then the point count
   int64_t* d_foff_ = nullptr;      // [kHeights][F + 1] frame offsets
+  // encoder's coarse heights 7..max_h_ (depths below b - 1 of every frame):
+  // keys ping-pong through the sort buffers, codes in the (then unused)
+  // table buffer, one P-byte slot per height
+  int64_t* d_cN_ = nullptr;        // [kMaxDepth + 2] rows per coarse height
+  int64_t* d_cfoff_ = nullptr;     // [kMaxDepth + 1][F + 1] frame offsets per coarse height
+  int64_t* h_cN_ = nullptr;
+  int64_t* h_cfoff_ = nullptr;
+  int max_h_ = kHeights - 1;
   DevFrame* d_fr_ = nullptr;       // [F]
   int* d_L_ = nullptr;             // [F] frame depths
   int* d_err_ = nullptr;
@@ -216,7 +227,7 @@ class Codec {
   };
   void* dgrow(Buf& b, size_t bytes);
   void* hgrow(Buf& b, size_t bytes);
-  Buf d_rcck_, d_rclen_, d_rcbuf_, h_rcck_, h_rclen_, h_rcbuf_;
+  Buf d_rcck_, d_rclen_, d_rcbuf_, h_rcck_, h_rclen_, h_rcbuf_, h_ccodes_;
   bool dev_rc_ = true;
   std::vector<int64_t> in_base_;  // each decoded frame's first byte in d_rcbuf_
   int decode_net_device(int nd, int64_t* n_out, const std::vector<int>& dev, const int64_t* caps);

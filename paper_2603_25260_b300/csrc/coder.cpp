@@ -126,6 +126,14 @@ size_t encode_adaptive(const uint8_t* syms, size_t n, uint8_t* out, size_t cap) 
   return e.size();
 }
 
+size_t encode_adaptive_codes(const uint8_t* codes, size_t n, uint8_t* out, size_t cap) {
+  RangeEncoder e(out, cap);
+  AdaptiveModel m;
+  for (size_t i = 0; i < n; i++) m.encode(e, codes[i] - 1);
+  e.finish();
+  return e.size();
+}
+
 // The tables were just written to host memory by DMA, so they are not in any
 // CPU cache: the eight 64-byte lines of a row are prefetched a few rows ahead
 // of the binary search.

@@ -102,6 +102,8 @@ inline size_t coded_bound(size_t n) { return 2 * n + 8; }
 size_t encode_packed(const uint32_t* lofreq, size_t n, uint8_t* out, size_t cap);
 // Encode symbols with the adaptive model (one model per substream).
 size_t encode_adaptive(const uint8_t* syms, size_t n, uint8_t* out, size_t cap);
+// The same from occupancy codes 1..255 (symbol = code - 1).
+size_t encode_adaptive_codes(const uint8_t* codes, size_t n, uint8_t* out, size_t cap);
 // Decode n symbols with table rows; returns false on a corrupt stream.
 bool decode_rows(const uint16_t* rows, size_t n, const uint8_t* in, size_t len, uint8_t* syms);
 bool decode_adaptive(size_t n, const uint8_t* in, size_t len, uint8_t* syms);

@@ -68,7 +68,7 @@ int64_t scan_tiles_for(int64_t cap);
 void launch_unique(const uint64_t* keys, const int64_t* d_n, int64_t cap, uint64_t* out,
                    int64_t* d_nout, const ScanScratch& s, cudaStream_t st);
 // One level up: children (sorted, unique) -> parents, codes, child offsets,
-// parent index of every child.
+// parent index of every child (poff and cpar may be null).
 void launch_level_up(const uint64_t* ckeys, const int64_t* d_nc, int64_t cap_c, uint64_t* pkeys,
                      uint8_t* pcodes, uint32_t* poff, uint32_t* cpar, int64_t* d_np,
                      const ScanScratch& s, cudaStream_t st);

@@ -385,11 +385,11 @@ struct LevelOp {
   }
   __device__ void emit(int64_t i, uint32_t ex, int64_t n) const {
     const uint32_t h = value(i);
-    cpar[i] = ex + h - 1;
+    if (cpar) cpar[i] = ex + h - 1;
     if (h) {
       const uint64_t p = parent_key(ck[i]);
       pk[ex] = p;
-      poff[ex] = (uint32_t)i;
+      if (poff) poff[ex] = (uint32_t)i;
       uint32_t code = 0;
       for (int64_t j = i; j < n && j < i + 8 && parent_key(ck[j]) == p; j++)
         code |= 1u << (ck[j] & 7);
@@ -398,7 +398,7 @@ struct LevelOp {
   }
   __device__ void finish(uint32_t total, int64_t n) const {
     *np = total;
-    poff[total] = (uint32_t)n;
+    if (poff) poff[total] = (uint32_t)n;
   }
 };
 
