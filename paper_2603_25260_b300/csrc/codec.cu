@@ -940,69 +940,44 @@ int Codec::decode(int nf, const uint8_t* const* in, const size_t* lens, int32_t*
     for (int f = 0; f < nd; f++) memcpy(hb + in_base_[f], fr_[f].in, fr_[f].len);
     cudaMemcpyAsync(db, hb, tot, cudaMemcpyHostToDevice, st_);
   }
-  // coarse levels: decoded and expanded to V_{b-1} on the host, one task per
-  // frame (levels are sequential within a frame: N_{d+1} = sum popcount Y_d)
-  std::vector<std::vector<uint64_t>> k6(nd);
+  // coarse levels (depths 0..b-1): adaptive-model decoding on the host
   std::atomic<int> cstat{0};
-  const int64_t maxp = cfg_.max_points;
-  auto coarse = [&](int f) {
+  {
+    // one task per frame, levels in order (N_{d+1} = sum of popcounts of Y_d);
+    // frame 0 on this thread: the thread that was just busy runs it fastest
+    const int64_t maxp = cfg_.max_points;
+    auto coarse = [&](int f) {
       Frame& F = fr_[f];
       F.coarse.assign(F.b, {});
-      std::vector<uint64_t> keys(1, 0), next;
+      int64_t n = 1;
       for (int d = 0; d < F.b; d++) {
         std::vector<uint8_t>& Y = F.coarse[d];
-        Y.resize(keys.size());
+        Y.resize((size_t)n);
         if (!decode_adaptive(Y.size(), F.in + F.soff[d], (size_t)F.slen[d], Y.data())) {
           cstat = LPC_CORRUPT_STREAM;
           return;
         }
-        for (auto& y : Y) y += 1;
-        if (d + 1 == F.b) break;
-        next.clear();
-        for (size_t p = 0; p < keys.size(); p++)
-          for (int c = 0; c < 8; c++)
-            if (Y[p] >> c & 1) next.push_back((keys[p] << 3) | (uint64_t)c);
-        if ((int64_t)next.size() > maxp) {
+        n = 0;
+        for (auto& y : Y) n += __builtin_popcount(++y);
+        if (n > maxp) {
           cstat = LPC_CAPACITY;
           return;
         }
-        keys.swap(next);
       }
-      k6[f].swap(keys);
-  };
-  // frame 0 on this thread (recently busy, so fast), the others on workers
-  for (int f = 1; f < nd; f++) pool_->submit(0, [&, f] { coarse(f); });
-  coarse(0);
-  pool_->wait(0);
+    };
+    for (int f = 1; f < nd; f++) pool_->submit(0, [&, f] { coarse(f); });
+    coarse(0);
+    pool_->wait(0);
+  }
   if (cstat == LPC_CORRUPT_STREAM) return fail(LPC_CORRUPT_STREAM, "decode: corrupt coarse substream");
   if (cstat == LPC_CAPACITY) return fail(LPC_CAPACITY, "decode: frame exceeds max_points");
-  // V_{b-1} of every frame (height 6) to the device
-  int64_t n6 = 0;
-  for (int f = 0; f < nd; f++) {
-    Frame& F = fr_[f];
-    F.off[6] = n6;
-    F.cnt[6] = (int64_t)k6[f].size();
-    n6 += F.cnt[6];
-  }
-  if (n6 > P_) return fail(LPC_CAPACITY, "decode: batch exceeds the codec's capacity");
-  for (int f = 0; f < nd; f++) {
-    Frame& F = fr_[f];
-    const uint64_t fb = (uint64_t)f << kFrameShift;
-    for (int64_t i = 0; i < F.cnt[6]; i++) {
-      h_keys6_[F.off[6] + i] = fb | k6[f][i];
-      h_codes_[6 * P_ + F.off[6] + i] = F.coarse[F.b - 1][i];
-    }
-  }
-  N_[6] = n6;
-  h_N_[6] = n6;
-  cudaMemcpyAsync(d_N_ + 6, h_N_ + 6, 8, cudaMemcpyHostToDevice, st_);
-  cudaMemcpyAsync(key_[6], h_keys6_, 8 * n6, cudaMemcpyHostToDevice, st_);
-  cudaMemcpyAsync(code_[6], h_codes_ + 6 * P_, n6, cudaMemcpyHostToDevice, st_);
+  if (int s = expand_coarse_device(nd)) return s;
   stats.phase_us[4] = now_us() - t0;
   for (int i = 5; i < 9; i++) stats.phase_us[i] = 0;
   if (dev_rc_) {
     if (int s = decode_net_device(nd, n_out, dev, caps)) return s;
   } else {
+  const int64_t maxp = cfg_.max_points;
   // substream index of (frame, relative level j, chunk 0)
   std::vector<std::vector<size_t>> sidx(nd, std::vector<size_t>(6, 0));
   std::atomic<bool> bad{false};
@@ -1127,6 +1102,68 @@ int Codec::decode(int nf, const uint8_t* const* in, const size_t* lens, int32_t*
   stats.phase_us[8] = stats.host_us;
   prof_collect();
   return LPC_OK;
+}
+
+// Coarse codes of every frame to the device, arranged by height (height h is
+// depth L_f - h; above a frame's root the root is carried up with code 1),
+// and expanded from the roots down to V_{b-1} (height 6) on the device.
+int Codec::expand_coarse_device(int nd) {
+  int top = kHeights - 1;
+  for (int f = 0; f < nd; f++) top = std::max(top, fr_[f].L);
+  std::vector<int64_t> hcnt(top + 1, 0), hoff(top + 1, 0);
+  size_t tot = 0;
+  for (int h = top; h >= kHeights - 1; h--) {
+    hoff[h] = (int64_t)tot;
+    for (int f = 0; f < nd; f++) {
+      const Frame& F = fr_[f];
+      hcnt[h] += h > F.L ? 1 : (int64_t)F.coarse[F.L - h].size();
+    }
+    tot += (size_t)hcnt[h];
+    if (hcnt[h] > P_) return fail(LPC_CAPACITY, "decode: batch exceeds the codec's capacity");
+  }
+  uint8_t* hc = static_cast<uint8_t*>(hgrow(h_ccodes_, tot + 16));
+  if (!hc) return fail(LPC_CUDA_ERROR, "decode: pinned allocation failed");
+  for (int h = top; h >= kHeights - 1; h--) {
+    uint8_t* o = hc + hoff[h];
+    for (int f = 0; f < nd; f++) {
+      Frame& F = fr_[f];
+      if (h == kHeights - 1) F.off[6] = o - (hc + hoff[h]);
+      if (h > F.L) {
+        *o++ = 1;
+      } else {
+        const std::vector<uint8_t>& Y = F.coarse[F.L - h];
+        memcpy(o, Y.data(), Y.size());
+        o += Y.size();
+      }
+      if (h == kHeights - 1) F.cnt[6] = (o - (hc + hoff[h])) - F.off[6];
+    }
+  }
+  // height-6 codes also on the host (the host-coding path counts from them)
+  memcpy(h_codes_ + 6 * P_, hc + hoff[kHeights - 1], (size_t)hcnt[kHeights - 1]);
+  N_[6] = hcnt[kHeights - 1];
+  h_N_[6] = N_[6];
+  // roots (one per frame) at the top height, then expansions down to 6
+  for (int f = 0; f < nd; f++) h_keys6_[f] = (uint64_t)f << kFrameShift;
+  h_cN_[top] = nd;
+  uint64_t* pp[2] = {d_keys0_, sort_.alt};
+  uint64_t* top_keys = top == kHeights - 1 ? key_[6] : pp[top & 1];
+  cudaMemcpyAsync(top_keys, h_keys6_, 8 * (size_t)nd, cudaMemcpyHostToDevice, st_);
+  cudaMemcpyAsync(top == kHeights - 1 ? d_N_ + 6 : d_cN_ + top, h_cN_ + top, 8,
+                  cudaMemcpyHostToDevice, st_);
+  for (int h = top; h >= kHeights; h--)
+    cudaMemcpyAsync(coarse_codes(h), hc + hoff[h], (size_t)hcnt[h], cudaMemcpyHostToDevice, st_);
+  cudaMemcpyAsync(code_[6], hc + hoff[kHeights - 1], (size_t)hcnt[kHeights - 1],
+                  cudaMemcpyHostToDevice, st_);
+  pbeg(kFamLevels);
+  for (int h = top; h >= kHeights; h--) {
+    uint64_t* src = pp[h & 1];
+    const bool to6 = h - 1 == kHeights - 1;
+    uint64_t* dst = to6 ? key_[6] : pp[(h - 1) & 1];
+    launch_expand(src, coarse_codes(h), d_cN_ + h, P_, dst, nullptr, nullptr, P_,
+                  to6 ? d_N_ + 6 : d_cN_ + h - 1, scan_, d_err_, st_);
+  }
+  pend(kFamLevels, 21.0 * (double)tot, 0);
+  return cuda_check("decode: coarse expansion");
 }
 
 // Network levels decoded on the device: per relative level, expand the

@@ -45,6 +45,7 @@ class Pool {
   bool stop_ = false;
 };
 
+
 // Kernel families timed by the optional CUDA-event profiler.
 enum Family {
   kFamSort = 0,  // Morton keys + radix sort + unique
@@ -231,6 +232,7 @@ class Codec {
   bool dev_rc_ = true;
   std::vector<int64_t> in_base_;  // each decoded frame's first byte in d_rcbuf_
   int decode_net_device(int nd, int64_t* n_out, const std::vector<int>& dev, const int64_t* caps);
+  int expand_coarse_device(int nd);
   std::vector<SubTask> tasks_;
   std::vector<cudaEvent_t> ev_;
 };

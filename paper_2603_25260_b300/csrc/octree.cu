@@ -426,7 +426,7 @@ struct ExpandOp {
     const uint32_t code = pc[p];
     if (code == 0) set_error(err, kErrExpand);
     int64_t r = ex;
-    poff[p] = (uint32_t)(r < cap_c ? r : cap_c);
+    if (poff) poff[p] = (uint32_t)(r < cap_c ? r : cap_c);
     for (int c = 0; c < 8; c++)
       if (code >> c & 1) {
         if (r >= cap_c) {
@@ -434,14 +434,14 @@ struct ExpandOp {
           break;
         }
         ck[r] = child_key(pk[p], (uint32_t)c);
-        cpar[r] = (uint32_t)p;
+        if (cpar) cpar[r] = (uint32_t)p;
         r++;
       }
   }
   __device__ void finish(uint32_t total, int64_t n) const {
     const int64_t t = (int64_t)total < cap_c ? (int64_t)total : cap_c;
     *nc = t;
-    poff[n] = (uint32_t)t;
+    if (poff) poff[n] = (uint32_t)t;
   }
 };
 
