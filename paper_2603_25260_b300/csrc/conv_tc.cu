@@ -11,18 +11,28 @@
 // such accumulators (separate TMEM column blocks) which the epilogue adds in
 // INT32.
 //
-// One CTA (256 threads) owns a tile of 128 output nodes (Morton order) at a
-// time, persistent over tiles.  The weights of all 27 offsets stay in shared
-// memory (bf16, 128-byte swizzled K-major).  For every offset that at least
-// one node of the tile has, the threads gather the 128 neighbour rows
-// (pre-subtracted bf16 rows, 16-byte cp.async copies, zero-filled when the
-// neighbour is absent, which is the exact zero padding of the sparse conv)
-// into a swizzled stage; one thread issues the M=128, N=32, K=16 MMAs into
-// the offset's accumulator.  Gathers run several offsets ahead of the MMAs.
-// The epilogue reads the accumulators from TMEM, adds the bias, applies the
-// PReLU and the fixed-point requantisation (Eq. 14), the fused residual
-// merge of the ResBlock, and writes int8 (and optionally the next conv's
-// bf16 input).
+// Warp-specialised and persistent: one CTA per SM walks its tiles of 128
+// output nodes (Morton order) and, for each, all 27 offsets.
+//  - 4 producer warps gather, for each (tile, offset), the 128 neighbour rows
+//    (pre-subtracted bf16 rows, 16-byte cp.async copies, zero-filled when the
+//    neighbour is absent: the exact zero padding of the sparse conv) into a
+//    ring of swizzled stages.  A thread that saw its copies of a stage land
+//    fences them to the async proxy and arrives on the stage's "full"
+//    barrier; it keeps kAhead stages of its own copies in flight.
+//  - 1 MMA warp: one thread waits for a full stage and issues the M=128,
+//    N=32, K=16 MMAs into the offset's accumulator; tcgen05.commit releases
+//    the stage ("empty" barrier) when they are done, and after the tile's
+//    last offset signals the accumulator buffer full.
+//  - 4 epilogue warps (one per TMEM lane quadrant, one output row a thread)
+//    read the accumulators, add them in INT32 with the bias, apply the PReLU
+//    and the fixed-point requantisation (Eq. 14) and the fused residual merge
+//    of the ResBlock, write int8 (and optionally the next conv's bf16 input),
+//    and hand the buffer back.  Two accumulator buffers let the epilogue of
+//    one tile overlap the MMAs of the next.
+// The weights of all 27 offsets stay in shared memory (bf16, 128-byte
+// swizzled K-major).  Every wait is bounded; a wait that gives up raises a
+// shared abort flag that ends every other wait, and the CTA drains its own
+// copies and MMAs before it frees its tensor memory.
 #include <cuda_bf16.h>
 
 #include <string.h>
@@ -38,224 +48,320 @@ namespace lpc {
 namespace {
 
 constexpr int kTileM = 128;
-constexpr int kThreads = 256;
-constexpr int kDepth = 3;  // offsets gathered ahead of the MMA issue
+constexpr int kProducers = 128;  // warps 0-3
+constexpr int kEpilogue = 128;   // warps 4-7
+constexpr int kThreads = kProducers + kEpilogue + 32;  // + the MMA warp (8)
 
 template <int CIN>
 struct ConvCfg {
   static constexpr int RB = CIN * 2;                 // bf16 row bytes
   static constexpr int SW = CIN == 64 ? 128 : 64;    // swizzle of the A stage
-  static constexpr int kStages = CIN == 64 ? 6 : 8;
+  static constexpr int kStages = CIN == 64 ? 5 : 12;
+  // stages of its own copies a producer keeps in flight
+  static constexpr int kAhead = kStages - 1 < 7 ? kStages - 1 : 7;
   static constexpr int kStageBytes = kTileM * RB;
   static constexpr int kPerGroup = 256 / CIN;        // offsets per fp32 accumulator
+  static constexpr int kGroups = (27 + kPerGroup - 1) / kPerGroup;
+  static constexpr int kBufCols = 256;               // TMEM columns per accumulator buffer
   static constexpr int kBBlocks = (27 * CIN + 63) / 64;
   static constexpr int kBBytes = kBBlocks * 4096;
   static constexpr int kChunks = RB / 16;            // 16-byte chunks per row
-  static constexpr int kNbrBytes = kTileM * 27 * 4;  // the tile's neighbour rows
+  static constexpr int kNbrBytes = kTileM * 27 * 4;  // a tile's neighbour rows
   static constexpr size_t kSmem =
-      1024 + kBBytes + (size_t)kStages * kStageBytes + kNbrBytes;
+      1024 + kBBytes + (size_t)kStages * kStageBytes + 2 * kNbrBytes;
+  static_assert(kStages > kAhead, "a producer must be able to run kAhead stages ahead");
+  static_assert(kGroups * 32 <= kBufCols, "accumulators of one tile exceed a buffer");
 };
 
 __device__ int g_conv_error = 0;
+
+
+// Bounded wait that also ends as soon as another thread has raised *abort.
+__device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity,
+                                              volatile int* abort) {
+  const uint32_t a = tc::smem_u32(bar);
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (*abort) return false;
+    if (clock64() - t0 > (1ll << 31)) {
+      *abort = 1;
+      return false;
+    }
+  }
+}
+
+// One bulk (TMA) copy global -> shared counted on bar; 16-byte aligned
+// addresses, size a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      ::"r"(tc::smem_u32(dst)), "l"(src), "r"(bytes), "r"(tc::smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void mbar_expect(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+                   tc::smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
+}
+
+// Barrier of the 128 producer threads that also ORs a flag over them, so
+// that they all take the same decision.
+__device__ __forceinline__ bool producer_sync_or(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n.reg .pred p, q;\nsetp.ne.u32 p, %1, 0;\nbar.red.or.pred q, 1, %2, p;\n"
+      "selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v), "n"(kProducers)
+      : "memory");
+  return r != 0;
+}
 
 template <int CIN>
 __global__ void __launch_bounds__(kThreads, 1)
 k_conv333_tc(ConvTcArgs a) {
   using Cfg = ConvCfg<CIN>;
+  constexpr int S = Cfg::kStages;
   extern __shared__ unsigned char smraw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
   unsigned char* sB = sm;
   unsigned char* sA = sm + Cfg::kBBytes;
-  int32_t* sNbr = reinterpret_cast<int32_t*>(sA + (size_t)Cfg::kStages * Cfg::kStageBytes);
-  __shared__ uint64_t bar[Cfg::kStages];
-  __shared__ uint64_t done_bar;
+  int32_t* sNbr0 = reinterpret_cast<int32_t*>(sA + (size_t)S * Cfg::kStageBytes);
+  __shared__ uint64_t full_bar[S], empty_bar[S], acc_full[2], acc_empty[2], drain_bar;
+  __shared__ uint64_t w_bar, nbr_bar[2];
   __shared__ uint32_t tslot;
-  __shared__ uint32_t tile_mask;
   __shared__ int abort_flag;
+  __shared__ int32_t sBias[32], sMult[32], sSlope[32], sMa[32], sMb[32], sRsl[32];
+  volatile int* abort = &abort_flag;
 
   const int t = threadIdx.x, w = t >> 5, lane = t & 31;
-  if (w == 0) tc::tmem_alloc(&tslot, 256);
+  if (w == 8) tc::tmem_alloc(&tslot, 512);
   if (t == 0) {
-    for (int s = 0; s < Cfg::kStages; s++) tc::mbar_init(&bar[s], 1);
-    tc::mbar_init(&done_bar, 1);
+    for (int s = 0; s < S; s++) {
+      tc::mbar_init(&full_bar[s], kProducers);
+      tc::mbar_init(&empty_bar[s], 1);
+    }
+    for (int b = 0; b < 2; b++) {
+      tc::mbar_init(&acc_full[b], 1);
+      tc::mbar_init(&acc_empty[b], kEpilogue);
+    }
+    tc::mbar_init(&drain_bar, 1);
+    tc::mbar_init(&w_bar, 1);
+    tc::mbar_init(&nbr_bar[0], 1);
+    tc::mbar_init(&nbr_bar[1], 1);
     tc::fence_mbar_init();
     abort_flag = 0;
+    // weights: the pre-swizzled image in bulk copies; only the MMA thread
+    // reads it, after waiting on w_bar
+    mbar_expect(&w_bar, Cfg::kBBytes);
+    for (int off = 0; off < Cfg::kBBytes; off += 16384)
+      bulk_g2s(sm + off, reinterpret_cast<const unsigned char*>(a.wimg) + off,
+               (uint32_t)min(16384, Cfg::kBBytes - off), &w_bar);
   }
-  // weights: pre-swizzled image, copied linearly
-  {
-    const uint4* src = reinterpret_cast<const uint4*>(a.wimg);
-    uint4* dst = reinterpret_cast<uint4*>(sB);
-    for (int i = t; i < Cfg::kBBytes / 16; i += kThreads) dst[i] = __ldg(src + i);
+  if (t < 32) {
+    sBias[t] = a.bias[t];
+    sMult[t] = a.mult[t];
+    sSlope[t] = a.prelu ? a.slope[t] : 0;
+    sMa[t] = a.has_res ? a.res_mab[t] : 0;
+    sMb[t] = a.has_res ? a.res_mab[32 + t] : 0;
+    sRsl[t] = a.has_res ? a.res_slope[t] : 0;
   }
-  tc::fence_async_smem();
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
   const uint32_t tbase = tslot;
   const int64_t n = *a.d_n;
   const int64_t ntiles = (n + kTileM - 1) / kTileM;
-  constexpr uint32_t idesc = tc::idesc_bf16(kTileM, 32);
+  const int my_tiles =
+      blockIdx.x < ntiles ? (int)((ntiles - 1 - blockIdx.x) / gridDim.x + 1) : 0;
 
-  // epilogue constants of this thread's 16 output channels
-  const int half = w >> 2;          // column half handled by this warp
-  const int lrow = (w & 3) * 32 + lane;  // TMEM lane = row within the tile
-  int32_t bias[16], mult[16], slope[16], ma[16], mb[16], rsl[16];
-#pragma unroll
-  for (int i = 0; i < 16; i++) {
-    const int co = half * 16 + i;
-    bias[i] = a.bias[co];
-    mult[i] = a.mult[co];
-    slope[i] = a.prelu ? a.slope[co] : 0;
-    ma[i] = a.has_res ? a.res_mab[co] : 0;
-    mb[i] = a.has_res ? a.res_mab[32 + co] : 0;
-    rsl[i] = a.has_res ? a.res_slope[co] : 0;
-  }
-
-  uint32_t use = 0;    // stage uses so far (stage = use % kStages)
-  uint32_t tiles_done = 0;
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t r0 = tile * kTileM;
-    // the tile's neighbour rows into shared memory (coalesced), then the
-    // offsets present in the tile (OR of the rows' neighbour masks)
-    if (t == 0) tile_mask = 0;
-    {
-      const int64_t base = r0 * 27, lim = n * 27;
-      for (int i = t; i < kTileM * 27; i += kThreads)
-        sNbr[i] = base + i < lim ? __ldg(a.nbr + base + i) : -1;
-    }
-    __syncthreads();
-    if (t < kTileM) {
-      uint32_t m = 0;
-#pragma unroll
-      for (int o = 0; o < 27; o++) m |= (uint32_t)(sNbr[t * 27 + o] >= 0) << o;
-      m = __reduce_or_sync(0xffffffffu, m);
-      if (lane == 0) atomicOr(&tile_mask, m);
-    }
-    __syncthreads();
-    const uint32_t mask = tile_mask;
-    const int count = __popc(mask);
-
-    // gathers for offset #j into stage (use0 + j) % kStages; MMAs kDepth behind
-    uint32_t rem = mask;
-    int next_o = rem ? __ffs(rem) - 1 : 0;
-    const uint32_t use0 = use;
-    int mma_o[32];
-    for (int j = 0; j < count + kDepth; j++) {
-      if (j < count) {
-        const int o = next_o;
-        rem &= rem - 1;
-        next_o = rem ? __ffs(rem) - 1 : 0;
-        mma_o[j] = o;
-        const uint32_t u = use0 + j;
-        const int s = (int)(u % Cfg::kStages);
-        if (u >= (uint32_t)Cfg::kStages && !abort_flag) {
-          // the MMAs that last read this stage must be done
-          const bool ok = tc::mbar_wait(&bar[s], ((u / Cfg::kStages) - 1) & 1);
-          if (!ok) abort_flag = 1;
-        }
+  if (w < 4) {
+    // ---------------------------------------------------------- producers --
+    // a tile's neighbour rows: one bulk copy into buffer lt & 1, issued a
+    // tile ahead (a partial last tile is read with plain loads instead)
+    auto tile_r0 = [&](int lt) { return (blockIdx.x + (int64_t)lt * gridDim.x) * kTileM; };
+    int last_issued = -1, last_used = -1;  // thread 0's bookkeeping of nbr copies
+    auto issue_nbr = [&](int lt) {
+      if (t == 0 && lt < my_tiles && tile_r0(lt) + kTileM <= n) {
+        last_issued = lt;
+        tc::fence_async_smem();  // earlier reads of the buffer come first
+        uint64_t* bar = &nbr_bar[lt & 1];
+        mbar_expect(bar, Cfg::kNbrBytes);
+        bulk_g2s(sNbr0 + (lt & 1) * kTileM * 27, a.nbr + tile_r0(lt) * 27, Cfg::kNbrBytes, bar);
+      }
+    };
+    issue_nbr(0);
+    uint32_t u = 0;  // stages filled so far
+    for (int lt = 0; lt < my_tiles; lt++) {
+      const int64_t r0 = tile_r0(lt);
+      int32_t* sNbr = sNbr0 + (lt & 1) * kTileM * 27;
+      // every producer is done issuing the previous tile's copies; all leave
+      // together if any saw the abort flag
+      if (producer_sync_or(*abort != 0)) break;
+      issue_nbr(lt + 1);
+      if (r0 + kTileM <= n) {
+        if (producer_sync_or(!wait_or_abort(&nbr_bar[lt & 1], (lt >> 1) & 1, abort))) break;
+        last_used = lt;
+      } else {
+        const int64_t base = r0 * 27, lim = n * 27;
+        for (int i = t; i < kTileM * 27; i += kProducers)
+          sNbr[i] = base + i < lim ? __ldg(a.nbr + base + i) : -1;
+        producer_sync_or(false);
+      }
+      for (int o = 0; o < 27; o++, u++) {
+        const int s = (int)(u % S);
+        if (u >= (uint32_t)S && !wait_or_abort(&empty_bar[s], ((u / S) - 1) & 1, abort)) break;
         const uint32_t sbase = tc::smem_u32(sA + (size_t)s * Cfg::kStageBytes);
-        for (int q = t; q < kTileM * Cfg::kChunks; q += kThreads) {
+#pragma unroll
+        for (int q = t; q < kTileM * Cfg::kChunks; q += kProducers) {
           const int row = q / Cfg::kChunks, c = q % Cfg::kChunks;
           const int32_t nb = sNbr[row * 27 + o];
           const bool present = nb >= 0;
-          const unsigned char* src =
-              reinterpret_cast<const unsigned char*>(a.xb) +
-              ((present ? (int64_t)nb : 0) * a.x_stride) * 2 + c * 16;
+          const unsigned char* src = reinterpret_cast<const unsigned char*>(a.xb) +
+                                     ((present ? (int64_t)nb : 0) * a.x_stride) * 2 + c * 16;
           tc::cp_async16(sbase + tc::swz<Cfg::SW>(row * Cfg::RB + c * 16), src, present);
         }
+        tc::cp_async_commit();
+        if (u >= (uint32_t)Cfg::kAhead) {  // stage u - kAhead has landed: publish it
+          tc::cp_async_wait<Cfg::kAhead>();
+          tc::fence_async_smem();
+          mbar_arrive(&full_bar[(u - Cfg::kAhead) % S]);
+        }
       }
-      tc::cp_async_commit();
-      if (j >= kDepth - 1 && j - (kDepth - 1) < count) {
-        const int jm = j - (kDepth - 1);
-        tc::cp_async_wait<kDepth - 1>();
-        tc::fence_async_smem();
-        __syncthreads();
-        if (t == 0 && !abort_flag) {
+    }
+    // a neighbour-row copy issued but not consumed (abort) lands before exit
+    if (t == 0 && last_issued > last_used)
+      tc::mbar_wait(&nbr_bar[last_issued & 1], (last_issued >> 1) & 1);
+    // publish the stages still in flight, oldest first
+    tc::cp_async_wait<0>();
+    tc::fence_async_smem();
+    for (uint32_t v = u > (uint32_t)Cfg::kAhead ? u - Cfg::kAhead : 0; v < u; v++)
+      mbar_arrive(&full_bar[v % S]);
+  } else if (w == 8) {
+    // ---------------------------------------------------------------- MMA --
+    if (lane == 0) {
+      constexpr uint32_t idesc = tc::idesc_bf16(kTileM, 32);
+      uint32_t u = 0;
+      const bool wok = wait_or_abort(&w_bar, 0, abort);  // the weights have landed
+      for (int lt = 0; lt < my_tiles && wok && !*abort; lt++) {
+        const int b = lt & 1;
+        if (lt >= 2 && !wait_or_abort(&acc_empty[b], ((lt >> 1) - 1) & 1, abort)) break;
+        tc::tc_fence_after();
+        const uint32_t dbase = tbase + (uint32_t)(b * Cfg::kBufCols);
+        bool ok = true;
+        for (int o = 0; o < 27; o++, u++) {
+          const int s = (int)(u % S);
+          if (!wait_or_abort(&full_bar[s], (u / S) & 1, abort)) {
+            ok = false;
+            break;
+          }
           tc::tc_fence_after();
-          const int o = mma_o[jm];
-          const uint32_t u = use0 + jm;
-          const int s = (int)(u % Cfg::kStages);
-          const int g = jm / Cfg::kPerGroup;
           const uint32_t sa = tc::smem_u32(sA + (size_t)s * Cfg::kStageBytes);
+          const int g = o / Cfg::kPerGroup;
 #pragma unroll
           for (int ks = 0; ks < CIN / 16; ks++) {
             const int k0 = o * CIN + ks * 16;
             const uint32_t sb = tc::smem_u32(sB) + (k0 / 64) * 4096 + (k0 % 64) * 2;
-            tc::mma_bf16(tbase + g * 32, tc::smem_desc<Cfg::SW>(sa + ks * 32, 8 * Cfg::RB),
+            tc::mma_bf16(dbase + g * 32, tc::smem_desc<Cfg::SW>(sa + ks * 32, 8 * Cfg::RB),
                          tc::smem_desc<128>(sb, 1024), idesc,
-                         (jm % Cfg::kPerGroup != 0 || ks > 0) ? 1u : 0u);
+                         (o % Cfg::kPerGroup != 0 || ks > 0) ? 1u : 0u);
           }
-          tc::mma_commit(&bar[s]);
+          tc::mma_commit(&empty_bar[s]);
+        }
+        if (!ok) break;
+        tc::mma_commit(&acc_full[b]);
+      }
+      // every MMA this thread issued has completed before the CTA frees TMEM
+      // (a plain bounded wait: this one must not end early on abort)
+      tc::mma_commit(&drain_bar);
+      if (!tc::mbar_wait(&drain_bar, 0)) *abort = 1;
+    }
+    __syncwarp();
+  } else {
+    // ----------------------------------------------------------- epilogue --
+    const int e = t - kProducers;            // row of the tile = TMEM lane
+    const uint32_t lane_off = (uint32_t)((w & 3) * 32) << 16;
+    for (int lt = 0; lt < my_tiles; lt++) {
+      const int b = lt & 1;
+      // the TMEM loads below are warp-collective: the warp leaves together
+      if (!__all_sync(0xffffffffu, wait_or_abort(&acc_full[b], (lt >> 1) & 1, abort))) break;
+      tc::tc_fence_after();
+      int32_t acc[32];
+#pragma unroll
+      for (int i = 0; i < 32; i++) acc[i] = sBias[i];
+      const uint32_t dbase = tbase + lane_off + (uint32_t)(b * Cfg::kBufCols);
+#pragma unroll
+      for (int g = 0; g < Cfg::kGroups; g++) {
+        float v[16];
+        tc::tmem_ld16(dbase + g * 32, v);
+#pragma unroll
+        for (int i = 0; i < 16; i++) acc[i] += __float2int_rn(v[i]);
+        tc::tmem_ld16(dbase + g * 32 + 16, v);
+#pragma unroll
+        for (int i = 0; i < 16; i++) acc[16 + i] += __float2int_rn(v[i]);
+      }
+      tc::tc_fence_before();
+      mbar_arrive(&acc_empty[b]);  // the buffer is free for tile lt + 2
+      const int64_t r = (blockIdx.x + (int64_t)lt * gridDim.x) * kTileM + e;
+      if (r < n) {
+        __align__(16) int8_t q[32];
+        if (a.has_res) {
+          __align__(16) int8_t y1[32];
+          const uint4* ys = reinterpret_cast<const uint4*>(a.y1 + r * a.y1_stride);
+          reinterpret_cast<uint4*>(y1)[0] = ys[0];
+          reinterpret_cast<uint4*>(y1)[1] = ys[1];
+#pragma unroll
+          for (int i = 0; i < 32; i++) {
+            int32_t v = acc[i];
+            if (a.prelu) v = prelu(v, sSlope[i]);
+            const int y2 = requant(v, sMult[i], a.shift, a.z_out);
+            int32_t m = (y1[i] - a.res_z1) * sMa[i] + (y2 - a.res_z2) * sMb[i];
+            m = prelu(m, sRsl[i]);
+            q[i] = (int8_t)requant(m, 1, a.res_shift, a.res_z_out);
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < 32; i++) {
+            int32_t v = acc[i];
+            if (a.prelu) v = prelu(v, sSlope[i]);
+            q[i] = (int8_t)requant(v, sMult[i], a.shift, a.z_out);
+          }
+        }
+        uint4* dst = reinterpret_cast<uint4*>(a.out + r * a.out_stride + a.out_col);
+        dst[0] = reinterpret_cast<const uint4*>(q)[0];
+        dst[1] = reinterpret_cast<const uint4*>(q)[1];
+        if (a.outb) {
+          __align__(16) __nv_bfloat16 bq[32];
+#pragma unroll
+          for (int i = 0; i < 32; i++) bq[i] = __int2bfloat16_rn((int)q[i] - a.outb_z);
+          uint4* db = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(a.outb) +
+                                               r * a.outb_stride);
+#pragma unroll
+          for (int k = 0; k < 4; k++) db[k] = reinterpret_cast<const uint4*>(bq)[k];
         }
       }
     }
-    use = use0 + count;
-    // all MMAs of the tile done
-    if (t == 0 && !abort_flag) tc::mma_commit(&done_bar);
-    bool to = false;
-    if (!abort_flag) to = !tc::mbar_wait(&done_bar, tiles_done & 1);
-    if (__syncthreads_or(to)) abort_flag = 1;
-    tiles_done++;
-    tc::tc_fence_after();
-
-    // epilogue: sum the accumulators in INT32, bias, PReLU, requant, residual
-    const int groups = (count + Cfg::kPerGroup - 1) / Cfg::kPerGroup;
-    int32_t acc[16];
-#pragma unroll
-    for (int i = 0; i < 16; i++) acc[i] = bias[i];
-    for (int g = 0; g < groups; g++) {
-      float v[16];
-      tc::tmem_ld16(tbase + ((uint32_t)((w & 3) * 32) << 16) + g * 32 + half * 16, v);
-#pragma unroll
-      for (int i = 0; i < 16; i++) acc[i] += __float2int_rn(v[i]);
-    }
-    const int64_t r = r0 + lrow;
-    if (r < n && !abort_flag) {
-      int8_t q[16];
-      if (a.has_res) {
-        __align__(16) int8_t y1[16];
-        *reinterpret_cast<uint4*>(y1) =
-            *reinterpret_cast<const uint4*>(a.y1 + r * a.y1_stride + half * 16);
-#pragma unroll
-        for (int i = 0; i < 16; i++) {
-          int32_t v = acc[i];
-          if (a.prelu) v = prelu(v, slope[i]);
-          const int y2 = requant(v, mult[i], a.shift, a.z_out);
-          int32_t m = (y1[i] - a.res_z1) * ma[i] + (y2 - a.res_z2) * mb[i];
-          m = prelu(m, rsl[i]);
-          q[i] = (int8_t)requant(m, 1, a.res_shift, a.res_z_out);
-        }
-      } else {
-#pragma unroll
-        for (int i = 0; i < 16; i++) {
-          int32_t v = acc[i];
-          if (a.prelu) v = prelu(v, slope[i]);
-          q[i] = (int8_t)requant(v, mult[i], a.shift, a.z_out);
-        }
-      }
-      __align__(16) int8_t qa[16];
-#pragma unroll
-      for (int i = 0; i < 16; i++) qa[i] = q[i];
-      *reinterpret_cast<uint4*>(a.out + r * a.out_stride + a.out_col + half * 16) =
-          *reinterpret_cast<const uint4*>(qa);
-      if (a.outb) {
-        __align__(16) __nv_bfloat16 b[16];
-#pragma unroll
-        for (int i = 0; i < 16; i++) b[i] = __int2bfloat16_rn((int)q[i] - a.outb_z);
-        uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(a.outb) +
-                                              r * a.outb_stride + half * 16);
-        dst[0] = reinterpret_cast<const uint4*>(b)[0];
-        dst[1] = reinterpret_cast<const uint4*>(b)[1];
-      }
-    }
-    tc::tc_fence_before();
-    __syncthreads();
   }
-  tc::cp_async_wait<0>();
   tc::tc_fence_before();
   __syncthreads();
-  if (w == 0) tc::tmem_dealloc(tbase, 256);
+  tc::tc_fence_after();
+  if (t == kThreads - 32) tc::mbar_wait(&w_bar, 0);  // the weights' copies have landed
+  if (w == 8) tc::tmem_dealloc(tbase, 512);
   if (t == 0 && abort_flag) atomicExch(&g_conv_error, 1);
 }
 
