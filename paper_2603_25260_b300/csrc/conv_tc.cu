@@ -16,9 +16,10 @@
 //  - 4 producer warps gather, for each (tile, offset), the 128 neighbour rows
 //    (pre-subtracted bf16 rows, 16-byte cp.async copies, zero-filled when the
 //    neighbour is absent: the exact zero padding of the sparse conv) into a
-//    ring of swizzled stages.  A thread that saw its copies of a stage land
-//    fences them to the async proxy and arrives on the stage's "full"
-//    barrier; it keeps kAhead stages of its own copies in flight.
+//    ring of swizzled stages.  Each thread's copies of a stage arrive on the
+//    stage's "full" barrier by themselves when they land
+//    (cp.async.mbarrier.arrive), so producers never wait on their own copies;
+//    the MMA thread fences the landed stage to the async proxy.
 //  - 1 MMA warp: one thread waits for a full stage and issues the M=128,
 //    N=32, K=16 MMAs into the offset's accumulator; tcgen05.commit releases
 //    the stage ("empty" barrier) when they are done, and after the tile's
@@ -57,8 +58,6 @@ struct ConvCfg {
   static constexpr int RB = CIN * 2;                 // bf16 row bytes
   static constexpr int SW = CIN == 64 ? 128 : 64;    // swizzle of the A stage
   static constexpr int kStages = CIN == 64 ? 5 : 12;
-  // stages of its own copies a producer keeps in flight
-  static constexpr int kAhead = kStages - 1 < 7 ? kStages - 1 : 7;
   static constexpr int kStageBytes = kTileM * RB;
   static constexpr int kPerGroup = 256 / CIN;        // offsets per fp32 accumulator
   static constexpr int kGroups = (27 + kPerGroup - 1) / kPerGroup;
@@ -69,7 +68,6 @@ struct ConvCfg {
   static constexpr int kNbrBytes = kTileM * 27 * 4;  // a tile's neighbour rows
   static constexpr size_t kSmem =
       1024 + kBBytes + (size_t)kStages * kStageBytes + 2 * kNbrBytes;
-  static_assert(kStages > kAhead, "a producer must be able to run kAhead stages ahead");
   static_assert(kGroups * 32 <= kBufCols, "accumulators of one tile exceed a buffer");
 };
 
@@ -236,22 +234,16 @@ k_conv333_tc(ConvTcArgs a) {
                                      ((present ? (int64_t)nb : 0) * a.x_stride) * 2 + c * 16;
           tc::cp_async16(sbase + tc::swz<Cfg::SW>(row * Cfg::RB + c * 16), src, present);
         }
-        tc::cp_async_commit();
-        if (u >= (uint32_t)Cfg::kAhead) {  // stage u - kAhead has landed: publish it
-          tc::cp_async_wait<Cfg::kAhead>();
-          tc::fence_async_smem();
-          mbar_arrive(&full_bar[(u - Cfg::kAhead) % S]);
-        }
+        // arrives on the stage's barrier once this thread's copies have landed
+        asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(
+                         tc::smem_u32(&full_bar[s]))
+                     : "memory");
       }
     }
     // a neighbour-row copy issued but not consumed (abort) lands before exit
     if (t == 0 && last_issued > last_used)
       tc::mbar_wait(&nbr_bar[last_issued & 1], (last_issued >> 1) & 1);
-    // publish the stages still in flight, oldest first
-    tc::cp_async_wait<0>();
-    tc::fence_async_smem();
-    for (uint32_t v = u > (uint32_t)Cfg::kAhead ? u - Cfg::kAhead : 0; v < u; v++)
-      mbar_arrive(&full_bar[v % S]);
+    tc::cp_async_wait<0>();  // every copy of this thread has landed
   } else if (w == 8) {
     // ---------------------------------------------------------------- MMA --
     if (lane == 0) {
@@ -270,6 +262,7 @@ k_conv333_tc(ConvTcArgs a) {
             ok = false;
             break;
           }
+          tc::fence_async_smem();  // the stage's landed copies, to the MMA's proxy
           tc::tc_fence_after();
           const uint32_t sa = tc::smem_u32(sA + (size_t)s * Cfg::kStageBytes);
           const int g = o / Cfg::kPerGroup;
