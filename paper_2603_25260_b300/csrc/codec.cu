@@ -416,19 +416,8 @@ int Codec::build_levels_device(int nf, const int32_t* const* xyz, const int64_t*
   // root; frames with a smaller depth carry their root up unchanged
   max_h_ = kHeights - 1;
   if (coarse) {
-    const uint64_t* src = key_[kHeights - 1];
-    const int64_t* dn = d_N_ + kHeights - 1;
-    uint64_t* pp[2] = {d_keys0_, sort_.alt};
-    for (int h = kHeights; h <= maxL; h++) {
-      uint64_t* dst = pp[h & 1];
-      launch_level_up(src, dn, P_, dst, coarse_codes(h), nullptr, nullptr, d_cN_ + h, scan_, st_);
-      LevelPtrs lp{};
-      lp.key[0] = dst;
-      lp.n[0] = d_cN_ + h;
-      launch_frame_offsets(lp, 1, nf, d_cfoff_ + (size_t)h * (nf + 1), st_);
-      src = dst;
-      dn = d_cN_ + h;
-    }
+    launch_coarse_up(key_[kHeights - 1], d_N_ + kHeights - 1, maxL, d_keys0_, sort_.alt,
+                     coarse_codes(kHeights), P_, d_cN_, nf, d_cfoff_, st_);
     max_h_ = std::max(maxL, kHeights - 1);
     if (max_h_ >= kHeights) {
       cudaMemcpyAsync(h_cN_ + kHeights, d_cN_ + kHeights, 8 * (max_h_ - kHeights + 1),
@@ -1148,20 +1137,15 @@ int Codec::expand_coarse_device(int nd) {
   uint64_t* pp[2] = {d_keys0_, sort_.alt};
   uint64_t* top_keys = top == kHeights - 1 ? key_[6] : pp[top & 1];
   cudaMemcpyAsync(top_keys, h_keys6_, 8 * (size_t)nd, cudaMemcpyHostToDevice, st_);
-  cudaMemcpyAsync(top == kHeights - 1 ? d_N_ + 6 : d_cN_ + top, h_cN_ + top, 8,
-                  cudaMemcpyHostToDevice, st_);
+  if (top == kHeights - 1)
+    cudaMemcpyAsync(d_N_ + 6, h_cN_ + top, 8, cudaMemcpyHostToDevice, st_);
   for (int h = top; h >= kHeights; h--)
     cudaMemcpyAsync(coarse_codes(h), hc + hoff[h], (size_t)hcnt[h], cudaMemcpyHostToDevice, st_);
   cudaMemcpyAsync(code_[6], hc + hoff[kHeights - 1], (size_t)hcnt[kHeights - 1],
                   cudaMemcpyHostToDevice, st_);
   pbeg(kFamLevels);
-  for (int h = top; h >= kHeights; h--) {
-    uint64_t* src = pp[h & 1];
-    const bool to6 = h - 1 == kHeights - 1;
-    uint64_t* dst = to6 ? key_[6] : pp[(h - 1) & 1];
-    launch_expand(src, coarse_codes(h), d_cN_ + h, P_, dst, nullptr, nullptr, P_,
-                  to6 ? d_N_ + 6 : d_cN_ + h - 1, scan_, d_err_, st_);
-  }
+  launch_coarse_down(top_keys, top, coarse_codes(kHeights), P_, hcnt.data(), P_, pp[0], pp[1],
+                     key_[6], d_N_ + 6, d_err_, st_);
   pend(kFamLevels, 21.0 * (double)tot, 0);
   return cuda_check("decode: coarse expansion");
 }
@@ -1185,13 +1169,20 @@ int Codec::decode_net_device(int nd, int64_t* n_out, const std::vector<int>& dev
     launch_expand(key_[h + 1], code_[h + 1], d_N_ + h + 1, P_, key_[h], par_[h], off_[h + 1], P_,
                   d_N_ + h, scan_, d_err_, st_);
     pend(kFamLevels, 13.0 * N_[h + 1] + 12.0 * 2.0 * N_[h + 1], 0);
-    LevelPtrs lp{};
-    lp.key[0] = key_[h];
-    lp.n[0] = d_N_ + h;
     int64_t* dfo = d_foff_ + (size_t)h * (nd + 1);
     int64_t* hfo = h_foff_ + (size_t)h * (nd + 1);
-    launch_frame_offsets(lp, 1, nd, dfo, st_);
-    cudaMemcpyAsync(hfo, dfo, 8 * (nd + 1), cudaMemcpyDeviceToHost, st_);
+    if (nd == 1) {  // one frame: its offsets are 0 and the level's size
+      hfo[0] = 0;
+      cudaMemsetAsync(dfo, 0, 8, st_);
+      cudaMemcpyAsync(dfo + 1, d_N_ + h, 8, cudaMemcpyDeviceToDevice, st_);
+      cudaMemcpyAsync(hfo + 1, d_N_ + h, 8, cudaMemcpyDeviceToHost, st_);
+    } else {
+      LevelPtrs lp{};
+      lp.key[0] = key_[h];
+      lp.n[0] = d_N_ + h;
+      launch_frame_offsets(lp, 1, nd, dfo, st_);
+      cudaMemcpyAsync(hfo, dfo, 8 * (nd + 1), cudaMemcpyDeviceToHost, st_);
+    }
     cudaMemcpyAsync(h_err_, d_err_, 4, cudaMemcpyDeviceToHost, st_);
     stats.phase_us[7] += now_us() - tl;
     tl = now_us();

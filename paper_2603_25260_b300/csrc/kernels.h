@@ -79,6 +79,14 @@ void launch_expand(const uint64_t* pkeys, const uint8_t* pcodes, const int64_t* 
                    int64_t cap_p, uint64_t* ckeys, uint32_t* cpar, uint32_t* poff, int64_t cap_c,
                    int64_t* d_nc, const ScanScratch& s, int* err, cudaStream_t st);
 
+// Coarse heights in one launch each (see octree.cu).
+void launch_coarse_up(const uint64_t* key6, const int64_t* d_n6, int top, uint64_t* k0,
+                      uint64_t* k1, uint8_t* codes, int64_t stride, int64_t* cN, int nf,
+                      int64_t* foff, cudaStream_t st);
+void launch_coarse_down(const uint64_t* roots, int top, const uint8_t* codes, int64_t stride,
+                        const int64_t* counts, int64_t cap, uint64_t* k0, uint64_t* k1,
+                        uint64_t* key6, int64_t* n6, int* err, cudaStream_t st);
+
 // ------------------------------------------------------ device range coding --
 // One substream: `rows` symbols starting at table / interval row `row`, its
 // bytes at `byte_off` of the byte buffer (`byte_len` = stream length when

@@ -187,6 +187,20 @@ void launch_down(const DLayer& W, const uint64_t* ckey, const uint32_t* poff, co
 //   M = max l_s; e_s = lut[M - l_s]; S = sum e_s (< 2^24);
 //   f_s = 1 + floor(e_s (2^16 - 255) / S)  (the product fits in 32 bits);
 //   the remainder 2^16 - sum f_s goes to the lowest s with l_s = M.
+// The 255 divisions by the row's S share one reciprocal: with
+// inv = floor((2^32 - 1) / S), q = umulhi(x, inv) is floor(x / S) or at most
+// two less (x < 2^32), and two conditional corrections make it exact.
+__device__ __forceinline__ uint32_t div_by(uint32_t x, uint32_t S, uint32_t inv) {
+  uint32_t q = __umulhi(x, inv);
+  uint32_t r = x - q * S;
+  if (r >= S) {
+    q++;
+    r -= S;
+  }
+  if (r >= S) q++;
+  return q;
+}
+
 __device__ __forceinline__ void softmax_freq(const int (&l)[8], const uint32_t* slut, int lane,
                                              uint32_t (&f)[8]) {
   int mx = -1000;
@@ -211,9 +225,10 @@ __device__ __forceinline__ void softmax_freq(const int (&l)[8], const uint32_t* 
     first = min(first, __shfl_xor_sync(0xffffffffu, first, o));
   }
   uint32_t tot = 0;
+  const uint32_t inv = 0xFFFFFFFFu / S;
 #pragma unroll
   for (int i = 0; i < 8; i++) {
-    f[i] = lane * 8 + i < kNsym ? 1u + (e[i] * (uint32_t)(kFreqTotal - kNsym)) / S : 0u;
+    f[i] = lane * 8 + i < kNsym ? 1u + div_by(e[i] * (uint32_t)(kFreqTotal - kNsym), S, inv) : 0u;
     tot += f[i];
   }
 #pragma unroll

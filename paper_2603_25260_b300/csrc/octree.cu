@@ -408,6 +408,141 @@ void launch_level_up(const uint64_t* ckeys, const int64_t* d_nc, int64_t cap_c, 
   run_scan(LevelOp{ckeys, pkeys, pcodes, poff, cpar, d_np}, d_nc, cap_c, s, st);
 }
 
+// --------------------------------------------------- coarse heights --
+// The coarse heights (above V_{b-1}) are small: one CTA walks all of them in
+// a single launch instead of a scan of three launches per height.
+constexpr int kCoThreads = 1024, kCoItems = 4, kCoChunk = kCoThreads * kCoItems;
+
+// Encoder: heights 7..top from the keys of height 6 by floor-halving with
+// duplicate removal; codes of height h into codes + (h - 7) * stride; keys
+// ping-pong through k0 / k1; counts into cN[h]; frame offsets of every height
+// into foff[h * (nf + 1) + f].
+__global__ void __launch_bounds__(kCoThreads)
+k_coarse_up(const uint64_t* __restrict__ key6, const int64_t* d_n6, int top, uint64_t* k0,
+            uint64_t* k1, uint8_t* codes, int64_t stride, int64_t* cN, int nf, int64_t* foff) {
+  __shared__ uint32_t sm[32];
+  const uint64_t* src = key6;
+  int64_t n = *d_n6;
+  for (int h = 7; h <= top; h++) {
+    uint64_t* dst = (h & 1) ? k1 : k0;
+    uint8_t* code = codes + (int64_t)(h - 7) * stride;
+    int64_t run = 0;
+    for (int64_t base = 0; base < n; base += kCoChunk) {
+      const int64_t first = base + (int64_t)threadIdx.x * kCoItems;
+      uint32_t flag[kCoItems], cnt = 0;
+#pragma unroll
+      for (int i = 0; i < kCoItems; i++) {
+        const int64_t j = first + i;
+        flag[i] = j < n && (j == 0 || parent_key(src[j]) != parent_key(src[j - 1]));
+        cnt += flag[i];
+      }
+      uint32_t tot;
+      int64_t at = run + block_excl_scan<kCoThreads>(cnt, &tot, sm);
+#pragma unroll
+      for (int i = 0; i < kCoItems; i++) {
+        if (!flag[i]) continue;
+        const int64_t j = first + i;
+        const uint64_t p = parent_key(src[j]);
+        uint32_t c = 0;
+        for (int64_t q = j; q < n && q < j + 8 && parent_key(src[q]) == p; q++)
+          c |= 1u << (src[q] & 7);
+        dst[at] = p;
+        code[at] = (uint8_t)c;
+        at++;
+      }
+      run += tot;
+    }
+    __syncthreads();  // the level is complete before it is searched and read
+    for (int f = threadIdx.x; f <= nf; f += kCoThreads) {
+      int64_t r = run;
+      if (f < nf) {
+        const uint64_t target = (uint64_t)f << kFrameShift;
+        int64_t lo = 0, hi = run;
+        while (lo < hi) {
+          const int64_t mid = (lo + hi) >> 1;
+          if (dst[mid] < target) lo = mid + 1;
+          else hi = mid;
+        }
+        r = lo;
+      }
+      foff[(int64_t)h * (nf + 1) + f] = r;
+    }
+    if (threadIdx.x == 0) cN[h] = run;
+    src = dst;
+    n = run;
+    __syncthreads();
+  }
+}
+
+void launch_coarse_up(const uint64_t* key6, const int64_t* d_n6, int top, uint64_t* k0,
+                      uint64_t* k1, uint8_t* codes, int64_t stride, int64_t* cN, int nf,
+                      int64_t* foff, cudaStream_t st) {
+  if (top < 7) return;
+  k_coarse_up<<<1, kCoThreads, 0, st>>>(key6, d_n6, top, k0, k1, codes, stride, cN, nf, foff);
+  count_launches(1);
+}
+
+// Decoder: from nf roots (frame f's root at the top height) down to height
+// 6 through the codes of heights top..7 (codes + (h - 7) * stride, counts
+// from the host in cnt[h]); children of every set bit in ascending order;
+// keys ping-pong through k0 / k1, height 6 into key6, its count into n6.
+// At most cap children per height are written (kErrCapacity beyond).
+struct CoarseCounts {
+  int64_t n[kMaxDepth + 1];
+};
+__global__ void __launch_bounds__(kCoThreads)
+k_coarse_down(const uint64_t* __restrict__ roots, int top, const uint8_t* __restrict__ codes,
+              int64_t stride, CoarseCounts cnt, int64_t cap, uint64_t* k0, uint64_t* k1,
+              uint64_t* key6, int64_t* n6, int* err) {
+  __shared__ uint32_t sm[32];
+  const uint64_t* src = roots;
+  for (int h = top; h >= 7; h--) {
+    const int64_t n = cnt.n[h];
+    const uint8_t* code = codes + (int64_t)(h - 7) * stride;
+    uint64_t* dst = h == 7 ? key6 : ((h - 1) & 1 ? k1 : k0);
+    int64_t run = 0;
+    for (int64_t base = 0; base < n; base += kCoChunk) {
+      const int64_t first = base + (int64_t)threadIdx.x * kCoItems;
+      uint32_t pc[kCoItems], c = 0;
+#pragma unroll
+      for (int i = 0; i < kCoItems; i++) {
+        pc[i] = first + i < n ? (uint32_t)code[first + i] : 0u;
+        c += __popc(pc[i]);
+      }
+      uint32_t tot;
+      int64_t at = run + block_excl_scan<kCoThreads>(c, &tot, sm);
+#pragma unroll
+      for (int i = 0; i < kCoItems; i++) {
+        if (!pc[i]) continue;
+        const uint64_t k = src[first + i];
+        for (int b = 0; b < 8; b++)
+          if (pc[i] >> b & 1) {
+            if (at >= cap) {
+              set_error(err, kErrCapacity);
+              break;
+            }
+            dst[at++] = child_key(k, (uint32_t)b);
+          }
+      }
+      run += tot;
+    }
+    if (h == 7 && threadIdx.x == 0) *n6 = run < cap ? run : cap;
+    src = dst;
+    __syncthreads();
+  }
+}
+
+void launch_coarse_down(const uint64_t* roots, int top, const uint8_t* codes, int64_t stride,
+                        const int64_t* counts, int64_t cap, uint64_t* k0, uint64_t* k1,
+                        uint64_t* key6, int64_t* n6, int* err, cudaStream_t st) {
+  if (top < 7) return;
+  CoarseCounts c{};
+  for (int h = 7; h <= top && h <= kMaxDepth; h++) c.n[h] = counts[h];
+  k_coarse_down<<<1, kCoThreads, 0, st>>>(roots, top, codes, stride, c, cap, k0, k1, key6, n6,
+                                          err);
+  count_launches(1);
+}
+
 // Children (parent << 3 | c) for every set bit c in ascending order: parents
 // are Morton-sorted, so the children are too (no reordering).
 // Codes decoded on the device may be corrupt: children past the capacity of
