@@ -124,6 +124,12 @@ double now_us() {
 // ---------------------------------------------------------------- create --
 Codec::~Codec() {
   delete pool_;
+  for (auto& row : gexec_)
+    for (auto& e : row)
+      if (e) cudaGraphExecDestroy(e);
+  for (auto e : gev_)
+    if (e) cudaEventDestroy(e);
+  if (gs_) cudaStreamDestroy(gs_);
   for (auto e : ev_) cudaEventDestroy(e);
   for (auto e : pev_) cudaEventDestroy(e);
   if (dmem_) cudaFree(dmem_);
@@ -289,6 +295,12 @@ int Codec::create(const lpc_config& cfg, const void* blob, size_t len) {
     *x.p = static_cast<uint8_t*>(hmem_) + ho;
     ho += (x.bytes + 255) / 256 * 256;
   }
+  if (cudaStreamCreateWithFlags(&gs_, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&gev_[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&gev_[1], cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    gs_ = nullptr;  // no graphs: direct launches
+  }
   ev_.resize(512);
   for (auto& e : ev_) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
   const int threads =
@@ -447,14 +459,15 @@ void Codec::fetch_frame_offsets(int nf) {
 // algorithmic work of that launch.  `h` is a height of the level arrays.
 void Codec::embed(const DEmb& E, int h, int8_t* out, int stride, int col) {
   pbeg(kFamEmbed);
-  launch_embed(E, code_[h], d_N_ + h, N_[h], out, stride, col, st_);
+  launch_embed(E, code_[h], d_N_ + h, gridn(h), out, stride, col, st_);
   pend(kFamEmbed, 33.0 * N_[h], 0);
 }
 
 // Pruning(Upsampling(x)) from height h to height h - 1
 void Codec::up(const DLayer& W, int h, const int8_t* x, int xs, int8_t* out, int os) {
   pbeg(kFamUp);
-  launch_up_prune(W, key_[h - 1], par_[h - 1], d_N_ + h - 1, N_[h - 1], x, xs, out, os, 0, st_);
+  launch_up_prune(W, key_[h - 1], par_[h - 1], d_N_ + h - 1, gridn(h - 1), x, xs, out, os, 0,
+                  st_);
   pend(kFamUp, (double)W.cin * N_[h] + 32.0 * N_[h - 1] + 8.0 * N_[h - 1],
        2.0 * N_[h - 1] * W.cin * 32);
 }
@@ -462,7 +475,7 @@ void Codec::up(const DLayer& W, int h, const int8_t* x, int xs, int8_t* out, int
 // int8 activations -> bf16 (q - z) rows, the tensor-core conv's input
 void Codec::to_bf16(const int8_t* x, int xs, int cols, int z, int h) {
   pbeg(kFamEmbed);
-  launch_to_bf16(x, xs, cols, z, d_N_ + h, N_[h], xb16_, st_);
+  launch_to_bf16(x, xs, cols, z, d_N_ + h, gridn(h), xb16_, st_);
   pend(kFamEmbed, 3.0 * cols * N_[h], 0);
 }
 
@@ -500,7 +513,7 @@ void Codec::conv(const DLayer& W, int h, const int32_t* nbr, int slot, const voi
     a.res_shift = res->shift;
   }
   pbeg(kFamConv);
-  launch_conv333_tc(a, W.cin, N_[h], st_);
+  launch_conv333_tc(a, W.cin, gridn(h), st_);
   // per neighbour pair: 2 Cin C ops and 2 Cin bytes gathered; per node: the
   // int8 output (+ the residual's y1 and the bf16 copy when present)
   pend(kFamConv,
@@ -510,8 +523,8 @@ void Codec::conv(const DLayer& W, int h, const int32_t* nbr, int slot, const voi
 
 void Codec::kmap(int h, int32_t* nbr, int slot) {
   pbeg(kFamHash);
-  const int64_t slots = hash_slots(N_[h]);
-  launch_kernel_map(key_[h], d_N_ + h, N_[h], d_L_, h, hash_, slots, nbr, d_err_, st_,
+  const int64_t slots = hash_slots(gridn(h));
+  launch_kernel_map(key_[h], d_N_ + h, gridn(h), d_L_, h, hash_, slots, nbr, d_err_, st_,
                     prof.mask ? d_pairs_ + slot : nullptr);
   pend(kFamHash, 12.0 * slots + 20.0 * N_[h] + 27.0 * N_[h] * (4 + 8), 0);
 }
@@ -550,7 +563,7 @@ void Codec::net_level(int j, int mode, uint16_t* cdf, uint32_t* enc, int8_t* log
   const int h = 5 - j;
   auto pred = [&](int jj, const int8_t* F, int stride) {
     pbeg(kFamPred);
-    launch_predictor(M_.P1[jj], M_.P2[jj], M_.d_lut, F, stride, d_N_ + h, N_[h], mode, code_[h],
+    launch_predictor(M_.P1[jj], M_.P2[jj], M_.d_lut, F, stride, d_N_ + h, gridn(h), mode, code_[h],
                      cdf, enc, logits, st_);
     const double n = (double)N_[h];
     pend(kFamPred,
@@ -581,7 +594,7 @@ void Codec::net_level(int j, int mode, uint16_t* cdf, uint32_t* enc, int8_t* log
       int8_t* dst = i == m - 1 ? xt_ : g_[i & 1];
       const int ds = i == m - 1 ? 64 : 32, dc = i == m - 1 ? 32 : 0;
       pbeg(kFamDown);
-      launch_down(M_.D[j][i], key_[hp - 1], off_[hp], d_N_ + hp, N_[hp], cur, 32, dst, ds, dc,
+      launch_down(M_.D[j][i], key_[hp - 1], off_[hp], d_N_ + hp, gridn(hp), cur, 32, dst, ds, dc,
                   st_);
       pend(kFamDown, 32.0 * (N_[hp - 1] + N_[hp]), 2.0 * N_[hp - 1] * 32 * 32);
       cur = dst;
@@ -603,6 +616,52 @@ void Codec::net_level(int j, int mode, uint16_t* cdf, uint32_t* enc, int8_t* log
     cur = 1 - cur;
   }
   pred(j, fo_, 32);
+}
+
+// A relative level's network as a CUDA graph: captured once per (mode, j)
+// on the codec's private stream with grids sized for the codec's capacity
+// (every kernel reads its level size on the device), then replayed after the
+// work already queued on the codec's stream.  The five levels of an encode
+// or a decode always run in the order j = 0..4, so each graph holds exactly
+// what that level issues in that order.  Falls back to direct launches while
+// profiling, or if a capture fails.
+void Codec::run_level(int j, int mode, uint16_t* cdf, uint32_t* enc) {
+  if (!gs_ || prof.mask) {
+    net_level(j, mode, cdf, enc, nullptr);
+    return;
+  }
+  cudaGraphExec_t& ex = gexec_[mode][j];
+  if (!ex && !gfail_[mode][j]) {
+    cudaStream_t saved = st_;
+    st_ = gs_;
+    cap_grid_ = true;
+    const int64_t c0 = launches_total();
+    cudaGraph_t g = nullptr;
+    bool ok = cudaStreamBeginCapture(gs_, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      net_level(j, mode, cdf, enc, nullptr);
+      ok = cudaStreamEndCapture(gs_, &g) == cudaSuccess && g;
+    }
+    const int64_t n = launches_total() - c0;
+    count_launches((int)-n);  // captured, not run
+    gkern_[mode][j] = (int)n;
+    if (ok && cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) ex = nullptr;
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    st_ = saved;
+    cap_grid_ = false;
+    if (!ex) gfail_[mode][j] = true;
+  }
+  if (!ex) {
+    net_level(j, mode, cdf, enc, nullptr);
+    return;
+  }
+  cudaEventRecord(gev_[0], st_);
+  cudaStreamWaitEvent(gs_, gev_[0], 0);
+  cudaGraphLaunch(ex, gs_);
+  cudaEventRecord(gev_[1], gs_);
+  cudaStreamWaitEvent(st_, gev_[1], 0);
+  count_launches(gkern_[mode][j]);
 }
 
 // --------------------------------------------------------------- encode --
@@ -668,7 +727,7 @@ int Codec::encode(int nf, const int32_t* const* xyz, const int64_t* n, const int
     // node; each level's intervals go to the host as soon as it is done
     for (int j = 0; j < 5; j++) {
       const int h = 5 - j;
-      net_level(j, kPredEnc, nullptr, d_enc_ + (size_t)j * P_, nullptr);
+      run_level(j, kPredEnc, nullptr, d_enc_ + (size_t)j * P_);
       if (!dev_rc_) {
         cudaMemcpyAsync(h_enc_ + (size_t)j * P_, d_enc_ + (size_t)j * P_, 4 * N_[h],
                         cudaMemcpyDeviceToHost, st_);
@@ -992,7 +1051,7 @@ int Codec::decode(int nf, const uint8_t* const* in, const size_t* lens, int32_t*
     launch_expand(key_[h + 1], code_[h + 1], d_N_ + h + 1, P_, key_[h], par_[h], off_[h + 1], P_,
                   d_N_ + h, scan_, d_err_, st_);
     pend(kFamLevels, 13.0 * N_[h + 1] + 12.0 * nh, 0);
-    net_level(j, kPredCdf, d_cdf_, nullptr, nullptr);
+    run_level(j, kPredCdf, d_cdf_, nullptr);
     if (int s = cuda_check("decode: launch")) return s;
     stats.phase_us[7] += now_us() - tl;
     tl = now_us();
@@ -1214,7 +1273,7 @@ int Codec::decode_net_device(int nd, int64_t* n_out, const std::vector<int>& dev
       }
     }
     cudaMemcpyAsync(dc, hc, sizeof(RcChunk) * (size_t)nck, cudaMemcpyHostToDevice, st_);
-    net_level(j, kPredCdf, d_cdf_, nullptr, nullptr);
+    run_level(j, kPredCdf, d_cdf_, nullptr);
     pbeg(kFamCoder);
     launch_rc_decode(dc, (int)nck, d_cdf_, d_in, code_[h], d_err_, st_);
     // table rows read, codes written

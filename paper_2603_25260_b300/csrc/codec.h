@@ -144,6 +144,16 @@ class Codec {
   void ensure_Ft();
   void ensure_nbr_t();
   void net_level(int j, int mode, uint16_t* cdf, uint32_t* enc, int8_t* logits);
+  void run_level(int j, int mode, uint16_t* cdf, uint32_t* enc);
+  // grid size for level height h: its size, or the capacity while a graph
+  // is captured (kernels read the real size on the device)
+  int64_t gridn(int h) const { return cap_grid_ ? P_ : N_[h]; }
+  bool cap_grid_ = false;
+  cudaStream_t gs_ = nullptr;
+  cudaEvent_t gev_[2] = {};
+  cudaGraphExec_t gexec_[3][5] = {};
+  int gkern_[3][5] = {};
+  bool gfail_[3][5] = {};
   int64_t hash_slots(int64_t n) const;
   // profiler: bracket a launch of family f; ops/bytes are algorithmic work
   // (pair_slot >= 0: ops/bytes are per neighbour pair, scaled at collection)

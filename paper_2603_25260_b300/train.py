@@ -20,6 +20,7 @@ import math
 
 import numpy as np
 import torch
+from torch.utils.checkpoint import checkpoint
 
 from . import lpc
 
@@ -273,8 +274,10 @@ ACT_SCALE = 1.0 / 32.0
 class QATModel(torch.nn.Module):
     """The float twin of the integer network with optional fake quantisation."""
 
-    def __init__(self, params: dict, qat: bool = False, bf16: bool = False):
+    def __init__(self, params: dict, qat: bool = False, bf16: bool = False,
+                 recompute: bool = False):
         super().__init__()
+        self.recompute = recompute
         self.names = sorted(params)
         self.p = torch.nn.ParameterDict(
             {k.replace(".", "__"): torch.nn.Parameter(torch.tensor(v, device="cuda"))
@@ -325,12 +328,16 @@ class QATModel(torch.nn.Module):
             return torch.nn.functional.cross_entropy(logits, fr.Y[d] - 1,
                                                      reduction="sum") / math.log(2.0)
 
-        Fb = upl("UP_0", b, emb("E_0", b - 1))
-        bits = ce(pred(0, Fb), b)
-        Sb = resblock(1, b, Fb)
-        Ft = upl("UP_1", t, torch.cat([Sb, emb("E_1", b)], 1))
-        bits = bits + ce(pred(1, Ft), t)
-        for j in range(2, 5):
+        def level0():
+            Fb = upl("UP_0", b, emb("E_0", b - 1))
+            return Fb, ce(pred(0, Fb), b)
+
+        def level1(Fb):
+            Sb = resblock(1, b, Fb)
+            Ft = upl("UP_1", t, torch.cat([Sb, emb("E_1", b)], 1))
+            return Ft, ce(pred(1, Ft), t)
+
+        def deep(j, Ft):
             m = j - 1
             d = t + m
             g = emb(f"G_{j}", d - 1)
@@ -343,7 +350,17 @@ class QATModel(torch.nn.Module):
             H = resblock(j, t, torch.cat([Ft, g], 1))
             for k in range(m):
                 H = upl(f"UP_{j}_{k}", t + k + 1, torch.cat([H, emb(f"E_{j}_{k}", t + k)], 1))
-            bits = bits + ce(pred(j, H), d)
+            return ce(pred(j, H), d)
+
+        # with recompute, each relative level keeps only its outputs; its
+        # activations are recomputed in the backward pass
+        run = ((lambda f, *a: checkpoint(f, *a, use_reentrant=False)) if self.recompute
+               else (lambda f, *a: f(*a)))
+        Fb, bits = run(level0)
+        Ft, b1 = run(level1, Fb)
+        bits = bits + b1
+        for j in range(2, 5):
+            bits = bits + run(lambda F, j=j: deep(j, F), Ft)
         return bits
 
     def grads(self) -> dict:

@@ -259,3 +259,21 @@ def test_training_steps_lower_the_rate(frames):
     losses = [G.train_step(m, opt, [gpu]) for _ in range(12)]
     assert all(np.isfinite(losses))
     assert losses[-1] < losses[0]
+
+
+def test_recompute_matches(frames):
+    """Recomputing each level's activations in the backward pass gives the
+    same loss and gradients (up to the order of atomic accumulations)."""
+    _, gpu, _ = frames
+    params = T.init_params(8)
+    from paper_2603_25260_b300 import train as G
+    out = []
+    for rc in (False, True):
+        m = G.QATModel(params, qat=True, bf16=0, recompute=rc)
+        bits = m.bits(gpu)
+        bits.backward()
+        torch.cuda.synchronize()
+        out.append((float(bits.detach()), m.grads()))
+    assert out[0][0] == pytest.approx(out[1][0], rel=1e-6)
+    name, err = _worst(out[1][1], out[0][1])
+    assert err < 1e-5, (name, err)
