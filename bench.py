@@ -440,6 +440,7 @@ def run_ours(args):
                 "step_ms": [round(t, 3) for t in e2e_ms],
                 "h2d_bytes_per_step": int(frame.nbytes), "d2h_bytes_per_step": int(12 * n_out)},
         "gpu_launches": int(gpu_launches),
+        "autotune": codec.tuning(),
         "roofline": roof,
         "families": {k: {"ms": round(v["ms"], 4), "launches": v["launches"]}
                      for k, v in fams.items()},

@@ -144,6 +144,13 @@ int codec_profile_read(codec_t* codec, int family, double* ms, int64_t* launches
                        double* ops);
 const char* codec_profile_name(int family);
 
+/* Conv autotuner state: variants[0], variants[1] = the chosen variant of the
+ * tensor-core 3x3x3 conv for 32- and 64-channel inputs (-1 while untuned),
+ * ms[c * 4 + v] = the timed milliseconds of variant v (bit 0: shallower stage
+ * ring, bit 1: contiguous tile order).  Tuning runs on the first encode or
+ * decode; every variant gives the same result. */
+int codec_tuning(codec_t* codec, int* variants, float* ms);
+
 /* Host timeline of the last encode / decode, microseconds (diagnostic):
  * [0] octree ready, [1] launches issued, [2] coding done, [3] encode total;
  * [4] coarse levels decoded, [5] network issue, [6] level decoding,

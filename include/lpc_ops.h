@@ -62,6 +62,13 @@ int lpc_conv333(const uint64_t* d_keys, int64_t N, int depth, const int8_t* d_x,
                 int z_in, const int8_t* h_W, const int32_t* h_bias, const int32_t* h_mult,
                 int shift, const int16_t* h_slope, int z_out, int cout, int8_t* d_out,
                 uint64_t stream);
+/* The same with an explicit kernel variant of the tensor-core conv (0..3:
+ * bit 0 shallower stage ring, bit 1 contiguous tile order; the codec's
+ * autotuner picks among them).  Every variant gives the same result. */
+int lpc_conv333_variant(const uint64_t* d_keys, int64_t N, int depth, const int8_t* d_x, int cin,
+                        int z_in, const int8_t* h_W, const int32_t* h_bias,
+                        const int32_t* h_mult, int shift, const int16_t* h_slope, int z_out,
+                        int cout, int8_t* d_out, int variant, uint64_t stream);
 
 /* Kernel-2 stride-2 sparse conv from the children (depth k+1, d_ckeys[Nc])
  * to the parents (depth k, d_pkeys[Np]), part of Downsampling (Eq. 4).

@@ -129,6 +129,8 @@ Codec::~Codec() {
       if (e) cudaGraphExecDestroy(e);
   for (auto e : gev_)
     if (e) cudaEventDestroy(e);
+  for (auto e : tev_)
+    if (e) cudaEventDestroy(e);
   if (gs_) cudaStreamDestroy(gs_);
   for (auto e : ev_) cudaEventDestroy(e);
   for (auto e : pev_) cudaEventDestroy(e);
@@ -295,6 +297,8 @@ int Codec::create(const lpc_config& cfg, const void* blob, size_t len) {
     *x.p = static_cast<uint8_t*>(hmem_) + ho;
     ho += (x.bytes + 255) / 256 * 256;
   }
+  if (cudaEventCreate(&tev_[0]) != cudaSuccess || cudaEventCreate(&tev_[1]) != cudaSuccess)
+    return fail(LPC_CUDA_ERROR, "event creation failed");
   if (cudaStreamCreateWithFlags(&gs_, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&gev_[0], cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&gev_[1], cudaEventDisableTiming) != cudaSuccess) {
@@ -512,13 +516,42 @@ void Codec::conv(const DLayer& W, int h, const int32_t* nbr, int slot, const voi
     a.res_z_out = res->z_out;
     a.res_shift = res->shift;
   }
+  const int ci = W.cin == 64;
+  if (conv_variant_[ci] < 0 && !cap_grid_) tune_conv(a, W.cin, h);
   pbeg(kFamConv);
-  launch_conv333_tc(a, W.cin, gridn(h), st_);
+  launch_conv333_tc(a, W.cin, gridn(h), st_, conv_variant_[ci] < 0 ? 0 : conv_variant_[ci]);
   // per neighbour pair: 2 Cin C ops and 2 Cin bytes gathered; per node: the
   // int8 output (+ the residual's y1 and the bf16 copy when present)
   pend(kFamConv,
        N_[h] * (32.0 + (res ? 32.0 : 0.0) + (outb ? 64.0 : 0.0)) + 27.0 * W.cin * 32 * 2, 0,
        slot, 2.0 * W.cin * 32, 2.0 * W.cin + 4.0);
+}
+
+// Autotuner: every variant of the conv runs on this launch's real input (all
+// give the same output, so the runs are harmless), warm once and timed once
+// with events; the fastest is kept for the codec's lifetime.
+void Codec::tune_conv(const ConvTcArgs& a, int cin, int h) {
+  const int ci = cin == 64;
+  float best = 1e30f;
+  int bv = 0;
+  for (int v = 0; v < kConvVariants; v++) {
+    launch_conv333_tc(a, cin, N_[h], st_, v);
+    cudaEventRecord(tev_[0], st_);
+    launch_conv333_tc(a, cin, N_[h], st_, v);
+    cudaEventRecord(tev_[1], st_);
+    float ms = 1e30f;
+    if (cudaEventSynchronize(tev_[1]) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, tev_[0], tev_[1]) != cudaSuccess) {
+      cudaGetLastError();
+      ms = 1e30f;
+    }
+    conv_tune_ms_[ci][v] = ms;
+    if (ms < best) {
+      best = ms;
+      bv = v;
+    }
+  }
+  conv_variant_[ci] = bv;
 }
 
 void Codec::kmap(int h, int32_t* nbr, int slot) {
@@ -626,7 +659,9 @@ void Codec::net_level(int j, int mode, uint16_t* cdf, uint32_t* enc, int8_t* log
 // what that level issues in that order.  Falls back to direct launches while
 // profiling, or if a capture fails.
 void Codec::run_level(int j, int mode, uint16_t* cdf, uint32_t* enc) {
-  if (!gs_ || prof.mask) {
+  // direct launches while profiling, and until the conv autotuner has picked
+  // its variants (it times real launches, which a capture cannot)
+  if (!gs_ || prof.mask || conv_variant_[0] < 0 || conv_variant_[1] < 0) {
     net_level(j, mode, cdf, enc, nullptr);
     return;
   }
@@ -1406,6 +1441,16 @@ const char* codec_profile_name(int family) {
 }
 
 int64_t lpc_kernel_launches(void) { return lpc::launches_total(); }
+
+int codec_tuning(codec_t* codec, int* variants, float* ms) {
+  if (!codec) return LPC_INVALID_ARG;
+  for (int c = 0; c < 2; c++) {
+    if (variants) variants[c] = codec->c.conv_variant_[c];
+    for (int v = 0; v < lpc::kConvVariants && ms; v++) ms[c * lpc::kConvVariants + v] =
+        codec->c.conv_tune_ms_[c][v];
+  }
+  return LPC_OK;
+}
 
 int codec_last_phases(codec_t* codec, double* us, int n) {
   if (!codec || !us) return LPC_INVALID_ARG;

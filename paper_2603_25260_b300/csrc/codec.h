@@ -154,6 +154,14 @@ class Codec {
   cudaGraphExec_t gexec_[3][5] = {};
   int gkern_[3][5] = {};
   bool gfail_[3][5] = {};
+  // conv autotuner: the fastest kernel variant per input width (32, 64),
+  // timed on the first direct launches of each width
+ public:
+  int conv_variant_[2] = {-1, -1};
+  float conv_tune_ms_[2][kConvVariants] = {};
+ private:
+  cudaEvent_t tev_[2] = {};
+  void tune_conv(const ConvTcArgs& a, int cin, int h);
   int64_t hash_slots(int64_t n) const;
   // profiler: bracket a launch of family f; ops/bytes are algorithmic work
   // (pair_slot >= 0: ops/bytes are per neighbour pair, scaled at collection)

@@ -53,11 +53,19 @@ constexpr int kProducers = 128;  // warps 0-3
 constexpr int kEpilogue = 128;   // warps 4-7
 constexpr int kThreads = kProducers + kEpilogue + 32;  // + the MMA warp (8)
 
+// Variants the autotuner chooses from: the stage-ring depth and the order in
+// which a CTA walks its tiles (strided over the grid, or one contiguous run
+// of Morton-adjacent tiles, whose neighbour rows overlap in L2).
 template <int CIN>
+constexpr int stages_of(int alt) {
+  return CIN == 64 ? (alt ? 4 : 5) : (alt ? 8 : 12);
+}
+
+template <int CIN, int S_ = stages_of<CIN>(0)>
 struct ConvCfg {
   static constexpr int RB = CIN * 2;                 // bf16 row bytes
   static constexpr int SW = CIN == 64 ? 128 : 64;    // swizzle of the A stage
-  static constexpr int kStages = CIN == 64 ? 5 : 12;
+  static constexpr int kStages = S_;
   static constexpr int kStageBytes = kTileM * RB;
   static constexpr int kPerGroup = 256 / CIN;        // offsets per fp32 accumulator
   static constexpr int kGroups = (27 + kPerGroup - 1) / kPerGroup;
@@ -129,10 +137,10 @@ __device__ __forceinline__ bool producer_sync_or(bool v) {
   return r != 0;
 }
 
-template <int CIN>
+template <int CIN, int S_, int ORDER>
 __global__ void __launch_bounds__(kThreads, 1)
 k_conv333_tc(ConvTcArgs a) {
-  using Cfg = ConvCfg<CIN>;
+  using Cfg = ConvCfg<CIN, S_>;
   constexpr int S = Cfg::kStages;
   extern __shared__ unsigned char smraw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>(
@@ -185,14 +193,25 @@ k_conv333_tc(ConvTcArgs a) {
   const uint32_t tbase = tslot;
   const int64_t n = *a.d_n;
   const int64_t ntiles = (n + kTileM - 1) / kTileM;
-  const int my_tiles =
-      blockIdx.x < ntiles ? (int)((ntiles - 1 - blockIdx.x) / gridDim.x + 1) : 0;
+  // this CTA's tiles: t_first + lt * t_step, lt < my_tiles
+  int64_t t_first, t_step;
+  int my_tiles;
+  if (ORDER == 0) {
+    t_first = blockIdx.x;
+    t_step = gridDim.x;
+    my_tiles = blockIdx.x < ntiles ? (int)((ntiles - 1 - blockIdx.x) / gridDim.x + 1) : 0;
+  } else {
+    const int64_t per = (ntiles + gridDim.x - 1) / gridDim.x;
+    t_first = (int64_t)blockIdx.x * per;
+    t_step = 1;
+    my_tiles = (int)std::max<int64_t>(0, std::min<int64_t>(per, ntiles - t_first));
+  }
+  auto tile_r0 = [&](int lt) { return (t_first + (int64_t)lt * t_step) * kTileM; };
 
   if (w < 4) {
     // ---------------------------------------------------------- producers --
     // a tile's neighbour rows: one bulk copy into buffer lt & 1, issued a
     // tile ahead (a partial last tile is read with plain loads instead)
-    auto tile_r0 = [&](int lt) { return (blockIdx.x + (int64_t)lt * gridDim.x) * kTileM; };
     int last_issued = -1, last_used = -1;  // thread 0's bookkeeping of nbr copies
     auto issue_nbr = [&](int lt) {
       if (t == 0 && lt < my_tiles && tile_r0(lt) + kTileM <= n) {
@@ -310,7 +329,7 @@ k_conv333_tc(ConvTcArgs a) {
       }
       tc::tc_fence_before();
       mbar_arrive(&acc_empty[b]);  // the buffer is free for tile lt + 2
-      const int64_t r = (blockIdx.x + (int64_t)lt * gridDim.x) * kTileM + e;
+      const int64_t r = tile_r0(lt) + e;
       if (r < n) {
         __align__(16) int8_t q[32];
         if (a.has_res) {
@@ -412,19 +431,36 @@ void launch_to_bf16(const int8_t* x, int x_stride, int cols, int z, const int64_
   count_launches(1);
 }
 
-void launch_conv333_tc(const ConvTcArgs& a, int cin, int64_t n_host, cudaStream_t st) {
+namespace {
+
+template <int CIN, int ALT, int ORDER>
+void launch_variant(const ConvTcArgs& a, int blocks, cudaStream_t st) {
+  constexpr int S = stages_of<CIN>(ALT);
+  constexpr size_t smem = ConvCfg<CIN, S>::kSmem;
+  cudaFuncSetAttribute(k_conv333_tc<CIN, S, ORDER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)smem);
+  k_conv333_tc<CIN, S, ORDER><<<blocks, kThreads, smem, st>>>(a);
+}
+
+template <int CIN>
+void launch_cin(const ConvTcArgs& a, int blocks, int variant, cudaStream_t st) {
+  switch (variant) {
+    case 1: launch_variant<CIN, 1, 0>(a, blocks, st); break;
+    case 2: launch_variant<CIN, 0, 1>(a, blocks, st); break;
+    case 3: launch_variant<CIN, 1, 1>(a, blocks, st); break;
+    default: launch_variant<CIN, 0, 0>(a, blocks, st); break;
+  }
+}
+
+}  // namespace
+
+void launch_conv333_tc(const ConvTcArgs& a, int cin, int64_t n_host, cudaStream_t st,
+                       int variant) {
   if (n_host <= 0) return;
   const int64_t ntiles = (n_host + kTileM - 1) / kTileM;
   const int blocks = (int)std::min<int64_t>(ntiles, 148);
-  if (cin == 64) {
-    cudaFuncSetAttribute(k_conv333_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)ConvCfg<64>::kSmem);
-    k_conv333_tc<64><<<blocks, kThreads, ConvCfg<64>::kSmem, st>>>(a);
-  } else {
-    cudaFuncSetAttribute(k_conv333_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)ConvCfg<32>::kSmem);
-    k_conv333_tc<32><<<blocks, kThreads, ConvCfg<32>::kSmem, st>>>(a);
-  }
+  if (cin == 64) launch_cin<64>(a, blocks, variant, st);
+  else launch_cin<32>(a, blocks, variant, st);
   count_launches(1);
 }
 

@@ -196,7 +196,12 @@ struct ConvTcArgs {
 };
 size_t conv_tc_weight_bytes(int cin);
 void pack_conv_tc_weights(const int8_t* W, int cin, uint16_t* img);
-void launch_conv333_tc(const ConvTcArgs& a, int cin, int64_t n_host, cudaStream_t st);
+// variant in [0, kConvVariants): stage-ring depth (bit 0) and tile order
+// (bit 1), chosen by the codec's autotuner; every variant gives the same
+// result.
+constexpr int kConvVariants = 4;
+void launch_conv333_tc(const ConvTcArgs& a, int cin, int64_t n_host, cudaStream_t st,
+                       int variant = 0);
 // int8 rows (stride x_stride) -> bf16 (q - z) rows of `cols` elements.
 void launch_to_bf16(const int8_t* x, int x_stride, int cols, int z, const int64_t* d_n,
                     int64_t n_host, void* out, cudaStream_t st);

@@ -173,11 +173,13 @@ int lpc_kernel_map(const uint64_t* d_keys, int64_t N, int depth, int32_t* d_nbr,
   return finish(st, d_err);
 }
 
-int lpc_conv333(const uint64_t* d_keys, int64_t N, int depth, const int8_t* d_x, int cin,
-                int z_in, const int8_t* h_W, const int32_t* h_bias, const int32_t* h_mult,
-                int shift, const int16_t* h_slope, int z_out, int cout, int8_t* d_out,
-                uint64_t stream) {
-  if (N < 0 || bad_layer(cin, cout, shift) || !h_W || !h_bias || !h_mult) return LPC_INVALID_ARG;
+int lpc_conv333_variant(const uint64_t* d_keys, int64_t N, int depth, const int8_t* d_x, int cin,
+                        int z_in, const int8_t* h_W, const int32_t* h_bias,
+                        const int32_t* h_mult, int shift, const int16_t* h_slope, int z_out,
+                        int cout, int8_t* d_out, int variant, uint64_t stream) {
+  if (N < 0 || bad_layer(cin, cout, shift) || !h_W || !h_bias || !h_mult || variant < 0 ||
+      variant >= kConvVariants)
+    return LPC_INVALID_ARG;
   if (N == 0) return LPC_OK;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   Tmp t;
@@ -208,10 +210,18 @@ int lpc_conv333(const uint64_t* d_keys, int64_t N, int depth, const int8_t* d_x,
   a.x_stride = cin;
   a.out = d_out;
   a.out_stride = cout;
-  launch_conv333_tc(a, cin, N, st);
+  launch_conv333_tc(a, cin, N, st, variant);
   s = finish(st, nullptr);
   if (conv_tc_error(true)) return LPC_TIMEOUT;
   return s;
+}
+
+int lpc_conv333(const uint64_t* d_keys, int64_t N, int depth, const int8_t* d_x, int cin,
+                int z_in, const int8_t* h_W, const int32_t* h_bias, const int32_t* h_mult,
+                int shift, const int16_t* h_slope, int z_out, int cout, int8_t* d_out,
+                uint64_t stream) {
+  return lpc_conv333_variant(d_keys, N, depth, d_x, cin, z_in, h_W, h_bias, h_mult, shift,
+                             h_slope, z_out, cout, d_out, 0, stream);
 }
 
 int lpc_down_s2(const uint64_t* d_ckeys, int64_t Nc, const uint64_t* d_pkeys, int64_t Np,

@@ -49,6 +49,7 @@ def lib():
         sig = {
             "codec_create": (I32, [C.POINTER(Config), P, SZ, C.POINTER(P)]),
             "codec_destroy": (None, [P]),
+            "codec_tuning": (I32, [P, P, P]),
             "codec_last_error": (C.c_char_p, [P]),
             "encode_frame": (I32, [P, P, I64, P, SZ, C.POINTER(SZ)]),
             "decode_frame": (I32, [P, P, SZ, P, I64, C.POINTER(I64)]),
@@ -66,6 +67,8 @@ def lib():
             "lpc_kernel_map_noalloc": (I32, [P, I64, I32, P, C.c_uint64]),
             "lpc_conv333": (I32, [P, I64, I32, P, I32, I32, P, P, P, I32, P, I32, I32, P,
                                   C.c_uint64]),
+            "lpc_conv333_variant": (I32, [P, I64, I32, P, I32, I32, P, P, P, I32, P, I32, I32, P,
+                                  I32, C.c_uint64]),
             "lpc_down_s2": (I32, [P, I64, P, I64, P, I32, I32, P, P, P, I32, P, I32, I32, P,
                                   C.c_uint64]),
             "lpc_up_prune": (I32, [P, P, I64, P, I64, P, I32, I32, P, P, P, I32, P, I32, I32, P,
@@ -215,6 +218,16 @@ class Codec:
             out[name] = {"ms": ms.value, "launches": n.value, "bytes": b.value, "ops": o.value}
         return out
 
+    def tuning(self) -> dict:
+        """The conv autotuner's choice per input width and the timed variants
+        (milliseconds; bit 0 of a variant = shallower stage ring, bit 1 =
+        contiguous tile order)."""
+        v = (C.c_int * 2)()
+        ms = (C.c_float * 8)()
+        self._check(self._lib.codec_tuning(self._h, v, ms))
+        return {"conv32": v[0], "conv64": v[1],
+                "ms32": [round(x, 4) for x in ms[:4]], "ms64": [round(x, 4) for x in ms[4:]]}
+
     def last_phases(self) -> list[float]:
         """Host timeline of the last encode / decode in microseconds (see lpc.h)."""
         us = (C.c_double * 16)()
@@ -295,7 +308,7 @@ def kernel_map_noalloc(keys: torch.Tensor, depth: int, out: torch.Tensor) -> tor
     return out[:N]
 
 
-def conv333(keys, depth, x, z_in, W, bias, mult, shift, slope, z_out):
+def conv333(keys, depth, x, z_in, W, bias, mult, shift, slope, z_out, variant=None):
     keys, x = _dev(keys, torch.int64), _dev(x, torch.int8)
     N, cin = x.shape
     W = _np(W, np.int8)
@@ -303,9 +316,15 @@ def conv333(keys, depth, x, z_in, W, bias, mult, shift, slope, z_out):
     out = torch.empty((max(N, 1), cout), dtype=torch.int8, device="cuda")
     b, m = _np(bias, np.int32), _np(mult, np.int32)
     s = None if slope is None else _np(slope, np.int16)
-    _ops_check(lib().lpc_conv333(keys.data_ptr(), N, depth, x.data_ptr(), cin, z_in, _hp(W),
-                                 _hp(b), _hp(m), shift, _hp(s), z_out, cout, out.data_ptr(),
-                                 _stream()), "lpc_conv333")
+    if variant is None:
+        _ops_check(lib().lpc_conv333(keys.data_ptr(), N, depth, x.data_ptr(), cin, z_in, _hp(W),
+                                     _hp(b), _hp(m), shift, _hp(s), z_out, cout, out.data_ptr(),
+                                     _stream()), "lpc_conv333")
+    else:
+        _ops_check(lib().lpc_conv333_variant(keys.data_ptr(), N, depth, x.data_ptr(), cin, z_in,
+                                             _hp(W), _hp(b), _hp(m), shift, _hp(s), z_out, cout,
+                                             out.data_ptr(), variant, _stream()),
+                   "lpc_conv333_variant")
     return out[:N]
 
 

@@ -124,6 +124,34 @@ def test_conv333(lpc, n, depth, cin, seed):
         assert np.array_equal(got, want)
 
 
+@pytest.mark.parametrize("variant", [1, 2, 3])
+@pytest.mark.parametrize("cin", [32, 64])
+def test_conv333_variants(lpc, cin, variant):
+    """Every kernel variant the autotuner may pick (stage-ring depth, tile
+    order) matches the oracle, over several tiles and a ragged tail."""
+    n, depth, seed = 40000, 9, 21
+    xyz = synth.random_cloud(n, depth, seed)
+    keys = O.leaf_keys(xyz, depth)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    x = rng.integers(-128, 128, size=(len(keys), cin)).astype(np.int8)
+    W, bias, mult, slope = _params(27, cin, 32, seed)
+    want = O.conv333(keys, depth, x, 7, W, bias, mult, 24, slope, -5)
+    got = lpc.conv333(_cuda(keys.view(np.int64)), depth, _cuda(x), 7, W, bias, mult, 24, slope,
+                      -5, variant=variant).cpu().numpy()
+    assert np.array_equal(got, want)
+
+
+def test_codec_autotuner_picks_variants(lpc, blob):
+    xyz = synth.random_cloud(20000, 14, 4)
+    cod = _codec(lpc, blob, 14, 20000)
+    data = cod.encode(_cuda(xyz))
+    t = cod.tuning()
+    assert 0 <= t["conv32"] < 4 and 0 <= t["conv64"] < 4
+    assert all(0 < m < 1e3 for m in t["ms32"] + t["ms64"])
+    assert data == O.encode(blob, xyz, 14)  # and the next call runs the captured graphs
+    assert cod.encode(_cuda(xyz)) == data
+
+
 def test_conv333_extreme_accumulator(lpc):
     """Worst-case magnitudes: every input at -128 with z = 127 and every
     weight at +-127 over 27 present neighbours (|acc| near 27*64*255*127)."""
