@@ -13,7 +13,7 @@
 //
 // Warp-specialised and persistent: one CTA per SM walks its tiles of 128
 // output nodes (Morton order) and, for each, all 27 offsets.
-//  - 4 producer warps gather, for each (tile, offset), the 128 neighbour rows
+//  - 8 producer warps gather, for each (tile, offset), the 128 neighbour rows
 //    (pre-subtracted bf16 rows, 16-byte cp.async copies, zero-filled when the
 //    neighbour is absent: the exact zero padding of the sparse conv) into a
 //    ring of swizzled stages.  Each thread's copies of a stage arrive on the
@@ -49,9 +49,11 @@ namespace lpc {
 namespace {
 
 constexpr int kTileM = 128;
-constexpr int kProducers = 128;  // warps 0-3
-constexpr int kEpilogue = 128;   // warps 4-7
-constexpr int kThreads = kProducers + kEpilogue + 32;  // + the MMA warp (8)
+constexpr int kProdWarps = 8;                   // warps 0 .. kProdWarps-1
+constexpr int kProducers = 32 * kProdWarps;
+constexpr int kEpilogue = 128;                  // the next 4 warps (TMEM quadrants w % 4)
+constexpr int kMmaWarp = kProdWarps + 4;        // then the MMA warp
+constexpr int kThreads = kProducers + kEpilogue + 32;
 
 // Variants the autotuner chooses from: the stage-ring depth and the order in
 // which a CTA walks its tiles (strided over the grid, or one contiguous run
@@ -156,7 +158,7 @@ k_conv333_tc(ConvTcArgs a) {
   volatile int* abort = &abort_flag;
 
   const int t = threadIdx.x, w = t >> 5, lane = t & 31;
-  if (w == 8) tc::tmem_alloc(&tslot, 512);
+  if (w == kMmaWarp) tc::tmem_alloc(&tslot, 512);
   if (t == 0) {
     for (int s = 0; s < S; s++) {
       tc::mbar_init(&full_bar[s], kProducers);
@@ -208,7 +210,7 @@ k_conv333_tc(ConvTcArgs a) {
   }
   auto tile_r0 = [&](int lt) { return (t_first + (int64_t)lt * t_step) * kTileM; };
 
-  if (w < 4) {
+  if (w < kProdWarps) {
     // ---------------------------------------------------------- producers --
     // a tile's neighbour rows: one bulk copy into buffer lt & 1, issued a
     // tile ahead (a partial last tile is read with plain loads instead)
@@ -263,7 +265,7 @@ k_conv333_tc(ConvTcArgs a) {
     if (t == 0 && last_issued > last_used)
       tc::mbar_wait(&nbr_bar[last_issued & 1], (last_issued >> 1) & 1);
     tc::cp_async_wait<0>();  // every copy of this thread has landed
-  } else if (w == 8) {
+  } else if (w == kMmaWarp) {
     // ---------------------------------------------------------------- MMA --
     if (lane == 0) {
       constexpr uint32_t idesc = tc::idesc_bf16(kTileM, 32);
@@ -373,7 +375,7 @@ k_conv333_tc(ConvTcArgs a) {
   __syncthreads();
   tc::tc_fence_after();
   if (t == kThreads - 32) tc::mbar_wait(&w_bar, 0);  // the weights' copies have landed
-  if (w == 8) tc::tmem_dealloc(tbase, 512);
+  if (w == kMmaWarp) tc::tmem_dealloc(tbase, 512);
   if (t == 0 && abort_flag) atomicExch(&g_conv_error, 1);
 }
 
