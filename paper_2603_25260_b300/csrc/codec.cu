@@ -29,6 +29,7 @@ Pool::~Pool() {
   {
     std::lock_guard<std::mutex> g(mu_);
     stop_ = true;
+    spin_.store(false, std::memory_order_relaxed);
   }
   cv_.notify_all();
   for (auto& t : th_) t.join();
@@ -40,6 +41,7 @@ bool Pool::run_one(std::unique_lock<std::mutex>& lk) {
   const int g = q_[head_].first;
   std::function<void()> f = std::move(q_[head_].second);
   head_++;
+  queued_.fetch_sub(1, std::memory_order_relaxed);
   running_++;
   lk.unlock();
   f();
@@ -57,10 +59,29 @@ bool Pool::run_one(std::unique_lock<std::mutex>& lk) {
 void Pool::loop() {
   std::unique_lock<std::mutex> lk(mu_);
   for (;;) {
-    cv_.wait(lk, [&] { return stop_ || head_ < q_.size(); });
     if (stop_) return;
-    run_one(lk);
+    if (run_one(lk)) continue;
+    if (spin_.load(std::memory_order_relaxed)) {
+      lk.unlock();
+      for (int k = 1; spin_.load(std::memory_order_relaxed) &&
+                      queued_.load(std::memory_order_relaxed) == 0;
+           k++)
+        if (k % 64 == 0) std::this_thread::yield();
+      lk.lock();
+      continue;
+    }
+    cv_.wait(lk, [&] {
+      return stop_ || head_ < q_.size() || spin_.load(std::memory_order_relaxed);
+    });
   }
+}
+
+void Pool::set_spin(bool on) {
+  {
+    std::lock_guard<std::mutex> g(mu_);
+    spin_.store(on, std::memory_order_relaxed);
+  }
+  if (on) cv_.notify_all();
 }
 
 void Pool::submit(int group, std::function<void()> task) {
@@ -72,6 +93,7 @@ void Pool::submit(int group, std::function<void()> task) {
     std::lock_guard<std::mutex> g(mu_);
     q_.emplace_back(group, std::move(task));
     pending_[group]++;
+    queued_.fetch_add(1, std::memory_order_relaxed);
   }
   cv_.notify_one();
 }
@@ -706,6 +728,7 @@ int Codec::encode(int nf, const int32_t* const* xyz, const int64_t* n, const int
   if (nf < 1 || nf > F_ || !xyz || !n || !Ls || !out || !caps || !lens)
     return fail(LPC_INVALID_ARG, "encode: bad arguments");
   const double t0 = now_us();
+  SpinScope spin(pool_, true);
   stats = Stats{};
   // frames with points go to the device batch, empty frames get a flag stream
   std::vector<int> dev;  // device frame index -> caller index
@@ -950,6 +973,7 @@ int Codec::decode(int nf, const uint8_t* const* in, const size_t* lens, int32_t*
   if (nf < 1 || nf > F_ || !in || !lens || !out || !caps || !n_out)
     return fail(LPC_INVALID_ARG, "decode: bad arguments");
   const double t0 = now_us();
+  SpinScope spin(pool_, true);
   stats = Stats{};
   std::vector<int> dev;
   std::vector<Frame> all(nf);

@@ -188,6 +188,44 @@ class Codec:
         self._check(self._lib.encode_batch(self._h, nf, ptrs, ns, ls, outs, capa, lens))
         return [bufs[i][:lens[i]].tobytes() for i in range(nf)]
 
+    @staticmethod
+    def batch_caps(frames: list[torch.Tensor]) -> list[int]:
+        """Output bytes reserved per frame by encode_batch_into."""
+        return [1024 + 64 * f.shape[0] for f in frames]
+
+    def encode_batch_into(self, frames: list[torch.Tensor], Ls: list[int],
+                          out: np.ndarray) -> list[tuple[int, int]]:
+        """Encode a batch into one caller-owned uint8 buffer (reusable across
+        calls, at least sum(batch_caps(frames)) bytes); frame i goes to its
+        own slice.  Returns (offset, length) per frame."""
+        nf = len(frames)
+        caps = self.batch_caps(frames)
+        offs = np.concatenate([[0], np.cumsum(caps)[:-1]]).astype(np.int64)
+        assert out.dtype == np.uint8 and out.size >= sum(caps)
+        base = out.ctypes.data
+        ptrs = (C.c_void_p * nf)(*[f.data_ptr() if f.shape[0] else 0 for f in frames])
+        ns = (C.c_int64 * nf)(*[f.shape[0] for f in frames])
+        ls = (C.c_int * nf)(*Ls)
+        outs = (C.c_void_p * nf)(*[base + int(o) for o in offs])
+        capa = (C.c_size_t * nf)(*caps)
+        lens = (C.c_size_t * nf)()
+        self._check(self._lib.encode_batch(self._h, nf, ptrs, ns, ls, outs, capa, lens))
+        return [(int(offs[i]), int(lens[i])) for i in range(nf)]
+
+    def decode_batch_from(self, buf: np.ndarray, spans: list[tuple[int, int]],
+                          outs_t: list[torch.Tensor]) -> list[torch.Tensor]:
+        """Decode streams lying in one host buffer (as encode_batch_into left
+        them) into caller-owned device tensors [cap_i, 3] int32."""
+        nf = len(spans)
+        base = buf.ctypes.data
+        ins = (C.c_void_p * nf)(*[base + o for o, _ in spans])
+        lens = (C.c_size_t * nf)(*[n for _, n in spans])
+        outs = (C.c_void_p * nf)(*[t.data_ptr() for t in outs_t])
+        capa = (C.c_int64 * nf)(*[t.shape[0] for t in outs_t])
+        nout = (C.c_int64 * nf)()
+        self._check(self._lib.decode_batch(self._h, nf, ins, lens, outs, capa, nout))
+        return [outs_t[i][:nout[i]] for i in range(nf)]
+
     def decode_batch(self, streams: list[bytes], caps: list[int]) -> list[torch.Tensor]:
         nf = len(streams)
         bufs = [np.frombuffer(s, dtype=np.uint8) for s in streams]

@@ -367,3 +367,21 @@ def test_corrupt_payload(lpc, blob, host_coding):
             outcomes.add(e.status)
     assert outcomes
     assert np.array_equal(cod.decode(data).cpu().numpy(), want)
+
+
+def test_batch_into_reusable_buffer(lpc, blob):
+    """The buffer-reusing batch calls give the same streams and voxels."""
+    specs = [(3000, 10, 11), (0, 9, 12), (8000, 14, 13)]
+    frames = [synth.random_cloud(n, L, s) for n, L, s in specs]
+    Ls = [L for _, L, _ in specs]
+    cod = lpc.Codec(blob, 14, 8000, max_frames=3)
+    xs = [_cuda(f) for f in frames]
+    want = cod.encode_batch(xs, Ls)
+    buf = np.zeros(sum(lpc.Codec.batch_caps(xs)), dtype=np.uint8)
+    outs = [torch.empty((max(f.shape[0], 1), 3), dtype=torch.int32, device="cuda") for f in frames]
+    for _ in range(2):
+        spans = cod.encode_batch_into(xs, Ls, buf)
+        assert [bytes(buf[o:o + n]) for o, n in spans] == want
+        decs = cod.decode_batch_from(buf, spans, outs)
+        for f, L, d in zip(frames, Ls, decs):
+            assert np.array_equal(O.leaf_keys(d.cpu().numpy(), L), O.leaf_keys(f, L))
