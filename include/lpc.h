@@ -144,12 +144,17 @@ int codec_profile_read(codec_t* codec, int family, double* ms, int64_t* launches
                        double* ops);
 const char* codec_profile_name(int family);
 
-/* Conv autotuner state: variants[0], variants[1] = the chosen variant of the
- * tensor-core 3x3x3 conv for 32- and 64-channel inputs (-1 while untuned),
- * ms[c * 4 + v] = the timed milliseconds of variant v (bit 0: shallower stage
- * ring, bit 1: contiguous tile order).  Tuning runs on the first encode or
- * decode; every variant gives the same result. */
+/* Autotuner state (variants[3], ms[10]): variants[0], variants[1] = the
+ * chosen variant of the tensor-core 3x3x3 conv for 32- and 64-channel inputs
+ * (-1 while untuned), ms[c * 4 + v] = the timed milliseconds of variant v
+ * (bit 0: shallower stage ring, bit 1: contiguous tile order); variants[2] =
+ * the predictor's (0 CUDA cores, 1 tensor cores), ms[8 + v] its timings.
+ * Tuning runs on the first encode or decode; every variant gives the same
+ * result. */
 int codec_tuning(codec_t* codec, int* variants, float* ms);
+/* Fix the variants (conv 32, conv 64, predictor) instead of tuning them;
+ * -1 leaves one to the tuner.  LPC_INVALID_ARG for an unknown variant. */
+int codec_set_tuning(codec_t* codec, const int* variants);
 
 /* Host timeline of the last encode / decode, microseconds (diagnostic):
  * [0] octree ready, [1] launches issued, [2] coding done, [3] encode total;

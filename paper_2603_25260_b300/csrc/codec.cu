@@ -406,6 +406,7 @@ void Codec::begin_batch() {
 
 int Codec::check_device_error() {
   if (conv_tc_error(true)) return fail(LPC_TIMEOUT, "tensor-core conv gave up on a bounded wait");
+  if (pred_tc_error(true)) return fail(LPC_TIMEOUT, "tensor-core predictor gave up on a bounded wait");
   const int e = *h_err_;
   if (e == 0) return LPC_OK;
   if (e == kErrCoord) return fail(LPC_INVALID_ARG, "coordinate outside [0, 2^L)");
@@ -617,9 +618,34 @@ void Codec::ensure_nbr_t() {
 void Codec::net_level(int j, int mode, uint16_t* cdf, uint32_t* enc, int8_t* logits) {
   const int h = 5 - j;
   auto pred = [&](int jj, const int8_t* F, int stride) {
+    auto go = [&](int v) {
+      launch_predictor(M_.P1[jj], M_.P2[jj], M_.d_lut, F, stride, d_N_ + h, gridn(h), mode,
+                       code_[h], cdf, enc, logits, st_, v);
+    };
+    if (pred_variant_ < 0 && !cap_grid_) {
+      // autotuner: both variants on this launch's input (same output), the
+      // faster kept for the codec
+      float best = 1e30f;
+      for (int v = 0; v < kPredVariants; v++) {
+        go(v);
+        cudaEventRecord(tev_[0], st_);
+        go(v);
+        cudaEventRecord(tev_[1], st_);
+        float ms = 1e30f;
+        if (cudaEventSynchronize(tev_[1]) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, tev_[0], tev_[1]) != cudaSuccess) {
+          cudaGetLastError();
+          ms = 1e30f;
+        }
+        pred_tune_ms_[v] = ms;
+        if (ms < best) {
+          best = ms;
+          pred_variant_ = v;
+        }
+      }
+    }
     pbeg(kFamPred);
-    launch_predictor(M_.P1[jj], M_.P2[jj], M_.d_lut, F, stride, d_N_ + h, gridn(h), mode, code_[h],
-                     cdf, enc, logits, st_);
+    go(pred_variant_ < 0 ? 0 : pred_variant_);
     const double n = (double)N_[h];
     pend(kFamPred,
          n * 32 + (mode == kPredCdf ? 512.0 * n : mode == kPredEnc ? 5.0 * n : 255.0 * n),
@@ -683,7 +709,7 @@ void Codec::net_level(int j, int mode, uint16_t* cdf, uint32_t* enc, int8_t* log
 void Codec::run_level(int j, int mode, uint16_t* cdf, uint32_t* enc) {
   // direct launches while profiling, and until the conv autotuner has picked
   // its variants (it times real launches, which a capture cannot)
-  if (!gs_ || prof.mask || conv_variant_[0] < 0 || conv_variant_[1] < 0) {
+  if (!gs_ || prof.mask || conv_variant_[0] < 0 || conv_variant_[1] < 0 || pred_variant_ < 0) {
     net_level(j, mode, cdf, enc, nullptr);
     return;
   }
@@ -1466,6 +1492,15 @@ const char* codec_profile_name(int family) {
 
 int64_t lpc_kernel_launches(void) { return lpc::launches_total(); }
 
+int codec_set_tuning(codec_t* codec, const int* variants) {
+  if (!codec || !variants) return LPC_INVALID_ARG;
+  for (int c = 0; c < 2; c++)
+    if (variants[c] < -1 || variants[c] >= lpc::kConvVariants) return LPC_INVALID_ARG;
+  if (variants[2] < -1 || variants[2] >= lpc::kPredVariants) return LPC_INVALID_ARG;
+  codec->c.set_tuning(variants);
+  return LPC_OK;
+}
+
 int codec_tuning(codec_t* codec, int* variants, float* ms) {
   if (!codec) return LPC_INVALID_ARG;
   for (int c = 0; c < 2; c++) {
@@ -1473,6 +1508,9 @@ int codec_tuning(codec_t* codec, int* variants, float* ms) {
     for (int v = 0; v < lpc::kConvVariants && ms; v++) ms[c * lpc::kConvVariants + v] =
         codec->c.conv_tune_ms_[c][v];
   }
+  if (variants) variants[2] = codec->c.pred_variant_;
+  for (int v = 0; v < lpc::kPredVariants && ms; v++)
+    ms[2 * lpc::kConvVariants + v] = codec->c.pred_tune_ms_[v];
   return LPC_OK;
 }
 

@@ -177,6 +177,20 @@ class Codec {
  public:
   int conv_variant_[2] = {-1, -1};
   float conv_tune_ms_[2][kConvVariants] = {};
+  int pred_variant_ = -1;  // predictor: CUDA cores or tensor cores
+  // fix the variants (captured graphs are dropped: they hold the old ones)
+  void set_tuning(const int* v) {
+    conv_variant_[0] = v[0];
+    conv_variant_[1] = v[1];
+    pred_variant_ = v[2];
+    for (auto& row : gexec_)
+      for (auto& e : row)
+        if (e) {
+          cudaGraphExecDestroy(e);
+          e = nullptr;
+        }
+  }
+  float pred_tune_ms_[kPredVariants] = {};
  private:
   cudaEvent_t tev_[2] = {};
   void tune_conv(const ConvTcArgs& a, int cin, int h);

@@ -132,7 +132,8 @@ struct DLayer {
   const int32_t* bias;   // [P][cout], P = S if per_slice else 1
   const int32_t* mult;   // [P][cout]
   const int16_t* slope;  // [P][cout]
-  const uint16_t* Wtc;   // 27-slice layers: packed bf16 weights for the tensor cores
+  const uint16_t* Wtc;   // 27-slice layers and the predictor's first layer: packed bf16
+                         // weights for the tensor cores
 };
 struct DEmb {
   int cout, z_out;
@@ -150,7 +151,13 @@ struct DPred2 {
   const int32_t* wsum;   // [256]
   const int32_t* bias;   // [256]
   const int32_t* mult;   // [256]
+  const uint16_t* Wtc;   // [256][32] bf16, K-major 64-byte swizzled rows (row 255 zero)
 };
+// Predictor weights for the tensor cores: W [rows][32] int8 -> bf16 rows of
+// 64 bytes, K-major, 64-byte swizzled; rows_total >= rows (extra rows zero).
+void pack_pred_tc_weights(const int8_t* W, int rows, int rows_total, uint16_t* img);
+// Non-zero if a tensor-core predictor gave up on a bounded wait (optionally reset).
+int pred_tc_error(bool reset);
 
 // Write E[codes[i]] into columns [col, col + C) of out (row stride `stride`).
 void launch_embed(const DEmb& E, const uint8_t* codes, const int64_t* d_n, int64_t n_host,
@@ -210,10 +217,14 @@ int conv_tc_error(bool reset);
 
 // Predictor + integer softmax + cumulative table.
 enum PredMode { kPredCdf = 0, kPredEnc = 1, kPredLogits = 2 };
+// variant 0: CUDA cores (dp4a, warp per row); 1: tcgen05 for both linear
+// layers (needs the packed bf16 weights).  Same results; the codec's
+// autotuner picks.
+constexpr int kPredVariants = 2;
 void launch_predictor(const DLayer& P1, const DPred2& P2, const uint32_t* lut, const int8_t* F,
                       int f_stride, const int64_t* d_n, int64_t n_host, int mode,
                       const uint8_t* codes, uint16_t* cdf, uint32_t* enc, int8_t* logits,
-                      cudaStream_t st);
+                      cudaStream_t st, int variant = 0);
 
 // Integer softmax only (logits given), CDF rows out.
 void launch_softmax_cdf(const int8_t* logits, int64_t n, const uint32_t* lut, uint16_t* cdf,

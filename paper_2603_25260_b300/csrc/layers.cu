@@ -10,10 +10,14 @@
 // so that lane co reads consecutive words (no bank conflicts).  INT8 x INT8
 // products accumulate exactly in INT32 with dp4a: sum (x - z) w is computed as
 // sum x w - z * sum w, which is the same integer.
+#include <cuda_bf16.h>
+#include <string.h>
+
 #include <algorithm>
 
 #include "common.cuh"
 #include "kernels.h"
+#include "tc_util.cuh"
 
 namespace lpc {
 
@@ -203,36 +207,33 @@ __device__ __forceinline__ uint32_t div_by(uint32_t x, uint32_t S, uint32_t inv)
 
 __device__ __forceinline__ void softmax_freq(const int (&l)[8], const uint32_t* slut, int lane,
                                              uint32_t (&f)[8]) {
+  // symbol 255 (lane 31, i = 7) is not a class
+  const bool last = lane == 31;
   int mx = -1000;
 #pragma unroll
   for (int i = 0; i < 8; i++)
-    if (lane * 8 + i < kNsym) mx = max(mx, l[i]);
-#pragma unroll
-  for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (i < 7 || !last) mx = max(mx, l[i]);
+  mx = __reduce_max_sync(0xffffffffu, mx);
   uint32_t e[8];
   uint32_t S = 0;
   int first = 1 << 20;
 #pragma unroll
-  for (int i = 0; i < 8; i++) {
-    const bool v = lane * 8 + i < kNsym;
+  for (int i = 7; i >= 0; i--) {  // descending: the lowest tie wins
+    const bool v = i < 7 || !last;
     e[i] = v ? slut[mx - l[i]] : 0u;
     S += e[i];
-    if (v && l[i] == mx && first == (1 << 20)) first = lane * 8 + i;
+    first = v && l[i] == mx ? lane * 8 + i : first;
   }
-#pragma unroll
-  for (int o = 16; o; o >>= 1) {
-    S += __shfl_xor_sync(0xffffffffu, S, o);
-    first = min(first, __shfl_xor_sync(0xffffffffu, first, o));
-  }
+  S = __reduce_add_sync(0xffffffffu, S);
+  first = __reduce_min_sync(0xffffffffu, first);
   uint32_t tot = 0;
   const uint32_t inv = 0xFFFFFFFFu / S;
 #pragma unroll
   for (int i = 0; i < 8; i++) {
-    f[i] = lane * 8 + i < kNsym ? 1u + div_by(e[i] * (uint32_t)(kFreqTotal - kNsym), S, inv) : 0u;
+    f[i] = (i < 7 || !last) ? 1u + div_by(e[i] * (uint32_t)(kFreqTotal - kNsym), S, inv) : 0u;
     tot += f[i];
   }
-#pragma unroll
-  for (int o = 16; o; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+  tot = __reduce_add_sync(0xffffffffu, tot);
   if ((first >> 3) == lane) {
 #pragma unroll
     for (int i = 0; i < 8; i++)
@@ -297,12 +298,12 @@ void launch_softmax_cdf(const int8_t* logits, int64_t n, const uint32_t* lut, ui
   count_launches(1);
 }
 
-// ------------------------------------------- predictor + softmax + CDF --
+// ----------------------------------- predictor, CUDA-core (dp4a) variant --
 // h = requant(prelu(W1 (F - z1) + b1)) (C -> C), logits = requant(W2 (h - z2)
 // + b2) (C -> 255), then the integer softmax.  Modes: full CDF row, the
 // (C_s, f_s) pair of the true symbol (encoder), or the logits (debug).
 __global__ void __launch_bounds__(kWarps * 32)
-k_predictor(DLayer P1, DPred2 P2, const uint32_t* __restrict__ lut,
+k_predictor_dp4a(DLayer P1, DPred2 P2, const uint32_t* __restrict__ lut,
             const int8_t* __restrict__ F, int f_stride, const int64_t* d_n, int mode,
             const uint8_t* __restrict__ codes, uint16_t* cdf, uint32_t* enc, int8_t* logits) {
   __shared__ int32_t sW1[8 * 32], sW1s[32], sB1[32], sM1[32], sS1[32];
@@ -378,14 +379,286 @@ k_predictor(DLayer P1, DPred2 P2, const uint32_t* __restrict__ lut,
   }
 }
 
+// ------------------------------------------- predictor + softmax + CDF --
+// h = requant(prelu(W1 (F - z1) + b1)) (C -> C), logits = requant(W2 (h - z2)
+// + b2) (C -> 255) on the tcgen05 tensor cores, then the integer softmax one
+// warp per row.  Modes: full CDF row, the (C_s, f_s) pair of the true symbol
+// (encoder), or the logits (debug).
+//
+// One persistent CTA of 16 warps per SM walks tiles of 128 rows: the rows
+// (F - z1) go to shared memory as bf16 (exact: |F - z1| <= 255), an M=128
+// N=32 K=32 MMA gives layer 1 in TMEM (every fp32 partial sum is an integer
+// below 2^23: 32 products of at most 255 * 127), the warps write (h - z2)
+// back as bf16 (warp w: TMEM lane quadrant w % 4, a quarter of the columns),
+// an M=128 N=256 K=32 MMA gives the 255 logits, which the warps requantise
+// into a shared logits tile; then every warp runs the softmax of 8 rows,
+// 8 symbols a lane.
+namespace {
+
+constexpr int kPTile = 128;
+constexpr int kPThreads = 512;
+constexpr int kLogStride = 272;  // logits row stride in shared memory (conflict-free)
+constexpr int kPredB1 = 0, kPredB2 = 2048, kPredA1 = 18432, kPredA2 = 26624, kPredLg = 34816;
+constexpr int kPredSmem = 1024 + kPredLg + kPTile * kLogStride;
+
+__device__ int g_pred_error = 0;
+
+// 8 consecutive fp32 columns of this thread's TMEM lane, as integers.
+__device__ __forceinline__ void tmem_ld8i(uint32_t taddr, int32_t (&v)[8]) {
+  uint32_t r[8];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; i++) v[i] = __float2int_rn(__uint_as_float(r[i]));
+}
+
+// 8 values (v - z) as bf16: chunk c of row `row` of a 64-byte-row,
+// 64-byte-swizzled tile at smem address base.
+__device__ __forceinline__ void bf16_chunk8(const int32_t (&v)[8], int z, uint32_t base, int row,
+                                            int c) {
+  uint32_t w[4];
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    const __nv_bfloat162 p =
+        __halves2bfloat162(__int2bfloat16_rn(v[2 * k] - z), __int2bfloat16_rn(v[2 * k + 1] - z));
+    w[k] = *reinterpret_cast<const uint32_t*>(&p);
+  }
+  const uint32_t a = base + tc::swz<64>(row * 64 + c * 16);
+  asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(w[0]), "r"(w[1]),
+               "r"(w[2]), "r"(w[3])
+               : "memory");
+}
+
+__global__ void __launch_bounds__(kPThreads, 1)
+k_predictor_tc(DLayer P1, DPred2 P2, const uint32_t* __restrict__ lut,
+               const int8_t* __restrict__ F, int f_stride, const int64_t* d_n, int mode,
+               const uint8_t* __restrict__ codes, uint16_t* cdf, uint32_t* enc, int8_t* logits) {
+  extern __shared__ unsigned char smraw[];
+  unsigned char* sm = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
+  __shared__ int32_t sB1[32], sM1[32], sS1[32], sB2[256], sM2[256];
+  __shared__ uint32_t slut[256];
+  __shared__ uint64_t mbar;
+  __shared__ uint32_t tslot;
+  const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+  if (w == 0) tc::tmem_alloc(&tslot, 256);
+  if (t == 0) {
+    tc::mbar_init(&mbar, 1);
+    tc::fence_mbar_init();
+  }
+  if (t < 256) {
+    sB2[t] = P2.bias[t];
+    sM2[t] = P2.mult[t];
+    slut[t] = lut[t];
+  }
+  if (t < 32) {
+    sB1[t] = P1.bias[t];
+    sM1[t] = P1.mult[t];
+    sS1[t] = P1.prelu ? P1.slope[t] : 0;
+  }
+  {  // the weight images: layer 1 (2 KB) and layer 2 (16 KB)
+    const uint4* s1 = reinterpret_cast<const uint4*>(P1.Wtc);
+    const uint4* s2 = reinterpret_cast<const uint4*>(P2.Wtc);
+    uint4* d1 = reinterpret_cast<uint4*>(sm + kPredB1);
+    uint4* d2 = reinterpret_cast<uint4*>(sm + kPredB2);
+    if (t < 128) d1[t] = __ldg(s1 + t);
+    for (int i = t; i < 1024; i += kPThreads) d2[i] = __ldg(s2 + i);
+  }
+  tc::fence_async_smem();
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tbase = tslot;
+  const int quad = w & 3, cg = w >> 2;  // TMEM lane quadrant, column group
+  const int erow = quad * 32 + lane;    // tile row this thread handles in the epilogues
+  const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
+  const uint32_t sA1 = tc::smem_u32(sm + kPredA1), sA2 = tc::smem_u32(sm + kPredA2);
+  const uint32_t sB1w = tc::smem_u32(sm + kPredB1), sB2w = tc::smem_u32(sm + kPredB2);
+  unsigned char* sLg = sm + kPredLg;
+  const int64_t n = *d_n;
+  const int64_t ntiles = (n + kPTile - 1) / kPTile;
+  uint32_t phase = 0;
+  bool ok = true;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t r0 = tile * kPTile;
+    // ---- layer-1 input: (F - z1) as bf16, thread = (row, 8-column chunk)
+    {
+      const int row = t >> 2, c = t & 3;
+      int32_t v[8];
+      if (r0 + row < n) {
+        const uint2 q = __ldg(reinterpret_cast<const uint2*>(F + (r0 + row) * f_stride) + c);
+        const int8_t* b = reinterpret_cast<const int8_t*>(&q);
+#pragma unroll
+        for (int k = 0; k < 8; k++) v[k] = b[k];
+      } else {
+#pragma unroll
+        for (int k = 0; k < 8; k++) v[k] = P1.z_in;
+      }
+      bf16_chunk8(v, P1.z_in, sA1, row, c);
+    }
+    tc::fence_async_smem();
+    tc::tc_fence_before();
+    __syncthreads();
+    if (t == 0) {
+      tc::tc_fence_after();
+#pragma unroll
+      for (int ks = 0; ks < 2; ks++)
+        tc::mma_bf16(tbase, tc::smem_desc<64>(sA1 + ks * 32, 512),
+                     tc::smem_desc<64>(sB1w + ks * 32, 512), tc::idesc_bf16(kPTile, 32),
+                     ks ? 1u : 0u);
+      tc::mma_commit(&mbar);
+    }
+    ok = tc::mbar_wait(&mbar, phase);
+    phase ^= 1;
+    if (__syncthreads_or(!ok)) {
+      ok = false;
+      break;
+    }
+    tc::tc_fence_after();
+    // ---- layer-1 epilogue: 8 columns a warp; (h - z2) as bf16
+    {
+      int32_t v[8];
+      tmem_ld8i(tbase + lane_off + 8 * cg, v);
+#pragma unroll
+      for (int i = 0; i < 8; i++) {
+        const int c = 8 * cg + i;
+        int32_t a = v[i] + sB1[c];
+        if (P1.prelu) a = prelu(a, sS1[c]);
+        v[i] = requant(a, sM1[c], P1.shift, P1.z_out);
+      }
+      bf16_chunk8(v, P2.z_in, sA2, erow, cg);
+    }
+    tc::fence_async_smem();
+    tc::tc_fence_before();
+    __syncthreads();
+    if (t == 0) {
+      tc::tc_fence_after();
+#pragma unroll
+      for (int ks = 0; ks < 2; ks++)
+        tc::mma_bf16(tbase, tc::smem_desc<64>(sA2 + ks * 32, 512),
+                     tc::smem_desc<64>(sB2w + ks * 32, 512), tc::idesc_bf16(kPTile, 256),
+                     ks ? 1u : 0u);
+      tc::mma_commit(&mbar);
+    }
+    ok = tc::mbar_wait(&mbar, phase);
+    phase ^= 1;
+    if (__syncthreads_or(!ok)) {
+      ok = false;
+      break;
+    }
+    tc::tc_fence_after();
+    // ---- logits: 64 columns a warp, requantised into the shared tile
+#pragma unroll
+    for (int g = 0; g < 4; g++) {
+      const int c0 = 64 * cg + 16 * g;
+      float f[16];
+      tc::tmem_ld16(tbase + lane_off + c0, f);
+      uint32_t pk[4] = {0, 0, 0, 0};
+#pragma unroll
+      for (int i = 0; i < 16; i++) {
+        const int c = c0 + i;
+        const int q = c < kNsym ? requant(__float2int_rn(f[i]) + sB2[c], sM2[c], P2.shift,
+                                          P2.z_out)
+                                : 0;
+        pk[i >> 2] |= (uint32_t)(uint8_t)q << (8 * (i & 3));
+      }
+      *reinterpret_cast<uint4*>(sLg + erow * kLogStride + c0) =
+          make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    // ---- integer softmax, one warp per row, 8 rows a warp
+#pragma unroll 1
+    for (int rr = 0; rr < kPTile / 16; rr++) {
+      const int tr = w * (kPTile / 16) + rr;
+      const int64_t r = r0 + tr;
+      if (r >= n) break;
+      const uint2 raw = *reinterpret_cast<const uint2*>(sLg + tr * kLogStride + 8 * lane);
+      const int8_t* lb = reinterpret_cast<const int8_t*>(&raw);
+      int l[8];
+#pragma unroll
+      for (int i = 0; i < 8; i++) l[i] = lb[i];
+      if (mode == kPredLogits) {
+#pragma unroll
+        for (int i = 0; i < 8; i++)
+          if (lane * 8 + i < kNsym) logits[r * kNsym + lane * 8 + i] = (int8_t)l[i];
+        continue;
+      }
+      uint32_t f[8], c[8];
+      softmax_freq(l, slut, lane, f);
+      cumulate(f, lane, c);
+      if (mode == kPredCdf) {
+        store_cdf_row(c, lane, cdf + r * 256);
+      } else {
+        const int s = (int)codes[r] - 1;
+        if ((s >> 3) == lane) {
+          const int i = s & 7;
+          uint32_t fs = 0, cs = 0;
+#pragma unroll
+          for (int k = 0; k < 8; k++)
+            if (k == i) {
+              fs = f[k];
+              cs = c[k] - f[k];
+            }
+          enc[r] = cs | (fs << 16);
+        }
+      }
+    }
+  }
+  if (!ok) {
+    if (t == 0) atomicExch(&g_pred_error, 1);
+    tc::mbar_wait(&mbar, phase ^ 1);  // an MMA still in flight lands first
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  if (w == 0) tc::tmem_dealloc(tbase, 256);
+}
+
+}  // namespace
+
+void pack_pred_tc_weights(const int8_t* W, int rows, int rows_total, uint16_t* img) {
+  unsigned char* p = reinterpret_cast<unsigned char*>(img);
+  for (int i = 0; i < rows_total * 64; i++) p[i] = 0;
+  for (int r = 0; r < rows; r++)
+    for (int k = 0; k < 32; k++) {
+      const __nv_bfloat16 b = __float2bfloat16_rn((float)W[(size_t)r * 32 + k]);
+      uint32_t off = (uint32_t)(r * 64 + k * 2);
+      off ^= ((off >> 7) & 3) << 4;
+      memcpy(p + off, &b, 2);
+    }
+}
+
+int pred_tc_error(bool reset) {
+  int e = 0;
+  cudaMemcpyFromSymbol(&e, g_pred_error, sizeof(int));
+  if (reset && e) {
+    const int z = 0;
+    cudaMemcpyToSymbol(g_pred_error, &z, sizeof(int));
+  }
+  return e;
+}
+
 void launch_predictor(const DLayer& P1, const DPred2& P2, const uint32_t* lut, const int8_t* F,
                       int f_stride, const int64_t* d_n, int64_t n_host, int mode,
                       const uint8_t* codes, uint16_t* cdf, uint32_t* enc, int8_t* logits,
-                      cudaStream_t st) {
+                      cudaStream_t st, int variant) {
   if (n_host <= 0) return;
-  const int blocks = (int)std::min<int64_t>((n_host + kWarps - 1) / kWarps, kBlocksRow);
-  k_predictor<<<blocks, kWarps * 32, 0, st>>>(P1, P2, lut, F, f_stride, d_n, mode, codes, cdf,
-                                              enc, logits);
+  if (variant == 1 && P1.Wtc && P2.Wtc) {
+    const int64_t ntiles = (n_host + kPTile - 1) / kPTile;
+    const int blocks = (int)std::min<int64_t>(ntiles, 148);
+    cudaFuncSetAttribute(k_predictor_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kPredSmem);
+    k_predictor_tc<<<blocks, kPThreads, kPredSmem, st>>>(P1, P2, lut, F, f_stride, d_n, mode,
+                                                           codes, cdf, enc, logits);
+  } else {
+    const int blocks = (int)std::min<int64_t>((n_host + kWarps - 1) / kWarps, kBlocksRow);
+    k_predictor_dp4a<<<blocks, kWarps * 32, 0, st>>>(P1, P2, lut, F, f_stride, d_n, mode, codes,
+                                                     cdf, enc, logits);
+  }
   count_launches(1);
 }
 

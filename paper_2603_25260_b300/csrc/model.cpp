@@ -75,6 +75,11 @@ LayerOffs pack_layer(Image& img, const BlobRecord& r) {
     pack_conv_tc_weights(r.W, cin, tcimg.data());
     o.tc = img.add(tcimg.data(), tcimg.size() * 2);
   }
+  if (r.S == 1 && r.kind == kSum && cout == 32 && cin == 32) {  // predictor layer 1
+    std::vector<uint16_t> tcimg(32 * 32);
+    pack_pred_tc_weights(r.W, 32, 32, tcimg.data());
+    o.tc = img.add(tcimg.data(), tcimg.size() * 2);
+  }
   return o;
 }
 
@@ -275,8 +280,11 @@ int model_load(const void* blob, size_t len, Model& M, std::string& err) {
         W[((size_t)i * K4 + k) * 32 + lane] = (int32_t)v;
       }
     }
+    std::vector<uint16_t> tcimg(256 * 32);
+    pack_pred_tc_weights(r->W, kNsym, 256, tcimg.data());
     fixes.push_back({&d, 3, {img.add(W.data(), W.size() * 4), img.add(ws.data(), 1024),
-                             img.add(bi.data(), 1024), img.add(mu.data(), 1024), 0}});
+                             img.add(bi.data(), 1024), img.add(mu.data(), 1024),
+                             img.add(tcimg.data(), tcimg.size() * 2)}});
   };
 
   emb(M.E0);
@@ -339,6 +347,7 @@ int model_load(const void* blob, size_t len, Model& M, std::string& err) {
       d->wsum = reinterpret_cast<const int32_t*>(base + f.o[1]);
       d->bias = reinterpret_cast<const int32_t*>(base + f.o[2]);
       d->mult = reinterpret_cast<const int32_t*>(base + f.o[3]);
+      d->Wtc = reinterpret_cast<const uint16_t*>(base + f.o[4]);
     }
   }
   return LPC_OK;

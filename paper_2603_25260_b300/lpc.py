@@ -49,6 +49,7 @@ def lib():
         sig = {
             "codec_create": (I32, [C.POINTER(Config), P, SZ, C.POINTER(P)]),
             "codec_destroy": (None, [P]),
+            "codec_set_tuning": (I32, [P, P]),
             "codec_tuning": (I32, [P, P, P]),
             "codec_last_error": (C.c_char_p, [P]),
             "encode_frame": (I32, [P, P, I64, P, SZ, C.POINTER(SZ)]),
@@ -260,11 +261,17 @@ class Codec:
         """The conv autotuner's choice per input width and the timed variants
         (milliseconds; bit 0 of a variant = shallower stage ring, bit 1 =
         contiguous tile order)."""
-        v = (C.c_int * 2)()
-        ms = (C.c_float * 8)()
+        v = (C.c_int * 3)()
+        ms = (C.c_float * 10)()
         self._check(self._lib.codec_tuning(self._h, v, ms))
-        return {"conv32": v[0], "conv64": v[1],
-                "ms32": [round(x, 4) for x in ms[:4]], "ms64": [round(x, 4) for x in ms[4:]]}
+        return {"conv32": v[0], "conv64": v[1], "predictor": v[2],
+                "ms32": [round(x, 4) for x in ms[:4]], "ms64": [round(x, 4) for x in ms[4:8]],
+                "ms_pred": [round(x, 4) for x in ms[8:10]]}
+
+    def set_tuning(self, conv32: int = -1, conv64: int = -1, predictor: int = -1):
+        """Fix kernel variants instead of autotuning them (-1: tune)."""
+        v = (C.c_int * 3)(conv32, conv64, predictor)
+        self._check(self._lib.codec_set_tuning(self._h, v))
 
     def last_phases(self) -> list[float]:
         """Host timeline of the last encode / decode in microseconds (see lpc.h)."""

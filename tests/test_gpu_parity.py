@@ -146,8 +146,8 @@ def test_codec_autotuner_picks_variants(lpc, blob):
     cod = _codec(lpc, blob, 14, 20000)
     data = cod.encode(_cuda(xyz))
     t = cod.tuning()
-    assert 0 <= t["conv32"] < 4 and 0 <= t["conv64"] < 4
-    assert all(0 < m < 1e3 for m in t["ms32"] + t["ms64"])
+    assert 0 <= t["conv32"] < 4 and 0 <= t["conv64"] < 4 and 0 <= t["predictor"] < 2
+    assert all(0 < m < 1e3 for m in t["ms32"] + t["ms64"] + t["ms_pred"])
     assert data == O.encode(blob, xyz, 14)  # and the next call runs the captured graphs
     assert cod.encode(_cuda(xyz)) == data
 
@@ -385,3 +385,19 @@ def test_batch_into_reusable_buffer(lpc, blob):
         decs = cod.decode_batch_from(buf, spans, outs)
         for f, L, d in zip(frames, Ls, decs):
             assert np.array_equal(O.leaf_keys(d.cpu().numpy(), L), O.leaf_keys(f, L))
+
+
+@pytest.mark.parametrize("variants", [(0, 0, 0), (3, 3, 1), (1, 2, 1), (2, 1, 0)])
+def test_fixed_variants_byte_identical(lpc, blob, variants):
+    """Every fixed combination of conv and predictor variants gives the
+    oracle's stream and decodes it (graphs captured with those variants)."""
+    xyz = synth.random_cloud(15000, 13, 6)
+    cod = _codec(lpc, blob, 13, 15000)
+    cod.set_tuning(*variants)
+    want = O.encode(blob, xyz, 13)
+    for _ in range(2):
+        data = cod.encode(_cuda(xyz))
+        assert data == want
+        dec = cod.decode(data).cpu().numpy()
+        assert np.array_equal(O.leaf_keys(dec, 13), O.leaf_keys(xyz, 13))
+    assert cod.tuning()["predictor"] == variants[2]
