@@ -39,6 +39,18 @@ int lpc_build_levels(const int32_t* d_xyz, int64_t n, int L, uint64_t* d_keys, u
 int lpc_kernel_map(const uint64_t* d_keys, int64_t N, int depth, int32_t* d_nbr, int table_log2,
                    uint64_t stream);
 
+/* The kernel map of a level from the map of its parent level (the octree
+ * neighbour rule; Sec. 3.3 builds maps at V_b and V_t, and V_t is the level
+ * below V_b): d_ckeys / d_cpar are the Nc children's keys and parent rows,
+ * d_pnbr the parents' map [Np][27], d_pcode their occupancy codes and d_poff
+ * their first child rows (exclusive scan of the code popcounts).  Writes the
+ * same d_nbr[Nc][27] as lpc_kernel_map on the children, without a hash
+ * table.  All pointers are device memory owned by the caller; inconsistent
+ * inputs (a parent row or child offset out of range) are not detected. */
+int lpc_kernel_map_child(const uint64_t* d_ckeys, const uint32_t* d_cpar, int64_t Nc,
+                         const int32_t* d_pnbr, const uint8_t* d_pcode, const uint32_t* d_poff,
+                         int32_t* d_nbr, uint64_t stream);
+
 /* Kernel map that allocates nothing (the paper has no counterpart; this is a
  * deployment convenience).  Same inputs, output and statuses as
  * lpc_kernel_map with automatic table size, for callers that may not call

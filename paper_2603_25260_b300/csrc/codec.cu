@@ -251,8 +251,7 @@ int Codec::create(const lpc_config& cfg, const void* blob, size_t len) {
   add((void**)&scan_.tiles, 4 * scan_.max_tiles);
   hash_.cap = 1024;
   while (hash_.cap < 2 * P) hash_.cap <<= 1;
-  add((void**)&hash_.keys, 8 * hash_.cap);
-  add((void**)&hash_.vals, 4 * hash_.cap);
+  add((void**)&hash_.slots, 16 * hash_.cap);
   add((void**)&nbr_b_, 4 * 27 * P);
   add((void**)&nbr_t_, 4 * 27 * P);
   add((void**)&fb_, 32 * P);
@@ -607,9 +606,15 @@ void Codec::ensure_Ft() {
   have_Ft_ = true;
 }
 
+// The map at V_t (height 4) from the map at V_b: every node of V_t is a
+// child of a node of V_b, so its neighbours are children of its parent's
+// neighbours (no second hash table).
 void Codec::ensure_nbr_t() {
   if (have_nbr_t_) return;
-  kmap(4, nbr_t_, 1);
+  pbeg(kFamHash);
+  launch_kernel_map_child(key_[4], par_[4], d_N_ + 4, gridn(4), nbr_b_, code_[5], off_[5], nbr_t_,
+                          st_, prof.mask ? d_pairs_ + 1 : nullptr);
+  pend(kFamHash, 120.0 * N_[4] + 113.0 * N_[5], 0);
   have_nbr_t_ = true;
 }
 

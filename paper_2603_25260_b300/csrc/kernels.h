@@ -110,9 +110,8 @@ void launch_rc_decode(const RcChunk* ck, int n, const uint16_t* cdf, const uint8
 
 // ------------------------------------------------------------------ hash --
 struct HashTable {
-  uint64_t* keys = nullptr;
-  uint32_t* vals = nullptr;
-  int64_t cap = 0;  // allocated slots (power of two)
+  ulonglong2* slots = nullptr;  // {key, row} pairs
+  int64_t cap = 0;              // allocated slots (power of two)
 };
 // Clear `slots` (power of two <= cap) slots, insert the N keys of one level,
 // then write the 27-neighbour map nbr[N][27].  Node depth: Lf[frame] - depth
@@ -122,6 +121,14 @@ struct HashTable {
 void launch_kernel_map(const uint64_t* keys, const int64_t* d_n, int64_t n_host, const int* Lf,
                        int depth, const HashTable& h, int64_t slots, int32_t* nbr, int* err,
                        cudaStream_t st, uint64_t* pairs = nullptr);
+// The 27-neighbour map of a level from its parents' map: ckeys / cpar are the
+// children's keys and parent rows (*d_n children), pnbr[Np][27] the parents'
+// map, pcode / poff their occupancy codes and first child rows.  Same output
+// as launch_kernel_map on the children; no hash table.
+void launch_kernel_map_child(const uint64_t* ckeys, const uint32_t* cpar, const int64_t* d_n,
+                             int64_t n_host, const int32_t* pnbr, const uint8_t* pcode,
+                             const uint32_t* poff, int32_t* nbr, cudaStream_t st,
+                             uint64_t* pairs = nullptr);
 
 // ---------------------------------------------------------------- layers --
 // Device-resident INT8 layer (blob kinds 1 and 4) in dp4a layout.

@@ -186,90 +186,140 @@ void launch_down(const DLayer& W, const uint64_t* ckey, const uint32_t* poff, co
 }
 
 // ------------------------------------------- integer softmax -> CDF row --
-// Lane l holds symbols s = 8l + i, i = 0..7; symbol 255 (lane 31, i = 7) is
-// not a class and takes no frequency.
-//   M = max l_s; e_s = lut[M - l_s]; S = sum e_s (< 2^24);
-//   f_s = 1 + floor(e_s (2^16 - 255) / S)  (the product fits in 32 bits);
-//   the remainder 2^16 - sum f_s goes to the lowest s with l_s = M.
-// The 255 divisions by the row's S share one reciprocal: with
-// inv = floor((2^32 - 1) / S), q = umulhi(x, inv) is floor(x / S) or at most
-// two less (x < 2^32), and two conditional corrections make it exact.
+// One warp per row; lane l holds the logits of symbols s = 8l + i, i = 0..7;
+// symbol 255 (lane 31, i = 7) is not a class and takes no frequency.
+//   M = max l_s; e_s = lut[M - l_s]; S = sum e_s (2^16 <= S < 2^24, as
+//   lut[0] = 2^16 and lut is nonincreasing);
+//   f_s = 1 + q_s with q_s = floor(e_s (2^16 - 255) / S) (the product fits
+//   in 32 bits); the remainder R = 2^16 - sum f_s goes to the lowest s with
+//   l_s = M.
+// M and its lowest index come from one reduction of the keys 256 l_s +
+// (255 - s).  The divisions share one reciprocal inv = floor((2^32 - 1) / S):
+// for x < 2^32, umulhi(x, inv) is floor(x / S) or one less (x inv / 2^32 >
+// x / S - x / 2^32), and one conditional step makes it exact.
+constexpr uint32_t kQScale = kFreqTotal - kNsym;
+
 __device__ __forceinline__ uint32_t div_by(uint32_t x, uint32_t S, uint32_t inv) {
   uint32_t q = __umulhi(x, inv);
-  uint32_t r = x - q * S;
-  if (r >= S) {
-    q++;
-    r -= S;
-  }
-  if (r >= S) q++;
+  if (x - q * S >= S) q++;
   return q;
 }
 
-__device__ __forceinline__ void softmax_freq(const int (&l)[8], const uint32_t* slut, int lane,
-                                             uint32_t (&f)[8]) {
-  // symbol 255 (lane 31, i = 7) is not a class
-  const bool last = lane == 31;
-  int mx = -1000;
-#pragma unroll
-  for (int i = 0; i < 8; i++)
-    if (i < 7 || !last) mx = max(mx, l[i]);
-  mx = __reduce_max_sync(0xffffffffu, mx);
-  uint32_t e[8];
-  uint32_t S = 0;
-  int first = 1 << 20;
-#pragma unroll
-  for (int i = 7; i >= 0; i--) {  // descending: the lowest tie wins
-    const bool v = i < 7 || !last;
-    e[i] = v ? slut[mx - l[i]] : 0u;
-    S += e[i];
-    first = v && l[i] == mx ? lane * 8 + i : first;
-  }
-  S = __reduce_add_sync(0xffffffffu, S);
-  first = __reduce_min_sync(0xffffffffu, first);
-  uint32_t tot = 0;
-  const uint32_t inv = 0xFFFFFFFFu / S;
-#pragma unroll
-  for (int i = 0; i < 8; i++) {
-    f[i] = (i < 7 || !last) ? 1u + div_by(e[i] * (uint32_t)(kFreqTotal - kNsym), S, inv) : 0u;
-    tot += f[i];
-  }
-  tot = __reduce_add_sync(0xffffffffu, tot);
-  if ((first >> 3) == lane) {
-#pragma unroll
-    for (int i = 0; i < 8; i++)
-      if (lane * 8 + i == first) f[i] += (uint32_t)kFreqTotal - tot;
-  }
+// floor((2^32 - 1) / S).  For 2^16 <= S < 2^24 the fp32 reciprocal scaled
+// by 2^32 is within 2^-8 of 2^32 / S, so its truncation is within one of
+// the result and one correction either way makes it exact; other S take
+// the integer division.
+__device__ __forceinline__ uint32_t recip32(uint32_t S) {
+  if (S < (1u << 16) || S >= (1u << 24)) return 0xFFFFFFFFu / S;
+  uint32_t g = __float2uint_rz(__frcp_rn((float)S) * 4294967296.0f);
+  const unsigned long long gs = (unsigned long long)g * S;
+  if (gs > 0xFFFFFFFFull)
+    g--;
+  else if (gs + S <= 0xFFFFFFFFull)
+    g++;
+  return g;
 }
 
-// Inclusive cumulative values c[i] = C_{s+1} for s = 8 lane + i.
-__device__ __forceinline__ void cumulate(const uint32_t (&f)[8], int lane, uint32_t (&c)[8]) {
+struct SoftRow {
+  uint32_t r[8];  // this lane's running sums q_{8l} + ... + q_{8l+i}
+  uint32_t tot;   // sum of q over the row
+  int first;      // lowest symbol with the maximum logit
+};
+
+// Per-lane tie-break constants 255 - (8 lane + i) of the max keys.
+__device__ __forceinline__ void tie_keys(int lane, int (&ck)[8]) {
+#pragma unroll
+  for (int i = 0; i < 8; i++) ck[i] = 255 - (8 * lane + i);
+}
+
+// l: this lane's logits (lane 31's l[7], the padding, is ignored).
+__device__ __forceinline__ void softmax_row(int (&l)[8], const int (&ck)[8], bool last,
+                                            const uint32_t* slut, SoftRow& o) {
+  if (last) l[7] = -128;  // key -32768: loses every tie
+  int key = l[0] * 256 + ck[0];
+#pragma unroll
+  for (int i = 1; i < 8; i++) key = max(key, l[i] * 256 + ck[i]);
+  key = __reduce_max_sync(0xffffffffu, key);
+  const int mx = key >> 8;  // floor: the low byte is the tie-break
+  o.first = 255 - (key & 255);
+  uint32_t e[8];
+  uint32_t S = 0;
+#pragma unroll
+  for (int i = 0; i < 8; i++) {
+    e[i] = slut[mx - l[i]];
+    S += e[i];
+  }
+  if (last) {
+    S -= e[7];
+    e[7] = 0;
+  }
+  S = __reduce_add_sync(0xffffffffu, S);
+  const uint32_t inv = recip32(S);
   uint32_t run = 0;
 #pragma unroll
   for (int i = 0; i < 8; i++) {
-    run += f[i];
-    c[i] = run;
+    run += div_by(e[i] * kQScale, S, inv);
+    o.r[i] = run;
   }
-  uint32_t x = run;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  const uint32_t ex = x - run;
-#pragma unroll
-  for (int i = 0; i < 8; i++) c[i] += ex;
+  o.tot = __reduce_add_sync(0xffffffffu, run);
 }
 
-__device__ __forceinline__ void store_cdf_row(const uint32_t (&c)[8], int lane, uint16_t* row) {
+// The row of cumulative values C_{s+1} = f_0 + ... + f_s as u16, entries
+// 254 and 255 = 0xFFFF (C_{s+1} <= 65535 for s <= 253 since every f >= 1).
+__device__ __forceinline__ void store_cdf_row(const SoftRow& o, int lane, uint16_t* row) {
+  uint32_t x = o.r[7];
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= d) x += y;
+  }
+  const uint32_t R = kQScale - o.tot;
+  const uint32_t base = x - o.r[7] + 8 * lane + 1;  // q before this lane; f = 1 + q
+  const int thr = o.first - 8 * lane;              // symbols from the first maximum on take R
   uint32_t h[8];
 #pragma unroll
-  for (int i = 0; i < 8; i++) h[i] = (lane * 8 + i <= 253) ? c[i] : 0xFFFFu;
+  for (int i = 0; i < 8; i++) h[i] = o.r[i] + base + i + (i >= thr ? R : 0u);
+  if (lane == 31) h[6] = h[7] = 0xFFFFu;
   uint4 v;
   v.x = h[0] | (h[1] << 16);
   v.y = h[2] | (h[3] << 16);
   v.z = h[4] | (h[5] << 16);
   v.w = h[6] | (h[7] << 16);
   reinterpret_cast<uint4*>(row)[lane] = v;
+}
+
+// The encoder's interval (C_s, f_s) of symbol s (0..254) packed as
+// C_s | f_s << 16; every lane takes part, the result is lane s / 8's.
+__device__ __forceinline__ uint32_t enc_pair(const SoftRow& o, int lane, int s) {
+  const int sl = s >> 3, si = s & 7;
+  const uint32_t before = __reduce_add_sync(0xffffffffu, lane < sl ? o.r[7] : 0u);
+  uint32_t rs = 0, rp = 0;  // r_si and r_{si-1}, by masks (no indexed access)
+#pragma unroll
+  for (int k = 0; k < 8; k++) {
+    rs |= o.r[k] & (0u - (uint32_t)(k == si));
+    rp |= o.r[k] & (0u - (uint32_t)(k + 1 == si));
+  }
+  const uint32_t R = kQScale - o.tot;
+  const uint32_t fs = 1 + (rs - rp) + (s == o.first ? R : 0u);
+  const uint32_t cs = (uint32_t)s + before + rp + (s > o.first ? R : 0u);
+  return cs | (fs << 16);
+}
+
+// Eq. 14 in a cheaper exact form when the shift r <= 32 and the multiplier
+// scaled by 2^(32 - r) stays below 2^31: floor((a m + 2^(r-1)) / 2^r) is the
+// high word of a (m 2^(32-r)) + 2^31; the zero point joins the high word.
+__device__ __forceinline__ int requant_hi(int32_t a, int32_t ms, int z) {
+  const long long p = (long long)a * ms + ((long long)z * 4294967296ll + 2147483648ll);
+  const int q = (int)(p >> 32);
+  return min(max(q, -128), 127);
+}
+
+// Whether a layer's multiplier m admits requant_hi, and the scaled form.
+__device__ __forceinline__ bool hi_ok(int32_t m, int r) {
+  return r >= 1 && r <= 32 && m >= 0 && ((long long)m << (32 - r)) <= 0x7FFFFFFFll;
+}
+__device__ __forceinline__ int32_t hi_scale(int32_t m, int r) {
+  return (int32_t)((long long)m << (32 - r));
 }
 
 __global__ void __launch_bounds__(kWarps * 32)
@@ -279,14 +329,15 @@ k_softmax_cdf(const int8_t* __restrict__ logits, int64_t n, const uint32_t* __re
   for (int i = threadIdx.x; i < 256; i += blockDim.x) slut[i] = lut[i];
   __syncthreads();
   const int lane = threadIdx.x & 31;
+  int ck[8];
+  tie_keys(lane, ck);
   for (int64_t r = warp_id_global(); r < n; r += warps_total()) {
     int l[8];
 #pragma unroll
     for (int i = 0; i < 8; i++) l[i] = lane * 8 + i < kNsym ? logits[r * kNsym + lane * 8 + i] : 0;
-    uint32_t f[8], c[8];
-    softmax_freq(l, slut, lane, f);
-    cumulate(f, lane, c);
-    store_cdf_row(c, lane, cdf + r * 256);
+    SoftRow o;
+    softmax_row(l, ck, lane == 31, slut, o);
+    store_cdf_row(o, lane, cdf + r * 256);
   }
 }
 
@@ -313,12 +364,18 @@ k_predictor_dp4a(DLayer P1, DPred2 P2, const uint32_t* __restrict__ lut,
   __shared__ int32_t hbuf[kWarps][8];
   for (int i = threadIdx.x; i < 8 * 32; i += blockDim.x) sW1[i] = P1.Wp[i];
   for (int i = threadIdx.x; i < 8 * 8 * 32; i += blockDim.x) sW2[i] = P2.Wp[i];
+  bool ok = true;
   for (int i = threadIdx.x; i < 256; i += blockDim.x) {
     sW2s[i] = P2.wsum[i];
     sB2[i] = P2.bias[i];
-    sM2[i] = P2.mult[i];
     slut[i] = lut[i];
+    ok = ok && hi_ok(P2.mult[i], P2.shift);
   }
+  // the logits' requantisation takes the high-word form when every
+  // multiplier admits it
+  const bool fast2 = __syncthreads_and(ok);
+  for (int i = threadIdx.x; i < 256; i += blockDim.x)
+    sM2[i] = fast2 ? hi_scale(P2.mult[i], P2.shift) : P2.mult[i];
   for (int i = threadIdx.x; i < 32; i += blockDim.x) {
     sW1s[i] = P1.wsum[i];
     sB1[i] = P1.bias[i];
@@ -327,6 +384,8 @@ k_predictor_dp4a(DLayer P1, DPred2 P2, const uint32_t* __restrict__ lut,
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int ck[8];
+  tie_keys(lane, ck);
   const int64_t n = *d_n;
   for (int64_t r = warp_id_global(); r < n; r += warps_total()) {
     int32_t xv[8];
@@ -349,7 +408,8 @@ k_predictor_dp4a(DLayer P1, DPred2 P2, const uint32_t* __restrict__ lut,
       int32_t acc = sB2[sidx] - P2.z_in * sW2s[sidx];
 #pragma unroll
       for (int k = 0; k < 8; k++) acc = __dp4a(hv[k], sW2[(i * 8 + k) * 32 + lane], acc);
-      l[i] = requant(acc, sM2[sidx], P2.shift, P2.z_out);
+      l[i] = fast2 ? requant_hi(acc, sM2[sidx], P2.z_out)
+                   : requant(acc, sM2[sidx], P2.shift, P2.z_out);
     }
     if (mode == kPredLogits) {
 #pragma unroll
@@ -357,24 +417,14 @@ k_predictor_dp4a(DLayer P1, DPred2 P2, const uint32_t* __restrict__ lut,
         if (lane * 8 + i < kNsym) logits[r * kNsym + lane * 8 + i] = (int8_t)l[i];
       continue;
     }
-    uint32_t f[8], c[8];
-    softmax_freq(l, slut, lane, f);
-    cumulate(f, lane, c);
+    SoftRow o;
+    softmax_row(l, ck, lane == 31, slut, o);
     if (mode == kPredCdf) {
-      store_cdf_row(c, lane, cdf + r * 256);
+      store_cdf_row(o, lane, cdf + r * 256);
     } else {
       const int s = (int)codes[r] - 1;
-      if ((s >> 3) == lane) {
-        const int i = s & 7;
-        uint32_t fs = 0, cs = 0;
-#pragma unroll
-        for (int k = 0; k < 8; k++)
-          if (k == i) {
-            fs = f[k];
-            cs = c[k] - f[k];
-          }
-        enc[r] = cs | (fs << 16);
-      }
+      const uint32_t pair = enc_pair(o, lane, s);
+      if ((s >> 3) == lane) enc[r] = pair;
     }
   }
 }
@@ -403,8 +453,16 @@ constexpr int kPredSmem = 1024 + kPredLg + kPTile * kLogStride;
 
 __device__ int g_pred_error = 0;
 
-// 8 consecutive fp32 columns of this thread's TMEM lane, as integers.
-__device__ __forceinline__ void tmem_ld8i(uint32_t taddr, int32_t (&v)[8]) {
+// fp32 x holding an integer |x| < 2^22: x + 1.5 2^23 has unit spacing, so
+// its bits are kMagicBits + x exactly; (bits - (kMagicBits - b)) = x + b.
+constexpr float kMagic = 12582912.0f;
+constexpr uint32_t kMagicBits = 0x4B400000u;
+__device__ __forceinline__ int32_t acc_plus(float x, int32_t off) {
+  return (int32_t)(__float_as_uint(x + kMagic) - (uint32_t)off);
+}
+
+// 8 consecutive fp32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld8f(uint32_t taddr, float (&v)[8]) {
   uint32_t r[8];
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
@@ -413,7 +471,7 @@ __device__ __forceinline__ void tmem_ld8i(uint32_t taddr, int32_t (&v)[8]) {
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-  for (int i = 0; i < 8; i++) v[i] = __float2int_rn(__uint_as_float(r[i]));
+  for (int i = 0; i < 8; i++) v[i] = __uint_as_float(r[i]);
 }
 
 // 8 values (v - z) as bf16: chunk c of row `row` of a 64-byte-row,
@@ -450,14 +508,20 @@ k_predictor_tc(DLayer P1, DPred2 P2, const uint32_t* __restrict__ lut,
     tc::mbar_init(&mbar, 1);
     tc::fence_mbar_init();
   }
+  // requantisation in the high-word form when every multiplier of a layer
+  // admits it; accumulators leave TMEM as fp32 holding integers below 2^22
+  // in magnitude (32 products of at most 255 x 127), converted exactly by
+  // adding 1.5 2^23 and reading the bits, the bias folded into the offset
+  const bool fast2 = __syncthreads_and(t >= 256 || hi_ok(P2.mult[t], P2.shift));
+  const bool fast1 = __syncthreads_and(t >= 32 || hi_ok(P1.mult[t], P1.shift));
   if (t < 256) {
-    sB2[t] = P2.bias[t];
-    sM2[t] = P2.mult[t];
+    sB2[t] = (int32_t)(kMagicBits - (uint32_t)P2.bias[t]);
+    sM2[t] = fast2 ? hi_scale(P2.mult[t], P2.shift) : P2.mult[t];
     slut[t] = lut[t];
   }
   if (t < 32) {
-    sB1[t] = P1.bias[t];
-    sM1[t] = P1.mult[t];
+    sB1[t] = (int32_t)(kMagicBits - (uint32_t)P1.bias[t]);
+    sM1[t] = fast1 ? hi_scale(P1.mult[t], P1.shift) : P1.mult[t];
     sS1[t] = P1.prelu ? P1.slope[t] : 0;
   }
   {  // the weight images: layer 1 (2 KB) and layer 2 (16 KB)
@@ -473,6 +537,8 @@ k_predictor_tc(DLayer P1, DPred2 P2, const uint32_t* __restrict__ lut,
   __syncthreads();
   tc::tc_fence_after();
   const uint32_t tbase = tslot;
+  int ck[8];
+  tie_keys(lane, ck);
   const int quad = w & 3, cg = w >> 2;  // TMEM lane quadrant, column group
   const int erow = quad * 32 + lane;    // tile row this thread handles in the epilogues
   const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
@@ -521,14 +587,15 @@ k_predictor_tc(DLayer P1, DPred2 P2, const uint32_t* __restrict__ lut,
     tc::tc_fence_after();
     // ---- layer-1 epilogue: 8 columns a warp; (h - z2) as bf16
     {
+      float fv[8];
       int32_t v[8];
-      tmem_ld8i(tbase + lane_off + 8 * cg, v);
+      tmem_ld8f(tbase + lane_off + 8 * cg, fv);
 #pragma unroll
       for (int i = 0; i < 8; i++) {
         const int c = 8 * cg + i;
-        int32_t a = v[i] + sB1[c];
+        int32_t a = acc_plus(fv[i], sB1[c]);
         if (P1.prelu) a = prelu(a, sS1[c]);
-        v[i] = requant(a, sM1[c], P1.shift, P1.z_out);
+        v[i] = fast1 ? requant_hi(a, sM1[c], P1.z_out) : requant(a, sM1[c], P1.shift, P1.z_out);
       }
       bf16_chunk8(v, P2.z_in, sA2, erow, cg);
     }
@@ -561,9 +628,10 @@ k_predictor_tc(DLayer P1, DPred2 P2, const uint32_t* __restrict__ lut,
 #pragma unroll
       for (int i = 0; i < 16; i++) {
         const int c = c0 + i;
-        const int q = c < kNsym ? requant(__float2int_rn(f[i]) + sB2[c], sM2[c], P2.shift,
-                                          P2.z_out)
-                                : 0;
+        const int32_t a = acc_plus(f[i], sB2[c]);
+        const int q = c >= kNsym ? 0
+                      : fast2    ? requant_hi(a, sM2[c], P2.z_out)
+                                 : requant(a, sM2[c], P2.shift, P2.z_out);
         pk[i >> 2] |= (uint32_t)(uint8_t)q << (8 * (i & 3));
       }
       *reinterpret_cast<uint4*>(sLg + erow * kLogStride + c0) =
@@ -578,34 +646,26 @@ k_predictor_tc(DLayer P1, DPred2 P2, const uint32_t* __restrict__ lut,
       const int64_t r = r0 + tr;
       if (r >= n) break;
       const uint2 raw = *reinterpret_cast<const uint2*>(sLg + tr * kLogStride + 8 * lane);
-      const int8_t* lb = reinterpret_cast<const int8_t*>(&raw);
       int l[8];
 #pragma unroll
-      for (int i = 0; i < 8; i++) l[i] = lb[i];
+      for (int i = 0; i < 4; i++) {
+        l[i] = (int)(raw.x << (24 - 8 * i)) >> 24;  // sign-extended byte i
+        l[4 + i] = (int)(raw.y << (24 - 8 * i)) >> 24;
+      }
       if (mode == kPredLogits) {
 #pragma unroll
         for (int i = 0; i < 8; i++)
           if (lane * 8 + i < kNsym) logits[r * kNsym + lane * 8 + i] = (int8_t)l[i];
         continue;
       }
-      uint32_t f[8], c[8];
-      softmax_freq(l, slut, lane, f);
-      cumulate(f, lane, c);
+      SoftRow o;
+      softmax_row(l, ck, lane == 31, slut, o);
       if (mode == kPredCdf) {
-        store_cdf_row(c, lane, cdf + r * 256);
+        store_cdf_row(o, lane, cdf + r * 256);
       } else {
         const int s = (int)codes[r] - 1;
-        if ((s >> 3) == lane) {
-          const int i = s & 7;
-          uint32_t fs = 0, cs = 0;
-#pragma unroll
-          for (int k = 0; k < 8; k++)
-            if (k == i) {
-              fs = f[k];
-              cs = c[k] - f[k];
-            }
-          enc[r] = cs | (fs << 16);
-        }
+        const uint32_t pair = enc_pair(o, lane, s);
+        if ((s >> 3) == lane) enc[r] = pair;
       }
     }
   }

@@ -9,8 +9,8 @@
 // exists for as long as the library is loaded, instead of allocating it per
 // call like lpc_kernel_map does.
 //
-// The array is a fixed 2^19-slot table (6 MiB of keys and rows, plus two
-// control words), enough for 262,144 nodes at a load factor of at most 1/2.
+// The array is a fixed 2^19-slot table (8 MiB of 16-byte key and row slots,
+// plus two control words), enough for 262,144 nodes at a load factor of at most 1/2.
 // Every GPU that loads this library holds that memory until the process
 // exits.  All calls share the one table: concurrent calls whose work
 // overlaps on a GPU (different streams, or different host threads) race and
@@ -27,11 +27,10 @@ namespace {
 
 constexpr int64_t kSlots = int64_t(1) << 19;
 constexpr int64_t kMaxNodes = kSlots / 2;
-constexpr size_t kKeyBytes = 8 * kSlots;
-constexpr size_t kValBytes = 4 * kSlots;
+constexpr size_t kSlotBytes = 16 * kSlots;
 constexpr size_t kCtlBytes = 256;  // node count (int64) and error word (int)
 
-__device__ __align__(256) unsigned char g_static_table[kKeyBytes + kValBytes + kCtlBytes];
+__device__ __align__(256) unsigned char g_static_table[kSlotBytes + kCtlBytes];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
@@ -67,11 +66,10 @@ extern "C" int lpc_kernel_map_noalloc(const uint64_t* d_keys, int64_t N, int dep
   if (int s = table_address(&base)) return s;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   lpc::HashTable h;
-  h.keys = reinterpret_cast<uint64_t*>(base);
-  h.vals = reinterpret_cast<uint32_t*>(base + kKeyBytes);
+  h.slots = reinterpret_cast<ulonglong2*>(base);
   h.cap = kSlots;
-  int64_t* d_n = reinterpret_cast<int64_t*>(base + kKeyBytes + kValBytes);
-  int* d_err = reinterpret_cast<int*>(base + kKeyBytes + kValBytes + 8);
+  int64_t* d_n = reinterpret_cast<int64_t*>(base + kSlotBytes);
+  int* d_err = reinterpret_cast<int*>(base + kSlotBytes + 8);
   int64_t slots = 1024;
   while (slots < 2 * N) slots <<= 1;
   const int64_t n_host = N;

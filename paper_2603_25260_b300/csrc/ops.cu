@@ -163,14 +163,27 @@ int lpc_kernel_map(const uint64_t* d_keys, int64_t N, int depth, int32_t* d_nbr,
     while (slots < 2 * N) slots <<= 1;
   HashTable h;
   h.cap = slots;
-  h.keys = t.get<uint64_t>(slots);
-  h.vals = t.get<uint32_t>(slots);
+  h.slots = t.get<ulonglong2>(slots);
   int64_t* d_n = dev_count(t, N, st);
   int* d_err = t.get<int>(1);
-  if (!h.keys || !h.vals || !d_n || !d_err) return LPC_CUDA_ERROR;
+  if (!h.slots || !d_n || !d_err) return LPC_CUDA_ERROR;
   cudaMemsetAsync(d_err, 0, 4, st);
   launch_kernel_map(d_keys, d_n, N, nullptr, depth, h, slots, d_nbr, d_err, st);
   return finish(st, d_err);
+}
+
+int lpc_kernel_map_child(const uint64_t* d_ckeys, const uint32_t* d_cpar, int64_t Nc,
+                         const int32_t* d_pnbr, const uint8_t* d_pcode, const uint32_t* d_poff,
+                         int32_t* d_nbr, uint64_t stream) {
+  if (Nc < 0 || (Nc > 0 && (!d_ckeys || !d_cpar || !d_pnbr || !d_pcode || !d_poff || !d_nbr)))
+    return LPC_INVALID_ARG;
+  if (Nc == 0) return LPC_OK;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  Tmp t;
+  int64_t* d_n = dev_count(t, Nc, st);
+  if (!d_n) return LPC_CUDA_ERROR;
+  launch_kernel_map_child(d_ckeys, d_cpar, d_n, Nc, d_pnbr, d_pcode, d_poff, d_nbr, st);
+  return finish(st, nullptr);
 }
 
 int lpc_conv333_variant(const uint64_t* d_keys, int64_t N, int depth, const int8_t* d_x, int cin,

@@ -66,6 +66,7 @@ def lib():
             "lpc_build_levels": (I32, [P, I64, I32, P, P, P, I64, C.c_uint64]),
             "lpc_kernel_map": (I32, [P, I64, I32, P, I32, C.c_uint64]),
             "lpc_kernel_map_noalloc": (I32, [P, I64, I32, P, C.c_uint64]),
+            "lpc_kernel_map_child": (I32, [P, P, I64, P, P, P, P, C.c_uint64]),
             "lpc_conv333": (I32, [P, I64, I32, P, I32, I32, P, P, P, I32, P, I32, I32, P,
                                   C.c_uint64]),
             "lpc_conv333_variant": (I32, [P, I64, I32, P, I32, I32, P, P, P, I32, P, I32, I32, P,
@@ -326,6 +327,19 @@ def kernel_map(keys: torch.Tensor, depth: int, table_log2: int = 0) -> torch.Ten
     nbr = torch.empty((max(N, 1), 27), dtype=torch.int32, device="cuda")
     _ops_check(lib().lpc_kernel_map(keys.data_ptr() if N else None, N, depth, nbr.data_ptr(),
                                     table_log2, _stream()), "lpc_kernel_map")
+    return nbr[:N]
+
+
+def kernel_map_child(ckeys, cpar, pnbr, pcode, poff) -> torch.Tensor:
+    """Kernel map of a level from its parent level's map (no hash table)."""
+    ckeys, cpar = _dev(ckeys, torch.int64), _dev(cpar, torch.int32)
+    pnbr, pcode, poff = _dev(pnbr, torch.int32), _dev(pcode, torch.uint8), _dev(poff, torch.int32)
+    N = ckeys.shape[0]
+    nbr = torch.empty((max(N, 1), 27), dtype=torch.int32, device="cuda")
+    _ops_check(lib().lpc_kernel_map_child(ckeys.data_ptr() if N else None,
+                                          cpar.data_ptr() if N else None, N, pnbr.data_ptr(),
+                                          pcode.data_ptr(), poff.data_ptr(), nbr.data_ptr(),
+                                          _stream()), "lpc_kernel_map_child")
     return nbr[:N]
 
 

@@ -263,7 +263,10 @@ class Frame:
                 op += N + 1
         for d in range(L):
             self.Y[d] = self.codes[d].long()
-        self.nbr = {d: lpc.kernel_map(self.keys[d], d) for d in (self.b, self.t)}
+        b, t = self.b, self.t
+        self.nbr = {b: lpc.kernel_map(self.keys[b], b)}
+        self.nbr[t] = lpc.kernel_map_child(self.keys[t], self.par[t], self.nbr[b], self.codes[b],
+                                           self.off[b])
 
 
 # ------------------------------------------------------------------ model --

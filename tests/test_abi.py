@@ -28,6 +28,7 @@ def test_headers_declare_the_boundary():
                  "decode_frame", "probs_level", "encode_batch", "decode_batch",
                  "lpc_build_levels", "lpc_kernel_map", "lpc_conv333", "lpc_down_s2",
                  "lpc_up_prune", "lpc_softmax_cdf", "lpc_kernel_map_noalloc",
+                 "lpc_kernel_map_child",
                  "lpc_t_conv_fwd", "lpc_t_conv_bwd", "lpc_t_up_fwd", "lpc_t_up_bwd",
                  "lpc_t_down_fwd", "lpc_t_down_bwd", "lpc_t_embed_fwd", "lpc_t_embed_bwd",
                  "lpc_t_prelu_fwd", "lpc_t_prelu_bwd", "lpc_t_fq_fwd", "lpc_t_fq_bwd",

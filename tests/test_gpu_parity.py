@@ -78,7 +78,8 @@ def test_out_of_range_coordinate_is_rejected(lpc):
 
 # -------------------------------------------------------------- kernel map --
 
-@pytest.mark.parametrize("n,depth,seed", [(1, 4, 1), (700, 5, 2), (5000, 7, 3), (40000, 12, 4)])
+@pytest.mark.parametrize("n,depth,seed", [(1, 4, 1), (700, 5, 2), (5000, 7, 3), (40000, 12, 4),
+                                          (3000, 20, 8), (3000, 21, 9)])
 def test_kernel_map(lpc, n, depth, seed):
     xyz = synth.random_cloud(n, depth, seed)
     keys = O.leaf_keys(xyz, depth)
@@ -98,6 +99,40 @@ def test_kernel_map(lpc, n, depth, seed):
             if 0 <= qx < side and 0 <= qy < side and 0 <= qz < side:
                 want = pos.get(O.morton(qx, qy, qz, depth), -1)
             assert nbr[i, o] == want
+
+
+def _brute_map(keys, depth):
+    """27-neighbour rows of Morton keys by coordinates and a dictionary."""
+    pos = {int(k): i for i, k in enumerate(keys.tolist())}
+    side = 1 << depth
+    out = np.full((len(keys), 27), -1, dtype=np.int32)
+    for i, k in enumerate(keys.tolist()):
+        x = y = z = 0
+        for b in range(depth):
+            x |= ((k >> (3 * b + 2)) & 1) << b
+            y |= ((k >> (3 * b + 1)) & 1) << b
+            z |= ((k >> (3 * b)) & 1) << b
+        for o in range(27):
+            qx, qy, qz = x + o // 9 - 1, y + (o // 3) % 3 - 1, z + o % 3 - 1
+            if 0 <= qx < side and 0 <= qy < side and 0 <= qz < side:
+                out[i, o] = pos.get(O.morton(qx, qy, qz, depth), -1)
+    return out
+
+
+@pytest.mark.parametrize("n,L,d,seed", [(1, 6, 3, 1), (900, 8, 6, 2), (6000, 12, 9, 3),
+                                        (4000, 19, 14, 4)])
+def test_kernel_map_child(lpc, n, L, d, seed):
+    """The map of depth d derived from the map of depth d - 1 (octree
+    neighbour rule) equals the brute-force map; every input is the oracle's."""
+    xyz = synth.random_cloud(n, L, seed)
+    ok, oc = O.build_levels(xyz, L)
+    pk, ck, pcode = ok[d - 1], ok[d], oc[d - 1]
+    cpar = np.searchsorted(pk, ck >> np.uint64(3)).astype(np.int32)
+    poff = np.concatenate([[0], np.cumsum([bin(int(c)).count("1") for c in pcode])])
+    pnbr = _brute_map(pk, d - 1)
+    got = lpc.kernel_map_child(_cuda(ck.view(np.int64)), _cuda(cpar), _cuda(pnbr), _cuda(pcode),
+                               _cuda(poff.astype(np.int32))).cpu().numpy()
+    assert np.array_equal(got, _brute_map(ck, d))
 
 
 def test_hash_full_is_reported(lpc):
