@@ -107,6 +107,71 @@ void Pool::wait(int group) {
 }
 
 // ------------------------------------------------------------ bitstream --
+// ------------------------------------------------- coarse-level decoding --
+// The coarse levels of a frame form a chain: N_d, the symbol count of level
+// d, is the popcount sum of the codes of level d - 1.  Every decoded code of
+// level d - 1 adds its popcount to a lower bound of N_d that level d's task
+// reads, and level d decodes only below that bound (never past N_d), so the
+// levels of a frame run side by side and the frame takes about as long as
+// its largest level instead of the sum.  Tasks wait only on the task of the
+// level above, submitted before them to the first-in first-out pool, so a
+// waited-on task is always running or done.
+namespace {
+
+struct CoarsePipe {
+  std::atomic<int64_t> avail[kMaxDepth + 1];  // codes of level d known to exist
+  std::atomic<bool> fin[kMaxDepth + 1];       // avail[d] is N_d
+  CoarsePipe() {
+    for (int d = 0; d <= kMaxDepth; d++) {
+      avail[d].store(d == 0 ? 1 : 0);
+      fin[d].store(d == 0);
+    }
+  }
+};
+constexpr int kMaxCoarseTasks = 64;
+constexpr int64_t kCoarseBatch = 128;  // codes decoded between bound updates
+
+void coarse_level(Frame& F, int d, CoarsePipe& P, int64_t maxp, std::atomic<int>& status) {
+  RangeDecoder dec(F.in + F.soff[d], (size_t)F.slen[d]);
+  AdaptiveModel m;
+  std::vector<uint8_t>& Y = F.coarse[d];
+  int64_t i = 0, pc = 0;
+  const bool last = d + 1 >= F.b;
+  for (;;) {
+    const bool fin = P.fin[d].load(std::memory_order_acquire);
+    const int64_t a = P.avail[d].load(std::memory_order_acquire);
+    if (status.load(std::memory_order_relaxed)) return;
+    if (i >= a) {
+      if (fin) break;
+      std::this_thread::yield();
+      continue;
+    }
+    const int64_t stop = std::min(a, i + kCoarseBatch);
+    if ((int64_t)Y.size() < stop) Y.resize((size_t)std::max<int64_t>(stop, 2 * (int64_t)Y.size()));
+    for (; i < stop; i++) {
+      const int y = m.decode(dec) + 1;
+      Y[(size_t)i] = (uint8_t)y;
+      pc += __builtin_popcount((unsigned)y);
+    }
+    if (dec.bad()) {
+      status = LPC_CORRUPT_STREAM;
+      return;
+    }
+    if (pc > maxp) {
+      status = LPC_CAPACITY;
+      return;
+    }
+    if (!last) P.avail[d + 1].store(pc, std::memory_order_release);
+  }
+  Y.resize((size_t)i);
+  if (!last) {
+    P.avail[d + 1].store(pc, std::memory_order_release);
+    P.fin[d + 1].store(true, std::memory_order_release);
+  }
+}
+
+}  // namespace
+
 // "LPC1", u8 version, u8 L, u8 b, u8 t, u8 C, u8 flags (bit0: empty frame),
 // u64 blob hash (little endian), varint chunk, varint n_sub, n_sub varint
 // lengths, then the substreams: coarse levels 0..b-1 (adaptive model, one
@@ -1103,9 +1168,22 @@ int Codec::decode(int nf, const uint8_t* const* in, const size_t* lens, int32_t*
         }
       }
     };
-    for (int f = 1; f < nd; f++) pool_->submit(0, [&, f] { coarse(f); });
-    coarse(0);
-    pool_->wait(0);
+    int tasks = 0;
+    for (int f = 0; f < nd; f++) tasks += fr_[f].b;
+    if (tasks <= pool_->size() && tasks <= kMaxCoarseTasks) {
+      // few frames: every level its own task, pipelined within a frame
+      std::vector<CoarsePipe> pipes(nd);
+      for (int f = 0; f < nd; f++) fr_[f].coarse.assign(fr_[f].b, {});
+      for (int f = 0; f < nd; f++)
+        for (int d = 0; d < fr_[f].b; d++)
+          if (f || d) pool_->submit(0, [&, f, d] { coarse_level(fr_[f], d, pipes[f], maxp, cstat); });
+      coarse_level(fr_[0], 0, pipes[0], maxp, cstat);
+      pool_->wait(0);
+    } else {
+      for (int f = 1; f < nd; f++) pool_->submit(0, [&, f] { coarse(f); });
+      coarse(0);
+      pool_->wait(0);
+    }
   }
   if (cstat == LPC_CORRUPT_STREAM) return fail(LPC_CORRUPT_STREAM, "decode: corrupt coarse substream");
   if (cstat == LPC_CAPACITY) return fail(LPC_CAPACITY, "decode: frame exceeds max_points");
