@@ -119,10 +119,40 @@ def peaks():
     return 6400.0, 2032.0, "fallback"
 
 
+def bf16_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f).get("bf16_tflops", 1800.0)
+    return 1800.0
+
+
 # The dp4a integer ALU peak: 148 SMs x 128 lanes x 4 int8 MACs x 2 ops per
 # clock at the maximum SM clock (unit counts and clock of the part).
 def alu_peak_tops(sm_mhz: float) -> float:
     return 148 * 128 * 4 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def family_rooflines(fams: dict, steps: float, hbm: float, bf16: float | None) -> dict:
+    """Per kernel family, from a profiling pass (CUDA events around each
+    launch): algorithmic bytes per launch over the mean launch time against
+    the measured copy bandwidth; for the tensor-core families also their
+    algorithmic MACs x 2 against the measured bf16 peak."""
+    out = {}
+    for name, v in fams.items():
+        if v["launches"] <= 0 or v["ms"] <= 0:
+            continue
+        t = v["ms"] / v["launches"] / 1e3
+        gbs = v["bytes"] / v["launches"] / t / 1e9
+        e = {"ms_per_launch": round(1e3 * t, 4), "launches_per_step": v["launches"] / steps,
+             "hbm_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4)}
+        if v["ops"] > 0:
+            tops = v["ops"] / v["launches"] / t / 1e12
+            e["tops"] = round(tops, 3)
+            if name == "conv333" and bf16:
+                e["tensor_frac_of_bf16"] = round(tops / bf16, 5)
+        out[name] = e
+    return out
 
 
 KERNEL_SOURCES = {
@@ -381,6 +411,36 @@ def run_ours(args):
                    "encode_mpts": round(n / (he / 1e3) / 1e6, 4),
                    "decode_mpts": round(n / (hd / 1e3) / 1e6, 4)}
 
+    # the same step with the exported blob of the trained twin (realistic
+    # bits per point: skewed predictions, fewer coded bytes)
+    trained = None
+    from paper_2603_25260_b300 import export
+    if os.path.exists(export.TRAINED_BLOB):
+        with open(export.TRAINED_BLOB, "rb") as f:
+            tcodec = lpc.Codec(f.read(), spec.L, n, chunk=args.chunk)
+        for _ in range(max(args.warmup, 10)):
+            ln = tcodec.encode_into(x, outbuf)
+            tcodec.decode(outbuf[:ln].tobytes(), out=out_dev)
+        tms = []
+        for _ in range(5):
+            flush.zero_()
+            a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            a.record(stream)
+            ln = tcodec.encode_into(x, outbuf)
+            b.record(stream)
+            tcodec.decode(outbuf[:ln].tobytes(), out=out_dev)
+            c.record(stream)
+            torch.cuda.synchronize()
+            tms.append((a.elapsed_time(b), b.elapsed_time(c)))
+        tcodec.close()
+        te = statistics.median(t[0] for t in tms)
+        td = statistics.median(t[1] for t in tms)
+        trained = {"blob": os.path.relpath(export.TRAINED_BLOB, ROOT),
+                   "bits_per_point": round(8 * ln / n, 4),
+                   "value": round(n / ((te + td) / 1e3) / 1e6, 4),
+                   "encode_mpts": round(n / (te / 1e3) / 1e6, 4),
+                   "decode_mpts": round(n / (td / 1e3) / 1e6, 4)}
+
     # batched form: the mixed-size 64-frame batch, whole batch per step
     batched = None
     if not args.no_batch and args.batch_frames > 0:
@@ -411,11 +471,21 @@ def run_ours(args):
             bt.append((a.elapsed_time(b), b.elapsed_time(c)))
         be = statistics.median(t[0] for t in bt)
         bd = statistics.median(t[1] for t in bt)
+        # one profiled (untimed) pass for the per-family breakdown
+        bcodec.profile((1 << len(lpc.Codec.FAMILIES)) - 1)
+        spans = bcodec.encode_batch_into(xs, Ls, bbuf)
+        bcodec.decode_batch_from(bbuf, spans, bouts)
+        torch.cuda.synchronize()
+        bfams = bcodec.profile_read()
+        bcodec.profile(0)
         batched = {"frames": len(frames), "points": npts,
                    "value": round(npts / ((be + bd) / 1e3) / 1e6, 4),
                    "encode_mpts": round(npts / (be / 1e3) / 1e6, 4),
                    "decode_mpts": round(npts / (bd / 1e3) / 1e6, 4),
-                   "bits_per_point": round(8 * sum(n for _, n in spans) / npts, 4)}
+                   "bits_per_point": round(8 * sum(n for _, n in spans) / npts, 4),
+                   "families": {k: {"ms": round(v["ms"], 4), "launches": v["launches"]}
+                                for k, v in bfams.items()},
+                   "rooflines": family_rooflines(bfams, 1, peaks()[0], bf16_peak())}
         bcodec.close()
 
     train = None if args.no_train else train_leg(args, flush, stream)
@@ -473,6 +543,7 @@ def run_ours(args):
         "bits_per_point": round(8 * nbytes / n, 4),
         "batched": batched,
         "host_coding": host_coding,
+        "trained_blob": trained,
         "train": train,
         "e2e": {"value": round(e2e_value, 4), "unit": "Mpoints/s",
                 "step_ms": [round(t, 3) for t in e2e_ms], "warmup_steps": e2e_warm,
@@ -483,6 +554,7 @@ def run_ours(args):
         "roofline": roof,
         "families": {k: {"ms": round(v["ms"], 4), "launches": v["launches"]}
                      for k, v in fams.items()},
+        "rooflines": family_rooflines(fams, 2, hbm, bf16_peak()),
         "cpu_baseline": cpu,
         "clocks": clk,
     }

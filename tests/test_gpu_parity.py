@@ -278,6 +278,24 @@ def test_encode_byte_identical_config1(lpc, blob, c1):
     assert cod.encode(_cuda(c1)) == O.encode(blob, c1, L)
 
 
+@pytest.mark.parametrize("n,L,seed", [(0, 12, 0), (20000, 16, 8)])
+def test_trained_blob_byte_identical(lpc, c1, n, L, seed):
+    """The exported blob of the trained twin (other value ranges than the
+    seeded blob: larger biases, skewed predictions): same streams as the
+    oracle, lossless round trip."""
+    from paper_2603_25260_b300 import export
+    with open(export.TRAINED_BLOB, "rb") as f:
+        tb = f.read()
+    xyz = c1 if n == 0 else synth.random_cloud(n, L, seed)
+    cod = _codec(lpc, tb, L, xyz.shape[0])
+    data = cod.encode(_cuda(xyz))
+    assert data == O.encode(tb, xyz, L)
+    dec = cod.decode(data).cpu().numpy()
+    assert np.array_equal(O.leaf_keys(dec, L), O.leaf_keys(xyz, L))
+    got = lpc.u16(cod.probs_level(_cuda(xyz), L - 1))
+    assert np.array_equal(got, O.probs_level(tb, xyz, L, L - 1))
+
+
 @pytest.mark.parametrize("host_coding", [False, True], ids=["device_rc", "host_rc"])
 @pytest.mark.parametrize("n,L,seed,chunk", [(1, 6, 1, 16384), (2, 7, 2, 16384),
                                             (3000, 10, 3, 100), (20000, 14, 4, 4096),
