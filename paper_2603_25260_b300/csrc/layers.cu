@@ -435,23 +435,44 @@ k_predictor_dp4a(DLayer P1, DPred2 P2, const uint32_t* __restrict__ lut,
 // warp per row.  Modes: full CDF row, the (C_s, f_s) pair of the true symbol
 // (encoder), or the logits (debug).
 //
-// One persistent CTA of 16 warps per SM walks tiles of 128 rows: the rows
+// One persistent CTA of 16 warps per SM, as two independent groups of 8
+// warps that take alternate tiles of 128 rows (own shared-memory tiles, own
+// half of TMEM, own mbarrier, own named barrier), so that one group's MMA
+// waits and loads overlap the other group's arithmetic.  Per tile: the rows
 // (F - z1) go to shared memory as bf16 (exact: |F - z1| <= 255), an M=128
 // N=32 K=32 MMA gives layer 1 in TMEM (every fp32 partial sum is an integer
-// below 2^23: 32 products of at most 255 * 127), the warps write (h - z2)
-// back as bf16 (warp w: TMEM lane quadrant w % 4, a quarter of the columns),
-// an M=128 N=256 K=32 MMA gives the 255 logits, which the warps requantise
-// into a shared logits tile; then every warp runs the softmax of 8 rows,
-// 8 symbols a lane.
+// below 2^22: 32 products of at most 255 * 127), the warps write (h - z2)
+// back as bf16 (warp: TMEM lane quadrant and half of the columns), an M=128
+// N=256 K=32 MMA gives the 255 logits, which the warps requantise into a
+// shared logits tile; then every warp runs the softmax of 16 rows, 8
+// symbols a lane.
 namespace {
 
 constexpr int kPTile = 128;
 constexpr int kPThreads = 512;
+constexpr int kPGroup = 256;     // threads of one group
 constexpr int kLogStride = 272;  // logits row stride in shared memory (conflict-free)
-constexpr int kPredB1 = 0, kPredB2 = 2048, kPredA1 = 18432, kPredA2 = 26624, kPredLg = 34816;
-constexpr int kPredSmem = 1024 + kPredLg + kPTile * kLogStride;
+constexpr int kPredB1 = 0, kPredB2 = 2048;  // weight images
+constexpr int kPredA = 18432;               // per group: A1 (8 KB), A2 (8 KB)
+constexpr int kPredLg = kPredA + 2 * 16384; // per group: logits tile
+constexpr int kPredSmem = 1024 + kPredLg + 2 * kPTile * kLogStride;
 
 __device__ int g_pred_error = 0;
+
+// Named barrier of one group (ids 1 and 2; 0 is __syncthreads).
+__device__ __forceinline__ void group_sync(int g) {
+  asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "n"(kPGroup) : "memory");
+}
+__device__ __forceinline__ bool group_sync_or(int g, bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n.reg .pred p, q;\nsetp.ne.u32 p, %1, 0;\nbar.red.or.pred q, %2, %3, p;\n"
+      "selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v), "r"(1 + g), "n"(kPGroup)
+      : "memory");
+  return r != 0;
+}
 
 // fp32 x holding an integer |x| < 2^22: x + 1.5 2^23 has unit spacing, so
 // its bits are kMagicBits + x exactly; (bits - (kMagicBits - b)) = x + b.
@@ -500,12 +521,13 @@ k_predictor_tc(DLayer P1, DPred2 P2, const uint32_t* __restrict__ lut,
       (reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
   __shared__ int32_t sB1[32], sM1[32], sS1[32], sB2[256], sM2[256];
   __shared__ uint32_t slut[256];
-  __shared__ uint64_t mbar;
+  __shared__ uint64_t mbars[2];
   __shared__ uint32_t tslot;
   const int t = threadIdx.x, w = t >> 5, lane = t & 31;
-  if (w == 0) tc::tmem_alloc(&tslot, 256);
+  if (w == 0) tc::tmem_alloc(&tslot, 512);
   if (t == 0) {
-    tc::mbar_init(&mbar, 1);
+    tc::mbar_init(&mbars[0], 1);
+    tc::mbar_init(&mbars[1], 1);
     tc::fence_mbar_init();
   }
   // requantisation in the high-word form when every multiplier of a layer
@@ -536,92 +558,97 @@ k_predictor_tc(DLayer P1, DPred2 P2, const uint32_t* __restrict__ lut,
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
-  const uint32_t tbase = tslot;
+  const int g = w >> 3, wl = w & 7, tl = t & (kPGroup - 1);  // group, warp and thread in it
+  const uint32_t tbase = tslot + 256 * g;
+  uint64_t* mbar = &mbars[g];
   int ck[8];
   tie_keys(lane, ck);
-  const int quad = w & 3, cg = w >> 2;  // TMEM lane quadrant, column group
-  const int erow = quad * 32 + lane;    // tile row this thread handles in the epilogues
+  const int quad = wl & 3, cg = wl >> 2;  // TMEM lane quadrant, column half
+  const int erow = quad * 32 + lane;      // tile row this thread handles in the epilogues
   const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
-  const uint32_t sA1 = tc::smem_u32(sm + kPredA1), sA2 = tc::smem_u32(sm + kPredA2);
+  const uint32_t sA1 = tc::smem_u32(sm + kPredA + g * 16384), sA2 = sA1 + 8192;
   const uint32_t sB1w = tc::smem_u32(sm + kPredB1), sB2w = tc::smem_u32(sm + kPredB2);
-  unsigned char* sLg = sm + kPredLg;
+  unsigned char* sLg = sm + kPredLg + g * (kPTile * kLogStride);
   const int64_t n = *d_n;
   const int64_t ntiles = (n + kPTile - 1) / kPTile;
   uint32_t phase = 0;
   bool ok = true;
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  for (int64_t tile = 2 * (int64_t)blockIdx.x + g; tile < ntiles; tile += 2 * (int64_t)gridDim.x) {
     const int64_t r0 = tile * kPTile;
-    // ---- layer-1 input: (F - z1) as bf16, thread = (row, 8-column chunk)
+    // ---- layer-1 input: (F - z1) as bf16, thread = (row, 16-column half)
     {
-      const int row = t >> 2, c = t & 3;
-      int32_t v[8];
+      const int row = tl >> 1, c2 = tl & 1;
+      int32_t v[2][8];
       if (r0 + row < n) {
-        const uint2 q = __ldg(reinterpret_cast<const uint2*>(F + (r0 + row) * f_stride) + c);
-        const int8_t* b = reinterpret_cast<const int8_t*>(&q);
+        const uint4 q = __ldg(reinterpret_cast<const uint4*>(F + (r0 + row) * f_stride) + c2);
+        const uint32_t wd[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
-        for (int k = 0; k < 8; k++) v[k] = b[k];
+        for (int k = 0; k < 16; k++) v[k >> 3][k & 7] = (int)(wd[k >> 2] << (24 - 8 * (k & 3))) >> 24;
       } else {
 #pragma unroll
-        for (int k = 0; k < 8; k++) v[k] = P1.z_in;
+        for (int k = 0; k < 16; k++) v[k >> 3][k & 7] = P1.z_in;
       }
-      bf16_chunk8(v, P1.z_in, sA1, row, c);
+      bf16_chunk8(v[0], P1.z_in, sA1, row, 2 * c2);
+      bf16_chunk8(v[1], P1.z_in, sA1, row, 2 * c2 + 1);
     }
     tc::fence_async_smem();
     tc::tc_fence_before();
-    __syncthreads();
-    if (t == 0) {
+    group_sync(g);
+    if (tl == 0) {
       tc::tc_fence_after();
 #pragma unroll
       for (int ks = 0; ks < 2; ks++)
         tc::mma_bf16(tbase, tc::smem_desc<64>(sA1 + ks * 32, 512),
                      tc::smem_desc<64>(sB1w + ks * 32, 512), tc::idesc_bf16(kPTile, 32),
                      ks ? 1u : 0u);
-      tc::mma_commit(&mbar);
+      tc::mma_commit(mbar);
     }
-    ok = tc::mbar_wait(&mbar, phase);
+    ok = tc::mbar_wait(mbar, phase);
     phase ^= 1;
-    if (__syncthreads_or(!ok)) {
+    if (group_sync_or(g, !ok)) {
       ok = false;
       break;
     }
     tc::tc_fence_after();
-    // ---- layer-1 epilogue: 8 columns a warp; (h - z2) as bf16
-    {
+    // ---- layer-1 epilogue: 16 columns a warp; (h - z2) as bf16
+#pragma unroll
+    for (int hh = 0; hh < 2; hh++) {
+      const int cb = 16 * cg + 8 * hh;
       float fv[8];
       int32_t v[8];
-      tmem_ld8f(tbase + lane_off + 8 * cg, fv);
+      tmem_ld8f(tbase + lane_off + cb, fv);
 #pragma unroll
       for (int i = 0; i < 8; i++) {
-        const int c = 8 * cg + i;
+        const int c = cb + i;
         int32_t a = acc_plus(fv[i], sB1[c]);
         if (P1.prelu) a = prelu(a, sS1[c]);
         v[i] = fast1 ? requant_hi(a, sM1[c], P1.z_out) : requant(a, sM1[c], P1.shift, P1.z_out);
       }
-      bf16_chunk8(v, P2.z_in, sA2, erow, cg);
+      bf16_chunk8(v, P2.z_in, sA2, erow, 2 * cg + hh);
     }
     tc::fence_async_smem();
     tc::tc_fence_before();
-    __syncthreads();
-    if (t == 0) {
+    group_sync(g);
+    if (tl == 0) {
       tc::tc_fence_after();
 #pragma unroll
       for (int ks = 0; ks < 2; ks++)
         tc::mma_bf16(tbase, tc::smem_desc<64>(sA2 + ks * 32, 512),
                      tc::smem_desc<64>(sB2w + ks * 32, 512), tc::idesc_bf16(kPTile, 256),
                      ks ? 1u : 0u);
-      tc::mma_commit(&mbar);
+      tc::mma_commit(mbar);
     }
-    ok = tc::mbar_wait(&mbar, phase);
+    ok = tc::mbar_wait(mbar, phase);
     phase ^= 1;
-    if (__syncthreads_or(!ok)) {
+    if (group_sync_or(g, !ok)) {
       ok = false;
       break;
     }
     tc::tc_fence_after();
-    // ---- logits: 64 columns a warp, requantised into the shared tile
+    // ---- logits: 128 columns a warp, requantised into the shared tile
 #pragma unroll
-    for (int g = 0; g < 4; g++) {
-      const int c0 = 64 * cg + 16 * g;
+    for (int gi = 0; gi < 8; gi++) {
+      const int c0 = 128 * cg + 16 * gi;
       float f[16];
       tc::tmem_ld16(tbase + lane_off + c0, f);
       uint32_t pk[4] = {0, 0, 0, 0};
@@ -638,11 +665,11 @@ k_predictor_tc(DLayer P1, DPred2 P2, const uint32_t* __restrict__ lut,
           make_uint4(pk[0], pk[1], pk[2], pk[3]);
     }
     tc::tc_fence_before();
-    __syncthreads();
-    // ---- integer softmax, one warp per row, 8 rows a warp
+    group_sync(g);
+    // ---- integer softmax, one warp per row, 16 rows a warp
 #pragma unroll 1
-    for (int rr = 0; rr < kPTile / 16; rr++) {
-      const int tr = w * (kPTile / 16) + rr;
+    for (int rr = 0; rr < kPTile / 8; rr++) {
+      const int tr = wl * (kPTile / 8) + rr;
       const int64_t r = r0 + tr;
       if (r >= n) break;
       const uint2 raw = *reinterpret_cast<const uint2*>(sLg + tr * kLogStride + 8 * lane);
@@ -670,13 +697,13 @@ k_predictor_tc(DLayer P1, DPred2 P2, const uint32_t* __restrict__ lut,
     }
   }
   if (!ok) {
-    if (t == 0) atomicExch(&g_pred_error, 1);
-    tc::mbar_wait(&mbar, phase ^ 1);  // an MMA still in flight lands first
+    if (tl == 0) atomicExch(&g_pred_error, 1);
+    tc::mbar_wait(mbar, phase ^ 1);  // an MMA still in flight lands first
   }
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
-  if (w == 0) tc::tmem_dealloc(tbase, 256);
+  if (w == 0) tc::tmem_dealloc(tslot, 512);
 }
 
 }  // namespace
@@ -710,7 +737,7 @@ void launch_predictor(const DLayer& P1, const DPred2& P2, const uint32_t* lut, c
   if (n_host <= 0) return;
   if (variant == 1 && P1.Wtc && P2.Wtc) {
     const int64_t ntiles = (n_host + kPTile - 1) / kPTile;
-    const int blocks = (int)std::min<int64_t>(ntiles, 148);
+    const int blocks = (int)std::min<int64_t>((ntiles + 1) / 2, 148);  // two groups a CTA
     cudaFuncSetAttribute(k_predictor_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kPredSmem);
     k_predictor_tc<<<blocks, kPThreads, kPredSmem, st>>>(P1, P2, lut, F, f_stride, d_n, mode,
                                                            codes, cdf, enc, logits);
