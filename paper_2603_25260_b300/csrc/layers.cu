@@ -226,6 +226,15 @@ struct SoftRow {
   int first;      // lowest symbol with the maximum logit
 };
 
+// Byte i of w, sign-extended (a byte permute whose upper selectors
+// replicate the byte's sign bit).
+__device__ __forceinline__ int sext_byte(uint32_t w, int i) {
+  const uint32_t sel = (uint32_t)(i | ((8 | i) << 4) | ((8 | i) << 8) | ((8 | i) << 12));
+  uint32_t r;
+  asm("prmt.b32 %0, %1, 0, %2;" : "=r"(r) : "r"(w), "r"(sel));
+  return (int)r;
+}
+
 // Per-lane tie-break constants 255 - (8 lane + i) of the max keys.
 __device__ __forceinline__ void tie_keys(int lane, int (&ck)[8]) {
 #pragma unroll
@@ -519,7 +528,9 @@ k_predictor_tc(DLayer P1, DPred2 P2, const uint32_t* __restrict__ lut,
   extern __shared__ unsigned char smraw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
-  __shared__ int32_t sB1[32], sM1[32], sS1[32], sB2[256], sM2[256];
+  __shared__ int32_t sB1[32], sM1[32], sS1[32];
+  __shared__ __align__(16) int32_t sB2[256], sM2[256];
+  __shared__ __align__(16) long long sK2[256];
   __shared__ uint32_t slut[256];
   __shared__ uint64_t mbars[2];
   __shared__ uint32_t tslot;
@@ -537,8 +548,14 @@ k_predictor_tc(DLayer P1, DPred2 P2, const uint32_t* __restrict__ lut,
   const bool fast2 = __syncthreads_and(t >= 256 || hi_ok(P2.mult[t], P2.shift));
   const bool fast1 = __syncthreads_and(t >= 32 || hi_ok(P1.mult[t], P1.shift));
   if (t < 256) {
-    sB2[t] = (int32_t)(kMagicBits - (uint32_t)P2.bias[t]);
+    const uint32_t off = kMagicBits - (uint32_t)P2.bias[t];
+    sB2[t] = (int32_t)off;
     sM2[t] = fast2 ? hi_scale(P2.mult[t], P2.shift) : P2.mult[t];
+    // high-word form with the accumulator's bits v = off + a: a ms + 2^31 +
+    // z 2^32 = v ms + K, K = 2^31 + z 2^32 - off ms (one wide multiply-add)
+    sK2[t] = fast2 ? 2147483648ll + (long long)P2.z_out * 4294967296ll -
+                         (long long)off * (long long)sM2[t]
+                   : 0ll;
     slut[t] = lut[t];
   }
   if (t < 32) {
@@ -652,14 +669,33 @@ k_predictor_tc(DLayer P1, DPred2 P2, const uint32_t* __restrict__ lut,
       float f[16];
       tc::tmem_ld16(tbase + lane_off + c0, f);
       uint32_t pk[4] = {0, 0, 0, 0};
+      if (fast2) {
+        int32_t ms[16];
+        long long kk[16];
 #pragma unroll
-      for (int i = 0; i < 16; i++) {
-        const int c = c0 + i;
-        const int32_t a = acc_plus(f[i], sB2[c]);
-        const int q = c >= kNsym ? 0
-                      : fast2    ? requant_hi(a, sM2[c], P2.z_out)
-                                 : requant(a, sM2[c], P2.shift, P2.z_out);
-        pk[i >> 2] |= (uint32_t)(uint8_t)q << (8 * (i & 3));
+        for (int i = 0; i < 16; i += 4) {
+          const int4 m4 = *reinterpret_cast<const int4*>(sM2 + c0 + i);
+          ms[i] = m4.x, ms[i + 1] = m4.y, ms[i + 2] = m4.z, ms[i + 3] = m4.w;
+        }
+#pragma unroll
+        for (int i = 0; i < 16; i += 2) {
+          const longlong2 k2 = *reinterpret_cast<const longlong2*>(sK2 + c0 + i);
+          kk[i] = k2.x, kk[i + 1] = k2.y;
+        }
+#pragma unroll
+        for (int i = 0; i < 16; i++) {
+          const int32_t v = (int32_t)__float_as_uint(f[i] + kMagic);
+          const int q = min(max((int)(((long long)v * ms[i] + kk[i]) >> 32), -128), 127);
+          pk[i >> 2] |= (uint32_t)(uint8_t)(c0 + i >= kNsym ? 0 : q) << (8 * (i & 3));
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < 16; i++) {
+          const int c = c0 + i;
+          const int32_t a = acc_plus(f[i], sB2[c]);
+          const int q = c >= kNsym ? 0 : requant(a, sM2[c], P2.shift, P2.z_out);
+          pk[i >> 2] |= (uint32_t)(uint8_t)q << (8 * (i & 3));
+        }
       }
       *reinterpret_cast<uint4*>(sLg + erow * kLogStride + c0) =
           make_uint4(pk[0], pk[1], pk[2], pk[3]);
@@ -676,8 +712,8 @@ k_predictor_tc(DLayer P1, DPred2 P2, const uint32_t* __restrict__ lut,
       int l[8];
 #pragma unroll
       for (int i = 0; i < 4; i++) {
-        l[i] = (int)(raw.x << (24 - 8 * i)) >> 24;  // sign-extended byte i
-        l[4 + i] = (int)(raw.y << (24 - 8 * i)) >> 24;
+        l[i] = sext_byte(raw.x, i);
+        l[4 + i] = sext_byte(raw.y, i);
       }
       if (mode == kPredLogits) {
 #pragma unroll
