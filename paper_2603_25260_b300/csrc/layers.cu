@@ -70,10 +70,13 @@ __device__ __forceinline__ SmemLayer stage_layer(const DLayer& L, int32_t* sm) {
   return s;
 }
 
-static size_t smem_layer_bytes(const DLayer& L) {
+__host__ __device__ __forceinline__ size_t smem_layer_bytes_dev(const DLayer& L) {
   const int P = L.per_slice ? L.S : 1;
-  return sizeof(int32_t) * ((size_t)L.S * (L.cin / 4) * 32 + (size_t)L.S * 32 + 3 * (size_t)P * 32);
+  // rounded up to 16 bytes: staging buffers follow the layer image
+  return (sizeof(int32_t) * ((size_t)L.S * (L.cin / 4) * 32 + (size_t)L.S * 32 + 3 * (size_t)P * 32) +
+          15) & ~(size_t)15;
 }
+static size_t smem_layer_bytes(const DLayer& L) { return smem_layer_bytes_dev(L); }
 
 template <int CIN>
 __device__ __forceinline__ int32_t dot_slice(const int32_t (&x)[CIN / 4], const int32_t* W,
@@ -106,6 +109,14 @@ void launch_embed(const DEmb& E, const uint8_t* codes, const int64_t* d_n, int64
 }
 
 // ------------------------------------------------------------- up-prune --
+// A warp takes 32 consecutive children at a time: lane i reads child i's
+// parent row and slot (coalesced) and copies the parent's input row into the
+// warp's shared staging buffer with cp.async, so 32 rows are in flight per
+// warp instead of one dependent chain per child; the next 32 rows are copied
+// while the current ones are computed (two buffers).  Then the warp walks
+// the 32 children, lane = output channel, reading each row as a broadcast.
+constexpr int kUpGroup = 32;
+
 template <int CIN>
 __global__ void __launch_bounds__(kWarps * 32)
 k_up_prune(DLayer L, const uint64_t* __restrict__ ckey, const uint32_t* __restrict__ cpar,
@@ -113,34 +124,75 @@ k_up_prune(DLayer L, const uint64_t* __restrict__ ckey, const uint32_t* __restri
            int out_stride, int out_col) {
   extern __shared__ int32_t sm[];
   const SmemLayer s = stage_layer(L, sm);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int8_t* stage = reinterpret_cast<int8_t*>(sm + smem_layer_bytes_dev(L) / 4) +
+                  (size_t)w * 2 * kUpGroup * CIN;
   __syncthreads();
-  const int lane = threadIdx.x & 31;
   const int64_t n = *d_nc;
-  for (int64_t r = warp_id_global(); r < n; r += warps_total()) {
-    const uint32_t p = cpar[r];
-    const int c = (int)(ckey[r] & 7);
-    int32_t xv[CIN / 4];
-    load_row<CIN>(x + (int64_t)p * x_stride, xv);
-    int32_t acc = s.bias[c * 32 + lane] - L.z_in * s.wsum[c * 32 + lane];
-    acc = dot_slice<CIN>(xv, s.W, c, lane, acc);
-    if (L.prelu) acc = prelu(acc, s.slope[c * 32 + lane]);
-    out[r * out_stride + out_col + lane] = (int8_t)requant(acc, s.mult[c * 32 + lane], L.shift,
-                                                           L.z_out);
+  const int64_t step = warps_total() * kUpGroup;
+  // lane's child of group g0: slot, and its parent row copied into buffer b
+  auto issue = [&](int64_t g0, int b) -> int {
+    const int64_t r = g0 + lane;
+    int c = 0;
+    const int8_t* src = x;
+    if (r < n) {
+      c = (int)(__ldg(ckey + r) & 7);
+      src = x + (int64_t)__ldg(cpar + r) * x_stride;
+    }
+    const uint32_t dst = tc::smem_u32(stage + (b * kUpGroup + lane) * CIN);
+#pragma unroll
+    for (int k = 0; k < CIN / 16; k++) tc::cp_async16(dst + 16 * k, src + 16 * k, r < n);
+    tc::cp_async_commit();
+    return c;
+  };
+  int64_t g0 = warp_id_global() * kUpGroup;
+  int b = 0;
+  int c_cur = g0 < n ? issue(g0, 0) : 0;
+  for (; g0 < n; g0 += step, b ^= 1) {
+    const int c_next = g0 + step < n ? issue(g0 + step, b ^ 1) : 0;
+    if (g0 + step < n)
+      tc::cp_async_wait<1>();  // this group's copies have landed
+    else
+      tc::cp_async_wait<0>();
+    __syncwarp();
+    const int m = (int)(n - g0 < kUpGroup ? n - g0 : kUpGroup);
+    for (int j = 0; j < m; j++) {
+      const int c = __shfl_sync(0xffffffffu, c_cur, j);
+      int32_t xv[CIN / 4];
+      const int4* row = reinterpret_cast<const int4*>(stage + (b * kUpGroup + j) * CIN);
+#pragma unroll
+      for (int i = 0; i < CIN / 16; i++) {
+        const int4 t = row[i];
+        xv[4 * i] = t.x, xv[4 * i + 1] = t.y, xv[4 * i + 2] = t.z, xv[4 * i + 3] = t.w;
+      }
+      int32_t acc = s.bias[c * 32 + lane] - L.z_in * s.wsum[c * 32 + lane];
+      acc = dot_slice<CIN>(xv, s.W, c, lane, acc);
+      if (L.prelu) acc = prelu(acc, s.slope[c * 32 + lane]);
+      out[(g0 + j) * out_stride + out_col + lane] =
+          (int8_t)requant(acc, s.mult[c * 32 + lane], L.shift, L.z_out);
+    }
+    __syncwarp();  // buffer b is free for the group after next
+    c_cur = c_next;
   }
+  tc::cp_async_wait<0>();
 }
 
 void launch_up_prune(const DLayer& W, const uint64_t* ckey, const uint32_t* cpar,
                      const int64_t* d_nc, int64_t nc_host, const int8_t* x, int x_stride,
                      int8_t* out, int out_stride, int out_col, cudaStream_t st) {
   if (nc_host <= 0) return;
-  const size_t smem = smem_layer_bytes(W);
-  const int blocks = (int)std::min<int64_t>((nc_host + kWarps - 1) / kWarps, kBlocksRow);
-  if (W.cin == 32)
+  const size_t smem = smem_layer_bytes(W) + (size_t)kWarps * 2 * kUpGroup * W.cin;
+  const int blocks = (int)std::min<int64_t>((nc_host + kWarps * kUpGroup - 1) / (kWarps * kUpGroup),
+                                            kBlocksRow);
+  if (W.cin == 32) {
+    cudaFuncSetAttribute(k_up_prune<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_up_prune<32><<<blocks, kWarps * 32, smem, st>>>(W, ckey, cpar, d_nc, x, x_stride, out,
                                                       out_stride, out_col);
-  else
+  } else {
+    cudaFuncSetAttribute(k_up_prune<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_up_prune<64><<<blocks, kWarps * 32, smem, st>>>(W, ckey, cpar, d_nc, x, x_stride, out,
                                                       out_stride, out_col);
+  }
   count_launches(1);
 }
 
