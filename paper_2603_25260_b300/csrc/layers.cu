@@ -197,6 +197,15 @@ void launch_up_prune(const DLayer& W, const uint64_t* ckey, const uint32_t* cpar
 }
 
 // ------------------------------------------------------------ down (s2) --
+// A warp takes 16 consecutive parents at a time.  Their children are the
+// consecutive rows poff[p0] .. poff[p0 + 16] - 1 (at most 128): the warp
+// copies those input rows into its staging buffer with cp.async and their
+// slots (key & 7) beside them, the next 16 parents' rows while the current
+// ones are computed (two buffers); then it walks the parents, lane = output
+// channel, summing the children's slices.
+constexpr int kDownGroup = 16;
+constexpr int kDownRows = 8 * kDownGroup;
+
 template <int CIN>
 __global__ void __launch_bounds__(kWarps * 32)
 k_down(DLayer L, const uint64_t* __restrict__ ckey, const uint32_t* __restrict__ poff,
@@ -204,36 +213,84 @@ k_down(DLayer L, const uint64_t* __restrict__ ckey, const uint32_t* __restrict__
        int out_stride, int out_col) {
   extern __shared__ int32_t sm[];
   const SmemLayer s = stage_layer(L, sm);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  constexpr int kBuf = kDownRows * CIN + kDownRows;  // rows, then slots
+  int8_t* stage = reinterpret_cast<int8_t*>(sm + smem_layer_bytes_dev(L) / 4) + (size_t)w * 2 * kBuf;
   __syncthreads();
-  const int lane = threadIdx.x & 31;
   const int64_t n = *d_np;
-  for (int64_t p = warp_id_global(); p < n; p += warps_total()) {
-    int32_t acc = s.bias[lane];
-    const uint32_t r0 = poff[p], r1 = poff[p + 1];
-    for (uint32_t r = r0; r < r1; r++) {
-      const int c = (int)(ckey[r] & 7);
-      int32_t xv[CIN / 4];
-      load_row<CIN>(x + (int64_t)r * x_stride, xv);
-      acc -= L.z_in * s.wsum[c * 32 + lane];
-      acc = dot_slice<CIN>(xv, s.W, c, lane, acc);
+  const int64_t step = warps_total() * kDownGroup;
+  // lane j <= 16 holds poff[p0 + j] (clamped at the last parent)
+  auto issue = [&](int64_t p0, int b) -> uint32_t {
+    const int64_t pj = p0 + (lane <= kDownGroup ? lane : kDownGroup);
+    const uint32_t o = __ldg(poff + (pj < n ? pj : n));
+    const uint32_t o0 = __shfl_sync(0xffffffffu, o, 0), o1 = __shfl_sync(0xffffffffu, o, kDownGroup);
+    const int rows = min((int)(o1 - o0), kDownRows);  // 8 children a parent at most
+    int8_t* buf = stage + b * kBuf;
+    const uint32_t dst = tc::smem_u32(buf);
+    for (int k = lane; k < rows * (CIN / 16); k += 32) {
+      const int r = k / (CIN / 16), part = k % (CIN / 16);
+      tc::cp_async16(dst + r * CIN + 16 * part, x + (int64_t)(o0 + r) * x_stride + 16 * part, true);
     }
-    if (L.prelu) acc = prelu(acc, s.slope[lane]);
-    out[p * out_stride + out_col + lane] = (int8_t)requant(acc, s.mult[lane], L.shift, L.z_out);
+    tc::cp_async_commit();
+    for (int r = lane; r < rows; r += 32) buf[kDownRows * CIN + r] = (int8_t)(__ldg(ckey + o0 + r) & 7);
+    return o;
+  };
+  int64_t p0 = warp_id_global() * kDownGroup;
+  int b = 0;
+  uint32_t o_cur = p0 < n ? issue(p0, 0) : 0;
+  for (; p0 < n; p0 += step, b ^= 1) {
+    const uint32_t o_next = p0 + step < n ? issue(p0 + step, b ^ 1) : 0;
+    if (p0 + step < n)
+      tc::cp_async_wait<1>();
+    else
+      tc::cp_async_wait<0>();
+    __syncwarp();
+    const int8_t* buf = stage + b * kBuf;
+    const uint32_t o0 = __shfl_sync(0xffffffffu, o_cur, 0);
+    const int m = (int)(n - p0 < kDownGroup ? n - p0 : kDownGroup);
+    for (int j = 0; j < m; j++) {
+      const int r0 = min((int)(__shfl_sync(0xffffffffu, o_cur, j) - o0), kDownRows);
+      const int r1 = min((int)(__shfl_sync(0xffffffffu, o_cur, j + 1) - o0), kDownRows);
+      int32_t acc = s.bias[lane];
+      for (int r = r0; r < r1; r++) {
+        const int c = buf[kDownRows * CIN + r];
+        int32_t xv[CIN / 4];
+        const int4* row = reinterpret_cast<const int4*>(buf + r * CIN);
+#pragma unroll
+        for (int i = 0; i < CIN / 16; i++) {
+          const int4 t = row[i];
+          xv[4 * i] = t.x, xv[4 * i + 1] = t.y, xv[4 * i + 2] = t.z, xv[4 * i + 3] = t.w;
+        }
+        acc -= L.z_in * s.wsum[c * 32 + lane];
+        acc = dot_slice<CIN>(xv, s.W, c, lane, acc);
+      }
+      if (L.prelu) acc = prelu(acc, s.slope[lane]);
+      out[(p0 + j) * out_stride + out_col + lane] =
+          (int8_t)requant(acc, s.mult[lane], L.shift, L.z_out);
+    }
+    __syncwarp();  // buffer b is free for the group after next
+    o_cur = o_next;
   }
+  tc::cp_async_wait<0>();
 }
 
 void launch_down(const DLayer& W, const uint64_t* ckey, const uint32_t* poff, const int64_t* d_np,
                  int64_t np_host, const int8_t* x, int x_stride, int8_t* out, int out_stride,
                  int out_col, cudaStream_t st) {
   if (np_host <= 0) return;
-  const size_t smem = smem_layer_bytes(W);
-  const int blocks = (int)std::min<int64_t>((np_host + kWarps - 1) / kWarps, kBlocksRow);
-  if (W.cin == 32)
+  const size_t smem =
+      smem_layer_bytes(W) + (size_t)kWarps * 2 * ((size_t)kDownRows * W.cin + kDownRows);
+  const int blocks = (int)std::min<int64_t>(
+      (np_host + kWarps * kDownGroup - 1) / (kWarps * kDownGroup), kBlocksRow);
+  if (W.cin == 32) {
+    cudaFuncSetAttribute(k_down<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_down<32><<<blocks, kWarps * 32, smem, st>>>(W, ckey, poff, d_np, x, x_stride, out,
                                                   out_stride, out_col);
-  else
+  } else {
+    cudaFuncSetAttribute(k_down<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_down<64><<<blocks, kWarps * 32, smem, st>>>(W, ckey, poff, d_np, x, x_stride, out,
                                                   out_stride, out_col);
+  }
   count_launches(1);
 }
 
