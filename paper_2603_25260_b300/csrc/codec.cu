@@ -179,6 +179,9 @@ void coarse_level(Frame& F, int d, CoarsePipe& P, int64_t maxp, std::atomic<int>
 namespace {
 
 constexpr int kHdr = 18;
+// Batches of at least this many points build their three lowest coarse
+// heights with the multi-block scan.
+constexpr int64_t kCoarseScanPoints = 262144;
 constexpr int kMaxL = 19;  // 3 L Morton bits stay below the frame bits
 
 void put_varint(std::vector<uint8_t>& o, uint64_t v) {
@@ -311,7 +314,7 @@ int Codec::create(const lpc_config& cfg, const void* blob, size_t len) {
   add((void**)&d_keys0_, 8 * P);
   sort_.n_max = P;
   add((void**)&sort_.alt, 8 * P);
-  add((void**)&sort_.hist, 4 * 256 * sort_tiles(P));
+  add((void**)&sort_.hist, 4 * 256 * (sort_tiles(P) + 1));
   scan_.max_tiles = scan_tiles_for(P);
   add((void**)&scan_.tiles, 4 * scan_.max_tiles);
   hash_.cap = 1024;
@@ -519,8 +522,11 @@ int Codec::build_levels_device(int nf, const int32_t* const* xyz, const int64_t*
   // root; frames with a smaller depth carry their root up unchanged
   max_h_ = kHeights - 1;
   if (coarse) {
+    // large batches: the lowest coarse heights are big enough for the
+    // multi-block scan
     launch_coarse_up(key_[kHeights - 1], d_N_ + kHeights - 1, maxL, d_keys0_, sort_.alt,
-                     coarse_codes(kHeights), P_, d_cN_, nf, d_cfoff_, st_);
+                     coarse_codes(kHeights), P_, d_cN_, nf, d_cfoff_,
+                     total >= kCoarseScanPoints ? 3 : 0, P_, scan_, st_);
     max_h_ = std::max(maxL, kHeights - 1);
     if (max_h_ >= kHeights) {
       cudaMemcpyAsync(h_cN_ + kHeights, d_cN_ + kHeights, 8 * (max_h_ - kHeights + 1),
@@ -1370,9 +1376,12 @@ int Codec::expand_coarse_device(int nd) {
     cudaMemcpyAsync(coarse_codes(h), hc + hoff[h], (size_t)hcnt[h], cudaMemcpyHostToDevice, st_);
   cudaMemcpyAsync(code_[6], hc + hoff[kHeights - 1], (size_t)hcnt[kHeights - 1],
                   cudaMemcpyHostToDevice, st_);
+  for (int h = kHeights; h <= top; h++) h_cN_[h] = hcnt[h];
+  cudaMemcpyAsync(d_cN_ + kHeights, h_cN_ + kHeights, 8 * (size_t)(top - kHeights + 1),
+                  cudaMemcpyHostToDevice, st_);
   pbeg(kFamLevels);
-  launch_coarse_down(top_keys, top, coarse_codes(kHeights), P_, hcnt.data(), P_, pp[0], pp[1],
-                     key_[6], d_N_ + 6, d_err_, st_);
+  launch_coarse_down(top_keys, top, coarse_codes(kHeights), P_, hcnt.data(), d_cN_, P_, pp[0],
+                     pp[1], key_[6], d_N_ + 6, scan_, d_err_, st_);
   pend(kFamLevels, 21.0 * (double)tot, 0);
   return cuda_check("decode: coarse expansion");
 }

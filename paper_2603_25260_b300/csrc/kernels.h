@@ -18,7 +18,7 @@ int64_t launches_total();
 // Radix sort scratch for up to n_max keys.
 struct SortScratch {
   uint64_t* alt = nullptr;     // n_max keys
-  uint32_t* hist = nullptr;    // 256 * tiles(n_max)
+  uint32_t* hist = nullptr;    // 256 * (tiles(n_max) + 1): per-tile counts, digit totals
   int64_t n_max = 0;
 };
 int64_t sort_tiles(int64_t n);
@@ -80,12 +80,19 @@ void launch_expand(const uint64_t* pkeys, const uint8_t* pcodes, const int64_t* 
                    int64_t* d_nc, const ScanScratch& s, int* err, cudaStream_t st);
 
 // Coarse heights in one launch each (see octree.cu).
+// scan_heights: how many of the lowest coarse heights (7, 8, ...) take the
+// multi-block scan (large batches) before the single-block kernel; cap
+// bounds their sizes.
 void launch_coarse_up(const uint64_t* key6, const int64_t* d_n6, int top, uint64_t* k0,
                       uint64_t* k1, uint8_t* codes, int64_t stride, int64_t* cN, int nf,
-                      int64_t* foff, cudaStream_t st);
+                      int64_t* foff, int scan_heights, int64_t cap, const ScanScratch& s,
+                      cudaStream_t st);
+// counts: host copy of the coarse level sizes by height, d_counts the same
+// on the device (the large heights expand with the multi-block scan).
 void launch_coarse_down(const uint64_t* roots, int top, const uint8_t* codes, int64_t stride,
-                        const int64_t* counts, int64_t cap, uint64_t* k0, uint64_t* k1,
-                        uint64_t* key6, int64_t* n6, int* err, cudaStream_t st);
+                        const int64_t* counts, const int64_t* d_counts, int64_t cap, uint64_t* k0,
+                        uint64_t* k1, uint64_t* key6, int64_t* n6, const ScanScratch& s, int* err,
+                        cudaStream_t st);
 
 // ------------------------------------------------------ device range coding --
 // One substream: `rows` symbols starting at table / interval row `row`, its

@@ -44,22 +44,6 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* total,
   return r;
 }
 
-// In-place exclusive scan of a[0..len) by one block of 1024 threads.
-__global__ void __launch_bounds__(1024) k_scan_single(uint32_t* a, int64_t len) {
-  __shared__ uint32_t sm[32];
-  const int64_t per = (len + 1023) / 1024;
-  const int64_t b = threadIdx.x * per, e = std::min(len, b + per);
-  uint32_t s = 0;
-  for (int64_t i = b; i < e; i++) s += a[i];
-  uint32_t tot;
-  uint32_t run = block_excl_scan<1024>(s, &tot, sm);
-  for (int64_t i = b; i < e; i++) {
-    uint32_t v = a[i];
-    a[i] = run;
-    run += v;
-  }
-}
-
 // ------------------------------------------------------------ radix sort --
 constexpr int kRsThreads = 256, kRsItems = 16, kRsTile = kRsThreads * kRsItems;
 
@@ -80,15 +64,39 @@ k_rs_hist(const uint64_t* __restrict__ keys, int64_t n, int shift, uint32_t* his
   hist[(int64_t)threadIdx.x * nt + blockIdx.x] = h[threadIdx.x];
 }
 
+// Per digit (one block each): exclusive scan of the digit's tile counts over
+// the tiles, in place, and the digit's total into dtot[digit].
+__global__ void __launch_bounds__(1024) k_rs_digit_scan(uint32_t* hist, int64_t nt,
+                                                        uint32_t* dtot) {
+  __shared__ uint32_t sm[32];
+  uint32_t* h = hist + (int64_t)blockIdx.x * nt;
+  uint32_t carry = 0;
+  for (int64_t base = 0; base < nt; base += 1024) {
+    const int64_t i = base + threadIdx.x;
+    const uint32_t v = i < nt ? h[i] : 0u;
+    uint32_t tot;
+    const uint32_t ex = block_excl_scan<1024>(v, &tot, sm);
+    if (i < nt) h[i] = carry + ex;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) dtot[blockIdx.x] = carry;
+}
+
 // Stable scatter: each warp ranks its 512 keys (warp-striped, so (item, lane)
 // order is the input order) with match.any, warps are ordered by a per-digit
-// prefix, tiles by the scanned histogram.
+// prefix, tiles by the per-digit scan of the histogram, digits by the
+// exclusive scan of the digit totals.
 __global__ void __launch_bounds__(kRsThreads)
 k_rs_scatter(const uint64_t* __restrict__ in, uint64_t* __restrict__ out, int64_t n, int shift,
-             const uint32_t* __restrict__ offs, int64_t nt) {
+             const uint32_t* __restrict__ offs, int64_t nt, const uint32_t* __restrict__ dtot) {
   __shared__ uint32_t cnt[kRsThreads / 32][256];
+  __shared__ uint32_t dbase[256], sm[32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < (kRsThreads / 32) * 256; i += kRsThreads) (&cnt[0][0])[i] = 0;
+  {
+    uint32_t tot;
+    dbase[threadIdx.x] = block_excl_scan<kRsThreads>(dtot[threadIdx.x], &tot, sm);
+  }
   __syncthreads();
   const int64_t seg = (int64_t)blockIdx.x * kRsTile + w * (kRsItems * 32);
   const uint32_t lt = (1u << lane) - 1u;
@@ -123,7 +131,8 @@ k_rs_scatter(const uint64_t* __restrict__ in, uint64_t* __restrict__ out, int64_
 #pragma unroll
   for (int i = 0; i < kRsItems; i++) {
     if (dig[i] < 256)
-      out[offs[(int64_t)dig[i] * nt + blockIdx.x] + cnt[w][dig[i]] + rank[i]] = key[i];
+      out[dbase[dig[i]] + offs[(int64_t)dig[i] * nt + blockIdx.x] + cnt[w][dig[i]] + rank[i]] =
+          key[i];
   }
 }
 
@@ -138,9 +147,10 @@ uint64_t* radix_sort(uint64_t* keys, int64_t n, int bits, bool frame_bits, const
   if (frame_bits || bits > 56) shifts[ns++] = 56;
   for (int i = 0; i < ns; i++) {
     const int shift = shifts[i];
+    uint32_t* dtot = s.hist + 256 * nt;
     k_rs_hist<<<(unsigned)nt, kRsThreads, 0, st>>>(a, n, shift, s.hist, nt);
-    k_scan_single<<<1, 1024, 0, st>>>(s.hist, 256 * nt);
-    k_rs_scatter<<<(unsigned)nt, kRsThreads, 0, st>>>(a, b, n, shift, s.hist, nt);
+    k_rs_digit_scan<<<256, 1024, 0, st>>>(s.hist, nt, dtot);
+    k_rs_scatter<<<(unsigned)nt, kRsThreads, 0, st>>>(a, b, n, shift, s.hist, nt, dtot);
     count_launches(3);
     std::swap(a, b);
   }
@@ -418,12 +428,13 @@ constexpr int kCoThreads = 1024, kCoItems = 4, kCoChunk = kCoThreads * kCoItems;
 // ping-pong through k0 / k1; counts into cN[h]; frame offsets of every height
 // into foff[h * (nf + 1) + f].
 __global__ void __launch_bounds__(kCoThreads)
-k_coarse_up(const uint64_t* __restrict__ key6, const int64_t* d_n6, int top, uint64_t* k0,
-            uint64_t* k1, uint8_t* codes, int64_t stride, int64_t* cN, int nf, int64_t* foff) {
+k_coarse_up(const uint64_t* __restrict__ first_src, const int64_t* d_nsrc, int h0, int top,
+            uint64_t* k0, uint64_t* k1, uint8_t* codes, int64_t stride, int64_t* cN, int nf,
+            int64_t* foff) {
   __shared__ uint32_t sm[32];
-  const uint64_t* src = key6;
-  int64_t n = *d_n6;
-  for (int h = 7; h <= top; h++) {
+  const uint64_t* src = first_src;
+  int64_t n = *d_nsrc;
+  for (int h = h0; h <= top; h++) {
     uint64_t* dst = (h & 1) ? k1 : k0;
     uint8_t* code = codes + (int64_t)(h - 7) * stride;
     int64_t run = 0;
@@ -476,9 +487,27 @@ k_coarse_up(const uint64_t* __restrict__ key6, const int64_t* d_n6, int top, uin
 
 void launch_coarse_up(const uint64_t* key6, const int64_t* d_n6, int top, uint64_t* k0,
                       uint64_t* k1, uint8_t* codes, int64_t stride, int64_t* cN, int nf,
-                      int64_t* foff, cudaStream_t st) {
+                      int64_t* foff, int scan_heights, int64_t cap, const ScanScratch& s,
+                      cudaStream_t st) {
   if (top < 7) return;
-  k_coarse_up<<<1, kCoThreads, 0, st>>>(key6, d_n6, top, k0, k1, codes, stride, cN, nf, foff);
+  // the first scan_heights heights by the multi-block scan (large levels),
+  // the rest by the single block
+  const uint64_t* src = key6;
+  const int64_t* nsrc = d_n6;
+  int h = 7;
+  for (; h <= top && h < 7 + scan_heights; h++) {
+    uint64_t* dst = (h & 1) ? k1 : k0;
+    launch_level_up(src, nsrc, cap, dst, codes + (int64_t)(h - 7) * stride, nullptr, nullptr,
+                    cN + h, s, st);
+    LevelPtrs lp{};
+    lp.key[0] = dst;
+    lp.n[0] = cN + h;
+    launch_frame_offsets(lp, 1, nf, foff + (int64_t)h * (nf + 1), st);
+    src = dst;
+    nsrc = cN + h;
+  }
+  if (h > top) return;
+  k_coarse_up<<<1, kCoThreads, 0, st>>>(src, nsrc, h, top, k0, k1, codes, stride, cN, nf, foff);
   count_launches(1);
 }
 
@@ -491,12 +520,12 @@ struct CoarseCounts {
   int64_t n[kMaxDepth + 1];
 };
 __global__ void __launch_bounds__(kCoThreads)
-k_coarse_down(const uint64_t* __restrict__ roots, int top, const uint8_t* __restrict__ codes,
-              int64_t stride, CoarseCounts cnt, int64_t cap, uint64_t* k0, uint64_t* k1,
-              uint64_t* key6, int64_t* n6, int* err) {
+k_coarse_down(const uint64_t* __restrict__ roots, int top, int bottom,
+              const uint8_t* __restrict__ codes, int64_t stride, CoarseCounts cnt, int64_t cap,
+              uint64_t* k0, uint64_t* k1, uint64_t* key6, int64_t* n6, int* err) {
   __shared__ uint32_t sm[32];
   const uint64_t* src = roots;
-  for (int h = top; h >= 7; h--) {
+  for (int h = top; h >= bottom; h--) {
     const int64_t n = cnt.n[h];
     const uint8_t* code = codes + (int64_t)(h - 7) * stride;
     uint64_t* dst = h == 7 ? key6 : ((h - 1) & 1 ? k1 : k0);
@@ -532,15 +561,31 @@ k_coarse_down(const uint64_t* __restrict__ roots, int top, const uint8_t* __rest
   }
 }
 
+constexpr int64_t kCoarseScanMin = 16384;  // parents per height worth a multi-block scan
+
 void launch_coarse_down(const uint64_t* roots, int top, const uint8_t* codes, int64_t stride,
-                        const int64_t* counts, int64_t cap, uint64_t* k0, uint64_t* k1,
-                        uint64_t* key6, int64_t* n6, int* err, cudaStream_t st) {
+                        const int64_t* counts, const int64_t* d_counts, int64_t cap, uint64_t* k0,
+                        uint64_t* k1, uint64_t* key6, int64_t* n6, const ScanScratch& s, int* err,
+                        cudaStream_t st) {
   if (top < 7) return;
   CoarseCounts c{};
   for (int h = 7; h <= top && h <= kMaxDepth; h++) c.n[h] = counts[h];
-  k_coarse_down<<<1, kCoThreads, 0, st>>>(roots, top, codes, stride, c, cap, k0, k1, key6, n6,
-                                          err);
-  count_launches(1);
+  // levels grow downward: parent heights bottom - 1 .. 7 are large enough for
+  // the multi-block expansion, the ones above go through the single block
+  int bottom = 7;
+  while (bottom <= top && counts[bottom] >= kCoarseScanMin) bottom++;
+  if (bottom <= top) {
+    k_coarse_down<<<1, kCoThreads, 0, st>>>(roots, top, bottom, codes, stride, c, cap, k0, k1,
+                                            key6, n6, err);
+    count_launches(1);
+  }
+  for (int h = std::min(bottom - 1, top); h >= 7; h--) {
+    const uint64_t* pk = h == top ? roots : ((h & 1) ? k1 : k0);
+    uint64_t* ck = h == 7 ? key6 : (((h - 1) & 1) ? k1 : k0);
+    // d_counts[h - 1] holds the child count already; the expansion rewrites it
+    launch_expand(pk, codes + (int64_t)(h - 7) * stride, d_counts + h, counts[h], ck, nullptr,
+                  nullptr, cap, h == 7 ? n6 : const_cast<int64_t*>(d_counts) + h - 1, s, err, st);
+  }
 }
 
 // Children (parent << 3 | c) for every set bit c in ascending order: parents

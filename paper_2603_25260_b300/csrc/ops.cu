@@ -100,7 +100,7 @@ int lpc_t_levels(const int32_t* d_xyz, int64_t n, int L, uint64_t* d_keys, uint8
   SortScratch ss;
   ss.n_max = nn;
   ss.alt = t.get<uint64_t>(nn);
-  ss.hist = t.get<uint32_t>(256 * sort_tiles(nn));
+  ss.hist = t.get<uint32_t>(256 * (sort_tiles(nn) + 1));
   ScanScratch sc;
   sc.max_tiles = scan_tiles_for(nn);
   sc.tiles = t.get<uint32_t>(sc.max_tiles);

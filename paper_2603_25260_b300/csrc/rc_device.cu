@@ -5,7 +5,7 @@
 //
 // Substreams are independent, so every chunk is coded in parallel:
 //  - encode: one warp per chunk (its lane 0) walks the packed (lo, f)
-//    intervals;
+//    intervals, or one lane per chunk when chunks are many;
 //  - decode: one warp per chunk.  Table rows are staged in shared memory by
 //    bulk copies well ahead of use; the 256 entries of a row are spread over
 //    the warp, 8 a lane.  The target floor(code / r) is never formed:
@@ -34,16 +34,16 @@ using tc::smem_u32;
 
 constexpr int kEncWarps = 4;
 constexpr int kEncAhead = 4;
+// With at least this many chunks every lane codes a chunk of its own (the
+// warps would otherwise issue one lane's instructions each and the launch
+// becomes issue-bound); with fewer, one chunk a warp.
+constexpr int kEncLaneChunks = 148 * 32;
 
-// One chunk per warp, coded by its lane 0: chunks are few and each is a
-// serial chain, so lanes of other chunks in the same warp would only add
-// divergence.
-__global__ void __launch_bounds__(kEncWarps * 32)
-k_rc_encode(const RcChunk* __restrict__ ck, int n, const uint32_t* __restrict__ lofreq,
-            uint8_t* __restrict__ out, uint32_t* __restrict__ lens, int* err) {
-  if ((threadIdx.x & 31) != 0) return;
-  const int t = blockIdx.x * kEncWarps + (threadIdx.x >> 5);
-  if (t >= n) return;
+// Code chunk t (a serial chain).
+__device__ __forceinline__ void encode_chunk(const RcChunk* __restrict__ ck, int t,
+                                             const uint32_t* __restrict__ lofreq,
+                                             uint8_t* __restrict__ out, uint32_t* __restrict__ lens,
+                                             int* err) {
   const RcChunk c = ck[t];
   uint8_t* o = out + c.byte_off;
   const int64_t cap = c.byte_len;
@@ -89,6 +89,24 @@ k_rc_encode(const RcChunk* __restrict__ ck, int n, const uint32_t* __restrict__ 
   for (int i = 0; i < 5; i++) shift_low();
   lens[t] = (uint32_t)len;
   if (len > cap) set_error(err, kErrCapacity);
+}
+
+// One chunk per warp, coded by its lane 0 (few chunks: lanes of other chunks
+// in the same warp would only lengthen each chain by divergence).
+__global__ void __launch_bounds__(kEncWarps * 32)
+k_rc_encode(const RcChunk* __restrict__ ck, int n, const uint32_t* __restrict__ lofreq,
+            uint8_t* __restrict__ out, uint32_t* __restrict__ lens, int* err) {
+  if ((threadIdx.x & 31) != 0) return;
+  const int t = blockIdx.x * kEncWarps + (threadIdx.x >> 5);
+  if (t < n) encode_chunk(ck, t, lofreq, out, lens, err);
+}
+
+// One chunk per lane (many chunks).
+__global__ void __launch_bounds__(128)
+k_rc_encode_lanes(const RcChunk* __restrict__ ck, int n, const uint32_t* __restrict__ lofreq,
+                  uint8_t* __restrict__ out, uint32_t* __restrict__ lens, int* err) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) encode_chunk(ck, t, lofreq, out, lens, err);
 }
 
 // Table rows reach shared memory by bulk copies (TMA, one per stage of
@@ -217,8 +235,11 @@ k_rc_decode(const RcChunk* __restrict__ ck, int n, const uint16_t* __restrict__ 
 void launch_rc_encode(const RcChunk* ck, int n, const uint32_t* lofreq, uint8_t* out,
                       uint32_t* lens, int* err, cudaStream_t st) {
   if (n <= 0) return;
-  k_rc_encode<<<(n + kEncWarps - 1) / kEncWarps, kEncWarps * 32, 0, st>>>(ck, n, lofreq, out,
-                                                                          lens, err);
+  if (n >= kEncLaneChunks)
+    k_rc_encode_lanes<<<(n + 127) / 128, 128, 0, st>>>(ck, n, lofreq, out, lens, err);
+  else
+    k_rc_encode<<<(n + kEncWarps - 1) / kEncWarps, kEncWarps * 32, 0, st>>>(ck, n, lofreq, out,
+                                                                            lens, err);
   count_launches(1);
 }
 
