@@ -129,7 +129,28 @@ struct CoarsePipe {
   }
 };
 constexpr int kMaxCoarseTasks = 64;
+constexpr int kSplitFrames = 8;  // decode batches of at least this many frames in two groups
 constexpr int64_t kCoarseBatch = 128;  // codes decoded between bound updates
+
+// All coarse levels of one frame in order on this thread.
+void coarse_frame(Frame& F, int64_t maxp, std::atomic<int>& status) {
+  F.coarse.assign(F.b, {});
+  int64_t n = 1;
+  for (int d = 0; d < F.b; d++) {
+    std::vector<uint8_t>& Y = F.coarse[d];
+    Y.resize((size_t)n);
+    if (!decode_adaptive(Y.size(), F.in + F.soff[d], (size_t)F.slen[d], Y.data())) {
+      status = LPC_CORRUPT_STREAM;
+      return;
+    }
+    n = 0;
+    for (auto& y : Y) n += __builtin_popcount(++y);
+    if (n > maxp) {
+      status = LPC_CAPACITY;
+      return;
+    }
+  }
+}
 
 void coarse_level(Frame& F, int d, CoarsePipe& P, int64_t maxp, std::atomic<int>& status) {
   RangeDecoder dec(F.in + F.soff[d], (size_t)F.slen[d]);
@@ -1123,207 +1144,269 @@ int Codec::decode(int nf, const uint8_t* const* in, const size_t* lens, int32_t*
     if (nsub < (uint64_t)b) return fail(LPC_CORRUPT_STREAM, "decode: missing substream");
     dev.push_back(i);
   }
-  const int nd = (int)dev.size();
-  nf_ = nd;
-  fr_.clear();
-  for (int i : dev) fr_.push_back(std::move(all[i]));
-  if (nd == 0) return LPC_OK;
-  begin_batch();
-  for (int f = 0; f < nd; f++) {
-    h_fr_[f] = DevFrame{nullptr, out[dev[f]], 0, 0, fr_[f].L, 0};
-    h_L_[f] = fr_[f].L;
-  }
-  cudaMemcpyAsync(d_L_, h_L_, 4 * nd, cudaMemcpyHostToDevice, st_);
-  // device coding: every frame's bytes go to the device while the host
-  // decodes the coarse levels
-  in_base_.assign(nd, 0);
-  if (dev_rc_) {
-    size_t tot = 0;
+  // Decodes the frames dev (caller indices) as one batch.  coarse_ready: their
+  // coarse levels were decoded by earlier pool tasks (group 3, status in
+  // async_stat); after_coarse runs once the group's coarse levels are done.
+  std::atomic<int> async_stat{0};
+  auto run_group = [&](const std::vector<int>& dev, bool coarse_ready,
+                       const std::function<void()>& after_coarse) -> int {
+    const int nd = (int)dev.size();
+    nf_ = nd;
+    if (coarse_ready) pool_->wait(3);  // the tasks write these frames: done before they move
+    fr_.clear();
+    for (int i : dev) fr_.push_back(std::move(all[i]));
+    if (nd == 0) return LPC_OK;
+    begin_batch();
     for (int f = 0; f < nd; f++) {
-      in_base_[f] = (int64_t)tot;
-      tot += (fr_[f].len + 15) & ~(size_t)15;
+      h_fr_[f] = DevFrame{nullptr, out[dev[f]], 0, 0, fr_[f].L, 0};
+      h_L_[f] = fr_[f].L;
     }
-    uint8_t* hb = static_cast<uint8_t*>(hgrow(h_rcbuf_, tot));
-    uint8_t* db = static_cast<uint8_t*>(dgrow(d_rcbuf_, tot));
-    if (!hb || !db) return fail(LPC_CUDA_ERROR, "decode: range coder buffer allocation failed");
-    for (int f = 0; f < nd; f++) memcpy(hb + in_base_[f], fr_[f].in, fr_[f].len);
-    cudaMemcpyAsync(db, hb, tot, cudaMemcpyHostToDevice, st_);
-  }
-  // coarse levels (depths 0..b-1): adaptive-model decoding on the host
-  std::atomic<int> cstat{0};
-  {
-    // one task per frame, levels in order (N_{d+1} = sum of popcounts of Y_d);
-    // frame 0 on this thread: the thread that was just busy runs it fastest
-    const int64_t maxp = cfg_.max_points;
-    auto coarse = [&](int f) {
-      Frame& F = fr_[f];
-      F.coarse.assign(F.b, {});
-      int64_t n = 1;
-      for (int d = 0; d < F.b; d++) {
-        std::vector<uint8_t>& Y = F.coarse[d];
-        Y.resize((size_t)n);
-        if (!decode_adaptive(Y.size(), F.in + F.soff[d], (size_t)F.slen[d], Y.data())) {
-          cstat = LPC_CORRUPT_STREAM;
-          return;
+    cudaMemcpyAsync(d_L_, h_L_, 4 * nd, cudaMemcpyHostToDevice, st_);
+    // device coding: every frame's bytes go to the device while the host
+    // decodes the coarse levels
+    in_base_.assign(nd, 0);
+    if (dev_rc_) {
+      size_t tot = 0;
+      for (int f = 0; f < nd; f++) {
+        in_base_[f] = (int64_t)tot;
+        tot += (fr_[f].len + 15) & ~(size_t)15;
+      }
+      uint8_t* hb = static_cast<uint8_t*>(hgrow(h_rcbuf_, tot));
+      uint8_t* db = static_cast<uint8_t*>(dgrow(d_rcbuf_, tot));
+      if (!hb || !db) return fail(LPC_CUDA_ERROR, "decode: range coder buffer allocation failed");
+      for (int f = 0; f < nd; f++) memcpy(hb + in_base_[f], fr_[f].in, fr_[f].len);
+      cudaMemcpyAsync(db, hb, tot, cudaMemcpyHostToDevice, st_);
+    }
+    // coarse levels (depths 0..b-1): adaptive-model decoding on the host
+    std::atomic<int> cstat{0};
+    if (!coarse_ready) {
+    {
+      // one task per frame, levels in order (N_{d+1} = sum of popcounts of Y_d);
+      // frame 0 on this thread: the thread that was just busy runs it fastest
+      const int64_t maxp = cfg_.max_points;
+      auto coarse = [&](int f) { coarse_frame(fr_[f], maxp, cstat); };
+      int tasks = 0;
+      for (int f = 0; f < nd; f++) tasks += fr_[f].b;
+      if (tasks <= pool_->size() && tasks <= kMaxCoarseTasks) {
+        // few frames: every level its own task, pipelined within a frame
+        std::vector<CoarsePipe> pipes(nd);
+        for (int f = 0; f < nd; f++) fr_[f].coarse.assign(fr_[f].b, {});
+        for (int f = 0; f < nd; f++)
+          for (int d = 0; d < fr_[f].b; d++)
+            if (f || d) pool_->submit(0, [&, f, d] { coarse_level(fr_[f], d, pipes[f], maxp, cstat); });
+        coarse_level(fr_[0], 0, pipes[0], maxp, cstat);
+        pool_->wait(0);
+      } else {
+        // many frames: one task per frame, the largest coarse streams first
+        // (longest-processing-time order balances the threads), the largest on
+        // this thread
+        std::vector<std::pair<uint64_t, int>> order(nd);
+        for (int f = 0; f < nd; f++) {
+          uint64_t bytes = 0;
+          for (int d = 0; d < fr_[f].b; d++) bytes += fr_[f].slen[d];
+          order[f] = {bytes, f};
         }
-        n = 0;
-        for (auto& y : Y) n += __builtin_popcount(++y);
-        if (n > maxp) {
-          cstat = LPC_CAPACITY;
-          return;
-        }
-      }
-    };
-    int tasks = 0;
-    for (int f = 0; f < nd; f++) tasks += fr_[f].b;
-    if (tasks <= pool_->size() && tasks <= kMaxCoarseTasks) {
-      // few frames: every level its own task, pipelined within a frame
-      std::vector<CoarsePipe> pipes(nd);
-      for (int f = 0; f < nd; f++) fr_[f].coarse.assign(fr_[f].b, {});
-      for (int f = 0; f < nd; f++)
-        for (int d = 0; d < fr_[f].b; d++)
-          if (f || d) pool_->submit(0, [&, f, d] { coarse_level(fr_[f], d, pipes[f], maxp, cstat); });
-      coarse_level(fr_[0], 0, pipes[0], maxp, cstat);
-      pool_->wait(0);
-    } else {
-      for (int f = 1; f < nd; f++) pool_->submit(0, [&, f] { coarse(f); });
-      coarse(0);
-      pool_->wait(0);
-    }
-  }
-  if (cstat == LPC_CORRUPT_STREAM) return fail(LPC_CORRUPT_STREAM, "decode: corrupt coarse substream");
-  if (cstat == LPC_CAPACITY) return fail(LPC_CAPACITY, "decode: frame exceeds max_points");
-  if (int s = expand_coarse_device(nd)) return s;
-  stats.phase_us[4] = now_us() - t0;
-  for (int i = 5; i < 9; i++) stats.phase_us[i] = 0;
-  if (dev_rc_) {
-    if (int s = decode_net_device(nd, n_out, dev, caps)) return s;
-  } else {
-  const int64_t maxp = cfg_.max_points;
-  // substream index of (frame, relative level j, chunk 0)
-  std::vector<std::vector<size_t>> sidx(nd, std::vector<size_t>(6, 0));
-  std::atomic<bool> bad{false};
-  for (int j = 0; j < 5; j++) {
-    const int h = 5 - j;
-    double tl = now_us();
-    // V at height h: children of height h + 1 (host knows the counts)
-    int64_t nh = 0;
-    for (int f = 0; f < nd; f++) {
-      Frame& F = fr_[f];
-      const uint8_t* Y = h_codes_ + (size_t)(h + 1) * P_ + F.off[h + 1];
-      int64_t c = 0;
-      for (int64_t i = 0; i < F.cnt[h + 1]; i++) c += __builtin_popcount(Y[i]);
-      if (c > maxp) return fail(LPC_CAPACITY, "decode: frame exceeds max_points");
-      F.off[h] = nh;
-      F.cnt[h] = c;
-      nh += c;
-      if (j == 0) sidx[f][0] = F.b;
-    }
-    if (nh > P_) return fail(LPC_CAPACITY, "decode: batch exceeds the codec's capacity");
-    N_[h] = nh;
-    pbeg(kFamLevels);
-    launch_expand(key_[h + 1], code_[h + 1], d_N_ + h + 1, P_, key_[h], par_[h], off_[h + 1], P_,
-                  d_N_ + h, scan_, d_err_, st_);
-    pend(kFamLevels, 13.0 * N_[h + 1] + 12.0 * nh, 0);
-    run_level(j, kPredCdf, d_cdf_, nullptr);
-    if (int s = cuda_check("decode: launch")) return s;
-    stats.phase_us[7] += now_us() - tl;
-    tl = now_us();
-    // tables to the host through the two-half ring; chunks are decoded as
-    // they land, one host task per (frame, chunk)
-    struct Ck {
-      int f;
-      int64_t r0, rows, local;
-      size_t sub;
-    };
-    std::vector<Ck> cks;
-    for (int f = 0; f < nd; f++) {
-      const Frame& F = fr_[f];
-      size_t s = sidx[f][j];
-      for (int64_t c0 = 0; c0 < F.cnt[h]; c0 += F.chunk, s++) {
-        if (s >= F.slen.size()) return fail(LPC_CORRUPT_STREAM, "decode: missing substream");
-        cks.push_back(Ck{f, F.off[h] + c0, std::min<int64_t>(F.chunk, F.cnt[h] - c0), c0, s});
-      }
-      sidx[f][j + 1] = s;
-    }
-    stats.phase_us[5] += now_us() - tl;
-    tl = now_us();
-    size_t c = 0;
-    int wave = 0;
-    while (c < cks.size()) {
-      const int half = wave & 1;
-      pool_->wait(1 + half);  // the tasks that last read this half are done
-      uint16_t* base = h_ring_ + (size_t)half * ring_slots_ * 256;
-      int64_t used = 0;
-      size_t c1 = c;
-      int e = 0;
-      while (c1 < cks.size() && used + cks[c1].rows <= ring_slots_ && e < 240) {
-        cudaMemcpyAsync(base + used * 256, d_cdf_ + cks[c1].r0 * 256, 512 * cks[c1].rows,
-                        cudaMemcpyDeviceToHost, st_);
-        cudaEventRecord(ev_[16 + half * 240 + e], st_);
-        used += cks[c1].rows;
-        c1++;
-        e++;
-      }
-      used = 0;
-      for (size_t k = c; k < c1; k++) {
-        cudaEventSynchronize(ev_[16 + half * 240 + (int)(k - c)]);
-        const Ck ck = cks[k];
-        const uint16_t* rows = base + used * 256;
-        used += ck.rows;
-        pool_->submit(1 + half, [this, ck, rows, h, &bad] {
-          const Frame& F = fr_[ck.f];
-          uint8_t* Y = h_codes_ + (size_t)h * P_ + ck.r0;
-          if (!decode_rows(rows, (size_t)ck.rows, F.in + F.soff[ck.sub], (size_t)F.slen[ck.sub],
-                           Y))
-            bad = true;
-          for (int64_t i = 0; i < ck.rows; i++) Y[i] += 1;
+        std::sort(order.begin(), order.end(), [](const auto& a, const auto& b) {
+          return a.first != b.first ? a.first > b.first : a.second < b.second;
         });
+        for (int k = 1; k < nd; k++) pool_->submit(0, [&, f = order[k].second] { coarse(f); });
+        coarse(order[0].second);
+        pool_->wait(0);
       }
-      c = c1;
-      wave++;
     }
-    pool_->wait(1);
-    pool_->wait(2);
-    stats.phase_us[6] += now_us() - tl;
-    if (bad) return fail(LPC_CORRUPT_STREAM, "decode: corrupt level substream");
-    cudaMemcpyAsync(code_[h], h_codes_ + (size_t)h * P_, nh, cudaMemcpyHostToDevice, st_);
+    if (cstat == LPC_CORRUPT_STREAM) return fail(LPC_CORRUPT_STREAM, "decode: corrupt coarse substream");
+    if (cstat == LPC_CAPACITY) return fail(LPC_CAPACITY, "decode: frame exceeds max_points");
+    } else {
+      if (async_stat == LPC_CORRUPT_STREAM)
+        return fail(LPC_CORRUPT_STREAM, "decode: corrupt coarse substream");
+      if (async_stat == LPC_CAPACITY) return fail(LPC_CAPACITY, "decode: frame exceeds max_points");
+    }
+    if (after_coarse) after_coarse();
+    if (int s = expand_coarse_device(nd)) return s;
+    stats.phase_us[4] = now_us() - t0;
+    for (int i = 5; i < 9; i++) stats.phase_us[i] = 0;
+    if (dev_rc_) {
+      if (int s = decode_net_device(nd, n_out, dev, caps)) return s;
+    } else {
+    const int64_t maxp = cfg_.max_points;
+    // substream index of (frame, relative level j, chunk 0)
+    std::vector<std::vector<size_t>> sidx(nd, std::vector<size_t>(6, 0));
+    std::atomic<bool> bad{false};
+    for (int j = 0; j < 5; j++) {
+      const int h = 5 - j;
+      double tl = now_us();
+      // V at height h: children of height h + 1 (host knows the counts)
+      int64_t nh = 0;
+      for (int f = 0; f < nd; f++) {
+        Frame& F = fr_[f];
+        const uint8_t* Y = h_codes_ + (size_t)(h + 1) * P_ + F.off[h + 1];
+        int64_t c = 0;
+        for (int64_t i = 0; i < F.cnt[h + 1]; i++) c += __builtin_popcount(Y[i]);
+        if (c > maxp) return fail(LPC_CAPACITY, "decode: frame exceeds max_points");
+        F.off[h] = nh;
+        F.cnt[h] = c;
+        nh += c;
+        if (j == 0) sidx[f][0] = F.b;
+      }
+      if (nh > P_) return fail(LPC_CAPACITY, "decode: batch exceeds the codec's capacity");
+      N_[h] = nh;
+      pbeg(kFamLevels);
+      launch_expand(key_[h + 1], code_[h + 1], d_N_ + h + 1, P_, key_[h], par_[h], off_[h + 1], P_,
+                    d_N_ + h, scan_, d_err_, st_);
+      pend(kFamLevels, 13.0 * N_[h + 1] + 12.0 * nh, 0);
+      run_level(j, kPredCdf, d_cdf_, nullptr);
+      if (int s = cuda_check("decode: launch")) return s;
+      stats.phase_us[7] += now_us() - tl;
+      tl = now_us();
+      // tables to the host through the two-half ring; chunks are decoded as
+      // they land, one host task per (frame, chunk)
+      struct Ck {
+        int f;
+        int64_t r0, rows, local;
+        size_t sub;
+      };
+      std::vector<Ck> cks;
+      for (int f = 0; f < nd; f++) {
+        const Frame& F = fr_[f];
+        size_t s = sidx[f][j];
+        for (int64_t c0 = 0; c0 < F.cnt[h]; c0 += F.chunk, s++) {
+          if (s >= F.slen.size()) return fail(LPC_CORRUPT_STREAM, "decode: missing substream");
+          cks.push_back(Ck{f, F.off[h] + c0, std::min<int64_t>(F.chunk, F.cnt[h] - c0), c0, s});
+        }
+        sidx[f][j + 1] = s;
+      }
+      stats.phase_us[5] += now_us() - tl;
+      tl = now_us();
+      size_t c = 0;
+      int wave = 0;
+      while (c < cks.size()) {
+        const int half = wave & 1;
+        pool_->wait(1 + half);  // the tasks that last read this half are done
+        uint16_t* base = h_ring_ + (size_t)half * ring_slots_ * 256;
+        int64_t used = 0;
+        size_t c1 = c;
+        int e = 0;
+        while (c1 < cks.size() && used + cks[c1].rows <= ring_slots_ && e < 240) {
+          cudaMemcpyAsync(base + used * 256, d_cdf_ + cks[c1].r0 * 256, 512 * cks[c1].rows,
+                          cudaMemcpyDeviceToHost, st_);
+          cudaEventRecord(ev_[16 + half * 240 + e], st_);
+          used += cks[c1].rows;
+          c1++;
+          e++;
+        }
+        used = 0;
+        for (size_t k = c; k < c1; k++) {
+          cudaEventSynchronize(ev_[16 + half * 240 + (int)(k - c)]);
+          const Ck ck = cks[k];
+          const uint16_t* rows = base + used * 256;
+          used += ck.rows;
+          pool_->submit(1 + half, [this, ck, rows, h, &bad] {
+            const Frame& F = fr_[ck.f];
+            uint8_t* Y = h_codes_ + (size_t)h * P_ + ck.r0;
+            if (!decode_rows(rows, (size_t)ck.rows, F.in + F.soff[ck.sub], (size_t)F.slen[ck.sub],
+                             Y))
+              bad = true;
+            for (int64_t i = 0; i < ck.rows; i++) Y[i] += 1;
+          });
+        }
+        c = c1;
+        wave++;
+      }
+      pool_->wait(1);
+      pool_->wait(2);
+      stats.phase_us[6] += now_us() - tl;
+      if (bad) return fail(LPC_CORRUPT_STREAM, "decode: corrupt level substream");
+      cudaMemcpyAsync(code_[h], h_codes_ + (size_t)h * P_, nh, cudaMemcpyHostToDevice, st_);
+    }
+    for (int f = 0; f < nd; f++)
+      if (sidx[f][5] != fr_[f].slen.size())
+        return fail(LPC_CORRUPT_STREAM, "decode: extra substreams");
+    // leaves: children of height 1
+    int64_t n0 = 0;
+    for (int f = 0; f < nd; f++) {
+      Frame& F = fr_[f];
+      const uint8_t* Y = h_codes_ + (size_t)P_ + F.off[1];
+      int64_t c = 0;
+      for (int64_t i = 0; i < F.cnt[1]; i++) c += __builtin_popcount(Y[i]);
+      F.off[0] = n0;
+      F.cnt[0] = c;
+      n0 += c;
+      n_out[dev[f]] = c;
+      if (c > caps[dev[f]]) return fail(LPC_CAPACITY, "decode: output capacity too small");
+    }
+    if (n0 > P_) return fail(LPC_CAPACITY, "decode: batch exceeds the codec's capacity");
+    N_[0] = n0;
+    pbeg(kFamLevels);
+    launch_expand(key_[1], code_[1], d_N_ + 1, P_, key_[0], par_[0], off_[1], P_, d_N_, scan_,
+                  d_err_, st_);
+    pend(kFamLevels, 13.0 * N_[1] + 12.0 * n0, 0);
+    for (int f = 0; f < nd; f++) h_foff_[f] = fr_[f].off[0];
+    cudaMemcpyAsync(d_fr_, h_fr_, sizeof(DevFrame) * nd, cudaMemcpyHostToDevice, st_);
+    cudaMemcpyAsync(d_foff_, h_foff_, 8 * nd, cudaMemcpyHostToDevice, st_);
+    launch_keys_to_xyz_batch(key_[0], d_N_, n0, d_fr_, d_foff_, st_);
+    if (int s = sync_and_check("decode")) return s;
+    }
+    stats.L = fr_[0].L;
+    for (int d = 0; d < fr_[0].b; d++) stats.N[d] = (int64_t)fr_[0].coarse[d].size();
+    for (int h = 0; h < kHeights; h++) stats.N[fr_[0].L - h] = fr_[0].cnt[h];
+    stats.host_us = now_us() - t0;
+    stats.phase_us[8] = stats.host_us;
+    prof_collect();
+    return LPC_OK;
+  };
+  // Many frames: two groups, the frames with the least coarse data first,
+  // about a third of it, so the host decodes the other group's coarse
+  // levels while the device decodes the first group's network levels.
+  if (!dev_rc_ || (int)dev.size() < kSplitFrames) return run_group(dev, false, nullptr);
+  std::vector<std::pair<uint64_t, int>> by(dev.size());
+  uint64_t all_bytes = 0;
+  for (size_t k = 0; k < dev.size(); k++) {
+    uint64_t bytes = 0;
+    for (int d = 0; d < all[dev[k]].b; d++) bytes += all[dev[k]].slen[d];
+    by[k] = {bytes, dev[k]};
+    all_bytes += bytes;
   }
-  for (int f = 0; f < nd; f++)
-    if (sidx[f][5] != fr_[f].slen.size())
-      return fail(LPC_CORRUPT_STREAM, "decode: extra substreams");
-  // leaves: children of height 1
-  int64_t n0 = 0;
-  for (int f = 0; f < nd; f++) {
-    Frame& F = fr_[f];
-    const uint8_t* Y = h_codes_ + (size_t)P_ + F.off[1];
-    int64_t c = 0;
-    for (int64_t i = 0; i < F.cnt[1]; i++) c += __builtin_popcount(Y[i]);
-    F.off[0] = n0;
-    F.cnt[0] = c;
-    n0 += c;
-    n_out[dev[f]] = c;
-    if (c > caps[dev[f]]) return fail(LPC_CAPACITY, "decode: output capacity too small");
+  std::sort(by.begin(), by.end());
+  std::vector<int> ga, gb;
+  uint64_t acc = 0;
+  for (auto& e : by) {
+    if (ga.empty() || (acc < all_bytes * 3 / 10 && gb.empty())) {
+      ga.push_back(e.second);
+      acc += e.first;
+    } else {
+      gb.push_back(e.second);
+    }
   }
-  if (n0 > P_) return fail(LPC_CAPACITY, "decode: batch exceeds the codec's capacity");
-  N_[0] = n0;
-  pbeg(kFamLevels);
-  launch_expand(key_[1], code_[1], d_N_ + 1, P_, key_[0], par_[0], off_[1], P_, d_N_, scan_,
-                d_err_, st_);
-  pend(kFamLevels, 13.0 * N_[1] + 12.0 * n0, 0);
-  for (int f = 0; f < nd; f++) h_foff_[f] = fr_[f].off[0];
-  cudaMemcpyAsync(d_fr_, h_fr_, sizeof(DevFrame) * nd, cudaMemcpyHostToDevice, st_);
-  cudaMemcpyAsync(d_foff_, h_foff_, 8 * nd, cudaMemcpyHostToDevice, st_);
-  launch_keys_to_xyz_batch(key_[0], d_N_, n0, d_fr_, d_foff_, st_);
-  if (int s = sync_and_check("decode")) return s;
+  std::sort(ga.begin(), ga.end());
+  std::sort(gb.begin(), gb.end());
+  if (gb.empty()) return run_group(ga, false, nullptr);
+  const int64_t maxp = cfg_.max_points;
+  auto start_b = [&] {
+    std::vector<std::pair<uint64_t, int>> order;
+    for (int i : gb) {
+      uint64_t bytes = 0;
+      for (int d = 0; d < all[i].b; d++) bytes += all[i].slen[d];
+      order.push_back({bytes, i});
+    }
+    std::sort(order.begin(), order.end(), [](const auto& x, const auto& y) {
+      return x.first != y.first ? x.first > y.first : x.second < y.second;
+    });
+    for (auto& e : order) pool_->submit(3, [this, &all, &async_stat, maxp, i = e.second] {
+      coarse_frame(all[i], maxp, async_stat);
+    });
+  };
+  const int sa = run_group(ga, false, start_b);
+  if (sa) {
+    pool_->wait(3);
+    return sa;
   }
-  stats.L = fr_[0].L;
-  for (int d = 0; d < fr_[0].b; d++) stats.N[d] = (int64_t)fr_[0].coarse[d].size();
-  for (int h = 0; h < kHeights; h++) stats.N[fr_[0].L - h] = fr_[0].cnt[h];
-  stats.host_us = now_us() - t0;
-  stats.phase_us[8] = stats.host_us;
-  prof_collect();
-  return LPC_OK;
+  const double pa[16] = {stats.phase_us[0], stats.phase_us[1], stats.phase_us[2],
+                         stats.phase_us[3], stats.phase_us[4], stats.phase_us[5],
+                         stats.phase_us[6], stats.phase_us[7]};
+  const int sb = run_group(gb, true, nullptr);
+  for (int i = 5; i < 8; i++) stats.phase_us[i] += pa[i];
+  stats.phase_us[4] = pa[4];
+  return sb;
 }
 
 // Coarse codes of every frame to the device, arranged by height (height h is
