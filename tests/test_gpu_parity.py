@@ -422,6 +422,42 @@ def test_corrupt_payload(lpc, blob, host_coding):
     assert np.array_equal(cod.decode(data).cpu().numpy(), want)
 
 
+def test_batch_split_decode(lpc, blob):
+    """Batches of 8 frames or more decode in two groups (coarse levels of the
+    second decoded on the host while the device decodes the first): the
+    voxels of every frame equal the oracle's decode of its own stream, in a
+    batch with mixed depths, sizes and an empty frame; a corrupt frame in the
+    second group is reported and the codec stays usable."""
+    specs = [(2000, 9, 21), (15000, 14, 22), (0, 11, 23), (500, 7, 24), (30000, 16, 25),
+             (7000, 12, 26), (12000, 18, 27), (100, 8, 28), (22000, 15, 29), (4000, 10, 30),
+             (9000, 13, 31), (1, 6, 32)]
+    frames = [synth.random_cloud(n, L, sd) for n, L, sd in specs]
+    Ls = [L for _, L, _ in specs]
+    cod = lpc.Codec(blob, 18, 30000, max_frames=len(frames), chunk=700)
+    streams = [O.encode(blob, f, L, 700) for f, L in zip(frames, Ls)]
+    caps = [max(f.shape[0], 1) for f in frames]
+    for _ in range(2):
+        decs = cod.decode_batch(streams, caps)
+        for f, L, s, dcd in zip(frames, Ls, streams, decs):
+            want = O.decode(blob, s, max(f.shape[0], 1))
+            assert np.array_equal(dcd.cpu().numpy(), want)
+    assert cod.encode_batch([_cuda(f) for f in frames], Ls) == streams
+    # corrupt the coarse data of the largest frame (second group)
+    big = int(np.argmax([f.shape[0] for f in frames]))
+    bad = list(streams)
+    b = bytearray(bad[big])
+    for pos in range(40, 60):
+        b[pos] ^= 0x5A
+    bad[big] = bytes(b)
+    try:
+        cod.decode_batch(bad, caps)
+    except lpc.LpcError as e:
+        assert e.status in (lpc.CORRUPT_STREAM, lpc.CAPACITY), e
+    decs = cod.decode_batch(streams, caps)
+    for f, L, dcd in zip(frames, Ls, decs):
+        assert np.array_equal(O.leaf_keys(dcd.cpu().numpy(), L), O.leaf_keys(f, L))
+
+
 def test_batch_into_reusable_buffer(lpc, blob):
     """The buffer-reusing batch calls give the same streams and voxels."""
     specs = [(3000, 10, 11), (0, 9, 12), (8000, 14, 13)]
