@@ -1037,8 +1037,17 @@ int Codec::encode(int nf, const int32_t* const* xyz, const int64_t* n, const int
     if (int s = check_device_error()) return s;
     prof_collect();
   }
-  // assemble every frame's stream straight into its caller buffer
+  // assemble every frame's stream straight into its caller buffer: headers
+  // and tables here, the substream bytes by the pool (parts of about equal
+  // size; the copies are the bulk of the work for large batches)
   int first = LPC_OK;
+  struct Copy {
+    uint8_t* dst;
+    const uint8_t* src;
+    size_t len;
+  };
+  std::vector<Copy> copies;
+  size_t copy_bytes = 0;
   for (int i = 0, f = 0; i < nf; i++) {
     const bool empty = n[i] == 0;
     const Frame* F = empty ? nullptr : &fr_[f];
@@ -1072,11 +1081,32 @@ int Codec::encode(int nf, const int32_t* const* xyz, const int64_t* n, const int
       for (size_t k = b0; k < b1; k++) {
         const SubTask& T = tasks_[k];
         const uint8_t* src = T.rc >= 0 ? static_cast<const uint8_t*>(h_rcbuf_.p) : h_arena_;
-        memcpy(p, src + T.arena, T.len);
+        copies.push_back(Copy{p, src + T.arena, T.len});
+        copy_bytes += T.len;
         p += T.len;
       }
     }
     if (!empty) f++;
+  }
+  {
+    const int parts = (int)std::min<size_t>((size_t)pool_->size(), 1 + copy_bytes / (256 << 10));
+    const size_t per = (copy_bytes + parts - 1) / parts;
+    size_t k = 0;
+    auto run = [&copies](size_t a, size_t b) {
+      for (size_t j = a; j < b; j++) memcpy(copies[j].dst, copies[j].src, copies[j].len);
+    };
+    std::vector<std::pair<size_t, size_t>> ranges;
+    if (parts <= 1) ranges.push_back({0, copies.size()});
+    while (parts > 1 && k < copies.size()) {
+      size_t b = k, acc = 0;
+      while (b < copies.size() && (acc < per || b == k)) acc += copies[b++].len;
+      ranges.push_back({k, b});
+      k = b;
+    }
+    for (size_t r = 1; r < ranges.size(); r++)
+      pool_->submit(0, [&run, a = ranges[r].first, b = ranges[r].second] { run(a, b); });
+    if (!ranges.empty()) run(ranges[0].first, ranges[0].second);
+    pool_->wait(0);
   }
   // statistics of the first frame
   if (nd > 0) {
