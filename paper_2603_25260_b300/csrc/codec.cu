@@ -1507,6 +1507,11 @@ int Codec::expand_coarse_device(int nd) {
 // leaves written to the callers' buffers.
 int Codec::decode_net_device(int nd, int64_t* n_out, const std::vector<int>& dev,
                              const int64_t* caps) {
+  // once every level's network is a captured graph (sizes read on the
+  // device), the levels need no host round trip
+  bool graphs = gs_ && !prof.mask;
+  for (int j = 0; j < 5 && graphs; j++) graphs = gexec_[kPredCdf][j] != nullptr;
+  if (graphs) return decode_net_async(nd, n_out, dev, caps);
   const int64_t maxp = cfg_.max_points;
   std::vector<size_t> sidx(nd);
   for (int f = 0; f < nd; f++) sidx[f] = (size_t)fr_[f].b;
@@ -1578,6 +1583,79 @@ int Codec::decode_net_device(int nd, int64_t* n_out, const std::vector<int>& dev
     n_out[dev[f]] = c;
     if (c > caps[dev[f]]) return fail(LPC_CAPACITY, "decode: output capacity too small");
   }
+  cudaMemcpyAsync(d_fr_, h_fr_, sizeof(DevFrame) * nd, cudaMemcpyHostToDevice, st_);
+  launch_keys_to_xyz_batch(key_[0], d_N_, N_[0], d_fr_, d_foff_, st_);
+  return sync_and_check("decode");
+}
+
+// The network levels without host round trips: each level's sizes, frame
+// offsets and substream table stay on the device (the table from every
+// frame's substream list, uploaded once), the range decoder's grid is the
+// table's capacity; the host reads the sizes back once, at the end.
+int Codec::decode_net_async(int nd, int64_t* n_out, const std::vector<int>& dev,
+                            const int64_t* caps) {
+  const int64_t maxp = cfg_.max_points;
+  int64_t nsub = 0, min_chunk = INT64_MAX;
+  for (int f = 0; f < nd; f++) {
+    nsub += (int64_t)fr_[f].slen.size();
+    min_chunk = std::min(min_chunk, fr_[f].chunk);
+  }
+  const int64_t cap_ck = P_ / min_chunk + nd;
+  auto* hsf = static_cast<DevSubFrame*>(hgrow(h_subfr_, sizeof(DevSubFrame) * nd));
+  auto* dsf = static_cast<DevSubFrame*>(dgrow(d_subfr_, sizeof(DevSubFrame) * nd));
+  auto* hsub = static_cast<int64_t*>(hgrow(h_subs_, 16 * (size_t)nsub + 16));
+  auto* dsub = static_cast<int64_t*>(dgrow(d_subs_, 16 * (size_t)nsub + 16));
+  auto* dnck = static_cast<int64_t*>(dgrow(d_nck_, 8));
+  auto* dc = static_cast<RcChunk*>(dgrow(d_rcck_, sizeof(RcChunk) * (size_t)cap_ck));
+  if (!hsf || !dsf || !hsub || !dsub || !dnck || !dc)
+    return fail(LPC_CUDA_ERROR, "decode: substream table allocation failed");
+  int64_t k = 0;
+  for (int f = 0; f < nd; f++) {
+    const Frame& F = fr_[f];
+    hsf[f] = DevSubFrame{k, (int64_t)F.slen.size(), F.chunk, in_base_[f], (int64_t)F.b};
+    for (size_t s = 0; s < F.slen.size(); s++, k++) {
+      hsub[2 * k] = (int64_t)F.soff[s];
+      hsub[2 * k + 1] = (int64_t)F.slen[s];
+    }
+  }
+  cudaMemcpyAsync(dsf, hsf, sizeof(DevSubFrame) * nd, cudaMemcpyHostToDevice, st_);
+  cudaMemcpyAsync(dsub, hsub, 16 * (size_t)nsub, cudaMemcpyHostToDevice, st_);
+  const uint8_t* d_in = static_cast<const uint8_t*>(d_rcbuf_.p);
+  for (int j = 0; j <= 5; j++) {  // j = 5: the leaves
+    const int h = 5 - j;
+    launch_expand(key_[h + 1], code_[h + 1], d_N_ + h + 1, P_, key_[h], par_[h], off_[h + 1], P_,
+                  d_N_ + h, scan_, d_err_, st_);
+    int64_t* dfo = d_foff_ + (size_t)h * (nd + 1);
+    if (nd == 1) {
+      cudaMemsetAsync(dfo, 0, 8, st_);
+      cudaMemcpyAsync(dfo + 1, d_N_ + h, 8, cudaMemcpyDeviceToDevice, st_);
+    } else {
+      LevelPtrs lp{};
+      lp.key[0] = key_[h];
+      lp.n[0] = d_N_ + h;
+      launch_frame_offsets(lp, 1, nd, dfo, st_);
+    }
+    if (h == 0) break;
+    launch_rc_chunks(dfo, nd, dsf, dsub, dc, cap_ck, maxp, dnck, d_err_, st_);
+    run_level(j, kPredCdf, d_cdf_, nullptr);
+    launch_rc_decode_dev(dc, dnck, cap_ck, d_cdf_, d_in, code_[h], d_err_, st_);
+    if (int s = cuda_check("decode: launch")) return s;
+  }
+  cudaMemcpyAsync(h_foff_, d_foff_, 8 * (size_t)kHeights * (nd + 1), cudaMemcpyDeviceToHost, st_);
+  cudaMemcpyAsync(hsf, dsf, sizeof(DevSubFrame) * nd, cudaMemcpyDeviceToHost, st_);
+  if (int s = sync_and_check("decode: levels")) return s;
+  for (int f = 0; f < nd; f++) {
+    Frame& F = fr_[f];
+    if (hsf[f].next != hsf[f].nsub) return fail(LPC_CORRUPT_STREAM, "decode: extra substreams");
+    for (int h = 0; h < 6; h++) {
+      const int64_t* hfo = h_foff_ + (size_t)h * (nd + 1);
+      F.off[h] = hfo[f];
+      F.cnt[h] = hfo[f + 1] - hfo[f];
+    }
+    n_out[dev[f]] = F.cnt[0];
+    if (F.cnt[0] > caps[dev[f]]) return fail(LPC_CAPACITY, "decode: output capacity too small");
+  }
+  for (int h = 0; h < 6; h++) N_[h] = h_foff_[(size_t)h * (nd + 1) + nd];
   cudaMemcpyAsync(d_fr_, h_fr_, sizeof(DevFrame) * nd, cudaMemcpyHostToDevice, st_);
   launch_keys_to_xyz_batch(key_[0], d_N_, N_[0], d_fr_, d_foff_, st_);
   return sync_and_check("decode");

@@ -279,9 +279,11 @@ class Codec {
   void* dgrow(Buf& b, size_t bytes);
   void* hgrow(Buf& b, size_t bytes);
   Buf d_rcck_, d_rclen_, d_rcbuf_, h_rcck_, h_rclen_, h_rcbuf_, h_ccodes_;
+  Buf d_subfr_, h_subfr_, d_subs_, h_subs_, d_nck_;  // device-built substream tables
   bool dev_rc_ = true;
   std::vector<int64_t> in_base_;  // each decoded frame's first byte in d_rcbuf_
   int decode_net_device(int nd, int64_t* n_out, const std::vector<int>& dev, const int64_t* caps);
+  int decode_net_async(int nd, int64_t* n_out, const std::vector<int>& dev, const int64_t* caps);
   int expand_coarse_device(int nd);
   std::vector<SubTask> tasks_;
   std::vector<cudaEvent_t> ev_;

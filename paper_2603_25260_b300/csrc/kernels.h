@@ -109,11 +109,30 @@ struct RcChunk {
 // the capacity).  Same bytes as the host encoder.
 void launch_rc_encode(const RcChunk* ck, int n, const uint32_t* lofreq, uint8_t* out,
                       uint32_t* lens, int* err, cudaStream_t st);
+// Per decoded frame, for the device-built substream tables: the frame's
+// substreams are subs[2 (sub0 + s)] (offset in its stream) and
+// subs[2 (sub0 + s) + 1] (length), s < nsub; `next` is the first substream
+// not yet given to a chunk (advanced level by level); in_base is the frame's
+// first byte in the device stream buffer.
+struct DevSubFrame {
+  int64_t sub0, nsub, chunk, in_base, next;
+};
+// The substream table of one network level, built on the device: frame f's
+// rows foff[f] .. foff[f + 1] - 1 in chunks of its chunk size, each taking
+// the frame's next substream.  *d_nck = chunk count.  kErrStream when a
+// frame runs out of substreams, kErrCapacity past cap chunks or maxp rows
+// of a frame (the table is then cut short).
+void launch_rc_chunks(const int64_t* foff, int nf, DevSubFrame* fr, const int64_t* subs,
+                      RcChunk* out, int64_t cap, int64_t maxp, int64_t* d_nck, int* err,
+                      cudaStream_t st);
 // Range-decode every chunk (one warp each) against the cumulative tables
 // (u16[256] rows, entry s = C_{s+1}); codes[row + i] = symbol + 1.  A corrupt
 // substream sets kErrStream.  Same symbols as the host decoder.
 void launch_rc_decode(const RcChunk* ck, int n, const uint16_t* cdf, const uint8_t* in,
                       uint8_t* codes, int* err, cudaStream_t st);
+// The same with the chunk count on the device (*d_n <= cap; grid of cap).
+void launch_rc_decode_dev(const RcChunk* ck, const int64_t* d_n, int64_t cap, const uint16_t* cdf,
+                          const uint8_t* in, uint8_t* codes, int* err, cudaStream_t st);
 
 // ------------------------------------------------------------------ hash --
 struct HashTable {

@@ -127,12 +127,14 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
 }
 
 __global__ void __launch_bounds__(32)
-k_rc_decode(const RcChunk* __restrict__ ck, int n, const uint16_t* __restrict__ cdf,
-            const uint8_t* __restrict__ in, uint8_t* __restrict__ codes, int* err) {
+k_rc_decode(const RcChunk* __restrict__ ck, int n, const int64_t* d_n,
+            const uint16_t* __restrict__ cdf, const uint8_t* __restrict__ in,
+            uint8_t* __restrict__ codes, int* err) {
   extern __shared__ __align__(128) uint8_t sm[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + (size_t)kStages * kStageRows * kRowBytes);
   const int lane = threadIdx.x;
   const int w = blockIdx.x;
+  if (d_n) n = (int)min(*d_n, (int64_t)n);
   if (w >= n) return;
   const RcChunk c = ck[w];
   const int64_t nst = (c.rows + kStageRows - 1) / kStageRows;
@@ -246,7 +248,73 @@ void launch_rc_encode(const RcChunk* ck, int n, const uint32_t* lofreq, uint8_t*
 void launch_rc_decode(const RcChunk* ck, int n, const uint16_t* cdf, const uint8_t* in,
                       uint8_t* codes, int* err, cudaStream_t st) {
   if (n <= 0) return;
-  k_rc_decode<<<n, 32, kDecSmem, st>>>(ck, n, cdf, in, codes, err);
+  k_rc_decode<<<n, 32, kDecSmem, st>>>(ck, n, nullptr, cdf, in, codes, err);
+  count_launches(1);
+}
+
+void launch_rc_decode_dev(const RcChunk* ck, const int64_t* d_n, int64_t cap, const uint16_t* cdf,
+                          const uint8_t* in, uint8_t* codes, int* err, cudaStream_t st) {
+  if (cap <= 0) return;
+  k_rc_decode<<<(unsigned)cap, 32, kDecSmem, st>>>(ck, (int)cap, d_n, cdf, in, codes, err);
+  count_launches(1);
+}
+
+// One block: per frame its chunk count (thread f), the frames' chunk bases
+// (a serial prefix over at most 64 frames), then each frame's chunks written
+// by the whole block.
+__global__ void __launch_bounds__(1024)
+k_rc_chunks(const int64_t* __restrict__ foff, int nf, DevSubFrame* fr,
+            const int64_t* __restrict__ subs, RcChunk* out, int64_t cap, int64_t maxp,
+            int64_t* d_nck, int* err) {
+  __shared__ int64_t base[kMaxBatch + 1], nch[kMaxBatch];
+  const int t = threadIdx.x;
+  if (t < nf) {
+    int64_t cnt = foff[t + 1] - foff[t];
+    if (cnt > maxp) {
+      set_error(err, kErrCapacity);
+      cnt = 0;
+    }
+    nch[t] = (cnt + fr[t].chunk - 1) / fr[t].chunk;
+  }
+  __syncthreads();
+  if (t == 0) {
+    int64_t b = 0;
+    for (int f = 0; f < nf; f++) {
+      base[f] = b;
+      if (b + nch[f] > cap) {
+        set_error(err, kErrCapacity);
+        nch[f] = b < cap ? cap - b : 0;
+      }
+      b += nch[f];
+    }
+    base[nf] = b;
+    *d_nck = b;
+  }
+  __syncthreads();
+  for (int f = 0; f < nf; f++) {
+    const DevSubFrame F = fr[f];
+    const int64_t r0 = foff[f], cnt = foff[f + 1] - foff[f];
+    for (int64_t c = t; c < nch[f]; c += blockDim.x) {
+      const int64_t s = F.next + c;
+      RcChunk k{r0 + c * F.chunk, min(F.chunk, cnt - c * F.chunk), 0, 0};
+      if (s < F.nsub) {
+        k.byte_off = F.in_base + subs[2 * (F.sub0 + s)];
+        k.byte_len = subs[2 * (F.sub0 + s) + 1];
+      } else {
+        set_error(err, kErrStream);  // a frame with too few substreams
+      }
+      out[base[f] + c] = k;
+    }
+  }
+  __syncthreads();
+  if (t < nf) fr[t].next += nch[t];
+}
+
+void launch_rc_chunks(const int64_t* foff, int nf, DevSubFrame* fr, const int64_t* subs,
+                      RcChunk* out, int64_t cap, int64_t maxp, int64_t* d_nck, int* err,
+                      cudaStream_t st) {
+  if (nf <= 0) return;
+  k_rc_chunks<<<1, 1024, 0, st>>>(foff, nf, fr, subs, out, cap, maxp, d_nck, err);
   count_launches(1);
 }
 

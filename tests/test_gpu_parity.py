@@ -422,6 +422,28 @@ def test_corrupt_payload(lpc, blob, host_coding):
     assert np.array_equal(cod.decode(data).cpu().numpy(), want)
 
 
+@pytest.mark.parametrize("n,L,seed,chunk", [(20000, 14, 41, 1024), (3000, 10, 42, 1),
+                                            (9000, 16, 43, 333)])
+def test_repeated_decode_graph_path(lpc, blob, n, L, seed, chunk):
+    """From the second decode on, the network levels run as captured graphs
+    with the substream tables built on the device (no host round trip per
+    level): the same voxels as the oracle on every call, also with one chunk
+    per node."""
+    xyz = synth.random_cloud(n, L, seed)
+    cod = _codec(lpc, blob, L, n, chunk=chunk)
+    data = O.encode(blob, xyz, L, chunk)
+    want = O.decode(blob, data, n)
+    for _ in range(3):
+        assert np.array_equal(cod.decode(data).cpu().numpy(), want)
+    bad = bytearray(data)
+    bad[len(bad) // 2] ^= 0x33
+    try:
+        cod.decode(bytes(bad), cap=n)
+    except lpc.LpcError as e:
+        assert e.status in (lpc.CORRUPT_STREAM, lpc.CAPACITY), e
+    assert np.array_equal(cod.decode(data).cpu().numpy(), want)
+
+
 def test_batch_split_decode(lpc, blob):
     """Batches of 8 frames or more decode in two groups (coarse levels of the
     second decoded on the host while the device decodes the first): the
