@@ -56,6 +56,12 @@ bool Pool::run_one(std::unique_lock<std::mutex>& lk) {
   return true;
 }
 
+static inline void cpu_relax() {
+#if defined(__x86_64__) || defined(__i386__)
+  __builtin_ia32_pause();
+#endif
+}
+
 void Pool::loop() {
   std::unique_lock<std::mutex> lk(mu_);
   for (;;) {
@@ -65,8 +71,10 @@ void Pool::loop() {
       lk.unlock();
       for (int k = 1; spin_.load(std::memory_order_relaxed) &&
                       queued_.load(std::memory_order_relaxed) == 0;
-           k++)
+           k++) {
+        cpu_relax();  // leaves the core's resources to a hyper-thread sibling
         if (k % 64 == 0) std::this_thread::yield();
+      }
       lk.lock();
       continue;
     }
@@ -164,6 +172,7 @@ void coarse_level(Frame& F, int d, CoarsePipe& P, int64_t maxp, std::atomic<int>
     if (status.load(std::memory_order_relaxed)) return;
     if (i >= a) {
       if (fin) break;
+      cpu_relax();
       std::this_thread::yield();
       continue;
     }
