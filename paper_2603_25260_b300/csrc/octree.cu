@@ -45,7 +45,7 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* total,
 }
 
 // ------------------------------------------------------------ radix sort --
-constexpr int kRsThreads = 256, kRsItems = 16, kRsTile = kRsThreads * kRsItems;
+constexpr int kRsThreads = 256, kRsItems = 4, kRsTile = kRsThreads * kRsItems;
 
 int64_t sort_tiles(int64_t n) { return (n + kRsTile - 1) / kRsTile; }
 
@@ -291,7 +291,7 @@ void launch_keys_to_xyz_batch(const uint64_t* keys, const int64_t* d_n, int64_t 
 // ------------------------------------------------- device-size scan pass --
 // Three kernels: per-tile sums, one-block scan of the tile sums, per-element
 // exclusive prefix handed to Op::emit.  Element count is read on the device.
-constexpr int kScThreads = 256, kScItems = 16, kScTile = kScThreads * kScItems;
+constexpr int kScThreads = 256, kScItems = 2, kScTile = kScThreads * kScItems;
 
 int64_t scan_tiles_for(int64_t cap) { return std::max<int64_t>(1, (cap + kScTile - 1) / kScTile); }
 
