@@ -1,5 +1,9 @@
 #include "coder.h"
 
+#if defined(__x86_64__)
+#include <immintrin.h>
+#endif
+
 namespace lpc {
 
 void RangeEncoder::shift_low() {
@@ -24,13 +28,24 @@ RangeDecoder::RangeDecoder(const uint8_t* p, size_t n) : p_(p), end_(p + n) {
   for (int i = 0; i < 5; i++) code_ = (code_ << 8) | next();
 }
 
+// Renormalisation without a loop: after an update range >= 255 (the
+// smallest interval of an adaptive total <= 65568), so at most three bytes
+// come in; they are read before the count is known.
 void RangeDecoder::update(uint32_t lo, uint32_t f) {
   code_ -= r_ * lo;
   range_ = r_ * f;
   if (code_ >= range_) bad_ = true;
-  while (range_ < (1u << 24)) {
-    code_ = (code_ << 8) | next();
-    range_ <<= 8;
+  const int nb = (range_ < (1u << 24)) + (range_ < (1u << 16)) + (range_ < (1u << 8));
+  const uint64_t b0 = p_ < end_ ? p_[0] : 0u, b1 = p_ + 1 < end_ ? p_[1] : 0u,
+                 b2 = p_ + 2 < end_ ? p_[2] : 0u;
+  const uint64_t c = ((uint64_t)code_ << 24) | (b0 << 16) | (b1 << 8) | b2;
+  code_ = (uint32_t)(c >> (24 - 8 * nb));
+  range_ <<= 8 * nb;
+  if (nb > end_ - p_) {
+    bad_ = true;
+    p_ = end_;
+  } else {
+    p_ += nb;
   }
 }
 
@@ -59,26 +74,65 @@ AdaptiveModel::AdaptiveModel() {
 }
 
 void AdaptiveModel::rebuild() {
-  for (int i = 0; i <= 256; i++) tree_[i] = 0;
-  for (int i = 0; i < 255; i++) {
-    for (int k = i + 1; k <= 255; k += k & (-k)) tree_[k] += f_[i];
+  uint32_t c = 0;
+  for (int g = 0; g < 16; g++) {
+    cg_[g] = c;
+    uint32_t w = 0;
+    for (int i = 0; i < 16; i++) {
+      cw_[16 * g + i] = w;
+      w += f_[16 * g + i];
+    }
+    c += w;
   }
 }
 
-uint32_t AdaptiveModel::prefix(int s) const {
-  uint32_t r = 0;
-  for (int k = s; k > 0; k -= k & (-k)) r += tree_[k];
-  return r;
+namespace {
+#if defined(__x86_64__)
+// AVX2 forms, used when the host has AVX2 (checked once at load).
+__attribute__((target("avx2"))) inline int count_above_avx2(const uint32_t* a, uint32_t v) {
+  const __m256i vv = _mm256_set1_epi32((int)v);
+  const __m256i* p = reinterpret_cast<const __m256i*>(a);
+  const unsigned m0 = (unsigned)_mm256_movemask_ps(_mm256_castsi256_ps(
+      _mm256_cmpgt_epi32(_mm256_load_si256(p), vv)));
+  const unsigned m1 = (unsigned)_mm256_movemask_ps(_mm256_castsi256_ps(
+      _mm256_cmpgt_epi32(_mm256_load_si256(p + 1), vv)));
+  return __builtin_popcount(m0 | (m1 << 8));
+}
+__attribute__((target("avx2"))) inline void add_after_avx2(uint32_t* a, int j) {
+  const __m256i jj = _mm256_set1_epi32(j), inc = _mm256_set1_epi32(32);
+  __m256i* p = reinterpret_cast<__m256i*>(a);
+  const __m256i i0 = _mm256_setr_epi32(0, 1, 2, 3, 4, 5, 6, 7);
+  const __m256i i1 = _mm256_setr_epi32(8, 9, 10, 11, 12, 13, 14, 15);
+  _mm256_store_si256(p, _mm256_add_epi32(_mm256_load_si256(p),
+                                         _mm256_and_si256(_mm256_cmpgt_epi32(i0, jj), inc)));
+  _mm256_store_si256(p + 1, _mm256_add_epi32(_mm256_load_si256(p + 1),
+                                             _mm256_and_si256(_mm256_cmpgt_epi32(i1, jj), inc)));
+}
+const bool g_avx2 = __builtin_cpu_supports("avx2");
+#endif
+
+// Number of the 16 values a[0..15] (< 2^31) that exceed v.
+inline int count_above(const uint32_t* a, uint32_t v) {
+#if defined(__x86_64__)
+  if (g_avx2) return count_above_avx2(a, v);
+#endif
+  int n = 0;
+  for (int i = 0; i < 16; i++) n += a[i] > v;
+  return n;
 }
 
-void AdaptiveModel::add(int s, int32_t v) {
-  for (int k = s + 1; k <= 255; k += k & (-k)) tree_[k] += (uint32_t)v;
+// a[i] += 32 for i > j (i < 16).
+inline void add_after(uint32_t* a, int j) {
+#if defined(__x86_64__)
+  if (g_avx2) return add_after_avx2(a, j);
+#endif
+  for (int i = j + 1; i < 16; i++) a[i] += 32;
 }
+}  // namespace
 
 void AdaptiveModel::bump(int s) {
   f_[s] += 32;
   total_ += 32;
-  add(s, 32);
   if (total_ > 65536u) {
     total_ = 0;
     for (int i = 0; i < 255; i++) {
@@ -86,29 +140,28 @@ void AdaptiveModel::bump(int s) {
       total_ += f_[i];
     }
     rebuild();
+    return;
   }
+  add_after(cg_, s >> 4);
+  add_after(cw_ + (s & ~15), s & 15);
 }
 
 void AdaptiveModel::encode(RangeEncoder& e, int s) {
-  e.code_total(prefix(s), f_[s], total_);
+  e.code_total(cg_[s >> 4] + cw_[s], f_[s], total_);
   bump(s);
 }
 
 int AdaptiveModel::decode(RangeDecoder& d) {
   const uint32_t v = d.target(total_);
-  // largest s with prefix(s) <= v (binary lifting over the Fenwick tree)
-  int pos = 0;
-  uint32_t rem = v;
-  for (int step = 128; step; step >>= 1) {
-    if (pos + step <= 255 && tree_[pos + step] <= rem) {
-      pos += step;
-      rem -= tree_[pos];
-    }
-  }
-  if (pos > 254) pos = 254;
-  d.update(v - rem, f_[pos]);
-  bump(pos);
-  return pos;
+  // the last group whose lower bound is <= v, then the last symbol in it;
+  // symbol 255 (count 0) shares its bound with the end of the range, never
+  // below v, so it is never chosen
+  const int g = 15 - count_above(cg_, v);
+  int s = 16 * g + 15 - count_above(cw_ + 16 * g, v - cg_[g]);
+  if (s > 254) s = 254;
+  d.update(cg_[g] + cw_[s], f_[s]);
+  bump(s);
+  return s;
 }
 
 size_t encode_packed(const uint32_t* lofreq, size_t n, uint8_t* out, size_t cap) {

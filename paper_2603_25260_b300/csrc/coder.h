@@ -75,9 +75,13 @@ class RangeDecoder {
 };
 
 // Adaptive frequencies of the 255 symbols: start at 1, +32 per coded symbol,
-// every count halved (rounding up) once the total exceeds 2^16.  Kept in a
-// Fenwick tree so that cumulative lookups and the decoder's search are
-// logarithmic.
+// every count halved (rounding up) once the total exceeds 2^16.  Cumulative
+// counts are kept in two levels, 16 groups of 16 symbols: cg[g] = counts
+// before group g, cw[s] = counts before s within its group.  The decoder's
+// search compares the target with the 16 group bounds, then with the 16
+// bounds inside the group (AVX2 compares and a popcount where the host has
+// AVX2, plain loops elsewhere); a coded symbol adds 32 to the bounds after
+// it (masked adds over 16 lanes).
 class AdaptiveModel {
  public:
   AdaptiveModel();
@@ -85,12 +89,11 @@ class AdaptiveModel {
   int decode(RangeDecoder& d);
 
  private:
-  uint32_t prefix(int s) const;  // sum of f[0..s)
-  void add(int s, int32_t v);
   void rebuild();
   void bump(int s);
+  alignas(32) uint32_t cg_[16];
+  alignas(32) uint32_t cw_[256];
   uint32_t f_[256];
-  uint32_t tree_[257];
   uint32_t total_;
 };
 
