@@ -71,6 +71,11 @@ int lpc_t_prelu_bwd(const float* x, const float* dy, int64_t N, int C, const flo
 int lpc_t_fq_fwd(const float* x, int64_t n, float s, int z, float* y, uint8_t* mask,
                  uint64_t stream);
 int lpc_t_fq_bwd(const float* dy, const uint8_t* mask, int64_t n, float* dx, uint64_t stream);
+/* Weight fake quantisation with the scale found on the device: s = max|w|/127
+ * (max|w| at least 1e-12; formed in double, rounded to float), then the same
+ * as lpc_t_fq_fwd with z = 0 (no host round trip for the scale).  w, y, mask
+ * device arrays of n elements owned by the caller. */
+int lpc_t_fq_w(const float* w, int64_t n, float* y, uint8_t* mask, uint64_t stream);
 
 /* Octree levels with parent rows and child offsets, for the index
  * structures above: concatenations over depths 0..L (keys, par) and

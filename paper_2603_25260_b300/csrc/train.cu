@@ -236,6 +236,33 @@ __global__ void k_fq_f(const float* x, int64_t n, float s, int z, float* y, uint
     mask[q] = r >= -128.f && r <= 127.f;
   }
 }
+// Weights: the symmetric per-tensor scale max|w| / 127 (at least 1e-12 / 127)
+// found on the device by one block, then the same rounding as k_fq_f with
+// z = 0; the scale is formed in double and rounded to float like a host-side
+// max(...) / 127.0 passed as a float.
+__global__ void __launch_bounds__(1024) k_fq_w(const float* w, int64_t n, float* y,
+                                               uint8_t* mask) {
+  __shared__ float red[32];
+  float m = 0.f;
+  for (int64_t q = threadIdx.x; q < n; q += blockDim.x) m = fmaxf(m, fabsf(w[q]));
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    m = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0) red[0] = m;
+  }
+  __syncthreads();
+  const float s = (float)((double)fmaxf(red[0], 1e-12f) / 127.0);
+  for (int64_t q = threadIdx.x; q < n; q += blockDim.x) {
+    const float r = rintf(w[q] / s);
+    const float c = fminf(fmaxf(r, -128.f), 127.f);
+    y[q] = c * s;
+    mask[q] = r >= -128.f && r <= 127.f;
+  }
+}
+
 __global__ void k_fq_b(const float* dy, const uint8_t* mask, int64_t n, float* dx) {
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
        q += (int64_t)gridDim.x * blockDim.x)
@@ -398,6 +425,14 @@ int lpc_t_fq_fwd(const float* x, int64_t n, float s, int z, float* y, uint8_t* m
   if (n < 0 || !(s > 0.f) || z < -128 || z > 127) return LPC_INVALID_ARG;
   if (n == 0) return LPC_OK;
   k_fq_f<<<grid_for(n), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(x, n, s, z, y, mask);
+  count_launches(1);
+  return cudaGetLastError() == cudaSuccess ? LPC_OK : LPC_CUDA_ERROR;
+}
+
+int lpc_t_fq_w(const float* w, int64_t n, float* y, uint8_t* mask, uint64_t stream) {
+  if (n < 0) return LPC_INVALID_ARG;
+  if (n == 0) return LPC_OK;
+  k_fq_w<<<1, 1024, 0, reinterpret_cast<cudaStream_t>(stream)>>>(w, n, y, mask);
   count_launches(1);
   return cudaGetLastError() == cudaSuccess ? LPC_OK : LPC_CUDA_ERROR;
 }

@@ -47,6 +47,7 @@ def _lib():
             "lpc_t_prelu_bwd": [P_, P_, I64, I32, P_, P_, P_, C.c_uint64],
             "lpc_t_fq_fwd": [P_, I64, C.c_float, I32, P_, P_, C.c_uint64],
             "lpc_t_fq_bwd": [P_, P_, I64, P_, C.c_uint64],
+            "lpc_t_fq_w": [P_, I64, P_, P_, C.c_uint64],
             "lpc_t_levels": [P_, I64, I32, P_, P_, P_, P_, P_, I64, C.c_uint64],
         }
         for name, args in sig.items():
@@ -223,9 +224,30 @@ class RoundBF16(torch.autograd.Function):
         return g
 
 
+class FakeQuantWFn(torch.autograd.Function):
+    """Per-tensor symmetric weight fake quantisation (scale max|w| / 127 found
+    on the device, no host round trip) with a straight-through gradient."""
+
+    @staticmethod
+    def forward(ctx, w):
+        w = w.contiguous()
+        y = torch.empty_like(w)
+        mask = torch.empty(w.shape, dtype=torch.uint8, device=w.device)
+        _ck(_lib().lpc_t_fq_w(_p(w), w.numel(), _p(y), _p(mask), _st()), "fq w")
+        ctx.save_for_backward(mask)
+        return y
+
+    @staticmethod
+    def backward(ctx, dy):
+        (mask,) = ctx.saved_tensors
+        dx = torch.empty_like(dy)
+        _ck(_lib().lpc_t_fq_bwd(_p(dy.contiguous()), _p(mask), dy.numel(), _p(dx), _st()),
+            "fq bwd")
+        return dx
+
+
 def fq_w(w):
-    s = float(w.detach().abs().max().clamp_min(1e-12)) / 127.0
-    return FakeQuantFn.apply(w, s, 0)
+    return FakeQuantWFn.apply(w)
 
 
 # ------------------------------------------------------------ structures --
@@ -375,14 +397,14 @@ def train_step(model: QATModel, opt, frames: list[Frame]) -> float:
     gradient norm clipped at 1.0 (supplement, training settings)."""
     opt.zero_grad(set_to_none=True)
     npts = sum(f.n for f in frames)
-    total = 0.0
+    total = None
     for f in frames:
         loss = model.bits(f) / npts
         loss.backward()
-        total += float(loss.detach())
+        total = loss.detach() if total is None else total + loss.detach()
     torch.nn.utils.clip_grad_norm_(model.parameters(), 1.0)
     opt.step()
-    return total
+    return float(total)  # the one host round trip of the step
 
 
 def make_optimizer(model: QATModel):

@@ -238,6 +238,24 @@ def test_model_gradients_bf16(frames):
     assert _rel(_flat(gg), _flat(gx)) < 2e-2
 
 
+@pytest.mark.parametrize("shape,scale", [((27, 32, 64), 0.05), ((255, 32), 3.0), ((7,), 1e-3)])
+def test_weight_fake_quant_device_scale(shape, scale):
+    """Weight fake quantisation with the scale max|w| / 127 found on the
+    device equals torch's per-tensor fake quantiser at the scale formed on the
+    host, values and gradients."""
+    from paper_2603_25260_b300 import train as G
+    g = torch.Generator().manual_seed(31)
+    w = torch.randn(*shape, generator=g) * scale
+    ws = w.cuda().requires_grad_()
+    gy = torch.randn(*shape, generator=g)
+    y, (dw,) = _grads(G.FakeQuantWFn.apply, (ws,), gy.cuda())
+    s = float(w.abs().max().clamp_min(1e-12)) / 127.0
+    w2 = w.clone().requires_grad_()
+    yr = torch.fake_quantize_per_tensor_affine(w2, s, 0, -128, 127)
+    (dwr,) = torch.autograd.grad(yr, [w2], gy)
+    assert torch.equal(y.cpu(), yr.detach()) and torch.equal(dw.cpu(), dwr)
+
+
 def test_model_gradients_qat(frames):
     """Fake-quantised forward: fp32 and FP64 can round an activation that sits
     on a half-step boundary differently, so the bound is looser than without
