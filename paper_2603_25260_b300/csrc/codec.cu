@@ -252,6 +252,7 @@ Codec::~Codec() {
   for (auto e : tev_)
     if (e) cudaEventDestroy(e);
   if (gs_) cudaStreamDestroy(gs_);
+  if (cs_) cudaStreamDestroy(cs_);
   for (auto e : ev_) cudaEventDestroy(e);
   for (auto e : pev_) cudaEventDestroy(e);
   if (dmem_) cudaFree(dmem_);
@@ -423,6 +424,10 @@ int Codec::create(const lpc_config& cfg, const void* blob, size_t len) {
       cudaEventCreateWithFlags(&gev_[1], cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
     gs_ = nullptr;  // no graphs: direct launches
+  }
+  if (cudaStreamCreateWithFlags(&cs_, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    cs_ = nullptr;
   }
   ev_.resize(512);
   for (auto& e : ev_) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
@@ -890,7 +895,23 @@ int Codec::encode(int nf, const int32_t* const* xyz, const int64_t* n, const int
   if (nd > 0) {
     begin_batch();
     build_levels_device(nd, dx.data(), dn.data(), true);
-    if (int s = sync_and_check("encode: octree")) return s;
+    // once every level's network is a captured graph (sizes read on the
+    // device), the network is queued behind the octree before the host has
+    // its sizes, and the host's copies go through the copy stream
+    bool early = gs_ && cs_ && !prof.mask;
+    for (int j = 0; j < 5 && early; j++) early = gexec_[kPredEnc][j] != nullptr;
+    if (early) {
+      cudaMemcpyAsync(h_err_, d_err_, 4, cudaMemcpyDeviceToHost, st_);
+      cudaEventRecord(ev_[8], st_);
+      for (int j = 0; j < 5; j++) run_level(j, kPredEnc, nullptr, d_enc_ + (size_t)j * P_);
+      if (cudaEventSynchronize(ev_[8]) != cudaSuccess) return cuda_check("encode: octree");
+      if (*h_err_ != 0) {
+        cudaStreamSynchronize(st_);
+        if (int s = check_device_error()) return s;
+      }
+    } else {
+      if (int s = sync_and_check("encode: octree")) return s;
+    }
     stats.phase_us[0] = now_us() - t0;
     for (int h = 0; h < kHeights; h++) N_[h] = h_N_[h];
     level_bytes();
@@ -908,16 +929,18 @@ int Codec::encode(int nf, const int32_t* const* xyz, const int64_t* n, const int
     }
     uint8_t* hcc = static_cast<uint8_t*>(hgrow(h_ccodes_, ctot + 16));
     if (!hcc) return fail(LPC_CUDA_ERROR, "encode: pinned allocation failed");
-    cudaMemcpyAsync(h_codes_ + 6 * P_, code_[6], N_[6], cudaMemcpyDeviceToHost, st_);
+    cudaStream_t cst = early ? cs_ : st_;
+    if (early) cudaStreamWaitEvent(cs_, ev_[8], 0);
+    cudaMemcpyAsync(h_codes_ + 6 * P_, code_[6], N_[6], cudaMemcpyDeviceToHost, cst);
     for (int h = kHeights; h <= max_h_; h++)
       cudaMemcpyAsync(hcc + hoff[h], coarse_codes(h), (size_t)h_cN_[h], cudaMemcpyDeviceToHost,
-                      st_);
-    cudaEventRecord(ev_[0], st_);
+                      cst);
+    cudaEventRecord(ev_[0], cst);
     // network levels of all frames: (C_s, f_s) of the true symbol of every
     // node; each level's intervals go to the host as soon as it is done
     for (int j = 0; j < 5; j++) {
       const int h = 5 - j;
-      run_level(j, kPredEnc, nullptr, d_enc_ + (size_t)j * P_);
+      if (!early) run_level(j, kPredEnc, nullptr, d_enc_ + (size_t)j * P_);
       if (!dev_rc_) {
         cudaMemcpyAsync(h_enc_ + (size_t)j * P_, d_enc_ + (size_t)j * P_, 4 * N_[h],
                         cudaMemcpyDeviceToHost, st_);

@@ -168,6 +168,7 @@ class Codec {
   int64_t gridn(int h) const { return cap_grid_ ? P_ : N_[h]; }
   bool cap_grid_ = false;
   cudaStream_t gs_ = nullptr;
+  cudaStream_t cs_ = nullptr;  // copies that overlap the network (encoder's coarse codes)
   cudaEvent_t gev_[2] = {};
   cudaGraphExec_t gexec_[3][5] = {};
   int gkern_[3][5] = {};
