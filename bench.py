@@ -285,7 +285,7 @@ def run_ours(args):
 
     def step():
         ln = codec.encode_into(x, outbuf)
-        codec.decode(outbuf[:ln].tobytes(), out=out_dev)
+        codec.decode(outbuf[:ln], out=out_dev)
         return ln
 
     # host cores on the GPU machine run slower for a while after any idle spell
@@ -332,7 +332,7 @@ def run_ours(args):
         ev[k][0].record(stream)
         ln = codec.encode_into(x, outbuf)
         ev[k][1].record(stream)
-        codec.decode(outbuf[:ln].tobytes(), out=out_dev)
+        codec.decode(outbuf[:ln], out=out_dev)
         ev[k][2].record(stream)
     torch.cuda.synchronize()
     gpu_launches = lpc.kernel_launches() - launches0
@@ -364,7 +364,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         x_dev.copy_(x_host, non_blocking=True)
         ln = codec.encode_into(x_dev, outbuf)
-        dec = codec.decode(outbuf[:ln].tobytes(), out=out_dev)
+        dec = codec.decode(outbuf[:ln], out=out_dev)
         n_out = dec.shape[0]
         y_host[:n_out].copy_(dec, non_blocking=True)
         torch.cuda.synchronize()
@@ -392,7 +392,7 @@ def run_ours(args):
     hcodec = lpc.Codec(blob, spec.L, n, chunk=args.chunk, host_coding=True)
     for _ in range(max(args.warmup, 10)):
         ln = hcodec.encode_into(x, outbuf)
-        hcodec.decode(outbuf[:ln].tobytes(), out=out_dev)
+        hcodec.decode(outbuf[:ln], out=out_dev)
     hms = []
     for _ in range(3):
         flush.zero_()
@@ -400,7 +400,7 @@ def run_ours(args):
         a.record(stream)
         ln = hcodec.encode_into(x, outbuf)
         b.record(stream)
-        hcodec.decode(outbuf[:ln].tobytes(), out=out_dev)
+        hcodec.decode(outbuf[:ln], out=out_dev)
         c.record(stream)
         torch.cuda.synchronize()
         hms.append((a.elapsed_time(b), b.elapsed_time(c)))
@@ -421,7 +421,7 @@ def run_ours(args):
         tbuf = np.empty_like(outbuf)  # outbuf keeps the seeded blob's stream
         for _ in range(max(args.warmup, 10)):
             ln = tcodec.encode_into(x, tbuf)
-            tcodec.decode(tbuf[:ln].tobytes(), out=out_dev)
+            tcodec.decode(tbuf[:ln], out=out_dev)
         tms = []
         for _ in range(5):
             flush.zero_()
@@ -429,7 +429,7 @@ def run_ours(args):
             a.record(stream)
             ln = tcodec.encode_into(x, tbuf)
             b.record(stream)
-            tcodec.decode(tbuf[:ln].tobytes(), out=out_dev)
+            tcodec.decode(tbuf[:ln], out=out_dev)
             c.record(stream)
             torch.cuda.synchronize()
             tms.append((a.elapsed_time(b), b.elapsed_time(c)))
@@ -584,7 +584,7 @@ def run_ncu_case(args):
 
         def step():
             ln = codec.encode_into(x, buf)
-            codec.decode(buf[:ln].tobytes(), out=out)
+            codec.decode(buf[:ln], out=out)
             return ln
     else:
         specs = synth.batch_specs(args.batch_frames)

@@ -156,7 +156,9 @@ class Codec:
                                            out.ctypes.data, out.nbytes, C.byref(ln)))
         return ln.value
 
-    def decode(self, data: bytes, cap: int | None = None, out: torch.Tensor | None = None):
+    def decode(self, data, cap: int | None = None, out: torch.Tensor | None = None):
+        """Decode one stream (bytes or a contiguous uint8 numpy array, read in
+        place) into device voxels [n, 3] int32 (out: optional caller buffer)."""
         cap = cap if cap is not None else self.max_points
         if out is None:
             out = torch.empty((max(cap, 1), 3), dtype=torch.int32, device="cuda")
