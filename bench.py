@@ -22,6 +22,7 @@ ranks.  `--impl reference` times the CPU oracle as the reference arm.
 from __future__ import annotations
 
 import argparse
+import gc
 import hashlib
 import json
 import os
@@ -320,6 +321,9 @@ def run_ours(args):
     dom_idx = lpc.Codec.FAMILIES.index(dominant)
     codec.profile(1 << dom_idx)
 
+    # the harness's own garbage collection stays out of the timed loops
+    gc.collect()
+    gc.disable()
     clocks = Clocks(local)
     if world > 1:
         dist.barrier()
@@ -381,6 +385,7 @@ def run_ours(args):
             break
     e2e_warm = len(warm)
     e2e_ms = [e2e_step() for _ in range(args.steps)]
+    gc.enable()
     e2e_total = sum(e2e_ms)
     if world > 1:
         t = torch.tensor([e2e_total], device="cuda")
