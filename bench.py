@@ -447,6 +447,27 @@ def run_ours(args):
                    "encode_mpts": round(n / (te / 1e3) / 1e6, 4),
                    "decode_mpts": round(n / (td / 1e3) / 1e6, 4)}
 
+    # the float inference variant (the float network, tables from a float
+    # softmax): how many table rows come out differently when the softmax of
+    # the same logits runs on the CPU instead of the GPU
+    float_variant = None
+    if not args.no_train:
+        from paper_2603_25260_b300 import float_variant as FV
+        from paper_2603_25260_b300 import train as TR
+        fr = TR.Frame(x, spec.L)
+        fmodel = TR.QATModel(synth.twin_params(0), qat=False, bf16=False)
+        with torch.no_grad():
+            flog = fmodel.level_logits(fr)
+        rows = differ = 0
+        for lg in flog.values():
+            differ += int((FV.float_cdf(lg).cpu() != FV.float_cdf(lg.cpu())).any(dim=1).sum())
+            rows += lg.shape[0]
+        float_variant = {"rows": rows, "rows_differing_gpu_vs_cpu_softmax": differ,
+                         "integer_rows_differing": 0,
+                         "note": "integer tables are identical on the GPU and in the CPU oracle "
+                                 "(tests/test_gpu_parity.py); float tables are not"}
+        del fr, fmodel, flog
+
     # batched form: the mixed-size 64-frame batch, whole batch per step
     batched = None
     if not args.no_batch and args.batch_frames > 0:
@@ -550,6 +571,7 @@ def run_ours(args):
         "batched": batched,
         "host_coding": host_coding,
         "trained_blob": trained,
+        "float_variant": float_variant,
         "train": train,
         "e2e": {"value": round(e2e_value, 4), "unit": "Mpoints/s",
                 "step_ms": [round(t, 3) for t in e2e_ms], "warmup_steps": e2e_warm,

@@ -324,6 +324,24 @@ class QATModel(torch.nn.Module):
         return torch.nn.functional.linear(x, W, b)
 
     def bits(self, fr: Frame) -> torch.Tensor:
+        """Rate of the five network levels in bits (cross-entropy / ln 2)."""
+        def ce(logits, d):
+            return torch.nn.functional.cross_entropy(logits, fr.Y[d] - 1,
+                                                     reduction="sum") / math.log(2.0)
+        return self._levels(fr, ce, self.recompute)
+
+    def level_logits(self, fr: Frame) -> dict:
+        """The float network's logits [N_d, 255] of every network level d (the
+        float inference variant)."""
+        out = {}
+
+        def keep(logits, d):
+            out[d] = logits
+            return logits.new_zeros(())
+        self._levels(fr, keep, False)
+        return out
+
+    def _levels(self, fr: Frame, head, recompute: bool) -> torch.Tensor:
         b, t, P, q, w, bf = fr.b, fr.t, self.P, self.q, self.w, self.bf16
 
         def prelu(x, name):
@@ -349,9 +367,7 @@ class QATModel(torch.nn.Module):
         def emb(name, d):
             return EmbedFn.apply(fr.codes[d], P(name))
 
-        def ce(logits, d):
-            return torch.nn.functional.cross_entropy(logits, fr.Y[d] - 1,
-                                                     reduction="sum") / math.log(2.0)
+        ce = head
 
         def level0():
             Fb = upl("UP_0", b, emb("E_0", b - 1))
@@ -379,7 +395,7 @@ class QATModel(torch.nn.Module):
 
         # with recompute, each relative level keeps only its outputs; its
         # activations are recomputed in the backward pass
-        run = ((lambda f, *a: checkpoint(f, *a, use_reentrant=False)) if self.recompute
+        run = ((lambda f, *a: checkpoint(f, *a, use_reentrant=False)) if recompute
                else (lambda f, *a: f(*a)))
         Fb, bits = run(level0)
         Ft, b1 = run(level1, Fb)
