@@ -73,6 +73,38 @@ def dist_env():
     return rank, world, local
 
 
+# ------------------------------------------------------------ multi-rank --
+
+def max_over_ranks(x: float, world: int) -> float:
+    """The largest x over the ranks (the job's time is its slowest rank's);
+    the tensor lives where the process group's backend expects it."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, world: int) -> float:
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def shard_frames(n_frames: int, rank: int, world: int) -> list[int]:
+    """Frames of a batch coded by this rank: round robin (frames are
+    independent; no exchange between ranks)."""
+    return list(range(rank, n_frames, world))
+
+
 # ---------------------------------------------------------------- clocks --
 
 class Clocks:
@@ -344,11 +376,8 @@ def run_ours(args):
     step_ms = [a.elapsed_time(c) for a, b, c in ev]
     enc_ms = [a.elapsed_time(b) for a, b, c in ev]
     dec_ms = [b.elapsed_time(c) for a, b, c in ev]
-    total_ms = sum(step_ms)
+    total_ms = max_over_ranks(sum(step_ms), world)
     if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
         dist.barrier()
     torch.cuda.synchronize()
     value = world * n * args.steps / (total_ms / 1e3) / 1e6
@@ -386,11 +415,7 @@ def run_ours(args):
     e2e_warm = len(warm)
     e2e_ms = [e2e_step() for _ in range(args.steps)]
     gc.enable()
-    e2e_total = sum(e2e_ms)
-    if world > 1:
-        t = torch.tensor([e2e_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
+    e2e_total = max_over_ranks(sum(e2e_ms), world)
     e2e_value = world * n * args.steps / (e2e_total / 1e3) / 1e6
 
     # the same step with the network levels range coded on host threads
@@ -471,7 +496,9 @@ def run_ours(args):
     # batched form: the mixed-size 64-frame batch, whole batch per step
     batched = None
     if not args.no_batch and args.batch_frames > 0:
-        specs = synth.batch_specs(args.batch_frames)
+        # every rank codes its round-robin share of the batch's frames
+        specs = [synth.batch_specs(args.batch_frames)[i]
+                 for i in shard_frames(args.batch_frames, rank, world)]
         frames = [synth.make_frame(s) for s in specs]
         Ls = [s.L for s in specs]
         bcodec = lpc.Codec(blob, max(Ls), max(f.shape[0] for f in frames),
@@ -505,10 +532,15 @@ def run_ours(args):
         torch.cuda.synchronize()
         bfams = bcodec.profile_read()
         bcodec.profile(0)
-        batched = {"frames": len(frames), "points": npts,
-                   "value": round(npts / ((be + bd) / 1e3) / 1e6, 4),
-                   "encode_mpts": round(npts / (be / 1e3) / 1e6, 4),
-                   "decode_mpts": round(npts / (bd / 1e3) / 1e6, 4),
+        # the whole batch over all ranks: points summed, time of the slowest
+        all_pts = sum_over_ranks(npts, world)
+        t_all = max_over_ranks(be + bd, world)
+        be_all, bd_all = max_over_ranks(be, world), max_over_ranks(bd, world)
+        batched = {"frames": args.batch_frames, "frames_this_rank": len(frames),
+                   "points": int(all_pts),
+                   "value": round(all_pts / (t_all / 1e3) / 1e6, 4),
+                   "encode_mpts": round(all_pts / (be_all / 1e3) / 1e6, 4),
+                   "decode_mpts": round(all_pts / (bd_all / 1e3) / 1e6, 4),
                    "bits_per_point": round(8 * sum(n for _, n in spans) / npts, 4),
                    "families": {k: {"ms": round(v["ms"], 4), "launches": v["launches"]}
                                 for k, v in bfams.items()},
