@@ -97,7 +97,8 @@ def train(steps: int, lr: float = 1e-3, seed: int = 0, log_every: int = 50) -> t
     from . import train as T
 
     specs = synth.training_specs()
-    frames = [T.Frame(torch.from_numpy(synth.make_frame(s)).cuda(), s.L) for s in specs]
+    frames = [T.BatchFrame([T.Frame(torch.from_numpy(synth.make_frame(s)).cuda(), s.L)
+                            for s in specs])]
     model = T.QATModel(synth.twin_params(seed), qat=True, bf16=False)
     opt = torch.optim.AdamW(model.parameters(), lr=lr, weight_decay=1e-4)
     hist = []

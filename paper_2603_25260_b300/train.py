@@ -291,6 +291,40 @@ class Frame:
                                            self.off[b])
 
 
+class BatchFrame:
+    """Frames of one depth L as a single frame: the rows of each level laid
+    out frame after frame, with parent rows, child offsets and kernel-map
+    entries shifted by the rows of the frames before.  No row of one frame
+    refers to a row of another, so every op sees the union of disjoint trees;
+    its rate is the sum of the frames' rates and each op runs once per batch
+    instead of once per frame."""
+
+    def __init__(self, frames: list):
+        L = frames[0].L
+        if any(f.L != L for f in frames):
+            raise ValueError("a batch holds frames of one depth")
+        self.L, self.b, self.t = L, L - 5, L - 4
+        self.n = sum(f.n for f in frames)
+        self.N = [sum(f.N[d] for f in frames) for d in range(L + 1)]
+        # R[d][i]: rows of level d in frames 0..i-1
+        R = [np.concatenate([[0], np.cumsum([f.N[d] for f in frames])]).tolist()
+             for d in range(L + 1)]
+        self.keys, self.codes, self.par, self.off, self.Y = {}, {}, {}, {}, {}
+        for d in range(L + 1):
+            self.keys[d] = torch.cat([f.keys[d] for f in frames])
+            if d > 0:
+                self.par[d] = torch.cat([f.par[d] + R[d - 1][i] for i, f in enumerate(frames)])
+            if d < L:
+                self.codes[d] = torch.cat([f.codes[d] for f in frames])
+                tail = torch.full((1,), self.N[d + 1], dtype=torch.int32, device="cuda")
+                self.off[d] = torch.cat([f.off[d][:-1] + R[d + 1][i]
+                                         for i, f in enumerate(frames)] + [tail])
+                self.Y[d] = self.codes[d].long()
+        self.nbr = {d: torch.cat([torch.where(f.nbr[d] >= 0, f.nbr[d] + R[d][i], f.nbr[d])
+                                  for i, f in enumerate(frames)])
+                    for d in (self.b, self.t)}
+
+
 # ------------------------------------------------------------------ model --
 
 ACT_SCALE = 1.0 / 32.0
@@ -408,9 +442,11 @@ class QATModel(torch.nn.Module):
         return {k: self.P(k).grad.detach().cpu().double().numpy() for k in self.names}
 
 
-def train_step(model: QATModel, opt, frames: list[Frame]) -> float:
+def train_step(model: QATModel, opt, frames: list) -> float:
     """One step on a batch of frames: bits per point of the batch, AdamW,
-    gradient norm clipped at 1.0 (supplement, training settings)."""
+    gradient norm clipped at 1.0 (supplement, training settings).  Each
+    element is a Frame or a BatchFrame (one forward and backward pass per
+    element)."""
     opt.zero_grad(set_to_none=True)
     npts = sum(f.n for f in frames)
     total = None

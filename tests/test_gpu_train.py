@@ -295,3 +295,49 @@ def test_recompute_matches(frames):
     assert out[0][0] == pytest.approx(out[1][0], rel=1e-6)
     name, err = _worst(out[1][1], out[0][1])
     assert err < 1e-5, (name, err)
+
+
+def test_batch_frame_equals_sum_of_frames():
+    """Frames laid out as one batch frame: the same structures shifted by the
+    rows before them, per-row logits equal to each frame's own, and the rate
+    and gradients of the batch equal to the sums over the frames (up to the
+    order of the accumulations)."""
+    import dataclasses
+
+    from paper_2603_25260_b300 import train as G
+    specs = [dataclasses.replace(synth.GRADCHECK, seed=4000 + 17 * i) for i in range(3)]
+    frs = [G.Frame(torch.from_numpy(synth.make_frame(s)).cuda(), s.L) for s in specs]
+    bf = G.BatchFrame(frs)
+    L = bf.L
+    assert bf.n == sum(f.n for f in frs)
+    for d in range(L):
+        off = bf.off[d].cpu().numpy().astype(np.int64)
+        assert off[0] == 0 and off[-1] == bf.N[d + 1] == bf.keys[d + 1].shape[0]
+        pc = [bin(int(c)).count("1") for c in bf.codes[d].cpu().numpy()]
+        np.testing.assert_array_equal(np.diff(off), pc)
+        par = bf.par[d + 1].cpu().numpy().astype(np.int64)
+        np.testing.assert_array_equal(par, np.repeat(np.arange(bf.N[d]), pc))
+    for d in (bf.b, bf.t):
+        nb = bf.nbr[d].cpu().numpy()
+        assert nb.shape == (bf.N[d], 27) and nb.max() < bf.N[d]
+        np.testing.assert_array_equal(nb[:, 13], np.arange(bf.N[d]))
+    params = T.init_params(9)
+    m = G.QATModel(params, qat=True, bf16=0)
+    lb = m.level_logits(bf)
+    row = {d: 0 for d in lb}
+    for f in frs:
+        for d, lg in m.level_logits(f).items():
+            torch.testing.assert_close(lb[d][row[d]:row[d] + lg.shape[0]], lg, rtol=1e-6,
+                                       atol=1e-6)
+            row[d] += lg.shape[0]
+    bits_b, gb = _model_grads(bf, params, qat=True, bf16=0)
+    m = G.QATModel(params, qat=True, bf16=0)
+    bits_s = 0.0
+    for f in frs:
+        bits = m.bits(f)
+        bits.backward()
+        bits_s += float(bits.detach())
+    torch.cuda.synchronize()
+    assert bits_b == pytest.approx(bits_s, rel=1e-5)
+    name, err = _worst(gb, m.grads())
+    assert err < 1e-5, (name, err)
