@@ -552,16 +552,22 @@ typedef struct {
 } rec;
 
 #define MAXREC 64
+/* Architectures (Sec. 4.4, Table 4): the paper's model and its two ablations */
+enum { ARCH_XFP = 0, ARCH_GRED = 1, ARCH_BASE = 2 };
+
 typedef struct {
   int C;
+  int arch; /* ARCH_* */
+  int toff; /* t = L - toff (Sec. 3.2; supplement, choice of t): 4 or 3 */
   uint32_t lut[256];
   uint64_t hash;
   int nrec;
   rec r[MAXREC];
   /* named slots, by relative level j = d - b */
-  rec *E0, *UP0, *E1, *UP1;
+  rec *ESH[5], *USH[5]; /* level b, and the propagated levels down to t */
   rec *RA[5], *RB[5], *RM[5], *P1[5], *P2[5], *G[5];
   rec *D[5][3], *E[5][3], *UP[5][3];
+  int span[5]; /* m = d - k of a level extracted at level k (0: propagated) */
 } model;
 
 static size_t pad16(size_t n) { return (n + 15) & ~(size_t)15; }
@@ -578,6 +584,10 @@ static int parse_blob(const void* blob, size_t len, model* M) {
   if (rd_u32(b + 4) != 1) return OR_INVALID_ARG;
   M->C = rd_u32(b + 8);
   M->nrec = rd_u32(b + 12);
+  M->arch = rd_u32(b + 20);
+  M->toff = rd_u32(b + 24) == 0 ? 4 : rd_u32(b + 24);
+  if (M->arch < ARCH_XFP || M->arch > ARCH_BASE || (M->toff != 3 && M->toff != 4))
+    return OR_INVALID_ARG;
   if (M->C < 8 || M->C > 128 || M->C % 8 || rd_u32(b + 16) != 256) return OR_INVALID_ARG;
   if (M->nrec < 1 || M->nrec > MAXREC) return OR_INVALID_ARG;
   for (int i = 0; i < 256; i++) M->lut[i] = (uint32_t)rd_u32(b + 32 + 4 * i);
@@ -650,27 +660,38 @@ static int bind_model(model* M) {
       return OR_INVALID_ARG;                                                               \
     (slot) = r_;                                                                           \
   } while (0)
-  TAKE(M->E0, K_EMB, 1, 256, C, 0);
-  TAKE(M->UP0, K_SEL, 8, C, C, 1);
+  /* level b: F^b = Up(E_0[Y_{b-1}]) with no earlier features, every architecture */
+  TAKE(M->ESH[0], K_EMB, 1, 256, C, 0);
+  TAKE(M->USH[0], K_SEL, 8, C, C, 1);
   TAKE(M->P1[0], K_SUM, 1, C, C, 1);
   TAKE(M->P2[0], K_SUM, 1, C, NSYM, 0);
-  TAKE(M->RA[1], K_SUM, 27, C, C, 1);
-  TAKE(M->RB[1], K_SUM, 27, C, C, 0);
-  TAKE(M->RM[1], K_RES, 2, C, C, 1);
-  TAKE(M->E1, K_EMB, 1, 256, C, 0);
-  TAKE(M->UP1, K_SEL, 8, 2 * C, C, 1);
-  TAKE(M->P1[1], K_SUM, 1, C, C, 1);
-  TAKE(M->P2[1], K_SUM, 1, C, NSYM, 0);
-  for (int j = 2; j < 5; j++) {
-    int m = j - 1;
-    TAKE(M->G[j], K_EMB, 1, 256, C, 0);
-    for (int k = 1; k < m; k++) TAKE(M->D[j][k], K_SUM, 8, C, C, 1);
-    TAKE(M->RA[j], K_SUM, 27, 2 * C, C, 1);
-    TAKE(M->RB[j], K_SUM, 27, C, C, 0);
-    TAKE(M->RM[j], K_RES, 2, C, C, 1);
-    for (int k = 0; k < m; k++) {
-      TAKE(M->E[j][k], K_EMB, 1, 256, C, 0);
-      TAKE(M->UP[j][k], K_SEL, 8, 2 * C, C, 1);
+  const int nsh = 5 - M->toff; /* relative levels 1..nsh lie at or above t */
+  for (int j = 1; j < 5; j++) {
+    if (M->arch == ARCH_XFP && j <= nsh) { /* propagated shallow level (Eq. 8-9) */
+      M->span[j] = 0;
+      TAKE(M->RA[j], K_SUM, 27, C, C, 1);
+      TAKE(M->RB[j], K_SUM, 27, C, C, 0);
+      TAKE(M->RM[j], K_RES, 2, C, C, 1);
+      TAKE(M->ESH[j], K_EMB, 1, 256, C, 0);
+      TAKE(M->USH[j], K_SEL, 8, 2 * C, C, 1);
+    } else {
+      /* XFP deep level: re-densified to t and fused with F^t (Eq. 10-11);
+       * otherwise features of X^{d-1} alone, extracted at k = t for GRED's
+       * deep levels (Eq. 4-6) and at k = d - 1 elsewhere */
+      const int deep = j - nsh;
+      const int m = M->arch == ARCH_XFP ? deep
+                    : (M->arch == ARCH_GRED && deep > 0) ? deep : 1;
+      const int cat = M->arch == ARCH_XFP ? 2 : 1;
+      M->span[j] = m;
+      TAKE(M->G[j], K_EMB, 1, 256, C, 0);
+      for (int k = 1; k < m; k++) TAKE(M->D[j][k], K_SUM, 8, C, C, 1);
+      TAKE(M->RA[j], K_SUM, 27, cat * C, C, 1);
+      TAKE(M->RB[j], K_SUM, 27, C, C, 0);
+      TAKE(M->RM[j], K_RES, 2, C, C, 1);
+      for (int k = 0; k < m; k++) {
+        if (cat == 2) TAKE(M->E[j][k], K_EMB, 1, 256, C, 0);
+        TAKE(M->UP[j][k], K_SEL, 8, cat * C, C, 1);
+      }
     }
     TAKE(M->P1[j], K_SUM, 1, C, C, 1);
     TAKE(M->P2[j], K_SUM, 1, C, NSYM, 0);
@@ -773,67 +794,56 @@ typedef struct {
   const model* M;
   octree* T;
   int L, b, t;
-  int8_t* Fb; /* F^b on V_b */
-  int8_t* Ft; /* F^t on V_t */
+  int8_t* F[22]; /* F^d on V_d of the propagated levels d = b..t (XFP), F^b otherwise */
 } net;
 
 static void net_free(net* S) {
-  free(S->Fb);
-  free(S->Ft);
-  S->Fb = S->Ft = NULL;
+  for (int d = 0; d < 22; d++) {
+    free(S->F[d]);
+    S->F[d] = NULL;
+  }
 }
 
-/* F^b = Pruning(Upsampling(E_0[Y_{b-1}]), Y_{b-1}) */
-static void ensure_Fb(net* S) {
-  if (S->Fb) return;
+/* F^b = Pruning(Upsampling(E_0[Y_{b-1}]), Y_{b-1}); with XFP, for b < d <= t:
+ * S^{d-1} = ResBlock(F^{d-1}) (Eq. 8),
+ * F^d = Pruning(Upsampling(Concat(S^{d-1}, Y_{d-1})), Y_{d-1}) (Eq. 9) */
+static const int8_t* shallow_F(net* S, int d) {
+  if (S->F[d]) return S->F[d];
   const model* M = S->M;
   const octree* T = S->T;
-  const int C = M->C, b = S->b;
-  int64_t Np = T->N[b - 1], Nc = T->N[b];
-  int8_t* x = (int8_t*)malloc((size_t)(Np > 0 ? Np : 1) * C);
-  embed(M->E0, T->code[b - 1], Np, x, C, 0);
-  S->Fb = (int8_t*)malloc((size_t)(Nc > 0 ? Nc : 1) * C);
-  up_rec(T, b - 1, M->UP0, x, S->Fb);
+  const int C = M->C, b = S->b, j = d - b;
+  int64_t Np = T->N[d - 1], Nc = T->N[d];
+  int8_t* x;
+  if (d == b) {
+    x = (int8_t*)malloc((size_t)(Np > 0 ? Np : 1) * C);
+    embed(M->ESH[0], T->code[b - 1], Np, x, C, 0);
+  } else {
+    const int8_t* Fp = shallow_F(S, d - 1);
+    int8_t* Sp = (int8_t*)malloc((size_t)(Np > 0 ? Np : 1) * C);
+    resblock(M, j, T, d - 1, Fp, Sp);
+    x = (int8_t*)malloc((size_t)(Np > 0 ? Np : 1) * 2 * C);
+    copy_cols(Sp, Np, C, x, 2 * C, 0);
+    embed(M->ESH[j], T->code[d - 1], Np, x, 2 * C, C);
+    free(Sp);
+  }
+  S->F[d] = (int8_t*)malloc((size_t)(Nc > 0 ? Nc : 1) * C);
+  up_rec(T, d - 1, M->USH[j], x, S->F[d]);
   free(x);
-}
-
-/* S^b = ResBlock(F^b) (Eq. 8); F^t = Pruning(Upsampling(Concat(S^b, Y_b)), Y_b) (Eq. 9) */
-static void ensure_Ft(net* S) {
-  if (S->Ft) return;
-  ensure_Fb(S);
-  const model* M = S->M;
-  const octree* T = S->T;
-  const int C = M->C, b = S->b, t = S->t;
-  int64_t Nb = T->N[b], Nt = T->N[t];
-  int8_t* Sb = (int8_t*)malloc((size_t)(Nb > 0 ? Nb : 1) * C);
-  resblock(M, 1, T, b, S->Fb, Sb);
-  int8_t* x = (int8_t*)malloc((size_t)(Nb > 0 ? Nb : 1) * 2 * C);
-  copy_cols(Sb, Nb, C, x, 2 * C, 0);
-  embed(M->E1, T->code[b], Nb, x, 2 * C, C);
-  S->Ft = (int8_t*)malloc((size_t)(Nt > 0 ? Nt : 1) * C);
-  up_rec(T, b, M->UP1, x, S->Ft);
-  free(Sb);
-  free(x);
+  return S->F[d];
 }
 
 /* Logits of every node of V_d (b <= d <= L-1); needs V_0..V_d, Y_0..Y_{d-1}. */
 static void net_level_logits(net* S, int d, int8_t* logits) {
   const model* M = S->M;
   const octree* T = S->T;
-  const int C = M->C, b = S->b, t = S->t;
-  if (d == b) {
-    ensure_Fb(S);
-    predictor(M, 0, S->Fb, T->N[b], logits);
+  const int C = M->C, b = S->b, t = S->t, j = d - b;
+  if (d == b || (M->arch == ARCH_XFP && d <= t)) {
+    predictor(M, j, shallow_F(S, d), T->N[d], logits);
     return;
   }
-  ensure_Ft(S);
-  if (d == t) {
-    predictor(M, 1, S->Ft, T->N[t], logits);
-    return;
-  }
-  /* deep level d = t + m: GRED with cross-scale fusion (Eq. 4, Eq. 10, Eq. 11) */
-  const int m = d - t, j = m + 1;
-  /* G^t = Downsampling(Y_{d-1}): embedding on V_{d-1}, then m-1 stride-2 convs */
+  /* G^k = Downsampling(Y_{d-1}) (Eq. 4): embedding on V_{d-1}, then m-1
+   * stride-2 convs down to V_k; k = t for XFP's deep levels */
+  const int m = M->span[j], k0 = d - m, cat = M->arch == ARCH_XFP ? 2 : 1;
   int64_t Ng = T->N[d - 1];
   int8_t* g = (int8_t*)malloc((size_t)(Ng > 0 ? Ng : 1) * C);
   embed(M->G[j], T->code[d - 1], Ng, g, C, 0);
@@ -844,24 +854,32 @@ static void net_level_logits(net* S, int d, int8_t* logits) {
     free(g);
     g = g2;
   }
-  /* H^t = ResBlock(Concat(F^t, G^t)) */
-  int64_t Nt = T->N[t];
-  int8_t* x = (int8_t*)malloc((size_t)(Nt > 0 ? Nt : 1) * 2 * C);
-  copy_cols(S->Ft, Nt, C, x, 2 * C, 0);
-  copy_cols(g, Nt, C, x, 2 * C, C);
-  free(g);
-  int8_t* h = (int8_t*)malloc((size_t)(Nt > 0 ? Nt : 1) * C);
-  resblock(M, j, T, t, x, h);
+  /* XFP: H^t = ResBlock(Concat(F^t, G^t)) (Eq. 10); otherwise
+   * F^k = ResBlock(G^k) (Eq. 5) */
+  int64_t Nk0 = T->N[k0];
+  int8_t* x = g;
+  if (cat == 2) {
+    x = (int8_t*)malloc((size_t)(Nk0 > 0 ? Nk0 : 1) * 2 * C);
+    copy_cols(shallow_F(S, t), Nk0, C, x, 2 * C, 0);
+    copy_cols(g, Nk0, C, x, 2 * C, C);
+    free(g);
+  }
+  int8_t* h = (int8_t*)malloc((size_t)(Nk0 > 0 ? Nk0 : 1) * C);
+  resblock(M, j, T, k0, x, h);
   free(x);
-  /* F^{k+1} = Pruning(Upsampling(Concat(H^k, Y_k)), Y_k), k = t..d-1 */
-  for (int k = t; k < d; k++) {
+  /* XFP: F^{k+1} = Pruning(Upsampling(Concat(H^k, Y_k)), Y_k) (Eq. 11);
+   * otherwise F^{k+1} = Pruning(Upsampling(F^k), Y_k) (Eq. 6); k = k0..d-1 */
+  for (int k = k0; k < d; k++) {
     int64_t Nk = T->N[k], Nn = T->N[k + 1];
-    int8_t* xc = (int8_t*)malloc((size_t)(Nk > 0 ? Nk : 1) * 2 * C);
-    copy_cols(h, Nk, C, xc, 2 * C, 0);
-    embed(M->E[j][k - t], T->code[k], Nk, xc, 2 * C, C);
-    free(h);
+    int8_t* xc = h;
+    if (cat == 2) {
+      xc = (int8_t*)malloc((size_t)(Nk > 0 ? Nk : 1) * 2 * C);
+      copy_cols(h, Nk, C, xc, 2 * C, 0);
+      embed(M->E[j][k - k0], T->code[k], Nk, xc, 2 * C, C);
+      free(h);
+    }
     h = (int8_t*)malloc((size_t)(Nn > 0 ? Nn : 1) * C);
-    up_rec(T, k, M->UP[j][k - t], xc, h);
+    up_rec(T, k, M->UP[j][k - k0], xc, h);
     free(xc);
   }
   predictor(M, j, h, T->N[d], logits);
@@ -878,7 +896,7 @@ static int level_logits(const void* blob, size_t blob_len, const int32_t* xyz, i
   if (st) { free(M); return st; }
   st = octree_from_points(xyz, n, L, T);
   if (st) { free(M); return st; }
-  net S = {M, T, L, L - 5, L - 4, NULL, NULL};
+  net S = {M, T, L, L - 5, L - M->toff, {NULL}};
   int64_t N = T->N[d];
   int8_t* lg = (int8_t*)malloc((size_t)(N > 0 ? N : 1) * NSYM);
   if (n > 0) net_level_logits(&S, d, lg);
@@ -976,7 +994,7 @@ int or_encode(const void* blob, size_t blob_len, const int32_t* xyz, int64_t n, 
   model* M = (model*)malloc(sizeof(model));
   int st = load_model(blob, blob_len, M);
   if (st) { free(M); return st; }
-  const int b = L - 5, t = L - 4;
+  const int b = L - 5, t = L - M->toff;
   octree T;
   memset(&T, 0, sizeof(T));
   if (n > 0) {
@@ -1001,7 +1019,7 @@ int or_encode(const void* blob, size_t blob_len, const int32_t* xyz, int64_t n, 
       free(tmp);
     }
     /* network levels */
-    net S = {M, &T, L, b, t, NULL, NULL};
+    net S = {M, &T, L, b, t, {NULL}};
     for (int d = b; d < L; d++) {
       int64_t N = T.N[d];
       int8_t* lg = (int8_t*)malloc((size_t)N * NSYM);
@@ -1061,8 +1079,9 @@ int or_decode(const void* blob, size_t blob_len, const uint8_t* in, size_t len,
   const int L = in[5], b = in[6], t = in[7], C = in[8], flags = in[9];
   uint64_t hash = 0;
   for (int i = 0; i < 8; i++) hash |= (uint64_t)in[10 + i] << (8 * i);
-  if (check_L(L) || b != L - 5 || t != L - 4) { free(M); return OR_CORRUPT_STREAM; }
+  if (check_L(L) || b != L - 5) { free(M); return OR_CORRUPT_STREAM; }
   if (hash != M->hash || C != M->C) { free(M); return OR_WEIGHTS_MISMATCH; }
+  if (t != L - M->toff) { free(M); return OR_CORRUPT_STREAM; }
   size_t pos = 18;
   uint64_t chunk, n_sub;
   if (rd_varint(in, len, &pos, &chunk) || rd_varint(in, len, &pos, &n_sub) || chunk < 1 ||
@@ -1099,7 +1118,7 @@ int or_decode(const void* blob, size_t blob_len, const uint8_t* in, size_t len,
       for (int64_t i = 0; !st && i < T.N[d]; i++) T.code[d][i] += 1;
       if (!st) st = octree_expand(&T, d);
     }
-    net S = {M, &T, L, b, t, NULL, NULL};
+    net S = {M, &T, L, b, t, {NULL}};
     for (int d = b; d < L && !st; d++) {
       int64_t N = T.N[d];
       int8_t* lg = (int8_t*)malloc((size_t)N * NSYM);

@@ -12,6 +12,11 @@ Network (Sec. 3.1-3.2, Eq. 4-11, with the readings of the integer oracle):
          F_t = prelu(Up_1([S_b | E_1[Y_b]]));          logits_t = Pred_1(F_t)
   j = 1 + m: G = E'_j[Y_{d-1}], m-1 x prelu(Down(G)) to V_t; H = ResBlock([F_t | G]);
          H = prelu(Up_{j,k}([H | E_{j,k}[Y_k]])), k = t..d-1;  logits_d = Pred_j(H)
+with t = L - 4 (or L - 3: levels b+1..t then repeat the j = 1 form).  The
+ablations of Sec. 4.4 drop the propagated features: every level d > b takes
+G = E'_j[Y_{d-1}] brought down to V_k, H = ResBlock(G), m = d - k plain
+up-samplings H = prelu(Up_{j,k}(H)); k = t for GRED's levels below t, k = d - 1
+for the others and for the baseline.
 Loss (supplement, training section): cross-entropy of the true codes, in bits
 (divided by ln 2), summed over the network-coded levels.  With qat=True every
 activation that is int8 in the integer network, and every weight, passes a
@@ -74,6 +79,18 @@ def neighbours(keys: np.ndarray, depth: int) -> np.ndarray:
     return out
 
 
+class _Neighbours(dict):
+    """Kernel maps by depth, computed on first use."""
+
+    def __init__(self, keys):
+        super().__init__()
+        self._keys = keys
+
+    def __missing__(self, d):
+        v = self[d] = torch.from_numpy(neighbours(self._keys[d], d))
+        return v
+
+
 class Frame:
     """Levels, codes and index structures of one frame."""
 
@@ -87,7 +104,7 @@ class Frame:
             ck = self.keys[d]
             self.par[d] = torch.from_numpy(np.searchsorted(pk, ck >> np.uint64(3)).astype(np.int64))
             self.slot[d] = torch.from_numpy((ck & np.uint64(7)).astype(np.int64))
-        self.nbr = {d: torch.from_numpy(neighbours(self.keys[d], d)) for d in (self.b, self.t)}
+        self.nbr = _Neighbours(self.keys)
         self.Y = {d: torch.from_numpy(self.codes[d].astype(np.int64)) for d in range(L)}
 
 
@@ -183,13 +200,36 @@ init_params = synth.twin_params
 ACT_SCALE = 1.0 / 32.0  # fixed activation scale of the fake quantisers
 
 
-def level_bits(P: dict, fr: Frame, qat: bool = False, bf16: bool = False) -> torch.Tensor:
+ARCH_XFP, ARCH_GRED, ARCH_BASE = 0, 1, 2  # GRED + XFP; GRED only; baseline (Sec. 4.4)
+
+
+def level_bits(P: dict, fr: Frame, qat: bool = False, bf16: bool = False, arch: int = ARCH_XFP,
+               t_off: int = 4) -> torch.Tensor:
     """Total bits (cross-entropy / ln 2) of the network-coded levels of a frame.
 
     bf16=True rounds what the device's bf16 mode rounds: both operands of
     every product, and in the sparse ops' backward the output gradient too;
     biases and accumulations stay exact."""
-    b, t = fr.b, fr.t
+    def ce(logits, d):
+        return torch.nn.functional.cross_entropy(logits, fr.Y[d] - 1, reduction="sum") / math.log(2.0)
+    return sum(_levels(P, fr, ce, qat, bf16, arch, t_off))
+
+
+def level_logits(P: dict, fr: Frame, qat: bool = False, arch: int = ARCH_XFP,
+                 t_off: int = 4) -> dict:
+    """Logits [N_d, 255] of every network-coded level d (in nats)."""
+    out = {}
+
+    def keep(logits, d):
+        out[d] = logits
+        return 0.0
+    _levels(P, fr, keep, qat, False, arch, t_off)
+    return out
+
+
+def _levels(P, fr, head, qat, bf16, arch, t_off):
+    b, L = fr.b, fr.L
+    t = L - t_off
     q = (lambda x: fq(x, ACT_SCALE)) if qat else (lambda x: x)
     w = (lambda n: fq_w(P[n])) if qat else (lambda n: P[n])
     r = rb if bf16 else (lambda x: x)
@@ -212,28 +252,32 @@ def level_bits(P: dict, fr: Frame, qat: bool = False, bf16: bool = False) -> tor
         y2 = conv(y1, d, f"RB_{j}")
         return prelu(P[f"RM_{j}.ma"] * y1 + P[f"RM_{j}.mb"] * y2, P[f"RM_{j}.a"])
 
-    def ce(logits, d):
-        return torch.nn.functional.cross_entropy(logits, fr.Y[d] - 1, reduction="sum") / math.log(2.0)
-
-    bits = ce(pred(0, Fb := upl("UP_0", b, P["E_0"][fr.Y[b - 1]])), b)
-    Sb = resblock(1, b, Fb)
-    Ft = upl("UP_1", t, torch.cat([Sb, P["E_1"][fr.Y[b]]], 1))
-    bits = bits + ce(pred(1, Ft), t)
-    for j in range(2, 5):
-        m = j - 1
-        d = t + m
+    F = {b: upl("UP_0", b, P["E_0"][fr.Y[b - 1]])}
+    terms = [head(pred(0, F[b]), b)]
+    for j in range(1, 5):
+        d = b + j
+        if arch == ARCH_XFP and d <= t:
+            S = resblock(j, d - 1, F[d - 1])
+            F[d] = upl(f"UP_{j}", d, torch.cat([S, P[f"E_{j}"][fr.Y[d - 1]]], 1))
+            terms.append(head(pred(j, F[d]), d))
+            continue
+        if arch == ARCH_XFP or (arch == ARCH_GRED and d > t):
+            k0 = t
+        else:
+            k0 = d - 1
         G = P[f"G_{j}"][fr.Y[d - 1]]
-        for i in range(1, m):
+        for i in range(1, d - k0):
             k = d - 1 - i  # V_{k+1} -> V_k
             name = f"D_{j}_{i}"
             y = g(down(r(q(G)), fr.par[k + 1], fr.slot[k + 1], len(fr.keys[k]),
                        r(w(name + ".W")), 0.0))
             G = prelu(y + P[name + ".b"], P[name + ".a"])
-        H = resblock(j, t, torch.cat([Ft, G], 1))
-        for k in range(m):
-            H = upl(f"UP_{j}_{k}", t + k + 1, torch.cat([H, P[f"E_{j}_{k}"][fr.Y[t + k]]], 1))
-        bits = bits + ce(pred(j, H), d)
-    return bits
+        H = resblock(j, k0, torch.cat([F[t], G], 1) if arch == ARCH_XFP else G)
+        for k in range(d - k0):
+            x = torch.cat([H, P[f"E_{j}_{k}"][fr.Y[k0 + k]]], 1) if arch == ARCH_XFP else H
+            H = upl(f"UP_{j}_{k}", k0 + k + 1, x)
+        terms.append(head(pred(j, H), d))
+    return terms
 
 
 def to_torch(params: dict, requires_grad: bool = True) -> dict:

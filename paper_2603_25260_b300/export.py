@@ -54,11 +54,12 @@ def _q15(a: np.ndarray) -> np.ndarray:
     return np.clip(np.round(np.asarray(a, dtype=np.float64) * 32768.0), -32768, 32767).astype(np.int16)
 
 
-def quantize_twin(P: dict, C: int = 32) -> bytes:
-    """The integer blob of twin parameters P (name -> float array)."""
+def quantize_twin(P: dict, C: int = 32, arch: int = synth.ARCH_XFP, t_off: int = 4) -> bytes:
+    """The integer blob of twin parameters P (name -> float array) of the
+    given architecture."""
     P = {k: np.asarray(v, dtype=np.float64) for k, v in P.items()}
     recs = []
-    for (name, kind, S, cin, cout, prelu, ins, out) in synth.network_records(C):
+    for (name, kind, S, cin, cout, prelu, ins, out) in synth.network_records(C, arch, t_off):
         rec = synth.Record(name, kind, S, cin, cout, prelu)  # every zero point is 0
         if kind == synth.KIND_EMBED:
             tab = np.clip(np.round(P[name] / ACT_SCALE), -128, 127)
@@ -86,7 +87,7 @@ def quantize_twin(P: dict, C: int = 32) -> bytes:
             rec.mult = np.stack([ma, mb]).astype(np.int32)
             rec.slope = _q15(P[name + ".a"])
         recs.append(rec)
-    return synth.pack_blob(recs, synth.exp_lut(LOGIT_SCALE), C)
+    return synth.pack_blob(recs, synth.exp_lut(LOGIT_SCALE), C, arch, t_off)
 
 
 def train(steps: int, lr: float = 1e-3, seed: int = 0, log_every: int = 50) -> tuple[dict, list]:

@@ -20,7 +20,9 @@ paper's trained weights are not available, so the blob is drawn from a seeded
 generator with analytic scales that keep activations in range.
 
 Blob layout (little endian):
-  header (32 B): "LPCW", u32 version=1, u32 C, u32 n_records, u32 lut_len=256, 3 x u32 pad
+  header (32 B): "LPCW", u32 version=1, u32 C, u32 n_records, u32 lut_len=256,
+                 u32 arch (0 GRED + XFP, 1 GRED only, 2 baseline), u32 t_off (t = L - t_off;
+                 3 or 4, 0 reads as 4), u32 pad
   u32 lut[256]                     exp table over the non-positive domain, lut[0] = 2^16
   n_records x record, in network order (see ``network_records``); each record is
   a 48-byte header  u32 kind, S, cin, cout; i32 z_in, z_in2, z_out, shift;
@@ -242,40 +244,76 @@ class Record:
     slope: np.ndarray | None = None
 
 
-def network_records(C: int) -> list[tuple]:
+# Architectures: the paper's model and the two ablations of Sec. 4.4 (Table 4),
+# all on the same five network-coded levels b = L-5 .. L-1 and the same ops.
+ARCH_XFP = 0   # GRED + XFP (Sec. 3.1-3.2, Eq. 4-11)
+ARCH_GRED = 1  # GRED only: no feature propagated between levels
+ARCH_BASE = 2  # neither: every level's features extracted at its parent level
+ARCHS = {"gred_xfp": ARCH_XFP, "gred": ARCH_GRED, "baseline": ARCH_BASE}
+
+
+def check_arch(arch: int, t_off: int) -> None:
+    if arch not in (ARCH_XFP, ARCH_GRED, ARCH_BASE) or t_off not in (3, 4):
+        raise ValueError(f"architecture {arch} with t = L - {t_off} is not defined")
+
+
+def dense_span(arch: int, t_off: int, j: int) -> int:
+    """m = d - k: the number of up-sampling steps from the level k whose
+    features a non-propagating level d = b + j (j >= 1) extracts.  GRED
+    re-densifies the levels below t to k = t (Eq. 4-6); the baseline and the
+    levels down to t extract at k = d - 1."""
+    d_minus_t = j - (5 - t_off)
+    return d_minus_t if (arch == ARCH_GRED and d_minus_t > 0) else 1
+
+
+def network_records(C: int, arch: int = ARCH_XFP, t_off: int = 4) -> list[tuple]:
     """(name, kind, S, cin, cout, prelu, input tensor(s), output tensor) in blob order.
 
     Tensor names are used only to give every activation tensor one zero point,
     shared by its producers and consumers (concatenated halves share one)."""
+    check_arch(arch, t_off)
+    n_sh = 5 - t_off  # relative levels 1..n_sh lie at or above t
     r = []
     # j = 0 : level b, shallow, no ResBlock input yet (coarse levels are frequency coded)
     r += [("E_0", KIND_EMBED, 1, 256, C, False, ("X0",), "X0"),
           ("UP_0", KIND_SELECT, 8, C, C, True, ("X0",), "F_b"),
           ("P1_0", KIND_SUM, 1, C, C, True, ("F_b",), "h_0"),
           ("P2_0", KIND_SUM, 1, C, N_SYMBOLS, False, ("h_0",), "logit_0")]
-    # j = 1 : level t, shallow: S_b = ResBlock(F_b); F_t = Up(Concat(S_b, X_b))
-    r += [("RA_1", KIND_SUM, 27, C, C, True, ("F_b",), "y1_1"),
-          ("RB_1", KIND_SUM, 27, C, C, False, ("y1_1",), "y2_1"),
-          ("RM_1", KIND_RESADD, 2, C, C, True, ("y1_1", "y2_1"), "X1"),
-          ("E_1", KIND_EMBED, 1, 256, C, False, ("X1",), "X1"),
-          ("UP_1", KIND_SELECT, 8, 2 * C, C, True, ("X1",), "Xt"),
-          ("P1_1", KIND_SUM, 1, C, C, True, ("Xt",), "h_1"),
-          ("P2_1", KIND_SUM, 1, C, N_SYMBOLS, False, ("h_1",), "logit_1")]
-    # j = 2..4 : deep levels t+m, m = j-1, with re-densification to level t
-    for j in range(2, N_REL_LEVELS):
-        m = j - 1
-        r.append((f"G_{j}", KIND_EMBED, 1, 256, C, False, ("Xt",) if m == 1 else (f"g_{j}_0",),
-                  "Xt" if m == 1 else f"g_{j}_0"))
+    for j in range(1, N_REL_LEVELS):
+        if arch == ARCH_XFP and j <= n_sh:
+            # shallow level d <= t: S^{d-1} = ResBlock(F^{d-1});
+            # F^d = Up(Concat(S^{d-1}, X^{d-1}))
+            src = "F_b" if j == 1 else f"F_{j - 1}"
+            dst = "Xt" if j == n_sh else f"F_{j}"
+            r += [(f"RA_{j}", KIND_SUM, 27, C, C, True, (src,), f"y1_{j}"),
+                  (f"RB_{j}", KIND_SUM, 27, C, C, False, (f"y1_{j}",), f"y2_{j}"),
+                  (f"RM_{j}", KIND_RESADD, 2, C, C, True, (f"y1_{j}", f"y2_{j}"), f"X{j}"),
+                  (f"E_{j}", KIND_EMBED, 1, 256, C, False, (f"X{j}",), f"X{j}"),
+                  (f"UP_{j}", KIND_SELECT, 8, 2 * C, C, True, (f"X{j}",), dst),
+                  (f"P1_{j}", KIND_SUM, 1, C, C, True, (dst,), f"h_{j}"),
+                  (f"P2_{j}", KIND_SUM, 1, C, N_SYMBOLS, False, (f"h_{j}",), f"logit_{j}")]
+            continue
+        if arch == ARCH_XFP:
+            # deep level t + m, re-densified to level t and fused with F^t
+            m, cat, gk = j - n_sh, 2, "Xt"
+        else:
+            # no propagation: features of level d from X^{d-1} alone
+            m, cat, gk = dense_span(arch, t_off, j), 1, f"gk_{j}"
+        r.append((f"G_{j}", KIND_EMBED, 1, 256, C, False, (gk,) if m == 1 else (f"g_{j}_0",),
+                  gk if m == 1 else f"g_{j}_0"))
         for i in range(1, m):
             src = f"g_{j}_{i - 1}"
-            dst = "Xt" if i == m - 1 else f"g_{j}_{i}"
+            dst = gk if i == m - 1 else f"g_{j}_{i}"
             r.append((f"D_{j}_{i}", KIND_SUM, 8, C, C, True, (src,), dst))
-        r += [(f"RA_{j}", KIND_SUM, 27, 2 * C, C, True, ("Xt",), f"y1_{j}"),
+        r += [(f"RA_{j}", KIND_SUM, 27, cat * C, C, True, (gk,), f"y1_{j}"),
               (f"RB_{j}", KIND_SUM, 27, C, C, False, (f"y1_{j}",), f"y2_{j}"),
               (f"RM_{j}", KIND_RESADD, 2, C, C, True, (f"y1_{j}", f"y2_{j}"), f"H_{j}_0")]
         for k in range(m):
-            r.append((f"E_{j}_{k}", KIND_EMBED, 1, 256, C, False, (f"H_{j}_{k}",), f"H_{j}_{k}"))
-            r.append((f"UP_{j}_{k}", KIND_SELECT, 8, 2 * C, C, True, (f"H_{j}_{k}",), f"H_{j}_{k + 1}"))
+            if cat == 2:
+                r.append((f"E_{j}_{k}", KIND_EMBED, 1, 256, C, False, (f"H_{j}_{k}",),
+                          f"H_{j}_{k}"))
+            r.append((f"UP_{j}_{k}", KIND_SELECT, 8, cat * C, C, True, (f"H_{j}_{k}",),
+                      f"H_{j}_{k + 1}"))
         r += [(f"P1_{j}", KIND_SUM, 1, C, C, True, (f"H_{j}_{m}",), f"h_{j}"),
               (f"P2_{j}", KIND_SUM, 1, C, N_SYMBOLS, False, (f"h_{j}",), f"logit_{j}")]
     return r
@@ -290,7 +328,8 @@ def exp_lut(logit_scale: float = 1.0 / 16.0) -> np.ndarray:
     return lut.astype(np.uint32)
 
 
-def make_blob_records(C: int = 32, seed: int = 7, act_sigma: float = 30.0) -> tuple[list[Record], np.ndarray]:
+def make_blob_records(C: int = 32, seed: int = 7, act_sigma: float = 30.0, arch: int = ARCH_XFP,
+                      t_off: int = 4) -> tuple[list[Record], np.ndarray]:
     rng = np.random.Generator(np.random.PCG64(seed))
     zp: dict[str, int] = {}
 
@@ -301,7 +340,7 @@ def make_blob_records(C: int = 32, seed: int = 7, act_sigma: float = 30.0) -> tu
 
     sigma_w = 127.0 / math.sqrt(3.0)
     recs = []
-    for (name, kind, S, cin, cout, prelu, ins, out) in network_records(C):
+    for (name, kind, S, cin, cout, prelu, ins, out) in network_records(C, arch, t_off):
         rec = Record(name, kind, S, cin, cout, prelu)
         rec.z_out = z_of(out)
         if kind == KIND_EMBED:
@@ -348,8 +387,11 @@ def _pad16(b: bytes) -> bytes:
     return b + b"\0" * ((-len(b)) % 16)
 
 
-def pack_blob(recs: list[Record], lut: np.ndarray, C: int) -> bytes:
-    out = [struct.pack("<4sIIII12x", b"LPCW", 1, C, len(recs), 256)]
+def pack_blob(recs: list[Record], lut: np.ndarray, C: int, arch: int = ARCH_XFP,
+              t_off: int = 4) -> bytes:
+    check_arch(arch, t_off)
+    out = [struct.pack("<4sIIIIII4x", b"LPCW", 1, C, len(recs), 256, arch,
+                       0 if t_off == 4 else t_off)]
     out.append(lut.astype("<u4").tobytes())
     for r in recs:
         out.append(struct.pack("<IIIIiiiiI12x", r.kind, r.S, r.cin, r.cout, r.z_in, r.z_in2,
@@ -367,62 +409,40 @@ def pack_blob(recs: list[Record], lut: np.ndarray, C: int) -> bytes:
     return b"".join(out)
 
 
-def make_blob(C: int = 32, seed: int = 7) -> bytes:
-    """The seeded weight blob (default: C = 32, seed 7)."""
-    recs, lut = make_blob_records(C, seed)
-    return pack_blob(recs, lut, C)
+def make_blob(C: int = 32, seed: int = 7, arch: int = ARCH_XFP, t_off: int = 4) -> bytes:
+    """The seeded weight blob (default: C = 32, seed 7, GRED + XFP, t = L - 4)."""
+    recs, lut = make_blob_records(C, seed, arch=arch, t_off=t_off)
+    return pack_blob(recs, lut, C, arch, t_off)
 
 
 # ----------------------------------------------------------------------------
 # Parameters of the differentiable twin (names, shapes, seeded initial values)
 # ----------------------------------------------------------------------------
 
-def twin_param_shapes(C: int = 32) -> dict:
-    """Parameter names and shapes of the twin (float counterparts of the
-    blob records; PReLU slopes are per output channel)."""
+def twin_param_shapes(C: int = 32, arch: int = ARCH_XFP, t_off: int = 4) -> dict:
+    """Parameter names and shapes of the twin: the float counterparts of the
+    blob records, in record order (PReLU slopes per output channel)."""
     s = {}
-
-    def emb(n):
-        s[n] = (256, C)
-
-    def lin(n, S, cin, prelu_=True, per_slice_bias=False):
-        s[n + ".W"] = (S, C, cin) if S > 1 else (C, cin)
-        s[n + ".b"] = (S, C) if per_slice_bias else (C,)
-        if prelu_:
-            s[n + ".a"] = (C,)
-
-    def res(j, cin):
-        lin(f"RA_{j}", 27, cin)
-        lin(f"RB_{j}", 27, C, prelu_=False)
-        s[f"RM_{j}.ma"] = (C,)
-        s[f"RM_{j}.mb"] = (C,)
-        s[f"RM_{j}.a"] = (C,)
-
-    def pred(j):
-        lin(f"P1_{j}", 1, C)
-        s[f"P2_{j}.W"] = (255, C)
-        s[f"P2_{j}.b"] = (255,)
-
-    emb("E_0"); lin("UP_0", 8, C, per_slice_bias=True); pred(0)
-    res(1, C); emb("E_1"); lin("UP_1", 8, 2 * C, per_slice_bias=True); pred(1)
-    for j in range(2, 5):
-        m = j - 1
-        emb(f"G_{j}")
-        for i in range(1, m):
-            lin(f"D_{j}_{i}", 8, C)
-        res(j, 2 * C)
-        for k in range(m):
-            emb(f"E_{j}_{k}")
-            lin(f"UP_{j}_{k}", 8, 2 * C, per_slice_bias=True)
-        pred(j)
+    for (name, kind, S, cin, cout, prelu, _, _) in network_records(C, arch, t_off):
+        if kind == KIND_EMBED:
+            s[name] = (256, C)
+        elif kind == KIND_RESADD:
+            s[name + ".ma"] = (C,)
+            s[name + ".mb"] = (C,)
+            s[name + ".a"] = (C,)
+        else:
+            s[name + ".W"] = (S, cout, cin) if S > 1 else (cout, cin)
+            s[name + ".b"] = (S, cout) if kind == KIND_SELECT else (cout,)
+            if prelu:
+                s[name + ".a"] = (cout,)
     return s
 
 
-def twin_params(seed: int = 0, C: int = 32) -> dict:
+def twin_params(seed: int = 0, C: int = 32, arch: int = ARCH_XFP, t_off: int = 4) -> dict:
     """Seeded float parameters (numpy float32) for both implementations."""
     rng = np.random.Generator(np.random.PCG64(seed))
     out = {}
-    for name, shape in twin_param_shapes(C).items():
+    for name, shape in twin_param_shapes(C, arch, t_off).items():
         if name.endswith(".W"):
             fan = shape[-1] * (shape[0] if len(shape) == 3 and shape[0] == 27 else 1)
             if len(shape) == 3 and shape[0] == 8 and name.startswith("D_"):
