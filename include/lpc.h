@@ -53,7 +53,8 @@ typedef struct {
   int L;              /* maximum octree depth handled (6..19); frames may use L' <= L */
   int C;              /* network width; must equal the blob's (32) */
   int b_off;          /* base level offset: b = L - b_off (5) */
-  int t_off;          /* threshold offset: t = L - t_off (4), Sec. 3.2 and supplement */
+  int t_off;          /* threshold offset: t = L - t_off (4 or 3), Sec. 3.2 and supplement;
+                         must equal the blob's */
   int64_t max_points; /* largest point count of one frame */
   int max_frames;     /* largest batch for encode_batch / decode_batch (1..64) */
   int chunk;          /* nodes per entropy-coded substream of a network level (1024) */
@@ -68,7 +69,11 @@ typedef struct {
 
 /* Create a codec.  `blob` is the integer weight blob (format in the Python
  * package's synth module docstring: exp table, then per-layer INT8 weights,
- * INT32 biases, multipliers, shifts, zero points and Q15 PReLU slopes).  The
+ * INT32 biases, multipliers, shifts, zero points and Q15 PReLU slopes).  Its
+ * header names the architecture -- GRED + XFP (Sec. 3.1-3.2), or one of the
+ * ablations of Sec. 4.4: GRED without cross-scale propagation, or neither --
+ * and the threshold offset t = L - 4 or L - 3; the same kernels run all of
+ * them.  The
  * codec validates it, copies it to the device and keeps its 64-bit FNV-1a
  * hash, which every bitstream header carries.  Allocates all device and
  * pinned-host workspace once, sized by cfg->L and cfg->max_points.

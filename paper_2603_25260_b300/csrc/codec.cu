@@ -305,17 +305,20 @@ int64_t Codec::hash_slots(int64_t n) const {
 
 int Codec::create(const lpc_config& cfg, const void* blob, size_t len) {
   cfg_ = cfg;
-  if (cfg.L < 6 || cfg.L > kMaxL || cfg.C != 32 || cfg.b_off != 5 || cfg.t_off != 4 ||
+  if (cfg.L < 6 || cfg.L > kMaxL || cfg.C != 32 || cfg.b_off != 5 ||
+      (cfg.t_off != 4 && cfg.t_off != 3) ||
       cfg.max_points < 1 || cfg.max_points > (int64_t)1 << 31 || cfg.max_frames < 1 ||
       cfg.max_frames > kMaxBatch || cfg.chunk < 1 || cfg.chunk > (1 << 24) ||
       cfg.host_coding < 0 || cfg.host_coding > 1)
     return fail(LPC_INVALID_ARG,
-                "config: need 6 <= L <= 19, C = 32, b_off = 5, t_off = 4, max_points >= 1, "
+                "config: need 6 <= L <= 19, C = 32, b_off = 5, t_off = 4 or 3, max_points >= 1, "
                 "1 <= max_frames <= 64, chunk >= 1");
   st_ = reinterpret_cast<cudaStream_t>(cfg.cuda_stream);
   dev_rc_ = cfg.host_coding == 0;
   int s = model_load(blob, len, M_, err);
   if (s) return s;
+  if (M_.toff != cfg.t_off)
+    return fail(LPC_INVALID_ARG, "config: t_off differs from the weight blob's threshold offset");
   F_ = cfg.max_frames;
   P_ = cfg.max_batch_points > 0 ? cfg.max_batch_points : cfg.max_points * (int64_t)cfg.max_frames;
   if (P_ > ((int64_t)1 << 31) - 2) return fail(LPC_INVALID_ARG, "config: batch capacity too large");
@@ -341,7 +344,7 @@ int Codec::create(const lpc_config& cfg, const void* blob, size_t len) {
   add((void**)&d_fr_, sizeof(DevFrame) * F_);
   add((void**)&d_L_, 4 * F_);
   add((void**)&d_err_, 16);
-  add((void**)&d_pairs_, 16);
+  add((void**)&d_pairs_, 32);
   add((void**)&d_keys0_, 8 * P);
   sort_.n_max = P;
   add((void**)&sort_.alt, 8 * P);
@@ -351,8 +354,11 @@ int Codec::create(const lpc_config& cfg, const void* blob, size_t len) {
   hash_.cap = 1024;
   while (hash_.cap < 2 * P) hash_.cap <<= 1;
   add((void**)&hash_.slots, 16 * hash_.cap);
-  add((void**)&nbr_b_, 4 * 27 * P);
-  add((void**)&nbr_t_, 4 * 27 * P);
+  // kernel maps from height 5 (level b) down to the deepest conv level:
+  // t for GRED + XFP and GRED, L - 2 (height 2) for the baseline
+  for (int h = 5; h >= (M_.arch == kArchBase ? 2 : M_.toff); h--) add((void**)&nbr_[h], 4 * 27 * P);
+  if (M_.arch == kArchXfp && M_.toff == 3) add((void**)&fmid_, 32 * P);
+  if (M_.arch != kArchXfp) add((void**)&gk_, 32 * P);
   add((void**)&fb_, 32 * P);
   add((void**)&xb_, 64 * P);
   add((void**)&xt_, 64 * P);
@@ -472,7 +478,7 @@ void Codec::pend(int f, double bytes, double ops, int pair_slot, double ppo, dou
 // After the call's final synchronisation: fold the marks into the totals.
 void Codec::prof_collect() {
   if (!prof.mask) return;
-  uint64_t pairs[2] = {0, 0};
+  uint64_t pairs[4] = {0, 0, 0, 0};
   cudaMemcpy(pairs, d_pairs_, sizeof(pairs), cudaMemcpyDeviceToHost);
   for (const Mark& m : marks_) {
     if (m.e1 < 0) continue;
@@ -501,9 +507,9 @@ void Codec::level_bytes() {
 
 // ------------------------------------------------------------- per batch --
 void Codec::begin_batch() {
-  have_Fb_ = have_Ft_ = have_nbr_t_ = false;
+  for (int h = 0; h < kHeights; h++) have_F_[h] = have_nbr_[h] = false;
   cudaMemsetAsync(d_err_, 0, 4, st_);
-  if (prof.mask) cudaMemsetAsync(d_pairs_, 0, 16, st_);
+  if (prof.mask) cudaMemsetAsync(d_pairs_, 0, 32, st_);
 }
 
 int Codec::check_device_error() {
@@ -690,38 +696,50 @@ void Codec::kmap(int h, int32_t* nbr, int slot) {
   pend(kFamHash, 12.0 * slots + 20.0 * N_[h] + 27.0 * N_[h] * (4 + 8), 0);
 }
 
-// F^b = Pruning(Upsampling(E_0[Y_{b-1}]), Y_{b-1}): height 6 -> 5
-void Codec::ensure_Fb() {
-  if (have_Fb_) return;
-  embed(M_.E0, 6, xe_, 32, 0);
-  up(M_.UP0, 6, xe_, 32, fb_, 32);
-  have_Fb_ = true;
+// Kernel map at height h: hashed at height 5 (level b); below it from the
+// parent level's map (every node is a child of a node one level up, so its
+// neighbours are children of its parent's neighbours; no second hash table).
+void Codec::ensure_nbr(int h) {
+  if (have_nbr_[h]) return;
+  if (h == 5) {
+    kmap(5, nbr_[5], 0);
+  } else {
+    ensure_nbr(h + 1);
+    pbeg(kFamHash);
+    launch_kernel_map_child(key_[h], par_[h], d_N_ + h, gridn(h), nbr_[h + 1], code_[h + 1],
+                            off_[h + 1], nbr_[h], st_, prof.mask ? d_pairs_ + (5 - h) : nullptr);
+    pend(kFamHash, 120.0 * N_[h] + 113.0 * N_[h + 1], 0);
+  }
+  have_nbr_[h] = true;
 }
 
-// S^b = ResBlock(F^b) (Eq. 8); F^t = Pruning(Upsampling(Concat(S^b, Y_b)), Y_b)
-// (Eq. 9): V_b is height 5, V_t height 4
-void Codec::ensure_Ft() {
-  if (have_Ft_) return;
-  ensure_Fb();
-  kmap(5, nbr_b_, 0);
-  to_bf16(fb_, 32, 32, M_.RA[1].z_in, 5);
-  conv(M_.RA[1], 5, nbr_b_, 0, xb16_, 32, y1_, 32, 0, nullptr, y1b16_, M_.RB[1].z_in);
-  conv(M_.RB[1], 5, nbr_b_, 0, y1b16_, 32, xb_, 64, 0, &M_.RM[1], nullptr, 0);
-  embed(M_.E1, 5, xb_, 64, 32);
-  up(M_.UP1, 5, xb_, 64, xt_, 64);
-  have_Ft_ = true;
-}
-
-// The map at V_t (height 4) from the map at V_b: every node of V_t is a
-// child of a node of V_b, so its neighbours are children of its parent's
-// neighbours (no second hash table).
-void Codec::ensure_nbr_t() {
-  if (have_nbr_t_) return;
-  pbeg(kFamHash);
-  launch_kernel_map_child(key_[4], par_[4], d_N_ + 4, gridn(4), nbr_b_, code_[5], off_[5], nbr_t_,
-                          st_, prof.mask ? d_pairs_ + 1 : nullptr);
-  pend(kFamHash, 120.0 * N_[4] + 113.0 * N_[5], 0);
-  have_nbr_t_ = true;
+// Propagated features F^d at height h = L - d: level b from Y_{b-1} alone,
+// F^b = Pruning(Upsampling(E_0[Y_{b-1}]), Y_{b-1}); with GRED + XFP, for the
+// levels below b down to t, S^{d-1} = ResBlock(F^{d-1}) (Eq. 8) and
+// F^d = Pruning(Upsampling(Concat(S^{d-1}, Y_{d-1})), Y_{d-1}) (Eq. 9).
+// F^t lands in the first half of xt_, where the deeper levels concatenate
+// G^t (Eq. 10).
+const int8_t* Codec::shallow_F(int h, int* stride) {
+  const bool at_t = h == M_.toff && M_.arch == kArchXfp;
+  int8_t* buf = h == 5 ? fb_ : at_t ? xt_ : fmid_;
+  *stride = at_t ? 64 : 32;
+  if (have_F_[h]) return buf;
+  if (h == 5) {
+    embed(M_.ESH[0], 6, xe_, 32, 0);
+    up(M_.USH[0], 6, xe_, 32, buf, *stride);
+  } else {
+    const int j = 5 - h, hp = h + 1;
+    int ps = 32;
+    const int8_t* Fp = shallow_F(hp, &ps);
+    ensure_nbr(hp);
+    to_bf16(Fp, ps, 32, M_.RA[j].z_in, hp);
+    conv(M_.RA[j], hp, nbr_[hp], 5 - hp, xb16_, 32, y1_, 32, 0, nullptr, y1b16_, M_.RB[j].z_in);
+    conv(M_.RB[j], hp, nbr_[hp], 5 - hp, y1b16_, 32, xb_, 64, 0, &M_.RM[j], nullptr, 0);
+    embed(M_.ESH[j], hp, xb_, 64, 32);
+    up(M_.USH[j], hp, xb_, 64, buf, *stride);
+  }
+  have_F_[h] = true;
+  return buf;
 }
 
 // Network of relative level j (depth b + j of every frame, height 5 - j):
@@ -762,29 +780,36 @@ void Codec::net_level(int j, int mode, uint16_t* cdf, uint32_t* enc, int8_t* log
          n * 32 + (mode == kPredCdf ? 512.0 * n : mode == kPredEnc ? 5.0 * n : 255.0 * n),
          2.0 * n * (32 * 32 + 255 * 32));
   };
-  if (j == 0) {
-    ensure_Fb();
-    pred(0, fb_, 32);
+  const int m = M_.span[j];
+  if (m == 0) {  // level b, and with GRED + XFP the levels down to t
+    int fs = 32;
+    const int8_t* F = shallow_F(h, &fs);
+    pred(j, F, fs);
     return;
   }
-  ensure_Ft();
-  if (j == 1) {
-    pred(1, xt_, 64);
-    return;
+  // features extracted at level k = d - m (height hk) from Y_{d-1}; with
+  // GRED + XFP fused with the propagated F^t (k = t)
+  const int hk = h + m;
+  const bool cat = M_.arch == kArchXfp;
+  const int w = cat ? 64 : 32;  // row width of the ResBlock's input
+  int8_t* gout = cat ? xt_ : gk_;
+  const int gc = cat ? 32 : 0;
+  if (cat) {
+    int fs = 32;
+    shallow_F(hk, &fs);
   }
-  // deep level t + m: G^t = Downsampling(Y_{d-1}) (Eq. 4), from height 5 - m
-  // down to V_t (height 4) in m - 1 stride-2 steps
-  ensure_nbr_t();
-  const int m = j - 1;
+  ensure_nbr(hk);
+  // G^k = Downsampling(Y_{d-1}) (Eq. 4): embedding at height h + 1, then
+  // m - 1 stride-2 steps up to height hk
   if (m == 1) {
-    embed(M_.G[j], 4, xt_, 64, 32);
+    embed(M_.G[j], h + 1, gout, w, gc);
   } else {
-    embed(M_.G[j], 5 - m, g_[0], 32, 0);
+    embed(M_.G[j], h + 1, g_[0], 32, 0);
     const int8_t* cur = g_[0];
     for (int i = 1; i < m; i++) {
-      const int hp = 5 - m + i;  // parent height of this step
-      int8_t* dst = i == m - 1 ? xt_ : g_[i & 1];
-      const int ds = i == m - 1 ? 64 : 32, dc = i == m - 1 ? 32 : 0;
+      const int hp = h + 1 + i;  // parent height of this step
+      int8_t* dst = i == m - 1 ? gout : g_[i & 1];
+      const int ds = i == m - 1 ? w : 32, dc = i == m - 1 ? gc : 0;
       pbeg(kFamDown);
       launch_down(M_.D[j][i], key_[hp - 1], off_[hp], d_N_ + hp, gridn(hp), cur, 32, dst, ds, dc,
                   st_);
@@ -792,19 +817,19 @@ void Codec::net_level(int j, int mode, uint16_t* cdf, uint32_t* enc, int8_t* log
       cur = dst;
     }
   }
-  // H^t = ResBlock(Concat(F^t, G^t)) (Eq. 10)
-  to_bf16(xt_, 64, 64, M_.RA[j].z_in, 4);
-  conv(M_.RA[j], 4, nbr_t_, 1, xb16_, 64, y1_, 32, 0, nullptr, y1b16_, M_.RB[j].z_in);
-  conv(M_.RB[j], 4, nbr_t_, 1, y1b16_, 32, hx_[0], 64, 0, &M_.RM[j], nullptr, 0);
-  // F^{k+1} = Pruning(Upsampling(Concat(H^k, Y_k)), Y_k), k = t..d-1 (Eq. 11):
-  // heights 4 -> h
+  // H^k = ResBlock(Concat(F^t, G^t)) (Eq. 10), or ResBlock(G^k) (Eq. 5)
+  to_bf16(gout, w, w, M_.RA[j].z_in, hk);
+  conv(M_.RA[j], hk, nbr_[hk], 5 - hk, xb16_, w, y1_, 32, 0, nullptr, y1b16_, M_.RB[j].z_in);
+  conv(M_.RB[j], hk, nbr_[hk], 5 - hk, y1b16_, 32, hx_[0], w, 0, &M_.RM[j], nullptr, 0);
+  // F^{k+1} = Pruning(Upsampling(Concat(H^k, Y_k)), Y_k) (Eq. 11), or
+  // Pruning(Upsampling(F^k), Y_k) (Eq. 6): heights hk -> h
   int cur = 0;
   for (int k = 0; k < m; k++) {
-    const int hk = 4 - k;
-    embed(M_.E[j][k], hk, hx_[cur], 64, 32);
+    const int hp = hk - k;
+    if (cat) embed(M_.E[j][k], hp, hx_[cur], 64, 32);
     int8_t* dst = k == m - 1 ? fo_ : hx_[1 - cur];
-    const int ds = k == m - 1 ? 32 : 64;
-    up(M_.UP[j][k], hk, hx_[cur], 64, dst, ds);
+    const int ds = k == m - 1 ? 32 : w;
+    up(M_.UP[j][k], hp, hx_[cur], w, dst, ds);
     cur = 1 - cur;
   }
   pred(j, fo_, 32);
@@ -820,7 +845,9 @@ void Codec::net_level(int j, int mode, uint16_t* cdf, uint32_t* enc, int8_t* log
 void Codec::run_level(int j, int mode, uint16_t* cdf, uint32_t* enc) {
   // direct launches while profiling, and until the conv autotuner has picked
   // its variants (it times real launches, which a capture cannot)
-  if (!gs_ || prof.mask || conv_variant_[0] < 0 || conv_variant_[1] < 0 || pred_variant_ < 0) {
+  // (the ablation architectures have no 64-channel conv)
+  if (!gs_ || prof.mask || conv_variant_[0] < 0 ||
+      (M_.arch == kArchXfp && conv_variant_[1] < 0) || pred_variant_ < 0) {
     net_level(j, mode, cdf, enc, nullptr);
     return;
   }
@@ -1172,10 +1199,11 @@ int Codec::decode(int nf, const uint8_t* const* in, const size_t* lens, int32_t*
     const int L = p[5], b = p[6], t = p[7], C = p[8], flags = p[9];
     uint64_t hash = 0;
     for (int k = 0; k < 8; k++) hash |= (uint64_t)p[10 + k] << (8 * k);
-    if (L < 6 || L > kMaxDepth || b != L - 5 || t != L - 4)
+    if (L < 6 || L > kMaxDepth || b != L - cfg_.b_off)
       return fail(LPC_CORRUPT_STREAM, "decode: bad depth fields");
     if (hash != M_.hash || C != M_.C)
       return fail(LPC_WEIGHTS_MISMATCH, "decode: stream was written with another weight blob");
+    if (t != L - cfg_.t_off) return fail(LPC_CORRUPT_STREAM, "decode: bad threshold field");
     if (L > std::min(cfg_.L, kMaxL))
       return fail(LPC_INVALID_ARG, "decode: stream depth exceeds the codec's L");
     size_t pos = kHdr;

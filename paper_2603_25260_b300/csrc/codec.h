@@ -158,9 +158,8 @@ class Codec {
   void conv(const DLayer& W, int h, const int32_t* nbr, int slot, const void* xb, int xbs,
             int8_t* out, int os, int oc, const DRes* res, void* outb, int outb_z);
   void kmap(int h, int32_t* nbr, int slot);
-  void ensure_Fb();
-  void ensure_Ft();
-  void ensure_nbr_t();
+  void ensure_nbr(int h);
+  const int8_t* shallow_F(int h, int* stride);
   void net_level(int j, int mode, uint16_t* cdf, uint32_t* enc, int8_t* logits);
   void run_level(int j, int mode, uint16_t* cdf, uint32_t* enc);
   // grid size for level height h: its size, or the capacity while a graph
@@ -221,7 +220,8 @@ class Codec {
   int nf_ = 0;
   std::vector<Frame> fr_;
   int64_t N_[kHeights] = {};  // rows per height (all frames)
-  bool have_Fb_ = false, have_Ft_ = false, have_nbr_t_ = false;
+  // per batch: which propagated features F (by height) and kernel maps exist
+  bool have_F_[kHeights] = {}, have_nbr_[kHeights] = {};
   // device workspace: level arrays by height (0 = leaves of every frame)
   void* dmem_ = nullptr;
   uint64_t* key_[kHeights] = {};
@@ -245,8 +245,9 @@ class Codec {
   SortScratch sort_;
   ScanScratch scan_;
   HashTable hash_;
-  int32_t *nbr_b_ = nullptr, *nbr_t_ = nullptr;
+  int32_t* nbr_[kHeights] = {};  // kernel maps by height, 5 down to the deepest conv level
   int8_t *fb_ = nullptr, *xb_ = nullptr, *xt_ = nullptr, *y1_ = nullptr, *xe_ = nullptr;
+  int8_t *fmid_ = nullptr, *gk_ = nullptr;  // F^{t-1} when t = L - 3; G^k of the ablations
   int8_t *g_[2] = {}, *hx_[2] = {}, *fo_ = nullptr;
   void *xb16_ = nullptr, *y1b16_ = nullptr;  // bf16 (q - z) inputs of the convs
   uint16_t* d_cdf_ = nullptr;

@@ -96,6 +96,12 @@ int model_load(const void* blob, size_t len, Model& M, std::string& err) {
   b = M.blob.data();
   M.C = le32(b + 8);
   const int nrec = le32(b + 12);
+  M.arch = le32(b + 20);
+  M.toff = le32(b + 24) == 0 ? 4 : le32(b + 24);
+  if (M.arch < kArchXfp || M.arch > kArchBase || (M.toff != 3 && M.toff != 4)) {
+    err = "weight blob: unknown architecture or threshold offset";
+    return LPC_INVALID_ARG;
+  }
   if (M.C != 32) {
     err = "weight blob: this build supports C = 32 only";
     return LPC_INVALID_ARG;
@@ -287,27 +293,38 @@ int model_load(const void* blob, size_t len, Model& M, std::string& err) {
                              img.add(tcimg.data(), tcimg.size() * 2)}});
   };
 
-  emb(M.E0);
-  layer(M.UP0, kSel, 8, C, 1);
+  // level b: features from Y_{b-1} alone, every architecture
+  emb(M.ESH[0]);
+  layer(M.USH[0], kSel, 8, C, 1);
   layer(M.P1[0], kSum, 1, C, 1);
   pred2(M.P2[0]);
-  layer(M.RA[1], kSum, 27, C, 1);
-  layer(M.RB[1], kSum, 27, C, 0);
-  resm(M.RM[1]);
-  emb(M.E1);
-  layer(M.UP1, kSel, 8, 2 * C, 1);
-  layer(M.P1[1], kSum, 1, C, 1);
-  pred2(M.P2[1]);
-  for (int j = 2; j < kRelLevels; j++) {
-    const int m = j - 1;
-    emb(M.G[j]);
-    for (int k = 1; k < m; k++) layer(M.D[j][k], kSum, 8, C, 1);
-    layer(M.RA[j], kSum, 27, 2 * C, 1);
-    layer(M.RB[j], kSum, 27, C, 0);
-    resm(M.RM[j]);
-    for (int k = 0; k < m; k++) {
-      emb(M.E[j][k]);
-      layer(M.UP[j][k], kSel, 8, 2 * C, 1);
+  const int nsh = 5 - M.toff;  // relative levels 1..nsh lie at or above t
+  for (int j = 1; j < kRelLevels; j++) {
+    if (M.arch == kArchXfp && j <= nsh) {
+      // S^{d-1} = ResBlock(F^{d-1}); F^d = Up(Concat(S^{d-1}, Y_{d-1})) (Eq. 8-9)
+      M.span[j] = 0;
+      layer(M.RA[j], kSum, 27, C, 1);
+      layer(M.RB[j], kSum, 27, C, 0);
+      resm(M.RM[j]);
+      emb(M.ESH[j]);
+      layer(M.USH[j], kSel, 8, 2 * C, 1);
+    } else {
+      // GRED + XFP below t: re-densified to t and fused with F^t (Eq. 10-11);
+      // the ablations: features of Y_{d-1} alone, extracted at k = t for
+      // GRED's levels below t (Eq. 4-6), at k = d - 1 otherwise
+      const int below = j - nsh;
+      const int m = (M.arch == kArchXfp || (M.arch == kArchGred && below > 0)) ? below : 1;
+      const int cat = M.arch == kArchXfp ? 2 : 1;
+      M.span[j] = m;
+      emb(M.G[j]);
+      for (int k = 1; k < m; k++) layer(M.D[j][k], kSum, 8, C, 1);
+      layer(M.RA[j], kSum, 27, cat * C, 1);
+      layer(M.RB[j], kSum, 27, C, 0);
+      resm(M.RM[j]);
+      for (int k = 0; k < m; k++) {
+        if (cat == 2) emb(M.E[j][k]);
+        layer(M.UP[j][k], kSel, 8, cat * C, 1);
+      }
     }
     layer(M.P1[j], kSum, 1, C, 1);
     pred2(M.P2[j]);

@@ -102,6 +102,13 @@ def _hp(a: np.ndarray | None):
     return None if a is None else a.ctypes.data
 
 
+def blob_t_off(blob: bytes) -> int:
+    """The threshold offset (t = L - t_off) a weight blob's header names;
+    0 there reads as 4."""
+    v = int.from_bytes(bytes(blob[24:28]), "little") if len(blob) >= 28 else 0
+    return v or 4
+
+
 class Codec:
     """One codec instance on the current CUDA device and stream."""
 
@@ -114,7 +121,8 @@ class Codec:
         self.blob = bytes(blob)
         self.L = L
         self.max_points = max_points
-        cfg = Config(L, 32, 5, 4, max_points, max_frames, chunk, host_threads,
+        cfg = Config(L, 32, 5, blob_t_off(self.blob), max_points, max_frames, chunk,
+                     host_threads,
                      _stream() if stream is None else stream, max_batch_points,
                      int(bool(host_coding)))
         h = P()
