@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-train", action="store_true")
+    ap.add_argument("--no-arch", action="store_true",
+                    help="skip the ablation-architecture timings")
     ap.add_argument("--train-steps", type=int, default=3)
     ap.add_argument("--ncu-case", choices=["single", "batch"],
                     help="profiling case: warm up, then one encode + decode inside the NVTX "
@@ -443,36 +445,53 @@ def run_ours(args):
                    "encode_mpts": round(n / (he / 1e3) / 1e6, 4),
                    "decode_mpts": round(n / (hd / 1e3) / 1e6, 4)}
 
+    ref_dec = out_dev[:n_out].clone()
+
+    def blob_leg(blob_bytes, steps=5):
+        """The step with another weight blob: median encode / decode times,
+        bits per point and whether the decoded voxels are the input's."""
+        bc = lpc.Codec(blob_bytes, spec.L, n, chunk=args.chunk)
+        buf = np.empty_like(outbuf)  # outbuf keeps the seeded blob's stream
+        for _ in range(max(args.warmup, 10)):
+            ln = bc.encode_into(x, buf)
+            bc.decode(buf[:ln], out=out_dev)
+        ms = []
+        for _ in range(steps):
+            flush.zero_()
+            a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            a.record(stream)
+            ln = bc.encode_into(x, buf)
+            b.record(stream)
+            bc.decode(buf[:ln], out=out_dev)
+            c.record(stream)
+            torch.cuda.synchronize()
+            ms.append((a.elapsed_time(b), b.elapsed_time(c)))
+        lossless = bool(torch.equal(out_dev[:n_out], ref_dec))
+        bc.close()
+        te = statistics.median(t[0] for t in ms)
+        td = statistics.median(t[1] for t in ms)
+        return {"bits_per_point": round(8 * ln / n, 4),
+                "value": round(n / ((te + td) / 1e3) / 1e6, 4),
+                "encode_mpts": round(n / (te / 1e3) / 1e6, 4),
+                "decode_mpts": round(n / (td / 1e3) / 1e6, 4), "lossless": lossless}
+
     # the same step with the exported blob of the trained twin (realistic
     # bits per point: skewed predictions, fewer coded bytes)
     trained = None
     from paper_2603_25260_b300 import export
     if os.path.exists(export.TRAINED_BLOB):
         with open(export.TRAINED_BLOB, "rb") as f:
-            tcodec = lpc.Codec(f.read(), spec.L, n, chunk=args.chunk)
-        tbuf = np.empty_like(outbuf)  # outbuf keeps the seeded blob's stream
-        for _ in range(max(args.warmup, 10)):
-            ln = tcodec.encode_into(x, tbuf)
-            tcodec.decode(tbuf[:ln], out=out_dev)
-        tms = []
-        for _ in range(5):
-            flush.zero_()
-            a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-            a.record(stream)
-            ln = tcodec.encode_into(x, tbuf)
-            b.record(stream)
-            tcodec.decode(tbuf[:ln], out=out_dev)
-            c.record(stream)
-            torch.cuda.synchronize()
-            tms.append((a.elapsed_time(b), b.elapsed_time(c)))
-        tcodec.close()
-        te = statistics.median(t[0] for t in tms)
-        td = statistics.median(t[1] for t in tms)
-        trained = {"blob": os.path.relpath(export.TRAINED_BLOB, ROOT),
-                   "bits_per_point": round(8 * ln / n, 4),
-                   "value": round(n / ((te + td) / 1e3) / 1e6, 4),
-                   "encode_mpts": round(n / (te / 1e3) / 1e6, 4),
-                   "decode_mpts": round(n / (td / 1e3) / 1e6, 4)}
+            trained = {"blob": os.path.relpath(export.TRAINED_BLOB, ROOT), **blob_leg(f.read())}
+
+    # the ablation architectures (Sec. 4.4) and t = L - 3 on the same
+    # kernels, seeded weights of each
+    architectures = None
+    if not args.no_arch:
+        architectures = {}
+        for name, arch in sorted(synth.ARCHS.items(), key=lambda kv: kv[1]):
+            for t_off in (4, 3):
+                architectures[f"{name}_t{t_off}"] = blob_leg(
+                    synth.make_blob(arch=arch, t_off=t_off), steps=7)
 
     # the float inference variant (the float network, tables from a float
     # softmax): how many table rows come out differently when the softmax of
@@ -605,6 +624,7 @@ def run_ours(args):
         "batched": batched,
         "host_coding": host_coding,
         "trained_blob": trained,
+        "architectures": architectures,
         "float_variant": float_variant,
         "train": train,
         "e2e": {"value": round(e2e_value, 4), "unit": "Mpoints/s",

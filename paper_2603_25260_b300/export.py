@@ -22,7 +22,8 @@ blob record the integer codec reads:
 ``python -m paper_2603_25260_b300.export --steps N --out PATH`` trains the
 twin for N AdamW steps on the seeded 8-frame training batch of the 64-beam
 generator (rate loss in bits per point, fake quantisers on) and writes the
-blob.
+blob; ``--arch gred|baseline`` and ``--t-off 3`` train and export the
+ablation architectures of Sec. 4.4 instead.
 """
 
 from __future__ import annotations
@@ -90,9 +91,11 @@ def quantize_twin(P: dict, C: int = 32, arch: int = synth.ARCH_XFP, t_off: int =
     return synth.pack_blob(recs, synth.exp_lut(LOGIT_SCALE), C, arch, t_off)
 
 
-def train(steps: int, lr: float = 1e-3, seed: int = 0, log_every: int = 50) -> tuple[dict, list]:
+def train(steps: int, lr: float = 1e-3, seed: int = 0, log_every: int = 50,
+          arch: int = synth.ARCH_XFP, t_off: int = 4) -> tuple[dict, list]:
     """AdamW on the rate loss of the 8-frame training batch, fake quantisers
-    and fp32 operands; returns the parameters and the loss history."""
+    and fp32 operands, for one architecture; returns the parameters and the
+    loss history."""
     import torch
 
     from . import train as T
@@ -100,7 +103,8 @@ def train(steps: int, lr: float = 1e-3, seed: int = 0, log_every: int = 50) -> t
     specs = synth.training_specs()
     frames = [T.BatchFrame([T.Frame(torch.from_numpy(synth.make_frame(s)).cuda(), s.L)
                             for s in specs])]
-    model = T.QATModel(synth.twin_params(seed), qat=True, bf16=False)
+    model = T.QATModel(synth.twin_params(seed, arch=arch, t_off=t_off), qat=True, bf16=False,
+                       arch=arch, t_off=t_off)
     opt = torch.optim.AdamW(model.parameters(), lr=lr, weight_decay=1e-4)
     hist = []
     for k in range(steps):
@@ -117,10 +121,13 @@ def main():
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--arch", choices=sorted(synth.ARCHS), default="gred_xfp")
+    ap.add_argument("--t-off", type=int, choices=(3, 4), default=4)
     ap.add_argument("--out", required=True)
     a = ap.parse_args()
-    params, hist = train(a.steps, a.lr, a.seed)
-    blob = quantize_twin(params)
+    arch = synth.ARCHS[a.arch]
+    params, hist = train(a.steps, a.lr, a.seed, arch=arch, t_off=a.t_off)
+    blob = quantize_twin(params, arch=arch, t_off=a.t_off)
     with open(a.out, "wb") as f:
         f.write(blob)
     np.savez(a.out + ".params.npz", **params)

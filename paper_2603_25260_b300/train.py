@@ -285,10 +285,38 @@ class Frame:
                 op += N + 1
         for d in range(L):
             self.Y[d] = self.codes[d].long()
-        b, t = self.b, self.t
-        self.nbr = {b: lpc.kernel_map(self.keys[b], b)}
-        self.nbr[t] = lpc.kernel_map_child(self.keys[t], self.par[t], self.nbr[b], self.codes[b],
-                                           self.off[b])
+        self.nbr = _KernelMaps(self)
+        self.nbr[self.b], self.nbr[self.t]  # built now; deeper ones on first use
+
+
+class _KernelMaps(dict):
+    """Kernel maps by depth: hashed at V_b, below it from the parent level's
+    map (every node is a child of a node one level up)."""
+
+    def __init__(self, fr):
+        super().__init__()
+        self._fr = fr
+
+    def __missing__(self, d):
+        fr = self._fr
+        if d == fr.b:
+            v = lpc.kernel_map(fr.keys[d], d)
+        else:
+            v = lpc.kernel_map_child(fr.keys[d], fr.par[d], self[d - 1], fr.codes[d - 1],
+                                     fr.off[d - 1])
+        self[d] = v
+        return v
+
+
+class _BatchMaps(dict):
+    def __init__(self, frames, R):
+        super().__init__()
+        self._frames, self._R = frames, R
+
+    def __missing__(self, d):
+        v = self[d] = torch.cat([torch.where(f.nbr[d] >= 0, f.nbr[d] + self._R[d][i], f.nbr[d])
+                                 for i, f in enumerate(self._frames)])
+        return v
 
 
 class BatchFrame:
@@ -320,9 +348,8 @@ class BatchFrame:
                 self.off[d] = torch.cat([f.off[d][:-1] + R[d + 1][i]
                                          for i, f in enumerate(frames)] + [tail])
                 self.Y[d] = self.codes[d].long()
-        self.nbr = {d: torch.cat([torch.where(f.nbr[d] >= 0, f.nbr[d] + R[d][i], f.nbr[d])
-                                  for i, f in enumerate(frames)])
-                    for d in (self.b, self.t)}
+        self.nbr = _BatchMaps(frames, R)
+        self.nbr[self.b], self.nbr[self.t]
 
 
 # ------------------------------------------------------------------ model --
@@ -334,9 +361,12 @@ class QATModel(torch.nn.Module):
     """The float twin of the integer network with optional fake quantisation."""
 
     def __init__(self, params: dict, qat: bool = False, bf16: bool = False,
-                 recompute: bool = False):
+                 recompute: bool = False, arch: int = 0, t_off: int = 4):
+        """arch, t_off: the architecture (0 GRED + XFP, 1 GRED only,
+        2 baseline; Sec. 4.4) and t = L - t_off, as in the weight blob."""
         super().__init__()
         self.recompute = recompute
+        self.arch, self.t_off = arch, t_off
         self.names = sorted(params)
         self.p = torch.nn.ParameterDict(
             {k.replace(".", "__"): torch.nn.Parameter(torch.tensor(v, device="cuda"))
@@ -401,41 +431,50 @@ class QATModel(torch.nn.Module):
         def emb(name, d):
             return EmbedFn.apply(fr.codes[d], P(name))
 
-        ce = head
+        L, arch = fr.L, self.arch
+        t = L - self.t_off
 
         def level0():
             Fb = upl("UP_0", b, emb("E_0", b - 1))
-            return Fb, ce(pred(0, Fb), b)
+            return Fb, head(pred(0, Fb), b)
 
-        def level1(Fb):
-            Sb = resblock(1, b, Fb)
-            Ft = upl("UP_1", t, torch.cat([Sb, emb("E_1", b)], 1))
-            return Ft, ce(pred(1, Ft), t)
+        def shallow(j, Fp):  # with XFP, b < d <= t (Eq. 8-9)
+            d = b + j
+            S = resblock(j, d - 1, Fp)
+            F = upl(f"UP_{j}", d, torch.cat([S, emb(f"E_{j}", d - 1)], 1))
+            return F, head(pred(j, F), d)
 
-        def deep(j, Ft):
-            m = j - 1
-            d = t + m
+        def extracted(j, Ft):
+            # features of Y_{d-1} re-densified to V_k; with XFP fused with
+            # F^t (Eq. 10-11), otherwise alone (Eq. 4-6)
+            d = b + j
+            k0 = t if (arch == 0 or (arch == 1 and d > t)) else d - 1
             g = emb(f"G_{j}", d - 1)
-            for i in range(1, m):
+            for i in range(1, d - k0):
                 k = d - 1 - i
                 name = f"D_{j}_{i}"
                 g = DownFn.apply(q(g), fr.par[k + 1], fr.keys[k + 1], fr.off[k], w(name + ".W"),
                                  P(name + ".b"), bf)
                 g = prelu(g, name + ".a")
-            H = resblock(j, t, torch.cat([Ft, g], 1))
-            for k in range(m):
-                H = upl(f"UP_{j}_{k}", t + k + 1, torch.cat([H, emb(f"E_{j}_{k}", t + k)], 1))
-            return ce(pred(j, H), d)
+            H = resblock(j, k0, torch.cat([Ft, g], 1) if arch == 0 else g)
+            for k in range(d - k0):
+                x = torch.cat([H, emb(f"E_{j}_{k}", k0 + k)], 1) if arch == 0 else H
+                H = upl(f"UP_{j}_{k}", k0 + k + 1, x)
+            return head(pred(j, H), d)
 
         # with recompute, each relative level keeps only its outputs; its
         # activations are recomputed in the backward pass
         run = ((lambda f, *a: checkpoint(f, *a, use_reentrant=False)) if recompute
                else (lambda f, *a: f(*a)))
-        Fb, bits = run(level0)
-        Ft, b1 = run(level1, Fb)
-        bits = bits + b1
-        for j in range(2, 5):
-            bits = bits + run(lambda F, j=j: deep(j, F), Ft)
+        F, bits = run(level0)
+        for j in range(1, 5):
+            if arch == 0 and b + j <= t:
+                F, bj = run(lambda Fp, j=j: shallow(j, Fp), F)
+            elif arch == 0:
+                bj = run(lambda Ft, j=j: extracted(j, Ft), F)
+            else:
+                bj = run(lambda j=j: extracted(j, None))
+            bits = bits + bj
         return bits
 
     def grads(self) -> dict:

@@ -341,3 +341,25 @@ def test_batch_frame_equals_sum_of_frames():
     assert bits_b == pytest.approx(bits_s, rel=1e-5)
     name, err = _worst(gb, m.grads())
     assert err < 1e-5, (name, err)
+
+
+@pytest.mark.parametrize("arch,t_off", [(1, 3), (2, 4), (0, 3), (1, 4)],
+                         ids=["gred_t3", "baseline", "gred_xfp_t3", "gred_t4"])
+def test_model_gradients_arch_variants(frames, arch, t_off):
+    """The ablation architectures (Sec. 4.4) and t = L - 3 in the twin: rate
+    and every parameter's gradient against the FP64 reference (fp32, 1e-4),
+    kernel maps below V_t built from the parent level's map."""
+    from paper_2603_25260_b300 import train as G
+    ref, gpu, _ = frames
+    params = synth.twin_params(11, arch=arch, t_off=t_off)
+    P = T.to_torch(params)
+    bits_r = T.level_bits(P, ref, arch=arch, t_off=t_off)
+    g = torch.autograd.grad(bits_r, list(P.values()))
+    gr = {k: v.numpy() for k, v in zip(P, g)}
+    m = G.QATModel(params, arch=arch, t_off=t_off, recompute=arch == 1)
+    bits = m.bits(gpu)
+    bits.backward()
+    torch.cuda.synchronize()
+    assert float(bits.detach()) == pytest.approx(float(bits_r.detach()), rel=1e-5)
+    name, err = _worst(m.grads(), gr)
+    assert err < 1e-4, (name, err)
