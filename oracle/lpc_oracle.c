@@ -12,7 +12,11 @@
  *  - coded alphabet: symbol = code - 1 in 0..254 (Sec. 3.1, 255 classes);
  *  - base level b = L-5 (levels below are coded with adaptive symbol
  *    frequencies, supplement "Detailed Model Structure"), threshold t = L-4
- *    (supplement, "Ablation on the Choice of t"), dense level k = t;
+ *    or L-3 (supplement, "Ablation on the Choice of t"), dense level k = t;
+ *  - ablations (Sec. 4.4): without XFP a level d > b takes no feature from
+ *    the level above, only G^k = Downsampling(X^{d-1}) with Eq. 5-6 as
+ *    printed, k = t below t (GRED) and k = d-1 otherwise (and for every
+ *    level in the baseline); level b is the same in all architectures;
  *  - requantisation: round half up, floor shift, clip to [-128, 127] (Eq. 14);
  *  - PReLU on the INT32 accumulator before requantisation, Q15 slope;
  *  - absent neighbours / children contribute zero (zero padding, Sec. 3.1);

@@ -7,10 +7,11 @@
  * benchmark may load it.  It shares no source with the CUDA path.
  *
  * Parity status per function is stated at each declaration ("pinned by ...").
- * The network semantics as a whole (the level recurrences with seeded
- * weights) have no worked example in the paper and are "parity unpinned":
- * each op is pinned separately and the pipeline is pinned by the lossless
- * round trip.
+ * The paper prints no worked example of the network as a whole (the level
+ * recurrences with their weights): each op is pinned separately, the
+ * pipeline by the lossless round trip, and the integer logits of every level
+ * and architecture by the separately written FP64 float twin run on the
+ * parameters the blob was exported from (within quantisation rounding).
  *
  * All functions return 0 on success or a negative status:
  */
