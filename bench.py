@@ -447,10 +447,11 @@ def run_ours(args):
 
     ref_dec = out_dev[:n_out].clone()
 
-    def blob_leg(blob_bytes, steps=5):
-        """The step with another weight blob: median encode / decode times,
-        bits per point and whether the decoded voxels are the input's."""
-        bc = lpc.Codec(blob_bytes, spec.L, n, chunk=args.chunk)
+    def blob_leg(blob_bytes, steps=5, chunk=None):
+        """The step with another weight blob (or substream length): median
+        encode / decode times, bits per point and whether the decoded voxels
+        are the input's."""
+        bc = lpc.Codec(blob_bytes, spec.L, n, chunk=chunk or args.chunk)
         buf = np.empty_like(outbuf)  # outbuf keeps the seeded blob's stream
         for _ in range(max(args.warmup, 10)):
             ln = bc.encode_into(x, buf)
@@ -492,6 +493,14 @@ def run_ours(args):
             for t_off in (4, 3):
                 architectures[f"{name}_t{t_off}"] = blob_leg(
                     synth.make_blob(arch=arch, t_off=t_off), steps=7)
+
+    # substream length: the device decoder runs one warp per substream, so
+    # a level's decode latency is about chunk x the per-symbol time, while
+    # every substream adds its flush bytes and a length to the stream
+    chunk_tradeoff = None
+    if not args.no_arch:
+        chunk_tradeoff = {str(c): blob_leg(blob, steps=7, chunk=c) for c in (256, 512, 4096)
+                          if c != args.chunk}
 
     # the float inference variant (the float network, tables from a float
     # softmax): how many table rows come out differently when the softmax of
@@ -625,6 +634,7 @@ def run_ours(args):
         "host_coding": host_coding,
         "trained_blob": trained,
         "architectures": architectures,
+        "chunk_tradeoff": chunk_tradeoff,
         "float_variant": float_variant,
         "train": train,
         "e2e": {"value": round(e2e_value, 4), "unit": "Mpoints/s",
