@@ -22,14 +22,14 @@ namespace lpc {
 
 // ------------------------------------------------------------------ pool --
 Pool::Pool(int workers) {
-  for (int i = 0; i < workers; i++) th_.emplace_back([this] { loop(); });
+  for (int i = 0; i < workers; i++) th_.emplace_back([this, i] { loop(i); });
 }
 
 Pool::~Pool() {
   {
     std::lock_guard<std::mutex> g(mu_);
     stop_ = true;
-    spin_.store(false, std::memory_order_relaxed);
+    spin_.store(0, std::memory_order_relaxed);
   }
   cv_.notify_all();
   for (auto& t : th_) t.join();
@@ -62,34 +62,31 @@ static inline void cpu_relax() {
 #endif
 }
 
-void Pool::loop() {
+void Pool::loop(int idx) {
   std::unique_lock<std::mutex> lk(mu_);
+  auto polls = [&] { return idx < spin_.load(std::memory_order_relaxed); };
   for (;;) {
     if (stop_) return;
     if (run_one(lk)) continue;
-    if (spin_.load(std::memory_order_relaxed)) {
+    if (polls()) {
       lk.unlock();
-      for (int k = 1; spin_.load(std::memory_order_relaxed) &&
-                      queued_.load(std::memory_order_relaxed) == 0;
-           k++) {
+      for (int k = 1; polls() && queued_.load(std::memory_order_relaxed) == 0; k++) {
         cpu_relax();  // leaves the core's resources to a hyper-thread sibling
         if (k % 64 == 0) std::this_thread::yield();
       }
       lk.lock();
       continue;
     }
-    cv_.wait(lk, [&] {
-      return stop_ || head_ < q_.size() || spin_.load(std::memory_order_relaxed);
-    });
+    cv_.wait(lk, [&] { return stop_ || head_ < q_.size() || polls(); });
   }
 }
 
-void Pool::set_spin(bool on) {
+void Pool::set_spin(int n) {
   {
     std::lock_guard<std::mutex> g(mu_);
-    spin_.store(on, std::memory_order_relaxed);
+    spin_.store(n, std::memory_order_relaxed);
   }
-  if (on) cv_.notify_all();
+  if (n > 0) cv_.notify_all();
 }
 
 void Pool::submit(int group, std::function<void()> task) {
@@ -103,7 +100,9 @@ void Pool::submit(int group, std::function<void()> task) {
     pending_[group]++;
     queued_.fetch_add(1, std::memory_order_relaxed);
   }
-  cv_.notify_one();
+  // while workers poll, they take the task; a sleeping worker is not woken
+  // (its first milliseconds after waking run several times slower)
+  if (spin_.load(std::memory_order_relaxed) == 0) cv_.notify_one();
 }
 
 void Pool::wait(int group) {
@@ -437,9 +436,14 @@ int Codec::create(const lpc_config& cfg, const void* blob, size_t len) {
   }
   ev_.resize(512);
   for (auto& e : ev_) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
-  const int threads =
-      cfg.host_threads > 0 ? cfg.host_threads : (int)std::thread::hardware_concurrency();
+  // every worker polls during a call: a single frame's host work that kept
+  // to half the cores, the other workers asleep, measured slower (the
+  // sleepers' wake-ups) and no steadier on the shared hosts
+  const int threads = cfg.host_threads > 0
+                          ? cfg.host_threads
+                          : std::max(1, (int)std::thread::hardware_concurrency());
   pool_ = new Pool(std::max(0, threads - 1));
+  lat_threads_ = threads;
   return cuda_check("codec_create");
 }
 
@@ -846,7 +850,7 @@ void Codec::run_level(int j, int mode, uint16_t* cdf, uint32_t* enc) {
   // direct launches while profiling, and until the conv autotuner has picked
   // its variants (it times real launches, which a capture cannot)
   // (the ablation architectures have no 64-channel conv)
-  if (!gs_ || prof.mask || conv_variant_[0] < 0 ||
+  if (!gs_ || (prof.mask & ~kAsyncProfiled) || conv_variant_[0] < 0 ||
       (M_.arch == kArchXfp && conv_variant_[1] < 0) || pred_variant_ < 0) {
     net_level(j, mode, cdf, enc, nullptr);
     return;
@@ -892,7 +896,7 @@ int Codec::encode(int nf, const int32_t* const* xyz, const int64_t* n, const int
   if (nf < 1 || nf > F_ || !xyz || !n || !Ls || !out || !caps || !lens)
     return fail(LPC_INVALID_ARG, "encode: bad arguments");
   const double t0 = now_us();
-  SpinScope spin(pool_, true);
+  SpinScope spin(pool_, nf > 1 ? pool_->size() - 1 : lat_threads_ - 1);
   stats = Stats{};
   // frames with points go to the device batch, empty frames get a flag stream
   std::vector<int> dev;  // device frame index -> caller index
@@ -925,7 +929,7 @@ int Codec::encode(int nf, const int32_t* const* xyz, const int64_t* n, const int
     // once every level's network is a captured graph (sizes read on the
     // device), the network is queued behind the octree before the host has
     // its sizes, and the host's copies go through the copy stream
-    bool early = gs_ && cs_ && !prof.mask;
+    bool early = gs_ && cs_ && !(prof.mask & ~kAsyncProfiled);
     for (int j = 0; j < 5 && early; j++) early = gexec_[kPredEnc][j] != nullptr;
     if (early) {
       cudaMemcpyAsync(h_err_, d_err_, 4, cudaMemcpyDeviceToHost, st_);
@@ -1185,7 +1189,7 @@ int Codec::decode(int nf, const uint8_t* const* in, const size_t* lens, int32_t*
   if (nf < 1 || nf > F_ || !in || !lens || !out || !caps || !n_out)
     return fail(LPC_INVALID_ARG, "decode: bad arguments");
   const double t0 = now_us();
-  SpinScope spin(pool_, true);
+  SpinScope spin(pool_, nf > 1 ? pool_->size() - 1 : lat_threads_ - 1);
   stats = Stats{};
   std::vector<int> dev;
   std::vector<Frame> all(nf);
@@ -1277,7 +1281,8 @@ int Codec::decode(int nf, const uint8_t* const* in, const size_t* lens, int32_t*
       auto coarse = [&](int f) { coarse_frame(fr_[f], maxp, cstat); };
       int tasks = 0;
       for (int f = 0; f < nd; f++) tasks += fr_[f].b;
-      if (tasks <= pool_->size() && tasks <= kMaxCoarseTasks) {
+      const int lat = nd > 1 ? pool_->size() : lat_threads_;
+      if (tasks <= lat && tasks <= kMaxCoarseTasks) {
         // few frames: every level its own task, pipelined within a frame
         std::vector<CoarsePipe> pipes(nd);
         for (int f = 0; f < nd; f++) fr_[f].coarse.assign(fr_[f].b, {});
@@ -1285,6 +1290,20 @@ int Codec::decode(int nf, const uint8_t* const* in, const size_t* lens, int32_t*
           for (int d = 0; d < fr_[f].b; d++)
             if (f || d) pool_->submit(0, [&, f, d] { coarse_level(fr_[f], d, pipes[f], maxp, cstat); });
         coarse_level(fr_[0], 0, pipes[0], maxp, cstat);
+        pool_->wait(0);
+      } else if (nd == 1 && lat > 1) {
+        // one frame, fewer threads than levels: the leading levels (the
+        // smallest) in order on this thread, every deeper level its own
+        // task, still pipelined (a task only waits on the level above it,
+        // which was submitted or started before it)
+        Frame& F = fr_[0];
+        const int nt = std::min(F.b, lat);  // tasks, this thread included
+        const int g = F.b - nt + 1;  // levels 0..g-1 on this thread
+        CoarsePipe pipe;
+        F.coarse.assign(F.b, {});
+        for (int d = g; d < F.b; d++)
+          pool_->submit(0, [&, d] { coarse_level(F, d, pipe, maxp, cstat); });
+        for (int d = 0; d < g; d++) coarse_level(F, d, pipe, maxp, cstat);
         pool_->wait(0);
       } else {
         // many frames: one task per frame, the largest coarse streams first
@@ -1569,7 +1588,7 @@ int Codec::decode_net_device(int nd, int64_t* n_out, const std::vector<int>& dev
                              const int64_t* caps) {
   // once every level's network is a captured graph (sizes read on the
   // device), the levels need no host round trip
-  bool graphs = gs_ && !prof.mask;
+  bool graphs = gs_ && !(prof.mask & ~kAsyncProfiled);
   for (int j = 0; j < 5 && graphs; j++) graphs = gexec_[kPredCdf][j] != nullptr;
   if (graphs) return decode_net_async(nd, n_out, dev, caps);
   const int64_t maxp = cfg_.max_points;
@@ -1681,6 +1700,8 @@ int Codec::decode_net_async(int nd, int64_t* n_out, const std::vector<int>& dev,
   cudaMemcpyAsync(dsf, hsf, sizeof(DevSubFrame) * nd, cudaMemcpyHostToDevice, st_);
   cudaMemcpyAsync(dsub, hsub, 16 * (size_t)nsub, cudaMemcpyHostToDevice, st_);
   const uint8_t* d_in = static_cast<const uint8_t*>(d_rcbuf_.p);
+  int coder_marks[kHeights];  // profiler mark of each height's decode launch
+  for (int h = 0; h < kHeights; h++) coder_marks[h] = -1;
   for (int j = 0; j <= 5; j++) {  // j = 5: the leaves
     const int h = 5 - j;
     launch_expand(key_[h + 1], code_[h + 1], d_N_ + h + 1, P_, key_[h], par_[h], off_[h + 1], P_,
@@ -1698,7 +1719,11 @@ int Codec::decode_net_async(int nd, int64_t* n_out, const std::vector<int>& dev,
     if (h == 0) break;
     launch_rc_chunks(dfo, nd, dsf, dsub, dc, cap_ck, maxp, dnck, d_err_, st_);
     run_level(j, kPredCdf, d_cdf_, nullptr);
+    pbeg(kFamCoder);
     launch_rc_decode_dev(dc, dnck, cap_ck, d_cdf_, d_in, code_[h], d_err_, st_);
+    pend(kFamCoder, 0, 0);  // bytes once the level sizes are on the host
+    if (!marks_.empty() && marks_.back().f == kFamCoder && marks_.back().e1 >= 0)
+      coder_marks[h] = (int)marks_.size() - 1;
     if (int s = cuda_check("decode: launch")) return s;
   }
   cudaMemcpyAsync(h_foff_, d_foff_, 8 * (size_t)kHeights * (nd + 1), cudaMemcpyDeviceToHost, st_);
@@ -1716,6 +1741,13 @@ int Codec::decode_net_async(int nd, int64_t* n_out, const std::vector<int>& dev,
     if (F.cnt[0] > caps[dev[f]]) return fail(LPC_CAPACITY, "decode: output capacity too small");
   }
   for (int h = 0; h < 6; h++) N_[h] = h_foff_[(size_t)h * (nd + 1) + nd];
+  for (int h = 1; h < 6; h++)
+    if (coder_marks[h] >= 0) {  // table rows read, codes written
+      double nck = 0;
+      for (int f = 0; f < nd; f++)
+        nck += (double)((fr_[f].cnt[h] + fr_[f].chunk - 1) / fr_[f].chunk);
+      marks_[(size_t)coder_marks[h]].bytes = 513.0 * N_[h] + 32.0 * nck;
+    }
   cudaMemcpyAsync(d_fr_, h_fr_, sizeof(DevFrame) * nd, cudaMemcpyHostToDevice, st_);
   launch_keys_to_xyz_batch(key_[0], d_N_, N_[0], d_fr_, d_foff_, st_);
   return sync_and_check("decode");

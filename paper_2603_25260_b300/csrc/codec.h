@@ -29,12 +29,13 @@ class Pool {
   ~Pool();
   void submit(int group, std::function<void()> task);
   void wait(int group);
-  void set_spin(bool on);
+  // workers 0..n-1 poll the queue instead of sleeping (0: all sleep)
+  void set_spin(int n);
   int size() const { return (int)th_.size() + 1; }
   static constexpr int kGroups = 4;
 
  private:
-  void loop();
+  void loop(int idx);
   bool run_one(std::unique_lock<std::mutex>& lk);
   std::vector<std::thread> th_;
   std::mutex mu_;
@@ -45,7 +46,7 @@ class Pool {
   int running_ = 0;
   bool stop_ = false;
   std::atomic<int> queued_{0};
-  std::atomic<bool> spin_{false};
+  std::atomic<int> spin_{0};
 };
 
 // Keeps idle workers polling the queue for the lifetime of a codec call: on
@@ -55,11 +56,11 @@ class Pool {
 // sleeping, 7.6 ms polling).
 struct SpinScope {
   Pool* p;
-  SpinScope(Pool* pool, bool on) : p(on ? pool : nullptr) {
-    if (p) p->set_spin(true);
+  SpinScope(Pool* pool, int workers) : p(workers > 0 ? pool : nullptr) {
+    if (p) p->set_spin(workers);
   }
   ~SpinScope() {
-    if (p) p->set_spin(false);
+    if (p) p->set_spin(0);
   }
 };
 
@@ -77,6 +78,11 @@ enum Family {
   kFamCoder,     // device range coding of the network levels
   kFamCount
 };
+
+// Families whose launches the profiler can time on the graph and
+// round-trip-free paths (their launches sit outside the captured graphs);
+// timing any other family switches the codec to direct launches.
+constexpr unsigned kAsyncProfiled = (1u << kFamSort) | (1u << kFamCoder);
 
 // Per-family totals: summed launch durations (CUDA events on the codec's
 // stream), launches, and the algorithmic bytes / integer ops the launches
@@ -216,6 +222,7 @@ class Codec {
   cudaStream_t st_ = nullptr;
   Model M_;
   Pool* pool_ = nullptr;
+  int lat_threads_ = 1;  // threads (this one included) a single frame's host work may use
   // per-batch state
   int nf_ = 0;
   std::vector<Frame> fr_;

@@ -512,3 +512,17 @@ def test_fixed_variants_byte_identical(lpc, blob, variants):
         dec = cod.decode(data).cpu().numpy()
         assert np.array_equal(O.leaf_keys(dec, 13), O.leaf_keys(xyz, 13))
     assert cod.tuning()["predictor"] == variants[2]
+
+
+@pytest.mark.parametrize("threads", [1, 2, 4])
+def test_few_host_threads(lpc, blob, threads):
+    """Fewer host threads than coarse levels: the leading levels run in order
+    on the calling thread and each deeper level on its own worker, still
+    pipelined; one thread decodes the levels in order.  Same voxels."""
+    xyz = synth.random_cloud(20000, 16, 61)
+    data = O.encode(blob, xyz, 16)
+    want = O.decode(blob, data, xyz.shape[0])
+    cod = _codec(lpc, blob, 16, xyz.shape[0], host_threads=threads)
+    assert cod.encode(_cuda(xyz)) == data
+    for _ in range(2):
+        assert np.array_equal(cod.decode(data).cpu().numpy(), want)
