@@ -246,6 +246,11 @@ Codec::~Codec() {
   for (auto& row : gexec_)
     for (auto& e : row)
       if (e) cudaGraphExecDestroy(e);
+  if (genc_) cudaGraphExecDestroy(genc_);
+  for (auto s : ls_)
+    if (s) cudaStreamDestroy(s);
+  for (auto e : lev_)
+    if (e) cudaEventDestroy(e);
   for (auto e : gev_)
     if (e) cudaEventDestroy(e);
   for (auto e : tev_)
@@ -357,7 +362,20 @@ int Codec::create(const lpc_config& cfg, const void* blob, size_t len) {
   // t for GRED + XFP and GRED, L - 2 (height 2) for the baseline
   for (int h = 5; h >= (M_.arch == kArchBase ? 2 : M_.toff); h--) add((void**)&nbr_[h], 4 * 27 * P);
   if (M_.arch == kArchXfp && M_.toff == 3) add((void**)&fmid_, 32 * P);
-  if (M_.arch != kArchXfp) add((void**)&gk_, 32 * P);
+  add((void**)&gk_, 32 * P);
+  if (P <= kLanePoints)
+    for (int l = 1; l < kLanes; l++) {
+      Scratch& S = lane_[l];
+      add((void**)&S.y1, 32 * P);
+      add((void**)&S.g0, 32 * P);
+      add((void**)&S.g1, 32 * P);
+      add((void**)&S.gk, 32 * P);
+      add((void**)&S.hx0, 64 * P);
+      add((void**)&S.hx1, 64 * P);
+      add((void**)&S.fo, 32 * P);
+      add((void**)&S.xb16, 2 * 64 * P);
+      add((void**)&S.y1b16, 2 * 32 * P);
+    }
   add((void**)&fb_, 32 * P);
   add((void**)&xb_, 64 * P);
   add((void**)&xt_, 64 * P);
@@ -434,6 +452,13 @@ int Codec::create(const lpc_config& cfg, const void* blob, size_t len) {
     cudaGetLastError();
     cs_ = nullptr;
   }
+  lane_[0] = Scratch{y1_, g_[0], g_[1], gk_, hx_[0], hx_[1], fo_, xb16_, y1b16_};
+  lanes_ = gs_ != nullptr && lane_[1].y1 != nullptr;
+  for (int l = 1; l < kLanes && lanes_; l++)
+    lanes_ = cudaStreamCreateWithFlags(&ls_[l], cudaStreamNonBlocking) == cudaSuccess;
+  for (auto& e : lev_)
+    if (lanes_) lanes_ = cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+  cudaGetLastError();
   ev_.resize(512);
   for (auto& e : ev_) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
   // every worker polls during a call: a single frame's host work that kept
@@ -748,7 +773,20 @@ const int8_t* Codec::shallow_F(int h, int* stride) {
 
 // Network of relative level j (depth b + j of every frame, height 5 - j):
 // needs the levels above it and their codes.
-void Codec::net_level(int j, int mode, uint16_t* cdf, uint32_t* enc, int8_t* logits) {
+void Codec::set_lane(int l) {
+  const Scratch& S = lane_[l];
+  y1_ = S.y1;
+  g_[0] = S.g0;
+  g_[1] = S.g1;
+  gk_ = S.gk;
+  hx_[0] = S.hx0;
+  hx_[1] = S.hx1;
+  fo_ = S.fo;
+  xb16_ = S.xb16;
+  y1b16_ = S.y1b16;
+}
+
+void Codec::net_level(int j, int mode, uint16_t* cdf, uint32_t* enc, int8_t* logits, int part) {
   const int h = 5 - j;
   auto pred = [&](int jj, const int8_t* F, int stride) {
     auto go = [&](int v) {
@@ -796,33 +834,37 @@ void Codec::net_level(int j, int mode, uint16_t* cdf, uint32_t* enc, int8_t* log
   const int hk = h + m;
   const bool cat = M_.arch == kArchXfp;
   const int w = cat ? 64 : 32;  // row width of the ResBlock's input
-  int8_t* gout = cat ? xt_ : gk_;
-  const int gc = cat ? 32 : 0;
-  if (cat) {
-    int fs = 32;
-    shallow_F(hk, &fs);
-  }
-  ensure_nbr(hk);
-  // G^k = Downsampling(Y_{d-1}) (Eq. 4): embedding at height h + 1, then
-  // m - 1 stride-2 steps up to height hk
-  if (m == 1) {
-    embed(M_.G[j], h + 1, gout, w, gc);
-  } else {
-    embed(M_.G[j], h + 1, g_[0], 32, 0);
-    const int8_t* cur = g_[0];
-    for (int i = 1; i < m; i++) {
-      const int hp = h + 1 + i;  // parent height of this step
-      int8_t* dst = i == m - 1 ? gout : g_[i & 1];
-      const int ds = i == m - 1 ? w : 32, dc = i == m - 1 ? gc : 0;
-      pbeg(kFamDown);
-      launch_down(M_.D[j][i], key_[hp - 1], off_[hp], d_N_ + hp, gridn(hp), cur, 32, dst, ds, dc,
-                  st_);
-      pend(kFamDown, 32.0 * (N_[hp - 1] + N_[hp]), 2.0 * N_[hp - 1] * 32 * 32);
-      cur = dst;
+  if (part != kNetPost) {
+    // G^k = Downsampling(Y_{d-1}) (Eq. 4): embedding at height h + 1, then
+    // m - 1 stride-2 steps up to height hk, into gk_
+    if (m == 1) {
+      embed(M_.G[j], h + 1, gk_, 32, 0);
+    } else {
+      embed(M_.G[j], h + 1, g_[0], 32, 0);
+      const int8_t* cur = g_[0];
+      for (int i = 1; i < m; i++) {
+        const int hp = h + 1 + i;  // parent height of this step
+        int8_t* dst = i == m - 1 ? gk_ : g_[i & 1];
+        pbeg(kFamDown);
+        launch_down(M_.D[j][i], key_[hp - 1], off_[hp], d_N_ + hp, gridn(hp), cur, 32, dst, 32, 0,
+                    st_);
+        pend(kFamDown, 32.0 * (N_[hp - 1] + N_[hp]), 2.0 * N_[hp - 1] * 32 * 32);
+        cur = dst;
+      }
     }
+    if (part == kNetPre) return;
   }
+  int fs = 32;
+  const int8_t* Ft = cat ? shallow_F(hk, &fs) : nullptr;
+  ensure_nbr(hk);
   // H^k = ResBlock(Concat(F^t, G^t)) (Eq. 10), or ResBlock(G^k) (Eq. 5)
-  to_bf16(gout, w, w, M_.RA[j].z_in, hk);
+  if (cat) {
+    pbeg(kFamEmbed);
+    launch_to_bf16_cat(Ft, fs, gk_, 32, M_.RA[j].z_in, d_N_ + hk, gridn(hk), xb16_, st_);
+    pend(kFamEmbed, 3.0 * 64 * N_[hk], 0);
+  } else {
+    to_bf16(gk_, 32, 32, M_.RA[j].z_in, hk);
+  }
   conv(M_.RA[j], hk, nbr_[hk], 5 - hk, xb16_, w, y1_, 32, 0, nullptr, y1b16_, M_.RB[j].z_in);
   conv(M_.RB[j], hk, nbr_[hk], 5 - hk, y1b16_, 32, hx_[0], w, 0, &M_.RM[j], nullptr, 0);
   // F^{k+1} = Pruning(Upsampling(Concat(H^k, Y_k)), Y_k) (Eq. 11), or
@@ -889,6 +931,95 @@ void Codec::run_level(int j, int mode, uint16_t* cdf, uint32_t* enc) {
   count_launches(gkern_[mode][j]);
 }
 
+// The encoder's five levels with levels 3 and 4 (the longest chains) on
+// lanes 1 and 2: each lane starts its level's Downsampling chain at once and
+// the rest once the propagated F^t and the kernel maps it reads exist; the
+// main stream computes those first, then runs levels 0..2.  Inside a capture
+// the lanes fork from and join the capturing stream.
+void Codec::enc_network_lanes() {
+  cudaStream_t main = st_;
+  const int jl[kLanes] = {-1, 4, 3};
+  cudaEventRecord(lev_[0], main);
+  for (int l = 1; l < kLanes; l++) {
+    cudaStreamWaitEvent(ls_[l], lev_[0], 0);
+    st_ = ls_[l];
+    set_lane(l);
+    net_level(jl[l], kPredEnc, nullptr, d_enc_ + (size_t)jl[l] * P_, nullptr, kNetPre);
+  }
+  st_ = main;
+  set_lane(0);
+  for (int l = 1; l < kLanes; l++) {  // what the lanes' levels read
+    const int hk = 5 - jl[l] + M_.span[jl[l]];
+    int fs = 32;
+    if (M_.arch == kArchXfp) shallow_F(hk, &fs);
+    ensure_nbr(hk);
+  }
+  cudaEventRecord(lev_[1], main);
+  for (int l = 1; l < kLanes; l++) {
+    st_ = ls_[l];
+    set_lane(l);
+    cudaStreamWaitEvent(ls_[l], lev_[1], 0);
+    net_level(jl[l], kPredEnc, nullptr, d_enc_ + (size_t)jl[l] * P_, nullptr, kNetPost);
+    cudaEventRecord(lev_[1 + l], ls_[l]);
+  }
+  st_ = main;
+  set_lane(0);
+  for (int j = 0; j < 3; j++) net_level(j, kPredEnc, nullptr, d_enc_ + (size_t)j * P_, nullptr);
+  for (int l = 1; l < kLanes; l++) cudaStreamWaitEvent(main, lev_[1 + l], 0);
+}
+
+bool Codec::enc_graphs_ready() const {
+  if (lanes_) return genc_ != nullptr;
+  for (int j = 0; j < 5; j++)
+    if (!gexec_[kPredEnc][j]) return false;
+  return true;
+}
+
+// The encoder's network: one captured graph of the laned levels when the
+// codec has lanes, else level by level.
+void Codec::run_enc_network() {
+  const bool direct = !gs_ || (prof.mask & ~kAsyncProfiled) || conv_variant_[0] < 0 ||
+                      (M_.arch == kArchXfp && conv_variant_[1] < 0) || pred_variant_ < 0;
+  if (!lanes_ || direct || genc_fail_) {
+    for (int j = 0; j < 5; j++) run_level(j, kPredEnc, nullptr, d_enc_ + (size_t)j * P_);
+    return;
+  }
+  if (!genc_) {
+    cudaStream_t saved = st_;
+    st_ = gs_;
+    cap_grid_ = true;
+    const int64_t c0 = launches_total();
+    cudaGraph_t g = nullptr;
+    bool ok = cudaStreamBeginCapture(gs_, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      enc_network_lanes();
+      ok = cudaStreamEndCapture(gs_, &g) == cudaSuccess && g;
+    }
+    const int64_t n = launches_total() - c0;
+    count_launches((int)-n);  // captured, not run
+    genc_kern_ = (int)n;
+    if (ok && cudaGraphInstantiate(&genc_, g, 0) != cudaSuccess) genc_ = nullptr;
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    st_ = saved;
+    set_lane(0);
+    cap_grid_ = false;
+    if (!genc_) {
+      // the capture's host-side marks (features and maps "made") are void
+      genc_fail_ = true;
+      for (int h = 0; h < kHeights; h++) have_F_[h] = have_nbr_[h] = false;
+      for (int j = 0; j < 5; j++) run_level(j, kPredEnc, nullptr, d_enc_ + (size_t)j * P_);
+      return;
+    }
+  }
+  cudaEventRecord(gev_[0], st_);
+  cudaStreamWaitEvent(gs_, gev_[0], 0);
+  cudaGraphLaunch(genc_, gs_);
+  cudaEventRecord(gev_[1], gs_);
+  cudaStreamWaitEvent(st_, gev_[1], 0);
+  count_launches(genc_kern_);
+}
+
 // --------------------------------------------------------------- encode --
 int Codec::encode(int nf, const int32_t* const* xyz, const int64_t* n, const int* Ls,
                   uint8_t* const* out, const size_t* caps, size_t* lens) {
@@ -929,12 +1060,11 @@ int Codec::encode(int nf, const int32_t* const* xyz, const int64_t* n, const int
     // once every level's network is a captured graph (sizes read on the
     // device), the network is queued behind the octree before the host has
     // its sizes, and the host's copies go through the copy stream
-    bool early = gs_ && cs_ && !(prof.mask & ~kAsyncProfiled);
-    for (int j = 0; j < 5 && early; j++) early = gexec_[kPredEnc][j] != nullptr;
+    const bool early = gs_ && cs_ && !(prof.mask & ~kAsyncProfiled) && enc_graphs_ready();
     if (early) {
       cudaMemcpyAsync(h_err_, d_err_, 4, cudaMemcpyDeviceToHost, st_);
       cudaEventRecord(ev_[8], st_);
-      for (int j = 0; j < 5; j++) run_level(j, kPredEnc, nullptr, d_enc_ + (size_t)j * P_);
+      run_enc_network();
       if (cudaEventSynchronize(ev_[8]) != cudaSuccess) return cuda_check("encode: octree");
       if (*h_err_ != 0) {
         cudaStreamSynchronize(st_);
@@ -968,10 +1098,10 @@ int Codec::encode(int nf, const int32_t* const* xyz, const int64_t* n, const int
                       cst);
     cudaEventRecord(ev_[0], cst);
     // network levels of all frames: (C_s, f_s) of the true symbol of every
-    // node; each level's intervals go to the host as soon as it is done
+    // node; with host coding each level's intervals then go to the host
+    if (!early) run_enc_network();
     for (int j = 0; j < 5; j++) {
       const int h = 5 - j;
-      if (!early) run_level(j, kPredEnc, nullptr, d_enc_ + (size_t)j * P_);
       if (!dev_rc_) {
         cudaMemcpyAsync(h_enc_ + (size_t)j * P_, d_enc_ + (size_t)j * P_, 4 * N_[h],
                         cudaMemcpyDeviceToHost, st_);

@@ -166,8 +166,33 @@ class Codec {
   void kmap(int h, int32_t* nbr, int slot);
   void ensure_nbr(int h);
   const int8_t* shallow_F(int h, int* stride);
-  void net_level(int j, int mode, uint16_t* cdf, uint32_t* enc, int8_t* logits);
+  // part: kNetAll, or a level's Downsampling chain alone (kNetPre) and the
+  // rest (kNetPost)
+  enum { kNetAll = 0, kNetPre = 1, kNetPost = 2 };
+  void net_level(int j, int mode, uint16_t* cdf, uint32_t* enc, int8_t* logits,
+                 int part = kNetAll);
   void run_level(int j, int mode, uint16_t* cdf, uint32_t* enc);
+  // Scratch of a level's network.  Lane 0 is the codec's own; lanes 1 and 2
+  // let the encoder run two levels beside the others (every level's input
+  // is known to the encoder, and the small levels leave most SMs idle).
+  struct Scratch {
+    int8_t *y1 = nullptr, *g0 = nullptr, *g1 = nullptr, *gk = nullptr, *hx0 = nullptr,
+           *hx1 = nullptr, *fo = nullptr;
+    void *xb16 = nullptr, *y1b16 = nullptr;
+  };
+  static constexpr int kLanes = 3;
+  static constexpr int64_t kLanePoints = (int64_t)1 << 22;  // lanes 1, 2 up to this capacity
+  Scratch lane_[kLanes];
+  cudaStream_t ls_[kLanes] = {};
+  cudaEvent_t lev_[4] = {};
+  bool lanes_ = false;
+  void set_lane(int l);
+  cudaGraphExec_t genc_ = nullptr;  // the encoder's five levels, lanes side by side
+  bool genc_fail_ = false;
+  int genc_kern_ = 0;
+  void enc_network_lanes();
+  void run_enc_network();
+  bool enc_graphs_ready() const;
   // grid size for level height h: its size, or the capacity while a graph
   // is captured (kernels read the real size on the device)
   int64_t gridn(int h) const { return cap_grid_ ? P_ : N_[h]; }
@@ -195,6 +220,8 @@ class Codec {
           cudaGraphExecDestroy(e);
           e = nullptr;
         }
+    if (genc_) cudaGraphExecDestroy(genc_);
+    genc_ = nullptr;
   }
   float pred_tune_ms_[kPredVariants] = {};
  private:

@@ -379,8 +379,10 @@ k_conv333_tc(ConvTcArgs a) {
   if (t == 0 && abort_flag) atomicExch(&g_conv_error, 1);
 }
 
-// int8 rows -> bf16 (q - z) rows for the tensor-core gather
-__global__ void k_to_bf16(const int8_t* __restrict__ x, int x_stride, int cols, int z,
+// int8 rows -> bf16 (q - z) rows for the tensor-core gather; columns
+// [0, x_cols) come from x, the rest (the concatenated second half) from x2
+__global__ void k_to_bf16(const int8_t* __restrict__ x, int x_stride, int x_cols,
+                          const int8_t* __restrict__ x2, int x2_stride, int cols, int z,
                           const int64_t* d_n, __nv_bfloat16* out) {
   const int64_t n = *d_n;
   const int per = cols / 8;
@@ -388,7 +390,9 @@ __global__ void k_to_bf16(const int8_t* __restrict__ x, int x_stride, int cols, 
        q += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = q / per;
     const int c = (int)(q - r * per);
-    const uint2 raw = *reinterpret_cast<const uint2*>(x + r * x_stride + c * 8);
+    const int8_t* src = c * 8 < x_cols ? x + r * x_stride + c * 8
+                                       : x2 + r * x2_stride + (c * 8 - x_cols);
+    const uint2 raw = *reinterpret_cast<const uint2*>(src);
     const int8_t* b = reinterpret_cast<const int8_t*>(&raw);
     __align__(16) __nv_bfloat16 v[8];
 #pragma unroll
@@ -428,7 +432,17 @@ void launch_to_bf16(const int8_t* x, int x_stride, int cols, int z, const int64_
   if (n_host <= 0) return;
   const int64_t work = n_host * (cols / 8);
   const int blocks = (int)std::min<int64_t>((work + 255) / 256, 148 * 8);
-  k_to_bf16<<<blocks, 256, 0, st>>>(x, x_stride, cols, z, d_n,
+  k_to_bf16<<<blocks, 256, 0, st>>>(x, x_stride, cols, x, x_stride, cols, z, d_n,
+                                    reinterpret_cast<__nv_bfloat16*>(out));
+  count_launches(1);
+}
+
+void launch_to_bf16_cat(const int8_t* a, int a_stride, const int8_t* b, int b_stride, int z,
+                        const int64_t* d_n, int64_t n_host, void* out, cudaStream_t st) {
+  if (n_host <= 0) return;
+  const int64_t work = n_host * 8;
+  const int blocks = (int)std::min<int64_t>((work + 255) / 256, 148 * 8);
+  k_to_bf16<<<blocks, 256, 0, st>>>(a, a_stride, 32, b, b_stride, 64, z, d_n,
                                     reinterpret_cast<__nv_bfloat16*>(out));
   count_launches(1);
 }

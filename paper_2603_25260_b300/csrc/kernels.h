@@ -245,6 +245,9 @@ void launch_conv333_tc(const ConvTcArgs& a, int cin, int64_t n_host, cudaStream_
 // int8 rows (stride x_stride) -> bf16 (q - z) rows of `cols` elements.
 void launch_to_bf16(const int8_t* x, int x_stride, int cols, int z, const int64_t* d_n,
                     int64_t n_host, void* out, cudaStream_t st);
+// The same for the 64 columns of Concat(a, b): 32 int8 columns from each.
+void launch_to_bf16_cat(const int8_t* a, int a_stride, const int8_t* b, int b_stride, int z,
+                        const int64_t* d_n, int64_t n_host, void* out, cudaStream_t st);
 // Non-zero if a tensor-core conv gave up on a bounded wait (optionally reset).
 int conv_tc_error(bool reset);
 
