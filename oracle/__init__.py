@@ -270,8 +270,10 @@ def logits_level(blob: bytes, xyz: np.ndarray, L: int, d: int) -> np.ndarray:
 def encode(blob: bytes, xyz: np.ndarray, L: int, chunk: int = 1024) -> bytes:
     xyz = np.ascontiguousarray(xyz, dtype=np.int32)
     # coded bytes: at most 2 per symbol, plus flush bytes and a length varint
-    # per substream (one substream per chunk of every network level)
-    cap = 64 + xyz.shape[0] * 4 * 4 + 4096 + 16 * (5 * (xyz.shape[0] // chunk + 1) + L)
+    # per substream (one substream per chunk of every network level and per
+    # 4096 nodes of every coarse level) and the coarse levels' sizes
+    n = xyz.shape[0]
+    cap = 64 + n * 4 * 4 + 4096 + 16 * (5 * (n // chunk + 1) + L) + 16 * L * (n // 4096 + 3)
     out = np.zeros(cap, dtype=np.uint8)
     ln = C.c_size_t()
     _check(lib().or_encode(blob, len(blob), _p(xyz), xyz.shape[0], L, chunk, _p(out), cap,

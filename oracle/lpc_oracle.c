@@ -944,10 +944,14 @@ int or_probs_level(const void* blob, size_t blob_len, const int32_t* xyz, int64_
 /* ------------------------------------------------------------------------ */
 /* Bitstream                                                                 */
 /* ------------------------------------------------------------------------ */
-/* "LPC1", u8 version, u8 L, u8 b, u8 t, u8 C, u8 flags (bit0 = empty),
- * u64 blob hash (LE), varint chunk, varint n_sub, n_sub x varint length,
- * then the substreams: coarse levels 0..b-1 (adaptive, one each), then for
- * d = b..L-1 the level's Morton-ordered nodes in chunks of `chunk`. */
+/* "LPC1", u8 version (2), u8 L, u8 b, u8 t, u8 C, u8 flags (bit0 = empty),
+ * u64 blob hash (LE), varint chunk, varint coarse chunk, varint N_1 ..
+ * N_{b-1} (the coarse levels' sizes; absent for an empty frame), varint
+ * n_sub, n_sub x varint length, then the substreams: coarse levels 0..b-1 in
+ * chunks of `coarse chunk` nodes (adaptive, a fresh model each), then for
+ * d = b..L-1 the level's Morton-ordered nodes in chunks of `chunk`.  With
+ * the sizes in the header every coarse chunk decodes on its own. */
+#define COARSE_CHUNK 4096
 
 typedef struct {
   uint8_t* p;
@@ -1008,19 +1012,23 @@ int or_encode(const void* blob, size_t blob_len, const int32_t* xyz, int64_t n, 
   bytes subs = {0}, lens = {0};
   uint64_t n_sub = 0;
   if (n > 0) {
-    /* coarse levels: adaptive symbol frequencies */
+    /* coarse levels: adaptive symbol frequencies, every COARSE_CHUNK
+     * symbols a substream with a fresh model */
     for (int d = 0; d < b; d++) {
-      rc_enc e;
-      amodel am;
-      uint8_t* tmp;
-      sub_begin(&e, &tmp, (size_t)T.N[d]);
-      am_init(&am);
-      for (int64_t i = 0; i < T.N[d]; i++) am_encode(&e, &am, T.code[d][i] - 1);
-      enc_flush(&e);
-      by_put(&subs, tmp, e.len);
-      by_varint(&lens, e.len);
-      n_sub++;
-      free(tmp);
+      for (int64_t s0 = 0; s0 < T.N[d]; s0 += COARSE_CHUNK) {
+        const int64_t s1 = s0 + COARSE_CHUNK < T.N[d] ? s0 + COARSE_CHUNK : T.N[d];
+        rc_enc e;
+        amodel am;
+        uint8_t* tmp;
+        sub_begin(&e, &tmp, (size_t)(s1 - s0));
+        am_init(&am);
+        for (int64_t i = s0; i < s1; i++) am_encode(&e, &am, T.code[d][i] - 1);
+        enc_flush(&e);
+        by_put(&subs, tmp, e.len);
+        by_varint(&lens, e.len);
+        n_sub++;
+        free(tmp);
+      }
     }
     /* network levels */
     net S = {M, &T, L, b, t, {NULL}};
@@ -1050,7 +1058,7 @@ int or_encode(const void* blob, size_t blob_len, const int32_t* xyz, int64_t n, 
   bytes H = {0};
   uint8_t hdr[18];
   memcpy(hdr, "LPC1", 4);
-  hdr[4] = 1;
+  hdr[4] = 2;
   hdr[5] = (uint8_t)L;
   hdr[6] = (uint8_t)b;
   hdr[7] = (uint8_t)t;
@@ -1059,6 +1067,9 @@ int or_encode(const void* blob, size_t blob_len, const int32_t* xyz, int64_t n, 
   for (int i = 0; i < 8; i++) hdr[10 + i] = (uint8_t)(M->hash >> (8 * i));
   by_put(&H, hdr, 18);
   by_varint(&H, (uint64_t)chunk);
+  by_varint(&H, (uint64_t)COARSE_CHUNK);
+  if (n > 0)
+    for (int d = 1; d < b; d++) by_varint(&H, (uint64_t)T.N[d]);
   by_varint(&H, n_sub);
   if (lens.len) by_put(&H, lens.p, lens.len);
   if (subs.len) by_put(&H, subs.p, subs.len);
@@ -1079,7 +1090,7 @@ int or_decode(const void* blob, size_t blob_len, const uint8_t* in, size_t len,
   int st = load_model(blob, blob_len, M);
   if (st) { free(M); return st; }
   *n_out = 0;
-  if (len < 18 || memcmp(in, "LPC1", 4) != 0 || in[4] != 1) { free(M); return OR_CORRUPT_STREAM; }
+  if (len < 18 || memcmp(in, "LPC1", 4) != 0 || in[4] != 2) { free(M); return OR_CORRUPT_STREAM; }
   const int L = in[5], b = in[6], t = in[7], C = in[8], flags = in[9];
   uint64_t hash = 0;
   for (int i = 0; i < 8; i++) hash |= (uint64_t)in[10 + i] << (8 * i);
@@ -1087,9 +1098,19 @@ int or_decode(const void* blob, size_t blob_len, const uint8_t* in, size_t len,
   if (hash != M->hash || C != M->C) { free(M); return OR_WEIGHTS_MISMATCH; }
   if (t != L - M->toff) { free(M); return OR_CORRUPT_STREAM; }
   size_t pos = 18;
-  uint64_t chunk, n_sub;
-  if (rd_varint(in, len, &pos, &chunk) || rd_varint(in, len, &pos, &n_sub) || chunk < 1 ||
-      chunk > (1u << 30) || n_sub > len) {
+  uint64_t chunk, cchunk, n_sub;
+  uint64_t cN[22] = {1}; /* coarse level sizes N_0 = 1, N_1 .. N_{b-1} from the header */
+  if (rd_varint(in, len, &pos, &chunk) || rd_varint(in, len, &pos, &cchunk) || chunk < 1 ||
+      chunk > (1u << 30) || cchunk < 1 || cchunk > (1u << 30)) {
+    free(M);
+    return OR_CORRUPT_STREAM;
+  }
+  for (int d = 1; d < b && !(flags & 1); d++)
+    if (rd_varint(in, len, &pos, &cN[d]) || cN[d] < 1 || cN[d] > 8 * cN[d - 1]) {
+      free(M);
+      return OR_CORRUPT_STREAM;
+    }
+  if (rd_varint(in, len, &pos, &n_sub) || n_sub > len) {
     free(M);
     return OR_CORRUPT_STREAM;
   }
@@ -1115,10 +1136,15 @@ int or_decode(const void* blob, size_t blob_len, const uint8_t* in, size_t len,
     T.N[0] = 1;
     T.key[0] = (uint64_t*)calloc(1, sizeof(uint64_t));
     for (int d = 0; d < b && !st; d++) {
-      if (si >= n_sub) { st = OR_CORRUPT_STREAM; break; }
+      /* the header's N_d must be what the level above expands to */
+      if ((uint64_t)T.N[d] != cN[d]) { st = OR_CORRUPT_STREAM; break; }
       T.code[d] = (uint8_t*)malloc((size_t)T.N[d]);
-      st = or_rc_decode_adaptive(T.N[d], in + so[si], (size_t)sl[si], T.code[d]);
-      si++;
+      for (int64_t s0 = 0; s0 < T.N[d] && !st; s0 += (int64_t)cchunk) {
+        const int64_t s1 = s0 + (int64_t)cchunk < T.N[d] ? s0 + (int64_t)cchunk : T.N[d];
+        if (si >= n_sub) { st = OR_CORRUPT_STREAM; break; }
+        st = or_rc_decode_adaptive(s1 - s0, in + so[si], (size_t)sl[si], T.code[d] + s0);
+        si++;
+      }
       for (int64_t i = 0; !st && i < T.N[d]; i++) T.code[d][i] += 1;
       if (!st) st = octree_expand(&T, d);
     }

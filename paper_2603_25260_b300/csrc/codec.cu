@@ -115,99 +115,68 @@ void Pool::wait(int group) {
 
 // ------------------------------------------------------------ bitstream --
 // ------------------------------------------------- coarse-level decoding --
-// The coarse levels of a frame form a chain: N_d, the symbol count of level
-// d, is the popcount sum of the codes of level d - 1.  Every decoded code of
-// level d - 1 adds its popcount to a lower bound of N_d that level d's task
-// reads, and level d decodes only below that bound (never past N_d), so the
-// levels of a frame run side by side and the frame takes about as long as
-// its largest level instead of the sum.  Tasks wait only on the task of the
-// level above, submitted before them to the first-in first-out pool, so a
-// waited-on task is always running or done.
+// Every coarse level is coded in chunks of kc nodes, each chunk its own
+// substream with a fresh adaptive model, and the stream's header carries the
+// levels' sizes: every chunk of every level decodes on its own, in parallel.
+// The sizes are checked afterwards against the codes (N_d is the popcount sum
+// of the codes of level d - 1).
 namespace {
 
-struct CoarsePipe {
-  std::atomic<int64_t> avail[kMaxDepth + 1];  // codes of level d known to exist
-  std::atomic<bool> fin[kMaxDepth + 1];       // avail[d] is N_d
-  CoarsePipe() {
-    for (int d = 0; d <= kMaxDepth; d++) {
-      avail[d].store(d == 0 ? 1 : 0);
-      fin[d].store(d == 0);
-    }
-  }
-};
 constexpr int kMaxCoarseTasks = 64;
 constexpr int kSplitFrames = 8;  // decode batches of at least this many frames in two groups
-constexpr int64_t kCoarseBatch = 128;  // codes decoded between bound updates
 
-// All coarse levels of one frame in order on this thread.
-void coarse_frame(Frame& F, int64_t maxp, std::atomic<int>& status) {
+void coarse_alloc(Frame& F) {
   F.coarse.assign(F.b, {});
-  int64_t n = 1;
-  for (int d = 0; d < F.b; d++) {
-    std::vector<uint8_t>& Y = F.coarse[d];
-    Y.resize((size_t)n);
-    if (!decode_adaptive(Y.size(), F.in + F.soff[d], (size_t)F.slen[d], Y.data())) {
-      status = LPC_CORRUPT_STREAM;
-      return;
-    }
-    n = 0;
-    for (auto& y : Y) n += __builtin_popcount(++y);
-    if (n > maxp) {
-      status = LPC_CAPACITY;
-      return;
-    }
-  }
+  for (int d = 0; d < F.b; d++) F.coarse[d].resize((size_t)F.cN[d]);
 }
 
-void coarse_level(Frame& F, int d, CoarsePipe& P, int64_t maxp, std::atomic<int>& status) {
-  RangeDecoder dec(F.in + F.soff[d], (size_t)F.slen[d]);
-  AdaptiveModel m;
-  std::vector<uint8_t>& Y = F.coarse[d];
-  int64_t i = 0, pc = 0;
-  const bool last = d + 1 >= F.b;
-  for (;;) {
-    const bool fin = P.fin[d].load(std::memory_order_acquire);
-    const int64_t a = P.avail[d].load(std::memory_order_acquire);
-    if (status.load(std::memory_order_relaxed)) return;
-    if (i >= a) {
-      if (fin) break;
-      cpu_relax();
-      std::this_thread::yield();
-      continue;
-    }
-    const int64_t stop = std::min(a, i + kCoarseBatch);
-    if ((int64_t)Y.size() < stop) Y.resize((size_t)std::max<int64_t>(stop, 2 * (int64_t)Y.size()));
-    for (; i < stop; i++) {
-      const int y = m.decode(dec) + 1;
-      Y[(size_t)i] = (uint8_t)y;
-      pc += __builtin_popcount((unsigned)y);
-    }
-    if (dec.bad()) {
-      status = LPC_CORRUPT_STREAM;
-      return;
-    }
-    if (pc > maxp) {
-      status = LPC_CAPACITY;
-      return;
-    }
-    if (!last) P.avail[d + 1].store(pc, std::memory_order_release);
+// Chunk k of coarse level d from substream `sub`.
+bool coarse_chunk(Frame& F, int d, int64_t k, size_t sub) {
+  const int64_t s0 = k * F.kc, n = std::min(F.kc, F.cN[d] - s0);
+  uint8_t* Y = F.coarse[d].data() + s0;
+  if (!decode_adaptive((size_t)n, F.in + F.soff[sub], (size_t)F.slen[sub], Y)) return false;
+  for (int64_t i = 0; i < n; i++) Y[i]++;  // symbol s codes occupancy s + 1
+  return true;
+}
+
+bool coarse_consistent(const Frame& F) {
+  for (int d = 1; d < F.b; d++) {
+    int64_t c = 0;
+    for (uint8_t y : F.coarse[d - 1]) c += __builtin_popcount(y);
+    if (c != F.cN[d]) return false;
   }
-  Y.resize((size_t)i);
-  if (!last) {
-    P.avail[d + 1].store(pc, std::memory_order_release);
-    P.fin[d + 1].store(true, std::memory_order_release);
-  }
+  return true;
+}
+
+// All coarse levels of one frame in order on this thread.
+void coarse_frame(Frame& F, std::atomic<int>& status) {
+  coarse_alloc(F);
+  size_t sub = 0;
+  for (int d = 0; d < F.b; d++)
+    for (int64_t k = 0; k * F.kc < F.cN[d]; k++)
+      if (!coarse_chunk(F, d, k, sub++)) {
+        status = LPC_CORRUPT_STREAM;
+        return;
+      }
+  if (!coarse_consistent(F)) status = LPC_CORRUPT_STREAM;
 }
 
 }  // namespace
 
-// "LPC1", u8 version, u8 L, u8 b, u8 t, u8 C, u8 flags (bit0: empty frame),
-// u64 blob hash (little endian), varint chunk, varint n_sub, n_sub varint
-// lengths, then the substreams: coarse levels 0..b-1 (adaptive model, one
-// each), then every network level d = b..L-1 in chunks of `chunk` nodes.
+// "LPC1", u8 version (2), u8 L, u8 b, u8 t, u8 C, u8 flags (bit0: empty
+// frame), u64 blob hash (little endian), varint chunk, varint coarse chunk,
+// varint N_1 .. N_{b-1} (not for an empty frame), varint n_sub, n_sub varint
+// lengths, then the substreams: coarse levels 0..b-1 in chunks of `coarse
+// chunk` nodes (adaptive model, a fresh one each), then every network level
+// d = b..L-1 in chunks of `chunk` nodes.
 namespace {
 
 constexpr int kHdr = 18;
+constexpr int64_t kCoarseChunk = 4096;
+// arena bytes of a coarse level of n nodes: every chunk's coded bound
+size_t coarse_level_bound(int64_t n) {
+  return 2 * (size_t)n + 8 * (size_t)((n + kCoarseChunk - 1) / kCoarseChunk);
+}
 // Batches of at least this many points build their three lowest coarse
 // heights with the multi-block scan.
 constexpr int64_t kCoarseScanPoints = 262144;
@@ -468,7 +437,6 @@ int Codec::create(const lpc_config& cfg, const void* blob, size_t len) {
                           ? cfg.host_threads
                           : std::max(1, (int)std::thread::hardware_concurrency());
   pool_ = new Pool(std::max(0, threads - 1));
-  lat_threads_ = threads;
   return cuda_check("codec_create");
 }
 
@@ -1027,7 +995,7 @@ int Codec::encode(int nf, const int32_t* const* xyz, const int64_t* n, const int
   if (nf < 1 || nf > F_ || !xyz || !n || !Ls || !out || !caps || !lens)
     return fail(LPC_INVALID_ARG, "encode: bad arguments");
   const double t0 = now_us();
-  SpinScope spin(pool_, nf > 1 ? pool_->size() - 1 : lat_threads_ - 1);
+  SpinScope spin(pool_, pool_->size() - 1);
   stats = Stats{};
   // frames with points go to the device batch, empty frames get a flag stream
   std::vector<int> dev;  // device frame index -> caller index
@@ -1117,7 +1085,7 @@ int Codec::encode(int nf, const int32_t* const* xyz, const int64_t* n, const int
     for (int f = 0; f < nd; f++) {
       Frame& F = fr_[f];
       F.sub_base = tasks_.size();
-      const size_t coarse_bound = coded_bound((size_t)F.b * (size_t)F.cnt[6]) + 8 * F.b;
+      const size_t coarse_bound = (size_t)F.b * coarse_level_bound(F.cnt[6]);
       tasks_.push_back(SubTask{f, -1, 0, 0, ao, 0});  // whole coarse region of the frame
       ao += coarse_bound;
       for (int d = 1; d < F.b; d++) tasks_.push_back(SubTask{f, -1, 0, 0, 0, 0});
@@ -1191,11 +1159,19 @@ int Codec::encode(int nf, const int32_t* const* xyz, const int64_t* n, const int
         SubTask& T = tasks_[F.sub_base + d];
         T.arena = ao;
         T.count = cnt;
-        ao += coded_bound((size_t)cnt);
+        ao += coarse_level_bound(cnt);
         stats.N[d] = f == 0 ? cnt : stats.N[d];
         auto task = [this, &T, codes, cnt] {
-          T.len = encode_adaptive_codes(codes, (size_t)cnt, h_arena_ + T.arena,
-                                        coded_bound((size_t)cnt));
+          T.parts.clear();
+          size_t used = 0;
+          for (int64_t s0 = 0; s0 < cnt; s0 += kCoarseChunk) {
+            const int64_t m = std::min(kCoarseChunk, cnt - s0);
+            const size_t l = encode_adaptive_codes(codes + s0, (size_t)m,
+                                                   h_arena_ + T.arena + used, coded_bound((size_t)m));
+            T.parts.push_back((uint32_t)l);
+            used += l;
+          }
+          T.len = used;
         };
         if (f == 0 && d == F.b - 1) mine = task;
         else pool_->submit(0, task);
@@ -1246,21 +1222,29 @@ int Codec::encode(int nf, const int32_t* const* xyz, const int64_t* n, const int
     const Frame* F = empty ? nullptr : &fr_[f];
     const int L = Ls[i];
     uint8_t head[kHdr];
-    const uint8_t hdr[10] = {'L', 'P', 'C', '1', 1, (uint8_t)L, (uint8_t)(L - cfg_.b_off),
+    const uint8_t hdr[10] = {'L', 'P', 'C', '1', 2, (uint8_t)L, (uint8_t)(L - cfg_.b_off),
                              (uint8_t)(L - cfg_.t_off), (uint8_t)M_.C, (uint8_t)(empty ? 1 : 0)};
     memcpy(head, hdr, 10);
     for (int k = 0; k < 8; k++) head[10 + k] = (uint8_t)(M_.hash >> (8 * k));
     std::vector<uint8_t> table;
     put_varint(table, (uint64_t)cfg_.chunk);
-    size_t b0 = 0, b1 = 0;
+    put_varint(table, (uint64_t)kCoarseChunk);
+    size_t b0 = 0, b1 = 0, nsub = 0;
     if (!empty) {
       b0 = F->sub_base;
       b1 = f + 1 < nd ? fr_[f + 1].sub_base : tasks_.size();
+      for (int d = 1; d < F->b; d++) put_varint(table, (uint64_t)tasks_[b0 + d].count);
+      for (size_t k = b0; k < b1; k++)
+        nsub += k < b0 + (size_t)F->b ? tasks_[k].parts.size() : 1;
     }
-    put_varint(table, b1 - b0);
+    put_varint(table, nsub);
     size_t body = 0;
     for (size_t k = b0; k < b1; k++) {
-      put_varint(table, tasks_[k].len);
+      if (k < b0 + (size_t)F->b) {
+        for (uint32_t l : tasks_[k].parts) put_varint(table, l);
+      } else {
+        put_varint(table, tasks_[k].len);
+      }
       body += tasks_[k].len;
     }
     const size_t total_len = kHdr + table.size() + body;
@@ -1319,7 +1303,7 @@ int Codec::decode(int nf, const uint8_t* const* in, const size_t* lens, int32_t*
   if (nf < 1 || nf > F_ || !in || !lens || !out || !caps || !n_out)
     return fail(LPC_INVALID_ARG, "decode: bad arguments");
   const double t0 = now_us();
-  SpinScope spin(pool_, nf > 1 ? pool_->size() - 1 : lat_threads_ - 1);
+  SpinScope spin(pool_, pool_->size() - 1);
   stats = Stats{};
   std::vector<int> dev;
   std::vector<Frame> all(nf);
@@ -1328,8 +1312,8 @@ int Codec::decode(int nf, const uint8_t* const* in, const size_t* lens, int32_t*
     Frame& F = all[i];
     const uint8_t* p = in[i];
     const size_t len = lens[i];
-    if (!p || len < (size_t)kHdr || memcmp(p, "LPC1", 4) != 0 || p[4] != 1)
-      return fail(LPC_CORRUPT_STREAM, "decode: not an LPC1 stream");
+    if (!p || len < (size_t)kHdr || memcmp(p, "LPC1", 4) != 0 || p[4] != 2)
+      return fail(LPC_CORRUPT_STREAM, "decode: not an LPC1 version 2 stream");
     const int L = p[5], b = p[6], t = p[7], C = p[8], flags = p[9];
     uint64_t hash = 0;
     for (int k = 0; k < 8; k++) hash |= (uint64_t)p[10 + k] << (8 * k);
@@ -1341,9 +1325,23 @@ int Codec::decode(int nf, const uint8_t* const* in, const size_t* lens, int32_t*
     if (L > std::min(cfg_.L, kMaxL))
       return fail(LPC_INVALID_ARG, "decode: stream depth exceeds the codec's L");
     size_t pos = kHdr;
-    uint64_t chunk, nsub;
-    if (!get_varint(p, len, pos, chunk) || !get_varint(p, len, pos, nsub) || chunk < 1 ||
-        chunk > (uint64_t)ring_slots_ || nsub > len)
+    uint64_t chunk, kc, nsub;
+    if (!get_varint(p, len, pos, chunk) || !get_varint(p, len, pos, kc) || chunk < 1 ||
+        chunk > (uint64_t)ring_slots_ || kc < 1 || kc > ((uint64_t)1 << 30))
+      return fail(LPC_CORRUPT_STREAM, "decode: bad stream table");
+    F.kc = (int64_t)kc;
+    F.cN[0] = 1;
+    F.nco = 1;
+    for (int d = 1; d < b && !(flags & 1); d++) {
+      uint64_t v;
+      if (!get_varint(p, len, pos, v) || v < 1 || v > 8 * (uint64_t)F.cN[d - 1])
+        return fail(LPC_CORRUPT_STREAM, "decode: bad coarse level size");
+      if (v > (uint64_t)cfg_.max_points)
+        return fail(LPC_CAPACITY, "decode: frame exceeds max_points");
+      F.cN[d] = (int64_t)v;
+      F.nco += (size_t)((v + kc - 1) / kc);
+    }
+    if (!get_varint(p, len, pos, nsub) || nsub > len)
       return fail(LPC_CORRUPT_STREAM, "decode: bad stream table");
     if (flags & 1) {
       if (nsub != 0) return fail(LPC_CORRUPT_STREAM, "decode: empty frame with substreams");
@@ -1365,7 +1363,7 @@ int Codec::decode(int nf, const uint8_t* const* in, const size_t* lens, int32_t*
       F.soff[k] = pos;
       pos += F.slen[k];
     }
-    if (nsub < (uint64_t)b) return fail(LPC_CORRUPT_STREAM, "decode: missing substream");
+    if (nsub < F.nco) return fail(LPC_CORRUPT_STREAM, "decode: missing substream");
     dev.push_back(i);
   }
   // Decodes the frames dev (caller indices) as one batch.  coarse_ready: their
@@ -1405,49 +1403,43 @@ int Codec::decode(int nf, const uint8_t* const* in, const size_t* lens, int32_t*
     std::atomic<int> cstat{0};
     if (!coarse_ready) {
     {
-      // one task per frame, levels in order (N_{d+1} = sum of popcounts of Y_d);
-      // frame 0 on this thread: the thread that was just busy runs it fastest
-      const int64_t maxp = cfg_.max_points;
-      auto coarse = [&](int f) { coarse_frame(fr_[f], maxp, cstat); };
-      int tasks = 0;
-      for (int f = 0; f < nd; f++) tasks += fr_[f].b;
-      const int lat = nd > 1 ? pool_->size() : lat_threads_;
-      if (tasks <= lat && tasks <= kMaxCoarseTasks) {
-        // few frames: every level its own task, pipelined within a frame
-        std::vector<CoarsePipe> pipes(nd);
-        for (int f = 0; f < nd; f++) fr_[f].coarse.assign(fr_[f].b, {});
-        for (int f = 0; f < nd; f++)
+      int64_t jobs = 0;
+      for (int f = 0; f < nd; f++) jobs += (int64_t)fr_[f].nco;
+      if (nd == 1 || jobs <= kMaxCoarseTasks) {
+        // few frames: every chunk of every coarse level its own task (the
+        // header gave every level's size), the largest levels first; the
+        // first on this thread
+        struct Job {
+          int f, d;
+          int64_t k;
+          size_t sub;
+        };
+        std::vector<Job> js;
+        for (int f = 0; f < nd; f++) {
+          coarse_alloc(fr_[f]);
+          size_t sub = 0;
           for (int d = 0; d < fr_[f].b; d++)
-            if (f || d) pool_->submit(0, [&, f, d] { coarse_level(fr_[f], d, pipes[f], maxp, cstat); });
-        coarse_level(fr_[0], 0, pipes[0], maxp, cstat);
+            for (int64_t k = 0; k * fr_[f].kc < fr_[f].cN[d]; k++) js.push_back({f, d, k, sub++});
+        }
+        std::stable_sort(js.begin(), js.end(), [](const Job& x, const Job& y) { return x.d > y.d; });
+        auto run = [&](const Job& J) {
+          if (!coarse_chunk(fr_[J.f], J.d, J.k, J.sub)) cstat = LPC_CORRUPT_STREAM;
+        };
+        for (size_t i = 1; i < js.size(); i++) pool_->submit(0, [&, i] { run(js[i]); });
+        if (!js.empty()) run(js[0]);
         pool_->wait(0);
-      } else if (nd == 1 && lat > 1) {
-        // one frame, fewer threads than levels: the leading levels (the
-        // smallest) in order on this thread, every deeper level its own
-        // task, still pipelined (a task only waits on the level above it,
-        // which was submitted or started before it)
-        Frame& F = fr_[0];
-        const int nt = std::min(F.b, lat);  // tasks, this thread included
-        const int g = F.b - nt + 1;  // levels 0..g-1 on this thread
-        CoarsePipe pipe;
-        F.coarse.assign(F.b, {});
-        for (int d = g; d < F.b; d++)
-          pool_->submit(0, [&, d] { coarse_level(F, d, pipe, maxp, cstat); });
-        for (int d = 0; d < g; d++) coarse_level(F, d, pipe, maxp, cstat);
-        pool_->wait(0);
+        for (int f = 0; f < nd && !cstat; f++)
+          if (!coarse_consistent(fr_[f])) cstat = LPC_CORRUPT_STREAM;
       } else {
         // many frames: one task per frame, the largest coarse streams first
         // (longest-processing-time order balances the threads), the largest on
         // this thread
         std::vector<std::pair<uint64_t, int>> order(nd);
-        for (int f = 0; f < nd; f++) {
-          uint64_t bytes = 0;
-          for (int d = 0; d < fr_[f].b; d++) bytes += fr_[f].slen[d];
-          order[f] = {bytes, f};
-        }
+        for (int f = 0; f < nd; f++) order[f] = {fr_[f].coarse_bytes(), f};
         std::sort(order.begin(), order.end(), [](const auto& a, const auto& b) {
           return a.first != b.first ? a.first > b.first : a.second < b.second;
         });
+        auto coarse = [&](int f) { coarse_frame(fr_[f], cstat); };
         for (int k = 1; k < nd; k++) pool_->submit(0, [&, f = order[k].second] { coarse(f); });
         coarse(order[0].second);
         pool_->wait(0);
@@ -1485,7 +1477,7 @@ int Codec::decode(int nf, const uint8_t* const* in, const size_t* lens, int32_t*
         F.off[h] = nh;
         F.cnt[h] = c;
         nh += c;
-        if (j == 0) sidx[f][0] = F.b;
+        if (j == 0) sidx[f][0] = F.nco;
       }
       if (nh > P_) return fail(LPC_CAPACITY, "decode: batch exceeds the codec's capacity");
       N_[h] = nh;
@@ -1601,7 +1593,7 @@ int Codec::decode(int nf, const uint8_t* const* in, const size_t* lens, int32_t*
   uint64_t all_bytes = 0;
   for (size_t k = 0; k < dev.size(); k++) {
     uint64_t bytes = 0;
-    for (int d = 0; d < all[dev[k]].b; d++) bytes += all[dev[k]].slen[d];
+    bytes = all[dev[k]].coarse_bytes();
     by[k] = {bytes, dev[k]};
     all_bytes += bytes;
   }
@@ -1619,19 +1611,16 @@ int Codec::decode(int nf, const uint8_t* const* in, const size_t* lens, int32_t*
   std::sort(ga.begin(), ga.end());
   std::sort(gb.begin(), gb.end());
   if (gb.empty()) return run_group(ga, false, nullptr);
-  const int64_t maxp = cfg_.max_points;
   auto start_b = [&] {
     std::vector<std::pair<uint64_t, int>> order;
     for (int i : gb) {
-      uint64_t bytes = 0;
-      for (int d = 0; d < all[i].b; d++) bytes += all[i].slen[d];
-      order.push_back({bytes, i});
+      order.push_back({all[i].coarse_bytes(), i});
     }
     std::sort(order.begin(), order.end(), [](const auto& x, const auto& y) {
       return x.first != y.first ? x.first > y.first : x.second < y.second;
     });
-    for (auto& e : order) pool_->submit(3, [this, &all, &async_stat, maxp, i = e.second] {
-      coarse_frame(all[i], maxp, async_stat);
+    for (auto& e : order) pool_->submit(3, [&all, &async_stat, i = e.second] {
+      coarse_frame(all[i], async_stat);
     });
   };
   const int sa = run_group(ga, false, start_b);
@@ -1821,7 +1810,7 @@ int Codec::decode_net_async(int nd, int64_t* n_out, const std::vector<int>& dev,
   int64_t k = 0;
   for (int f = 0; f < nd; f++) {
     const Frame& F = fr_[f];
-    hsf[f] = DevSubFrame{k, (int64_t)F.slen.size(), F.chunk, in_base_[f], (int64_t)F.b};
+    hsf[f] = DevSubFrame{k, (int64_t)F.slen.size(), F.chunk, in_base_[f], (int64_t)F.nco};
     for (size_t s = 0; s < F.slen.size(); s++, k++) {
       hsub[2 * k] = (int64_t)F.soff[s];
       hsub[2 * k + 1] = (int64_t)F.slen[s];

@@ -118,8 +118,16 @@ struct Frame {
   const uint8_t* in = nullptr;
   size_t len = 0;
   int64_t chunk = 0;
+  int64_t kc = 0;                   // coarse chunk: nodes per coarse substream
+  int64_t cN[kMaxDepth + 1] = {};   // the coarse levels' sizes N_0 = 1, N_1 .. N_{b-1}
+  size_t nco = 0;                   // coarse substreams (the network's follow them)
   std::vector<uint64_t> slen;
   std::vector<size_t> soff;
+  uint64_t coarse_bytes() const {
+    uint64_t s = 0;
+    for (size_t k = 0; k < nco && k < slen.size(); k++) s += slen[k];
+    return s;
+  }
   size_t sub_base = 0;           // first substream task of this frame
   int status = 0;
 };
@@ -249,7 +257,6 @@ class Codec {
   cudaStream_t st_ = nullptr;
   Model M_;
   Pool* pool_ = nullptr;
-  int lat_threads_ = 1;  // threads (this one included) a single frame's host work may use
   // per-batch state
   int nf_ = 0;
   std::vector<Frame> fr_;
@@ -305,6 +312,7 @@ class Codec {
     int64_t start, count;
     size_t arena, len;  // offset in the host arena, or in the device-coded bytes if rc >= 0
     int64_t rc = -1;    // index of the device-coded chunk
+    std::vector<uint32_t> parts;  // a coarse level: its substreams' lengths, in order
   };
   // growable buffers for the device range coder (replaced only when a call
   // needs more; the stream is synchronised first)
