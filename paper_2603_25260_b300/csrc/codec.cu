@@ -65,18 +65,31 @@ static inline void cpu_relax() {
 void Pool::loop(int idx) {
   std::unique_lock<std::mutex> lk(mu_);
   auto polls = [&] { return idx < spin_.load(std::memory_order_relaxed); };
+  auto queued = [&] { return queued_.load(std::memory_order_relaxed) != 0; };
   for (;;) {
     if (stop_) return;
     if (run_one(lk)) continue;
+    lk.unlock();
     if (polls()) {
-      lk.unlock();
-      for (int k = 1; polls() && queued_.load(std::memory_order_relaxed) == 0; k++) {
+      for (int k = 1; polls() && !queued(); k++) {
         cpu_relax();  // leaves the core's resources to a hyper-thread sibling
         if (k % 64 == 0) std::this_thread::yield();
       }
-      lk.lock();
-      continue;
+    } else {
+      // a call just ended: keep polling a few milliseconds, since the next
+      // call usually follows at once and a woken worker runs its first
+      // milliseconds several times slower
+      const auto until = std::chrono::steady_clock::now() + std::chrono::milliseconds(3);
+      for (int k = 1; !polls() && !queued(); k++) {
+        cpu_relax();
+        if (k % 64 == 0) {
+          std::this_thread::yield();
+          if (std::chrono::steady_clock::now() > until) break;
+        }
+      }
     }
+    lk.lock();
+    if (stop_ || head_ < q_.size() || polls()) continue;
     cv_.wait(lk, [&] { return stop_ || head_ < q_.size() || polls(); });
   }
 }
@@ -1712,7 +1725,7 @@ int Codec::decode_net_device(int nd, int64_t* n_out, const std::vector<int>& dev
   if (graphs) return decode_net_async(nd, n_out, dev, caps);
   const int64_t maxp = cfg_.max_points;
   std::vector<size_t> sidx(nd);
-  for (int f = 0; f < nd; f++) sidx[f] = (size_t)fr_[f].b;
+  for (int f = 0; f < nd; f++) sidx[f] = fr_[f].nco;
   const uint8_t* d_in = static_cast<const uint8_t*>(d_rcbuf_.p);
   for (int j = 0; j <= 5; j++) {  // j = 5: the leaves
     const int h = 5 - j;
