@@ -1,14 +1,17 @@
 // Codec orchestration over a batch of frames: workspace, octree build, the
-// per-level network schedule of Sec. 3 (GRED + XFP), and host range coding of
-// the device-made cumulative tables.  Exported through the C ABI of lpc.h.
+// per-level network schedule of Sec. 3 (GRED + XFP, or an ablation of
+// Sec. 4.4), and the range coding of the network levels (on the device, or
+// on host threads from the device-made tables).  Exported through the C ABI
+// of lpc.h.
 //
 // Every level array holds all frames of a batch at once, frame-major then
 // Morton order, indexed by height above the leaves: height h is depth L_f - h
 // of frame f.  The network-coded levels b..L-1 of every frame are heights
 // 5..1, so relative level j = d - b is height 5 - j for every frame, whatever
 // its depth L_f: one launch sequence per relative level codes every frame.
-// The coarse levels (depth < b) are small and are built, coded and decoded on
-// the host, one frame per host task.
+// The coarse levels (depth < b) are built on the device; their codes are
+// range coded on host threads with an adaptive model, in chunks of 4096
+// nodes that each code and decode on their own.
 #include "codec.h"
 
 #include <string.h>
