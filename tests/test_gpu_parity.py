@@ -526,3 +526,25 @@ def test_few_host_threads(lpc, blob, threads):
     assert cod.encode(_cuda(xyz)) == data
     for _ in range(2):
         assert np.array_equal(cod.decode(data).cpu().numpy(), want)
+
+
+def test_bad_coarse_size_is_corrupt(lpc, blob):
+    """A coarse level size in the header that the codes above it do not
+    expand to, or zero: the stream is reported corrupt (and a good stream
+    still decodes after it)."""
+    xyz = synth.random_cloud(3000, 12, 72)
+    data = O.encode(blob, xyz, 12)
+    cod = _codec(lpc, blob, 12, 3000)
+    pos = 18
+    for _ in range(2):  # chunk, coarse chunk
+        while data[pos] >= 0x80:
+            pos += 1
+        pos += 1
+    assert data[pos] < 0x80
+    for v in (data[pos] + 1, 0):
+        bad = bytearray(data)
+        bad[pos] = v
+        with pytest.raises(lpc.LpcError) as e:
+            cod.decode(bytes(bad))
+        assert e.value.status == lpc.CORRUPT_STREAM
+    assert np.array_equal(cod.decode(data).cpu().numpy(), O.decode(blob, data, 3000))

@@ -476,3 +476,57 @@ def test_fnv1a64_published_vectors():
     assert O.fnv1a64(b"") == 0xcbf29ce484222325
     assert O.fnv1a64(b"a") == 0xaf63dc4c8601ec8c
     assert O.fnv1a64(b"foobar") == 0x85944171f73967e8
+
+
+def _varint(data, pos):
+    v = s = 0
+    while True:
+        b = data[pos]
+        pos += 1
+        v |= (b & 0x7F) << s
+        s += 7
+        if b < 0x80:
+            return v, pos
+
+
+def test_stream_header_coarse_sizes():
+    """Stream version 2: after the chunk lengths the header lists the coarse
+    levels' sizes N_1 .. N_{b-1} (those of the octree of the frame), and the
+    substream table holds ceil(N_d / 4096) substreams per coarse level before
+    the network levels' chunks."""
+    blob = synth.make_blob()
+    xyz = synth.random_cloud(60000, 17, 71)
+    L, chunk = 17, 1000
+    data = O.encode(blob, xyz, L, chunk)
+    assert data[:4] == b"LPC1" and data[4] == 2
+    keys, codes = O.build_levels(xyz, L)
+    b = L - 5
+    c, pos = _varint(data, 18)
+    kc, pos = _varint(data, pos)
+    assert (c, kc) == (chunk, 4096)
+    sizes = []
+    for _ in range(1, b):
+        v, pos = _varint(data, pos)
+        sizes.append(v)
+    assert sizes == [len(keys[d]) for d in range(1, b)]
+    nsub, pos = _varint(data, pos)
+    want = sum(-(-len(keys[d]) // kc) for d in range(b)) + \
+        sum(-(-len(keys[d]) // chunk) for d in range(b, L))
+    assert nsub == want
+    assert max(len(keys[d]) for d in range(b)) > kc  # a level in several chunks
+
+
+def test_stream_header_bad_coarse_size_is_corrupt():
+    blob = synth.make_blob()
+    xyz = synth.random_cloud(3000, 12, 72)
+    data = bytearray(O.encode(blob, xyz, 12))
+    pos = 18
+    _, pos = _varint(data, pos)
+    _, pos = _varint(data, pos)
+    assert data[pos] < 0x80  # N_1 is a one-byte varint
+    for v in (data[pos] + 1, 0):
+        bad = bytearray(data)
+        bad[pos] = v
+        with pytest.raises(O.OracleError) as e:
+            O.decode(blob, bytes(bad), 3000)
+        assert e.value.status == -4
