@@ -129,7 +129,6 @@ void Pool::wait(int group) {
   }
 }
 
-// ------------------------------------------------------------ bitstream --
 // ------------------------------------------------- coarse-level decoding --
 // Every coarse level is coded in chunks of kc nodes, each chunk its own
 // substream with a fresh adaptive model, and the stream's header carries the
@@ -179,6 +178,7 @@ void coarse_frame(Frame& F, std::atomic<int>& status) {
 
 }  // namespace
 
+// ------------------------------------------------------------ bitstream --
 // "LPC1", u8 version (2), u8 L, u8 b, u8 t, u8 C, u8 flags (bit0: empty
 // frame), u64 blob hash (little endian), varint chunk, varint coarse chunk,
 // varint N_1 .. N_{b-1} (not for an empty frame), varint n_sub, n_sub varint
