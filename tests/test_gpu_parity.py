@@ -548,3 +548,16 @@ def test_bad_coarse_size_is_corrupt(lpc, blob):
             cod.decode(bytes(bad))
         assert e.value.status == lpc.CORRUPT_STREAM
     assert np.array_equal(cod.decode(data).cpu().numpy(), O.decode(blob, data, 3000))
+
+
+@pytest.mark.parametrize("host_coding", [False, True], ids=["device_rc", "host_rc"])
+def test_repeated_encode_graph_path(lpc, blob, host_coding):
+    """From the second encode on, the five levels run as one captured graph
+    with levels 3 and 4 on their own streams and scratch, queued behind the
+    octree: the same stream as the oracle on every call."""
+    xyz = synth.random_cloud(30000, 16, 81)
+    want = O.encode(blob, xyz, 16)
+    cod = _codec(lpc, blob, 16, xyz.shape[0], host_coding=host_coding)
+    x = _cuda(xyz)
+    for _ in range(4):
+        assert cod.encode(x) == want
