@@ -88,6 +88,11 @@ const char* codec_last_error(codec_t* codec);
 
 /* Encode one frame.  d_xyz: device int32 [n][3].  The bitstream goes to the
  * caller's host buffer h_out of `cap` bytes; *out_len receives its length.
+ * Stream (version 2): "LPC1", version, L, b, t, C, flags, the blob's hash,
+ * then varints: network chunk, coarse chunk (4096), the coarse levels' sizes
+ * N_1 .. N_{b-1}, the substream count and lengths; then the substreams: the
+ * coarse levels in coarse chunks (adaptive symbol frequencies, a fresh model
+ * each), the network levels in network chunks (the integer softmax tables). 
  * If cap is too small, returns LPC_CAPACITY with the required length in
  * *out_len.  n = 0 gives an empty-frame stream.
  * Errors: LPC_INVALID_ARG (coordinate outside [0, 2^L)), LPC_CAPACITY
