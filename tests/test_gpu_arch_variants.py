@@ -87,3 +87,21 @@ def test_stream_of_another_architecture_is_refused(lpc):
     with pytest.raises(lpc.LpcError) as e:
         lpc.Codec(b, 11, 3000).decode(data)
     assert e.value.status == lpc.WEIGHTS_MISMATCH
+
+
+def test_batch_two_groups_ablation(lpc):
+    """Ten frames (the decoder's two-group path: host coarse decoding of one
+    group beside the device's network levels of the other) with GRED only
+    and t = L - 3: every stream equals the oracle's, the batch decodes
+    exactly."""
+    blob = synth.make_blob(arch=synth.ARCH_GRED, t_off=3)
+    specs = [(2000 + 700 * i, 9 + i % 8, 90 + i) for i in range(10)]
+    frames = [synth.random_cloud(n, L, s) for n, L, s in specs]
+    Ls = [L for _, L, _ in specs]
+    cod = lpc.Codec(blob, 16, max(f.shape[0] for f in frames), max_frames=len(frames))
+    for _ in range(2):
+        outs = cod.encode_batch([_cuda(f) for f in frames], Ls)
+        assert outs == [O.encode(blob, f, L) for f, L in zip(frames, Ls)]
+        decs = cod.decode_batch(outs, [f.shape[0] for f in frames])
+        for f, L, dcd in zip(frames, Ls, decs):
+            assert np.array_equal(O.leaf_keys(dcd.cpu().numpy(), L), O.leaf_keys(f, L))
