@@ -26,6 +26,7 @@ import gc
 import hashlib
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -143,6 +144,17 @@ class Clocks:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
                 "samples": len(rows)}
+
+
+def cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.startswith("model name"):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or "unknown"
 
 
 def peaks():
@@ -640,7 +652,19 @@ def run_ours(args):
         cpu = {"value": round(n / (te + td) / 1e6, 4), "unit": "Mpoints/s", "cores": cores,
                "kind": "oracle", "sample": f"one full {args.workload} frame ({n} points), "
                                            f"encode {te:.2f} s + decode {td:.2f} s",
-               "bitstream_identical": data == bytes(outbuf[:nbytes])}
+               "bitstream_identical": data == bytes(outbuf[:nbytes]),
+               "cpu_model": cpu_model()}
+        # the same oracle on one core, on the small 16-beam frame
+        small = synth.make_frame(WORKLOADS["tiny16_L12"])
+        O.set_threads(1)
+        t0 = time.perf_counter()
+        sd = O.encode(blob, small, WORKLOADS["tiny16_L12"].L, args.chunk)
+        O.decode(blob, sd, small.shape[0])
+        t1 = time.perf_counter() - t0
+        O.set_threads(cores)
+        cpu["single_core"] = {"value": round(small.shape[0] / t1 / 1e6, 4), "unit": "Mpoints/s",
+                              "sample": f"one tiny16_L12 frame ({small.shape[0]} points), "
+                                        f"encode + decode {t1:.2f} s"}
     line = {
         "metric": METRIC, "value": round(value, 4), "unit": "Mpoints/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
