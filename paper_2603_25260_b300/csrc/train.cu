@@ -134,40 +134,64 @@ k_outer(Pairs pairs, const float* __restrict__ dy, const float* __restrict__ x, 
         float* dW, int bf16) {
   __shared__ float sy[kStage][A];
   __shared__ float sx[kStage][B];
-  constexpr int kPer = A * B / 256;
+  // every thread a register tile of outputs i = ti + 16 a, j = tj + 16 b,
+  // so each staged value it loads feeds several products
+  constexpr int NA = A / 16, NB = B / 16;
   const int s = blockIdx.y;
-  float acc[kPer];
+  const int ti = threadIdx.x >> 4, tj = threadIdx.x & 15;
+  float acc[NA][NB];
 #pragma unroll
-  for (int u = 0; u < kPer; u++) acc[u] = 0.f;
+  for (int u = 0; u < NA; u++)
+#pragma unroll
+    for (int v = 0; v < NB; v++) acc[u][v] = 0.f;
+  // the block's rows that contribute to slice s, as (dy row, x row) pairs
+  // (absent neighbours and children of other slices take no work)
+  __shared__ int64_t pa[kOuterRows], pb[kOuterRows];
+  __shared__ int np;
+  if (threadIdx.x == 0) np = 0;
+  __syncthreads();
   const int64_t r0 = (int64_t)blockIdx.x * kOuterRows;
   const int64_t r1 = std::min<int64_t>(rows, r0 + kOuterRows);
-  for (int64_t base = r0; base < r1; base += kStage) {
+  for (int64_t row = r0 + threadIdx.x; row < r1; row += 256) {
+    int64_t a = -1, b = -1;
+    pairs.pair(s, row, a, b);
+    if (a >= 0) {
+      const int k = atomicAdd(&np, 1);
+      pa[k] = a;
+      pb[k] = b;
+    }
+  }
+  __syncthreads();
+  const int n = np;
+  if (n == 0) return;  // nothing of this slice in the block's rows
+  for (int base = 0; base < n; base += kStage) {
     for (int idx = threadIdx.x; idx < kStage * (A + B); idx += 256) {
       const int r = idx / (A + B), c = idx % (A + B);
-      const int64_t row = base + r;
-      int64_t a = -1, b = -1;
-      if (row < r1) pairs.pair(s, row, a, b);
       float v = 0.f;
-      if (a >= 0) v = c < A ? dy[a * A + c] : x[b * B + (c - A)];
+      if (base + r < n) v = c < A ? dy[pa[base + r] * A + c] : x[pb[base + r] * B + (c - A)];
       if (c < A) sy[r][c] = rnd(v, bf16);
       else sx[r][c - A] = rnd(v, bf16);
     }
     __syncthreads();
+#pragma unroll 4
+    for (int r = 0; r < kStage; r++) {
+      float ya[NA], xb[NB];
 #pragma unroll
-    for (int u = 0; u < kPer; u++) {
-      const int q = threadIdx.x + 256 * u, i = q / B, j = q % B;
-      float t = 0.f;
-#pragma unroll 8
-      for (int r = 0; r < kStage; r++) t += sy[r][i] * sx[r][j];
-      acc[u] += t;
+      for (int u = 0; u < NA; u++) ya[u] = sy[r][ti + 16 * u];
+#pragma unroll
+      for (int v = 0; v < NB; v++) xb[v] = sx[r][tj + 16 * v];
+#pragma unroll
+      for (int u = 0; u < NA; u++)
+#pragma unroll
+        for (int v = 0; v < NB; v++) acc[u][v] += ya[u] * xb[v];
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int u = 0; u < kPer; u++) {
-    const int q = threadIdx.x + 256 * u;
-    atomicAdd(dW + (size_t)s * A * B + q, acc[u]);
-  }
+  for (int u = 0; u < NA; u++)
+#pragma unroll
+    for (int v = 0; v < NB; v++)
+      atomicAdd(dW + (size_t)s * A * B + (size_t)(ti + 16 * u) * B + tj + 16 * v, acc[u][v]);
 }
 
 // db[slice(row)][j] += dy[row][j]; slice_key = nullptr: one slice.
