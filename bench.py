@@ -517,7 +517,7 @@ def run_ours(args):
         with open(export.TRAINED_BLOB, "rb") as f:
             trained = {"blob": os.path.relpath(export.TRAINED_BLOB, ROOT), **blob_leg(f.read())}
 
-    # the ablation architectures (Sec. 4.4) and t = L - 3 on the same
+    # the ablation architectures (Sec. 4.3) and t = L - 3 on the same
     # kernels, seeded weights of each
     architectures = None
     if not args.no_arch:

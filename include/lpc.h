@@ -71,7 +71,7 @@ typedef struct {
  * package's synth module docstring: exp table, then per-layer INT8 weights,
  * INT32 biases, multipliers, shifts, zero points and Q15 PReLU slopes).  Its
  * header names the architecture -- GRED + XFP (Sec. 3.1-3.2), or one of the
- * ablations of Sec. 4.4: GRED without cross-scale propagation, or neither --
+ * ablations of Sec. 4.3: GRED without cross-scale propagation, or neither --
  * and the threshold offset t = L - 4 or L - 3; the same kernels run all of
  * them.  The
  * codec validates it, copies it to the device and keeps its 64-bit FNV-1a

@@ -13,7 +13,7 @@
  *  - base level b = L-5 (levels below are coded with adaptive symbol
  *    frequencies, supplement "Detailed Model Structure"), threshold t = L-4
  *    or L-3 (supplement, "Ablation on the Choice of t"), dense level k = t;
- *  - ablations (Sec. 4.4): without XFP a level d > b takes no feature from
+ *  - ablations (Sec. 4.3): without XFP a level d > b takes no feature from
  *    the level above, only G^k = Downsampling(X^{d-1}) with Eq. 5-6 as
  *    printed, k = t below t (GRED) and k = d-1 otherwise (and for every
  *    level in the baseline); level b is the same in all architectures;
@@ -556,7 +556,7 @@ typedef struct {
 } rec;
 
 #define MAXREC 64
-/* Architectures (Sec. 4.4, Table 4): the paper's model and its two ablations */
+/* Architectures (Sec. 4.3, Table 4): the paper's model and its two ablations */
 enum { ARCH_XFP = 0, ARCH_GRED = 1, ARCH_BASE = 2 };
 
 typedef struct {

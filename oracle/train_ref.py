@@ -13,7 +13,7 @@ Network (Sec. 3.1-3.2, Eq. 4-11, with the readings of the integer oracle):
   j = 1 + m: G = E'_j[Y_{d-1}], m-1 x prelu(Down(G)) to V_t; H = ResBlock([F_t | G]);
          H = prelu(Up_{j,k}([H | E_{j,k}[Y_k]])), k = t..d-1;  logits_d = Pred_j(H)
 with t = L - 4 (or L - 3: levels b+1..t then repeat the j = 1 form).  The
-ablations of Sec. 4.4 drop the propagated features: every level d > b takes
+ablations of Sec. 4.3 drop the propagated features: every level d > b takes
 G = E'_j[Y_{d-1}] brought down to V_k, H = ResBlock(G), m = d - k plain
 up-samplings H = prelu(Up_{j,k}(H)); k = t for GRED's levels below t, k = d - 1
 for the others and for the baseline.
@@ -200,7 +200,7 @@ init_params = synth.twin_params
 ACT_SCALE = 1.0 / 32.0  # fixed activation scale of the fake quantisers
 
 
-ARCH_XFP, ARCH_GRED, ARCH_BASE = 0, 1, 2  # GRED + XFP; GRED only; baseline (Sec. 4.4)
+ARCH_XFP, ARCH_GRED, ARCH_BASE = 0, 1, 2  # GRED + XFP; GRED only; baseline (Sec. 4.3)
 
 
 def level_bits(P: dict, fr: Frame, qat: bool = False, bf16: bool = False, arch: int = ARCH_XFP,

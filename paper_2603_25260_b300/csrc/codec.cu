@@ -1,6 +1,6 @@
 // Codec orchestration over a batch of frames: workspace, octree build, the
 // per-level network schedule of Sec. 3 (GRED + XFP, or an ablation of
-// Sec. 4.4), and the range coding of the network levels (on the device, or
+// Sec. 4.3), and the range coding of the network levels (on the device, or
 // on host threads from the device-made tables).  Exported through the C ABI
 // of lpc.h.
 //

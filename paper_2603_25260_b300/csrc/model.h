@@ -13,7 +13,7 @@ namespace lpc {
 
 constexpr int kRelLevels = 5;  // network-coded levels b .. L-1 (b = L-5)
 
-// Network architectures: the paper's model and its two ablations (Sec. 4.4).
+// Network architectures: the paper's model and its two ablations (Sec. 4.3).
 enum Arch { kArchXfp = 0, kArchGred = 1, kArchBase = 2 };
 
 struct BlobRecord {

@@ -23,7 +23,7 @@ blob record the integer codec reads:
 twin for N AdamW steps on the seeded 8-frame training batch of the 64-beam
 generator (rate loss in bits per point, fake quantisers on) and writes the
 blob; ``--arch gred|baseline`` and ``--t-off 3`` train and export the
-ablation architectures of Sec. 4.4 instead.
+ablation architectures of Sec. 4.3 instead.
 """
 
 from __future__ import annotations

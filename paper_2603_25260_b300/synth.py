@@ -244,7 +244,7 @@ class Record:
     slope: np.ndarray | None = None
 
 
-# Architectures: the paper's model and the two ablations of Sec. 4.4 (Table 4),
+# Architectures: the paper's model and the two ablations of Sec. 4.3 (Table 4),
 # all on the same five network-coded levels b = L-5 .. L-1 and the same ops.
 ARCH_XFP = 0   # GRED + XFP (Sec. 3.1-3.2, Eq. 4-11)
 ARCH_GRED = 1  # GRED only: no feature propagated between levels

@@ -363,7 +363,7 @@ class QATModel(torch.nn.Module):
     def __init__(self, params: dict, qat: bool = False, bf16: bool = False,
                  recompute: bool = False, arch: int = 0, t_off: int = 4):
         """arch, t_off: the architecture (0 GRED + XFP, 1 GRED only,
-        2 baseline; Sec. 4.4) and t = L - t_off, as in the weight blob."""
+        2 baseline; Sec. 4.3) and t = L - t_off, as in the weight blob."""
         super().__init__()
         self.recompute = recompute
         self.arch, self.t_off = arch, t_off

@@ -1,4 +1,4 @@
-"""Architecture switches of the ablations (Sec. 4.4, Table 4; supplement,
+"""Architecture switches of the ablations (Sec. 4.3, Table 4; supplement,
 choice of t): GRED + XFP, GRED only and the baseline, each with t = L - 4 or
 L - 3, on the CPU oracle.
 

@@ -1,4 +1,4 @@
-"""GPU parity of the ablation architectures (Sec. 4.4; supplement, choice of
+"""GPU parity of the ablation architectures (Sec. 4.3; supplement, choice of
 t): GRED + XFP, GRED only and the baseline, each with t = L - 4 or L - 3, run
 by the same kernels.  Every stream equals the CPU oracle's byte for byte,
 per frame, in batches of mixed depths, with device and host range coding,

@@ -346,7 +346,7 @@ def test_batch_frame_equals_sum_of_frames():
 @pytest.mark.parametrize("arch,t_off", [(1, 3), (2, 4), (0, 3), (1, 4)],
                          ids=["gred_t3", "baseline", "gred_xfp_t3", "gred_t4"])
 def test_model_gradients_arch_variants(frames, arch, t_off):
-    """The ablation architectures (Sec. 4.4) and t = L - 3 in the twin: rate
+    """The ablation architectures (Sec. 4.3) and t = L - 3 in the twin: rate
     and every parameter's gradient against the FP64 reference (fp32, 1e-4),
     kernel maps below V_t built from the parent level's map."""
     from paper_2603_25260_b300 import train as G
