@@ -58,8 +58,12 @@ int lpc_kernel_map_child(const uint64_t* d_ckeys, const uint32_t* d_cpar, int64_
  * a component that does not own the CUDA allocator).  The voxel hash table is
  * a file-scope device array of 2^19 slots that every GPU loading the library
  * holds until exit; N above 262,144 nodes returns LPC_CAPACITY.  The first
- * call on each device looks up the array's device address (make that first
- * call before any stream capture).  All calls share the array, which keeps
+ * call on each device loads the array's module (CUDA loads modules lazily by
+ * default, so that is when the 8 MiB is committed, and it may synchronise
+ * the device) and looks up the array's device address: make that first call
+ * at start-up, before any stream capture; later calls allocate nothing.  The
+ * address is cached per device and goes stale after cudaDeviceReset.  All
+ * calls share the array, which keeps
  * the previous call's contents (each call clears what it uses): calls whose
  * GPU work overlaps race with each other and must be serialised by the
  * caller.  Synchronises the stream before returning. */

@@ -10,13 +10,20 @@
 // call like lpc_kernel_map does.
 //
 // The array is a fixed 2^19-slot table (8 MiB of 16-byte key and row slots,
-// plus two control words), enough for 262,144 nodes at a load factor of at most 1/2.
-// Every GPU that loads this library holds that memory until the process
-// exits.  All calls share the one table: concurrent calls whose work
-// overlaps on a GPU (different streams, or different host threads) race and
-// must be serialised by the caller.  The table keeps the previous call's
-// contents; each call clears the slots it uses and its control words before
-// inserting.
+// plus two control words), enough for 262,144 nodes at a load factor of at
+// most 1/2.  This file is its own device module, and CUDA loads modules
+// lazily by default: the array's 8 MiB is committed on a device when the
+// first call there looks up its address, and that load may synchronise the
+// device.  A caller that must not allocate later makes one call per device
+// at start-up; from then on the device holds the array until the process
+// exits, and no call allocates.  The address is cached per device index; a
+// cudaDeviceReset (or anything else that replaces the device's primary
+// context) makes the cached address stale, so this entry point must not be
+// used across such a reset.  All calls share the one table: concurrent calls
+// whose work overlaps on a GPU (different streams, or different host
+// threads) race and must be serialised by the caller.  The table keeps the
+// previous call's contents; each call clears the slots it uses and its
+// control words before inserting.
 #include <mutex>
 
 #include "../../include/lpc_ops.h"
