@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="kitti64_L16", choices=sorted(WORKLOADS))
-    ap.add_argument("--chunk", type=int, default=1024)
+    ap.add_argument("--chunk", type=int, default=256)
     ap.add_argument("--batch-frames", type=int, default=64)
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -193,6 +193,12 @@ def family_rooflines(fams: dict, steps: float, hbm: float, bf16: float | None) -
         gbs = v["bytes"] / v["launches"] / t / 1e9
         e = {"ms_per_launch": round(1e3 * t, 4), "launches_per_step": v["launches"] / steps,
              "hbm_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4)}
+        sb = v.get("staged_bytes", v["bytes"])
+        if abs(sb - v["bytes"]) > 1e-6 * max(sb, 1.0):
+            # what this implementation's layouts actually move (bf16 rows, maps)
+            sgbs = sb / v["launches"] / t / 1e9
+            e["staged_gbs"] = round(sgbs, 1)
+            e["staged_frac"] = round(sgbs / hbm, 4)
         if v["ops"] > 0:
             tops = v["ops"] / v["launches"] / t / 1e12
             e["tops"] = round(tops, 3)
@@ -226,6 +232,88 @@ def traffic_for(family: str, launches_per_step: float):
     if h != e.get("source_sha256"):
         return None
     return e.get("dram_bytes_per_launch")
+
+
+# ------------------------------------------------------------ CPU oracle --
+
+# The CPU plan's C4 subset: two frames of the mixed batch (a 128-beam L = 18
+# frame and a 64-beam L = 14 frame), small enough for one core.
+C4_SUBSET = (16, 32)
+
+
+def oracle_run(O, blob, frames, Ls, chunk):
+    """Encode then decode every frame with the oracle at its current thread
+    count: seconds for encode and decode, the network + softmax share and
+    the range-coding share of each, the streams."""
+    te = td = net = code = 0.0
+    streams = []
+    for f, L in zip(frames, Ls):
+        t0 = time.perf_counter()
+        data = O.encode(blob, f, L, chunk)
+        te += time.perf_counter() - t0
+        a, b = O.last_phase_times()
+        net, code = net + a, code + b
+        t0 = time.perf_counter()
+        O.decode(blob, data, max(f.shape[0], 1))
+        td += time.perf_counter() - t0
+        a, b = O.last_phase_times()
+        net, code = net + a, code + b
+        streams.append(data)
+    return te, td, net, code, streams
+
+
+def cpu_baseline_leg(blob, frame, spec, n, chunk, gpu_stream):
+    """The oracle timed on this host, as the CPU baseline: on all cores
+    (OpenMP over independent output rows) and on one core, on the 16-, 64-
+    and 128-beam frames in full and on a stated subset of the 64-frame batch,
+    encode and decode Mpoints/s with the time split into the network with
+    its softmax tables and the range coding (the rest is octree work).
+    Headline value: the bench workload's frame on all cores."""
+    import oracle as O
+    cores = os.cpu_count() or 1
+    cases = [("tiny16_L12", [synth.make_frame(synth.C1)], [synth.C1.L])]
+    cases.append((spec_name(spec), [frame], [spec.L]))
+    for wl in ("kitti64_L16", "dense128_L18"):
+        if WORKLOADS[wl] is not spec:
+            cases.append((wl, [synth.make_frame(WORKLOADS[wl])], [WORKLOADS[wl].L]))
+    bspecs = synth.batch_specs(64)
+    sub = [bspecs[i] for i in C4_SUBSET]
+    cases.append((f"batch64_frames_{'_'.join(map(str, C4_SUBSET))}", synth.make_frames(sub),
+                  [s.L for s in sub]))
+    plan = {}
+    identical = None
+    for name, frames, Ls in cases:
+        pts = sum(f.shape[0] for f in frames)
+        e = {"frames": len(frames), "points": int(pts), "L": Ls}
+        for label, th in (("all_cores", cores), ("single_core", 1)):
+            O.set_threads(th)
+            te, td, net, code, streams = oracle_run(O, blob, frames, Ls, chunk)
+            e[label] = {"threads": th, "value": round(pts / (te + td) / 1e6, 5),
+                        "encode_mpts": round(pts / te / 1e6, 5),
+                        "decode_mpts": round(pts / td / 1e6, 5),
+                        "encode_s": round(te, 3), "decode_s": round(td, 3),
+                        "network_cdf_s": round(net, 3), "range_coding_s": round(code, 3),
+                        "octree_other_s": round(te + td - net - code, 3)}
+            if name == spec_name(spec) and label == "all_cores":
+                identical = streams[0] == gpu_stream
+                e["bits_per_point"] = round(8 * len(streams[0]) / pts, 4)
+        plan[name] = e
+    O.set_threads(cores)
+    head = plan[spec_name(spec)]["all_cores"]
+    return {"value": head["value"], "unit": "Mpoints/s", "cores": cores, "kind": "oracle",
+            "sample": f"one full {spec_name(spec)} frame ({n} points) on all {cores} cores, "
+                      f"encode {head['encode_s']:.2f} s + decode {head['decode_s']:.2f} s; "
+                      "`plan` adds one core and the other workloads",
+            "bitstream_identical": identical, "cpu_model": cpu_model(), "plan": plan,
+            "c4_subset": f"frames {list(C4_SUBSET)} of the 64-frame batch (seeds "
+                         f"{[2000 + i for i in C4_SUBSET]})"}
+
+
+def spec_name(spec) -> str:
+    for k, v in WORKLOADS.items():
+        if v is spec:
+            return k
+    return "frame"
 
 
 # ------------------------------------------------------------- reference --
@@ -280,7 +368,7 @@ def train_leg(args, flush, stream):
     from paper_2603_25260_b300 import train as TR
 
     specs = synth.training_specs()
-    xyz = [synth.make_frame(s) for s in specs]
+    xyz = synth.make_frames(specs)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     frames = [TR.Frame(torch.from_numpy(f).cuda(), s.L) for f, s in zip(xyz, specs)]
@@ -303,12 +391,31 @@ def train_leg(args, flush, stream):
         ms.append(a.elapsed_time(b))
     npts = sum(f.n for f in frames)
     step = statistics.median(ms)
+    # one profiled step (untimed): device time per op of the twin, and the
+    # dominant op's algorithmic flops against the fp32 FMA peak of the CUDA
+    # cores (the twin's kernels multiply on them: 148 SMs x 128 lanes x 2 x
+    # the maximum SM clock)
+    TR.profile(True)
+    TR.train_step(model, opt, batch)
+    ops = TR.profile_read()
+    TR.profile(False)
+    fp32_peak = 148 * 128 * 2 * peaks()[1] * 1e6 / 1e12
+    dom = max(ops, key=lambda k: ops[k]["ms"])
+    d = ops[dom]
+    tflops = d["flops"] / (d["ms"] / 1e3) / 1e12 if d["ms"] > 0 else 0.0
     return {"frames_per_step": len(frames), "points_per_step": npts,
             "ms_per_step": round(step, 3), "steps_per_s": round(1e3 / step, 4),
             "mpoints_per_s": round(npts / step / 1e3, 4), "bits_per_point": round(loss, 4),
             "mode": "fake-quant on, bf16 operands, fp32 accumulation, the frames as one "
                     "batch frame",
-            "structure_ms_per_frame": round(build_ms, 3)}
+            "structure_ms_per_frame": round(build_ms, 3),
+            "ops_ms": {k: round(v["ms"], 3) for k, v in sorted(ops.items(),
+                                                               key=lambda kv: -kv[1]["ms"])},
+            "roofline": {"op": dom, "bound": "fp32 fma", "achieved": round(tflops, 3),
+                         "peak": round(fp32_peak, 1), "unit": "TFLOP/s",
+                         "frac": round(tflops / fp32_peak, 4),
+                         "peak_source": "derived: 148 SM x 128 FP32 lanes x 2 x "
+                                        f"{peaks()[1]:.0f} MHz"}}
 
 
 def run_ours(args):
@@ -532,7 +639,7 @@ def run_ours(args):
     # every substream adds its flush bytes and a length to the stream
     chunk_tradeoff = None
     if not args.no_arch:
-        chunk_tradeoff = {str(c): blob_leg(blob, steps=7, chunk=c) for c in (256, 512, 4096)
+        chunk_tradeoff = {str(c): blob_leg(blob, steps=7, chunk=c) for c in (128, 512, 1024)
                           if c != args.chunk}
 
     # the float inference variant (the float network, tables from a float
@@ -550,10 +657,22 @@ def run_ours(args):
         for lg in flog.values():
             differ += int((FV.float_cdf(lg).cpu() != FV.float_cdf(lg.cpu())).any(dim=1).sum())
             rows += lg.shape[0]
+        # the float stream coded with the GPU softmax's tables, decoded with
+        # the CPU softmax's tables of the same logits
+        xd = FV.cross_device_decode(flog, fr.codes, args.chunk)
+        lv = xd["levels"].values()
         float_variant = {"rows": rows, "rows_differing_gpu_vs_cpu_softmax": differ,
-                         "note": "the integer path's stream is the CPU oracle's byte for byte "
-                                 "(cpu_baseline.bitstream_identical); float tables are not "
-                                 "device-independent"}
+                         "cross_device_decode": {
+                             "same_device_round_trip": xd["same_device_round_trip"],
+                             "cloud_differs": xd["cloud_differs"],
+                             "substreams": sum(v["substreams"] for v in lv),
+                             "substreams_failing": sum(v["substreams_failing"] for v in lv),
+                             "symbols_wrong": sum(v["symbols_wrong"] for v in lv),
+                             "per_level": xd["levels"]},
+                         "note": "float stream: coded with the GPU softmax's tables, decoded "
+                                 "with the CPU softmax's tables of the same logits; the integer "
+                                 "path's stream is the CPU oracle's byte for byte "
+                                 "(cpu_baseline.bitstream_identical)"}
         del fr, fmodel, flog
 
     # batched form: the mixed-size 64-frame batch, whole batch per step
@@ -562,7 +681,7 @@ def run_ours(args):
         # every rank codes its round-robin share of the batch's frames
         specs = [synth.batch_specs(args.batch_frames)[i]
                  for i in shard_frames(args.batch_frames, rank, world)]
-        frames = [synth.make_frame(s) for s in specs]
+        frames = synth.make_frames(specs)
         Ls = [s.L for s in specs]
         bcodec = lpc.Codec(blob, max(Ls), max(f.shape[0] for f in frames),
                            max_frames=len(frames), chunk=args.chunk,
@@ -588,6 +707,13 @@ def run_ours(args):
             bt.append((a.elapsed_time(b), b.elapsed_time(c)))
         be = statistics.median(t[0] for t in bt)
         bd = statistics.median(t[1] for t in bt)
+        # lossless: every frame's decoded voxels (last timed decode) are the
+        # unique voxels of its input
+        decs = bcodec.decode_batch_from(bbuf, spans, bouts)
+        batch_lossless = all(
+            dcd.shape[0] == torch.unique(xx, dim=0).shape[0]
+            and torch.equal(torch.unique(dcd, dim=0), torch.unique(xx, dim=0))
+            for dcd, xx in zip(decs, xs))
         # one profiled (untimed) pass for the per-family breakdown
         bcodec.profile((1 << len(lpc.Codec.FAMILIES)) - 1)
         spans = bcodec.encode_batch_into(xs, Ls, bbuf)
@@ -605,6 +731,7 @@ def run_ours(args):
                    "encode_mpts": round(all_pts / (be_all / 1e3) / 1e6, 4),
                    "decode_mpts": round(all_pts / (bd_all / 1e3) / 1e6, 4),
                    "bits_per_point": round(8 * sum(n for _, n in spans) / npts, 4),
+                   "lossless": bool(batch_lossless),
                    "families": {k: {"ms": round(v["ms"], 4), "launches": v["launches"]}
                                 for k, v in bfams.items()},
                    "rooflines": family_rooflines(bfams, 1, peaks()[0], bf16_peak())}
@@ -630,7 +757,18 @@ def run_ours(args):
             "algorithmic_ops_per_launch": round(ops_pl),
             "timed_in": "the timed steps" if in_loop else
                         "a pass of its own after the timed steps (direct launches)"}
-    if ops_pl > 0:
+    if ops_pl > 0 and dominant == "conv333":
+        # the conv multiplies on the bf16 tensor pipe: its roofs are HBM
+        # (algorithmic bytes) and the measured bf16 peak; the higher
+        # fraction binds
+        tops = ops_pl / per_launch_s / 1e12
+        if tops / bf16_peak() > hbm_frac:
+            roof.update({"bound": "tensor", "achieved": round(tops, 3),
+                         "peak": round(bf16_peak(), 1), "unit": "TFLOP/s",
+                         "frac": round(tops / bf16_peak(), 4),
+                         "peak_source": "measured (bf16 burst)"})
+        roof["tensor_frac_of_bf16"] = round(tops / bf16_peak(), 5)
+    elif ops_pl > 0:
         alu = alu_peak_tops(sm_max)
         tops = ops_pl / per_launch_s / 1e12
         if tops / alu > hbm_frac:
@@ -638,33 +776,23 @@ def run_ours(args):
                          "unit": "TOPS", "frac": round(tops / alu, 4),
                          "peak_source": "derived: 148 SM x 128 lanes x dp4a (4 MAC) x 2 x "
                                         f"{sm_max:.0f} MHz"})
+    if dominant == "range_coder":
+        # a chain of dependent instructions per substream, not a memory or
+        # ALU roof: its time per symbol along that chain (the launch's time
+        # over the symbols of one substream); beside it the family with the
+        # most time among the bandwidth- and tensor-bound ones
+        roof["ns_per_symbol_chain"] = round(1e9 * per_launch_s / args.chunk, 1)
+        roof["symbols_per_chain"] = args.chunk
+        fr = family_rooflines(fams, 2, hbm, bf16_peak())
+        others = [k for k in fr if k not in ("range_coder", "levels", "sort")]
+        if others:
+            k = max(others, key=lambda k: fams[k]["ms"])
+            e = dict(fr[k])
+            e["family"] = k
+            roof["dominant_streaming_family"] = e
     cpu = None
     if not args.no_cpu:
-        import oracle as O
-        cores = os.cpu_count() or 1
-        O.set_threads(cores)
-        t0 = time.perf_counter()
-        data = O.encode(blob, frame, spec.L, args.chunk)
-        te = time.perf_counter() - t0
-        t0 = time.perf_counter()
-        O.decode(blob, data, n)
-        td = time.perf_counter() - t0
-        cpu = {"value": round(n / (te + td) / 1e6, 4), "unit": "Mpoints/s", "cores": cores,
-               "kind": "oracle", "sample": f"one full {args.workload} frame ({n} points), "
-                                           f"encode {te:.2f} s + decode {td:.2f} s",
-               "bitstream_identical": data == bytes(outbuf[:nbytes]),
-               "cpu_model": cpu_model()}
-        # the same oracle on one core, on the small 16-beam frame
-        small = synth.make_frame(WORKLOADS["tiny16_L12"])
-        O.set_threads(1)
-        t0 = time.perf_counter()
-        sd = O.encode(blob, small, WORKLOADS["tiny16_L12"].L, args.chunk)
-        O.decode(blob, sd, small.shape[0])
-        t1 = time.perf_counter() - t0
-        O.set_threads(cores)
-        cpu["single_core"] = {"value": round(small.shape[0] / t1 / 1e6, 4), "unit": "Mpoints/s",
-                              "sample": f"one tiny16_L12 frame ({small.shape[0]} points), "
-                                        f"encode + decode {t1:.2f} s"}
+        cpu = cpu_baseline_leg(blob, frame, spec, n, args.chunk, bytes(outbuf[:nbytes]))
     line = {
         "metric": METRIC, "value": round(value, 4), "unit": "Mpoints/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
@@ -726,7 +854,7 @@ def run_ncu_case(args):
             return ln
     else:
         specs = synth.batch_specs(args.batch_frames)
-        frames = [synth.make_frame(s) for s in specs]
+        frames = synth.make_frames(specs)
         Ls = [s.L for s in specs]
         codec = lpc.Codec(blob, max(Ls), max(f.shape[0] for f in frames),
                           max_frames=len(frames), chunk=args.chunk,

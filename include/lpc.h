@@ -57,7 +57,7 @@ typedef struct {
                          must equal the blob's */
   int64_t max_points; /* largest point count of one frame */
   int max_frames;     /* largest batch for encode_batch / decode_batch (1..64) */
-  int chunk;          /* nodes per entropy-coded substream of a network level (1024) */
+  int chunk;          /* nodes per entropy-coded substream of a network level (256) */
   int host_threads;   /* host threads for range coding (0 = hardware concurrency) */
   uint64_t cuda_stream; /* cudaStream_t as an integer (0 = legacy default stream) */
   int64_t max_batch_points; /* points of one batch, all frames (0 = max_points * max_frames);
@@ -88,11 +88,15 @@ const char* codec_last_error(codec_t* codec);
 
 /* Encode one frame.  d_xyz: device int32 [n][3].  The bitstream goes to the
  * caller's host buffer h_out of `cap` bytes; *out_len receives its length.
- * Stream (version 2): "LPC1", version, L, b, t, C, flags, the blob's hash,
+ * Stream (version 3): "LPC1", version, L, b, t, C, flags, the blob's hash,
  * then varints: network chunk, coarse chunk (4096), the coarse levels' sizes
- * N_1 .. N_{b-1}, the substream count and lengths; then the substreams: the
+ * N_1 .. N_{b-1}, the substream count, and each substream's length as the
+ * zigzag-coded difference to the previous one's; then the substreams: the
  * coarse levels in coarse chunks (adaptive symbol frequencies, a fresh model
- * each), the network levels in network chunks (the integer softmax tables). 
+ * each), the network levels in network chunks (the integer softmax tables).
+ * A substream is range coded without the coder's always-zero leading byte
+ * and ends with the shortest flush (up to four trailing zero bytes left out
+ * and read back as zero). 
  * If cap is too small, returns LPC_CAPACITY with the required length in
  * *out_len.  n = 0 gives an empty-frame stream.
  * Errors: LPC_INVALID_ARG (coordinate outside [0, 2^L)), LPC_CAPACITY
@@ -148,10 +152,15 @@ int codec_last_stats(codec_t* codec, int64_t* counts, double* gpu_us, double* ho
  * codec_profile_read returns, for one family, the summed launch time (ms),
  * the launch count, and the algorithmic bytes and integer ops those launches
  * must touch (counted from level sizes and neighbour pairs, not from the
- * kernels' actual traffic).  codec_profile_name gives the family's name. */
+ * kernels' actual traffic).  codec_profile_staged returns the bytes those
+ * launches actually move in this implementation's layouts (for the 3x3x3
+ * conv: bf16 gathered rows, the 27-entry map rows, the bf16 copy of the
+ * output and the bf16 weight image; for every other family the algorithmic
+ * figure).  codec_profile_name gives the family's name. */
 int codec_profile(codec_t* codec, unsigned family_mask);
 int codec_profile_read(codec_t* codec, int family, double* ms, int64_t* launches, double* bytes,
                        double* ops);
+int codec_profile_staged(codec_t* codec, int family, double* bytes);
 const char* codec_profile_name(int family);
 
 /* Autotuner state (variants[3], ms[10]): variants[0], variants[1] = the

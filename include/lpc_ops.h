@@ -109,6 +109,24 @@ int lpc_up_prune(const uint64_t* d_pkeys, const uint8_t* d_codes, int64_t Np,
 int lpc_softmax_cdf(const int8_t* d_logits, int64_t N, const uint32_t* h_lut, uint16_t* d_cdf,
                     uint64_t stream);
 
+/* Host range coding of one substream with caller tables (the coder the
+ * network levels use, Sec. 3.3: the 16-bit cumulative tables drive an
+ * entropy coder; stream version 3 framing).  h_rows: host u16 [n][256],
+ * entry s = C_{s+1} for s = 0..253 (C_0 = 0, C_255 = 2^16 implicit; entries
+ * 254, 255 unused), strictly increasing; h_syms: host symbols 0..254.
+ * lpc_rc_encode_rows writes the substream to h_out[0..cap) and its length to
+ * *out_len (LPC_CAPACITY, with the required length, if cap is too small;
+ * LPC_INVALID_ARG for a symbol above 254).  lpc_rc_decode_rows decodes n
+ * symbols from h_in[0..len) with the given rows into h_syms; LPC_CORRUPT_STREAM
+ * if the stream is inconsistent with the rows (an interval the decoder's
+ * value falls outside of, or reads beyond the four zero bytes a flush may
+ * leave out) -- the symbols are then whatever the decoder produced.  Host
+ * memory only, no CUDA calls. */
+int lpc_rc_encode_rows(const uint16_t* h_rows, const uint8_t* h_syms, int64_t n, uint8_t* h_out,
+                       size_t cap, size_t* out_len);
+int lpc_rc_decode_rows(const uint16_t* h_rows, int64_t n, const uint8_t* h_in, size_t len,
+                       uint8_t* h_syms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -77,6 +77,24 @@ int lpc_t_fq_bwd(const float* dy, const uint8_t* mask, int64_t n, float* dx, uin
  * device arrays of n elements owned by the caller. */
 int lpc_t_fq_w(const float* w, int64_t n, float* y, uint8_t* mask, uint64_t stream);
 
+/* Predictor (Eq. 7) and rate loss (supplement, Training, Eq. 16), fused:
+ * per row i of F [N][32], x = q(F[i]), h = prelu(W1 x + b1, a1), l = W2 q(h)
+ * + b2 (255 logits), and bits += -log2 softmax(l)[codes[i] - 1].  W1 [32][32],
+ * b1, a1 [32], W2 [255][32], b2 [255]; codes u8 [N] in 1..255; q = the fake
+ * quantiser of lpc_t_fq_fwd at s = 1/32, z = 0 when qat = 1, else identity.
+ * *bits (device double) is added to; logits, if not NULL, receives l [N][255]
+ * (float).  The backward recomputes the rows and, from the device scalar
+ * *dbits = d(loss)/d(bits), writes dF [N][32] (may be NULL) and adds into dW1,
+ * db1, da1, dW2, db2 (zero them first); the logits and their gradients never
+ * reach device memory. */
+int lpc_t_pred_fwd(const float* F, int64_t N, const float* W1, const float* b1, const float* a1,
+                   const float* W2, const float* b2, const uint8_t* codes, int qat, int bf16,
+                   float* logits, double* bits, uint64_t stream);
+int lpc_t_pred_bwd(const float* F, int64_t N, const float* W1, const float* b1, const float* a1,
+                   const float* W2, const float* b2, const uint8_t* codes, int qat, int bf16,
+                   const float* dbits, float* dF, float* dW1, float* db1, float* da1, float* dW2,
+                   float* db2, uint64_t stream);
+
 /* Octree levels with parent rows and child offsets, for the index
  * structures above: concatenations over depths 0..L (keys, par) and
  * 0..L-1 (codes, off with N_d + 1 entries each); counts[d] = N_d. */

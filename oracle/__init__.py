@@ -57,6 +57,7 @@ def _declare(L):
     sig = {
         "or_set_threads": (None, [C.c_int]),
         "or_get_threads": (C.c_int, []),
+        "or_last_phase_times": (None, [P, P]),
         "or_requant": (C.c_int, [I64, C.c_int32, C.c_int, C.c_int]),
         "or_prelu": (I64, [I64, C.c_int]),
         "or_morton": (C.c_uint64, [C.c_uint32, C.c_uint32, C.c_uint32, C.c_int]),
@@ -104,6 +105,18 @@ def _buf(b: bytes):
 
 def set_threads(n: int):
     lib().or_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return int(lib().or_get_threads())
+
+
+def last_phase_times() -> tuple[float, float]:
+    """(network + softmax seconds, range-coding seconds) of the calling
+    thread's last encode or decode."""
+    a, b = C.c_double(), C.c_double()
+    lib().or_last_phase_times(C.byref(a), C.byref(b))
+    return a.value, b.value
 
 
 def requant(acc: int, m: int, r: int, z: int) -> int:
@@ -267,7 +280,7 @@ def logits_level(blob: bytes, xyz: np.ndarray, L: int, d: int) -> np.ndarray:
     return _level_call(lib().or_logits_level, blob, xyz, L, d, 255, np.int8, "logits_level")
 
 
-def encode(blob: bytes, xyz: np.ndarray, L: int, chunk: int = 1024) -> bytes:
+def encode(blob: bytes, xyz: np.ndarray, L: int, chunk: int = 256) -> bytes:
     xyz = np.ascontiguousarray(xyz, dtype=np.int32)
     # coded bytes: at most 2 per symbol, plus flush bytes and a length varint
     # per substream (one substream per chunk of every network level and per

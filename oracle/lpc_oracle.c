@@ -32,12 +32,27 @@
 
 #include <stdlib.h>
 #include <string.h>
+#include <time.h>
 #ifdef _OPENMP
 #include <omp.h>
 #endif
 
 static int g_threads = 1;
 void or_set_threads(int n) { g_threads = n < 1 ? 1 : n; }
+
+/* Wall time of the last or_encode / or_decode on the calling thread, split
+ * into the network with its softmax tables and the range coding (for the
+ * CPU baseline's breakdown; no effect on any result). */
+static _Thread_local double g_t_net, g_t_code;
+static double now_s(void) {
+  struct timespec ts;
+  clock_gettime(CLOCK_MONOTONIC, &ts);
+  return (double)ts.tv_sec + 1e-9 * (double)ts.tv_nsec;
+}
+void or_last_phase_times(double* network_s, double* coding_s) {
+  *network_s = g_t_net;
+  *coding_s = g_t_code;
+}
 int or_get_threads(void) { return g_threads; }
 
 /* ------------------------------------------------------------------------ */
@@ -349,10 +364,20 @@ static void row_interval(const uint16_t* row, int s, uint32_t* lo, uint32_t* f) 
 /* with the usual cache-byte carry scheme).                                  */
 /* ------------------------------------------------------------------------ */
 
+/* Stream version 3 (the paper leaves the entropy coder open): the byte the cache holds before the first
+ * output is never written (it is always 0: every coded interval lies inside
+ * the initial [0, 2^32), so no carry reaches it), the decoder starts from
+ * the first four bytes, and the flush writes the value with the most
+ * trailing zero bits inside the final interval, whose trailing zero bytes
+ * (up to four) are left out: the decoder reads up to four bytes past a
+ * substream's end as zero. */
+#define RC_PAD 4
+
 typedef struct {
   uint8_t* buf;
   size_t cap, len;
   int overflow;
+  int skip; /* the leading cache byte is still to be dropped */
   uint64_t low;
   uint32_t range;
   uint8_t cache;
@@ -360,12 +385,13 @@ typedef struct {
 } rc_enc;
 
 static void enc_put(rc_enc* e, uint8_t b) {
+  if (e->skip) { e->skip = 0; return; }
   if (e->len < e->cap) e->buf[e->len] = b; else e->overflow = 1;
   e->len++;
 }
 
 static void enc_init(rc_enc* e, uint8_t* buf, size_t cap) {
-  e->buf = buf; e->cap = cap; e->len = 0; e->overflow = 0;
+  e->buf = buf; e->cap = cap; e->len = 0; e->overflow = 0; e->skip = 1;
   e->low = 0; e->range = 0xFFFFFFFFu; e->cache = 0; e->cache_size = 1;
 }
 
@@ -393,7 +419,19 @@ static void enc_code(rc_enc* e, uint32_t r, uint32_t lo, uint32_t f) {
 }
 
 static void enc_flush(rc_enc* e) {
+  /* any value in [low, low + range) identifies the coded symbols: take the
+   * multiple of 2^k in it with k largest (k >= 24 since range >= 2^24) */
+  const uint64_t end = e->low + e->range;
+  for (int k = 32; k > 0; k--) {
+    const uint64_t v = ((e->low + (((uint64_t)1 << k) - 1)) >> k) << k;
+    if (v < end) {
+      e->low = v;
+      break;
+    }
+  }
   for (int i = 0; i < 5; i++) enc_shift_low(e);
+  for (int i = 0; i < RC_PAD && !e->overflow && e->len > 0 && e->buf[e->len - 1] == 0; i++)
+    e->len--;
 }
 
 typedef struct {
@@ -405,14 +443,15 @@ typedef struct {
 
 static uint8_t dec_get(rc_dec* d) {
   if (d->pos < d->len) return d->buf[d->pos++];
-  d->bad = 1;
+  /* past the end: the flush's dropped zero bytes, at most RC_PAD of them */
+  if (++d->pos > d->len + RC_PAD) d->bad = 1;
   return 0;
 }
 
 static void dec_init(rc_dec* d, const uint8_t* buf, size_t len) {
   d->buf = buf; d->len = len; d->pos = 0; d->bad = 0;
   d->range = 0xFFFFFFFFu; d->code = 0;
-  for (int i = 0; i < 5; i++) d->code = (d->code << 8) | dec_get(d);
+  for (int i = 0; i < 4; i++) d->code = (d->code << 8) | dec_get(d);
 }
 
 static void dec_update(rc_dec* d, uint32_t r, uint32_t lo, uint32_t f) {
@@ -944,10 +983,12 @@ int or_probs_level(const void* blob, size_t blob_len, const int32_t* xyz, int64_
 /* ------------------------------------------------------------------------ */
 /* Bitstream                                                                 */
 /* ------------------------------------------------------------------------ */
-/* "LPC1", u8 version (2), u8 L, u8 b, u8 t, u8 C, u8 flags (bit0 = empty),
+/* "LPC1", u8 version (3), u8 L, u8 b, u8 t, u8 C, u8 flags (bit0 = empty),
  * u64 blob hash (LE), varint chunk, varint coarse chunk, varint N_1 ..
  * N_{b-1} (the coarse levels' sizes; absent for an empty frame), varint
- * n_sub, n_sub x varint length, then the substreams: coarse levels 0..b-1 in
+ * n_sub, n_sub x varint of the zigzag-coded difference between a substream's
+ * length and the previous one's (0 before the first), then the substreams:
+ * coarse levels 0..b-1 in
  * chunks of `coarse chunk` nodes (adaptive, a fresh model each), then for
  * d = b..L-1 the level's Morton-ordered nodes in chunks of `chunk`.  With
  * the sizes in the header every coarse chunk decodes on its own. */
@@ -976,6 +1017,13 @@ static void by_varint(bytes* B, uint64_t v) {
     if (v) c |= 0x80;
     by_put(B, &c, 1);
   } while (v);
+}
+
+/* substream lengths: zigzag varints of the difference to the previous length */
+static void by_len(bytes* B, size_t len, size_t* prev) {
+  const int64_t d = (int64_t)len - (int64_t)*prev;
+  by_varint(B, d >= 0 ? (uint64_t)d << 1 : (((uint64_t)(-d)) << 1) - 1);
+  *prev = len;
 }
 
 static int rd_varint(const uint8_t* in, size_t len, size_t* pos, uint64_t* v) {
@@ -1011,9 +1059,12 @@ int or_encode(const void* blob, size_t blob_len, const int32_t* xyz, int64_t n, 
   }
   bytes subs = {0}, lens = {0};
   uint64_t n_sub = 0;
+  size_t prev_len = 0;
+  g_t_net = g_t_code = 0;
   if (n > 0) {
     /* coarse levels: adaptive symbol frequencies, every COARSE_CHUNK
      * symbols a substream with a fresh model */
+    double t0 = now_s();
     for (int d = 0; d < b; d++) {
       for (int64_t s0 = 0; s0 < T.N[d]; s0 += COARSE_CHUNK) {
         const int64_t s1 = s0 + COARSE_CHUNK < T.N[d] ? s0 + COARSE_CHUNK : T.N[d];
@@ -1025,19 +1076,23 @@ int or_encode(const void* blob, size_t blob_len, const int32_t* xyz, int64_t n, 
         for (int64_t i = s0; i < s1; i++) am_encode(&e, &am, T.code[d][i] - 1);
         enc_flush(&e);
         by_put(&subs, tmp, e.len);
-        by_varint(&lens, e.len);
+        by_len(&lens, e.len, &prev_len);
         n_sub++;
         free(tmp);
       }
     }
+    g_t_code += now_s() - t0;
     /* network levels */
     net S = {M, &T, L, b, t, {NULL}};
     for (int d = b; d < L; d++) {
       int64_t N = T.N[d];
       int8_t* lg = (int8_t*)malloc((size_t)N * NSYM);
       uint16_t* cdf = (uint16_t*)malloc((size_t)N * 256 * sizeof(uint16_t));
+      t0 = now_s();
       net_level_logits(&S, d, lg);
       or_softmax_cdf(lg, N, M->lut, cdf);
+      const double t1 = now_s();
+      g_t_net += t1 - t0;
       for (int64_t s0 = 0; s0 < N; s0 += chunk) {
         int64_t s1 = s0 + chunk < N ? s0 + chunk : N;
         rc_enc e;
@@ -1046,10 +1101,11 @@ int or_encode(const void* blob, size_t blob_len, const int32_t* xyz, int64_t n, 
         for (int64_t i = s0; i < s1; i++) enc_symbol_row(&e, cdf + i * 256, T.code[d][i] - 1);
         enc_flush(&e);
         by_put(&subs, tmp, e.len);
-        by_varint(&lens, e.len);
+        by_len(&lens, e.len, &prev_len);
         n_sub++;
         free(tmp);
       }
+      g_t_code += now_s() - t1;
       free(lg);
       free(cdf);
     }
@@ -1058,7 +1114,7 @@ int or_encode(const void* blob, size_t blob_len, const int32_t* xyz, int64_t n, 
   bytes H = {0};
   uint8_t hdr[18];
   memcpy(hdr, "LPC1", 4);
-  hdr[4] = 2;
+  hdr[4] = 3;
   hdr[5] = (uint8_t)L;
   hdr[6] = (uint8_t)b;
   hdr[7] = (uint8_t)t;
@@ -1090,7 +1146,7 @@ int or_decode(const void* blob, size_t blob_len, const uint8_t* in, size_t len,
   int st = load_model(blob, blob_len, M);
   if (st) { free(M); return st; }
   *n_out = 0;
-  if (len < 18 || memcmp(in, "LPC1", 4) != 0 || in[4] != 2) { free(M); return OR_CORRUPT_STREAM; }
+  if (len < 18 || memcmp(in, "LPC1", 4) != 0 || in[4] != 3) { free(M); return OR_CORRUPT_STREAM; }
   const int L = in[5], b = in[6], t = in[7], C = in[8], flags = in[9];
   uint64_t hash = 0;
   for (int i = 0; i < 8; i++) hash |= (uint64_t)in[10 + i] << (8 * i);
@@ -1120,8 +1176,14 @@ int or_decode(const void* blob, size_t blob_len, const uint8_t* in, size_t len,
   }
   uint64_t* sl = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(n_sub + 1));
   size_t* so = (size_t*)malloc(sizeof(size_t) * (size_t)(n_sub + 1));
-  for (uint64_t i = 0; i < n_sub; i++)
-    if (rd_varint(in, len, &pos, &sl[i])) { st = OR_CORRUPT_STREAM; break; }
+  uint64_t prev = 0;
+  for (uint64_t i = 0; i < n_sub; i++) {
+    uint64_t z;
+    if (rd_varint(in, len, &pos, &z)) { st = OR_CORRUPT_STREAM; break; }
+    const uint64_t mag = (z + 1) >> 1;
+    if ((z & 1) ? mag > prev : mag > len) { st = OR_CORRUPT_STREAM; break; }
+    sl[i] = prev = (z & 1) ? prev - mag : prev + mag;
+  }
   size_t p = pos;
   for (uint64_t i = 0; !st && i < n_sub; i++) {
     so[i] = p;
@@ -1132,6 +1194,7 @@ int or_decode(const void* blob, size_t blob_len, const uint8_t* in, size_t len,
   memset(&T, 0, sizeof(T));
   T.L = L;
   uint64_t si = 0;
+  g_t_net = g_t_code = 0;
   if (!st) {
     T.N[0] = 1;
     T.key[0] = (uint64_t*)calloc(1, sizeof(uint64_t));
@@ -1139,12 +1202,14 @@ int or_decode(const void* blob, size_t blob_len, const uint8_t* in, size_t len,
       /* the header's N_d must be what the level above expands to */
       if ((uint64_t)T.N[d] != cN[d]) { st = OR_CORRUPT_STREAM; break; }
       T.code[d] = (uint8_t*)malloc((size_t)T.N[d]);
+      const double t0 = now_s();
       for (int64_t s0 = 0; s0 < T.N[d] && !st; s0 += (int64_t)cchunk) {
         const int64_t s1 = s0 + (int64_t)cchunk < T.N[d] ? s0 + (int64_t)cchunk : T.N[d];
         if (si >= n_sub) { st = OR_CORRUPT_STREAM; break; }
         st = or_rc_decode_adaptive(s1 - s0, in + so[si], (size_t)sl[si], T.code[d] + s0);
         si++;
       }
+      g_t_code += now_s() - t0;
       for (int64_t i = 0; !st && i < T.N[d]; i++) T.code[d][i] += 1;
       if (!st) st = octree_expand(&T, d);
     }
@@ -1153,8 +1218,11 @@ int or_decode(const void* blob, size_t blob_len, const uint8_t* in, size_t len,
       int64_t N = T.N[d];
       int8_t* lg = (int8_t*)malloc((size_t)N * NSYM);
       uint16_t* cdf = (uint16_t*)malloc((size_t)N * 256 * sizeof(uint16_t));
+      const double t0 = now_s();
       net_level_logits(&S, d, lg);
       or_softmax_cdf(lg, N, M->lut, cdf);
+      const double t1 = now_s();
+      g_t_net += t1 - t0;
       T.code[d] = (uint8_t*)malloc((size_t)N);
       for (int64_t s0 = 0; s0 < N && !st; s0 += (int64_t)chunk) {
         int64_t s1 = s0 + (int64_t)chunk < N ? s0 + (int64_t)chunk : N;
@@ -1163,6 +1231,7 @@ int or_decode(const void* blob, size_t blob_len, const uint8_t* in, size_t len,
                               T.code[d] + s0);
         si++;
       }
+      g_t_code += now_s() - t1;
       for (int64_t i = 0; !st && i < N; i++) T.code[d][i] += 1;
       free(lg);
       free(cdf);

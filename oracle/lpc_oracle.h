@@ -33,6 +33,9 @@ extern "C" {
 /* Number of OpenMP threads used by the per-node loops (1 = single thread). */
 void or_set_threads(int n);
 int or_get_threads(void);
+/* Seconds spent by the calling thread's last or_encode / or_decode in the
+ * network with its softmax tables and in range coding (CPU-baseline split). */
+void or_last_phase_times(double* network_s, double* coding_s);
 
 /* ---- integer primitives (Sec. 3.3, Eq. 13-14; pinned against exact
  *      rational arithmetic in the tests) ---- */

@@ -179,12 +179,13 @@ void coarse_frame(Frame& F, std::atomic<int>& status) {
 }  // namespace
 
 // ------------------------------------------------------------ bitstream --
-// "LPC1", u8 version (2), u8 L, u8 b, u8 t, u8 C, u8 flags (bit0: empty
+// "LPC1", u8 version (3), u8 L, u8 b, u8 t, u8 C, u8 flags (bit0: empty
 // frame), u64 blob hash (little endian), varint chunk, varint coarse chunk,
-// varint N_1 .. N_{b-1} (not for an empty frame), varint n_sub, n_sub varint
-// lengths, then the substreams: coarse levels 0..b-1 in chunks of `coarse
-// chunk` nodes (adaptive model, a fresh one each), then every network level
-// d = b..L-1 in chunks of `chunk` nodes.
+// varint N_1 .. N_{b-1} (not for an empty frame), varint n_sub, n_sub varints
+// of the zigzag-coded difference between a substream's length and the
+// previous one's (0 before the first), then the substreams: coarse levels
+// 0..b-1 in chunks of `coarse chunk` nodes (adaptive model, a fresh one
+// each), then every network level d = b..L-1 in chunks of `chunk` nodes.
 namespace {
 
 constexpr int kHdr = 18;
@@ -204,6 +205,14 @@ void put_varint(std::vector<uint8_t>& o, uint64_t v) {
     v >>= 7;
   }
   o.push_back((uint8_t)v);
+}
+
+constexpr uint8_t kStreamVersion = 3;
+
+// a substream length as the zigzag varint of its difference to `prev`
+void put_len(std::vector<uint8_t>& o, uint64_t len, uint64_t& prev) {
+  put_varint(o, len >= prev ? (len - prev) << 1 : ((prev - len) << 1) - 1);
+  prev = len;
 }
 
 bool get_varint(const uint8_t* in, size_t len, size_t& pos, uint64_t& v) {
@@ -475,7 +484,8 @@ void Codec::pbeg(int f) {
   pev_used_ += 2;
 }
 
-void Codec::pend(int f, double bytes, double ops, int pair_slot, double ppo, double ppb) {
+void Codec::pend(int f, double bytes, double ops, int pair_slot, double ppo, double ppb,
+                 double staged, double pps) {
   if (!(prof.mask >> f & 1) || marks_.empty() || marks_.back().e1 >= 0 || marks_.back().f != f)
     return;
   Mark& m = marks_.back();
@@ -486,6 +496,8 @@ void Codec::pend(int f, double bytes, double ops, int pair_slot, double ppo, dou
   m.pair_slot = pair_slot;
   m.ppo = ppo;
   m.ppb = ppb;
+  m.staged = staged < 0 ? bytes : staged;
+  m.pps = pps < 0 ? ppb : pps;
 }
 
 // After the call's final synchronisation: fold the marks into the totals.
@@ -502,6 +514,7 @@ void Codec::prof_collect() {
     const double P = m.pair_slot >= 0 ? (double)pairs[m.pair_slot] : 0.0;
     prof.bytes[m.f] += m.bytes + P * m.ppb;
     prof.ops[m.f] += m.ops + P * m.ppo;
+    prof.staged[m.f] += m.staged + P * m.pps;
   }
   marks_.clear();
   pev_used_ = 0;
@@ -667,11 +680,15 @@ void Codec::conv(const DLayer& W, int h, const int32_t* nbr, int slot, const voi
   if (conv_variant_[ci] < 0 && !cap_grid_) tune_conv(a, W.cin, h);
   pbeg(kFamConv);
   launch_conv333_tc(a, W.cin, gridn(h), st_, conv_variant_[ci] < 0 ? 0 : conv_variant_[ci]);
-  // per neighbour pair: 2 Cin C ops and 2 Cin bytes gathered; per node: the
-  // int8 output (+ the residual's y1 and the bf16 copy when present)
-  pend(kFamConv,
-       N_[h] * (32.0 + (res ? 32.0 : 0.0) + (outb ? 64.0 : 0.0)) + 27.0 * W.cin * 32 * 2, 0,
-       slot, 2.0 * W.cin * 32, 2.0 * W.cin + 4.0);
+  // algorithmic: per present neighbour pair 2 Cin C ops and Cin int8 bytes
+  // gathered; per node the int8 output (+ the residual's y1 read); the int8
+  // weights once.  Staged: the bf16 rows actually gathered (2 Cin a pair),
+  // the map's 27 entries a node, the bf16 copy of the output for the next
+  // conv, the bf16 weight image.
+  const double node_b = 32.0 + (res ? 32.0 : 0.0);
+  pend(kFamConv, N_[h] * node_b + 27.0 * W.cin * 32, 0, slot, 2.0 * W.cin * 32, (double)W.cin,
+       N_[h] * (node_b + 27.0 * 4 + (outb ? 64.0 : 0.0)) + 27.0 * W.cin * 32 * 2,
+       2.0 * W.cin);
 }
 
 // Autotuner: every variant of the conv runs on this launch's real input (all
@@ -1238,7 +1255,8 @@ int Codec::encode(int nf, const int32_t* const* xyz, const int64_t* n, const int
     const Frame* F = empty ? nullptr : &fr_[f];
     const int L = Ls[i];
     uint8_t head[kHdr];
-    const uint8_t hdr[10] = {'L', 'P', 'C', '1', 2, (uint8_t)L, (uint8_t)(L - cfg_.b_off),
+    const uint8_t hdr[10] = {'L', 'P', 'C', '1', kStreamVersion, (uint8_t)L,
+                             (uint8_t)(L - cfg_.b_off),
                              (uint8_t)(L - cfg_.t_off), (uint8_t)M_.C, (uint8_t)(empty ? 1 : 0)};
     memcpy(head, hdr, 10);
     for (int k = 0; k < 8; k++) head[10 + k] = (uint8_t)(M_.hash >> (8 * k));
@@ -1255,11 +1273,12 @@ int Codec::encode(int nf, const int32_t* const* xyz, const int64_t* n, const int
     }
     put_varint(table, nsub);
     size_t body = 0;
+    uint64_t prev = 0;
     for (size_t k = b0; k < b1; k++) {
       if (k < b0 + (size_t)F->b) {
-        for (uint32_t l : tasks_[k].parts) put_varint(table, l);
+        for (uint32_t l : tasks_[k].parts) put_len(table, l, prev);
       } else {
-        put_varint(table, tasks_[k].len);
+        put_len(table, tasks_[k].len, prev);
       }
       body += tasks_[k].len;
     }
@@ -1328,8 +1347,8 @@ int Codec::decode(int nf, const uint8_t* const* in, const size_t* lens, int32_t*
     Frame& F = all[i];
     const uint8_t* p = in[i];
     const size_t len = lens[i];
-    if (!p || len < (size_t)kHdr || memcmp(p, "LPC1", 4) != 0 || p[4] != 2)
-      return fail(LPC_CORRUPT_STREAM, "decode: not an LPC1 version 2 stream");
+    if (!p || len < (size_t)kHdr || memcmp(p, "LPC1", 4) != 0 || p[4] != kStreamVersion)
+      return fail(LPC_CORRUPT_STREAM, "decode: not an LPC1 version 3 stream");
     const int L = p[5], b = p[6], t = p[7], C = p[8], flags = p[9];
     uint64_t hash = 0;
     for (int k = 0; k < 8; k++) hash |= (uint64_t)p[10 + k] << (8 * k);
@@ -1371,9 +1390,15 @@ int Codec::decode(int nf, const uint8_t* const* in, const size_t* lens, int32_t*
     F.chunk = (int64_t)chunk;
     F.slen.resize(nsub);
     F.soff.resize(nsub);
-    for (uint64_t k = 0; k < nsub; k++)
-      if (!get_varint(p, len, pos, F.slen[k]))
+    uint64_t prev = 0;
+    for (uint64_t k = 0; k < nsub; k++) {
+      uint64_t z;
+      if (!get_varint(p, len, pos, z)) return fail(LPC_CORRUPT_STREAM, "decode: bad stream table");
+      const uint64_t mag = (z + 1) >> 1;
+      if ((z & 1) ? mag > prev : mag > len)
         return fail(LPC_CORRUPT_STREAM, "decode: bad stream table");
+      F.slen[k] = prev = (z & 1) ? prev - mag : prev + mag;
+    }
     for (uint64_t k = 0; k < nsub; k++) {
       if (F.slen[k] > len - pos) return fail(LPC_CORRUPT_STREAM, "decode: truncated stream");
       F.soff[k] = pos;
@@ -1990,6 +2015,12 @@ int codec_profile_read(codec_t* codec, int family, double* ms, int64_t* launches
   if (launches) *launches = p.launches[family];
   if (bytes) *bytes = p.bytes[family];
   if (ops) *ops = p.ops[family];
+  return LPC_OK;
+}
+
+int codec_profile_staged(codec_t* codec, int family, double* bytes) {
+  if (!codec || !bytes || family < 0 || family >= lpc::kFamCount) return LPC_INVALID_ARG;
+  *bytes = codec->c.prof.staged[family];
   return LPC_OK;
 }
 

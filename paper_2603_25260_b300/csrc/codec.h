@@ -93,6 +93,7 @@ struct Profile {
   int64_t launches[kFamCount] = {};
   double bytes[kFamCount] = {};
   double ops[kFamCount] = {};
+  double staged[kFamCount] = {};  // bytes the kernels actually move (layout copies, maps)
 };
 
 struct Stats {
@@ -237,14 +238,16 @@ class Codec {
   void tune_conv(const ConvTcArgs& a, int cin, int h);
   int64_t hash_slots(int64_t n) const;
   // profiler: bracket a launch of family f; ops/bytes are algorithmic work
-  // (pair_slot >= 0: ops/bytes are per neighbour pair, scaled at collection)
+  // (pair_slot >= 0: ops/bytes are per neighbour pair, scaled at collection);
+  // staged / per_pair_staged (< 0: the algorithmic figures) are the bytes
+  // the launch actually moves
   void pbeg(int f);
   void pend(int f, double bytes, double ops, int pair_slot = -1, double per_pair_ops = 0,
-            double per_pair_bytes = 0);
+            double per_pair_bytes = 0, double staged = -1, double per_pair_staged = -1);
   void prof_collect();
   struct Mark {
     int f, e0, e1, pair_slot;
-    double bytes, ops, ppo, ppb;
+    double bytes, ops, ppo, ppb, staged, pps;
   };
   std::vector<cudaEvent_t> pev_;
   std::vector<Mark> marks_;

@@ -21,11 +21,24 @@ void RangeEncoder::shift_low() {
 }
 
 void RangeEncoder::finish() {
+  // the multiple of 2^k in [low, low + range) with k largest (k >= 24)
+  const uint64_t end = low_ + range_;
+  for (int k = 32; k > 0; k--) {
+    const uint64_t v = ((low_ + ((uint64_t{1} << k) - 1)) >> k) << k;
+    if (v < end) {
+      low_ = v;
+      break;
+    }
+  }
   for (int i = 0; i < 5; i++) shift_low();
+  for (size_t i = 0; i < RangeDecoder::kPad && len_ > 0 && len_ <= cap_ && out_[len_ - 1] == 0;
+       i++)
+    len_--;
 }
 
-RangeDecoder::RangeDecoder(const uint8_t* p, size_t n) : p_(p), end_(p + n) {
-  for (int i = 0; i < 5; i++) code_ = (code_ << 8) | next();
+RangeDecoder::RangeDecoder(const uint8_t* p, size_t n) : p_(p), n_(n) {
+  code_ = (at(0) << 24) | (at(1) << 16) | (at(2) << 8) | at(3);
+  pos_ = 4;
 }
 
 // Renormalisation without a loop: after an update range >= 255 (the
@@ -36,17 +49,11 @@ void RangeDecoder::update(uint32_t lo, uint32_t f) {
   range_ = r_ * f;
   if (code_ >= range_) bad_ = true;
   const int nb = (range_ < (1u << 24)) + (range_ < (1u << 16)) + (range_ < (1u << 8));
-  const uint64_t b0 = p_ < end_ ? p_[0] : 0u, b1 = p_ + 1 < end_ ? p_[1] : 0u,
-                 b2 = p_ + 2 < end_ ? p_[2] : 0u;
+  const uint64_t b0 = at(pos_), b1 = at(pos_ + 1), b2 = at(pos_ + 2);
   const uint64_t c = ((uint64_t)code_ << 24) | (b0 << 16) | (b1 << 8) | b2;
   code_ = (uint32_t)(c >> (24 - 8 * nb));
   range_ <<= 8 * nb;
-  if (nb > end_ - p_) {
-    bad_ = true;
-    p_ = end_;
-  } else {
-    p_ += nb;
-  }
+  pos_ += nb;
 }
 
 int RangeDecoder::decode_row(const uint16_t* row) {
@@ -214,3 +221,32 @@ bool decode_adaptive(size_t n, const uint8_t* in, size_t len, uint8_t* syms) {
 }
 
 }  // namespace lpc
+
+// ------------------------------------------------ C ABI (lpc_ops.h) --
+#include "../../include/lpc.h"
+#include "../../include/lpc_ops.h"
+
+extern "C" int lpc_rc_encode_rows(const uint16_t* h_rows, const uint8_t* h_syms, int64_t n,
+                                  uint8_t* h_out, size_t cap, size_t* out_len) {
+  if (n < 0 || !out_len || (n > 0 && (!h_rows || !h_syms)) || (cap > 0 && !h_out))
+    return LPC_INVALID_ARG;
+  lpc::RangeEncoder e(h_out, cap);
+  for (int64_t i = 0; i < n; i++) {
+    const int s = h_syms[i];
+    if (s > 254) return LPC_INVALID_ARG;
+    const uint16_t* row = h_rows + i * 256;
+    const uint32_t lo = s ? row[s - 1] : 0u;
+    const uint32_t hi = s == 254 ? 65536u : row[s];
+    if (hi <= lo) return LPC_INVALID_ARG;
+    e.code16(lo, hi - lo);
+  }
+  e.finish();
+  *out_len = e.size();
+  return e.overflow() ? LPC_CAPACITY : LPC_OK;
+}
+
+extern "C" int lpc_rc_decode_rows(const uint16_t* h_rows, int64_t n, const uint8_t* h_in,
+                                  size_t len, uint8_t* h_syms) {
+  if (n < 0 || (n > 0 && (!h_rows || !h_syms)) || (len > 0 && !h_in)) return LPC_INVALID_ARG;
+  return lpc::decode_rows(h_rows, (size_t)n, h_in, len, h_syms) ? LPC_OK : LPC_CORRUPT_STREAM;
+}

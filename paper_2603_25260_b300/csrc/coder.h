@@ -1,6 +1,11 @@
 // Host entropy coding: a range coder with a 32-bit range and byte-wise carry
 // propagation (low kept to 33 bits; a settled byte is held back in a cache
 // together with a count of pending 0xFF bytes until the carry is known).
+// Stream version 3 substreams: the cache's initial byte (always 0, since no
+// carry can reach it) is not written, the decoder starts from the first four
+// bytes, and the flush codes the value with the most trailing zero bits in
+// the final interval and leaves out up to four trailing zero bytes, which
+// the decoder reads back as zero.
 // Two probability sources: the device-made 16-bit cumulative tables of the
 // network levels, and an adaptive symbol-frequency model for the coarse
 // levels below b (supplement, "Detailed Model Structure").
@@ -37,11 +42,16 @@ class RangeEncoder {
   }
   void shift_low();
   inline void put(uint8_t b) {
+    if (skip_) {  // the leading cache byte
+      skip_ = false;
+      return;
+    }
     if (len_ < cap_) out_[len_] = b;
     len_++;
   }
   uint8_t* out_;
   size_t cap_, len_ = 0;
+  bool skip_ = true;
   uint64_t low_ = 0;
   uint32_t range_ = 0xFFFFFFFFu;
   uint8_t cache_ = 0;
@@ -60,16 +70,14 @@ class RangeDecoder {
     return v < total ? v : total - 1;
   }
   void update(uint32_t lo, uint32_t f);
-  bool bad() const { return bad_; }
+  bool bad() const { return bad_ || pos_ > n_ + kPad; }
+  // bytes a substream may be short of at its end (read as zero)
+  static constexpr size_t kPad = 4;
 
  private:
-  inline uint8_t next() {
-    if (p_ < end_) return *p_++;
-    bad_ = true;
-    return 0;
-  }
+  inline uint32_t at(size_t i) const { return i < n_ ? p_[i] : 0u; }
   const uint8_t* p_;
-  const uint8_t* end_;
+  size_t n_, pos_ = 0;
   uint32_t range_ = 0xFFFFFFFFu, code_ = 0, r_ = 0;
   bool bad_ = false;
 };

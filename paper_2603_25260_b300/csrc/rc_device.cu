@@ -1,7 +1,10 @@
 // Range coding of the network levels on the device, byte-identical to the
 // host coder (coder.h): 32-bit range, low kept to 33 bits, a settled byte
-// held back with a count of pending 0xFF bytes until the carry is known,
-// 5 flush bytes; intervals of a total 2^16 from the integer softmax tables.
+// held back with a count of pending 0xFF bytes until the carry is known;
+// stream version 3 substreams (the cache's initial byte is not written, the
+// flush codes the value with the most trailing zero bits in the final
+// interval and leaves out up to four trailing zero bytes, which the decoder
+// reads as zero); intervals of a total 2^16 from the integer softmax tables.
 //
 // Substreams are independent, so every chunk is coded in parallel:
 //  - encode: one warp per chunk (its lane 0) walks the packed (lo, f)
@@ -33,6 +36,8 @@ using tc::mbar_wait;
 using tc::smem_u32;
 
 constexpr int kEncWarps = 4;
+// bytes a substream may be short of at its end (read as zero)
+constexpr int kRcPad = 4;
 constexpr int kEncAhead = 4;
 // With at least this many chunks every lane codes a chunk of its own (the
 // warps would otherwise issue one lane's instructions each and the launch
@@ -47,6 +52,7 @@ __device__ __forceinline__ void encode_chunk(const RcChunk* __restrict__ ck, int
   const RcChunk c = ck[t];
   uint8_t* o = out + c.byte_off;
   const int64_t cap = c.byte_len;
+  // len counts the leading cache byte too; byte i is stored at o[i - 1]
   int64_t len = 0;
   uint64_t low = 0;
   uint32_t range = 0xFFFFFFFFu;
@@ -57,7 +63,7 @@ __device__ __forceinline__ void encode_chunk(const RcChunk* __restrict__ ck, int
       const uint32_t carry = (uint32_t)(low >> 32);
       uint32_t b = cache;
       for (; pending > 0; pending--) {
-        if (len < cap) o[len] = (uint8_t)(b + carry);
+        if (len > 0 && len <= cap) o[len - 1] = (uint8_t)(b + carry);
         len++;
         b = 0xFF;
       }
@@ -86,9 +92,23 @@ __device__ __forceinline__ void encode_chunk(const RcChunk* __restrict__ ck, int
       }
     }
   }
+  // flush: the multiple of 2^k in [low, low + range) with k largest
+  const uint64_t end = low + range;
+  for (int k = 32; k > 0; k--) {
+    const uint64_t v = ((low + ((1ull << k) - 1)) >> k) << k;
+    if (v < end) {
+      low = v;
+      break;
+    }
+  }
   for (int i = 0; i < 5; i++) shift_low();
+  len -= 1;  // the leading cache byte is not part of the stream
+  if (len > cap) {
+    set_error(err, kErrCapacity);
+  } else {
+    for (int i = 0; i < kRcPad && len > 0 && o[len - 1] == 0; i++) len--;
+  }
   lens[t] = (uint32_t)len;
-  if (len > cap) set_error(err, kErrCapacity);
 }
 
 // One chunk per warp, coded by its lane 0 (few chunks: lanes of other chunks
@@ -157,9 +177,8 @@ k_rc_decode(const RcChunk* __restrict__ ck, int n, const int64_t* d_n,
   const uint8_t* const end = p + c.byte_len;
   bool bad = false, lost = false;
   uint32_t range = 0xFFFFFFFFu, code = 0;
-  for (int i = 0; i < 5; i++) {
+  for (int i = 0; i < 4; i++) {
     code = (code << 8) | (p < end ? __ldg(p) : 0u);
-    if (p >= end) bad = true;
     p++;
   }
   // lane l holds entries 8l .. 8l+7 of a row; only entries 0..253 are
@@ -210,7 +229,6 @@ k_rc_decode(const RcChunk* __restrict__ ck, int n, const int64_t* d_n,
           code = (code << 16) | (b0 << 8) | b1;
         }
         range <<= 8 * nb;
-        if (p + nb > end) bad = true;
         p += nb;
         if (lane == 0) dst[r0 + k] = (uint8_t)(s + 1);
       }
@@ -229,6 +247,7 @@ k_rc_decode(const RcChunk* __restrict__ ck, int n, const int64_t* d_n,
       mbar_wait(bar + (int)(q % kStages), (uint32_t)((q / kStages) & 1));
     return;
   }
+  if (p > end + kRcPad) bad = true;  // read past the zero bytes a flush may leave out
   if (bad && lane == 0) set_error(err, kErrStream);
 }
 

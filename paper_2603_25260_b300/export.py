@@ -15,7 +15,7 @@ blob record the integer codec reads:
   last layer;
 - PReLU slope  round(a 2^15) (Q15; PReLU commutes with the positive scale,
   so it acts on the accumulator);
-- residual merge (Q8): round(m_a 2^15), round(m_b 2^15) with a 15-bit
+- residual merge (the ResBlock reading): round(m_a 2^15), round(m_b 2^15) with a 15-bit
   rounding shift, inputs and output at s_a;
 - embeddings   clip(round(E / s_a), -128, 127).
 

@@ -60,12 +60,15 @@ def lib():
             "codec_last_stats": (I32, [P, P, P, P]),
             "codec_profile": (I32, [P, C.c_uint]),
             "codec_profile_read": (I32, [P, I32, P, P, P, P]),
+            "codec_profile_staged": (I32, [P, I32, P]),
             "codec_profile_name": (C.c_char_p, [I32]),
             "lpc_kernel_launches": (I64, []),
             "codec_last_phases": (I32, [P, P, I32]),
             "lpc_build_levels": (I32, [P, I64, I32, P, P, P, I64, C.c_uint64]),
             "lpc_kernel_map": (I32, [P, I64, I32, P, I32, C.c_uint64]),
             "lpc_kernel_map_noalloc": (I32, [P, I64, I32, P, C.c_uint64]),
+            "lpc_rc_encode_rows": (I32, [P, P, I64, P, C.c_size_t, P]),
+            "lpc_rc_decode_rows": (I32, [P, I64, P, C.c_size_t, P]),
             "lpc_kernel_map_child": (I32, [P, P, I64, P, P, P, P, C.c_uint64]),
             "lpc_conv333": (I32, [P, I64, I32, P, I32, I32, P, P, P, I32, P, I32, I32, P,
                                   C.c_uint64]),
@@ -113,15 +116,15 @@ class Codec:
     """One codec instance on the current CUDA device and stream."""
 
     def __init__(self, blob: bytes, L: int, max_points: int, max_frames: int = 1,
-                 chunk: int = 1024, host_threads: int = 0, stream: int | None = None,
+                 chunk: int = 256, host_threads: int = 0, stream: int | None = None,
                  max_batch_points: int = 0, host_coding: bool = False):
         """blob: the integer weight blob; its header names the architecture
         (GRED + XFP or an ablation) and t = L - t_off, which the codec takes.
         chunk: nodes per range-coded substream of a network level.  The
         device decoder runs one warp per substream, so a level's decode
-        latency is about chunk x ~170 ns, while each substream adds ~9 bytes;
-        1024 keeps the rate, 256-512 trade ~0.5-1.5 % of it for ~15-25 %
-        more frames per second.  host_coding: range-code the network levels on
+        latency is about chunk x ~170 ns, while each substream adds about two
+        bytes (its length and the short flush); 256 costs ~0.1 bits per point
+        over 1024 on a 64-beam frame.  host_coding: range-code the network levels on
         host threads (tables copied to the host) instead of on the device;
         same bitstream."""
         self._lib = lib()
@@ -272,7 +275,10 @@ class Codec:
             n = C.c_int64()
             self._check(self._lib.codec_profile_read(self._h, i, C.byref(ms), C.byref(n),
                                                      C.byref(b), C.byref(o)))
-            out[name] = {"ms": ms.value, "launches": n.value, "bytes": b.value, "ops": o.value}
+            sb = C.c_double()
+            self._check(self._lib.codec_profile_staged(self._h, i, C.byref(sb)))
+            out[name] = {"ms": ms.value, "launches": n.value, "bytes": b.value, "ops": o.value,
+                         "staged_bytes": sb.value}
         return out
 
     def tuning(self) -> dict:
@@ -382,6 +388,35 @@ def kernel_map_noalloc(keys: torch.Tensor, depth: int, out: torch.Tensor) -> tor
                            f"limit of {NOALLOC_MAX_NODES}")
     _ops_check(st, "lpc_kernel_map_noalloc")
     return out[:N]
+
+
+def rc_encode_rows(rows: np.ndarray, syms: np.ndarray) -> bytes:
+    """Range code symbols 0..254 with host table rows u16 [n, 256] (one
+    substream, the codec's host coder)."""
+    rows = np.ascontiguousarray(rows, dtype=np.uint16)
+    syms = np.ascontiguousarray(syms, dtype=np.uint8)
+    n = syms.shape[0]
+    assert rows.shape == (n, 256)
+    out = np.empty(2 * n + 16, dtype=np.uint8)
+    ln = C.c_size_t()
+    _ops_check(lib().lpc_rc_encode_rows(rows.ctypes.data, syms.ctypes.data, n, out.ctypes.data,
+                                        out.shape[0], C.byref(ln)), "lpc_rc_encode_rows")
+    return out[:ln.value].tobytes()
+
+
+def rc_decode_rows(rows: np.ndarray, data: bytes) -> tuple[int, np.ndarray]:
+    """Decode one substream with host table rows u16 [n, 256]: (status, the
+    n symbols).  A stream inconsistent with the rows gives CORRUPT_STREAM
+    (and whatever symbols the decoder produced), not an exception."""
+    rows = np.ascontiguousarray(rows, dtype=np.uint16)
+    n = rows.shape[0]
+    syms = np.zeros(n, dtype=np.uint8)
+    buf = np.frombuffer(bytes(data) + b"\0", dtype=np.uint8)
+    st = lib().lpc_rc_decode_rows(rows.ctypes.data, n, buf.ctypes.data, len(data),
+                                  syms.ctypes.data)
+    if st not in (OK, CORRUPT_STREAM):
+        _ops_check(st, "lpc_rc_decode_rows")
+    return st, syms
 
 
 def conv333(keys, depth, x, z_in, W, bias, mult, shift, slope, z_out, variant=None):

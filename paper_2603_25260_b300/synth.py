@@ -202,6 +202,20 @@ def make_frame(spec: FrameSpec) -> np.ndarray:
     return quantize(lidar_points(spec), spec.L, spec.cube)
 
 
+def make_frames(specs: list[FrameSpec], workers: int | None = None) -> list[np.ndarray]:
+    """make_frame for many specs on a thread pool (the ray caster's array
+    operations release the GIL); every frame has its own seeded generator, so
+    the result does not depend on the number of workers."""
+    import concurrent.futures as cf
+    import os
+
+    workers = workers or min(len(specs), os.cpu_count() or 1)
+    if workers <= 1 or len(specs) <= 1:
+        return [make_frame(s) for s in specs]
+    with cf.ThreadPoolExecutor(workers) as ex:
+        return list(ex.map(make_frame, specs))
+
+
 def random_cloud(n: int, L: int, seed: int, clustered: bool = True) -> np.ndarray:
     """Small random int32 [n, 3] clouds for unit tests (optionally clustered so
     that 3x3x3 neighbourhoods are populated)."""

@@ -16,7 +16,6 @@ the codec's own octree and kernel-map kernels.
 from __future__ import annotations
 
 import ctypes as C
-import math
 
 import numpy as np
 import torch
@@ -49,6 +48,9 @@ def _lib():
             "lpc_t_fq_bwd": [P_, P_, I64, P_, C.c_uint64],
             "lpc_t_fq_w": [P_, I64, P_, P_, C.c_uint64],
             "lpc_t_levels": [P_, I64, I32, P_, P_, P_, P_, P_, I64, C.c_uint64],
+            "lpc_t_pred_fwd": [P_, I64, P_, P_, P_, P_, P_, P_, I32, I32, P_, P_, C.c_uint64],
+            "lpc_t_pred_bwd": [P_, I64, P_, P_, P_, P_, P_, P_, I32, I32, P_, P_, P_, P_, P_,
+                               P_, P_, C.c_uint64],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -71,6 +73,54 @@ def _ck(s, what):
         raise lpc.LpcError(s, what)
 
 
+# Per-op device time (profiling passes only): CUDA events on the current
+# stream around every kernel call of the twin, by op name.
+_PROF = None
+
+
+def profile(on: bool) -> None:
+    """Start (on) or stop timing every op of the twin; profile_read() sums."""
+    global _PROF
+    _PROF = {} if on else None
+
+
+def profile_read() -> dict:
+    """{op: {"ms": total device ms, "launches": calls, "flops": algorithmic
+    floating-point operations}} since profile(True)."""
+    torch.cuda.synchronize()
+    fl = (_PROF or {}).get("_flops", {})
+    return {k: {"ms": sum(a.elapsed_time(b) for a, b in v), "launches": len(v),
+                "flops": fl.get(k, 0.0)}
+            for k, v in (_PROF or {}).items() if k != "_flops"}
+
+
+def _flops(what, n):
+    """Algorithmic flops of one call (profiling passes only)."""
+    if _PROF is not None:
+        f = _PROF.setdefault("_flops", {})
+        f[what] = f.get(what, 0.0) + float(n)
+
+
+def _pairs(nbr):
+    return float((nbr >= 0).sum()) if _PROF is not None else 0.0
+
+
+# per predictor row: two linear layers (2 x 32 x 32 + 2 x 255 x 32 flops);
+# the backward recomputes them and forms three more products of each size
+PRED_FLOPS = 2.0 * 32 * 32 + 2.0 * 255 * 32
+
+
+def _call(what, fn, *args):
+    if _PROF is None:
+        return _ck(fn(*args), what)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    st = fn(*args)
+    b.record()
+    _PROF.setdefault(what, []).append((a, b))
+    return _ck(st, what)
+
+
 # ------------------------------------------------------------- autograd ops --
 
 class ConvFn(torch.autograd.Function):
@@ -79,8 +129,9 @@ class ConvFn(torch.autograd.Function):
         x, W, b = x.contiguous(), W.contiguous(), b.contiguous()
         N, cin = x.shape
         y = torch.empty(N, W.shape[1], device=x.device, dtype=torch.float32)
-        _ck(_lib().lpc_t_conv_fwd(_p(x), N, cin, _p(nbr), _p(W), _p(b), W.shape[1], _p(y),
-                                  bf16, _st()), "conv fwd")
+        _flops("conv fwd", 2.0 * _pairs(nbr) * cin * W.shape[1])
+        _call("conv fwd", _lib().lpc_t_conv_fwd, _p(x), N, cin, _p(nbr), _p(W), _p(b), W.shape[1],
+              _p(y), bf16, _st())
         ctx.save_for_backward(x, nbr, W)
         ctx.bf16 = bf16
         return y
@@ -93,8 +144,9 @@ class ConvFn(torch.autograd.Function):
         dx = torch.empty_like(x) if ctx.needs_input_grad[0] else None
         dW = torch.zeros_like(W)
         db = torch.zeros(W.shape[1], device=x.device, dtype=torch.float32)
-        _ck(_lib().lpc_t_conv_bwd(_p(x), _p(dy), N, cin, _p(nbr), _p(W), W.shape[1], _p(dx),
-                                  _p(dW), _p(db), ctx.bf16, _st()), "conv bwd")
+        _flops("conv bwd", 4.0 * _pairs(nbr) * cin * W.shape[1])
+        _call("conv bwd", _lib().lpc_t_conv_bwd, _p(x), _p(dy), N, cin, _p(nbr), _p(W), W.shape[1],
+              _p(dx), _p(dW), _p(db), ctx.bf16, _st())
         return dx, None, dW, db, None
 
 
@@ -106,8 +158,9 @@ class UpFn(torch.autograd.Function):
         x, W, b = x.contiguous(), W.contiguous(), b.contiguous()
         Nc = par.shape[0]
         y = torch.empty(Nc, W.shape[1], device=x.device, dtype=torch.float32)
-        _ck(_lib().lpc_t_up_fwd(_p(x), x.shape[1], _p(par), _p(ckey), Nc, _p(W), _p(b),
-                                W.shape[1], _p(y), bf16, _st()), "up fwd")
+        _flops("up fwd", 2.0 * Nc * x.shape[1] * W.shape[1])
+        _call("up fwd", _lib().lpc_t_up_fwd, _p(x), x.shape[1], _p(par), _p(ckey), Nc, _p(W),
+              _p(b), W.shape[1], _p(y), bf16, _st())
         ctx.save_for_backward(x, par, ckey, off, W)
         ctx.bf16 = bf16
         return y
@@ -119,9 +172,10 @@ class UpFn(torch.autograd.Function):
         dx = torch.empty_like(x) if ctx.needs_input_grad[0] else None
         dW = torch.zeros_like(W)
         db = torch.zeros(8, W.shape[1], device=x.device, dtype=torch.float32)
-        _ck(_lib().lpc_t_up_bwd(_p(x), _p(dy), x.shape[0], x.shape[1], _p(off), _p(par),
-                                _p(ckey), par.shape[0], _p(W), W.shape[1], _p(dx), _p(dW),
-                                _p(db), ctx.bf16, _st()), "up bwd")
+        _flops("up bwd", 4.0 * par.shape[0] * x.shape[1] * W.shape[1])
+        _call("up bwd", _lib().lpc_t_up_bwd, _p(x), _p(dy), x.shape[0], x.shape[1], _p(off),
+              _p(par), _p(ckey), par.shape[0], _p(W), W.shape[1], _p(dx), _p(dW), _p(db), ctx.bf16,
+              _st())
         return dx, None, None, None, dW, db, None
 
 
@@ -133,8 +187,9 @@ class DownFn(torch.autograd.Function):
         x, W, b = x.contiguous(), W.contiguous(), b.contiguous()
         Np = off.shape[0] - 1
         y = torch.empty(Np, W.shape[1], device=x.device, dtype=torch.float32)
-        _ck(_lib().lpc_t_down_fwd(_p(x), x.shape[1], _p(off), _p(ckey), Np, _p(W), _p(b),
-                                  W.shape[1], _p(y), bf16, _st()), "down fwd")
+        _flops("down fwd", 2.0 * x.shape[0] * x.shape[1] * W.shape[1])
+        _call("down fwd", _lib().lpc_t_down_fwd, _p(x), x.shape[1], _p(off), _p(ckey), Np, _p(W),
+              _p(b), W.shape[1], _p(y), bf16, _st())
         ctx.save_for_backward(x, par, ckey, off, W)
         ctx.bf16 = bf16
         return y
@@ -146,9 +201,10 @@ class DownFn(torch.autograd.Function):
         dx = torch.empty_like(x) if ctx.needs_input_grad[0] else None
         dW = torch.zeros_like(W)
         db = torch.zeros(W.shape[1], device=x.device, dtype=torch.float32)
-        _ck(_lib().lpc_t_down_bwd(_p(x), _p(dy), x.shape[0], x.shape[1], _p(par), _p(ckey),
-                                  off.shape[0] - 1, _p(W), W.shape[1], _p(dx), _p(dW), _p(db),
-                                  ctx.bf16, _st()), "down bwd")
+        _flops("down bwd", 4.0 * x.shape[0] * x.shape[1] * W.shape[1])
+        _call("down bwd", _lib().lpc_t_down_bwd, _p(x), _p(dy), x.shape[0], x.shape[1], _p(par),
+              _p(ckey), off.shape[0] - 1, _p(W), W.shape[1], _p(dx), _p(dW), _p(db), ctx.bf16,
+              _st())
         return dx, None, None, None, dW, db, None
 
 
@@ -157,8 +213,8 @@ class EmbedFn(torch.autograd.Function):
     def forward(ctx, codes, E):
         E = E.contiguous()
         y = torch.empty(codes.shape[0], E.shape[1], device=E.device, dtype=torch.float32)
-        _ck(_lib().lpc_t_embed_fwd(_p(codes), codes.shape[0], _p(E), E.shape[1], _p(y), _st()),
-            "embed fwd")
+        _call("embed fwd", _lib().lpc_t_embed_fwd, _p(codes), codes.shape[0], _p(E), E.shape[1],
+              _p(y), _st())
         ctx.save_for_backward(codes)
         ctx.shape = E.shape
         return y
@@ -167,8 +223,8 @@ class EmbedFn(torch.autograd.Function):
     def backward(ctx, dy):
         (codes,) = ctx.saved_tensors
         dE = torch.zeros(ctx.shape, device=dy.device, dtype=torch.float32)
-        _ck(_lib().lpc_t_embed_bwd(_p(codes), codes.shape[0], _p(dy.contiguous()), ctx.shape[1],
-                                   _p(dE), _st()), "embed bwd")
+        _call("embed bwd", _lib().lpc_t_embed_bwd, _p(codes), codes.shape[0], _p(dy.contiguous()),
+              ctx.shape[1], _p(dE), _st())
         return None, dE
 
 
@@ -177,8 +233,8 @@ class PReLUFn(torch.autograd.Function):
     def forward(ctx, x, a):
         x, a = x.contiguous(), a.contiguous()
         y = torch.empty_like(x)
-        _ck(_lib().lpc_t_prelu_fwd(_p(x), x.shape[0], x.shape[1], _p(a), _p(y), _st()),
-            "prelu fwd")
+        _call("prelu fwd", _lib().lpc_t_prelu_fwd, _p(x), x.shape[0], x.shape[1], _p(a), _p(y),
+              _st())
         ctx.save_for_backward(x, a)
         return y
 
@@ -187,8 +243,8 @@ class PReLUFn(torch.autograd.Function):
         x, a = ctx.saved_tensors
         dx = torch.empty_like(x)
         da = torch.zeros_like(a)
-        _ck(_lib().lpc_t_prelu_bwd(_p(x), _p(dy.contiguous()), x.shape[0], x.shape[1], _p(a),
-                                   _p(dx), _p(da), _st()), "prelu bwd")
+        _call("prelu bwd", _lib().lpc_t_prelu_bwd, _p(x), _p(dy.contiguous()), x.shape[0],
+              x.shape[1], _p(a), _p(dx), _p(da), _st())
         return dx, da
 
 
@@ -198,8 +254,8 @@ class FakeQuantFn(torch.autograd.Function):
         x = x.contiguous()
         y = torch.empty_like(x)
         mask = torch.empty(x.shape, dtype=torch.uint8, device=x.device)
-        _ck(_lib().lpc_t_fq_fwd(_p(x), x.numel(), float(s), int(z), _p(y), _p(mask), _st()),
-            "fq fwd")
+        _call("fq fwd", _lib().lpc_t_fq_fwd, _p(x), x.numel(), float(s), int(z), _p(y), _p(mask),
+              _st())
         ctx.save_for_backward(mask)
         return y
 
@@ -207,21 +263,56 @@ class FakeQuantFn(torch.autograd.Function):
     def backward(ctx, dy):
         (mask,) = ctx.saved_tensors
         dx = torch.empty_like(dy)
-        _ck(_lib().lpc_t_fq_bwd(_p(dy.contiguous()), _p(mask), dy.numel(), _p(dx), _st()),
-            "fq bwd")
+        _call("fq bwd", _lib().lpc_t_fq_bwd, _p(dy.contiguous()), _p(mask), dy.numel(), _p(dx),
+              _st())
         return dx, None, None
 
 
-class RoundBF16(torch.autograd.Function):
-    """bf16 rounding of a float32 operand with an identity gradient."""
+class PredBitsFn(torch.autograd.Function):
+    """Predictor (Eq. 7) and rate loss (supplement, Training, Eq. 16) in one
+    hand-written kernel: bits = sum over rows of -log2 softmax(W2 q(prelu(W1
+    q(F) + b1)) + b2)[code - 1]; the backward kernel recomputes the rows and
+    returns the gradients of F, both weights, both biases and the slope."""
 
     @staticmethod
-    def forward(ctx, x):
-        return x.bfloat16().float()
+    def forward(ctx, F, W1, b1, a1, W2, b2, codes, qat, bf16):
+        F = F.contiguous()
+        W1, b1, a1, W2, b2 = (t.contiguous() for t in (W1, b1, a1, W2, b2))
+        bits = torch.zeros(1, dtype=torch.float64, device=F.device)
+        _flops("pred fwd", PRED_FLOPS * F.shape[0])
+        _call("pred fwd", _lib().lpc_t_pred_fwd, _p(F), F.shape[0], _p(W1), _p(b1), _p(a1), _p(W2),
+              _p(b2), _p(codes), int(qat), int(bf16), None, _p(bits), _st())
+        ctx.save_for_backward(F, W1, b1, a1, W2, b2, codes)
+        ctx.flags = (int(qat), int(bf16))
+        return bits.float().reshape(())
 
     @staticmethod
     def backward(ctx, g):
-        return g
+        F, W1, b1, a1, W2, b2, codes = ctx.saved_tensors
+        qat, bf16 = ctx.flags
+        g = g.reshape(1).float().contiguous()
+        dF = torch.empty_like(F)
+        dW1, db1, da1 = torch.zeros_like(W1), torch.zeros_like(b1), torch.zeros_like(a1)
+        dW2, db2 = torch.zeros_like(W2), torch.zeros_like(b2)
+        _flops("pred bwd", 3.0 * PRED_FLOPS * F.shape[0])
+        _call("pred bwd", _lib().lpc_t_pred_bwd, _p(F), F.shape[0], _p(W1), _p(b1), _p(a1), _p(W2),
+              _p(b2), _p(codes), qat, bf16, _p(g), _p(dF), _p(dW1), _p(db1), _p(da1), _p(dW2),
+              _p(db2), _st())
+        return dF, dW1, db1, da1, dW2, db2, None, None, None
+
+
+def pred_logits(F, W1, b1, a1, W2, b2, qat, bf16):
+    """The predictor's float logits [N, 255] (no gradient; the float
+    inference variant), from the same kernel as PredBitsFn."""
+    F = F.detach().contiguous()
+    W1, b1, a1, W2, b2 = (t.detach().contiguous() for t in (W1, b1, a1, W2, b2))
+    N = F.shape[0]
+    out = torch.empty((N, 255), dtype=torch.float32, device=F.device)
+    bits = torch.zeros(1, dtype=torch.float64, device=F.device)
+    codes = torch.ones(N, dtype=torch.uint8, device=F.device)  # any valid code
+    _call("pred logits", _lib().lpc_t_pred_fwd, _p(F), N, _p(W1), _p(b1), _p(a1), _p(W2), _p(b2),
+          _p(codes), int(qat), int(bf16), _p(out), _p(bits), _st())
+    return out
 
 
 class FakeQuantWFn(torch.autograd.Function):
@@ -233,7 +324,7 @@ class FakeQuantWFn(torch.autograd.Function):
         w = w.contiguous()
         y = torch.empty_like(w)
         mask = torch.empty(w.shape, dtype=torch.uint8, device=w.device)
-        _ck(_lib().lpc_t_fq_w(_p(w), w.numel(), _p(y), _p(mask), _st()), "fq w")
+        _call("fq w", _lib().lpc_t_fq_w, _p(w), w.numel(), _p(y), _p(mask), _st())
         ctx.save_for_backward(mask)
         return y
 
@@ -241,8 +332,8 @@ class FakeQuantWFn(torch.autograd.Function):
     def backward(ctx, dy):
         (mask,) = ctx.saved_tensors
         dx = torch.empty_like(dy)
-        _ck(_lib().lpc_t_fq_bwd(_p(dy.contiguous()), _p(mask), dy.numel(), _p(dx), _st()),
-            "fq bwd")
+        _call("fq bwd", _lib().lpc_t_fq_bwd, _p(dy.contiguous()), _p(mask), dy.numel(), _p(dx),
+              _st())
         return dx
 
 
@@ -267,8 +358,8 @@ class Frame:
         par = torch.empty(cap, dtype=torch.int32, device="cuda")
         off = torch.empty(cap + L + 1, dtype=torch.int32, device="cuda")
         counts = np.zeros(L + 1, dtype=np.int64)
-        _ck(_lib().lpc_t_levels(_p(xyz), n, L, _p(keys), _p(codes), _p(par), _p(off),
-                                counts.ctypes.data, cap, _st()), "levels")
+        _call("levels", _lib().lpc_t_levels, _p(xyz), n, L, _p(keys), _p(codes), _p(par), _p(off),
+              counts.ctypes.data, cap, _st())
         self.N = counts.tolist()
         self.keys, self.codes, self.par, self.off, self.Y = {}, {}, {}, {}, {}
         kp = cp = op = 0
@@ -382,16 +473,14 @@ class QATModel(torch.nn.Module):
     def q(self, x):
         return FakeQuantFn.apply(x, ACT_SCALE, 0) if self.qat else x
 
-    def linear(self, x, W, b):
-        if self.bf16:  # operands rounded to bf16, products accumulated in fp32
-            x, W = RoundBF16.apply(x), RoundBF16.apply(W)
-        return torch.nn.functional.linear(x, W, b)
+    def _pred_args(self, j):
+        return (self.w(f"P1_{j}.W"), self.P(f"P1_{j}.b"), self.P(f"P1_{j}.a"),
+                self.w(f"P2_{j}.W"), self.P(f"P2_{j}.b"))
 
     def bits(self, fr: Frame) -> torch.Tensor:
         """Rate of the five network levels in bits (cross-entropy / ln 2)."""
-        def ce(logits, d):
-            return torch.nn.functional.cross_entropy(logits, fr.Y[d] - 1,
-                                                     reduction="sum") / math.log(2.0)
+        def ce(j, F, d):
+            return PredBitsFn.apply(F, *self._pred_args(j), fr.codes[d], self.qat, self.bf16)
         return self._levels(fr, ce, self.recompute)
 
     def level_logits(self, fr: Frame) -> dict:
@@ -399,9 +488,9 @@ class QATModel(torch.nn.Module):
         float inference variant)."""
         out = {}
 
-        def keep(logits, d):
-            out[d] = logits
-            return logits.new_zeros(())
+        def keep(j, F, d):
+            out[d] = pred_logits(F, *self._pred_args(j), self.qat, self.bf16)
+            return F.new_zeros(())
         self._levels(fr, keep, False)
         return out
 
@@ -410,10 +499,6 @@ class QATModel(torch.nn.Module):
 
         def prelu(x, name):
             return PReLUFn.apply(x, P(name))
-
-        def pred(j, F):
-            h = prelu(self.linear(q(F), w(f"P1_{j}.W"), P(f"P1_{j}.b")), f"P1_{j}.a")
-            return self.linear(q(h), w(f"P2_{j}.W"), P(f"P2_{j}.b"))
 
         def upl(name, d, x):  # V_{d-1} -> V_d
             y = UpFn.apply(q(x), fr.par[d], fr.keys[d], fr.off[d - 1], w(name + ".W"),
@@ -436,13 +521,13 @@ class QATModel(torch.nn.Module):
 
         def level0():
             Fb = upl("UP_0", b, emb("E_0", b - 1))
-            return Fb, head(pred(0, Fb), b)
+            return Fb, head(0, Fb, b)
 
         def shallow(j, Fp):  # with XFP, b < d <= t (Eq. 8-9)
             d = b + j
             S = resblock(j, d - 1, Fp)
             F = upl(f"UP_{j}", d, torch.cat([S, emb(f"E_{j}", d - 1)], 1))
-            return F, head(pred(j, F), d)
+            return F, head(j, F, d)
 
         def extracted(j, Ft):
             # features of Y_{d-1} re-densified to V_k; with XFP fused with
@@ -460,7 +545,7 @@ class QATModel(torch.nn.Module):
             for k in range(d - k0):
                 x = torch.cat([H, emb(f"E_{j}_{k}", k0 + k)], 1) if arch == 0 else H
                 H = upl(f"UP_{j}_{k}", k0 + k + 1, x)
-            return head(pred(j, H), d)
+            return head(j, H, d)
 
         # with recompute, each relative level keeps only its outputs; its
         # activations are recomputed in the backward pass

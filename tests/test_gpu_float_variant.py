@@ -59,3 +59,36 @@ def test_float_cdf_closed_forms(mods):
     assert f0[0] == 258 and (f0[1:] == 257).all()
     f1 = np.diff(np.concatenate([[0], t[1, :254], [65536]]))
     assert f1[17] == 65536 - 254 and (np.delete(f1, 17) == 1).all()
+
+
+def test_float_stream_fails_across_devices_integer_stream_does_not(mods):
+    """The paper's cross-platform failure (Sec. 1, Fig. 1b/c) shown on the
+    float variant of the 64-beam frame: a stream range coded with the tables
+    of the GPU's float softmax decodes exactly with those tables, but the
+    tables the CPU's softmax makes from the very same logits decode it wrong
+    (a corrupt stream or other occupancy codes, so another cloud).  The
+    integer path's stream of the same frame is the CPU oracle's byte for
+    byte, and the oracle decodes it to the GPU decoder's voxels."""
+    lpc, TR, FV = mods
+    spec = synth.C2
+    xyz = synth.make_frame(spec)
+    L, n = spec.L, xyz.shape[0]
+    fr = TR.Frame(torch.from_numpy(xyz).cuda(), L)
+    model = TR.QATModel(synth.twin_params(0), qat=False, bf16=False)
+    with torch.no_grad():
+        logits = model.level_logits(fr)
+    r = FV.cross_device_decode(logits, fr.codes)
+    print(r)
+    assert r["same_device_round_trip"]
+    levels = r["levels"].values()
+    assert sum(v["rows_differing"] for v in levels) > 0
+    assert r["cloud_differs"]
+    assert sum(v["symbols_wrong"] + v["substreams_reported_corrupt"] for v in levels) > 0
+    for v in levels:  # where every row agrees, the other device decodes it too
+        if v["rows_differing"] == 0:
+            assert v["substreams_failing"] == 0
+    blob = synth.make_blob()
+    cod = lpc.Codec(blob, L, n, chunk=256)
+    data = cod.encode(torch.from_numpy(xyz).cuda())
+    assert data == O.encode(blob, xyz, L, 256)
+    assert np.array_equal(cod.decode(data).cpu().numpy(), O.decode(blob, data, n))

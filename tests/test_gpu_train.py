@@ -134,6 +134,40 @@ def test_down_fwd_bwd(frames, bf16):
     assert _rel(db, dy.double().sum(0)) < 1e-5
 
 
+@pytest.mark.parametrize("qat,bf16", [(0, 0), (1, 0), (0, 1), (1, 1)])
+def test_pred_bits_fwd_bwd(frames, qat, bf16):
+    """The fused predictor + rate-loss kernels against the FP64 reference's
+    predictor (two linear layers, PReLU, fake quantisers, cross-entropy in
+    bits), bits and every gradient; the logits the forward can write out
+    against the reference logits."""
+    from paper_2603_25260_b300 import train as G
+    ref, gpu, _ = frames
+    d = ref.t + 1
+    N = len(ref.keys[d])
+    g = torch.Generator().manual_seed(40 + 2 * qat + bf16)
+    F = torch.randn(N, 32, generator=g) * 2
+    W1 = torch.randn(32, 32, generator=g) / 4
+    b1 = torch.randn(32, generator=g) / 4
+    a1 = torch.rand(32, generator=g) / 2
+    W2 = torch.randn(255, 32, generator=g) / 3
+    b2 = torch.randn(255, generator=g)
+    ins = [t.cuda().requires_grad_() for t in (F, W1, b1, a1, W2, b2)]
+    bits = G.PredBitsFn.apply(*ins, gpu.codes[d], qat, bf16)
+    grads = torch.autograd.grad(bits * 0.37, ins)
+    rf = [t.double().requires_grad_() for t in (F, W1, b1, a1, W2, b2)]
+    q = (lambda x: T.fq(x, 1 / 32)) if qat else (lambda x: x)
+    r = T.rb if bf16 else (lambda x: x)
+    h = T.prelu(T.linear(r(q(rf[0])), r(rf[1]), rf[2]), rf[3])
+    lg = T.linear(r(q(h)), r(rf[4]), rf[5])
+    ce = torch.nn.functional.cross_entropy(lg, ref.Y[d] - 1, reduction="sum") / np.log(2.0)
+    gr = torch.autograd.grad(ce * 0.37, rf)
+    assert float(bits) == pytest.approx(float(ce), rel=1e-5)
+    for name, a, b in zip(("F", "W1", "b1", "a1", "W2", "b2"), grads, gr):
+        assert _rel(a, b) < 1e-5, name
+    lgs = G.pred_logits(*ins, qat, bf16)
+    assert _rel(lgs, lg) < 1e-6
+
+
 def test_embed_prelu_fq(frames):
     from paper_2603_25260_b300 import train as G
     ref, gpu, _ = frames
@@ -218,20 +252,21 @@ def _flat(g):
 def test_model_gradients_bf16(frames):
     """bf16 mode against the FP64 reference that rounds the same operands.
 
-    What separates them is accumulation order and the operands whose fp32 and
-    FP64 values round to different bf16 neighbours.  Those flips make a bf16
-    gradient sensitive at the percent level: on the FP64 reference itself a
-    1e-6 relative change of the parameters moves single parameters' gradients
-    by up to 2% and the whole gradient by 0.2% (norm-relative).  The bounds sit
-    at about 2.5x that floor; against the unrounded FP64 gradients the whole
-    gradient must agree to 2e-2."""
+    The 2e-2 bound for bf16 holds per parameter tensor (norm-relative) against
+    the FP64 gradients of the same bf16 roundings, and over the whole
+    gradient against the unrounded FP64 gradients.  What separates the GPU
+    from that reference is accumulation order and the operands whose fp32 and
+    FP64 values round to different bf16 neighbours; those flips make single
+    tensors' gradients move at the percent level (on the FP64 reference
+    itself a 1e-6 relative change of the parameters moves them by up to 2%),
+    the whole gradient at 0.2%."""
     ref, gpu, _ = frames
     params = T.init_params(5)
     bits_r, gr = _ref_grads(ref, params, qat=False, bf16=True)
     bits_g, gg = _model_grads(gpu, params, qat=False, bf16=1)
     assert bits_g == pytest.approx(bits_r, rel=1e-5)
     name, err = _worst(gg, gr)
-    assert err < 5e-2, (name, err)
+    assert err < 2e-2, (name, err)
     assert _rel(_flat(gg), _flat(gr)) < 5e-3
     bits_x, gx = _ref_grads(ref, params, qat=False)
     assert bits_g == pytest.approx(bits_x, rel=5e-3)

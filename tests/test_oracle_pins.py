@@ -358,6 +358,49 @@ def test_rc_cdf_round_trip_and_length(n, seed):
     assert np.array_equal(O.rc_decode_cdf(cdf, data), syms)
 
 
+@pytest.mark.parametrize("n,seed", [(1, 11), (40, 12), (3000, 13)])
+def test_rc_flush_costs_at_most_a_byte(n, seed):
+    """Version 3 flush: the coded value is the one with the most trailing
+    zero bits inside the final interval, and its trailing zero bytes are left
+    out, so a substream costs at most one byte (plus one bit) over the ideal
+    length sum -log2(f/2^16), besides the table coder's truncation of
+    range / 2^16 (below 2^-8 relative per symbol, so under 0.006 bits); and
+    the stream never ends in a zero byte that could have been left out."""
+    cdf = _random_cdf_rows(n, seed)
+    rng = np.random.Generator(np.random.PCG64(seed + 1))
+    worst = -1e9
+    for rep in range(20):
+        syms = np.zeros(n, dtype=np.uint8)
+        ideal = 0.0
+        for i in range(n):
+            f = _freqs_from_row(cdf[i])
+            syms[i] = rng.choice(255, p=f / 65536.0)
+            ideal += -math.log2(f[syms[i]] / 65536.0)
+        data = O.rc_encode_cdf(cdf, syms)
+        assert np.array_equal(O.rc_decode_cdf(cdf, data), syms)
+        worst = max(worst, 8 * len(data) - ideal - 0.006 * n)
+        assert len(data) == 0 or data[-1] != 0
+    assert worst <= 9.0, worst
+
+
+def test_rc_empty_substream_is_empty():
+    # no symbols: the value 0 lies in the initial interval and every byte of
+    # it is a zero the decoder supplies
+    assert O.rc_encode_cdf(np.zeros((0, 256), np.uint16), np.zeros(0, np.uint8)) == b""
+    assert O.rc_encode_adaptive(np.zeros(0, np.uint8)) == b""
+
+
+def test_rc_reads_at_most_four_bytes_past_the_end():
+    """The decoder supplies at most four zero bytes after a substream's end;
+    a stream that needs more is corrupt (a cut stream is detected)."""
+    cdf = _random_cdf_rows(4000, 17)
+    syms = RNG.integers(0, 255, size=4000).astype(np.uint8)
+    data = O.rc_encode_cdf(cdf, syms)
+    for cut in (5, 9, 64):
+        with pytest.raises(O.OracleError):
+            O.rc_decode_cdf(cdf, data[:-cut])
+
+
 def test_rc_extreme_symbols():
     lut = synth.exp_lut()
     lg = np.full((3000, 255), -128, np.int8)
@@ -390,11 +433,11 @@ def test_rc_adaptive_round_trip(n, seed):
 
 def _adaptive_ideal_bits(syms):
     """Ideal code length, in bits, of the coarse-level frequency model
-    (supplement, Detailed Model Structure: coarse levels coded by their
-    symbol frequencies; reading Q4): every count starts at 1, the coded
-    symbol's count grows by 32, and once the total exceeds 2^16 every count
-    is halved, rounding up.  Each symbol costs -log2(f_s / total) under the
-    counts seen before it."""
+    (supplement, Detailed Model Structure: coarse levels are coded by their
+    symbol frequencies; the update rule is this codec's reading): every count
+    starts at 1, the coded symbol's count grows by 32, and once the total
+    exceeds 2^16 every count is halved, rounding up.  Each symbol costs
+    -log2(f_s / total) under the counts seen before it."""
     f = [1] * 255
     total = 255
     bits = 0.0
@@ -534,15 +577,16 @@ def _varint(data, pos):
 
 
 def test_stream_header_coarse_sizes():
-    """Stream version 2: after the chunk lengths the header lists the coarse
+    """Stream version 3: after the chunk lengths the header lists the coarse
     levels' sizes N_1 .. N_{b-1} (those of the octree of the frame), and the
     substream table holds ceil(N_d / 4096) substreams per coarse level before
-    the network levels' chunks."""
+    the network levels' chunks; the lengths (zigzag varints of the difference
+    to the previous length) add up to the rest of the stream exactly."""
     blob = synth.make_blob()
     xyz = synth.random_cloud(60000, 17, 71)
     L, chunk = 17, 1000
     data = O.encode(blob, xyz, L, chunk)
-    assert data[:4] == b"LPC1" and data[4] == 2
+    assert data[:4] == b"LPC1" and data[4] == 3
     keys, codes = O.build_levels(xyz, L)
     b = L - 5
     c, pos = _varint(data, 18)
@@ -558,6 +602,13 @@ def test_stream_header_coarse_sizes():
         sum(-(-len(keys[d]) // chunk) for d in range(b, L))
     assert nsub == want
     assert max(len(keys[d]) for d in range(b)) > kc  # a level in several chunks
+    prev, total = 0, 0
+    for _ in range(nsub):
+        z, pos = _varint(data, pos)
+        prev += z >> 1 if z % 2 == 0 else -((z + 1) >> 1)
+        assert prev >= 0
+        total += prev
+    assert pos + total == len(data)
 
 
 def test_stream_header_bad_coarse_size_is_corrupt():
