@@ -89,7 +89,7 @@ const char* codec_last_error(codec_t* codec);
 /* Encode one frame.  d_xyz: device int32 [n][3].  The bitstream goes to the
  * caller's host buffer h_out of `cap` bytes; *out_len receives its length.
  * Stream (version 3): "LPC1", version, L, b, t, C, flags, the blob's hash,
- * then varints: network chunk, coarse chunk (4096), the coarse levels' sizes
+ * then varints: network chunk, coarse chunk (512), the coarse levels' sizes
  * N_1 .. N_{b-1}, the substream count, and each substream's length as the
  * zigzag-coded difference to the previous one's; then the substreams: the
  * coarse levels in coarse chunks (adaptive symbol frequencies, a fresh model
@@ -179,7 +179,10 @@ int codec_set_tuning(codec_t* codec, const int* variants);
  * [0] octree ready, [1] launches issued, [2] coding done, [3] encode total;
  * [4] coarse levels decoded, [5] network issue, [6] level decoding,
  * [7] expansion issue (sums over levels), [8] decode total; encode again:
- * [9] coarse keys on the host, [10] device work done, [11] host coding done. */
+ * [9] coarse keys on the host, [10] device work done, [11] host coding done;
+ * decode again: [12] streams parsed and sent to the device, [13] coarse
+ * substreams decoded, [14] coarse sizes checked (then [4] after their
+ * expansion on the device). */
 int codec_last_phases(codec_t* codec, double* us, int n);
 
 /* Number of CUDA kernels this library has launched in this process so far

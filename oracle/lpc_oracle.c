@@ -992,7 +992,7 @@ int or_probs_level(const void* blob, size_t blob_len, const int32_t* xyz, int64_
  * chunks of `coarse chunk` nodes (adaptive, a fresh model each), then for
  * d = b..L-1 the level's Morton-ordered nodes in chunks of `chunk`.  With
  * the sizes in the header every coarse chunk decodes on its own. */
-#define COARSE_CHUNK 4096
+#define COARSE_CHUNK 512
 
 typedef struct {
   uint8_t* p;

@@ -10,7 +10,7 @@
 // 5..1, so relative level j = d - b is height 5 - j for every frame, whatever
 // its depth L_f: one launch sequence per relative level codes every frame.
 // The coarse levels (depth < b) are built on the device; their codes are
-// range coded on host threads with an adaptive model, in chunks of 4096
+// range coded on host threads with an adaptive model, in chunks of 512
 // nodes that each code and decode on their own.
 #include "codec.h"
 
@@ -121,6 +121,18 @@ void Pool::submit(int group, std::function<void()> task) {
   if (spin_.load(std::memory_order_relaxed) == 0) cv_.notify_one();
 }
 
+void Pool::run_indexed(int64_t n, const std::function<void(int64_t)>& fn) {
+  if (n <= 0) return;
+  std::atomic<int64_t> next{0};
+  auto runner = [&] {
+    for (int64_t i = next.fetch_add(1); i < n; i = next.fetch_add(1)) fn(i);
+  };
+  const int64_t helpers = std::min<int64_t>(n - 1, (int64_t)th_.size());
+  for (int64_t k = 0; k < helpers; k++) submit(kIndexedGroup, runner);
+  runner();
+  wait(kIndexedGroup);
+}
+
 void Pool::wait(int group) {
   std::unique_lock<std::mutex> lk(mu_);
   while (pending_[group] > 0) {
@@ -137,7 +149,14 @@ void Pool::wait(int group) {
 // of the codes of level d - 1).
 namespace {
 
-constexpr int kMaxCoarseTasks = 64;
+constexpr int kMaxCoarseTasks = 512;
+constexpr size_t kCopyPart = 64 << 10;  // host copies split for the pool
+
+struct HostCopy {
+  uint8_t* dst;
+  const uint8_t* src;
+  size_t len;
+};
 constexpr int kSplitFrames = 8;  // decode batches of at least this many frames in two groups
 
 void coarse_alloc(Frame& F) {
@@ -189,7 +208,7 @@ void coarse_frame(Frame& F, std::atomic<int>& status) {
 namespace {
 
 constexpr int kHdr = 18;
-constexpr int64_t kCoarseChunk = 4096;
+constexpr int64_t kCoarseChunk = 512;
 // arena bytes of a coarse level of n nodes: every chunk's coded bound
 size_t coarse_level_bound(int64_t n) {
   return 2 * (size_t)n + 8 * (size_t)((n + kCoarseChunk - 1) / kCoarseChunk);
@@ -1428,6 +1447,10 @@ int Codec::decode(int nf, const uint8_t* const* in, const size_t* lens, int32_t*
     // device coding: every frame's bytes go to the device while the host
     // decodes the coarse levels
     in_base_.assign(nd, 0);
+    std::vector<HostCopy> cps;
+    void* up_dst = nullptr;
+    const void* up_src = nullptr;
+    size_t up_len = 0;
     if (dev_rc_) {
       size_t tot = 0;
       for (int f = 0; f < nd; f++) {
@@ -1437,9 +1460,17 @@ int Codec::decode(int nf, const uint8_t* const* in, const size_t* lens, int32_t*
       uint8_t* hb = static_cast<uint8_t*>(hgrow(h_rcbuf_, tot));
       uint8_t* db = static_cast<uint8_t*>(dgrow(d_rcbuf_, tot));
       if (!hb || !db) return fail(LPC_CUDA_ERROR, "decode: range coder buffer allocation failed");
-      for (int f = 0; f < nd; f++) memcpy(hb + in_base_[f], fr_[f].in, fr_[f].len);
-      cudaMemcpyAsync(db, hb, tot, cudaMemcpyHostToDevice, st_);
+      // the copies into the pinned staging buffer run on the pool beside the
+      // coarse decoding (parts of at most 64 KiB); the upload follows it
+      for (int f = 0; f < nd; f++)
+        for (size_t o = 0; o < fr_[f].len; o += kCopyPart)
+          cps.push_back(HostCopy{hb + in_base_[f] + o, fr_[f].in + o,
+                                 std::min(kCopyPart, fr_[f].len - o)});
+      up_dst = db;
+      up_src = hb;
+      up_len = tot;
     }
+    stats.phase_us[12] = now_us() - t0;
     // coarse levels (depths 0..b-1): adaptive-model decoding on the host
     std::atomic<int> cstat{0};
     if (!coarse_ready) {
@@ -1466,9 +1497,14 @@ int Codec::decode(int nf, const uint8_t* const* in, const size_t* lens, int32_t*
         auto run = [&](const Job& J) {
           if (!coarse_chunk(fr_[J.f], J.d, J.k, J.sub)) cstat = LPC_CORRUPT_STREAM;
         };
-        for (size_t i = 1; i < js.size(); i++) pool_->submit(0, [&, i] { run(js[i]); });
-        if (!js.empty()) run(js[0]);
-        pool_->wait(0);
+        // the coarse chunks first (the critical path), then the copies
+        const int64_t nj = (int64_t)js.size();
+        pool_->run_indexed(nj + (int64_t)cps.size(), [&](int64_t i) {
+          if (i < nj) run(js[i]);
+          else memcpy(cps[i - nj].dst, cps[i - nj].src, cps[i - nj].len);
+        });
+        cps.clear();
+        stats.phase_us[13] = now_us() - t0;
         for (int f = 0; f < nd && !cstat; f++)
           if (!coarse_consistent(fr_[f])) cstat = LPC_CORRUPT_STREAM;
       } else {
@@ -1494,6 +1530,11 @@ int Codec::decode(int nf, const uint8_t* const* in, const size_t* lens, int32_t*
       if (async_stat == LPC_CAPACITY) return fail(LPC_CAPACITY, "decode: frame exceeds max_points");
     }
     if (after_coarse) after_coarse();
+    pool_->run_indexed((int64_t)cps.size(), [&](int64_t i) {
+      memcpy(cps[i].dst, cps[i].src, cps[i].len);
+    });
+    if (up_len) cudaMemcpyAsync(up_dst, up_src, up_len, cudaMemcpyHostToDevice, st_);
+    stats.phase_us[14] = now_us() - t0;
     if (int s = expand_coarse_device(nd)) return s;
     stats.phase_us[4] = now_us() - t0;
     for (int i = 5; i < 9; i++) stats.phase_us[i] = 0;

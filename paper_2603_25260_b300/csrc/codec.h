@@ -29,10 +29,15 @@ class Pool {
   ~Pool();
   void submit(int group, std::function<void()> task);
   void wait(int group);
+  // fn(0) .. fn(n - 1) on the workers and the calling thread, each index
+  // once, claimed in order from a shared counter (no lock per index); returns
+  // when every index is done
+  void run_indexed(int64_t n, const std::function<void(int64_t)>& fn);
   // workers 0..n-1 poll the queue instead of sleeping (0: all sleep)
   void set_spin(int n);
   int size() const { return (int)th_.size() + 1; }
-  static constexpr int kGroups = 4;
+  static constexpr int kGroups = 5;
+  static constexpr int kIndexedGroup = 4;
 
  private:
   void loop(int idx);

@@ -161,7 +161,7 @@ def test_pred_bits_fwd_bwd(frames, qat, bf16):
     lg = T.linear(r(q(h)), r(rf[4]), rf[5])
     ce = torch.nn.functional.cross_entropy(lg, ref.Y[d] - 1, reduction="sum") / np.log(2.0)
     gr = torch.autograd.grad(ce * 0.37, rf)
-    assert float(bits) == pytest.approx(float(ce), rel=1e-5)
+    assert float(bits.detach()) == pytest.approx(float(ce), rel=1e-5)
     for name, a, b in zip(("F", "W1", "b1", "a1", "W2", "b2"), grads, gr):
         assert _rel(a, b) < 1e-5, name
     lgs = G.pred_logits(*ins, qat, bf16)

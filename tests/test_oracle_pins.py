@@ -579,7 +579,7 @@ def _varint(data, pos):
 def test_stream_header_coarse_sizes():
     """Stream version 3: after the chunk lengths the header lists the coarse
     levels' sizes N_1 .. N_{b-1} (those of the octree of the frame), and the
-    substream table holds ceil(N_d / 4096) substreams per coarse level before
+    substream table holds ceil(N_d / 512) substreams per coarse level before
     the network levels' chunks; the lengths (zigzag varints of the difference
     to the previous length) add up to the rest of the stream exactly."""
     blob = synth.make_blob()
@@ -591,7 +591,7 @@ def test_stream_header_coarse_sizes():
     b = L - 5
     c, pos = _varint(data, 18)
     kc, pos = _varint(data, pos)
-    assert (c, kc) == (chunk, 4096)
+    assert (c, kc) == (chunk, 512)
     sizes = []
     for _ in range(1, b):
         v, pos = _varint(data, pos)
