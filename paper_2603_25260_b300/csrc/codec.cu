@@ -157,7 +157,6 @@ struct HostCopy {
   const uint8_t* src;
   size_t len;
 };
-constexpr int kSplitFrames = 8;  // decode batches of at least this many frames in two groups
 
 void coarse_alloc(Frame& F) {
   F.coarse.assign(F.b, {});
@@ -274,9 +273,9 @@ Codec::~Codec() {
   for (auto e : pev_) cudaEventDestroy(e);
   if (dmem_) cudaFree(dmem_);
   if (hmem_) cudaFreeHost(hmem_);
-  for (Buf* b : {&d_rcck_, &d_rclen_, &d_rcbuf_})
+  for (Buf* b : {&d_rcck_, &d_rclen_, &d_rcbuf_, &d_subfr_, &d_subs_, &d_nck_, &d_cck_, &d_cchk_})
     if (b->p) cudaFree(b->p);
-  for (Buf* b : {&h_rcck_, &h_rclen_, &h_rcbuf_, &h_ccodes_})
+  for (Buf* b : {&h_rcck_, &h_rclen_, &h_rcbuf_, &h_ccodes_, &h_subfr_, &h_subs_, &h_cck_, &h_cchk_})
     if (b->p) cudaFreeHost(b->p);
   model_free(M_);
 }
@@ -1471,6 +1470,26 @@ int Codec::decode(int nf, const uint8_t* const* in, const size_t* lens, int32_t*
       up_len = tot;
     }
     stats.phase_us[12] = now_us() - t0;
+    if (dev_rc_) {
+      // device range coding: the stream goes up first and the coarse levels
+      // are decoded there too (every coarse chunk of every frame at once)
+      pool_->run_indexed((int64_t)cps.size(), [&](int64_t i) {
+        memcpy(cps[i].dst, cps[i].src, cps[i].len);
+      });
+      cudaMemcpyAsync(up_dst, up_src, up_len, cudaMemcpyHostToDevice, st_);
+      stats.phase_us[13] = now_us() - t0;
+      if (int s = expand_coarse_device(nd, true)) return s;
+      stats.phase_us[14] = stats.phase_us[4] = now_us() - t0;
+      for (int i = 5; i < 9; i++) stats.phase_us[i] = 0;
+      if (int s = decode_net_device(nd, n_out, dev, caps)) return s;
+      stats.L = fr_[0].L;
+      for (int d = 0; d < fr_[0].b; d++) stats.N[d] = fr_[0].cN[d];
+      for (int h = 0; h < kHeights; h++) stats.N[fr_[0].L - h] = fr_[0].cnt[h];
+      stats.host_us = now_us() - t0;
+      stats.phase_us[8] = stats.host_us;
+      prof_collect();
+      return LPC_OK;
+    }
     // coarse levels (depths 0..b-1): adaptive-model decoding on the host
     std::atomic<int> cstat{0};
     if (!coarse_ready) {
@@ -1535,7 +1554,7 @@ int Codec::decode(int nf, const uint8_t* const* in, const size_t* lens, int32_t*
     });
     if (up_len) cudaMemcpyAsync(up_dst, up_src, up_len, cudaMemcpyHostToDevice, st_);
     stats.phase_us[14] = now_us() - t0;
-    if (int s = expand_coarse_device(nd)) return s;
+    if (int s = expand_coarse_device(nd, false)) return s;
     stats.phase_us[4] = now_us() - t0;
     for (int i = 5; i < 9; i++) stats.phase_us[i] = 0;
     if (dev_rc_) {
@@ -1667,94 +1686,93 @@ int Codec::decode(int nf, const uint8_t* const* in, const size_t* lens, int32_t*
     prof_collect();
     return LPC_OK;
   };
-  // Many frames: two groups, the frames with the least coarse data first,
-  // about a third of it, so the host decodes the other group's coarse
-  // levels while the device decodes the first group's network levels.
-  if (!dev_rc_ || (int)dev.size() < kSplitFrames) return run_group(dev, false, nullptr);
-  std::vector<std::pair<uint64_t, int>> by(dev.size());
-  uint64_t all_bytes = 0;
-  for (size_t k = 0; k < dev.size(); k++) {
-    uint64_t bytes = 0;
-    bytes = all[dev[k]].coarse_bytes();
-    by[k] = {bytes, dev[k]};
-    all_bytes += bytes;
-  }
-  std::sort(by.begin(), by.end());
-  std::vector<int> ga, gb;
-  uint64_t acc = 0;
-  for (auto& e : by) {
-    if (ga.empty() || (acc < all_bytes * 3 / 10 && gb.empty())) {
-      ga.push_back(e.second);
-      acc += e.first;
-    } else {
-      gb.push_back(e.second);
-    }
-  }
-  std::sort(ga.begin(), ga.end());
-  std::sort(gb.begin(), gb.end());
-  if (gb.empty()) return run_group(ga, false, nullptr);
-  auto start_b = [&] {
-    std::vector<std::pair<uint64_t, int>> order;
-    for (int i : gb) {
-      order.push_back({all[i].coarse_bytes(), i});
-    }
-    std::sort(order.begin(), order.end(), [](const auto& x, const auto& y) {
-      return x.first != y.first ? x.first > y.first : x.second < y.second;
-    });
-    for (auto& e : order) pool_->submit(3, [&all, &async_stat, i = e.second] {
-      coarse_frame(all[i], async_stat);
-    });
-  };
-  const int sa = run_group(ga, false, start_b);
-  if (sa) {
-    pool_->wait(3);
-    return sa;
-  }
-  const double pa[16] = {stats.phase_us[0], stats.phase_us[1], stats.phase_us[2],
-                         stats.phase_us[3], stats.phase_us[4], stats.phase_us[5],
-                         stats.phase_us[6], stats.phase_us[7]};
-  const int sb = run_group(gb, true, nullptr);
-  for (int i = 5; i < 8; i++) stats.phase_us[i] += pa[i];
-  stats.phase_us[4] = pa[4];
-  return sb;
+  return run_group(dev, false, nullptr);
 }
 
 // Coarse codes of every frame to the device, arranged by height (height h is
 // depth L_f - h; above a frame's root the root is carried up with code 1),
 // and expanded from the roots down to V_{b-1} (height 6) on the device.
-int Codec::expand_coarse_device(int nd) {
+int Codec::expand_coarse_device(int nd, bool on_device) {
   int top = kHeights - 1;
   for (int f = 0; f < nd; f++) top = std::max(top, fr_[f].L);
-  std::vector<int64_t> hcnt(top + 1, 0), hoff(top + 1, 0);
+  // rows by height (frames in order; a frame shallower than the height
+  // carries its root up as one node with code 1), from the headers' sizes
+  std::vector<int64_t> hcnt(top + 1, 0), hoff(top + 1, 0), fbase((size_t)(top + 1) * nd, 0);
   size_t tot = 0;
   for (int h = top; h >= kHeights - 1; h--) {
     hoff[h] = (int64_t)tot;
     for (int f = 0; f < nd; f++) {
       const Frame& F = fr_[f];
-      hcnt[h] += h > F.L ? 1 : (int64_t)F.coarse[F.L - h].size();
+      fbase[(size_t)h * nd + f] = hcnt[h];
+      hcnt[h] += h > F.L ? 1 : F.cN[F.L - h];
     }
     tot += (size_t)hcnt[h];
     if (hcnt[h] > P_) return fail(LPC_CAPACITY, "decode: batch exceeds the codec's capacity");
   }
-  uint8_t* hc = static_cast<uint8_t*>(hgrow(h_ccodes_, tot + 16));
-  if (!hc) return fail(LPC_CUDA_ERROR, "decode: pinned allocation failed");
-  for (int h = top; h >= kHeights - 1; h--) {
-    uint8_t* o = hc + hoff[h];
-    for (int f = 0; f < nd; f++) {
-      Frame& F = fr_[f];
-      if (h == kHeights - 1) F.off[6] = o - (hc + hoff[h]);
-      if (h > F.L) {
-        *o++ = 1;
-      } else {
-        const std::vector<uint8_t>& Y = F.coarse[F.L - h];
-        memcpy(o, Y.data(), Y.size());
-        o += Y.size();
-      }
-      if (h == kHeights - 1) F.cnt[6] = (o - (hc + hoff[h])) - F.off[6];
-    }
+  for (int f = 0; f < nd; f++) {
+    Frame& F = fr_[f];
+    F.off[6] = fbase[(size_t)(kHeights - 1) * nd + f];
+    F.cnt[6] = F.cN[F.L - (kHeights - 1)];
   }
-  // height-6 codes also on the host (the host-coding path counts from them)
-  memcpy(h_codes_ + 6 * P_, hc + hoff[kHeights - 1], (size_t)hcnt[kHeights - 1]);
+  auto dev_codes = [&](int h) { return h == kHeights - 1 ? code_[6] : coarse_codes(h); };
+  if (on_device) {
+    // every coarse chunk of every frame decoded by one launch straight into
+    // the arrays by height; then the level sizes checked against the codes
+    int64_t nck = 0, nchk = 0;
+    for (int f = 0; f < nd; f++) {
+      const Frame& F = fr_[f];
+      nck += (int64_t)F.nco + std::max(0, top - F.L);
+      nchk += F.b - 1;
+    }
+    auto* hc = static_cast<CoarseChunk*>(hgrow(h_cck_, sizeof(CoarseChunk) * (size_t)nck));
+    auto* dc = static_cast<CoarseChunk*>(dgrow(d_cck_, sizeof(CoarseChunk) * (size_t)nck));
+    auto* hk = static_cast<CoarseCheck*>(hgrow(h_cchk_, sizeof(CoarseCheck) * (size_t)nchk + 16));
+    auto* dk = static_cast<CoarseCheck*>(dgrow(d_cchk_, sizeof(CoarseCheck) * (size_t)nchk + 16));
+    if (!hc || !dc || !hk || !dk) return fail(LPC_CUDA_ERROR, "decode: coarse table allocation failed");
+    int64_t k = 0, q = 0;
+    for (int f = 0; f < nd; f++) {
+      const Frame& F = fr_[f];
+      for (int h = top; h > F.L; h--)
+        hc[k++] = CoarseChunk{0, 0, dev_codes(h) + fbase[(size_t)h * nd + f], 1, 1};
+      size_t sub = 0;
+      for (int d = 0; d < F.b; d++) {
+        const int h = F.L - d;
+        uint8_t* row0 = dev_codes(h) + fbase[(size_t)h * nd + f];
+        for (int64_t c0 = 0; c0 < F.cN[d]; c0 += F.kc, sub++) {
+          if (sub >= F.slen.size()) return fail(LPC_CORRUPT_STREAM, "decode: missing substream");
+          hc[k++] = CoarseChunk{in_base_[f] + (int64_t)F.soff[sub], (int64_t)F.slen[sub], row0 + c0,
+                                (int32_t)std::min<int64_t>(F.kc, F.cN[d] - c0), 0};
+        }
+        if (d + 1 < F.b) hk[q++] = CoarseCheck{row0, F.cN[d], F.cN[d + 1]};
+      }
+    }
+    cudaMemcpyAsync(dc, hc, sizeof(CoarseChunk) * (size_t)k, cudaMemcpyHostToDevice, st_);
+    cudaMemcpyAsync(dk, hk, sizeof(CoarseCheck) * (size_t)q, cudaMemcpyHostToDevice, st_);
+    pbeg(kFamCoder);
+    launch_coarse_decode(dc, (int)k, static_cast<const uint8_t*>(d_rcbuf_.p), d_err_, st_);
+    pend(kFamCoder, 2.0 * (double)tot, 0);
+    launch_coarse_check(dk, (int)q, d_err_, st_);
+  } else {
+    uint8_t* hc = static_cast<uint8_t*>(hgrow(h_ccodes_, tot + 16));
+    if (!hc) return fail(LPC_CUDA_ERROR, "decode: pinned allocation failed");
+    for (int h = top; h >= kHeights - 1; h--) {
+      uint8_t* o = hc + hoff[h];
+      for (int f = 0; f < nd; f++) {
+        const Frame& F = fr_[f];
+        if (h > F.L) {
+          *o++ = 1;
+        } else {
+          const std::vector<uint8_t>& Y = F.coarse[F.L - h];
+          memcpy(o, Y.data(), Y.size());
+          o += Y.size();
+        }
+      }
+    }
+    // height-6 codes also on the host (the host-coding path counts from them)
+    memcpy(h_codes_ + 6 * P_, hc + hoff[kHeights - 1], (size_t)hcnt[kHeights - 1]);
+    for (int h = top; h >= kHeights - 1; h--)
+      cudaMemcpyAsync(dev_codes(h), hc + hoff[h], (size_t)hcnt[h], cudaMemcpyHostToDevice, st_);
+  }
   N_[6] = hcnt[kHeights - 1];
   h_N_[6] = N_[6];
   // roots (one per frame) at the top height, then expansions down to 6
@@ -1765,10 +1783,6 @@ int Codec::expand_coarse_device(int nd) {
   cudaMemcpyAsync(top_keys, h_keys6_, 8 * (size_t)nd, cudaMemcpyHostToDevice, st_);
   if (top == kHeights - 1)
     cudaMemcpyAsync(d_N_ + 6, h_cN_ + top, 8, cudaMemcpyHostToDevice, st_);
-  for (int h = top; h >= kHeights; h--)
-    cudaMemcpyAsync(coarse_codes(h), hc + hoff[h], (size_t)hcnt[h], cudaMemcpyHostToDevice, st_);
-  cudaMemcpyAsync(code_[6], hc + hoff[kHeights - 1], (size_t)hcnt[kHeights - 1],
-                  cudaMemcpyHostToDevice, st_);
   for (int h = kHeights; h <= top; h++) h_cN_[h] = hcnt[h];
   cudaMemcpyAsync(d_cN_ + kHeights, h_cN_ + kHeights, 8 * (size_t)(top - kHeights + 1),
                   cudaMemcpyHostToDevice, st_);

@@ -332,11 +332,14 @@ class Codec {
   void* hgrow(Buf& b, size_t bytes);
   Buf d_rcck_, d_rclen_, d_rcbuf_, h_rcck_, h_rclen_, h_rcbuf_, h_ccodes_;
   Buf d_subfr_, h_subfr_, d_subs_, h_subs_, d_nck_;  // device-built substream tables
+  Buf h_cck_, d_cck_, h_cchk_, d_cchk_;  // coarse substreams decoded on the device
   bool dev_rc_ = true;
   std::vector<int64_t> in_base_;  // each decoded frame's first byte in d_rcbuf_
   int decode_net_device(int nd, int64_t* n_out, const std::vector<int>& dev, const int64_t* caps);
   int decode_net_async(int nd, int64_t* n_out, const std::vector<int>& dev, const int64_t* caps);
-  int expand_coarse_device(int nd);
+  // coarse codes to the device arrays (decoded on the host, or decoded there
+  // from the uploaded stream when on_device) and expanded to the keys of V_{b-1}
+  int expand_coarse_device(int nd, bool on_device);
   std::vector<SubTask> tasks_;
   std::vector<cudaEvent_t> ev_;
 };

@@ -94,6 +94,28 @@ void launch_coarse_down(const uint64_t* roots, int top, const uint8_t* codes, in
                         uint64_t* k1, uint64_t* key6, int64_t* n6, const ScanScratch& s, int* err,
                         cudaStream_t st);
 
+// ------------------------------------------------- coarse-level decoding --
+// One coarse substream: n symbols of the adaptive model from in[in_off ..
+// in_off + in_len) into out[0 .. n) (device) as codes (symbol + 1); fill != 0
+// instead writes n copies of the code `fill` (no stream).
+struct CoarseChunk {
+  int64_t in_off;
+  int64_t in_len;
+  uint8_t* out;
+  int32_t n;
+  int32_t fill;
+};
+// Decode every chunk, one warp each; a corrupt substream sets kErrStream.
+void launch_coarse_decode(const CoarseChunk* ck, int n, const uint8_t* in, int* err,
+                          cudaStream_t st);
+// The popcounts of n codes must add up to expect (kErrStream otherwise).
+struct CoarseCheck {
+  const uint8_t* codes;
+  int64_t n;
+  int64_t expect;
+};
+void launch_coarse_check(const CoarseCheck* ck, int n, int* err, cudaStream_t st);
+
 // ------------------------------------------------------ device range coding --
 // One substream: `rows` symbols starting at table / interval row `row`, its
 // bytes at `byte_off` of the byte buffer (`byte_len` = stream length when
