@@ -85,19 +85,23 @@ __device__ int g_conv_error = 0;
 
 
 // Bounded wait that also ends as soon as another thread has raised *abort.
+__device__ __forceinline__ bool try_wait_parity(uint32_t a, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(a), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
 __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity,
                                               volatile int* abort) {
   const uint32_t a = tc::smem_u32(bar);
+  if (try_wait_parity(a, parity)) return true;  // the usual case: no clock read
   const long long t0 = clock64();
   for (;;) {
-    uint32_t ok;
-    asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        "selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (ok) return true;
+    if (try_wait_parity(a, parity)) return true;
     if (*abort) return false;
     if (clock64() - t0 > (1ll << 31)) {
       *abort = 1;
@@ -225,6 +229,23 @@ k_conv333_tc(ConvTcArgs a) {
       }
     };
     issue_nbr(0);
+    // this thread's copies of a stage: (row, 16-byte chunk) pairs fixed for
+    // the whole kernel, so their swizzled destinations and source columns
+    // are formed once; per stage only the neighbour's row changes
+    constexpr int kPer = kTileM * Cfg::kChunks / kProducers;
+    static_assert(kPer * kProducers == kTileM * Cfg::kChunks, "copies must split evenly");
+    int prow[kPer];
+    uint32_t pdst[kPer];
+    const unsigned char* psrc[kPer];
+    const uint32_t rbytes = (uint32_t)a.x_stride * 2;
+#pragma unroll
+    for (int k = 0; k < kPer; k++) {
+      const int q = t + k * kProducers;
+      const int c = q % Cfg::kChunks;
+      prow[k] = q / Cfg::kChunks;
+      pdst[k] = tc::swz<Cfg::SW>(prow[k] * Cfg::RB + c * 16);
+      psrc[k] = reinterpret_cast<const unsigned char*>(a.xb) + c * 16;
+    }
     uint32_t u = 0;  // stages filled so far
     for (int lt = 0; lt < my_tiles; lt++) {
       const int64_t r0 = tile_r0(lt);
@@ -247,13 +268,11 @@ k_conv333_tc(ConvTcArgs a) {
         if (u >= (uint32_t)S && !wait_or_abort(&empty_bar[s], ((u / S) - 1) & 1, abort)) break;
         const uint32_t sbase = tc::smem_u32(sA + (size_t)s * Cfg::kStageBytes);
 #pragma unroll
-        for (int q = t; q < kTileM * Cfg::kChunks; q += kProducers) {
-          const int row = q / Cfg::kChunks, c = q % Cfg::kChunks;
-          const int32_t nb = sNbr[row * 27 + o];
-          const bool present = nb >= 0;
-          const unsigned char* src = reinterpret_cast<const unsigned char*>(a.xb) +
-                                     ((present ? (int64_t)nb : 0) * a.x_stride) * 2 + c * 16;
-          tc::cp_async16(sbase + tc::swz<Cfg::SW>(row * Cfg::RB + c * 16), src, present);
+        for (int k = 0; k < kPer; k++) {
+          const int32_t nb = sNbr[prow[k] * 27 + o];
+          // absent neighbours (nb < 0): zero-filled, the address kept valid
+          const uint32_t r = (uint32_t)max(nb, 0);
+          tc::cp_async16(sbase + pdst[k], psrc[k] + (size_t)r * rbytes, nb >= 0);
         }
         // arrives on the stage's barrier once this thread's copies have landed
         asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(
