@@ -16,8 +16,9 @@
 //  - 8 producer warps gather, for each (tile, offset), the 128 neighbour rows
 //    (pre-subtracted bf16 rows, 16-byte cp.async copies, zero-filled when the
 //    neighbour is absent: the exact zero padding of the sparse conv) into a
-//    ring of swizzled stages.  Each thread's copies of a stage arrive on the
-//    stage's "full" barrier by themselves when they land
+//    ring of swizzled stages (the 32-channel conv fills three offsets' stages
+//    per pipeline step).  Each thread's copies of a step arrive on the
+//    step's "full" barrier by themselves when they land
 //    (cp.async.mbarrier.arrive), so producers never wait on their own copies;
 //    the MMA thread fences the landed stage to the async proxy.
 //  - 1 MMA warp: one thread waits for a full stage and issues the M=128,
@@ -60,7 +61,7 @@ constexpr int kThreads = kProducers + kEpilogue + 32;
 // of Morton-adjacent tiles, whose neighbour rows overlap in L2).
 template <int CIN>
 constexpr int stages_of(int alt) {
-  return CIN == 64 ? (alt ? 4 : 5) : (alt ? 8 : 12);
+  return CIN == 64 ? 6 : (alt ? 9 : 12);
 }
 
 template <int CIN, int S_ = stages_of<CIN>(0)>
@@ -68,6 +69,13 @@ struct ConvCfg {
   static constexpr int RB = CIN * 2;                 // bf16 row bytes
   static constexpr int SW = CIN == 64 ? 128 : 64;    // swizzle of the A stage
   static constexpr int kStages = S_;
+  // offsets per pipeline step: three offsets' rows per barrier round trip
+  // (one wait, one arrival, one commit for three)
+  static constexpr int kG = 3;
+  // neighbour-map buffers: two (the next tile's map loads a tile ahead), or
+  // one for 64 channels, whose weights leave room for six stages only then
+  static constexpr int kNbrBufs = CIN == 64 ? 1 : 2;
+  static_assert(kStages % kG == 0 && 27 % kG == 0, "stage groups must tile the ring and offsets");
   static constexpr int kStageBytes = kTileM * RB;
   static constexpr int kPerGroup = 256 / CIN;        // offsets per fp32 accumulator
   static constexpr int kGroups = (27 + kPerGroup - 1) / kPerGroup;
@@ -77,7 +85,7 @@ struct ConvCfg {
   static constexpr int kChunks = RB / 16;            // 16-byte chunks per row
   static constexpr int kNbrBytes = kTileM * 27 * 4;  // a tile's neighbour rows
   static constexpr size_t kSmem =
-      1024 + kBBytes + (size_t)kStages * kStageBytes + 2 * kNbrBytes;
+      1024 + kBBytes + (size_t)kStages * kStageBytes + kNbrBufs * kNbrBytes;
   static_assert(kGroups * 32 <= kBufCols, "accumulators of one tile exceed a buffer");
 };
 
@@ -148,13 +156,16 @@ __global__ void __launch_bounds__(kThreads, 1)
 k_conv333_tc(ConvTcArgs a) {
   using Cfg = ConvCfg<CIN, S_>;
   constexpr int S = Cfg::kStages;
+  constexpr int G = Cfg::kG;       // offsets per pipeline step
+  constexpr int SG = S / G;        // steps in the ring
+  constexpr int NB = Cfg::kNbrBufs;
   extern __shared__ unsigned char smraw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
   unsigned char* sB = sm;
   unsigned char* sA = sm + Cfg::kBBytes;
   int32_t* sNbr0 = reinterpret_cast<int32_t*>(sA + (size_t)S * Cfg::kStageBytes);
-  __shared__ uint64_t full_bar[S], empty_bar[S], acc_full[2], acc_empty[2], drain_bar;
+  __shared__ uint64_t full_bar[SG], empty_bar[SG], acc_full[2], acc_empty[2], drain_bar;
   __shared__ uint64_t w_bar, nbr_bar[2];
   __shared__ uint32_t tslot;
   __shared__ int abort_flag;
@@ -164,7 +175,7 @@ k_conv333_tc(ConvTcArgs a) {
   const int t = threadIdx.x, w = t >> 5, lane = t & 31;
   if (w == kMmaWarp) tc::tmem_alloc(&tslot, 512);
   if (t == 0) {
-    for (int s = 0; s < S; s++) {
+    for (int s = 0; s < SG; s++) {
       tc::mbar_init(&full_bar[s], kProducers);
       tc::mbar_init(&empty_bar[s], 1);
     }
@@ -223,9 +234,9 @@ k_conv333_tc(ConvTcArgs a) {
       if (t == 0 && lt < my_tiles && tile_r0(lt) + kTileM <= n) {
         last_issued = lt;
         tc::fence_async_smem();  // earlier reads of the buffer come first
-        uint64_t* bar = &nbr_bar[lt & 1];
+        uint64_t* bar = &nbr_bar[lt % NB];
         mbar_expect(bar, Cfg::kNbrBytes);
-        bulk_g2s(sNbr0 + (lt & 1) * kTileM * 27, a.nbr + tile_r0(lt) * 27, Cfg::kNbrBytes, bar);
+        bulk_g2s(sNbr0 + (lt % NB) * kTileM * 27, a.nbr + tile_r0(lt) * 27, Cfg::kNbrBytes, bar);
       }
     };
     issue_nbr(0);
@@ -249,13 +260,16 @@ k_conv333_tc(ConvTcArgs a) {
     uint32_t u = 0;  // stages filled so far
     for (int lt = 0; lt < my_tiles; lt++) {
       const int64_t r0 = tile_r0(lt);
-      int32_t* sNbr = sNbr0 + (lt & 1) * kTileM * 27;
+      int32_t* sNbr = sNbr0 + (lt % NB) * kTileM * 27;
       // every producer is done issuing the previous tile's copies; all leave
       // together if any saw the abort flag
       if (producer_sync_or(*abort != 0)) break;
-      issue_nbr(lt + 1);
+      // the next tile's map a tile ahead (two buffers), or this tile's now
+      // that the one buffer is free (tile 0's went out before the loop)
+      if (NB == 2) issue_nbr(lt + 1);
+      else if (lt > 0) issue_nbr(lt);
       if (r0 + kTileM <= n) {
-        if (producer_sync_or(!wait_or_abort(&nbr_bar[lt & 1], (lt >> 1) & 1, abort))) break;
+        if (producer_sync_or(!wait_or_abort(&nbr_bar[lt % NB], (lt / NB) & 1, abort))) break;
         last_used = lt;
       } else {
         const int64_t base = r0 * 27, lim = n * 27;
@@ -263,26 +277,31 @@ k_conv333_tc(ConvTcArgs a) {
           sNbr[i] = base + i < lim ? __ldg(a.nbr + base + i) : -1;
         producer_sync_or(false);
       }
-      for (int o = 0; o < 27; o++, u++) {
-        const int s = (int)(u % S);
-        if (u >= (uint32_t)S && !wait_or_abort(&empty_bar[s], ((u / S) - 1) & 1, abort)) break;
-        const uint32_t sbase = tc::smem_u32(sA + (size_t)s * Cfg::kStageBytes);
+      for (int og = 0; og < 27 / G; og++, u++) {
+        const int sg = (int)(u % SG);
+        if (u >= (uint32_t)SG && !wait_or_abort(&empty_bar[sg], ((u / SG) - 1) & 1, abort))
+          break;
 #pragma unroll
-        for (int k = 0; k < kPer; k++) {
-          const int32_t nb = sNbr[prow[k] * 27 + o];
-          // absent neighbours (nb < 0): zero-filled, the address kept valid
-          const uint32_t r = (uint32_t)max(nb, 0);
-          tc::cp_async16(sbase + pdst[k], psrc[k] + (size_t)r * rbytes, nb >= 0);
+        for (int i = 0; i < G; i++) {
+          const int o = og * G + i;
+          const uint32_t sbase = tc::smem_u32(sA + (size_t)(sg * G + i) * Cfg::kStageBytes);
+#pragma unroll
+          for (int k = 0; k < kPer; k++) {
+            const int32_t nb = sNbr[prow[k] * 27 + o];
+            // absent neighbours (nb < 0): zero-filled, the address kept valid
+            const uint32_t r = (uint32_t)max(nb, 0);
+            tc::cp_async16(sbase + pdst[k], psrc[k] + (size_t)r * rbytes, nb >= 0);
+          }
         }
-        // arrives on the stage's barrier once this thread's copies have landed
+        // arrives on the step's barrier once this thread's copies have landed
         asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(
-                         tc::smem_u32(&full_bar[s]))
+                         tc::smem_u32(&full_bar[sg]))
                      : "memory");
       }
     }
     // a neighbour-row copy issued but not consumed (abort) lands before exit
     if (t == 0 && last_issued > last_used)
-      tc::mbar_wait(&nbr_bar[last_issued & 1], (last_issued >> 1) & 1);
+      tc::mbar_wait(&nbr_bar[last_issued % NB], (last_issued / NB) & 1);
     tc::cp_async_wait<0>();  // every copy of this thread has landed
   } else if (w == kMmaWarp) {
     // ---------------------------------------------------------------- MMA --
@@ -296,25 +315,29 @@ k_conv333_tc(ConvTcArgs a) {
         tc::tc_fence_after();
         const uint32_t dbase = tbase + (uint32_t)(b * Cfg::kBufCols);
         bool ok = true;
-        for (int o = 0; o < 27; o++, u++) {
-          const int s = (int)(u % S);
-          if (!wait_or_abort(&full_bar[s], (u / S) & 1, abort)) {
+        for (int og = 0; og < 27 / G; og++, u++) {
+          const int sg = (int)(u % SG);
+          if (!wait_or_abort(&full_bar[sg], (u / SG) & 1, abort)) {
             ok = false;
             break;
           }
-          tc::fence_async_smem();  // the stage's landed copies, to the MMA's proxy
+          tc::fence_async_smem();  // the step's landed copies, to the MMA's proxy
           tc::tc_fence_after();
-          const uint32_t sa = tc::smem_u32(sA + (size_t)s * Cfg::kStageBytes);
-          const int g = o / Cfg::kPerGroup;
 #pragma unroll
-          for (int ks = 0; ks < CIN / 16; ks++) {
-            const int k0 = o * CIN + ks * 16;
-            const uint32_t sb = tc::smem_u32(sB) + (k0 / 64) * 4096 + (k0 % 64) * 2;
-            tc::mma_bf16(dbase + g * 32, tc::smem_desc<Cfg::SW>(sa + ks * 32, 8 * Cfg::RB),
-                         tc::smem_desc<128>(sb, 1024), idesc,
-                         (o % Cfg::kPerGroup != 0 || ks > 0) ? 1u : 0u);
+          for (int i = 0; i < G; i++) {
+            const int o = og * G + i;
+            const uint32_t sa = tc::smem_u32(sA + (size_t)(sg * G + i) * Cfg::kStageBytes);
+            const int g = o / Cfg::kPerGroup;
+#pragma unroll
+            for (int ks = 0; ks < CIN / 16; ks++) {
+              const int k0 = o * CIN + ks * 16;
+              const uint32_t sb = tc::smem_u32(sB) + (k0 / 64) * 4096 + (k0 % 64) * 2;
+              tc::mma_bf16(dbase + g * 32, tc::smem_desc<Cfg::SW>(sa + ks * 32, 8 * Cfg::RB),
+                           tc::smem_desc<128>(sb, 1024), idesc,
+                           (o % Cfg::kPerGroup != 0 || ks > 0) ? 1u : 0u);
+            }
           }
-          tc::mma_commit(&empty_bar[s]);
+          tc::mma_commit(&empty_bar[sg]);
         }
         if (!ok) break;
         tc::mma_commit(&acc_full[b]);
