@@ -59,22 +59,36 @@ constexpr int kThreads = kProducers + kEpilogue + 32;
 // Variants the autotuner chooses from: the stage-ring depth and the order in
 // which a CTA walks its tiles (strided over the grid, or one contiguous run
 // of Morton-adjacent tiles, whose neighbour rows overlap in L2).
+// Ring shapes the autotuner chooses from (alt = 0 / 1): stages, offsets per
+// pipeline step, neighbour-map buffers.  32 channels: 12 stages in steps of
+// three with the map a tile ahead, or 18 stages in steps of nine with one map
+// buffer; 64 channels (its weights take half the shared memory): 6 stages in
+// steps of three, one map buffer.
 template <int CIN>
 constexpr int stages_of(int alt) {
-  return CIN == 64 ? 6 : (alt ? 9 : 12);
+  return CIN == 64 ? 6 : (alt ? 18 : 12);
+}
+template <int CIN>
+constexpr int step_of(int alt) {
+  return CIN == 64 ? 3 : (alt ? 9 : 3);
+}
+template <int CIN>
+constexpr int nbr_bufs_of(int alt) {
+  return CIN == 64 ? 1 : (alt ? 1 : 2);
 }
 
-template <int CIN, int S_ = stages_of<CIN>(0)>
+template <int CIN, int S_ = stages_of<CIN>(0), int G_ = step_of<CIN>(0),
+          int NB_ = nbr_bufs_of<CIN>(0)>
 struct ConvCfg {
   static constexpr int RB = CIN * 2;                 // bf16 row bytes
   static constexpr int SW = CIN == 64 ? 128 : 64;    // swizzle of the A stage
   static constexpr int kStages = S_;
-  // offsets per pipeline step: three offsets' rows per barrier round trip
-  // (one wait, one arrival, one commit for three)
-  static constexpr int kG = 3;
-  // neighbour-map buffers: two (the next tile's map loads a tile ahead), or
-  // one for 64 channels, whose weights leave room for six stages only then
-  static constexpr int kNbrBufs = CIN == 64 ? 1 : 2;
+  // offsets per pipeline step: their rows share one barrier round trip (one
+  // wait, one arrival, one commit)
+  static constexpr int kG = G_;
+  // neighbour-map buffers: two (the next tile's map loads a tile ahead) or
+  // one (loaded at the tile's start; leaves room for more stages)
+  static constexpr int kNbrBufs = NB_;
   static_assert(kStages % kG == 0 && 27 % kG == 0, "stage groups must tile the ring and offsets");
   static constexpr int kStageBytes = kTileM * RB;
   static constexpr int kPerGroup = 256 / CIN;        // offsets per fp32 accumulator
@@ -151,10 +165,10 @@ __device__ __forceinline__ bool producer_sync_or(bool v) {
   return r != 0;
 }
 
-template <int CIN, int S_, int ORDER>
+template <int CIN, int ALT, int ORDER>
 __global__ void __launch_bounds__(kThreads, 1)
 k_conv333_tc(ConvTcArgs a) {
-  using Cfg = ConvCfg<CIN, S_>;
+  using Cfg = ConvCfg<CIN, stages_of<CIN>(ALT), step_of<CIN>(ALT), nbr_bufs_of<CIN>(ALT)>;
   constexpr int S = Cfg::kStages;
   constexpr int G = Cfg::kG;       // offsets per pipeline step
   constexpr int SG = S / G;        // steps in the ring
@@ -493,11 +507,12 @@ namespace {
 
 template <int CIN, int ALT, int ORDER>
 void launch_variant(const ConvTcArgs& a, int blocks, cudaStream_t st) {
-  constexpr int S = stages_of<CIN>(ALT);
-  constexpr size_t smem = ConvCfg<CIN, S>::kSmem;
-  cudaFuncSetAttribute(k_conv333_tc<CIN, S, ORDER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  constexpr size_t smem =
+      ConvCfg<CIN, stages_of<CIN>(ALT), step_of<CIN>(ALT), nbr_bufs_of<CIN>(ALT)>::kSmem;
+  static_assert(smem <= 232448, "shared memory of a conv variant exceeds the limit");
+  cudaFuncSetAttribute(k_conv333_tc<CIN, ALT, ORDER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)smem);
-  k_conv333_tc<CIN, S, ORDER><<<blocks, kThreads, smem, st>>>(a);
+  k_conv333_tc<CIN, ALT, ORDER><<<blocks, kThreads, smem, st>>>(a);
 }
 
 template <int CIN>

@@ -283,7 +283,7 @@ class Codec:
 
     def tuning(self) -> dict:
         """The conv autotuner's choice per input width and the timed variants
-        (milliseconds; bit 0 of a variant = shallower stage ring, bit 1 =
+        (milliseconds; bit 0 of a variant = alternative ring shape, bit 1 =
         contiguous tile order)."""
         v = (C.c_int * 3)()
         ms = (C.c_float * 10)()
