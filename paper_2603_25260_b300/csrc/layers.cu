@@ -571,14 +571,25 @@ k_predictor_tc(DLayer P1, DPred2 P2, const uint32_t* __restrict__ lut,
   const int64_t ntiles = (n + kPTile - 1) / kPTile;
   uint32_t phase = 0;
   bool ok = true;
+  // this thread's 16 input bytes of a tile (row, 16-column half), loaded a
+  // tile ahead so that the load's latency overlaps the previous tile
+  const int in_row = tl >> 1, in_c2 = tl & 1;
+  auto load_in = [&](int64_t tile) {
+    const int64_t r = tile * kPTile + in_row;
+    return tile < ntiles && r < n
+               ? __ldg(reinterpret_cast<const uint4*>(F + r * f_stride) + in_c2)
+               : make_uint4(0, 0, 0, 0);
+  };
+  uint4 q_next = load_in(2 * (int64_t)blockIdx.x + g);
   for (int64_t tile = 2 * (int64_t)blockIdx.x + g; tile < ntiles; tile += 2 * (int64_t)gridDim.x) {
     const int64_t r0 = tile * kPTile;
     // ---- layer-1 input: (F - z1) as bf16, thread = (row, 16-column half)
     {
-      const int row = tl >> 1, c2 = tl & 1;
+      const int row = in_row, c2 = in_c2;
+      const uint4 q = q_next;
+      q_next = load_in(tile + 2 * (int64_t)gridDim.x);
       int32_t v[2][8];
       if (r0 + row < n) {
-        const uint4 q = __ldg(reinterpret_cast<const uint4*>(F + (r0 + row) * f_stride) + c2);
         const uint32_t wd[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
         for (int k = 0; k < 16; k++) v[k >> 3][k & 7] = (int)(wd[k >> 2] << (24 - 8 * (k & 3))) >> 24;
@@ -643,12 +654,20 @@ k_predictor_tc(DLayer P1, DPred2 P2, const uint32_t* __restrict__ lut,
       break;
     }
     tc::tc_fence_after();
-    // ---- logits: 128 columns a warp, requantised into the shared tile
+    // ---- logits: 128 columns a warp, requantised into the shared tile;
+    // the accumulator columns come in pairs of 16-column loads per wait
+    uint32_t fr[2][16];
 #pragma unroll
     for (int gi = 0; gi < 8; gi++) {
       const int c0 = 128 * cg + 16 * gi;
+      if ((gi & 1) == 0) {
+        tc::tmem_ld16_issue(tbase + lane_off + c0, fr[0]);
+        tc::tmem_ld16_issue(tbase + lane_off + c0 + 16, fr[1]);
+        tc::tmem_wait_ld();
+      }
       float f[16];
-      tc::tmem_ld16(tbase + lane_off + c0, f);
+#pragma unroll
+      for (int i = 0; i < 16; i++) f[i] = __uint_as_float(fr[gi & 1][i]);
       uint32_t pk[4] = {0, 0, 0, 0};
       if (fast2) {
         int32_t ms[16];
@@ -683,33 +702,48 @@ k_predictor_tc(DLayer P1, DPred2 P2, const uint32_t* __restrict__ lut,
     }
     tc::tc_fence_before();
     group_sync(g);
-    // ---- integer softmax, one warp per row, 16 rows a warp
+    // ---- integer softmax, one warp per row, 16 rows a warp, two rows at a
+    // time so that their dependent chains (reductions, table loads, the
+    // divisions) overlap; a row past the end is computed and not stored
 #pragma unroll 1
-    for (int rr = 0; rr < kPTile / 8; rr++) {
+    for (int rr = 0; rr < kPTile / 8; rr += 2) {
       const int tr = wl * (kPTile / 8) + rr;
       const int64_t r = r0 + tr;
       if (r >= n) break;
-      const uint2 raw = *reinterpret_cast<const uint2*>(sLg + tr * kLogStride + 8 * lane);
-      int l[8];
+      const bool two = r + 1 < n;
+      int l[2][8];
 #pragma unroll
-      for (int i = 0; i < 4; i++) {
-        l[i] = sext_byte(raw.x, i);
-        l[4 + i] = sext_byte(raw.y, i);
+      for (int k = 0; k < 2; k++) {
+        const uint2 raw =
+            *reinterpret_cast<const uint2*>(sLg + (tr + k) * kLogStride + 8 * lane);
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+          l[k][i] = sext_byte(raw.x, i);
+          l[k][4 + i] = sext_byte(raw.y, i);
+        }
       }
       if (mode == kPredLogits) {
 #pragma unroll
-        for (int i = 0; i < 8; i++)
-          if (lane * 8 + i < kNsym) logits[r * kNsym + lane * 8 + i] = (int8_t)l[i];
+        for (int k = 0; k < 2; k++)
+#pragma unroll
+          for (int i = 0; i < 8; i++)
+            if (lane * 8 + i < kNsym && (k == 0 || two))
+              logits[(r + k) * kNsym + lane * 8 + i] = (int8_t)l[k][i];
         continue;
       }
-      SoftRow o;
-      softmax_row(l, ck, lane == 31, slut, o);
+      SoftRow o0, o1;
+      softmax_row(l[0], ck, lane == 31, slut, o0);
+      softmax_row(l[1], ck, lane == 31, slut, o1);
       if (mode == kPredCdf) {
-        store_cdf_row(o, lane, cdf + r * 256);
+        store_cdf_row(o0, lane, cdf + r * 256);
+        if (two) store_cdf_row(o1, lane, cdf + (r + 1) * 256);
       } else {
-        const int s = (int)codes[r] - 1;
-        const uint32_t pair = enc_pair(o, lane, s);
-        if ((s >> 3) == lane) enc[r] = pair;
+        const int s0 = (int)codes[r] - 1;
+        const int s1 = two ? (int)codes[r + 1] - 1 : 0;
+        const uint32_t p0 = enc_pair(o0, lane, s0);
+        const uint32_t p1 = enc_pair(o1, lane, s1);
+        if ((s0 >> 3) == lane) enc[r] = p0;
+        if (two && (s1 >> 3) == lane) enc[r + 1] = p1;
       }
     }
   }
