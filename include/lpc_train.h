@@ -26,7 +26,12 @@
 extern "C" {
 #endif
 
-/* Sparse 3x3x3 conv (Eq. 5): y[i] = b + sum_o W[o] x[nbr[i][o]]. */
+/* Sparse 3x3x3 conv (Eq. 5): y[i] = b + sum_o W[o] x[nbr[i][o]].  With
+ * bf16 = 1 the forward and the input gradient run as gather-GEMMs on the
+ * tcgen05 tensor cores (bf16 operands, fp32 accumulators in tensor memory);
+ * they use a device scratch the library grows on demand (cudaMalloc on the
+ * first calls and on growth only).  lpc_t_tc_error reports (and with
+ * reset = 1 clears) a tensor-core launch that gave up on a bounded wait. */
 int lpc_t_conv_fwd(const float* x, int64_t N, int cin, const int32_t* nbr, const float* W,
                    const float* b, int cout, float* y, int bf16, uint64_t stream);
 /* dx[i] = sum_o W[o]^T dy[nbr[i][26 - o]] (mirror offset); dW[o] += sum_i
@@ -34,6 +39,7 @@ int lpc_t_conv_fwd(const float* x, int64_t N, int cin, const int32_t* nbr, const
 int lpc_t_conv_bwd(const float* x, const float* dy, int64_t N, int cin, const int32_t* nbr,
                    const float* W, int cout, float* dx, float* dW, float* db, int bf16,
                    uint64_t stream);
+int lpc_t_tc_error(int reset);
 
 /* Upsampling + Pruning (Eq. 6): y[r] = b[c] + W[c] x[par[r]], c = ckey[r] & 7. */
 int lpc_t_up_fwd(const float* x, int cin, const uint32_t* par, const uint64_t* ckey, int64_t Nc,

@@ -273,6 +273,13 @@ void launch_to_bf16_cat(const int8_t* a, int a_stride, const int8_t* b, int b_st
 // Non-zero if a tensor-core conv gave up on a bounded wait (optionally reset).
 int conv_tc_error(bool reset);
 
+// The differentiable twin's 3x3x3 conv in bf16 mode on tcgen05: forward
+// (mirror 0: in = x [n][cin], out = y [n][32], plus bias) or input gradient
+// (mirror 1: in = dy [n][32], out = dx [n][cin], no bias); W [27][32][cin]
+// float; operands rounded to bf16, fp32 accumulation.
+int tconv_tc(const float* in, int64_t n, int cin, const int32_t* nbr, const float* W,
+             const float* bias, float* out, int mirror, cudaStream_t st);
+
 // Predictor + integer softmax + cumulative table.
 enum PredMode { kPredCdf = 0, kPredEnc = 1, kPredLogits = 2 };
 // variant 0: CUDA cores (dp4a, warp per row); 1: tcgen05 for both linear

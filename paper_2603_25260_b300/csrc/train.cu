@@ -351,6 +351,8 @@ extern "C" {
 int lpc_t_conv_fwd(const float* x, int64_t N, int cin, const int32_t* nbr, const float* W,
                    const float* b, int cout, float* y, int bf16, uint64_t stream) {
   if (N < 0 || !ok_dims(cin, cout)) return LPC_INVALID_ARG;
+  // bf16 operands: the gather-GEMM on the tensor cores
+  if (bf16) return tconv_tc(x, N, cin, nbr, W, b, y, 0, reinterpret_cast<cudaStream_t>(stream));
   return gmv(ConvItems{nbr, 0}, W, 27, cout, cin, 0, b, b ? 1 : 0, x, N, y, bf16,
              reinterpret_cast<cudaStream_t>(stream));
 }
@@ -361,7 +363,8 @@ int lpc_t_conv_bwd(const float* x, const float* dy, int64_t N, int cin, const in
   if (N < 0 || !ok_dims(cin, cout)) return LPC_INVALID_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   int s = LPC_OK;
-  if (dx) s = gmv(ConvItems{nbr, 1}, W, 27, cin, cout, 1, nullptr, 0, dy, N, dx, bf16, st);
+  if (dx && bf16) s = tconv_tc(dy, N, cin, nbr, W, nullptr, dx, 1, st);
+  else if (dx) s = gmv(ConvItems{nbr, 1}, W, 27, cin, cout, 1, nullptr, 0, dy, N, dx, bf16, st);
   if (!s) s = outer(ConvPairs{nbr}, 27, cout, cin, dy, x, N, dW, bf16, st);
   if (!s) s = bias_grad(dy, N, cout, nullptr, db, st);
   return s;

@@ -1,0 +1,420 @@
+// The differentiable twin's 3x3x3 sparse conv in bf16 mode on the tcgen05
+// tensor cores: the forward y[i] = b + sum_o W[o] x[nbr[i][o]] (Eq. 5) and the
+// input gradient dx[i] = sum_o W[o]^T dy[nbr[i][26 - o]].  bf16 mode rounds
+// both operands of every product to bf16 and accumulates in fp32, which is
+// what kind::f16 MMAs with fp32 accumulators in tensor memory compute.
+//
+// The kernel is the inference conv's gather-GEMM (see conv_tc.cu) with a
+// float epilogue: per CTA and tile of 128 output rows, 8 producer warps
+// gather the bf16 rows of the tile's neighbours offset by offset (zero rows
+// for absent neighbours) into a ring of swizzled stages, three offsets per
+// pipeline step; one thread issues the M=128 MMAs into one fp32 accumulator
+// for all 27 offsets (N = the output width, 32 or 64); 4 epilogue warps add
+// the bias and store fp32 rows.  The input gradient is the same gather over
+// the rounded output gradient (32 channels) with the weight slices reversed
+// and transposed (slice o' = W[26 - o']^T), so it reads the same kernel map.
+// Every wait is bounded; a wait that gives up raises a shared abort flag,
+// the CTA drains its copies and MMAs, frees its tensor memory and sets an
+// error word that lpc_t_tc_error reports.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "../../include/lpc.h"
+#include "../../include/lpc_train.h"
+#include "common.cuh"
+#include "kernels.h"
+#include "tc_util.cuh"
+
+namespace lpc {
+namespace {
+
+constexpr int kTM = 128;
+constexpr int kPWarps = 8;
+constexpr int kProd = 32 * kPWarps;
+constexpr int kEpi = 128;
+constexpr int kMmaW = kPWarps + 4;
+constexpr int kThr = kProd + kEpi + 32;
+
+// CIN: gathered row width (bf16 elements); NOUT: output width.  Ring shapes:
+// 64-wide rows take 16 KB stages beside a 110 KB weight image (6 stages, one
+// neighbour-map buffer); 32-wide rows 8 KB stages.
+template <int CIN, int NOUT>
+struct TCfg {
+  static constexpr int RB = CIN * 2;
+  static constexpr int SW = CIN == 64 ? 128 : 64;
+  static constexpr int kChunks = RB / 16;
+  static constexpr int kBBlocks = (27 * CIN + 63) / 64;
+  static constexpr int kBBlockBytes = NOUT * 128;
+  static constexpr int kBBytes = kBBlocks * kBBlockBytes;
+  static constexpr int kStageBytes = kTM * RB;
+  static constexpr int kStages = CIN == 64 ? 6 : 12;
+  static constexpr int kG = 3;
+  static constexpr int kNbrBufs = (CIN == 64 || NOUT == 64) ? 1 : 2;
+  static constexpr int kNbrBytes = kTM * 27 * 4;
+  static constexpr size_t kSmem =
+      1024 + kBBytes + (size_t)kStages * kStageBytes + kNbrBufs * kNbrBytes;
+  static constexpr int kTmemCols = NOUT == 64 ? 128 : 64;  // two accumulator buffers
+  static_assert(kSmem <= 232448, "shared memory of a training conv variant exceeds the limit");
+};
+
+__device__ int g_tconv_error = 0;
+
+__device__ __forceinline__ bool try_wait_parity(uint32_t a, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(a), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity,
+                                              volatile int* abort) {
+  const uint32_t a = tc::smem_u32(bar);
+  if (try_wait_parity(a, parity)) return true;
+  const long long t0 = clock64();
+  for (;;) {
+    if (try_wait_parity(a, parity)) return true;
+    if (*abort) return false;
+    if (clock64() - t0 > (1ll << 31)) {
+      *abort = 1;
+      return false;
+    }
+  }
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      ::"r"(tc::smem_u32(dst)), "l"(src), "r"(bytes), "r"(tc::smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void mbar_expect(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+                   tc::smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool producer_sync_or(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n.reg .pred p, q;\nsetp.ne.u32 p, %1, 0;\nbar.red.or.pred q, 1, %2, p;\n"
+      "selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v), "n"(kProd)
+      : "memory");
+  return r != 0;
+}
+
+struct TConvArgs {
+  const __nv_bfloat16* xb;  // gathered rows [rows][CIN], bf16
+  const int32_t* nbr;       // [n][27]
+  int64_t n;
+  const uint16_t* wimg;     // weight image, TCfg::kBBytes
+  const float* bias;        // [NOUT] or null
+  float* out;               // [n][NOUT]
+};
+
+template <int CIN, int NOUT>
+__global__ void __launch_bounds__(kThr, 1) k_tconv_tc(TConvArgs a) {
+  using Cfg = TCfg<CIN, NOUT>;
+  constexpr int S = Cfg::kStages, G = Cfg::kG, SG = S / G, NB = Cfg::kNbrBufs;
+  extern __shared__ unsigned char smraw[];
+  unsigned char* sm = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
+  unsigned char* sB = sm;
+  unsigned char* sA = sm + Cfg::kBBytes;
+  int32_t* sNbr0 = reinterpret_cast<int32_t*>(sA + (size_t)S * Cfg::kStageBytes);
+  __shared__ uint64_t full_bar[SG], empty_bar[SG], acc_full[2], acc_empty[2], drain_bar;
+  __shared__ uint64_t w_bar, nbr_bar[2];
+  __shared__ uint32_t tslot;
+  __shared__ int abort_flag;
+  __shared__ float sBias[NOUT];
+  volatile int* abort = &abort_flag;
+
+  const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+  if (w == kMmaW) tc::tmem_alloc(&tslot, Cfg::kTmemCols);
+  if (t == 0) {
+    for (int s = 0; s < SG; s++) {
+      tc::mbar_init(&full_bar[s], kProd);
+      tc::mbar_init(&empty_bar[s], 1);
+    }
+    for (int b = 0; b < 2; b++) {
+      tc::mbar_init(&acc_full[b], 1);
+      tc::mbar_init(&acc_empty[b], kEpi);
+    }
+    tc::mbar_init(&drain_bar, 1);
+    tc::mbar_init(&w_bar, 1);
+    tc::mbar_init(&nbr_bar[0], 1);
+    tc::mbar_init(&nbr_bar[1], 1);
+    tc::fence_mbar_init();
+    abort_flag = 0;
+    mbar_expect(&w_bar, Cfg::kBBytes);
+    for (int off = 0; off < Cfg::kBBytes; off += 16384)
+      bulk_g2s(sm + off, reinterpret_cast<const unsigned char*>(a.wimg) + off,
+               (uint32_t)min(16384, Cfg::kBBytes - off), &w_bar);
+  }
+  if (t < NOUT) sBias[t] = a.bias ? a.bias[t] : 0.f;
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tbase = tslot;
+  const int64_t n = a.n;
+  const int64_t ntiles = (n + kTM - 1) / kTM;
+  const int my_tiles = blockIdx.x < ntiles ? (int)((ntiles - 1 - blockIdx.x) / gridDim.x + 1) : 0;
+  auto tile_r0 = [&](int lt) { return ((int64_t)blockIdx.x + (int64_t)lt * gridDim.x) * kTM; };
+
+  if (w < kPWarps) {
+    // ---------------------------------------------------------- producers --
+    int last_issued = -1, last_used = -1;
+    auto issue_nbr = [&](int lt) {
+      if (t == 0 && lt < my_tiles && tile_r0(lt) + kTM <= n) {
+        last_issued = lt;
+        tc::fence_async_smem();
+        uint64_t* bar = &nbr_bar[lt % NB];
+        mbar_expect(bar, Cfg::kNbrBytes);
+        bulk_g2s(sNbr0 + (lt % NB) * kTM * 27, a.nbr + tile_r0(lt) * 27, Cfg::kNbrBytes, bar);
+      }
+    };
+    issue_nbr(0);
+    constexpr int kPer = kTM * Cfg::kChunks / kProd;
+    static_assert(kPer * kProd == kTM * Cfg::kChunks, "copies must split evenly");
+    int prow[kPer];
+    uint32_t pdst[kPer];
+    const unsigned char* psrc[kPer];
+#pragma unroll
+    for (int k = 0; k < kPer; k++) {
+      const int q = t + k * kProd;
+      const int c = q % Cfg::kChunks;
+      prow[k] = q / Cfg::kChunks;
+      pdst[k] = tc::swz<Cfg::SW>(prow[k] * Cfg::RB + c * 16);
+      psrc[k] = reinterpret_cast<const unsigned char*>(a.xb) + c * 16;
+    }
+    uint32_t u = 0;
+    for (int lt = 0; lt < my_tiles; lt++) {
+      const int64_t r0 = tile_r0(lt);
+      int32_t* sNbr = sNbr0 + (lt % NB) * kTM * 27;
+      if (producer_sync_or(*abort != 0)) break;
+      if (NB == 2) issue_nbr(lt + 1);
+      else if (lt > 0) issue_nbr(lt);
+      if (r0 + kTM <= n) {
+        if (producer_sync_or(!wait_or_abort(&nbr_bar[lt % NB], (lt / NB) & 1, abort))) break;
+        last_used = lt;
+      } else {
+        const int64_t base = r0 * 27, lim = n * 27;
+        for (int i = t; i < kTM * 27; i += kProd)
+          sNbr[i] = base + i < lim ? __ldg(a.nbr + base + i) : -1;
+        producer_sync_or(false);
+      }
+      for (int og = 0; og < 27 / G; og++, u++) {
+        const int sg = (int)(u % SG);
+        if (u >= (uint32_t)SG && !wait_or_abort(&empty_bar[sg], ((u / SG) - 1) & 1, abort))
+          break;
+#pragma unroll
+        for (int i = 0; i < G; i++) {
+          const int o = og * G + i;
+          const uint32_t sbase = tc::smem_u32(sA + (size_t)(sg * G + i) * Cfg::kStageBytes);
+#pragma unroll
+          for (int k = 0; k < kPer; k++) {
+            const int32_t nb = sNbr[prow[k] * 27 + o];
+            const uint32_t r = (uint32_t)max(nb, 0);
+            tc::cp_async16(sbase + pdst[k], psrc[k] + (size_t)r * Cfg::RB, nb >= 0);
+          }
+        }
+        asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(
+                         tc::smem_u32(&full_bar[sg]))
+                     : "memory");
+      }
+    }
+    if (t == 0 && last_issued > last_used)
+      tc::mbar_wait(&nbr_bar[last_issued % NB], (last_issued / NB) & 1);
+    tc::cp_async_wait<0>();
+  } else if (w == kMmaW) {
+    // ---------------------------------------------------------------- MMA --
+    if (lane == 0) {
+      constexpr uint32_t idesc = tc::idesc_bf16(kTM, NOUT);
+      uint32_t u = 0;
+      const bool wok = wait_or_abort(&w_bar, 0, abort);
+      for (int lt = 0; lt < my_tiles && wok && !*abort; lt++) {
+        const int b = lt & 1;
+        if (lt >= 2 && !wait_or_abort(&acc_empty[b], ((lt >> 1) - 1) & 1, abort)) break;
+        tc::tc_fence_after();
+        const uint32_t dbase = tbase + (uint32_t)(b * NOUT);
+        bool ok = true;
+        for (int og = 0; og < 27 / G; og++, u++) {
+          const int sg = (int)(u % SG);
+          if (!wait_or_abort(&full_bar[sg], (u / SG) & 1, abort)) {
+            ok = false;
+            break;
+          }
+          tc::fence_async_smem();
+          tc::tc_fence_after();
+#pragma unroll
+          for (int i = 0; i < G; i++) {
+            const int o = og * G + i;
+            const uint32_t sa = tc::smem_u32(sA + (size_t)(sg * G + i) * Cfg::kStageBytes);
+#pragma unroll
+            for (int ks = 0; ks < CIN / 16; ks++) {
+              const int k0 = o * CIN + ks * 16;
+              const uint32_t sb =
+                  tc::smem_u32(sB) + (k0 / 64) * Cfg::kBBlockBytes + (k0 % 64) * 2;
+              tc::mma_bf16(dbase, tc::smem_desc<Cfg::SW>(sa + ks * 32, 8 * Cfg::RB),
+                           tc::smem_desc<128>(sb, 1024), idesc, (o > 0 || ks > 0) ? 1u : 0u);
+            }
+          }
+          tc::mma_commit(&empty_bar[sg]);
+        }
+        if (!ok) break;
+        tc::mma_commit(&acc_full[b]);
+      }
+      tc::mma_commit(&drain_bar);
+      if (!tc::mbar_wait(&drain_bar, 0)) *abort = 1;
+    }
+    __syncwarp();
+  } else {
+    // ----------------------------------------------------------- epilogue --
+    const int e = t - kProd;
+    const uint32_t lane_off = (uint32_t)((w & 3) * 32) << 16;
+    for (int lt = 0; lt < my_tiles; lt++) {
+      const int b = lt & 1;
+      if (!__all_sync(0xffffffffu, wait_or_abort(&acc_full[b], (lt >> 1) & 1, abort))) break;
+      tc::tc_fence_after();
+      uint32_t raw[NOUT / 16][16];
+      const uint32_t dbase = tbase + lane_off + (uint32_t)(b * NOUT);
+#pragma unroll
+      for (int g = 0; g < NOUT / 16; g++) tc::tmem_ld16_issue(dbase + g * 16, raw[g]);
+      tc::tmem_wait_ld();
+      tc::tc_fence_before();
+      mbar_arrive(&acc_empty[b]);
+      const int64_t r = tile_r0(lt) + e;
+      if (r < n) {
+        float4* dst = reinterpret_cast<float4*>(a.out + r * NOUT);
+#pragma unroll
+        for (int c = 0; c < NOUT; c += 4)
+          dst[c / 4] = make_float4(__uint_as_float(raw[c / 16][c % 16]) + sBias[c],
+                                   __uint_as_float(raw[c / 16][c % 16 + 1]) + sBias[c + 1],
+                                   __uint_as_float(raw[c / 16][c % 16 + 2]) + sBias[c + 2],
+                                   __uint_as_float(raw[c / 16][c % 16 + 3]) + sBias[c + 3]);
+      }
+    }
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  if (t == kThr - 32) tc::mbar_wait(&w_bar, 0);
+  if (w == kMmaW) tc::tmem_dealloc(tbase, Cfg::kTmemCols);
+  if (t == 0 && abort_flag) atomicExch(&g_tconv_error, 1);
+}
+
+// float rows -> bf16 rows (round to nearest even), n x cols
+__global__ void k_f32_to_bf16(const float* __restrict__ x, int64_t count, __nv_bfloat16* out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count / 4;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float4 v = reinterpret_cast<const float4*>(x)[i];
+    __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y), hi = __floats2bfloat162_rn(v.z, v.w);
+    reinterpret_cast<__nv_bfloat162*>(out)[2 * i] = lo;
+    reinterpret_cast<__nv_bfloat162*>(out)[2 * i + 1] = hi;
+  }
+}
+
+// Weight image of the gather-GEMM (K-major, 64-element blocks of nout rows x
+// 128 bytes, 128-byte swizzled): forward (mirror 0) row n = output channel,
+// k = o cin + ci, value W[o][n][ci]; input gradient (mirror 1) row n = ci,
+// k = o' 32 + c, value W[26 - o'][c][ci].  W is [27][32][cin].
+__global__ void k_pack_tw(const float* __restrict__ W, int cin, int mirror, int nout, int kper,
+                          unsigned char* img) {
+  const int64_t total = (int64_t)27 * kper * nout;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int nrow = (int)(idx % nout);
+    const int k = (int)(idx / nout);
+    const int o = k / kper, kk = k % kper;
+    const float v = mirror ? W[((size_t)(26 - o) * 32 + kk) * cin + nrow]
+                           : W[((size_t)o * 32 + nrow) * cin + kk];
+    const __nv_bfloat16 b = __float2bfloat16_rn(v);
+    const int blk = k / 64, kb = k % 64;
+    uint32_t off = (uint32_t)(nrow * 128 + kb * 2);
+    off ^= ((off >> 7) & 7) << 4;
+    *reinterpret_cast<__nv_bfloat16*>(img + (size_t)blk * nout * 128 + off) = b;
+  }
+}
+
+// Growable device scratch for the bf16 rows and the weight image (allocated
+// on the first calls and on growth only).
+struct Scratch {
+  std::mutex mu;
+  void* p = nullptr;
+  size_t cap = 0;
+};
+Scratch g_rows, g_img;
+
+void* grow(Scratch& s, size_t bytes) {
+  std::lock_guard<std::mutex> g(s.mu);
+  if (bytes <= s.cap) return s.p;
+  if (s.p) cudaFree(s.p);
+  s.cap = std::max<size_t>(bytes + bytes / 4, 1 << 16);
+  if (cudaMalloc(&s.p, s.cap) != cudaSuccess) {
+    cudaGetLastError();
+    s.p = nullptr;
+    s.cap = 0;
+  }
+  return s.p;
+}
+
+template <int CIN, int NOUT>
+int launch(const TConvArgs& a, cudaStream_t st) {
+  using Cfg = TCfg<CIN, NOUT>;
+  const int64_t ntiles = (a.n + kTM - 1) / kTM;
+  const int blocks = (int)std::min<int64_t>(ntiles, 148);
+  cudaFuncSetAttribute(k_tconv_tc<CIN, NOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)Cfg::kSmem);
+  k_tconv_tc<CIN, NOUT><<<blocks, kThr, Cfg::kSmem, st>>>(a);
+  count_launches(1);
+  return cudaGetLastError() == cudaSuccess ? LPC_OK : LPC_CUDA_ERROR;
+}
+
+}  // namespace
+
+// bf16-mode forward (mirror 0: x [n][cin] -> y [n][32]) or input gradient
+// (mirror 1: dy [n][32] -> dx [n][cin]) of the 3x3x3 conv on tcgen05.
+int tconv_tc(const float* in, int64_t n, int cin, const int32_t* nbr, const float* W,
+             const float* bias, float* out, int mirror, cudaStream_t st) {
+  if (n <= 0) return LPC_OK;
+  const int gw = mirror ? 32 : cin;    // gathered row width
+  const int nout = mirror ? cin : 32;  // output width
+  const int64_t rows_bytes = n * gw * 2;
+  const size_t img_bytes = (size_t)((27 * gw + 63) / 64) * nout * 128;
+  void* xb = grow(g_rows, (size_t)rows_bytes);
+  void* img = grow(g_img, img_bytes);
+  if (!xb || !img) return LPC_CUDA_ERROR;
+  const int64_t cnt = n * gw;
+  k_f32_to_bf16<<<(int)std::min<int64_t>((cnt / 4 + 255) / 256, 148 * 8), 256, 0, st>>>(
+      in, cnt, static_cast<__nv_bfloat16*>(xb));
+  cudaMemsetAsync(img, 0, img_bytes, st);
+  k_pack_tw<<<(int)std::min<int64_t>((27 * gw * nout + 255) / 256, 148 * 4), 256, 0, st>>>(
+      W, cin, mirror, nout, gw, static_cast<unsigned char*>(img));
+  count_launches(2);
+  const TConvArgs a{static_cast<const __nv_bfloat16*>(xb), nbr, n,
+                    static_cast<const uint16_t*>(img), bias, out};
+  if (gw == 64) return launch<64, 32>(a, st);
+  if (nout == 64) return launch<32, 64>(a, st);
+  return launch<32, 32>(a, st);
+}
+
+}  // namespace lpc
+
+extern "C" int lpc_t_tc_error(int reset) {
+  int e = 0;
+  cudaMemcpyFromSymbol(&e, lpc::g_tconv_error, sizeof(int));
+  if (reset && e) {
+    const int z = 0;
+    cudaMemcpyToSymbol(lpc::g_tconv_error, &z, sizeof(int));
+  }
+  return e;
+}

@@ -48,6 +48,7 @@ def _lib():
             "lpc_t_fq_bwd": [P_, P_, I64, P_, C.c_uint64],
             "lpc_t_fq_w": [P_, I64, P_, P_, C.c_uint64],
             "lpc_t_levels": [P_, I64, I32, P_, P_, P_, P_, P_, I64, C.c_uint64],
+            "lpc_t_tc_error": [I32],
             "lpc_t_pred_fwd": [P_, I64, P_, P_, P_, P_, P_, P_, I32, I32, P_, P_, C.c_uint64],
             "lpc_t_pred_bwd": [P_, I64, P_, P_, P_, P_, P_, P_, I32, I32, P_, P_, P_, P_, P_,
                                P_, P_, C.c_uint64],
@@ -62,6 +63,11 @@ def _lib():
 
 def _p(t):
     return None if t is None else t.data_ptr()
+
+
+def tc_error(reset: bool = True) -> int:
+    """Non-zero if a tensor-core op of the twin gave up on a bounded wait."""
+    return int(_lib().lpc_t_tc_error(int(reset)))
 
 
 def _st():

@@ -84,6 +84,7 @@ def test_conv_fwd_bwd(frames, cin, bf16):
     assert _rel(dx, dxr) < 1e-5 and _rel(dW, dWr) < 1e-5
     # the bias gradient sums the unrounded dy in both modes
     assert _rel(db, dy.double().sum(0)) < 1e-5
+    assert G.tc_error() == 0  # bf16: forward and dx ran on the tensor cores
 
 
 @pytest.mark.parametrize("bf16", [0, 1])
