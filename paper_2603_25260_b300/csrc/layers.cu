@@ -44,6 +44,9 @@ __device__ __forceinline__ void load_row(const int8_t* p, int32_t (&w)[CIN / 4])
 }
 
 // Shared-memory image of one layer: W words, wsum, bias, mult, slope (int32).
+// W is kept four words a lane: int4 (slice c, words 4q .. 4q + 3, lane) at
+// index (c (cin / 16) + q) 32 + lane, so that a lane reads its weights of
+// four dp4a's in one 16-byte load (a warp's load: 512 contiguous bytes).
 struct SmemLayer {
   int32_t* W;
   int32_t* wsum;
@@ -61,7 +64,25 @@ __device__ __forceinline__ SmemLayer stage_layer(const DLayer& L, int32_t* sm) {
   s.bias = s.wsum + L.S * 32;
   s.mult = s.bias + P * 32;
   s.slope = s.mult + P * 32;
-  for (int i = threadIdx.x; i < nw; i += blockDim.x) s.W[i] = L.Wp[i];
+  // packed word (4 g + e) 32 + lane goes to int4 g 32 + lane, component e;
+  // four int4's a thread per pass, their 16 loads in flight together
+  const int nq = nw / 4;
+  int4* Wq = reinterpret_cast<int4*>(s.W);
+  for (int d0 = threadIdx.x; d0 < nq; d0 += 4 * blockDim.x) {
+    int32_t v[4][4];
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+      const int d = d0 + e * (int)blockDim.x;
+      const int g = (d < nq ? d : 0) >> 5, ln = d & 31;
+#pragma unroll
+      for (int q = 0; q < 4; q++) v[e][q] = __ldg(L.Wp + (4 * g + q) * 32 + ln);
+    }
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+      const int d = d0 + e * (int)blockDim.x;
+      if (d < nq) Wq[d] = make_int4(v[e][0], v[e][1], v[e][2], v[e][3]);
+    }
+  }
   for (int i = threadIdx.x; i < L.S * 32; i += blockDim.x) s.wsum[i] = L.wsum[i];
   for (int i = threadIdx.x; i < P * 32; i += blockDim.x) {
     s.bias[i] = L.bias[i];
@@ -82,9 +103,15 @@ static size_t smem_layer_bytes(const DLayer& L) { return smem_layer_bytes_dev(L)
 template <int CIN>
 __device__ __forceinline__ int32_t dot_slice(const int32_t (&x)[CIN / 4], const int32_t* W,
                                              int slice, int lane, int32_t acc) {
-  const int32_t* w = W + slice * (CIN / 4) * 32 + lane;
+  const int4* w = reinterpret_cast<const int4*>(W) + slice * (CIN / 16) * 32 + lane;
 #pragma unroll
-  for (int k = 0; k < CIN / 4; k++) acc = __dp4a(x[k], w[k * 32], acc);
+  for (int q = 0; q < CIN / 16; q++) {
+    const int4 t = w[q * 32];
+    acc = __dp4a(x[4 * q], t.x, acc);
+    acc = __dp4a(x[4 * q + 1], t.y, acc);
+    acc = __dp4a(x[4 * q + 2], t.z, acc);
+    acc = __dp4a(x[4 * q + 3], t.w, acc);
+  }
   return acc;
 }
 
@@ -117,6 +144,7 @@ void launch_embed(const DEmb& E, const uint8_t* codes, const int64_t* d_n, int64
 // while the current ones are computed (two buffers).  Then the warp walks
 // the 32 children, lane = output channel, reading each row as a broadcast.
 constexpr int kUpGroup = 32;
+constexpr int kUpIlp = 4;  // children computed side by side
 
 template <int CIN>
 __global__ void __launch_bounds__(kWarps * 32)
@@ -124,11 +152,9 @@ k_up_prune(DLayer L, const uint64_t* __restrict__ ckey, const uint32_t* __restri
            const int64_t* d_nc, const int8_t* __restrict__ x, int x_stride, int8_t* out,
            int out_stride, int out_col) {
   extern __shared__ int32_t sm[];
-  const SmemLayer s = stage_layer(L, sm);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   int8_t* stage = reinterpret_cast<int8_t*>(sm + smem_layer_bytes_dev(L) / 4) +
                   (size_t)w * 2 * kUpGroup * CIN;
-  __syncthreads();
   const int64_t n = *d_nc;
   const int64_t step = warps_total() * kUpGroup;
   // lane's child of group g0: slot, and its parent row copied into buffer b
@@ -148,7 +174,9 @@ k_up_prune(DLayer L, const uint64_t* __restrict__ ckey, const uint32_t* __restri
   };
   int64_t g0 = warp_id_global() * kUpGroup;
   int b = 0;
-  int c_cur = g0 < n ? issue(g0, 0) : 0;
+  int c_cur = g0 < n ? issue(g0, 0) : 0;  // in flight while the layer is staged
+  const SmemLayer s = stage_layer(L, sm);
+  __syncthreads();
   for (; g0 < n; g0 += step, b ^= 1) {
     const int c_next = g0 + step < n ? issue(g0 + step, b ^ 1) : 0;
     if (g0 + step < n)
@@ -157,7 +185,44 @@ k_up_prune(DLayer L, const uint64_t* __restrict__ ckey, const uint32_t* __restri
       tc::cp_async_wait<0>();
     __syncwarp();
     const int m = (int)(n - g0 < kUpGroup ? n - g0 : kUpGroup);
-    for (int j = 0; j < m; j++) {
+    // four children at a time: independent dp4a chains overlap
+    int j = 0;
+    for (; j + kUpIlp <= m; j += kUpIlp) {
+      int c[kUpIlp];
+      int32_t acc[kUpIlp];
+      int32_t xv[kUpIlp][CIN / 4];
+#pragma unroll
+      for (int u = 0; u < kUpIlp; u++) {
+        c[u] = __shfl_sync(0xffffffffu, c_cur, j + u);
+        const int4* row = reinterpret_cast<const int4*>(stage + (b * kUpGroup + j + u) * CIN);
+#pragma unroll
+        for (int i = 0; i < CIN / 16; i++) {
+          const int4 t = row[i];
+          xv[u][4 * i] = t.x, xv[u][4 * i + 1] = t.y, xv[u][4 * i + 2] = t.z,
+          xv[u][4 * i + 3] = t.w;
+        }
+        acc[u] = s.bias[c[u] * 32 + lane] - L.z_in * s.wsum[c[u] * 32 + lane];
+      }
+      const int4* Wq = reinterpret_cast<const int4*>(s.W) + lane;
+#pragma unroll
+      for (int q = 0; q < CIN / 16; q++)
+#pragma unroll
+        for (int u = 0; u < kUpIlp; u++) {
+          const int4 t = Wq[(c[u] * (CIN / 16) + q) * 32];
+          acc[u] = __dp4a(xv[u][4 * q], t.x, acc[u]);
+          acc[u] = __dp4a(xv[u][4 * q + 1], t.y, acc[u]);
+          acc[u] = __dp4a(xv[u][4 * q + 2], t.z, acc[u]);
+          acc[u] = __dp4a(xv[u][4 * q + 3], t.w, acc[u]);
+        }
+#pragma unroll
+      for (int u = 0; u < kUpIlp; u++) {
+        int32_t a = acc[u];
+        if (L.prelu) a = prelu(a, s.slope[c[u] * 32 + lane]);
+        out[(g0 + j + u) * out_stride + out_col + lane] =
+            (int8_t)requant(a, s.mult[c[u] * 32 + lane], L.shift, L.z_out);
+      }
+    }
+    for (; j < m; j++) {
       const int c = __shfl_sync(0xffffffffu, c_cur, j);
       int32_t xv[CIN / 4];
       const int4* row = reinterpret_cast<const int4*>(stage + (b * kUpGroup + j) * CIN);
@@ -213,11 +278,9 @@ k_down(DLayer L, const uint64_t* __restrict__ ckey, const uint32_t* __restrict__
        const int64_t* d_np, const int8_t* __restrict__ x, int x_stride, int8_t* out,
        int out_stride, int out_col) {
   extern __shared__ int32_t sm[];
-  const SmemLayer s = stage_layer(L, sm);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   constexpr int kBuf = kDownRows * CIN + kDownRows;  // rows, then slots
   int8_t* stage = reinterpret_cast<int8_t*>(sm + smem_layer_bytes_dev(L) / 4) + (size_t)w * 2 * kBuf;
-  __syncthreads();
   const int64_t n = *d_np;
   const int64_t step = warps_total() * kDownGroup;
   // lane j <= 16 holds poff[p0 + j] (clamped at the last parent)
@@ -238,7 +301,9 @@ k_down(DLayer L, const uint64_t* __restrict__ ckey, const uint32_t* __restrict__
   };
   int64_t p0 = warp_id_global() * kDownGroup;
   int b = 0;
-  uint32_t o_cur = p0 < n ? issue(p0, 0) : 0;
+  uint32_t o_cur = p0 < n ? issue(p0, 0) : 0;  // in flight while the layer is staged
+  const SmemLayer s = stage_layer(L, sm);
+  __syncthreads();
   for (; p0 < n; p0 += step, b ^= 1) {
     const uint32_t o_next = p0 + step < n ? issue(p0 + step, b ^ 1) : 0;
     if (p0 + step < n)
@@ -249,7 +314,62 @@ k_down(DLayer L, const uint64_t* __restrict__ ckey, const uint32_t* __restrict__
     const int8_t* buf = stage + b * kBuf;
     const uint32_t o0 = __shfl_sync(0xffffffffu, o_cur, 0);
     const int m = (int)(n - p0 < kDownGroup ? n - p0 : kDownGroup);
-    for (int j = 0; j < m; j++) {
+    // four parents at a time: their children's dp4a chains are independent;
+    // a parent with fewer children repeats its last row and drops the sum.
+    // A parent without children (a corrupt code 0, or the capacity clamp)
+    // reads row ra, which this group may not have copied: its slot is masked
+    // so that a stale byte still indexes the weights in range.
+    int j = 0;
+    for (; j + kUpIlp <= m; j += kUpIlp) {
+      int ra[kUpIlp], len[kUpIlp], maxlen = 0;
+      int32_t acc[kUpIlp];
+#pragma unroll
+      for (int u = 0; u < kUpIlp; u++) {
+        ra[u] = min((int)(__shfl_sync(0xffffffffu, o_cur, j + u) - o0), kDownRows);
+        const int rb = min((int)(__shfl_sync(0xffffffffu, o_cur, j + u + 1) - o0), kDownRows);
+        len[u] = rb - ra[u];
+        maxlen = max(maxlen, len[u]);
+        acc[u] = s.bias[lane];
+      }
+      for (int k = 0; k < maxlen; k++) {
+        int c[kUpIlp];
+        int32_t xv[kUpIlp][CIN / 4], part[kUpIlp];
+#pragma unroll
+        for (int u = 0; u < kUpIlp; u++) {
+          const int r = ra[u] + max(0, min(k, len[u] - 1));
+          c[u] = buf[kDownRows * CIN + r] & 7;
+          const int4* row = reinterpret_cast<const int4*>(buf + r * CIN);
+#pragma unroll
+          for (int i = 0; i < CIN / 16; i++) {
+            const int4 t = row[i];
+            xv[u][4 * i] = t.x, xv[u][4 * i + 1] = t.y, xv[u][4 * i + 2] = t.z,
+            xv[u][4 * i + 3] = t.w;
+          }
+          part[u] = -L.z_in * s.wsum[c[u] * 32 + lane];
+        }
+        const int4* Wq = reinterpret_cast<const int4*>(s.W) + lane;
+#pragma unroll
+        for (int q = 0; q < CIN / 16; q++)
+#pragma unroll
+          for (int u = 0; u < kUpIlp; u++) {
+            const int4 t = Wq[(c[u] * (CIN / 16) + q) * 32];
+            part[u] = __dp4a(xv[u][4 * q], t.x, part[u]);
+            part[u] = __dp4a(xv[u][4 * q + 1], t.y, part[u]);
+            part[u] = __dp4a(xv[u][4 * q + 2], t.z, part[u]);
+            part[u] = __dp4a(xv[u][4 * q + 3], t.w, part[u]);
+          }
+#pragma unroll
+        for (int u = 0; u < kUpIlp; u++) acc[u] += k < len[u] ? part[u] : 0;
+      }
+#pragma unroll
+      for (int u = 0; u < kUpIlp; u++) {
+        int32_t a = acc[u];
+        if (L.prelu) a = prelu(a, s.slope[lane]);
+        out[(p0 + j + u) * out_stride + out_col + lane] =
+            (int8_t)requant(a, s.mult[lane], L.shift, L.z_out);
+      }
+    }
+    for (; j < m; j++) {
       const int r0 = min((int)(__shfl_sync(0xffffffffu, o_cur, j) - o0), kDownRows);
       const int r1 = min((int)(__shfl_sync(0xffffffffu, o_cur, j + 1) - o0), kDownRows);
       int32_t acc = s.bias[lane];
