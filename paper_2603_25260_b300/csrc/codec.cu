@@ -212,9 +212,6 @@ constexpr int64_t kCoarseChunk = 512;
 size_t coarse_level_bound(int64_t n) {
   return 2 * (size_t)n + 8 * (size_t)((n + kCoarseChunk - 1) / kCoarseChunk);
 }
-// Batches of at least this many points build their three lowest coarse
-// heights with the multi-block scan.
-constexpr int64_t kCoarseScanPoints = 262144;
 constexpr int kMaxL = 19;  // 3 L Morton bits stay below the frame bits
 
 void put_varint(std::vector<uint8_t>& o, uint64_t v) {
@@ -367,6 +364,7 @@ int Codec::create(const lpc_config& cfg, const void* blob, size_t len) {
   add((void**)&sort_.hist, 4 * 256 * (sort_tiles(P) + 1));
   scan_.max_tiles = scan_tiles_for(P);
   add((void**)&scan_.tiles, 4 * scan_.max_tiles);
+  add((void**)&d_cup_, 4 * 32 * coarse_up_blocks(P));
   hash_.cap = 1024;
   while (hash_.cap < 2 * P) hash_.cap <<= 1;
   add((void**)&hash_.slots, 16 * hash_.cap);
@@ -607,11 +605,8 @@ int Codec::build_levels_device(int nf, const int32_t* const* xyz, const int64_t*
   // root; frames with a smaller depth carry their root up unchanged
   max_h_ = kHeights - 1;
   if (coarse) {
-    // large batches: the lowest coarse heights are big enough for the
-    // multi-block scan
-    launch_coarse_up(key_[kHeights - 1], d_N_ + kHeights - 1, maxL, d_keys0_, sort_.alt,
-                     coarse_codes(kHeights), P_, d_cN_, nf, d_cfoff_,
-                     total >= kCoarseScanPoints ? 3 : 0, P_, scan_, st_);
+    launch_coarse_up(key_[kHeights - 1], d_N_ + kHeights - 1, P_, maxL, coarse_codes(kHeights), P_,
+                     d_cN_, nf, d_cfoff_, d_cup_, st_);
     max_h_ = std::max(maxL, kHeights - 1);
     if (max_h_ >= kHeights) {
       cudaMemcpyAsync(h_cN_ + kHeights, d_cN_ + kHeights, 8 * (max_h_ - kHeights + 1),

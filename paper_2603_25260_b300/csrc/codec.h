@@ -283,6 +283,7 @@ class Codec {
   // keys ping-pong through the sort buffers, codes in the (then unused)
   // table buffer, one P-byte slot per height
   int64_t* d_cN_ = nullptr;        // [kMaxDepth + 2] rows per coarse height
+  uint32_t* d_cup_ = nullptr;      // tile counts and offsets of the coarse heights (encoder)
   int64_t* d_cfoff_ = nullptr;     // [kMaxDepth + 1][F + 1] frame offsets per coarse height
   int64_t* h_cN_ = nullptr;
   int64_t* h_cfoff_ = nullptr;

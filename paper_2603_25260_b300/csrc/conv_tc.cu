@@ -35,6 +35,7 @@
 // swizzled K-major).  Every wait is bounded; a wait that gives up raises a
 // shared abort flag that ends every other wait, and the CTA drains its own
 // copies and MMAs before it frees its tensor memory.
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include <string.h>
@@ -50,11 +51,18 @@ namespace lpc {
 namespace {
 
 constexpr int kTileM = 128;
-constexpr int kProdWarps = 8;                   // warps 0 .. kProdWarps-1
-constexpr int kProducers = 32 * kProdWarps;
-constexpr int kEpilogue = 128;                  // the next 4 warps (TMEM quadrants w % 4)
-constexpr int kMmaWarp = kProdWarps + 4;        // then the MMA warp
-constexpr int kThreads = kProducers + kEpilogue + 32;
+constexpr int kEpilogue = 128;  // 4 warps after the producers (TMEM quadrants w % 4)
+
+// Thread roles of the two gather schedules: 8 producer warps of cp.async
+// copies (GATHER 0), or one producer warp of TMA gather4 loads (GATHER 1);
+// then the 4 epilogue warps and the MMA warp.
+template <int GATHER>
+struct Roles {
+  static constexpr int kProdWarps = GATHER ? 1 : 8;  // warps 0 .. kProdWarps-1
+  static constexpr int kProducers = 32 * kProdWarps;
+  static constexpr int kMmaWarp = kProdWarps + 4;
+  static constexpr int kThreads = kProducers + kEpilogue + 32;
+};
 
 // Variants the autotuner chooses from: the stage-ring depth and the order in
 // which a CTA walks its tiles (strided over the grid, or one contiguous run
@@ -152,22 +160,41 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
 }
 
-// Barrier of the 128 producer threads that also ORs a flag over them, so
-// that they all take the same decision.
+// Barrier of the producer threads that also ORs a flag over them, so that
+// they all take the same decision.
+template <int NPROD>
 __device__ __forceinline__ bool producer_sync_or(bool v) {
+  if (NPROD == 32) return __any_sync(0xffffffffu, v);
   uint32_t r;
   asm volatile(
       "{\n.reg .pred p, q;\nsetp.ne.u32 p, %1, 0;\nbar.red.or.pred q, 1, %2, p;\n"
       "selp.u32 %0, 1, 0, q;\n}\n"
       : "=r"(r)
-      : "r"((uint32_t)v), "n"(kProducers)
+      : "r"((uint32_t)v), "n"(NPROD)
       : "memory");
   return r != 0;
 }
 
-template <int CIN, int ALT, int ORDER>
-__global__ void __launch_bounds__(kThreads, 1)
-k_conv333_tc(ConvTcArgs a) {
+// TMA gather of four rows (one row high boxes of the 2D tensor map: columns
+// from col, rows r0..r3) into 4 consecutive swizzled rows at dst, counted
+// on bar.  A row at or past the map's row extent is not read: it lands as
+// zeros.
+__device__ __forceinline__ void tma_gather4(uint32_t dst, const void* tmap, int col, int r0,
+                                            int r1, int r2, int r3, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cta.global.tile::gather4.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst),
+      "l"(tmap), "r"(col), "r"(r0), "r"(r1), "r"(r2), "r"(r3), "r"(tc::smem_u32(bar))
+      : "memory");
+}
+
+template <int CIN, int ALT, int ORDER, int GATHER>
+__global__ void __launch_bounds__(Roles<GATHER>::kThreads, 1)
+k_conv333_tc(const __grid_constant__ ConvTcArgs a) {
+  constexpr int kProdWarps = Roles<GATHER>::kProdWarps;
+  constexpr int kProducers = Roles<GATHER>::kProducers;
+  constexpr int kMmaWarp = Roles<GATHER>::kMmaWarp;
+  constexpr int kThreads = Roles<GATHER>::kThreads;
   using Cfg = ConvCfg<CIN, stages_of<CIN>(ALT), step_of<CIN>(ALT), nbr_bufs_of<CIN>(ALT)>;
   constexpr int S = Cfg::kStages;
   constexpr int G = Cfg::kG;       // offsets per pipeline step
@@ -190,7 +217,8 @@ k_conv333_tc(ConvTcArgs a) {
   if (w == kMmaWarp) tc::tmem_alloc(&tslot, 512);
   if (t == 0) {
     for (int s = 0; s < SG; s++) {
-      tc::mbar_init(&full_bar[s], kProducers);
+      // cp.async: every producer's copies arrive; TMA: one expect_tx arrival
+      tc::mbar_init(&full_bar[s], GATHER ? 1 : kProducers);
       tc::mbar_init(&empty_bar[s], 1);
     }
     for (int b = 0; b < 2; b++) {
@@ -254,22 +282,26 @@ k_conv333_tc(ConvTcArgs a) {
       }
     };
     issue_nbr(0);
-    // this thread's copies of a stage: (row, 16-byte chunk) pairs fixed for
-    // the whole kernel, so their swizzled destinations and source columns
-    // are formed once; per stage only the neighbour's row changes
-    constexpr int kPer = kTileM * Cfg::kChunks / kProducers;
-    static_assert(kPer * kProducers == kTileM * Cfg::kChunks, "copies must split evenly");
+    // cp.async: this thread's copies of a stage are (row, 16-byte chunk)
+    // pairs fixed for the whole kernel, so their swizzled destinations and
+    // source columns are formed once; per stage only the neighbour's row
+    // changes.  TMA: lane l loads rows 4l .. 4l + 3 of every stage.
+    constexpr int kPer = GATHER ? 1 : kTileM * Cfg::kChunks / kProducers;
+    static_assert(GATHER || kPer * kProducers == kTileM * Cfg::kChunks,
+                  "copies must split evenly");
     int prow[kPer];
     uint32_t pdst[kPer];
     const unsigned char* psrc[kPer];
     const uint32_t rbytes = (uint32_t)a.x_stride * 2;
+    if (!GATHER) {
 #pragma unroll
-    for (int k = 0; k < kPer; k++) {
-      const int q = t + k * kProducers;
-      const int c = q % Cfg::kChunks;
-      prow[k] = q / Cfg::kChunks;
-      pdst[k] = tc::swz<Cfg::SW>(prow[k] * Cfg::RB + c * 16);
-      psrc[k] = reinterpret_cast<const unsigned char*>(a.xb) + c * 16;
+      for (int k = 0; k < kPer; k++) {
+        const int q = t + k * kProducers;
+        const int c = q % Cfg::kChunks;
+        prow[k] = q / Cfg::kChunks;
+        pdst[k] = tc::swz<Cfg::SW>(prow[k] * Cfg::RB + c * 16);
+        psrc[k] = reinterpret_cast<const unsigned char*>(a.xb) + c * 16;
+      }
     }
     uint32_t u = 0;  // stages filled so far
     for (int lt = 0; lt < my_tiles; lt++) {
@@ -277,46 +309,78 @@ k_conv333_tc(ConvTcArgs a) {
       int32_t* sNbr = sNbr0 + (lt % NB) * kTileM * 27;
       // every producer is done issuing the previous tile's copies; all leave
       // together if any saw the abort flag
-      if (producer_sync_or(*abort != 0)) break;
+      if (producer_sync_or<kProducers>(*abort != 0)) break;
       // the next tile's map a tile ahead (two buffers), or this tile's now
       // that the one buffer is free (tile 0's went out before the loop)
       if (NB == 2) issue_nbr(lt + 1);
       else if (lt > 0) issue_nbr(lt);
       if (r0 + kTileM <= n) {
-        if (producer_sync_or(!wait_or_abort(&nbr_bar[lt % NB], (lt / NB) & 1, abort))) break;
+        if (producer_sync_or<kProducers>(!wait_or_abort(&nbr_bar[lt % NB], (lt / NB) & 1, abort)))
+          break;
         last_used = lt;
       } else {
         const int64_t base = r0 * 27, lim = n * 27;
         for (int i = t; i < kTileM * 27; i += kProducers)
           sNbr[i] = base + i < lim ? __ldg(a.nbr + base + i) : -1;
-        producer_sync_or(false);
+        producer_sync_or<kProducers>(false);
       }
+      // a failed wait has raised the abort flag: the step loop ends here and
+      // the producers leave together at the next tile's barrier
       for (int og = 0; og < 27 / G; og++, u++) {
         const int sg = (int)(u % SG);
-        if (u >= (uint32_t)SG && !wait_or_abort(&empty_bar[sg], ((u / SG) - 1) & 1, abort))
-          break;
+        if (GATHER) {
+          // one lane's failed wait ends the warp's issuing together
+          if (!__all_sync(0xffffffffu, u < (uint32_t)SG ||
+                                           wait_or_abort(&empty_bar[sg], ((u / SG) - 1) & 1, abort)))
+            break;
+          if (lane == 0) mbar_expect(&full_bar[sg], (uint32_t)(G * Cfg::kStageBytes));
+          __syncwarp();
+          const int32_t* m = sNbr + lane * 4 * 27;
 #pragma unroll
-        for (int i = 0; i < G; i++) {
-          const int o = og * G + i;
-          const uint32_t sbase = tc::smem_u32(sA + (size_t)(sg * G + i) * Cfg::kStageBytes);
-#pragma unroll
-          for (int k = 0; k < kPer; k++) {
-            const int32_t nb = sNbr[prow[k] * 27 + o];
-            // absent neighbours (nb < 0): zero-filled, the address kept valid
-            const uint32_t r = (uint32_t)max(nb, 0);
-            tc::cp_async16(sbase + pdst[k], psrc[k] + (size_t)r * rbytes, nb >= 0);
+          for (int i = 0; i < G; i++) {
+            const int o = og * G + i;
+            const uint32_t dst = tc::smem_u32(sA + (size_t)(sg * G + i) * Cfg::kStageBytes) +
+                                 (uint32_t)(lane * 4 * Cfg::RB);
+            // absent neighbours (< 0) name the row past the map's extent
+            const int32_t n0 = m[o], n1 = m[27 + o], n2 = m[54 + o], n3 = m[81 + o];
+            tma_gather4(dst, &a.tmap, 0, n0 < 0 ? a.tma_rows : n0, n1 < 0 ? a.tma_rows : n1,
+                        n2 < 0 ? a.tma_rows : n2, n3 < 0 ? a.tma_rows : n3, &full_bar[sg]);
           }
+        } else {
+          if (u >= (uint32_t)SG && !wait_or_abort(&empty_bar[sg], ((u / SG) - 1) & 1, abort))
+            break;
+#pragma unroll
+          for (int i = 0; i < G; i++) {
+            const int o = og * G + i;
+            const uint32_t sbase = tc::smem_u32(sA + (size_t)(sg * G + i) * Cfg::kStageBytes);
+#pragma unroll
+            for (int k = 0; k < kPer; k++) {
+              const int32_t nb = sNbr[prow[k] * 27 + o];
+              // absent neighbours (nb < 0): zero-filled, the address kept valid
+              const uint32_t r = (uint32_t)max(nb, 0);
+              tc::cp_async16(sbase + pdst[k], psrc[k] + (size_t)r * rbytes, nb >= 0);
+            }
+          }
+          // arrives on the step's barrier once this thread's copies have landed
+          asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(
+                           tc::smem_u32(&full_bar[sg]))
+                       : "memory");
         }
-        // arrives on the step's barrier once this thread's copies have landed
-        asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(
-                         tc::smem_u32(&full_bar[sg]))
-                     : "memory");
       }
     }
     // a neighbour-row copy issued but not consumed (abort) lands before exit
     if (t == 0 && last_issued > last_used)
       tc::mbar_wait(&nbr_bar[last_issued % NB], (last_issued / NB) & 1);
-    tc::cp_async_wait<0>();  // every copy of this thread has landed
+    if (GATHER) {
+      // the loads of the last steps issued land before the CTA exits (the
+      // MMA thread has waited for them unless it stopped on abort)
+      if (lane == 0)
+        for (uint32_t q = u > (uint32_t)SG ? u - SG : 0; q < u; q++)
+          tc::mbar_wait(&full_bar[q % SG], (q / SG) & 1);
+      __syncwarp();
+    } else {
+      tc::cp_async_wait<0>();  // every copy of this thread has landed
+    }
   } else if (w == kMmaWarp) {
     // ---------------------------------------------------------------- MMA --
     if (lane == 0) {
@@ -335,7 +399,9 @@ k_conv333_tc(ConvTcArgs a) {
             ok = false;
             break;
           }
-          tc::fence_async_smem();  // the step's landed copies, to the MMA's proxy
+          // the step's landed cp.async copies, to the MMA's proxy (TMA
+          // loads are in that proxy already)
+          if (!GATHER) tc::fence_async_smem();
           tc::tc_fence_after();
 #pragma unroll
           for (int i = 0; i < G; i++) {
@@ -364,7 +430,7 @@ k_conv333_tc(ConvTcArgs a) {
     __syncwarp();
   } else {
     // ----------------------------------------------------------- epilogue --
-    const int e = t - kProducers;            // row of the tile = TMEM lane
+    const int e = ((w & 3) << 5) | lane;  // row of the tile = TMEM lane (the warp's quadrant)
     const uint32_t lane_off = (uint32_t)((w & 3) * 32) << 16;
     for (int lt = 0; lt < my_tiles; lt++) {
       const int b = lt & 1;
@@ -505,24 +571,64 @@ void launch_to_bf16_cat(const int8_t* a, int a_stride, const int8_t* b, int b_st
 
 namespace {
 
-template <int CIN, int ALT, int ORDER>
+template <int CIN, int ALT, int ORDER, int GATHER>
 void launch_variant(const ConvTcArgs& a, int blocks, cudaStream_t st) {
   constexpr size_t smem =
       ConvCfg<CIN, stages_of<CIN>(ALT), step_of<CIN>(ALT), nbr_bufs_of<CIN>(ALT)>::kSmem;
   static_assert(smem <= 232448, "shared memory of a conv variant exceeds the limit");
-  cudaFuncSetAttribute(k_conv333_tc<CIN, ALT, ORDER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)smem);
-  k_conv333_tc<CIN, ALT, ORDER><<<blocks, kThreads, smem, st>>>(a);
+  auto* k = k_conv333_tc<CIN, ALT, ORDER, GATHER>;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k<<<blocks, Roles<GATHER>::kThreads, smem, st>>>(a);
 }
 
-template <int CIN>
+template <int CIN, int GATHER>
 void launch_cin(const ConvTcArgs& a, int blocks, int variant, cudaStream_t st) {
-  switch (variant) {
-    case 1: launch_variant<CIN, 1, 0>(a, blocks, st); break;
-    case 2: launch_variant<CIN, 0, 1>(a, blocks, st); break;
-    case 3: launch_variant<CIN, 1, 1>(a, blocks, st); break;
-    default: launch_variant<CIN, 0, 0>(a, blocks, st); break;
+  switch (variant & 3) {
+    case 1: launch_variant<CIN, 1, 0, GATHER>(a, blocks, st); break;
+    case 2: launch_variant<CIN, 0, 1, GATHER>(a, blocks, st); break;
+    case 3: launch_variant<CIN, 1, 1, GATHER>(a, blocks, st); break;
+    default: launch_variant<CIN, 0, 0, GATHER>(a, blocks, st); break;
   }
+}
+
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                 const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                 const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                 CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// The driver's tensor-map encoder, looked up once through the runtime.
+EncodeTiled encoder() {
+  static EncodeTiled fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<EncodeTiled>(p);
+  }();
+  return fn;
+}
+
+// The bf16 input rows as a 2D tensor (cin columns, rows rows, row pitch
+// x_stride elements) with one-row boxes of the whole row, swizzled like the
+// A stages (64-byte rows: 64B swizzle, 128-byte rows: 128B).
+bool encode_rows(ConvTcArgs& a, int cin, int64_t rows) {
+  static_assert(sizeof(TmaDesc) == sizeof(CUtensorMap), "tensor map size");
+  const EncodeTiled fn = encoder();
+  if (!fn || rows <= 0 || rows > 0x7fffffff || ((uintptr_t)a.xb & 15) || (a.x_stride * 2) % 16)
+    return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)cin, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)a.x_stride * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)cin, 1};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = fn(reinterpret_cast<CUtensorMap*>(&a.tmap), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                        2, const_cast<void*>(a.xb), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        cin == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                        CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  a.tma_rows = (int)rows;
+  return r == CUDA_SUCCESS;
 }
 
 }  // namespace
@@ -532,8 +638,20 @@ void launch_conv333_tc(const ConvTcArgs& a, int cin, int64_t n_host, cudaStream_
   if (n_host <= 0) return;
   const int64_t ntiles = (n_host + kTileM - 1) / kTileM;
   const int blocks = (int)std::min<int64_t>(ntiles, 148);
-  if (cin == 64) launch_cin<64>(a, blocks, variant, st);
-  else launch_cin<32>(a, blocks, variant, st);
+  if (variant & 4) {
+    // TMA gather: the map covers rows [0, n_host), every neighbour index the
+    // kernel reads is below the level's size <= n_host.  An input the
+    // encoder rejects (unaligned rows) takes the copy gather of the same ring.
+    ConvTcArgs b = a;
+    if (encode_rows(b, cin, n_host)) {
+      if (cin == 64) launch_cin<64, 1>(b, blocks, variant, st);
+      else launch_cin<32, 1>(b, blocks, variant, st);
+      count_launches(1);
+      return;
+    }
+  }
+  if (cin == 64) launch_cin<64, 0>(a, blocks, variant, st);
+  else launch_cin<32, 0>(a, blocks, variant, st);
   count_launches(1);
 }
 

@@ -83,10 +83,14 @@ void launch_expand(const uint64_t* pkeys, const uint8_t* pcodes, const int64_t* 
 // scan_heights: how many of the lowest coarse heights (7, 8, ...) take the
 // multi-block scan (large batches) before the single-block kernel; cap
 // bounds their sizes.
-void launch_coarse_up(const uint64_t* key6, const int64_t* d_n6, int top, uint64_t* k0,
-                      uint64_t* k1, uint8_t* codes, int64_t stride, int64_t* cN, int nf,
-                      int64_t* foff, int scan_heights, int64_t cap, const ScanScratch& s,
-                      cudaStream_t st);
+// Encoder's coarse heights 7..top from the sorted keys of height 6 (count on
+// the device, at most cap6): codes of height h into codes + (h - 7) *
+// stride, sizes into cN[h], frame offsets into foff[h * (nf + 1) + f];
+// scratch holds 32 * coarse_up_blocks(cap6) words.
+int64_t coarse_up_blocks(int64_t cap6);
+void launch_coarse_up(const uint64_t* key6, const int64_t* d_n6, int64_t cap6, int top,
+                      uint8_t* codes, int64_t stride, int64_t* cN, int nf, int64_t* foff,
+                      uint32_t* scratch, cudaStream_t st);
 // counts: host copy of the coarse level sizes by height, d_counts the same
 // on the device (the large heights expand with the multi-block scan).
 void launch_coarse_down(const uint64_t* roots, int top, const uint8_t* codes, int64_t stride,
@@ -235,7 +239,13 @@ void launch_down(const DLayer& W, const uint64_t* ckey, const uint32_t* poff, co
 // ResBlock's residual merge is fused into the epilogue (y1 = the first conv's
 // int8 output).  outb (optional) receives bf16 (q - outb_z) rows for the next
 // conv.
+// A TMA tensor map (the driver's 128-byte CUtensorMap), kept opaque here.
+struct alignas(64) TmaDesc {
+  unsigned long long q[16];
+};
 struct ConvTcArgs {
+  TmaDesc tmap;          // the bf16 input rows, set by the launcher (TMA gather)
+  int tma_rows;          // the map's row extent: a row index here reads as zeros
   const uint16_t* wimg;  // packed weights, conv_tc_weight_bytes(cin)
   const int32_t* bias;
   const int32_t* mult;
@@ -258,10 +268,10 @@ struct ConvTcArgs {
 };
 size_t conv_tc_weight_bytes(int cin);
 void pack_conv_tc_weights(const int8_t* W, int cin, uint16_t* img);
-// variant in [0, kConvVariants): stage-ring depth (bit 0) and tile order
-// (bit 1), chosen by the codec's autotuner; every variant gives the same
-// result.
-constexpr int kConvVariants = 4;
+// variant in [0, kConvVariants): ring shape (bit 0), tile order (bit 1) and
+// gather schedule (bit 2: cp.async copies, or TMA gather4 loads), chosen by
+// the codec's autotuner; every variant gives the same result.
+constexpr int kConvVariants = 8;
 void launch_conv333_tc(const ConvTcArgs& a, int cin, int64_t n_host, cudaStream_t st,
                        int variant = 0);
 // int8 rows (stride x_stride) -> bf16 (q - z) rows of `cols` elements.

@@ -419,96 +419,214 @@ void launch_level_up(const uint64_t* ckeys, const int64_t* d_nc, int64_t cap_c, 
 }
 
 // --------------------------------------------------- coarse heights --
-// The coarse heights (above V_{b-1}) are small: one CTA walks all of them in
-// a single launch instead of a scan of three launches per height.
+// The coarse heights (above V_{b-1}) are small.  Decoder: one block walks
+// the heights under 16384 parents each (kCoarseScanMin) in a single launch.
 constexpr int kCoThreads = 1024, kCoItems = 4, kCoChunk = kCoThreads * kCoItems;
 
-// Encoder: heights 7..top from the keys of height 6 by floor-halving with
-// duplicate removal; codes of height h into codes + (h - 7) * stride; keys
-// ping-pong through k0 / k1; counts into cN[h]; frame offsets of every height
-// into foff[h * (nf + 1) + f].
-__global__ void __launch_bounds__(kCoThreads)
-k_coarse_up(const uint64_t* __restrict__ first_src, const int64_t* d_nsrc, int h0, int top,
-            uint64_t* k0, uint64_t* k1, uint8_t* codes, int64_t stride, int64_t* cN, int nf,
-            int64_t* foff) {
-  __shared__ uint32_t sm[32];
-  const uint64_t* src = first_src;
-  int64_t n = *d_nsrc;
-  for (int h = h0; h <= top; h++) {
-    uint64_t* dst = (h & 1) ? k1 : k0;
-    uint8_t* code = codes + (int64_t)(h - 7) * stride;
-    int64_t run = 0;
-    for (int64_t base = 0; base < n; base += kCoChunk) {
-      const int64_t first = base + (int64_t)threadIdx.x * kCoItems;
-      uint32_t flag[kCoItems], cnt = 0;
+// Encoder: every coarse height 7..top at once, from the sorted keys of
+// height 6.  A node of height h >= 6 is the key's frame bits with its Morton
+// bits shifted down by 3 (h - 6), so key j opens a node at height h exactly
+// when h <= hmax_j: the top height if j opens a frame (or is the first key),
+// else 6 + floor(p / 3) for p the highest Morton bit in which keys j - 1 and
+// j differ (they agree above bit 3 (h - 6) - 1 exactly when p < 3 (h - 6)).
+// The nodes of height h are the keys with hmax >= h, in key order, so a
+// scan of [hmax_j >= h] numbers them; the node of height h - 1 that key j
+// opens has the octant (key_j >> 3 (h - 7)) & 7 within its parent, the node
+// of height h holding key j.  Three launches, all heights together:
+//  - count: per tile of keys, the nodes each height has there (and the
+//    tile's code bytes cleared at every height);
+//  - scan (one block): tile offsets per height, the heights' sizes, and the
+//    offsets of the frames after the last key's;
+//  - emit: every opened node ORs its octant bit into its parent's code and
+//    a key that opens a frame writes that frame's offset at every height.
+// The keys of the coarse heights themselves are not needed and not written.
+constexpr int kCuThreads = 256, kCuItems = 2, kCuTile = kCuThreads * kCuItems;
+constexpr int kCuWords = 8;  // per-thread node counts of heights 7 .. 22, two 16-bit halves a word
+
+int64_t coarse_up_blocks(int64_t cap) { return std::max<int64_t>(1, (cap + kCuTile - 1) / kCuTile); }
+
+__device__ __forceinline__ int open_height(uint64_t prev, uint64_t cur, bool first, int top) {
+  const uint64_t x = prev ^ cur;
+  if (first || (x >> kFrameShift)) return top;
+  const int p = 63 - __clzll((long long)(x & kLowMask));  // keys are unique: x != 0
+  return min(top, 6 + p / 3);
+}
+
+// This thread's kCuItems consecutive keys from j0: their keys, hmax (0 past
+// the end) and the packed counts of the nodes they open per height.
+struct CuItems {
+  uint64_t key[kCuItems];
+  int hm[kCuItems];
+  uint64_t prev;  // the key before j0
+  uint32_t w[kCuWords];
+};
+
+__device__ __forceinline__ void cu_items(const uint64_t* __restrict__ key6, int64_t n6, int64_t j0,
+                                         int top, CuItems& it) {
+  uint64_t prev = j0 > 0 && j0 - 1 < n6 ? key6[j0 - 1] : 0ull;
+  it.prev = prev;
 #pragma unroll
-      for (int i = 0; i < kCoItems; i++) {
-        const int64_t j = first + i;
-        flag[i] = j < n && (j == 0 || parent_key(src[j]) != parent_key(src[j - 1]));
-        cnt += flag[i];
-      }
-      uint32_t tot;
-      int64_t at = run + block_excl_scan<kCoThreads>(cnt, &tot, sm);
+  for (int k = 0; k < kCuWords; k++) it.w[k] = 0;
 #pragma unroll
-      for (int i = 0; i < kCoItems; i++) {
-        if (!flag[i]) continue;
-        const int64_t j = first + i;
-        const uint64_t p = parent_key(src[j]);
-        uint32_t c = 0;
-        for (int64_t q = j; q < n && q < j + 8 && parent_key(src[q]) == p; q++)
-          c |= 1u << (src[q] & 7);
-        dst[at] = p;
-        code[at] = (uint8_t)c;
-        at++;
-      }
-      run += tot;
-    }
-    __syncthreads();  // the level is complete before it is searched and read
-    for (int f = threadIdx.x; f <= nf; f += kCoThreads) {
-      int64_t r = run;
-      if (f < nf) {
-        const uint64_t target = (uint64_t)f << kFrameShift;
-        int64_t lo = 0, hi = run;
-        while (lo < hi) {
-          const int64_t mid = (lo + hi) >> 1;
-          if (dst[mid] < target) lo = mid + 1;
-          else hi = mid;
-        }
-        r = lo;
-      }
-      foff[(int64_t)h * (nf + 1) + f] = r;
-    }
-    if (threadIdx.x == 0) cN[h] = run;
-    src = dst;
-    n = run;
-    __syncthreads();
+  for (int i = 0; i < kCuItems; i++) {
+    const int64_t j = j0 + i;
+    const uint64_t cur = j < n6 ? key6[j] : 0ull;
+    it.key[i] = cur;
+    const int hm = j < n6 ? open_height(prev, cur, j == 0, top) : 0;
+    it.hm[i] = hm;
+    prev = cur;
+#pragma unroll
+    for (int k = 0; k < kCuWords; k++)
+      it.w[k] += (uint32_t)(hm >= 7 + 2 * k) | ((uint32_t)(hm >= 8 + 2 * k) << 16);
   }
 }
 
-void launch_coarse_up(const uint64_t* key6, const int64_t* d_n6, int top, uint64_t* k0,
-                      uint64_t* k1, uint8_t* codes, int64_t stride, int64_t* cN, int nf,
-                      int64_t* foff, int scan_heights, int64_t cap, const ScanScratch& s,
-                      cudaStream_t st) {
-  if (top < 7) return;
-  // the first scan_heights heights by the multi-block scan (large levels),
-  // the rest by the single block
-  const uint64_t* src = key6;
-  const int64_t* nsrc = d_n6;
-  int h = 7;
-  for (; h <= top && h < 7 + scan_heights; h++) {
-    uint64_t* dst = (h & 1) ? k1 : k0;
-    launch_level_up(src, nsrc, cap, dst, codes + (int64_t)(h - 7) * stride, nullptr, nullptr,
-                    cN + h, s, st);
-    LevelPtrs lp{};
-    lp.key[0] = dst;
-    lp.n[0] = cN + h;
-    launch_frame_offsets(lp, 1, nf, foff + (int64_t)h * (nf + 1), st);
-    src = dst;
-    nsrc = cN + h;
+__global__ void __launch_bounds__(kCuThreads)
+k_cu_count(const uint64_t* __restrict__ key6, const int64_t* d_n6, int top, uint8_t* codes,
+           int64_t stride, uint32_t* bt, int64_t nbmax) {
+  __shared__ uint32_t ws[kCuThreads / 32][kCuWords];
+  const int64_t n6 = *d_n6;
+  const int64_t b = blockIdx.x, t0 = b * kCuTile;
+  if (t0 >= n6) return;  // the scan reads only the tiles below n6
+  // a height has at most n6 nodes: clear this tile's share of every
+  // height's code bytes before the emit pass ORs bits into them
+  const int64_t e = min(n6, t0 + (int64_t)kCuTile);
+  for (int h = 7; h <= top; h++)
+    for (int64_t i = t0 + threadIdx.x; i < e; i += kCuThreads) codes[(int64_t)(h - 7) * stride + i] = 0;
+  CuItems it;
+  cu_items(key6, n6, t0 + (int64_t)threadIdx.x * kCuItems, top, it);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < kCuWords; k++) {
+    const uint32_t v = __reduce_add_sync(0xffffffffu, it.w[k]);  // halves stay below 2^16
+    if (lane == 0) ws[w][k] = v;
   }
+  __syncthreads();
+  if (threadIdx.x < kCuWords) {
+    uint32_t v = 0;
+#pragma unroll
+    for (int q = 0; q < kCuThreads / 32; q++) v += ws[q][threadIdx.x];
+    bt[(int64_t)(2 * threadIdx.x) * nbmax + b] = v & 0xFFFFu;
+    bt[(int64_t)(2 * threadIdx.x + 1) * nbmax + b] = v >> 16;
+  }
+}
+
+// One warp per height: the tiles' node counts scanned 32 at a time.
+__global__ void __launch_bounds__(32 * 2 * kCuWords)
+k_cu_scan(const uint64_t* __restrict__ key6, const int64_t* d_n6, int top, const uint32_t* bt,
+          uint32_t* bo, int64_t nbmax, int64_t* cN, int nf, int64_t* foff) {
+  const int lane = threadIdx.x & 31, h = 7 + (threadIdx.x >> 5);
   if (h > top) return;
-  k_coarse_up<<<1, kCoThreads, 0, st>>>(src, nsrc, h, top, k0, k1, codes, stride, cN, nf, foff);
-  count_launches(1);
+  const int64_t n6 = *d_n6;
+  const int64_t nb = (n6 + kCuTile - 1) / kCuTile;
+  const uint32_t* src = bt + (int64_t)(h - 7) * nbmax;
+  uint32_t* dst = bo + (int64_t)(h - 7) * nbmax;
+  uint32_t run = 0;
+  for (int64_t base = 0; base < nb; base += 32) {
+    const int64_t i = base + lane;
+    const uint32_t v = i < nb ? src[i] : 0u;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (i < nb) dst[i] = run + x - v;
+    run += __shfl_sync(0xffffffffu, x, 31);
+  }
+  if (lane == 0) cN[h] = run;
+  // frames after the last key's have no node: they start at the end
+  const int lastf = n6 > 0 ? (int)(key6[n6 - 1] >> kFrameShift) : -1;
+  for (int f = lastf + 1 + lane; f <= nf; f += 32) foff[(int64_t)h * (nf + 1) + f] = run;
+}
+
+// OR v into the byte at p through its aligned 32-bit word.
+__device__ __forceinline__ void or_byte(uint8_t* p, uint32_t v) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+  atomicOr(reinterpret_cast<unsigned int*>(a & ~(uintptr_t)3), v << (8 * (a & 3)));
+}
+
+__global__ void __launch_bounds__(kCuThreads)
+k_cu_emit(const uint64_t* __restrict__ key6, const int64_t* d_n6, int top, uint8_t* codes,
+          int64_t stride, const uint32_t* __restrict__ bo, int64_t nbmax, int nf, int64_t* foff) {
+  __shared__ uint32_t ws[kCuThreads / 32][kCuWords];
+  const int64_t n6 = *d_n6;
+  const int64_t b = blockIdx.x, t0 = b * kCuTile;
+  if (t0 >= n6) return;
+  const int64_t j0 = t0 + (int64_t)threadIdx.x * kCuItems;
+  CuItems it;
+  cu_items(key6, n6, j0, top, it);
+  // block-exclusive scan of the packed counts: warp scans, then the warps'
+  // totals in front
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t ex[kCuWords];
+#pragma unroll
+  for (int k = 0; k < kCuWords; k++) {
+    uint32_t x = it.w[k];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    ex[k] = x - it.w[k];
+    if (lane == 31) ws[w][k] = x;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < kCuWords; k++)
+    for (int q = 0; q < w; q++) ex[k] += ws[q][k];
+  // pos[hi]: nodes of height 7 + hi before this thread's next key
+  uint32_t pos[2 * kCuWords];
+#pragma unroll
+  for (int hi = 0; hi < 2 * kCuWords; hi++)
+    pos[hi] = hi + 7 <= top ? bo[(int64_t)hi * nbmax + b] + ((ex[hi >> 1] >> (16 * (hi & 1))) & 0xFFFFu)
+                            : 0u;
+  uint64_t prev = it.prev;
+#pragma unroll
+  for (int i = 0; i < kCuItems; i++) {
+    const int64_t j = j0 + i;
+    if (j >= n6) break;
+    const uint64_t key = it.key[i];
+    const int hm = it.hm[i];
+    const int fj = (int)(key >> kFrameShift);
+    const int fp = j == 0 ? -1 : (int)(prev >> kFrameShift);
+    if (fj != fp) {  // key j opens frame fj (and the empty frames before it) at every height
+#pragma unroll
+      for (int hi = 0; hi < 2 * kCuWords; hi++) {
+        if (hi + 7 > top) break;
+        for (int f = fp + 1; f <= fj; f++) foff[(int64_t)(hi + 7) * (nf + 1) + f] = pos[hi];
+      }
+    }
+    // the node of height h - 1 that key j opens (h - 1 <= hm): its octant
+    // bit into the code of its parent, node pos - 1 (or pos when key j opens
+    // the parent too) of height h
+#pragma unroll
+    for (int hi = 0; hi < 2 * kCuWords; hi++) {
+      const int h = hi + 7;
+      if (h > top || h - 1 > hm) break;
+      const uint32_t P = pos[hi] + (hm >= h ? 1u : 0u) - 1u;
+      or_byte(codes + (int64_t)hi * stride + P, 1u << ((key >> (3 * hi)) & 7));
+    }
+#pragma unroll
+    for (int hi = 0; hi < 2 * kCuWords; hi++)
+      if (hi + 7 <= hm) pos[hi]++;
+    prev = key;
+  }
+}
+
+void launch_coarse_up(const uint64_t* key6, const int64_t* d_n6, int64_t cap6, int top,
+                      uint8_t* codes, int64_t stride, int64_t* cN, int nf, int64_t* foff,
+                      uint32_t* scratch, cudaStream_t st) {
+  if (top < 7) return;
+  top = std::min(top, 6 + 2 * kCuWords);
+  const int64_t nbmax = coarse_up_blocks(cap6);
+  uint32_t* bt = scratch;
+  uint32_t* bo = scratch + (int64_t)2 * kCuWords * nbmax;
+  k_cu_count<<<(unsigned)nbmax, kCuThreads, 0, st>>>(key6, d_n6, top, codes, stride, bt, nbmax);
+  k_cu_scan<<<1, 32 * 2 * kCuWords, 0, st>>>(key6, d_n6, top, bt, bo, nbmax, cN, nf, foff);
+  k_cu_emit<<<(unsigned)nbmax, kCuThreads, 0, st>>>(key6, d_n6, top, codes, stride, bo, nbmax, nf,
+                                                      foff);
+  count_launches(3);
 }
 
 // Decoder: from nf roots (frame f's root at the top height) down to height
@@ -533,9 +651,12 @@ k_coarse_down(const uint64_t* __restrict__ roots, int top, int bottom,
     for (int64_t base = 0; base < n; base += kCoChunk) {
       const int64_t first = base + (int64_t)threadIdx.x * kCoItems;
       uint32_t pc[kCoItems], c = 0;
+      uint64_t pk[kCoItems];  // the parents' keys, loaded beside their codes
 #pragma unroll
       for (int i = 0; i < kCoItems; i++) {
-        pc[i] = first + i < n ? (uint32_t)code[first + i] : 0u;
+        const bool in = first + i < n;
+        pc[i] = in ? (uint32_t)code[first + i] : 0u;
+        pk[i] = in ? src[first + i] : 0ull;
         c += __popc(pc[i]);
       }
       uint32_t tot;
@@ -543,15 +664,16 @@ k_coarse_down(const uint64_t* __restrict__ roots, int top, int bottom,
 #pragma unroll
       for (int i = 0; i < kCoItems; i++) {
         if (!pc[i]) continue;
-        const uint64_t k = src[first + i];
-        for (int b = 0; b < 8; b++)
-          if (pc[i] >> b & 1) {
-            if (at >= cap) {
-              set_error(err, kErrCapacity);
-              break;
-            }
-            dst[at++] = child_key(k, (uint32_t)b);
-          }
+        // the children of the set bits, lowest first; the capacity is
+        // checked once per parent
+        const uint64_t k = pk[i];
+        uint32_t m = pc[i];
+        if (at + __popc(m) > cap) {
+          set_error(err, kErrCapacity);
+          for (; m && at < cap; m &= m - 1) dst[at++] = child_key(k, (uint32_t)(__ffs(m) - 1));
+          continue;
+        }
+        for (; m; m &= m - 1) dst[at++] = child_key(k, (uint32_t)(__ffs(m) - 1));
       }
       run += tot;
     }

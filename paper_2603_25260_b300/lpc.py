@@ -284,13 +284,14 @@ class Codec:
     def tuning(self) -> dict:
         """The conv autotuner's choice per input width and the timed variants
         (milliseconds; bit 0 of a variant = alternative ring shape, bit 1 =
-        contiguous tile order)."""
+        contiguous tile order, bit 2 = TMA gather4 loads of the neighbour rows
+        instead of cp.async copies)."""
         v = (C.c_int * 3)()
-        ms = (C.c_float * 10)()
+        ms = (C.c_float * 18)()
         self._check(self._lib.codec_tuning(self._h, v, ms))
         return {"conv32": v[0], "conv64": v[1], "predictor": v[2],
-                "ms32": [round(x, 4) for x in ms[:4]], "ms64": [round(x, 4) for x in ms[4:8]],
-                "ms_pred": [round(x, 4) for x in ms[8:10]]}
+                "ms32": [round(x, 4) for x in ms[:8]], "ms64": [round(x, 4) for x in ms[8:16]],
+                "ms_pred": [round(x, 4) for x in ms[16:18]]}
 
     def set_tuning(self, conv32: int = -1, conv64: int = -1, predictor: int = -1):
         """Fix kernel variants instead of autotuning them (-1: tune)."""

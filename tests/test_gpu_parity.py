@@ -159,11 +159,12 @@ def test_conv333(lpc, n, depth, cin, seed):
         assert np.array_equal(got, want)
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5, 6, 7])
 @pytest.mark.parametrize("cin", [32, 64])
 def test_conv333_variants(lpc, cin, variant):
-    """Every kernel variant the autotuner may pick (stage-ring depth, tile
-    order) matches the oracle, over several tiles and a ragged tail."""
+    """Every kernel variant the autotuner may pick (ring shape, tile order,
+    cp.async or TMA gather4 gather) matches the oracle, over several tiles
+    and a ragged tail."""
     n, depth, seed = 40000, 9, 21
     xyz = synth.random_cloud(n, depth, seed)
     keys = O.leaf_keys(xyz, depth)
@@ -181,7 +182,7 @@ def test_codec_autotuner_picks_variants(lpc, blob):
     cod = _codec(lpc, blob, 14, 20000)
     data = cod.encode(_cuda(xyz))
     t = cod.tuning()
-    assert 0 <= t["conv32"] < 4 and 0 <= t["conv64"] < 4 and 0 <= t["predictor"] < 2
+    assert 0 <= t["conv32"] < 8 and 0 <= t["conv64"] < 8 and 0 <= t["predictor"] < 2
     assert all(0 < m < 1e3 for m in t["ms32"] + t["ms64"] + t["ms_pred"])
     assert data == O.encode(blob, xyz, 14)  # and the next call runs the captured graphs
     assert cod.encode(_cuda(xyz)) == data
@@ -498,7 +499,8 @@ def test_batch_into_reusable_buffer(lpc, blob):
             assert np.array_equal(O.leaf_keys(d.cpu().numpy(), L), O.leaf_keys(f, L))
 
 
-@pytest.mark.parametrize("variants", [(0, 0, 0), (3, 3, 1), (1, 2, 1), (2, 1, 0)])
+@pytest.mark.parametrize("variants", [(0, 0, 0), (3, 3, 1), (1, 2, 1), (2, 1, 0), (4, 4, 1),
+                                      (7, 5, 1), (5, 6, 0)])
 def test_fixed_variants_byte_identical(lpc, blob, variants):
     """Every fixed combination of conv and predictor variants gives the
     oracle's stream and decodes it (graphs captured with those variants)."""
