@@ -13,7 +13,9 @@
 // since C <= total and r total <= range); the symbol is the count of
 // cumulative values with r C <= code, less one, its interval the largest
 // such value and the smallest other one (or the total), as in the table
-// decoder.  Every lane keeps the same decoder state.  The stream framing is
+// decoder; the one division a symbol, floor(range / total), is a high
+// multiply by a reciprocal formed a symbol ahead.  Every lane keeps the same
+// decoder state.  The stream framing is
 // stream version 3's: the decoder starts from the first four bytes, and up to
 // four bytes past the substream's end read as zero.
 #include "common.cuh"
@@ -40,13 +42,19 @@ k_coarse_decode(const CoarseChunk* __restrict__ ck, int n, const uint8_t* __rest
     return;
   }
   const bool pad = lane == 31;  // lane 31's entry 7 is symbol 255: no symbol
-  uint32_t f[8], cum[8];
+  // cum[m]: the cumulative count before symbol 8 lane + m (lane 31's entry 7
+  // stays the total); the counts themselves are only needed when the model
+  // halves, and are the differences of neighbouring entries then
+  uint32_t cum[8];
 #pragma unroll
-  for (int m = 0; m < 8; m++) {
-    f[m] = (pad && m == 7) ? 0u : 1u;
-    cum[m] = 8 * lane + m;  // every count 1: C_s = s
-  }
+  for (int m = 0; m < 8; m++) cum[m] = 8 * lane + m;  // every count 1: C_s = s
   uint32_t total = 255;
+  // r = floor(range / total) from inv = floor((2^32 - 1) / total): inv >=
+  // (2^32 - total) / total, so range inv / 2^32 > range / total - 1 and the
+  // high word of range inv is the quotient or one less (one correction).
+  // total grows by kAmInc whatever the symbol, so the next reciprocal is
+  // formed beside the search instead of a division on the serial chain.
+  uint32_t inv = 0xFFFFFFFFu / total;
   const uint8_t* p = in + c.in_off;
   const int64_t len = c.in_len;
   auto byte = [&](int64_t i) -> uint32_t { return i < len ? (uint32_t)__ldg(p + i) : 0u; };
@@ -55,39 +63,51 @@ k_coarse_decode(const CoarseChunk* __restrict__ ck, int n, const uint8_t* __rest
   int64_t pos = 4;
   bool bad = false;
   for (int i = 0; i < c.n; i++) {
+    const uint32_t inv_next = 0xFFFFFFFFu / (total + kAmInc);
     const uint32_t b0 = byte(pos), b1 = byte(pos + 1), b2 = byte(pos + 2);
-    const uint32_t r = range / total;
-    uint32_t cnt = 0, lo = 0, hi = total;
+    uint32_t r = __umulhi(range, inv);
+    if (range - r * total >= total) r++;
+    // cumulative counts increase with the symbol (every count >= 1): one
+    // max reduction of the qualifying keys C << 8 | symbol gives the symbol
+    // and its interval's start together, a min reduction of the others (or
+    // the total) its end
+    uint32_t kv[8], hv[8];
 #pragma unroll
     for (int m = 0; m < 8; m++) {
       const bool real = m < 7 || !pad;
       const bool le = real && r * cum[m] <= code;
-      cnt += le;
-      lo = le ? cum[m] : lo;  // cumulative counts ascend: the last one is the largest
-      hi = (real && !le) ? min(hi, cum[m]) : hi;
+      kv[m] = le ? (cum[m] << 8) | (uint32_t)(8 * lane + m) : 0u;
+      hv[m] = (real && !le) ? cum[m] : total;
     }
-    const uint32_t s = __reduce_add_sync(0xffffffffu, cnt) - 1;
-    lo = __reduce_max_sync(0xffffffffu, lo);
-    hi = __reduce_min_sync(0xffffffffu, hi);
+    const uint32_t kmax = max(max(max(kv[0], kv[1]), max(kv[2], kv[3])), max(max(kv[4], kv[5]), max(kv[6], kv[7])));
+    const uint32_t hmin = min(min(min(hv[0], hv[1]), min(hv[2], hv[3])), min(min(hv[4], hv[5]), min(hv[6], hv[7])));
+    const uint32_t key = __reduce_max_sync(0xffffffffu, kmax);
+    const uint32_t hi = __reduce_min_sync(0xffffffffu, hmin);
+    const uint32_t lo = key >> 8, s = key & 0xFFu;
     code -= r * lo;
     range = r * (hi - lo);
     if (code >= range) bad = true;
     // renormalise: range >= r >= 255 here, so at most three bytes
     const int nb = (range < (1u << 24)) + (range < (1u << 16)) + (range < (1u << 8));
-    const uint64_t wide = ((uint64_t)code << 24) | (b0 << 16) | (b1 << 8) | b2;
-    code = (uint32_t)(wide >> (24 - 8 * nb));
+    // the top 32 bits of code:b0:b1:b2 shifted left by 8 nb (one funnel shift)
+    code = __funnelshift_l((b0 << 24) | (b1 << 16) | (b2 << 8), code, 8 * nb);
     range <<= 8 * nb;
     pos += nb;
     if (lane == 0) dst[i] = (uint8_t)(s + 1);  // symbol s codes occupancy s + 1
-    // the model after symbol s
+    // the model after symbol s: every cumulative count past s grows
+    const int ds = (int)s - 8 * lane;
 #pragma unroll
-    for (int m = 0; m < 8; m++) {
-      const uint32_t sym = 8 * lane + m;
-      if (sym == s) f[m] += kAmInc;
-      if (sym > s) cum[m] += kAmInc;
-    }
+    for (int m = 0; m < 8; m++) cum[m] += m > ds ? kAmInc : 0u;
     total += kAmInc;
+    inv = inv_next;
     if (total > kAmLimit) {
+      // counts from the differences (lane 31's entry 7 has none), halved
+      // rounding up, and the cumulative counts again
+      const uint32_t nxt = __shfl_down_sync(0xffffffffu, cum[0], 1);
+      uint32_t f[8];
+#pragma unroll
+      for (int m = 0; m < 8; m++)
+        f[m] = m < 7 ? cum[m + 1] - cum[m] : (pad ? 0u : nxt - cum[7]);
       uint32_t run = 0;
 #pragma unroll
       for (int m = 0; m < 8; m++) {
@@ -105,6 +125,7 @@ k_coarse_decode(const CoarseChunk* __restrict__ ck, int n, const uint8_t* __rest
 #pragma unroll
       for (int m = 0; m < 8; m++) cum[m] += before;
       total = __shfl_sync(0xffffffffu, x, 31);
+      inv = 0xFFFFFFFFu / total;
     }
   }
   if (pos > len + kPadBytes) bad = true;  // read past the zero bytes a flush may leave out

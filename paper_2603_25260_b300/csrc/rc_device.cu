@@ -16,7 +16,8 @@
 //    the clamp of the target to 2^16 - 1 changes nothing since every C is
 //    below 2^16.  The symbol s is the count of entries with r C <= code, the
 //    interval [C_s, C_{s+1}) the largest such entry and the smallest other
-//    one: three independent warp reductions.  The two stream bytes a
+//    one: a max reduction of keys C << 8 | count (which increase with the
+//    entry) and a min reduction, independent of each other.  The two stream bytes a
 //    renormalisation can take (range >= 2^8 after every update) are loaded
 //    before they are needed.  Every lane keeps the same copy of the decoder
 //    state, so no broadcasts are needed.  The symbol loop is a serial chain
@@ -44,21 +45,18 @@ constexpr int kEncAhead = 4;
 // becomes issue-bound); with fewer, one chunk a warp.
 constexpr int kEncLaneChunks = 148 * 32;
 
-// Code chunk t (a serial chain).
-__device__ __forceinline__ void encode_chunk(const RcChunk* __restrict__ ck, int t,
-                                             const uint32_t* __restrict__ lofreq,
-                                             uint8_t* __restrict__ out, uint32_t* __restrict__ lens,
-                                             int* err) {
-  const RcChunk c = ck[t];
-  uint8_t* o = out + c.byte_off;
-  const int64_t cap = c.byte_len;
-  // len counts the leading cache byte too; byte i is stored at o[i - 1]
-  int64_t len = 0;
+// Range-encoder state of one chunk, kept by one thread: put() codes one
+// packed interval lo | f << 16, finish() flushes and returns the length.
+struct RcEnc {
+  uint8_t* o;
+  int64_t cap;
+  int64_t len = 0;  // counts the leading cache byte too; byte i is o[i - 1]
+  int64_t pending = 1;
   uint64_t low = 0;
   uint32_t range = 0xFFFFFFFFu;
   uint32_t cache = 0;
-  int64_t pending = 1;
-  auto shift_low = [&]() {
+
+  __device__ void shift_low() {
     if ((uint32_t)low < 0xFF000000u || (low >> 32) != 0) {
       const uint32_t carry = (uint32_t)(low >> 32);
       uint32_t b = cache;
@@ -71,9 +69,102 @@ __device__ __forceinline__ void encode_chunk(const RcChunk* __restrict__ ck, int
     }
     pending++;
     low = (low & 0x00FFFFFFull) << 8;
-  };
+  }
+  __device__ __forceinline__ void put(uint32_t x) {
+    const uint32_t r = range >> 16;
+    low += (uint64_t)r * (x & 0xFFFFu);
+    range = r * (x >> 16);
+    while (range < (1u << 24)) {
+      range <<= 8;
+      shift_low();
+    }
+  }
+  // flush: the multiple of 2^k in [low, low + range) with k largest; up to
+  // kRcPad trailing zero bytes are left out
+  __device__ uint32_t finish(int* err) {
+    const uint64_t end = low + range;
+    for (int k = 32; k > 0; k--) {
+      const uint64_t v = ((low + ((1ull << k) - 1)) >> k) << k;
+      if (v < end) {
+        low = v;
+        break;
+      }
+    }
+    for (int i = 0; i < 5; i++) shift_low();
+    len -= 1;  // the leading cache byte is not part of the stream
+    if (len > cap) {
+      set_error(err, kErrCapacity);
+    } else {
+      for (int i = 0; i < kRcPad && len > 0 && o[len - 1] == 0; i++) len--;
+    }
+    return (uint32_t)len;
+  }
+};
+
+// 4-byte asynchronous copy global -> shared (both 4-byte aligned).
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+}
+
+// One chunk per warp, coded by its lane 0 (few chunks: lanes of other chunks
+// in the same warp would only lengthen each chain by divergence).  The whole
+// warp copies the chunk's intervals into shared memory a piece of
+// kEncPiece ahead, so the serial chain reads them at shared-memory latency.
+constexpr int kEncPiece = 256;
+
+__global__ void __launch_bounds__(kEncWarps * 32)
+k_rc_encode(const RcChunk* __restrict__ ck, int n, const uint32_t* __restrict__ lofreq,
+            uint8_t* __restrict__ out, uint32_t* __restrict__ lens, int* err) {
+  __shared__ __align__(16) uint32_t stage[kEncWarps][2][kEncPiece];
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+  const int t = blockIdx.x * kEncWarps + wi;
+  if (t >= n) return;  // t is the same for the whole warp
+  const RcChunk c = ck[t];
   const uint32_t* src = lofreq + c.row;
-  uint32_t nx[kEncAhead];  // intervals loaded ahead of use
+  const int64_t npc = (c.rows + kEncPiece - 1) / kEncPiece;
+  auto load = [&](int64_t p) {  // every lane: its entries of piece p, into buffer p & 1
+    uint32_t* b = stage[wi][p & 1];
+    const int64_t i0 = p * kEncPiece;
+    for (int k = lane; k < kEncPiece && i0 + k < c.rows; k += 32)
+      cp_async4(smem_u32(b + k), src + i0 + k);
+    tc::cp_async_commit();
+  };
+  RcEnc e;
+  e.o = out + c.byte_off;
+  e.cap = c.byte_len;
+  if (npc > 0) load(0);
+  for (int64_t p = 0; p < npc; p++) {
+    if (p + 1 < npc) {
+      load(p + 1);  // in flight while piece p is coded
+      tc::cp_async_wait<1>();
+    } else {
+      tc::cp_async_wait<0>();
+    }
+    __syncwarp();  // every lane's copies of piece p are visible to lane 0
+    if (lane == 0) {
+      const uint32_t* b = stage[wi][p & 1];
+      const int m = (int)(c.rows - p * kEncPiece < kEncPiece ? c.rows - p * kEncPiece : kEncPiece);
+#pragma unroll 8
+      for (int k = 0; k < m; k++) e.put(b[k]);
+    }
+    __syncwarp();  // buffer p & 1 is free for piece p + 2
+  }
+  if (lane == 0) lens[t] = e.finish(err);
+}
+
+// One chunk per lane (many chunks: the lanes' chains hide each other's
+// latency); intervals loaded kEncAhead ahead into registers.
+__global__ void __launch_bounds__(128)
+k_rc_encode_lanes(const RcChunk* __restrict__ ck, int n, const uint32_t* __restrict__ lofreq,
+                  uint8_t* __restrict__ out, uint32_t* __restrict__ lens, int* err) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const RcChunk c = ck[t];
+  RcEnc e;
+  e.o = out + c.byte_off;
+  e.cap = c.byte_len;
+  const uint32_t* src = lofreq + c.row;
+  uint32_t nx[kEncAhead];
 #pragma unroll
   for (int k = 0; k < kEncAhead; k++) nx[k] = k < c.rows ? __ldg(src + k) : 0u;
   for (int64_t i0 = 0; i0 < c.rows; i0 += kEncAhead) {
@@ -82,51 +173,11 @@ __device__ __forceinline__ void encode_chunk(const RcChunk* __restrict__ ck, int
       if (i0 + k < c.rows) {
         const uint32_t x = nx[k];
         if (i0 + k + kEncAhead < c.rows) nx[k] = __ldg(src + i0 + k + kEncAhead);
-        const uint32_t r = range >> 16;
-        low += (uint64_t)r * (x & 0xFFFFu);
-        range = r * (x >> 16);
-        while (range < (1u << 24)) {
-          range <<= 8;
-          shift_low();
-        }
+        e.put(x);
       }
     }
   }
-  // flush: the multiple of 2^k in [low, low + range) with k largest
-  const uint64_t end = low + range;
-  for (int k = 32; k > 0; k--) {
-    const uint64_t v = ((low + ((1ull << k) - 1)) >> k) << k;
-    if (v < end) {
-      low = v;
-      break;
-    }
-  }
-  for (int i = 0; i < 5; i++) shift_low();
-  len -= 1;  // the leading cache byte is not part of the stream
-  if (len > cap) {
-    set_error(err, kErrCapacity);
-  } else {
-    for (int i = 0; i < kRcPad && len > 0 && o[len - 1] == 0; i++) len--;
-  }
-  lens[t] = (uint32_t)len;
-}
-
-// One chunk per warp, coded by its lane 0 (few chunks: lanes of other chunks
-// in the same warp would only lengthen each chain by divergence).
-__global__ void __launch_bounds__(kEncWarps * 32)
-k_rc_encode(const RcChunk* __restrict__ ck, int n, const uint32_t* __restrict__ lofreq,
-            uint8_t* __restrict__ out, uint32_t* __restrict__ lens, int* err) {
-  if ((threadIdx.x & 31) != 0) return;
-  const int t = blockIdx.x * kEncWarps + (threadIdx.x >> 5);
-  if (t < n) encode_chunk(ck, t, lofreq, out, lens, err);
-}
-
-// One chunk per lane (many chunks).
-__global__ void __launch_bounds__(128)
-k_rc_encode_lanes(const RcChunk* __restrict__ ck, int n, const uint32_t* __restrict__ lofreq,
-                  uint8_t* __restrict__ out, uint32_t* __restrict__ lens, int* err) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n) encode_chunk(ck, t, lofreq, out, lens, err);
+  lens[t] = e.finish(err);
 }
 
 // Table rows reach shared memory by bulk copies (TMA, one per stage of
@@ -196,38 +247,46 @@ k_rc_decode(const RcChunk* __restrict__ ck, int n, const int64_t* d_n,
     const uint8_t* stage = sm + (size_t)slot * kStageRows * kRowBytes;
     const int64_t r0 = st * kStageRows;
     const int nr = (int)(c.rows - r0 < kStageRows ? c.rows - r0 : kStageRows);
+    // the next row's entries are read a symbol ahead.  Entry i of a row is
+    // C_{i+1} (C_0 = 0 is implicit), so the symbol is the number of
+    // qualifying entries; the keys C_{i+1} << 8 | (i + 1) increase with i
+    // (every f >= 1), and one max reduction of the qualifying keys (0 when
+    // none qualifies: s = 0, C_0 = 0) gives s and C_s together, beside one
+    // min reduction for C_{s+1} (max / min reductions take about half the
+    // time of an add reduction)
+    uint4 qn = *reinterpret_cast<const uint4*>(stage + 16 * lane);
 #pragma unroll
     for (int k = 0; k < kStageRows; k++) {
+      const uint4 q = qn;
+      if (k + 1 < kStageRows)
+        qn = *reinterpret_cast<const uint4*>(stage + (k + 1) * kRowBytes + 16 * lane);
       if (k < nr) {
-        const uint4 q = *reinterpret_cast<const uint4*>(stage + k * kRowBytes + 16 * lane);
         const uint32_t b0 = p < end ? __ldg(p) : 0u;
         const uint32_t b1 = p + 1 < end ? __ldg(p + 1) : 0u;
-        const uint32_t r = range >> 16;
         const uint32_t e[8] = {q.x & 0xFFFFu, q.x >> 16, q.y & 0xFFFFu, q.y >> 16,
                                q.z & 0xFFFFu, q.z >> 16, q.w & 0xFFFFu, q.w >> 16};
-        uint32_t cnt = 0, lo = 0, hi = 65536u;
+        const uint32_t r = range >> 16;
+        uint32_t kv[8], hv[8];
 #pragma unroll
         for (int m = 0; m < 8; m++) {
           const bool real = m < 6 || !pad;
           const bool le = real && r * e[m] <= code;
-          cnt += le;
-          lo = le ? e[m] : lo;  // entries ascend: the last qualifying one is the largest
-          hi = real && !le ? min(hi, e[m]) : hi;
+          kv[m] = le ? (e[m] << 8) | (uint32_t)(8 * lane + m + 1) : 0u;
+          hv[m] = real && !le ? e[m] : 65536u;
         }
-        // the three reductions are independent and overlap
-        const uint32_t s = __reduce_add_sync(0xFFFFFFFFu, cnt);
-        lo = __reduce_max_sync(0xFFFFFFFFu, lo);
-        hi = __reduce_min_sync(0xFFFFFFFFu, hi);
+        const uint32_t kmax = max(max(max(kv[0], kv[1]), max(kv[2], kv[3])),
+                                  max(max(kv[4], kv[5]), max(kv[6], kv[7])));
+        const uint32_t hmin = min(min(min(hv[0], hv[1]), min(hv[2], hv[3])),
+                                  min(min(hv[4], hv[5]), min(hv[6], hv[7])));
+        const uint32_t key = __reduce_max_sync(0xFFFFFFFFu, kmax);
+        const uint32_t hi = __reduce_min_sync(0xFFFFFFFFu, hmin);
+        const uint32_t lo = key >> 8, s = key & 0xFFu;
         code -= r * lo;
         range = r * (hi - lo);
         if (code >= range) bad = true;
         // renormalise: range >= 2^8 here, so at most two bytes
         const int nb = (range < (1u << 24)) + (range < (1u << 16));
-        if (nb == 1) {
-          code = (code << 8) | b0;
-        } else if (nb == 2) {
-          code = (code << 16) | (b0 << 8) | b1;
-        }
+        code = __funnelshift_l((b0 << 24) | (b1 << 16), code, 8 * nb);  // code:b0:b1 << 8 nb
         range <<= 8 * nb;
         p += nb;
         if (lane == 0) dst[r0 + k] = (uint8_t)(s + 1);
