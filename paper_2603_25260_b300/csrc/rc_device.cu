@@ -47,32 +47,37 @@ constexpr int kEncLaneChunks = 148 * 32;
 
 // Range-encoder state of one chunk, kept by one thread: put() codes one
 // packed interval lo | f << 16, finish() flushes and returns the length.
+// low stays below 2^32 + range <= 2^33, so it is kept as its low word l and
+// one carry bit c; lengths fit 32 bits (a chunk's capacity does).
 struct RcEnc {
   uint8_t* o;
-  int64_t cap;
-  int64_t len = 0;  // counts the leading cache byte too; byte i is o[i - 1]
-  int64_t pending = 1;
-  uint64_t low = 0;
+  uint32_t cap;
+  uint32_t len = 0;      // counts the leading cache byte too; byte i is o[i - 1]
+  uint32_t pending = 1;  // the cache byte and the 0xFF bytes held back with it
+  uint32_t l = 0, c = 0;
   uint32_t range = 0xFFFFFFFFu;
   uint32_t cache = 0;
 
-  __device__ void shift_low() {
-    if ((uint32_t)low < 0xFF000000u || (low >> 32) != 0) {
-      const uint32_t carry = (uint32_t)(low >> 32);
-      uint32_t b = cache;
-      for (; pending > 0; pending--) {
-        if (len > 0 && len <= cap) o[len - 1] = (uint8_t)(b + carry);
-        len++;
-        b = 0xFF;
-      }
-      cache = (uint32_t)(low >> 24) & 0xFF;
+  __device__ __forceinline__ void emit(uint32_t b) {
+    if (len - 1 < cap) o[len - 1] = (uint8_t)b;  // 0 < len <= cap
+    len++;
+  }
+  __device__ __forceinline__ void shift_low() {
+    if (l < 0xFF000000u || c != 0) {
+      emit(cache + c);
+      for (; pending > 1; pending--) emit(0xFFu + c);
+      pending = 0;
+      cache = l >> 24;
     }
     pending++;
-    low = (low & 0x00FFFFFFull) << 8;
+    l <<= 8;  // (low mod 2^24) << 8: the top byte leaves, the carry was spent
+    c = 0;
   }
   __device__ __forceinline__ void put(uint32_t x) {
     const uint32_t r = range >> 16;
-    low += (uint64_t)r * (x & 0xFFFFu);
+    const uint32_t a = r * (x & 0xFFFFu);  // below 2^32
+    l += a;
+    c += l < a;
     range = r * (x >> 16);
     while (range < (1u << 24)) {
       range <<= 8;
@@ -82,22 +87,24 @@ struct RcEnc {
   // flush: the multiple of 2^k in [low, low + range) with k largest; up to
   // kRcPad trailing zero bytes are left out
   __device__ uint32_t finish(int* err) {
+    const uint64_t low = ((uint64_t)c << 32) | l;
     const uint64_t end = low + range;
     for (int k = 32; k > 0; k--) {
       const uint64_t v = ((low + ((1ull << k) - 1)) >> k) << k;
       if (v < end) {
-        low = v;
+        l = (uint32_t)v;
+        c = (uint32_t)(v >> 32);
         break;
       }
     }
     for (int i = 0; i < 5; i++) shift_low();
-    len -= 1;  // the leading cache byte is not part of the stream
-    if (len > cap) {
+    uint32_t n = len - 1;  // the leading cache byte is not part of the stream
+    if (n > cap) {
       set_error(err, kErrCapacity);
     } else {
-      for (int i = 0; i < kRcPad && len > 0 && o[len - 1] == 0; i++) len--;
+      for (int i = 0; i < kRcPad && n > 0 && o[n - 1] == 0; i++) n--;
     }
-    return (uint32_t)len;
+    return n;
   }
 };
 
@@ -131,7 +138,7 @@ k_rc_encode(const RcChunk* __restrict__ ck, int n, const uint32_t* __restrict__ 
   };
   RcEnc e;
   e.o = out + c.byte_off;
-  e.cap = c.byte_len;
+  e.cap = (uint32_t)min(c.byte_len, (int64_t)0x7fffffff);
   if (npc > 0) load(0);
   for (int64_t p = 0; p < npc; p++) {
     if (p + 1 < npc) {
@@ -162,7 +169,7 @@ k_rc_encode_lanes(const RcChunk* __restrict__ ck, int n, const uint32_t* __restr
   const RcChunk c = ck[t];
   RcEnc e;
   e.o = out + c.byte_off;
-  e.cap = c.byte_len;
+  e.cap = (uint32_t)min(c.byte_len, (int64_t)0x7fffffff);
   const uint32_t* src = lofreq + c.row;
   uint32_t nx[kEncAhead];
 #pragma unroll
