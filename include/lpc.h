@@ -148,7 +148,8 @@ int codec_last_stats(codec_t* codec, int64_t* counts, double* gpu_us, double* ho
  * every later launch of the families whose bit is set in `mask` with CUDA
  * events on the codec's stream (0 turns it off).  Families: 0 sort (Morton +
  * radix sort + unique), 1 levels (level build / decoder expansion), 2 hash_kmap,
- * 3 embed, 4 up_prune, 5 down_s2, 6 conv333, 7 predictor_cdf, 8 range_coder.
+ * 3 embed (code embeddings and the bf16 conversions of the conv inputs),
+ * 4 up_prune, 5 down_s2, 6 conv333, 7 predictor_cdf, 8 range_coder.
  * codec_profile_read returns, for one family, the summed launch time (ms),
  * the launch count, and the algorithmic bytes and integer ops those launches
  * must touch (counted from level sizes and neighbour pairs, not from the

@@ -390,9 +390,9 @@ int Codec::create(const lpc_config& cfg, const void* blob, size_t len) {
   add((void**)&xb_, 64 * P);
   add((void**)&xt_, 64 * P);
   add((void**)&y1_, 32 * P);
+  add((void**)&xe_, 32 * P);
   add((void**)&xb16_, 2 * 64 * P);
   add((void**)&y1b16_, 2 * 32 * P);
-  add((void**)&xe_, 32 * P);
   add((void**)&g_[0], 32 * P);
   add((void**)&g_[1], 32 * P);
   add((void**)&hx_[0], 64 * P);
@@ -634,17 +634,20 @@ void Codec::fetch_frame_offsets(int nf) {
 // --------------------------------------------------------------- network --
 // Launch wrappers: one kernel each, bracketed by the profiler with the
 // algorithmic work of that launch.  `h` is a height of the level arrays.
+
 void Codec::embed(const DEmb& E, int h, int8_t* out, int stride, int col) {
   pbeg(kFamEmbed);
   launch_embed(E, code_[h], d_N_ + h, gridn(h), out, stride, col, st_);
   pend(kFamEmbed, 33.0 * N_[h], 0);
 }
 
-// Pruning(Upsampling(x)) from height h to height h - 1
-void Codec::up(const DLayer& W, int h, const int8_t* x, int xs, int8_t* out, int os) {
+// Pruning(Upsampling(x)) from height h to height h - 1; with oe, the output
+// rows' columns [oe_col, oe_col + 32) also get E[Y] of their codes
+void Codec::up(const DLayer& W, int h, const int8_t* x, int xs, int8_t* out, int os, EmbSrc oe,
+               int oe_col) {
   pbeg(kFamUp);
   launch_up_prune(W, key_[h - 1], par_[h - 1], d_N_ + h - 1, gridn(h - 1), x, xs, out, os, 0,
-                  st_);
+                  st_, oe, oe_col);
   pend(kFamUp, (double)W.cin * N_[h] + 32.0 * N_[h - 1] + 8.0 * N_[h - 1],
        2.0 * N_[h - 1] * W.cin * 32);
 }
@@ -659,7 +662,8 @@ void Codec::to_bf16(const int8_t* x, int xs, int cols, int z, int h) {
 // 3x3x3 conv at height h: bf16 input rows xb (stride xbs elements); with res
 // the residual merge reads y1_; outb (optional) gets the next conv's input.
 void Codec::conv(const DLayer& W, int h, const int32_t* nbr, int slot, const void* xb, int xbs,
-                 int8_t* out, int os, int oc, const DRes* res, void* outb, int outb_z) {
+                 int8_t* out, int os, int oc, const DRes* res, void* outb, int outb_z,
+                 EmbSrc emb, int emb_col) {
   ConvTcArgs a{};
   a.wimg = W.Wtc;
   a.bias = W.bias;
@@ -678,6 +682,8 @@ void Codec::conv(const DLayer& W, int h, const int32_t* nbr, int slot, const voi
   a.outb = outb;
   a.outb_stride = 32;
   a.outb_z = outb_z;
+  a.emb = emb;
+  a.emb_col = emb_col;
   if (res) {
     a.has_res = 1;
     a.y1 = y1_;
@@ -777,8 +783,9 @@ const int8_t* Codec::shallow_F(int h, int* stride) {
     ensure_nbr(hp);
     to_bf16(Fp, ps, 32, M_.RA[j].z_in, hp);
     conv(M_.RA[j], hp, nbr_[hp], 5 - hp, xb16_, 32, y1_, 32, 0, nullptr, y1b16_, M_.RB[j].z_in);
-    conv(M_.RB[j], hp, nbr_[hp], 5 - hp, y1b16_, 32, xb_, 64, 0, &M_.RM[j], nullptr, 0);
-    embed(M_.ESH[j], hp, xb_, 64, 32);
+    // Concat(S, E[Y]): the ResBlock's epilogue writes both halves
+    conv(M_.RB[j], hp, nbr_[hp], 5 - hp, y1b16_, 32, xb_, 64, 0, &M_.RM[j], nullptr, 0,
+         emb_src(M_.ESH[j], hp), 32);
     up(M_.USH[j], hp, xb_, 64, buf, *stride);
   }
   have_F_[h] = true;
@@ -850,10 +857,9 @@ void Codec::net_level(int j, int mode, uint16_t* cdf, uint32_t* enc, int8_t* log
   const int w = cat ? 64 : 32;  // row width of the ResBlock's input
   if (part != kNetPost) {
     // G^k = Downsampling(Y_{d-1}) (Eq. 4): embedding at height h + 1, then
-    // m - 1 stride-2 steps up to height hk, into gk_
-    if (m == 1) {
-      embed(M_.G[j], h + 1, gk_, 32, 0);
-    } else {
+    // m - 1 stride-2 steps up to height hk, into gk_ (with m = 1 the bf16
+    // conversion of the ResBlock's input reads the embedding from its table)
+    if (m > 1) {
       embed(M_.G[j], h + 1, g_[0], 32, 0);
       const int8_t* cur = g_[0];
       for (int i = 1; i < m; i++) {
@@ -872,24 +878,29 @@ void Codec::net_level(int j, int mode, uint16_t* cdf, uint32_t* enc, int8_t* log
   const int8_t* Ft = cat ? shallow_F(hk, &fs) : nullptr;
   ensure_nbr(hk);
   // H^k = ResBlock(Concat(F^t, G^t)) (Eq. 10), or ResBlock(G^k) (Eq. 5)
-  if (cat) {
-    pbeg(kFamEmbed);
+  pbeg(kFamEmbed);
+  if (m == 1)  // G^k = E[Y] at height hk itself, read from the table
+    launch_to_bf16_emb(cat ? Ft : nullptr, fs, cat ? 32 : 0, emb_src(M_.G[j], hk),
+                       M_.RA[j].z_in, d_N_ + hk, gridn(hk), xb16_, st_);
+  else if (cat)
     launch_to_bf16_cat(Ft, fs, gk_, 32, M_.RA[j].z_in, d_N_ + hk, gridn(hk), xb16_, st_);
-    pend(kFamEmbed, 3.0 * 64 * N_[hk], 0);
-  } else {
-    to_bf16(gk_, 32, 32, M_.RA[j].z_in, hk);
-  }
+  else
+    launch_to_bf16(gk_, 32, 32, M_.RA[j].z_in, d_N_ + hk, gridn(hk), xb16_, st_);
+  pend(kFamEmbed, 3.0 * w * N_[hk], 0);
   conv(M_.RA[j], hk, nbr_[hk], 5 - hk, xb16_, w, y1_, 32, 0, nullptr, y1b16_, M_.RB[j].z_in);
-  conv(M_.RB[j], hk, nbr_[hk], 5 - hk, y1b16_, 32, hx_[0], w, 0, &M_.RM[j], nullptr, 0);
+  // with GRED + XFP the ResBlock's epilogue writes the first up-step's
+  // Concat(H^k, E[Y]) whole, and every up-step the next one's
+  conv(M_.RB[j], hk, nbr_[hk], 5 - hk, y1b16_, 32, hx_[0], w, 0, &M_.RM[j], nullptr, 0,
+       cat ? emb_src(M_.E[j][0], hk) : EmbSrc{}, 32);
   // F^{k+1} = Pruning(Upsampling(Concat(H^k, Y_k)), Y_k) (Eq. 11), or
   // Pruning(Upsampling(F^k), Y_k) (Eq. 6): heights hk -> h
   int cur = 0;
   for (int k = 0; k < m; k++) {
     const int hp = hk - k;
-    if (cat) embed(M_.E[j][k], hp, hx_[cur], 64, 32);
     int8_t* dst = k == m - 1 ? fo_ : hx_[1 - cur];
     const int ds = k == m - 1 ? 32 : w;
-    up(M_.UP[j][k], hp, hx_[cur], w, dst, ds);
+    up(M_.UP[j][k], hp, hx_[cur], w, dst, ds,
+       cat && k + 1 < m ? emb_src(M_.E[j][k + 1], hp - 1) : EmbSrc{}, 32);
     cur = 1 - cur;
   }
   pred(j, fo_, 32);

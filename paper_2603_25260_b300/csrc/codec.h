@@ -173,10 +173,14 @@ class Codec {
   void level_bytes();
   // network
   void embed(const DEmb& E, int h, int8_t* out, int stride, int col);
-  void up(const DLayer& W, int h, const int8_t* x, int xs, int8_t* out, int os);
+  void up(const DLayer& W, int h, const int8_t* x, int xs, int8_t* out, int os, EmbSrc oe = {},
+          int oe_col = 0);
+  // E[Y] of the height-h codes, read from the embedding table
+  EmbSrc emb_src(const DEmb& E, int h) const { return EmbSrc{E.table, code_[h]}; }
   void to_bf16(const int8_t* x, int xs, int cols, int z, int h);
   void conv(const DLayer& W, int h, const int32_t* nbr, int slot, const void* xb, int xbs,
-            int8_t* out, int os, int oc, const DRes* res, void* outb, int outb_z);
+            int8_t* out, int os, int oc, const DRes* res, void* outb, int outb_z,
+            EmbSrc emb = {}, int emb_col = 0);
   void kmap(int h, int32_t* nbr, int slot);
   void ensure_nbr(int h);
   const int8_t* shallow_F(int h, int* stride);

@@ -481,6 +481,12 @@ k_conv333_tc(const __grid_constant__ ConvTcArgs a) {
         uint4* dst = reinterpret_cast<uint4*>(a.out + r * a.out_stride + a.out_col);
         dst[0] = reinterpret_cast<const uint4*>(q)[0];
         dst[1] = reinterpret_cast<const uint4*>(q)[1];
+        if (a.emb.table) {  // the next step's Concat(., E[Y]) half of the row
+          const uint4* e4 = reinterpret_cast<const uint4*>(a.emb.table + (int)a.emb.code[r] * 32);
+          uint4* de = reinterpret_cast<uint4*>(a.out + r * a.out_stride + a.emb_col);
+          de[0] = __ldg(e4);
+          de[1] = __ldg(e4 + 1);
+        }
         if (a.outb) {
           __align__(16) __nv_bfloat16 bq[32];
 #pragma unroll
@@ -502,10 +508,13 @@ k_conv333_tc(const __grid_constant__ ConvTcArgs a) {
 }
 
 // int8 rows -> bf16 (q - z) rows for the tensor-core gather; columns
-// [0, x_cols) come from x, the rest (the concatenated second half) from x2
+// [0, x_cols) come from x, the rest (the concatenated second half) from x2,
+// or from the embedding table row of the node's code when etab is set
 __global__ void k_to_bf16(const int8_t* __restrict__ x, int x_stride, int x_cols,
                           const int8_t* __restrict__ x2, int x2_stride, int cols, int z,
-                          const int64_t* d_n, __nv_bfloat16* out) {
+                          const int64_t* d_n, __nv_bfloat16* out,
+                          const int8_t* __restrict__ etab = nullptr,
+                          const uint8_t* __restrict__ ecode = nullptr) {
   const int64_t n = *d_n;
   const int per = cols / 8;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n * per;
@@ -513,7 +522,8 @@ __global__ void k_to_bf16(const int8_t* __restrict__ x, int x_stride, int x_cols
     const int64_t r = q / per;
     const int c = (int)(q - r * per);
     const int8_t* src = c * 8 < x_cols ? x + r * x_stride + c * 8
-                                       : x2 + r * x2_stride + (c * 8 - x_cols);
+                        : etab ? etab + (int)ecode[r] * 32 + (c * 8 - x_cols)
+                               : x2 + r * x2_stride + (c * 8 - x_cols);
     const uint2 raw = *reinterpret_cast<const uint2*>(src);
     const int8_t* b = reinterpret_cast<const int8_t*>(&raw);
     __align__(16) __nv_bfloat16 v[8];
@@ -556,6 +566,17 @@ void launch_to_bf16(const int8_t* x, int x_stride, int cols, int z, const int64_
   const int blocks = (int)std::min<int64_t>((work + 255) / 256, 148 * 8);
   k_to_bf16<<<blocks, 256, 0, st>>>(x, x_stride, cols, x, x_stride, cols, z, d_n,
                                     reinterpret_cast<__nv_bfloat16*>(out));
+  count_launches(1);
+}
+
+void launch_to_bf16_emb(const int8_t* a, int a_stride, int a_cols, EmbSrc e, int z,
+                        const int64_t* d_n, int64_t n_host, void* out, cudaStream_t st) {
+  if (n_host <= 0) return;
+  const int cols = a_cols + 32;
+  const int64_t work = n_host * (cols / 8);
+  const int blocks = (int)std::min<int64_t>((work + 255) / 256, 148 * 8);
+  k_to_bf16<<<blocks, 256, 0, st>>>(a, a_stride, a_cols, nullptr, 0, cols, z, d_n,
+                                    reinterpret_cast<__nv_bfloat16*>(out), e.table, e.code);
   count_launches(1);
 }
 

@@ -203,6 +203,15 @@ struct DRes {
   const int32_t* mab;    // [2][C]
   const int16_t* slope;  // [C]
 };
+
+// A code embedding E[Y]: node r's row is the 32-column row code[r] of table
+// (its occupancy code's embedding).  A kernel that writes a node's row can
+// write its embedding half too, and one that reads it can take it from the
+// table, so that no kernel of its own copies it.
+struct EmbSrc {
+  const int8_t* table = nullptr;  // [256][32]
+  const uint8_t* code = nullptr;  // the nodes' codes (the rows' level)
+};
 // Predictor second layer in the per-lane layout: s = lane * 8 + i.
 struct DPred2 {
   int z_in, z_out, shift;
@@ -222,11 +231,16 @@ int pred_tc_error(bool reset);
 void launch_embed(const DEmb& E, const uint8_t* codes, const int64_t* d_n, int64_t n_host,
                   int8_t* out, int stride, int col, cudaStream_t st);
 
+
+
 // Upsampling + Pruning: every child r of V_d gets slice (ckey[r] & 7) of the
-// layer applied to its parent row x[par[r]] (cin columns, stride x_stride).
+// layer applied to its parent row x[par[r]] (cin columns, stride x_stride);
+// with oe, the output row's columns [oe_col, oe_col + 32) get E[Y] of the
+// child's code (the next step's Concat half).
 void launch_up_prune(const DLayer& W, const uint64_t* ckey, const uint32_t* cpar,
                      const int64_t* d_nc, int64_t nc_host, const int8_t* x, int x_stride,
-                     int8_t* out, int out_stride, int out_col, cudaStream_t st);
+                     int8_t* out, int out_stride, int out_col, cudaStream_t st, EmbSrc oe = {},
+                     int oe_col = 0);
 
 // Stride-2 down conv: parent p sums slices (ckey & 7) over its children
 // off[p]..off[p+1]-1 of x (child rows).
@@ -239,6 +253,7 @@ void launch_down(const DLayer& W, const uint64_t* ckey, const uint32_t* poff, co
 // ResBlock's residual merge is fused into the epilogue (y1 = the first conv's
 // int8 output).  outb (optional) receives bf16 (q - outb_z) rows for the next
 // conv.
+
 // A TMA tensor map (the driver's 128-byte CUtensorMap), kept opaque here.
 struct alignas(64) TmaDesc {
   unsigned long long q[16];
@@ -260,6 +275,8 @@ struct ConvTcArgs {
   void* outb;
   int outb_stride, outb_z;
   int has_res;
+  EmbSrc emb;   // optional: E[Y] of the rows' codes into columns [emb_col, emb_col + 32) of out
+  int emb_col;
   const int8_t* y1;
   int y1_stride;
   const int32_t* res_mab;
@@ -279,6 +296,10 @@ void launch_to_bf16(const int8_t* x, int x_stride, int cols, int z, const int64_
                     int64_t n_host, void* out, cudaStream_t st);
 // The same for the 64 columns of Concat(a, b): 32 int8 columns from each.
 void launch_to_bf16_cat(const int8_t* a, int a_stride, const int8_t* b, int b_stride, int z,
+                        const int64_t* d_n, int64_t n_host, void* out, cudaStream_t st);
+// bf16 rows of Concat(a, E[code]) (a_cols = 32) or of E[code] alone
+// (a_cols = 0): the embedding read from its table.
+void launch_to_bf16_emb(const int8_t* a, int a_stride, int a_cols, EmbSrc e, int z,
                         const int64_t* d_n, int64_t n_host, void* out, cudaStream_t st);
 // Non-zero if a tensor-core conv gave up on a bounded wait (optionally reset).
 int conv_tc_error(bool reset);

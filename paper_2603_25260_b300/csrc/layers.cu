@@ -150,20 +150,22 @@ template <int CIN>
 __global__ void __launch_bounds__(kWarps * 32)
 k_up_prune(DLayer L, const uint64_t* __restrict__ ckey, const uint32_t* __restrict__ cpar,
            const int64_t* d_nc, const int8_t* __restrict__ x, int x_stride, int8_t* out,
-           int out_stride, int out_col) {
+           int out_stride, int out_col, EmbSrc oe, int oe_col) {
   extern __shared__ int32_t sm[];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   int8_t* stage = reinterpret_cast<int8_t*>(sm + smem_layer_bytes_dev(L) / 4) +
                   (size_t)w * 2 * kUpGroup * CIN;
   const int64_t n = *d_nc;
   const int64_t step = warps_total() * kUpGroup;
-  // lane's child of group g0: slot, and its parent row copied into buffer b
+  // lane's child of group g0: slot (with oe, its code << 8 beside it), and
+  // its parent row copied into buffer b
   auto issue = [&](int64_t g0, int b) -> int {
     const int64_t r = g0 + lane;
     int c = 0;
     const int8_t* src = x;
     if (r < n) {
       c = (int)(__ldg(ckey + r) & 7);
+      if (oe.table) c |= (int)__ldg(oe.code + r) << 8;
       src = x + (int64_t)__ldg(cpar + r) * x_stride;
     }
     const uint32_t dst = tc::smem_u32(stage + (b * kUpGroup + lane) * CIN);
@@ -191,9 +193,12 @@ k_up_prune(DLayer L, const uint64_t* __restrict__ ckey, const uint32_t* __restri
       int c[kUpIlp];
       int32_t acc[kUpIlp];
       int32_t xv[kUpIlp][CIN / 4];
+      int ec[kUpIlp];  // the children's codes (with oe)
 #pragma unroll
       for (int u = 0; u < kUpIlp; u++) {
-        c[u] = __shfl_sync(0xffffffffu, c_cur, j + u);
+        const int cu = __shfl_sync(0xffffffffu, c_cur, j + u);
+        c[u] = cu & 7;
+        ec[u] = cu >> 8;
         const int4* row = reinterpret_cast<const int4*>(stage + (b * kUpGroup + j + u) * CIN);
 #pragma unroll
         for (int i = 0; i < CIN / 16; i++) {
@@ -220,10 +225,12 @@ k_up_prune(DLayer L, const uint64_t* __restrict__ ckey, const uint32_t* __restri
         if (L.prelu) a = prelu(a, s.slope[c[u] * 32 + lane]);
         out[(g0 + j + u) * out_stride + out_col + lane] =
             (int8_t)requant(a, s.mult[c[u] * 32 + lane], L.shift, L.z_out);
+        if (oe.table) out[(g0 + j + u) * out_stride + oe_col + lane] = __ldg(oe.table + ec[u] * 32 + lane);
       }
     }
     for (; j < m; j++) {
-      const int c = __shfl_sync(0xffffffffu, c_cur, j);
+      const int cj = __shfl_sync(0xffffffffu, c_cur, j);
+      const int c = cj & 7;
       int32_t xv[CIN / 4];
       const int4* row = reinterpret_cast<const int4*>(stage + (b * kUpGroup + j) * CIN);
 #pragma unroll
@@ -236,6 +243,7 @@ k_up_prune(DLayer L, const uint64_t* __restrict__ ckey, const uint32_t* __restri
       if (L.prelu) acc = prelu(acc, s.slope[c * 32 + lane]);
       out[(g0 + j) * out_stride + out_col + lane] =
           (int8_t)requant(acc, s.mult[c * 32 + lane], L.shift, L.z_out);
+      if (oe.table) out[(g0 + j) * out_stride + oe_col + lane] = __ldg(oe.table + (cj >> 8) * 32 + lane);
     }
     __syncwarp();  // buffer b is free for the group after next
     c_cur = c_next;
@@ -245,7 +253,8 @@ k_up_prune(DLayer L, const uint64_t* __restrict__ ckey, const uint32_t* __restri
 
 void launch_up_prune(const DLayer& W, const uint64_t* ckey, const uint32_t* cpar,
                      const int64_t* d_nc, int64_t nc_host, const int8_t* x, int x_stride,
-                     int8_t* out, int out_stride, int out_col, cudaStream_t st) {
+                     int8_t* out, int out_stride, int out_col, cudaStream_t st, EmbSrc oe,
+                     int oe_col) {
   if (nc_host <= 0) return;
   const size_t smem = smem_layer_bytes(W) + (size_t)kWarps * 2 * kUpGroup * W.cin;
   const int blocks = (int)std::min<int64_t>((nc_host + kWarps * kUpGroup - 1) / (kWarps * kUpGroup),
@@ -253,11 +262,11 @@ void launch_up_prune(const DLayer& W, const uint64_t* ckey, const uint32_t* cpar
   if (W.cin == 32) {
     cudaFuncSetAttribute(k_up_prune<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_up_prune<32><<<blocks, kWarps * 32, smem, st>>>(W, ckey, cpar, d_nc, x, x_stride, out,
-                                                      out_stride, out_col);
+                                                      out_stride, out_col, oe, oe_col);
   } else {
     cudaFuncSetAttribute(k_up_prune<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_up_prune<64><<<blocks, kWarps * 32, smem, st>>>(W, ckey, cpar, d_nc, x, x_stride, out,
-                                                      out_stride, out_col);
+                                                      out_stride, out_col, oe, oe_col);
   }
   count_launches(1);
 }
