@@ -715,25 +715,30 @@ void Codec::conv(const DLayer& W, int h, const int32_t* nbr, int slot, const voi
 // with events; the fastest is kept for the codec's lifetime.
 void Codec::tune_conv(const ConvTcArgs& a, int cin, int h) {
   const int ci = cin == 64;
-  float best = 1e30f;
-  int bv = 0;
+  // every variant warm once, then kTuneRounds interleaved rounds of one
+  // timed launch each; a variant's time is its best round (a single timing
+  // picked variants up to 15 % slower than the best)
+  constexpr int kTuneRounds = 3;
   for (int v = 0; v < kConvVariants; v++) {
     launch_conv333_tc(a, cin, N_[h], st_, v);
-    cudaEventRecord(tev_[0], st_);
-    launch_conv333_tc(a, cin, N_[h], st_, v);
-    cudaEventRecord(tev_[1], st_);
-    float ms = 1e30f;
-    if (cudaEventSynchronize(tev_[1]) != cudaSuccess ||
-        cudaEventElapsedTime(&ms, tev_[0], tev_[1]) != cudaSuccess) {
-      cudaGetLastError();
-      ms = 1e30f;
-    }
-    conv_tune_ms_[ci][v] = ms;
-    if (ms < best) {
-      best = ms;
-      bv = v;
-    }
+    conv_tune_ms_[ci][v] = 1e30f;
   }
+  for (int rd = 0; rd < kTuneRounds; rd++)
+    for (int v = 0; v < kConvVariants; v++) {
+      cudaEventRecord(tev_[0], st_);
+      launch_conv333_tc(a, cin, N_[h], st_, v);
+      cudaEventRecord(tev_[1], st_);
+      float ms = 1e30f;
+      if (cudaEventSynchronize(tev_[1]) != cudaSuccess ||
+          cudaEventElapsedTime(&ms, tev_[0], tev_[1]) != cudaSuccess) {
+        cudaGetLastError();
+        ms = 1e30f;
+      }
+      conv_tune_ms_[ci][v] = std::min(conv_tune_ms_[ci][v], ms);
+    }
+  int bv = 0;
+  for (int v = 1; v < kConvVariants; v++)
+    if (conv_tune_ms_[ci][v] < conv_tune_ms_[ci][bv]) bv = v;
   conv_variant_[ci] = bv;
 }
 
@@ -817,24 +822,27 @@ void Codec::net_level(int j, int mode, uint16_t* cdf, uint32_t* enc, int8_t* log
     if (pred_variant_ < 0 && !cap_grid_) {
       // autotuner: both variants on this launch's input (same output), the
       // faster kept for the codec
-      float best = 1e30f;
+      // as the conv's: warm once, best of three interleaved timed rounds
       for (int v = 0; v < kPredVariants; v++) {
         go(v);
-        cudaEventRecord(tev_[0], st_);
-        go(v);
-        cudaEventRecord(tev_[1], st_);
-        float ms = 1e30f;
-        if (cudaEventSynchronize(tev_[1]) != cudaSuccess ||
-            cudaEventElapsedTime(&ms, tev_[0], tev_[1]) != cudaSuccess) {
-          cudaGetLastError();
-          ms = 1e30f;
-        }
-        pred_tune_ms_[v] = ms;
-        if (ms < best) {
-          best = ms;
-          pred_variant_ = v;
-        }
+        pred_tune_ms_[v] = 1e30f;
       }
+      for (int rd = 0; rd < 3; rd++)
+        for (int v = 0; v < kPredVariants; v++) {
+          cudaEventRecord(tev_[0], st_);
+          go(v);
+          cudaEventRecord(tev_[1], st_);
+          float ms = 1e30f;
+          if (cudaEventSynchronize(tev_[1]) != cudaSuccess ||
+              cudaEventElapsedTime(&ms, tev_[0], tev_[1]) != cudaSuccess) {
+            cudaGetLastError();
+            ms = 1e30f;
+          }
+          pred_tune_ms_[v] = std::min(pred_tune_ms_[v], ms);
+        }
+      pred_variant_ = 0;
+      for (int v = 1; v < kPredVariants; v++)
+        if (pred_tune_ms_[v] < pred_tune_ms_[pred_variant_]) pred_variant_ = v;
     }
     pbeg(kFamPred);
     go(pred_variant_ < 0 ? 0 : pred_variant_);
