@@ -370,7 +370,11 @@ int Codec::create(const lpc_config& cfg, const void* blob, size_t len) {
   add((void**)&hash_.slots, 16 * hash_.cap);
   // kernel maps from height 5 (level b) down to the deepest conv level:
   // t for GRED + XFP and GRED, L - 2 (height 2) for the baseline
-  for (int h = 5; h >= (M_.arch == kArchBase ? 2 : M_.toff); h--) add((void**)&nbr_[h], 4 * 27 * P);
+  for (int h = 5; h >= (M_.arch == kArchBase ? 2 : M_.toff); h--) {
+    add((void**)&nbr_[h], 4 * 27 * P);
+    add((void**)&tmask_[h], 4 * conv_tiles(P));
+    add((void**)&ranges_[h], 8 * 148);
+  }
   if (M_.arch == kArchXfp && M_.toff == 3) add((void**)&fmid_, 32 * P);
   add((void**)&gk_, 32 * P);
   if (P <= kLanePoints)
@@ -673,6 +677,8 @@ void Codec::conv(const DLayer& W, int h, const int32_t* nbr, int slot, const voi
   a.shift = W.shift;
   a.z_out = W.z_out;
   a.nbr = nbr;
+  a.tmask = nbr == nbr_[h] ? tmask_[h] : nullptr;
+  a.ranges = a.tmask ? ranges_[h] : nullptr;
   a.d_n = d_N_ + h;
   a.xb = xb;
   a.x_stride = xbs;
@@ -746,7 +752,7 @@ void Codec::kmap(int h, int32_t* nbr, int slot) {
   pbeg(kFamHash);
   const int64_t slots = hash_slots(gridn(h));
   launch_kernel_map(key_[h], d_N_ + h, gridn(h), d_L_, h, hash_, slots, nbr, d_err_, st_,
-                    prof.mask ? d_pairs_ + slot : nullptr);
+                    prof.mask ? d_pairs_ + slot : nullptr, tmask_[h]);
   pend(kFamHash, 12.0 * slots + 20.0 * N_[h] + 27.0 * N_[h] * (4 + 8), 0);
 }
 
@@ -757,11 +763,14 @@ void Codec::ensure_nbr(int h) {
   if (have_nbr_[h]) return;
   if (h == 5) {
     kmap(5, nbr_[5], 0);
+    launch_conv_ranges(tmask_[5], d_N_ + 5, gridn(5), ranges_[5], st_);
   } else {
     ensure_nbr(h + 1);
     pbeg(kFamHash);
     launch_kernel_map_child(key_[h], par_[h], d_N_ + h, gridn(h), nbr_[h + 1], code_[h + 1],
-                            off_[h + 1], nbr_[h], st_, prof.mask ? d_pairs_ + (5 - h) : nullptr);
+                            off_[h + 1], nbr_[h], st_, prof.mask ? d_pairs_ + (5 - h) : nullptr,
+                            tmask_[h]);
+    launch_conv_ranges(tmask_[h], d_N_ + h, gridn(h), ranges_[h], st_);
     pend(kFamHash, 120.0 * N_[h] + 113.0 * N_[h + 1], 0);
   }
   have_nbr_[h] = true;

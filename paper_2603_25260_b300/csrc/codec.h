@@ -300,6 +300,8 @@ class Codec {
   ScanScratch scan_;
   HashTable hash_;
   int32_t* nbr_[kHeights] = {};  // kernel maps by height, 5 down to the deepest conv level
+  uint32_t* tmask_[kHeights] = {};  // their conv tiles' present-offset masks
+  int2* ranges_[kHeights] = {};     // and the conv CTAs' tile runs of about equal cost
   int8_t *fb_ = nullptr, *xb_ = nullptr, *xt_ = nullptr, *y1_ = nullptr, *xe_ = nullptr;
   int8_t *fmid_ = nullptr, *gk_ = nullptr;  // F^{t-1} when t = L - 3; G^k of the ablations
   int8_t *g_[2] = {}, *hx_[2] = {}, *fo_ = nullptr;

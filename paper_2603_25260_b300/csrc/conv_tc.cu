@@ -50,7 +50,7 @@ namespace lpc {
 
 namespace {
 
-constexpr int kTileM = 128;
+constexpr int kTileM = kConvTile;  // the tiles of the kernel map's present-offset masks
 constexpr int kEpilogue = 128;  // 4 warps after the producers (TMEM quadrants w % 4)
 
 // Thread roles of the two gather schedules: 8 producer warps of cp.async
@@ -259,6 +259,11 @@ k_conv333_tc(const __grid_constant__ ConvTcArgs a) {
     t_first = blockIdx.x;
     t_step = gridDim.x;
     my_tiles = blockIdx.x < ntiles ? (int)((ntiles - 1 - blockIdx.x) / gridDim.x + 1) : 0;
+  } else if (a.ranges) {  // contiguous runs of about equal cost (launch_conv_ranges)
+    const int2 rg = a.ranges[blockIdx.x];
+    t_first = rg.x;
+    t_step = 1;
+    my_tiles = rg.y;
   } else {
     const int64_t per = (ntiles + gridDim.x - 1) / gridDim.x;
     t_first = (int64_t)blockIdx.x * per;
@@ -266,6 +271,13 @@ k_conv333_tc(const __grid_constant__ ConvTcArgs a) {
     my_tiles = (int)std::max<int64_t>(0, std::min<int64_t>(per, ntiles - t_first));
   }
   auto tile_r0 = [&](int lt) { return (t_first + (int64_t)lt * t_step) * kTileM; };
+  // the tile's present offsets (bit o: some node of the tile has its offset-o
+  // neighbour): every role walks the same sequence, the present offsets in
+  // ascending order, G to a pipeline step; absent ones are neither gathered
+  // nor multiplied (their rows would all be zeros)
+  auto tile_mask = [&](int lt) -> uint32_t {
+    return a.tmask ? __ldg(a.tmask + t_first + (int64_t)lt * t_step) : 0x7FFFFFFu;
+  };
 
   if (w < kProdWarps) {
     // ---------------------------------------------------------- producers --
@@ -304,16 +316,16 @@ k_conv333_tc(const __grid_constant__ ConvTcArgs a) {
       }
     }
     uint32_t u = 0;  // stages filled so far
+    uint32_t tm_next = my_tiles > 0 ? tile_mask(0) : 0u;  // masks are read a tile ahead
     for (int lt = 0; lt < my_tiles; lt++) {
       const int64_t r0 = tile_r0(lt);
       int32_t* sNbr = sNbr0 + (lt % NB) * kTileM * 27;
       // every producer is done issuing the previous tile's copies; all leave
       // together if any saw the abort flag
       if (producer_sync_or<kProducers>(*abort != 0)) break;
-      // the next tile's map a tile ahead (two buffers), or this tile's now
-      // that the one buffer is free (tile 0's went out before the loop)
+      // the next tile's map a tile ahead (two buffers; with one buffer it
+      // went out at the end of the previous tile, tile 0's before the loop)
       if (NB == 2) issue_nbr(lt + 1);
-      else if (lt > 0) issue_nbr(lt);
       if (r0 + kTileM <= n) {
         if (producer_sync_or<kProducers>(!wait_or_abort(&nbr_bar[lt % NB], (lt / NB) & 1, abort)))
           break;
@@ -326,19 +338,31 @@ k_conv333_tc(const __grid_constant__ ConvTcArgs a) {
       }
       // a failed wait has raised the abort flag: the step loop ends here and
       // the producers leave together at the next tile's barrier
-      for (int og = 0; og < 27 / G; og++, u++) {
+      const uint32_t tm = tm_next;
+      if (lt + 1 < my_tiles) tm_next = tile_mask(lt + 1);
+      const int nsteps = (__popc(tm) + G - 1) / G;
+      uint32_t mrem = tm;  // present offsets not yet staged
+      for (int og = 0; og < nsteps; og++, u++) {
         const int sg = (int)(u % SG);
         if (GATHER) {
           // one lane's failed wait ends the warp's issuing together
           if (!__all_sync(0xffffffffu, u < (uint32_t)SG ||
                                            wait_or_abort(&empty_bar[sg], ((u / SG) - 1) & 1, abort)))
             break;
-          if (lane == 0) mbar_expect(&full_bar[sg], (uint32_t)(G * Cfg::kStageBytes));
+          int os[G];  // this step's offsets (-1: none; the last step may have fewer)
+#pragma unroll
+          for (int i = 0; i < G; i++) {
+            os[i] = mrem ? __ffs(mrem) - 1 : -1;
+            mrem &= mrem - 1;
+          }
+          if (lane == 0)
+            mbar_expect(&full_bar[sg], (uint32_t)(min(G, __popc(tm) - og * G) * Cfg::kStageBytes));
           __syncwarp();
           const int32_t* m = sNbr + lane * 4 * 27;
 #pragma unroll
           for (int i = 0; i < G; i++) {
-            const int o = og * G + i;
+            const int o = os[i];
+            if (o < 0) continue;
             const uint32_t dst = tc::smem_u32(sA + (size_t)(sg * G + i) * Cfg::kStageBytes) +
                                  (uint32_t)(lane * 4 * Cfg::RB);
             // absent neighbours (< 0) name the row past the map's extent
@@ -351,7 +375,9 @@ k_conv333_tc(const __grid_constant__ ConvTcArgs a) {
             break;
 #pragma unroll
           for (int i = 0; i < G; i++) {
-            const int o = og * G + i;
+            const int o = mrem ? __ffs(mrem) - 1 : -1;
+            mrem &= mrem - 1;
+            if (o < 0) continue;
             const uint32_t sbase = tc::smem_u32(sA + (size_t)(sg * G + i) * Cfg::kStageBytes);
 #pragma unroll
             for (int k = 0; k < kPer; k++) {
@@ -366,6 +392,12 @@ k_conv333_tc(const __grid_constant__ ConvTcArgs a) {
                            tc::smem_u32(&full_bar[sg]))
                        : "memory");
         }
+      }
+      // one map buffer: every producer has read this tile's map (its copies
+      // are issued), so the next tile's goes out now, beside the last steps
+      if (NB == 1 && lt + 1 < my_tiles) {
+        producer_sync_or<kProducers>(false);
+        issue_nbr(lt + 1);
       }
     }
     // a neighbour-row copy issued but not consumed (abort) lands before exit
@@ -387,13 +419,18 @@ k_conv333_tc(const __grid_constant__ ConvTcArgs a) {
       constexpr uint32_t idesc = tc::idesc_bf16(kTileM, 32);
       uint32_t u = 0;
       const bool wok = wait_or_abort(&w_bar, 0, abort);  // the weights have landed
+      uint32_t tm_next = my_tiles > 0 ? tile_mask(0) : 0u;
       for (int lt = 0; lt < my_tiles && wok && !*abort; lt++) {
         const int b = lt & 1;
         if (lt >= 2 && !wait_or_abort(&acc_empty[b], ((lt >> 1) - 1) & 1, abort)) break;
         tc::tc_fence_after();
         const uint32_t dbase = tbase + (uint32_t)(b * Cfg::kBufCols);
         bool ok = true;
-        for (int og = 0; og < 27 / G; og++, u++) {
+        const uint32_t tm = tm_next;
+        if (lt + 1 < my_tiles) tm_next = tile_mask(lt + 1);
+        const int nsteps = (__popc(tm) + G - 1) / G;
+        uint32_t mrem = tm, started = 0;  // started: accumulator groups written this tile
+        for (int og = 0; og < nsteps; og++, u++) {
           const int sg = (int)(u % SG);
           if (!wait_or_abort(&full_bar[sg], (u / SG) & 1, abort)) {
             ok = false;
@@ -405,16 +442,20 @@ k_conv333_tc(const __grid_constant__ ConvTcArgs a) {
           tc::tc_fence_after();
 #pragma unroll
           for (int i = 0; i < G; i++) {
-            const int o = og * G + i;
+            const int o = mrem ? __ffs(mrem) - 1 : -1;
+            mrem &= mrem - 1;
+            if (o < 0) continue;
             const uint32_t sa = tc::smem_u32(sA + (size_t)(sg * G + i) * Cfg::kStageBytes);
             const int g = o / Cfg::kPerGroup;
+            // a group's first present offset overwrites its accumulator
+            const uint32_t acc0 = (started >> g) & 1u;
+            started |= 1u << g;
 #pragma unroll
             for (int ks = 0; ks < CIN / 16; ks++) {
               const int k0 = o * CIN + ks * 16;
               const uint32_t sb = tc::smem_u32(sB) + (k0 / 64) * 4096 + (k0 % 64) * 2;
               tc::mma_bf16(dbase + g * 32, tc::smem_desc<Cfg::SW>(sa + ks * 32, 8 * Cfg::RB),
-                           tc::smem_desc<128>(sb, 1024), idesc,
-                           (o % Cfg::kPerGroup != 0 || ks > 0) ? 1u : 0u);
+                           tc::smem_desc<128>(sb, 1024), idesc, (acc0 || ks > 0) ? 1u : 0u);
             }
           }
           tc::mma_commit(&empty_bar[sg]);
@@ -432,8 +473,25 @@ k_conv333_tc(const __grid_constant__ ConvTcArgs a) {
     // ----------------------------------------------------------- epilogue --
     const int e = ((w & 3) << 5) | lane;  // row of the tile = TMEM lane (the warp's quadrant)
     const uint32_t lane_off = (uint32_t)((w & 3) * 32) << 16;
+    uint32_t tm_next = my_tiles > 0 ? tile_mask(0) : 0u;
     for (int lt = 0; lt < my_tiles; lt++) {
       const int b = lt & 1;
+      const int64_t r = tile_r0(lt) + e;
+      // the row's inputs that do not wait for the accumulators (the
+      // residual's y1 row, the embedding row) are loaded before the wait
+      uint4 y1v[2] = {}, ev[2] = {};
+      if (r < n) {
+        if (a.has_res) {
+          const uint4* ys = reinterpret_cast<const uint4*>(a.y1 + r * a.y1_stride);
+          y1v[0] = ys[0];
+          y1v[1] = ys[1];
+        }
+        if (a.emb.table) {
+          const uint4* e4 = reinterpret_cast<const uint4*>(a.emb.table + (int)a.emb.code[r] * 32);
+          ev[0] = __ldg(e4);
+          ev[1] = __ldg(e4 + 1);
+        }
+      }
       // the TMEM loads below are warp-collective: the warp leaves together
       if (!__all_sync(0xffffffffu, wait_or_abort(&acc_full[b], (lt >> 1) & 1, abort))) break;
       tc::tc_fence_after();
@@ -441,26 +499,31 @@ k_conv333_tc(const __grid_constant__ ConvTcArgs a) {
 #pragma unroll
       for (int i = 0; i < 32; i++) acc[i] = sBias[i];
       const uint32_t dbase = tbase + lane_off + (uint32_t)(b * Cfg::kBufCols);
+      const uint32_t tm = tm_next;  // groups without a present offset hold nothing
+      if (lt + 1 < my_tiles) tm_next = tile_mask(lt + 1);
+      // a group's 32 columns in flight per wait
 #pragma unroll
       for (int g = 0; g < Cfg::kGroups; g++) {
-        float v[16];
-        tc::tmem_ld16(dbase + g * 32, v);
+        if (!((tm >> (g * Cfg::kPerGroup)) & ((1u << Cfg::kPerGroup) - 1))) continue;
+        uint32_t v[2][16];
+        tc::tmem_ld16_issue(dbase + g * 32, v[0]);
+        tc::tmem_ld16_issue(dbase + g * 32 + 16, v[1]);
+        tc::tmem_wait_ld();
 #pragma unroll
-        for (int i = 0; i < 16; i++) acc[i] += __float2int_rn(v[i]);
-        tc::tmem_ld16(dbase + g * 32 + 16, v);
+        for (int k = 0; k < 2; k++) {
+          tc::tmem_regs_ready(v[k]);
 #pragma unroll
-        for (int i = 0; i < 16; i++) acc[16 + i] += __float2int_rn(v[i]);
+          for (int i = 0; i < 16; i++) acc[k * 16 + i] += __float2int_rn(__uint_as_float(v[k][i]));
+        }
       }
       tc::tc_fence_before();
       mbar_arrive(&acc_empty[b]);  // the buffer is free for tile lt + 2
-      const int64_t r = tile_r0(lt) + e;
       if (r < n) {
         __align__(16) int8_t q[32];
         if (a.has_res) {
           __align__(16) int8_t y1[32];
-          const uint4* ys = reinterpret_cast<const uint4*>(a.y1 + r * a.y1_stride);
-          reinterpret_cast<uint4*>(y1)[0] = ys[0];
-          reinterpret_cast<uint4*>(y1)[1] = ys[1];
+          reinterpret_cast<uint4*>(y1)[0] = y1v[0];
+          reinterpret_cast<uint4*>(y1)[1] = y1v[1];
 #pragma unroll
           for (int i = 0; i < 32; i++) {
             int32_t v = acc[i];
@@ -482,10 +545,9 @@ k_conv333_tc(const __grid_constant__ ConvTcArgs a) {
         dst[0] = reinterpret_cast<const uint4*>(q)[0];
         dst[1] = reinterpret_cast<const uint4*>(q)[1];
         if (a.emb.table) {  // the next step's Concat(., E[Y]) half of the row
-          const uint4* e4 = reinterpret_cast<const uint4*>(a.emb.table + (int)a.emb.code[r] * 32);
           uint4* de = reinterpret_cast<uint4*>(a.out + r * a.out_stride + a.emb_col);
-          de[0] = __ldg(e4);
-          de[1] = __ldg(e4 + 1);
+          de[0] = ev[0];
+          de[1] = ev[1];
         }
         if (a.outb) {
           __align__(16) __nv_bfloat16 bq[32];
@@ -654,11 +716,84 @@ bool encode_rows(ConvTcArgs& a, int cin, int64_t rows) {
 
 }  // namespace
 
+int conv_ctas(int64_t n_host) { return (int)std::min<int64_t>((n_host + kTileM - 1) / kTileM, 148); }
+
+// Tile runs of about equal cost for the contiguous tile order: a tile costs
+// its present offsets plus kTileCost for its fixed work (map, epilogue,
+// hand-offs).  With the exclusive cost prefix P_t, the tile's midpoint
+// K_t = P_t + floor(c_t / 2) and the total T, CTA b starts at the first tile
+// with K_t >= floor(b T / ctas) (a tile goes to the run its cost's middle
+// falls in): tile t starts the CTAs b in [cnt(K_{t-1}), cnt(K_t)) (K_{-1} =
+// -1), cnt(K) = #{b : floor(b T / ctas) <= K} = ceil((K + 1) ctas / T), so
+// every tile finds its CTAs at once.
+constexpr int kTileCost = 12;
+
+__global__ void __launch_bounds__(1024)
+k_conv_ranges(const uint32_t* __restrict__ tmask, const int64_t* d_n, int ctas, int2* ranges) {
+  __shared__ uint32_t sm[32];
+  __shared__ int start[149];
+  const int64_t n = *d_n;
+  const int nt = (int)((n + kTileM - 1) / kTileM);
+  auto cost = [&](int t) { return (uint32_t)(__popc(tmask[t]) + kTileCost); };
+  uint32_t total = 0;
+  for (int t = threadIdx.x; t < nt; t += 1024) total += cost(t);
+  total = __reduce_add_sync(0xffffffffu, total);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = total;
+  for (int b = threadIdx.x; b <= ctas; b += 1024) start[b] = nt;  // CTAs past the last tile
+  __syncthreads();
+  total = 0;
+  for (int i = 0; i < 32; i++) total += sm[i];
+  __syncthreads();
+  auto cnt = [&](int64_t P) -> int {  // CTAs whose boundary is at most P
+    const int64_t c = ((P + 1) * ctas + total - 1) / total;
+    return c < ctas ? (int)c : ctas;
+  };
+  uint32_t run = 0;
+  for (int base = 0; base < nt; base += 1024) {
+    const int t = base + threadIdx.x;
+    const uint32_t c = t < nt ? cost(t) : 0u;
+    uint32_t x = c;  // block-inclusive scan of the costs
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+      if ((threadIdx.x & 31) >= d) x += y;
+    }
+    if ((threadIdx.x & 31) == 31) sm[threadIdx.x >> 5] = x;
+    __syncthreads();
+    uint32_t before = 0;
+    for (int i = 0; i < (int)(threadIdx.x >> 5); i++) before += sm[i];
+    const uint32_t blk = sm[0] + sm[1] + sm[2] + sm[3] + sm[4] + sm[5] + sm[6] + sm[7] + sm[8] +
+                         sm[9] + sm[10] + sm[11] + sm[12] + sm[13] + sm[14] + sm[15] + sm[16] +
+                         sm[17] + sm[18] + sm[19] + sm[20] + sm[21] + sm[22] + sm[23] + sm[24] +
+                         sm[25] + sm[26] + sm[27] + sm[28] + sm[29] + sm[30] + sm[31];
+    if (t < nt) {
+      const int64_t P = (int64_t)run + before + x - c;  // exclusive prefix of tile t
+      const int64_t K = P + c / 2;
+      int64_t Kp = -1;  // the midpoint of tile t - 1
+      if (t > 0) {
+        const uint32_t cp = cost(t - 1);
+        Kp = P - cp + cp / 2;
+      }
+      for (int b = cnt(Kp); b < cnt(K); b++) start[b] = t;
+    }
+    run += blk;
+    __syncthreads();
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < ctas; b += 1024) ranges[b] = make_int2(start[b], start[b + 1] - start[b]);
+}
+
+void launch_conv_ranges(const uint32_t* tmask, const int64_t* d_n, int64_t n_host, int2* ranges,
+                        cudaStream_t st) {
+  if (n_host <= 0) return;
+  k_conv_ranges<<<1, 1024, 0, st>>>(tmask, d_n, conv_ctas(n_host), ranges);
+  count_launches(1);
+}
+
 void launch_conv333_tc(const ConvTcArgs& a, int cin, int64_t n_host, cudaStream_t st,
                        int variant) {
   if (n_host <= 0) return;
-  const int64_t ntiles = (n_host + kTileM - 1) / kTileM;
-  const int blocks = (int)std::min<int64_t>(ntiles, 148);
+  const int blocks = conv_ctas(n_host);
   if (variant & 4) {
     // TMA gather: the map covers rows [0, n_host), every neighbour index the
     // kernel reads is below the level's size <= n_host.  An input the

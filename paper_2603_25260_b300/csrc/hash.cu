@@ -85,6 +85,29 @@ __device__ __forceinline__ void count_pairs(unsigned long long* pairs, bool pres
   if ((threadIdx.x & 31) == __ffs(am) - 1) atomicAdd(pairs, (unsigned long long)__popc(bm));
 }
 
+// OR bit 1 << o of a present (node i, offset o) pair into the present-offset
+// mask of i's tile of kConvTile nodes.  A warp's 32 consecutive pairs span
+// at most three nodes, so nearly always one tile (one OR reduction and one
+// atomic), at a tile boundary two (one reduction and atomic each).
+__device__ __forceinline__ void tile_mask_or(uint32_t* tmask, int64_t i, int o, bool present) {
+  const unsigned am = __activemask();
+  const int leader = __ffs(am) - 1;
+  const uint32_t tile = (uint32_t)(i / kConvTile);
+  const uint32_t t0 = __shfl_sync(am, tile, leader);  // the lowest tile: pairs ascend by lane
+  const uint32_t bit = present ? 1u << o : 0u;
+  if (__all_sync(am, tile == t0)) {
+    const uint32_t a = __reduce_or_sync(am, bit);
+    if ((int)(threadIdx.x & 31) == leader && a) atomicOr(tmask + t0, a);
+  } else {
+    const uint32_t a = __reduce_or_sync(am, tile == t0 ? bit : 0u);
+    const uint32_t b = __reduce_or_sync(am, tile != t0 ? bit : 0u);
+    if ((int)(threadIdx.x & 31) == leader) {
+      if (a) atomicOr(tmask + t0, a);
+      if (b) atomicOr(tmask + t0 + 1, b);
+    }
+  }
+}
+
 // One thread per (node, offset); offset o = 9(dx+1) + 3(dy+1) + (dz+1).
 // The depth of a node is Lf[frame] - h for a frame batch (Lf != nullptr),
 // else h itself; neighbours keep the node's frame bits.  IdxT is 32-bit
@@ -93,7 +116,7 @@ template <typename IdxT>
 __global__ void k_kernel_map(const uint64_t* __restrict__ keys, const int64_t* d_n,
                              const int* __restrict__ Lf, int h,
                              const ulonglong2* __restrict__ tab, uint64_t mask, int shift,
-                             int32_t* nbr, int* err, unsigned long long* pairs) {
+                             int32_t* nbr, int* err, unsigned long long* pairs, uint32_t* tmask) {
   const IdxT total = (IdxT)(*d_n * 27);
   for (IdxT t = blockIdx.x * (IdxT)blockDim.x + threadIdx.x; t < total;
        t += (IdxT)gridDim.x * blockDim.x) {
@@ -126,6 +149,7 @@ __global__ void k_kernel_map(const uint64_t* __restrict__ keys, const int64_t* d
     }
     nbr[t] = r;
     if (pairs) count_pairs(pairs, r >= 0);
+    if (tmask) tile_mask_or(tmask, (int64_t)i, o, r >= 0);
   }
 }
 
@@ -138,7 +162,7 @@ __global__ void k_kernel_map_child(const uint64_t* __restrict__ ckeys,
                                    const int32_t* __restrict__ pnbr,
                                    const uint8_t* __restrict__ pcode,
                                    const uint32_t* __restrict__ poff, int32_t* nbr,
-                                   unsigned long long* pairs) {
+                                   unsigned long long* pairs, uint32_t* tmask) {
   const IdxT total = (IdxT)(*d_n * 27);
   for (IdxT t = blockIdx.x * (IdxT)blockDim.x + threadIdx.x; t < total;
        t += (IdxT)gridDim.x * blockDim.x) {
@@ -161,6 +185,7 @@ __global__ void k_kernel_map_child(const uint64_t* __restrict__ ckeys,
     }
     nbr[t] = r;
     if (pairs) count_pairs(pairs, r >= 0);
+    if (tmask) tile_mask_or(tmask, (int64_t)i, o, r >= 0);
   }
 }
 
@@ -172,8 +197,9 @@ int grid_for(int64_t work, int per_sm) {
 
 void launch_kernel_map(const uint64_t* keys, const int64_t* d_n, int64_t n_host, const int* Lf,
                        int depth, const HashTable& h, int64_t slots, int32_t* nbr, int* err,
-                       cudaStream_t st, uint64_t* pairs) {
+                       cudaStream_t st, uint64_t* pairs, uint32_t* tmask) {
   if (n_host <= 0) return;
+  if (tmask) cudaMemsetAsync(tmask, 0, 4 * (size_t)conv_tiles(n_host), st);
   const uint64_t mask = (uint64_t)slots - 1;
   int lg = 0;
   while (((int64_t)1 << lg) < slots) lg++;
@@ -183,25 +209,26 @@ void launch_kernel_map(const uint64_t* keys, const int64_t* d_n, int64_t n_host,
   k_hash_insert<<<grid_for(n_host, 8), 256, 0, st>>>(keys, d_n, h.slots, mask, shift, err);
   if (n_host * 27 < ((int64_t)1 << 31))
     k_kernel_map<uint32_t><<<grid_for(n_host * 27, 16), 256, 0, st>>>(
-        keys, d_n, Lf, depth, h.slots, mask, shift, nbr, err, pc);
+        keys, d_n, Lf, depth, h.slots, mask, shift, nbr, err, pc, tmask);
   else
     k_kernel_map<int64_t><<<grid_for(n_host * 27, 16), 256, 0, st>>>(
-        keys, d_n, Lf, depth, h.slots, mask, shift, nbr, err, pc);
+        keys, d_n, Lf, depth, h.slots, mask, shift, nbr, err, pc, tmask);
   count_launches(3);
 }
 
 void launch_kernel_map_child(const uint64_t* ckeys, const uint32_t* cpar, const int64_t* d_n,
                              int64_t n_host, const int32_t* pnbr, const uint8_t* pcode,
                              const uint32_t* poff, int32_t* nbr, cudaStream_t st,
-                             uint64_t* pairs) {
+                             uint64_t* pairs, uint32_t* tmask) {
   if (n_host <= 0) return;
+  if (tmask) cudaMemsetAsync(tmask, 0, 4 * (size_t)conv_tiles(n_host), st);
   auto pc = reinterpret_cast<unsigned long long*>(pairs);
   if (n_host * 27 < ((int64_t)1 << 31))
     k_kernel_map_child<uint32_t><<<grid_for(n_host * 27, 16), 256, 0, st>>>(
-        ckeys, cpar, d_n, pnbr, pcode, poff, nbr, pc);
+        ckeys, cpar, d_n, pnbr, pcode, poff, nbr, pc, tmask);
   else
     k_kernel_map_child<int64_t><<<grid_for(n_host * 27, 16), 256, 0, st>>>(
-        ckeys, cpar, d_n, pnbr, pcode, poff, nbr, pc);
+        ckeys, cpar, d_n, pnbr, pcode, poff, nbr, pc, tmask);
   count_launches(1);
 }
 

@@ -169,10 +169,15 @@ struct HashTable {
 // then write the 27-neighbour map nbr[N][27].  Node depth: Lf[frame] - depth
 // for a frame batch (Lf = per-frame octree depths on the device), else
 // `depth`.  If pairs != nullptr, the number of present (node, neighbour)
-// pairs, centre included, is added to it.
+// pairs, centre included, is added to it.  If tmask != nullptr (at least
+// conv_tiles(n_host) words), tmask[t] gets bit o set when some node of tile
+// t (nodes t kConvTile .. (t + 1) kConvTile - 1) has its offset-o neighbour:
+// the conv skips the offsets a tile lacks.
+constexpr int kConvTile = 128;  // output nodes per tile of the tensor-core conv
+inline int64_t conv_tiles(int64_t n) { return (n + kConvTile - 1) / kConvTile; }
 void launch_kernel_map(const uint64_t* keys, const int64_t* d_n, int64_t n_host, const int* Lf,
                        int depth, const HashTable& h, int64_t slots, int32_t* nbr, int* err,
-                       cudaStream_t st, uint64_t* pairs = nullptr);
+                       cudaStream_t st, uint64_t* pairs = nullptr, uint32_t* tmask = nullptr);
 // The 27-neighbour map of a level from its parents' map: ckeys / cpar are the
 // children's keys and parent rows (*d_n children), pnbr[Np][27] the parents'
 // map, pcode / poff their occupancy codes and first child rows.  Same output
@@ -180,7 +185,7 @@ void launch_kernel_map(const uint64_t* keys, const int64_t* d_n, int64_t n_host,
 void launch_kernel_map_child(const uint64_t* ckeys, const uint32_t* cpar, const int64_t* d_n,
                              int64_t n_host, const int32_t* pnbr, const uint8_t* pcode,
                              const uint32_t* poff, int32_t* nbr, cudaStream_t st,
-                             uint64_t* pairs = nullptr);
+                             uint64_t* pairs = nullptr, uint32_t* tmask = nullptr);
 
 // ---------------------------------------------------------------- layers --
 // Device-resident INT8 layer (blob kinds 1 and 4) in dp4a layout.
@@ -267,6 +272,8 @@ struct ConvTcArgs {
   const int16_t* slope;
   int prelu, shift, z_out;
   const int32_t* nbr;
+  const uint32_t* tmask;  // per tile of kConvTile nodes: its present offsets (null: all 27)
+  const int2* ranges;     // contiguous order: each CTA's tile run (null: equal tile counts)
   const int64_t* d_n;
   const void* xb;
   int x_stride;  // elements
@@ -289,6 +296,12 @@ void pack_conv_tc_weights(const int8_t* W, int cin, uint16_t* img);
 // gather schedule (bit 2: cp.async copies, or TMA gather4 loads), chosen by
 // the codec's autotuner; every variant gives the same result.
 constexpr int kConvVariants = 8;
+// CTAs of a conv launch over n_host nodes (its grid), and their tile runs
+// of about equal cost from the tiles' present-offset masks (ranges[ctas]),
+// which the contiguous tile order takes when given.
+int conv_ctas(int64_t n_host);
+void launch_conv_ranges(const uint32_t* tmask, const int64_t* d_n, int64_t n_host, int2* ranges,
+                        cudaStream_t st);
 void launch_conv333_tc(const ConvTcArgs& a, int cin, int64_t n_host, cudaStream_t st,
                        int variant = 0);
 // int8 rows (stride x_stride) -> bf16 (q - z) rows of `cols` elements.
