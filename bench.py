@@ -66,6 +66,9 @@ def parse():
     ap.add_argument("--ncu-case", choices=["single", "batch"],
                     help="profiling case: warm up, then one encode + decode inside the NVTX "
                          "range 'profile' (for ncu --nvtx-include profile/), no timing")
+    ap.add_argument("--tuning", default=None,
+                    help="profiling case: fix the kernel variants as conv32,conv64,predictor "
+                         "(the ones a plain run chose) instead of tuning under the profiler")
     return ap.parse_args()
 
 
@@ -866,6 +869,8 @@ def run_ncu_case(args):
             out = codec.encode_batch(xs, Ls)
             codec.decode_batch(out, counts)
             return sum(len(o) for o in out)
+    if args.tuning:
+        codec.set_tuning(*[int(v) for v in args.tuning.split(",")])
     for _ in range(max(args.warmup, 1)):
         step()
     torch.cuda.synchronize()
