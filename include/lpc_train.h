@@ -41,24 +41,34 @@ int lpc_t_conv_bwd(const float* x, const float* dy, int64_t N, int cin, const in
                    uint64_t stream);
 int lpc_t_tc_error(int reset);
 
-/* Upsampling + Pruning (Eq. 6): y[r] = b[c] + W[c] x[par[r]], c = ckey[r] & 7. */
-int lpc_t_up_fwd(const float* x, int cin, const uint32_t* par, const uint64_t* ckey, int64_t Nc,
-                 const float* W, const float* b, int cout, float* y, int bf16, uint64_t stream);
+/* Upsampling + Pruning (Eq. 6): y[r] = b[c] + W[c] x[par[r]], c = ckey[r] & 7.
+ * x [Np][cin]; off [Np + 1] the parents' first children (children of parent
+ * p: off[p] .. off[p + 1] - 1).  bf16 mode with cout = 32 runs on the tensor
+ * cores: every parent against all eight slots' weights, each child taking
+ * its slot's columns. */
+int lpc_t_up_fwd(const float* x, int64_t Np, int cin, const uint32_t* off, const uint32_t* par,
+                 const uint64_t* ckey, int64_t Nc, const float* W, const float* b, int cout,
+                 float* y, int bf16, uint64_t stream);
 /* dx[p] = sum over children r of W[c_r]^T dy[r]; dW[c] += sum_{c_r = c} dy[r]
- * x[par r]^T; db[c] += sum_{c_r = c} dy[r]. */
+ * x[par r]^T; db[c] += sum_{c_r = c} dy[r].  bf16 mode with cout = 32 takes dx
+ * on the tensor cores (a gather of each parent's eight child slots). */
 int lpc_t_up_bwd(const float* x, const float* dy, int64_t Np, int cin, const uint32_t* off,
                  const uint32_t* par, const uint64_t* ckey, int64_t Nc, const float* W, int cout,
                  float* dx, float* dW, float* db, int bf16, uint64_t stream);
 
-/* Stride-2 down conv (Eq. 4): y[p] = b + sum_{r child of p} W[c_r] x[r]. */
-int lpc_t_down_fwd(const float* x, int cin, const uint32_t* off, const uint64_t* ckey, int64_t Np,
-                   const float* W, const float* b, int cout, float* y, int bf16,
+/* Stride-2 down conv (Eq. 4): y[p] = b + sum_{r child of p} W[c_r] x[r].
+ * bf16 mode with cin = 32 runs on the tensor cores (a gather of each
+ * parent's eight child slots). */
+int lpc_t_down_fwd(const float* x, int64_t Nc, int cin, const uint32_t* off, const uint64_t* ckey,
+                   int64_t Np, const float* W, const float* b, int cout, float* y, int bf16,
                    uint64_t stream);
 /* dx[r] = W[c_r]^T dy[par r]; dW[c] += sum_{c_r = c} dy[par r] x[r]^T;
- * db += sum_p dy[p]. */
-int lpc_t_down_bwd(const float* x, const float* dy, int64_t Nc, int cin, const uint32_t* par,
-                   const uint64_t* ckey, int64_t Np, const float* W, int cout, float* dx,
-                   float* dW, float* db, int bf16, uint64_t stream);
+ * db += sum_p dy[p].  off [Np + 1] as for lpc_t_up_fwd; bf16 mode with
+ * cin = 32 takes dx on the tensor cores (every parent's dy against all eight
+ * slots' transposed weights, each child taking its slot's columns). */
+int lpc_t_down_bwd(const float* x, const float* dy, int64_t Nc, int cin, const uint32_t* off,
+                   const uint32_t* par, const uint64_t* ckey, int64_t Np, const float* W,
+                   int cout, float* dx, float* dW, float* db, int bf16, uint64_t stream);
 
 /* Occupancy-code embedding: y[i] = E[codes[i]]; dE[codes[i]] += dy[i]. */
 int lpc_t_embed_fwd(const uint8_t* codes, int64_t N, const float* E, int C, float* y,

@@ -323,6 +323,21 @@ int conv_tc_error(bool reset);
 // float; operands rounded to bf16, fp32 accumulation.
 int tconv_tc(const float* in, int64_t n, int cin, const int32_t* nbr, const float* W,
              const float* bias, float* out, int mirror, cudaStream_t st);
+// The up- and down-steps of the twin in bf16 mode on tcgen05 (W [8][cout][cin],
+// off [np + 1] the parents' first children, ckey the children's keys):
+// tslot_tc gathers each parent's eight child slots (transpose 0: the
+// down-step forward, in = child rows [nc][cin], out [np][cout] + bias; 1:
+// the up-step's input gradient, in = dy [nc][cout], out [np][cin]);
+// texpand_tc multiplies each parent's row by all eight slots and scatters
+// each child its slot's 32 columns (transpose 0: the up-step forward, in =
+// x [np][cin], out [nc][cout] + per-slot bias [8][cout]; 1: the down-step's
+// input gradient, in = dy [np][cout], out [nc][cin]).
+int tslot_tc(const float* in, int64_t np, int64_t nc, const uint32_t* off, const uint64_t* ckey,
+             const float* W, int cout, int cin, const float* bias, float* out, int transpose,
+             cudaStream_t st);
+int texpand_tc(const float* in, int64_t np, const uint32_t* off, const uint64_t* ckey,
+               const float* W, int cout, int cin, const float* slot_bias, float* out,
+               int transpose, cudaStream_t st);
 
 // Predictor + integer softmax + cumulative table.
 enum PredMode { kPredCdf = 0, kPredEnc = 1, kPredLogits = 2 };

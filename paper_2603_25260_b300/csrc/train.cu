@@ -370,11 +370,14 @@ int lpc_t_conv_bwd(const float* x, const float* dy, int64_t N, int cin, const in
   return s;
 }
 
-int lpc_t_up_fwd(const float* x, int cin, const uint32_t* par, const uint64_t* ckey, int64_t Nc,
-                 const float* W, const float* b, int cout, float* y, int bf16, uint64_t stream) {
-  if (Nc < 0 || !ok_dims(cin, cout)) return LPC_INVALID_ARG;
-  return gmv(UpFwdItems{par, ckey}, W, 8, cout, cin, 0, b, b ? 2 : 0, x, Nc, y, bf16,
-             reinterpret_cast<cudaStream_t>(stream));
+int lpc_t_up_fwd(const float* x, int64_t Np, int cin, const uint32_t* off, const uint32_t* par,
+                 const uint64_t* ckey, int64_t Nc, const float* W, const float* b, int cout,
+                 float* y, int bf16, uint64_t stream) {
+  if (Nc < 0 || Np < 0 || !ok_dims(cin, cout)) return LPC_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  // bf16 operands: every parent against all eight slots on the tensor cores
+  if (bf16 && cout == 32 && off) return texpand_tc(x, Np, off, ckey, W, cout, cin, b, y, 0, st);
+  return gmv(UpFwdItems{par, ckey}, W, 8, cout, cin, 0, b, b ? 2 : 0, x, Nc, y, bf16, st);
 }
 
 int lpc_t_up_bwd(const float* x, const float* dy, int64_t Np, int cin, const uint32_t* off,
@@ -383,27 +386,36 @@ int lpc_t_up_bwd(const float* x, const float* dy, int64_t Np, int cin, const uin
   if (Nc < 0 || Np < 0 || !ok_dims(cin, cout)) return LPC_INVALID_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   int s = LPC_OK;
-  if (dx) s = gmv(ChildItems{off, ckey}, W, 8, cin, cout, 1, nullptr, 0, dy, Np, dx, bf16, st);
+  if (dx && bf16 && cout == 32)  // the parents' eight child slots on the tensor cores
+    s = tslot_tc(dy, Np, Nc, off, ckey, W, cout, cin, nullptr, dx, 1, st);
+  else if (dx)
+    s = gmv(ChildItems{off, ckey}, W, 8, cin, cout, 1, nullptr, 0, dy, Np, dx, bf16, st);
   if (!s) s = outer(UpPairs{par, ckey}, 8, cout, cin, dy, x, Nc, dW, bf16, st);
   if (!s) s = bias_grad(dy, Nc, cout, ckey, db, st);
   return s;
 }
 
-int lpc_t_down_fwd(const float* x, int cin, const uint32_t* off, const uint64_t* ckey, int64_t Np,
-                   const float* W, const float* b, int cout, float* y, int bf16,
+int lpc_t_down_fwd(const float* x, int64_t Nc, int cin, const uint32_t* off, const uint64_t* ckey,
+                   int64_t Np, const float* W, const float* b, int cout, float* y, int bf16,
                    uint64_t stream) {
-  if (Np < 0 || !ok_dims(cin, cout)) return LPC_INVALID_ARG;
-  return gmv(ChildItems{off, ckey}, W, 8, cout, cin, 0, b, b ? 1 : 0, x, Np, y, bf16,
-             reinterpret_cast<cudaStream_t>(stream));
+  if (Np < 0 || Nc < 0 || !ok_dims(cin, cout)) return LPC_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  // bf16 operands: the parents' eight child slots gathered on the tensor cores
+  if (bf16 && cin == 32 && (cout == 32 || cout == 64))
+    return tslot_tc(x, Np, Nc, off, ckey, W, cout, cin, b, y, 0, st);
+  return gmv(ChildItems{off, ckey}, W, 8, cout, cin, 0, b, b ? 1 : 0, x, Np, y, bf16, st);
 }
 
-int lpc_t_down_bwd(const float* x, const float* dy, int64_t Nc, int cin, const uint32_t* par,
-                   const uint64_t* ckey, int64_t Np, const float* W, int cout, float* dx,
-                   float* dW, float* db, int bf16, uint64_t stream) {
+int lpc_t_down_bwd(const float* x, const float* dy, int64_t Nc, int cin, const uint32_t* off,
+                   const uint32_t* par, const uint64_t* ckey, int64_t Np, const float* W,
+                   int cout, float* dx, float* dW, float* db, int bf16, uint64_t stream) {
   if (Nc < 0 || Np < 0 || !ok_dims(cin, cout)) return LPC_INVALID_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   int s = LPC_OK;
-  if (dx) s = gmv(UpFwdItems{par, ckey}, W, 8, cin, cout, 1, nullptr, 0, dy, Nc, dx, bf16, st);
+  if (dx && bf16 && cin == 32 && off)  // every parent's dy against all slots on the tensor cores
+    s = texpand_tc(dy, Np, off, ckey, W, cout, cin, nullptr, dx, 1, st);
+  else if (dx)
+    s = gmv(UpFwdItems{par, ckey}, W, 8, cin, cout, 1, nullptr, 0, dy, Nc, dx, bf16, st);
   if (!s) s = outer(DownPairs{par, ckey}, 8, cout, cin, dy, x, Nc, dW, bf16, st);
   if (!s) s = bias_grad(dy, Np, cout, nullptr, db, st);
   return s;

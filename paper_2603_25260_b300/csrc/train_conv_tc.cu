@@ -37,25 +37,29 @@ constexpr int kEpi = 128;
 constexpr int kMmaW = kPWarps + 4;
 constexpr int kThr = kProd + kEpi + 32;
 
-// CIN: gathered row width (bf16 elements); NOUT: output width.  Ring shapes:
-// 64-wide rows take 16 KB stages beside a 110 KB weight image (6 stages, one
-// neighbour-map buffer); 32-wide rows 8 KB stages.
-template <int CIN, int NOUT>
+// CIN: gathered row width (bf16 elements); NOUT: output width; KO: offsets
+// gathered per output row (27: the 3x3x3 conv's kernel map; 8: a parent's
+// eight child slots; 1: the row itself).  Ring shapes: 64-wide rows take
+// 16 KB stages (6 stages), 32-wide rows 8 KB stages (12); G offsets share a
+// pipeline step (3 of 27, 2 of 8, 1 of 1).
+template <int CIN, int NOUT, int KO>
 struct TCfg {
   static constexpr int RB = CIN * 2;
   static constexpr int SW = CIN == 64 ? 128 : 64;
   static constexpr int kChunks = RB / 16;
-  static constexpr int kBBlocks = (27 * CIN + 63) / 64;
+  static constexpr int kBBlocks = (KO * CIN + 63) / 64;
   static constexpr int kBBlockBytes = NOUT * 128;
   static constexpr int kBBytes = kBBlocks * kBBlockBytes;
   static constexpr int kStageBytes = kTM * RB;
   static constexpr int kStages = CIN == 64 ? 6 : 12;
-  static constexpr int kG = 3;
-  static constexpr int kNbrBufs = (CIN == 64 || NOUT == 64) ? 1 : 2;
-  static constexpr int kNbrBytes = kTM * 27 * 4;
+  static constexpr int kG = KO == 27 ? 3 : (KO == 8 ? 2 : 1);
+  static constexpr int kNbrBufs = KO == 1 ? 0 : ((CIN == 64 || NOUT == 64) && KO == 27 ? 1 : 2);
+  static constexpr int kNbrBytes = kTM * KO * 4;
   static constexpr size_t kSmem =
       1024 + kBBytes + (size_t)kStages * kStageBytes + kNbrBufs * kNbrBytes;
-  static constexpr int kTmemCols = NOUT == 64 ? 128 : 64;  // two accumulator buffers
+  static constexpr int kTmemCols = 2 * NOUT;  // two accumulator buffers
+  static_assert(kStages % kG == 0 && KO % kG == 0, "steps must tile the ring and the offsets");
+  static_assert(kTmemCols == 64 || kTmemCols == 128 || kTmemCols == 512, "TMEM allocation");
   static_assert(kSmem <= 232448, "shared memory of a training conv variant exceeds the limit");
 };
 
@@ -114,16 +118,22 @@ __device__ __forceinline__ bool producer_sync_or(bool v) {
 
 struct TConvArgs {
   const __nv_bfloat16* xb;  // gathered rows [rows][CIN], bf16
-  const int32_t* nbr;       // [n][27]
+  const int32_t* nbr;       // [n][KO] (KO > 1): the gathered row of each offset, -1 absent
   int64_t n;
   const uint16_t* wimg;     // weight image, TCfg::kBBytes
-  const float* bias;        // [NOUT] or null
-  float* out;               // [n][NOUT]
+  const float* bias;        // rows: [NOUT]; scatter: [8][32] per slot; or null
+  float* out;               // rows: [n][NOUT]; scatter: [children][32]
+  // scatter epilogue (NOUT = 256 = 8 slots x 32): output row p is a parent
+  // whose children off[p] .. off[p + 1] - 1 (slot ckey & 7) take the 32
+  // columns of their slot
+  const uint32_t* off;
+  const uint64_t* ckey;
 };
 
-template <int CIN, int NOUT>
+// EPI 0: output rows of NOUT floats (+ bias); EPI 1: the scatter above.
+template <int CIN, int NOUT, int KO, int EPI>
 __global__ void __launch_bounds__(kThr, 1) k_tconv_tc(TConvArgs a) {
-  using Cfg = TCfg<CIN, NOUT>;
+  using Cfg = TCfg<CIN, NOUT, KO>;
   constexpr int S = Cfg::kStages, G = Cfg::kG, SG = S / G, NB = Cfg::kNbrBufs;
   extern __shared__ unsigned char smraw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>(
@@ -172,14 +182,16 @@ __global__ void __launch_bounds__(kThr, 1) k_tconv_tc(TConvArgs a) {
 
   if (w < kPWarps) {
     // ---------------------------------------------------------- producers --
+    // (with one offset the gathered row is the output row itself: no map)
+    constexpr int NBX = NB > 0 ? NB : 1;
     int last_issued = -1, last_used = -1;
     auto issue_nbr = [&](int lt) {
-      if (t == 0 && lt < my_tiles && tile_r0(lt) + kTM <= n) {
+      if (KO > 1 && t == 0 && lt < my_tiles && tile_r0(lt) + kTM <= n) {
         last_issued = lt;
         tc::fence_async_smem();
-        uint64_t* bar = &nbr_bar[lt % NB];
+        uint64_t* bar = &nbr_bar[lt % NBX];
         mbar_expect(bar, Cfg::kNbrBytes);
-        bulk_g2s(sNbr0 + (lt % NB) * kTM * 27, a.nbr + tile_r0(lt) * 27, Cfg::kNbrBytes, bar);
+        bulk_g2s(sNbr0 + (lt % NBX) * kTM * KO, a.nbr + tile_r0(lt) * KO, Cfg::kNbrBytes, bar);
       }
     };
     issue_nbr(0);
@@ -199,20 +211,22 @@ __global__ void __launch_bounds__(kThr, 1) k_tconv_tc(TConvArgs a) {
     uint32_t u = 0;
     for (int lt = 0; lt < my_tiles; lt++) {
       const int64_t r0 = tile_r0(lt);
-      int32_t* sNbr = sNbr0 + (lt % NB) * kTM * 27;
+      int32_t* sNbr = sNbr0 + (lt % NBX) * kTM * KO;
       if (producer_sync_or(*abort != 0)) break;
-      if (NB == 2) issue_nbr(lt + 1);
-      else if (lt > 0) issue_nbr(lt);
-      if (r0 + kTM <= n) {
-        if (producer_sync_or(!wait_or_abort(&nbr_bar[lt % NB], (lt / NB) & 1, abort))) break;
-        last_used = lt;
-      } else {
-        const int64_t base = r0 * 27, lim = n * 27;
-        for (int i = t; i < kTM * 27; i += kProd)
-          sNbr[i] = base + i < lim ? __ldg(a.nbr + base + i) : -1;
-        producer_sync_or(false);
+      if (KO > 1) {
+        if (NB == 2) issue_nbr(lt + 1);
+        else if (lt > 0) issue_nbr(lt);
+        if (r0 + kTM <= n) {
+          if (producer_sync_or(!wait_or_abort(&nbr_bar[lt % NBX], (lt / NBX) & 1, abort))) break;
+          last_used = lt;
+        } else {
+          const int64_t base = r0 * KO, lim = n * KO;
+          for (int i = t; i < kTM * KO; i += kProd)
+            sNbr[i] = base + i < lim ? __ldg(a.nbr + base + i) : -1;
+          producer_sync_or(false);
+        }
       }
-      for (int og = 0; og < 27 / G; og++, u++) {
+      for (int og = 0; og < KO / G; og++, u++) {
         const int sg = (int)(u % SG);
         if (u >= (uint32_t)SG && !wait_or_abort(&empty_bar[sg], ((u / SG) - 1) & 1, abort))
           break;
@@ -222,7 +236,8 @@ __global__ void __launch_bounds__(kThr, 1) k_tconv_tc(TConvArgs a) {
           const uint32_t sbase = tc::smem_u32(sA + (size_t)(sg * G + i) * Cfg::kStageBytes);
 #pragma unroll
           for (int k = 0; k < kPer; k++) {
-            const int32_t nb = sNbr[prow[k] * 27 + o];
+            const int32_t nb = KO > 1 ? sNbr[prow[k] * KO + o]
+                                      : (r0 + prow[k] < n ? (int32_t)(r0 + prow[k]) : -1);
             const uint32_t r = (uint32_t)max(nb, 0);
             tc::cp_async16(sbase + pdst[k], psrc[k] + (size_t)r * Cfg::RB, nb >= 0);
           }
@@ -233,7 +248,7 @@ __global__ void __launch_bounds__(kThr, 1) k_tconv_tc(TConvArgs a) {
       }
     }
     if (t == 0 && last_issued > last_used)
-      tc::mbar_wait(&nbr_bar[last_issued % NB], (last_issued / NB) & 1);
+      tc::mbar_wait(&nbr_bar[last_issued % NBX], (last_issued / NBX) & 1);
     tc::cp_async_wait<0>();
   } else if (w == kMmaW) {
     // ---------------------------------------------------------------- MMA --
@@ -247,7 +262,7 @@ __global__ void __launch_bounds__(kThr, 1) k_tconv_tc(TConvArgs a) {
         tc::tc_fence_after();
         const uint32_t dbase = tbase + (uint32_t)(b * NOUT);
         bool ok = true;
-        for (int og = 0; og < 27 / G; og++, u++) {
+        for (int og = 0; og < KO / G; og++, u++) {
           const int sg = (int)(u % SG);
           if (!wait_or_abort(&full_bar[sg], (u / SG) & 1, abort)) {
             ok = false;
@@ -283,24 +298,64 @@ __global__ void __launch_bounds__(kThr, 1) k_tconv_tc(TConvArgs a) {
     const uint32_t lane_off = (uint32_t)((w & 3) * 32) << 16;
     for (int lt = 0; lt < my_tiles; lt++) {
       const int b = lt & 1;
-      if (!__all_sync(0xffffffffu, wait_or_abort(&acc_full[b], (lt >> 1) & 1, abort))) break;
-      tc::tc_fence_after();
-      uint32_t raw[NOUT / 16][16];
-      const uint32_t dbase = tbase + lane_off + (uint32_t)(b * NOUT);
+      if constexpr (EPI == 1) {
+        // output row p is a parent: its first child and the slots it has,
+        // read before the accumulators are waited for
+        const int64_t p = tile_r0(lt) + e;
+        uint32_t c0 = 0, smask = 0;
+        if (p < n) {
+          c0 = __ldg(a.off + p);
+          const uint32_t c1 = __ldg(a.off + p + 1);
+          for (uint32_t r = c0; r < c1 && r < c0 + 8; r++) smask |= 1u << (__ldg(a.ckey + r) & 7);
+        }
+        if (!__all_sync(0xffffffffu, wait_or_abort(&acc_full[b], (lt >> 1) & 1, abort))) break;
+        tc::tc_fence_after();
+        const uint32_t dbase = tbase + lane_off + (uint32_t)(b * NOUT);
+        // the TMEM loads are warp-collective (one column address a warp), so
+        // every lane reads every slot and stores the ones its parent has
+#pragma unroll 1
+        for (int s = 0; s < 8; s++) {
+          uint32_t v[2][16];
+          tc::tmem_ld16_issue(dbase + s * 32, v[0]);
+          tc::tmem_ld16_issue(dbase + s * 32 + 16, v[1]);
+          tc::tmem_wait_ld();
+          tc::tmem_regs_ready(v[0]);
+          tc::tmem_regs_ready(v[1]);
+          if (p < n && ((smask >> s) & 1u)) {
+            const uint32_t r = c0 + __popc(smask & ((1u << s) - 1u));
+            float4* dst = reinterpret_cast<float4*>(a.out + (int64_t)r * 32);
 #pragma unroll
-      for (int g = 0; g < NOUT / 16; g++) tc::tmem_ld16_issue(dbase + g * 16, raw[g]);
-      tc::tmem_wait_ld();
-      tc::tc_fence_before();
-      mbar_arrive(&acc_empty[b]);
-      const int64_t r = tile_r0(lt) + e;
-      if (r < n) {
-        float4* dst = reinterpret_cast<float4*>(a.out + r * NOUT);
+            for (int c = 0; c < 32; c += 4)
+              dst[c / 4] = make_float4(__uint_as_float(v[c / 16][c % 16]) + sBias[s * 32 + c],
+                                       __uint_as_float(v[c / 16][c % 16 + 1]) + sBias[s * 32 + c + 1],
+                                       __uint_as_float(v[c / 16][c % 16 + 2]) + sBias[s * 32 + c + 2],
+                                       __uint_as_float(v[c / 16][c % 16 + 3]) + sBias[s * 32 + c + 3]);
+          }
+        }
+        tc::tc_fence_before();
+        mbar_arrive(&acc_empty[b]);
+      } else {
+        if (!__all_sync(0xffffffffu, wait_or_abort(&acc_full[b], (lt >> 1) & 1, abort))) break;
+        tc::tc_fence_after();
+        uint32_t raw[NOUT / 16][16];
+        const uint32_t dbase = tbase + lane_off + (uint32_t)(b * NOUT);
 #pragma unroll
-        for (int c = 0; c < NOUT; c += 4)
-          dst[c / 4] = make_float4(__uint_as_float(raw[c / 16][c % 16]) + sBias[c],
-                                   __uint_as_float(raw[c / 16][c % 16 + 1]) + sBias[c + 1],
-                                   __uint_as_float(raw[c / 16][c % 16 + 2]) + sBias[c + 2],
-                                   __uint_as_float(raw[c / 16][c % 16 + 3]) + sBias[c + 3]);
+        for (int g = 0; g < NOUT / 16; g++) tc::tmem_ld16_issue(dbase + g * 16, raw[g]);
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int g = 0; g < NOUT / 16; g++) tc::tmem_regs_ready(raw[g]);
+        tc::tc_fence_before();
+        mbar_arrive(&acc_empty[b]);
+        const int64_t r = tile_r0(lt) + e;
+        if (r < n) {
+          float4* dst = reinterpret_cast<float4*>(a.out + r * NOUT);
+#pragma unroll
+          for (int c = 0; c < NOUT; c += 4)
+            dst[c / 4] = make_float4(__uint_as_float(raw[c / 16][c % 16]) + sBias[c],
+                                     __uint_as_float(raw[c / 16][c % 16 + 1]) + sBias[c + 1],
+                                     __uint_as_float(raw[c / 16][c % 16 + 2]) + sBias[c + 2],
+                                     __uint_as_float(raw[c / 16][c % 16 + 3]) + sBias[c + 3]);
+        }
       }
     }
   }
@@ -324,24 +379,46 @@ __global__ void k_f32_to_bf16(const float* __restrict__ x, int64_t count, __nv_b
 }
 
 // Weight image of the gather-GEMM (K-major, 64-element blocks of nout rows x
-// 128 bytes, 128-byte swizzled): forward (mirror 0) row n = output channel,
-// k = o cin + ci, value W[o][n][ci]; input gradient (mirror 1) row n = ci,
-// k = o' 32 + c, value W[26 - o'][c][ci].  W is [27][32][cin].
-__global__ void k_pack_tw(const float* __restrict__ W, int cin, int mirror, int nout, int kper,
-                          unsigned char* img) {
-  const int64_t total = (int64_t)27 * kper * nout;
+// 128 bytes, 128-byte swizzled) from W [S][cout][cin]; k = o kper + kk:
+//  mode 0, gather forward: row n = output channel, value W[o][n][kk];
+//  mode 1, the conv's input gradient: row n = ci, value W[26 - o][kk][n];
+//  mode 2, gather transposed (the up-step's input gradient): W[o][kk][n];
+//  mode 3, expand (the up-step forward, one offset): row n = s cout + co,
+//          value W[s][co][kk];
+//  mode 4, expand transposed (the down-step's input gradient): row n =
+//          s cin + ci, value W[s][kk][ci].
+__global__ void k_pack_tw(const float* __restrict__ W, int cout, int cin, int mode, int ko,
+                          int kper, int nout, unsigned char* img) {
+  const int64_t total = (int64_t)ko * kper * nout;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int nrow = (int)(idx % nout);
     const int k = (int)(idx / nout);
     const int o = k / kper, kk = k % kper;
-    const float v = mirror ? W[((size_t)(26 - o) * 32 + kk) * cin + nrow]
-                           : W[((size_t)o * 32 + nrow) * cin + kk];
+    float v;
+    if (mode == 0) v = W[((size_t)o * cout + nrow) * cin + kk];
+    else if (mode == 1) v = W[((size_t)(26 - o) * cout + kk) * cin + nrow];
+    else if (mode == 2) v = W[((size_t)o * cout + kk) * cin + nrow];
+    else if (mode == 3) v = W[((size_t)(nrow / cout) * cout + nrow % cout) * cin + kk];
+    else v = W[((size_t)(nrow / cin) * cout + kk) * cin + nrow % cin];
     const __nv_bfloat16 b = __float2bfloat16_rn(v);
     const int blk = k / 64, kb = k % 64;
     uint32_t off = (uint32_t)(nrow * 128 + kb * 2);
     off ^= ((off >> 7) & 7) << 4;
     *reinterpret_cast<__nv_bfloat16*>(img + (size_t)blk * nout * 128 + off) = b;
+  }
+}
+
+// A parent's eight child slots: smap[p][s] = its child in slot s, else -1.
+__global__ void k_slot_map(const uint32_t* __restrict__ off, const uint64_t* __restrict__ ckey,
+                           int64_t np, int32_t* smap) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < np;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    int32_t m[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
+    const uint32_t c1 = off[p + 1];
+    for (uint32_t r = off[p]; r < c1; r++) m[ckey[r] & 7] = (int32_t)r;
+#pragma unroll
+    for (int s = 0; s < 8; s++) smap[p * 8 + s] = m[s];
   }
 }
 
@@ -367,16 +444,37 @@ void* grow(Scratch& s, size_t bytes) {
   return s.p;
 }
 
-template <int CIN, int NOUT>
+Scratch g_smap;
+
+template <int CIN, int NOUT, int KO, int EPI>
 int launch(const TConvArgs& a, cudaStream_t st) {
-  using Cfg = TCfg<CIN, NOUT>;
+  using Cfg = TCfg<CIN, NOUT, KO>;
   const int64_t ntiles = (a.n + kTM - 1) / kTM;
   const int blocks = (int)std::min<int64_t>(ntiles, 148);
-  cudaFuncSetAttribute(k_tconv_tc<CIN, NOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)Cfg::kSmem);
-  k_tconv_tc<CIN, NOUT><<<blocks, kThr, Cfg::kSmem, st>>>(a);
+  auto* k = k_tconv_tc<CIN, NOUT, KO, EPI>;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::kSmem);
+  k<<<blocks, kThr, Cfg::kSmem, st>>>(a);
   count_launches(1);
   return cudaGetLastError() == cudaSuccess ? LPC_OK : LPC_CUDA_ERROR;
+}
+
+// The float input rows as bf16 and the weight image (mode, ko offsets of
+// kper, nout rows) in scratch; returns false if scratch is missing.
+bool stage_inputs(const float* in, int64_t rows, int gw, const float* W, int cout, int cin,
+                  int mode, int ko, int nout, void** xb, void** img, cudaStream_t st) {
+  const size_t img_bytes = (size_t)((ko * gw + 63) / 64) * nout * 128;
+  *xb = grow(g_rows, (size_t)std::max<int64_t>(rows * gw * 2, 16));
+  *img = grow(g_img, img_bytes);
+  if (!*xb || !*img) return false;
+  const int64_t cnt = rows * gw;
+  if (cnt > 0)
+    k_f32_to_bf16<<<(int)std::min<int64_t>((cnt / 4 + 255) / 256, 148 * 8), 256, 0, st>>>(
+        in, cnt, static_cast<__nv_bfloat16*>(*xb));
+  cudaMemsetAsync(*img, 0, img_bytes, st);
+  k_pack_tw<<<(int)std::min<int64_t>(((int64_t)ko * gw * nout + 255) / 256, 148 * 4), 256, 0,
+              st>>>(W, cout, cin, mode, ko, gw, nout, static_cast<unsigned char*>(*img));
+  count_launches(2);
+  return true;
 }
 
 }  // namespace
@@ -388,23 +486,57 @@ int tconv_tc(const float* in, int64_t n, int cin, const int32_t* nbr, const floa
   if (n <= 0) return LPC_OK;
   const int gw = mirror ? 32 : cin;    // gathered row width
   const int nout = mirror ? cin : 32;  // output width
-  const int64_t rows_bytes = n * gw * 2;
-  const size_t img_bytes = (size_t)((27 * gw + 63) / 64) * nout * 128;
-  void* xb = grow(g_rows, (size_t)rows_bytes);
-  void* img = grow(g_img, img_bytes);
-  if (!xb || !img) return LPC_CUDA_ERROR;
-  const int64_t cnt = n * gw;
-  k_f32_to_bf16<<<(int)std::min<int64_t>((cnt / 4 + 255) / 256, 148 * 8), 256, 0, st>>>(
-      in, cnt, static_cast<__nv_bfloat16*>(xb));
-  cudaMemsetAsync(img, 0, img_bytes, st);
-  k_pack_tw<<<(int)std::min<int64_t>((27 * gw * nout + 255) / 256, 148 * 4), 256, 0, st>>>(
-      W, cin, mirror, nout, gw, static_cast<unsigned char*>(img));
-  count_launches(2);
+  void *xb, *img;
+  if (!stage_inputs(in, n, gw, W, 32, cin, mirror ? 1 : 0, 27, nout, &xb, &img, st))
+    return LPC_CUDA_ERROR;
   const TConvArgs a{static_cast<const __nv_bfloat16*>(xb), nbr, n,
-                    static_cast<const uint16_t*>(img), bias, out};
-  if (gw == 64) return launch<64, 32>(a, st);
-  if (nout == 64) return launch<32, 64>(a, st);
-  return launch<32, 32>(a, st);
+                    static_cast<const uint16_t*>(img), bias, out, nullptr, nullptr};
+  if (gw == 64) return launch<64, 32, 27, 0>(a, st);
+  if (nout == 64) return launch<32, 64, 27, 0>(a, st);
+  return launch<32, 32, 27, 0>(a, st);
+}
+
+// Parents from their eight child slots: the down-step forward (transpose 0:
+// child rows x [][cin] -> y [np][cout], bias [cout]) or the up-step's input
+// gradient (transpose 1: child rows dy [][cout] -> dx [np][cin]); W is
+// [8][cout][cin], off / ckey the parents' first children and the children's
+// keys (slot = ckey & 7).
+int tslot_tc(const float* in, int64_t np, int64_t nc, const uint32_t* off, const uint64_t* ckey,
+             const float* W, int cout, int cin, const float* bias, float* out, int transpose,
+             cudaStream_t st) {
+  if (np <= 0) return LPC_OK;
+  const int gw = transpose ? cout : cin, nout = transpose ? cin : cout;
+  if (gw != 32 || (nout != 32 && nout != 64)) return LPC_INVALID_ARG;
+  auto* smap = static_cast<int32_t*>(grow(g_smap, (size_t)np * 8 * 4));
+  void *xb, *img;
+  if (!smap || !stage_inputs(in, nc, gw, W, cout, cin, transpose ? 2 : 0, 8, nout, &xb, &img, st))
+    return LPC_CUDA_ERROR;
+  k_slot_map<<<(int)std::min<int64_t>((np + 255) / 256, 148 * 8), 256, 0, st>>>(off, ckey, np, smap);
+  count_launches(1);
+  const TConvArgs a{static_cast<const __nv_bfloat16*>(xb), smap, np,
+                    static_cast<const uint16_t*>(img), bias, out, nullptr, nullptr};
+  if (nout == 64) return launch<32, 64, 8, 0>(a, st);
+  return launch<32, 32, 8, 0>(a, st);
+}
+
+// Children from their parent's row: the up-step forward (transpose 0:
+// parent rows x [np][cin] -> y [children][cout], per-slot bias [8][cout])
+// or the down-step's input gradient (transpose 1: parent rows dy [np][cout]
+// -> dx [children][cin]).  One GEMM of every parent against all eight
+// slots' weights (N = 256), each child taking its slot's 32 columns.
+int texpand_tc(const float* in, int64_t np, const uint32_t* off, const uint64_t* ckey,
+               const float* W, int cout, int cin, const float* slot_bias, float* out,
+               int transpose, cudaStream_t st) {
+  if (np <= 0) return LPC_OK;
+  const int gw = transpose ? cout : cin, per_child = transpose ? cin : cout;
+  if (per_child != 32 || (gw != 32 && gw != 64)) return LPC_INVALID_ARG;
+  void *xb, *img;
+  if (!stage_inputs(in, np, gw, W, cout, cin, transpose ? 4 : 3, 1, 256, &xb, &img, st))
+    return LPC_CUDA_ERROR;
+  const TConvArgs a{static_cast<const __nv_bfloat16*>(xb), nullptr, np,
+                    static_cast<const uint16_t*>(img), slot_bias, out, off, ckey};
+  if (gw == 64) return launch<64, 256, 1, 1>(a, st);
+  return launch<32, 256, 1, 1>(a, st);
 }
 
 }  // namespace lpc

@@ -34,11 +34,11 @@ def _lib():
         sig = {
             "lpc_t_conv_fwd": [P_, I64, I32, P_, P_, P_, I32, P_, I32, C.c_uint64],
             "lpc_t_conv_bwd": [P_, P_, I64, I32, P_, P_, I32, P_, P_, P_, I32, C.c_uint64],
-            "lpc_t_up_fwd": [P_, I32, P_, P_, I64, P_, P_, I32, P_, I32, C.c_uint64],
+            "lpc_t_up_fwd": [P_, I64, I32, P_, P_, P_, I64, P_, P_, I32, P_, I32, C.c_uint64],
             "lpc_t_up_bwd": [P_, P_, I64, I32, P_, P_, P_, I64, P_, I32, P_, P_, P_, I32,
                              C.c_uint64],
-            "lpc_t_down_fwd": [P_, I32, P_, P_, I64, P_, P_, I32, P_, I32, C.c_uint64],
-            "lpc_t_down_bwd": [P_, P_, I64, I32, P_, P_, I64, P_, I32, P_, P_, P_, I32,
+            "lpc_t_down_fwd": [P_, I64, I32, P_, P_, I64, P_, P_, I32, P_, I32, C.c_uint64],
+            "lpc_t_down_bwd": [P_, P_, I64, I32, P_, P_, P_, I64, P_, I32, P_, P_, P_, I32,
                                C.c_uint64],
             "lpc_t_embed_fwd": [P_, I64, P_, I32, P_, C.c_uint64],
             "lpc_t_embed_bwd": [P_, I64, P_, I32, P_, C.c_uint64],
@@ -165,8 +165,8 @@ class UpFn(torch.autograd.Function):
         Nc = par.shape[0]
         y = torch.empty(Nc, W.shape[1], device=x.device, dtype=torch.float32)
         _flops("up fwd", 2.0 * Nc * x.shape[1] * W.shape[1])
-        _call("up fwd", _lib().lpc_t_up_fwd, _p(x), x.shape[1], _p(par), _p(ckey), Nc, _p(W),
-              _p(b), W.shape[1], _p(y), bf16, _st())
+        _call("up fwd", _lib().lpc_t_up_fwd, _p(x), x.shape[0], x.shape[1], _p(off), _p(par),
+              _p(ckey), Nc, _p(W), _p(b), W.shape[1], _p(y), bf16, _st())
         ctx.save_for_backward(x, par, ckey, off, W)
         ctx.bf16 = bf16
         return y
@@ -194,8 +194,8 @@ class DownFn(torch.autograd.Function):
         Np = off.shape[0] - 1
         y = torch.empty(Np, W.shape[1], device=x.device, dtype=torch.float32)
         _flops("down fwd", 2.0 * x.shape[0] * x.shape[1] * W.shape[1])
-        _call("down fwd", _lib().lpc_t_down_fwd, _p(x), x.shape[1], _p(off), _p(ckey), Np, _p(W),
-              _p(b), W.shape[1], _p(y), bf16, _st())
+        _call("down fwd", _lib().lpc_t_down_fwd, _p(x), x.shape[0], x.shape[1], _p(off),
+              _p(ckey), Np, _p(W), _p(b), W.shape[1], _p(y), bf16, _st())
         ctx.save_for_backward(x, par, ckey, off, W)
         ctx.bf16 = bf16
         return y
@@ -208,9 +208,9 @@ class DownFn(torch.autograd.Function):
         dW = torch.zeros_like(W)
         db = torch.zeros(W.shape[1], device=x.device, dtype=torch.float32)
         _flops("down bwd", 4.0 * x.shape[0] * x.shape[1] * W.shape[1])
-        _call("down bwd", _lib().lpc_t_down_bwd, _p(x), _p(dy), x.shape[0], x.shape[1], _p(par),
-              _p(ckey), off.shape[0] - 1, _p(W), W.shape[1], _p(dx), _p(dW), _p(db), ctx.bf16,
-              _st())
+        _call("down bwd", _lib().lpc_t_down_bwd, _p(x), _p(dy), x.shape[0], x.shape[1], _p(off),
+              _p(par), _p(ckey), off.shape[0] - 1, _p(W), W.shape[1], _p(dx), _p(dW), _p(db),
+              ctx.bf16, _st())
         return dx, None, None, None, dW, db, None
 
 

@@ -109,6 +109,7 @@ def test_up_fwd_bwd(frames, bf16):
     dbr = torch.zeros(8, 32, dtype=DT).index_add(0, ref.slot[d], dy.double())
     assert _rel(y, yr) < 1e-5
     assert _rel(dx, dxr) < 1e-5 and _rel(dW, dWr) < 1e-5 and _rel(db, dbr) < 1e-5
+    assert G.tc_error() == 0  # bf16: forward (all eight slots per parent) and dx on the tensor cores
 
 
 @pytest.mark.parametrize("bf16", [0, 1])
@@ -133,6 +134,7 @@ def test_down_fwd_bwd(frames, bf16):
     assert _rel(y, yr) < 1e-5
     assert _rel(dx, dxr) < 1e-5 and _rel(dW, dWr) < 1e-5
     assert _rel(db, dy.double().sum(0)) < 1e-5
+    assert G.tc_error() == 0  # bf16: forward (eight child slots per parent) and dx on the tensor cores
 
 
 @pytest.mark.parametrize("qat,bf16", [(0, 0), (1, 0), (0, 1), (1, 1)])
