@@ -338,6 +338,19 @@ int tslot_tc(const float* in, int64_t np, int64_t nc, const uint32_t* off, const
 int texpand_tc(const float* in, int64_t np, const uint32_t* off, const uint64_t* ckey,
                const float* W, int cout, int cin, const float* slot_bias, float* out,
                int transpose, cudaStream_t st);
+// Weight gradients in bf16 mode on tcgen05, accumulated into dW, each from
+// one gather that also gives the input gradient where dx is not null:
+// tconv_bwd_tc the conv (dW [27][32][cin], dx [n][cin] from dy [n][32]);
+// tup_bwd_tc the up-step (x [np][cin] parents, dy [nc][32] children; dW
+// [8][32][cin], dx [np][cin]); tdown_dw_tc the down-step's dW [8][cout][32]
+// (x [nc][32] children, dy [np][cout] parents).
+int tconv_bwd_tc(const float* x, const float* dy, int64_t n, int cin, const int32_t* nbr,
+                 const float* W, float* dx, float* dW, cudaStream_t st);
+int tup_bwd_tc(const float* x, const float* dy, int64_t np, int64_t nc, int cin,
+               const uint32_t* off, const uint64_t* ckey, const float* W, float* dx, float* dW,
+               cudaStream_t st);
+int tdown_dw_tc(const float* x, const float* dy, int64_t np, int64_t nc, int cout,
+                const uint32_t* off, const uint64_t* ckey, float* dW, cudaStream_t st);
 
 // Predictor + integer softmax + cumulative table.
 enum PredMode { kPredCdf = 0, kPredEnc = 1, kPredLogits = 2 };

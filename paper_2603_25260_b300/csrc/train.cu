@@ -194,72 +194,205 @@ k_outer(Pairs pairs, const float* __restrict__ dy, const float* __restrict__ x, 
       atomicAdd(dW + (size_t)s * A * B + (size_t)(ti + 16 * u) * B + tj + 16 * v, acc[u][v]);
 }
 
-// db[slice(row)][j] += dy[row][j]; slice_key = nullptr: one slice.
-__global__ void k_bias_grad(const float* __restrict__ dy, int64_t rows, int C,
-                            const uint64_t* __restrict__ slice_key, float* db) {
-  __shared__ float part[8 * 64];
-  for (int i = threadIdx.x; i < 8 * C; i += blockDim.x) part[i] = 0.f;
+// ---- embedding, PReLU, fake quantisation, bias gradients --------------------
+// Row kernels: one warp per row of C channels (lane l holds channels l,
+// l + 32, ..., at most kCh of them), kRowIlp rows in flight per warp.  No
+// per-element division; PReLU slopes and the per-channel gradient sums stay
+// in registers until one shared-memory reduction per block.
+constexpr int kCh = 8, kRowIlp = 4, kRowThreads = 256;
+
+struct RowWalk {  // the warp's rows r0, r0 + 1, ... r0 + kRowIlp - 1 per step
+  int64_t first, step;
+  __device__ RowWalk()
+      : first(((blockIdx.x * (int64_t)kRowThreads + threadIdx.x) >> 5) * kRowIlp),
+        step((((int64_t)gridDim.x * kRowThreads) >> 5) * kRowIlp) {}
+};
+
+__global__ void __launch_bounds__(kRowThreads)
+    k_embed_f(const uint8_t* __restrict__ codes, int64_t N, const float* __restrict__ E, int C,
+              float* __restrict__ y) {
+  const int lane = threadIdx.x & 31;
+  const RowWalk w;
+  for (int64_t r0 = w.first; r0 < N; r0 += w.step) {
+    int code[kRowIlp];
+#pragma unroll
+    for (int u = 0; u < kRowIlp; u++) code[u] = r0 + u < N ? codes[r0 + u] : 0;
+#pragma unroll
+    for (int u = 0; u < kRowIlp; u++) {
+      if (r0 + u >= N) break;
+      for (int j = lane; j < C; j += 32) y[(r0 + u) * C + j] = __ldg(E + code[u] * C + j);
+    }
+  }
+}
+
+// dE[code] += dy[row]: with acc_smem, into a block-private [256][C] table in
+// shared memory first (the codes of a level are few and skewed: global
+// atomics on them serialise), flushed once per block where non-zero.
+__global__ void __launch_bounds__(kRowThreads)
+    k_embed_b(const uint8_t* __restrict__ codes, int64_t N, const float* __restrict__ dy, int C,
+              float* dE, int acc_smem) {
+  extern __shared__ float tab[];
+  float* acc = acc_smem ? tab : dE;
+  if (acc_smem) {
+    for (int i = threadIdx.x; i < 256 * C; i += kRowThreads) tab[i] = 0.f;
+    __syncthreads();
+  }
+  const int lane = threadIdx.x & 31;
+  const RowWalk w;
+  for (int64_t r0 = w.first; r0 < N; r0 += w.step) {
+    int code[kRowIlp];
+#pragma unroll
+    for (int u = 0; u < kRowIlp; u++) code[u] = r0 + u < N ? codes[r0 + u] : 0;
+    for (int j = lane; j < C; j += 32) {
+      float g[kRowIlp];
+#pragma unroll
+      for (int u = 0; u < kRowIlp; u++) g[u] = r0 + u < N ? __ldg(dy + (r0 + u) * C + j) : 0.f;
+#pragma unroll
+      for (int u = 0; u < kRowIlp; u++)
+        if (r0 + u < N) atomicAdd(acc + code[u] * C + j, g[u]);
+    }
+  }
+  if (acc_smem) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < 256 * C; i += kRowThreads)
+      if (tab[i] != 0.f) atomicAdd(dE + i, tab[i]);
+  }
+}
+
+__global__ void __launch_bounds__(kRowThreads)
+    k_prelu_f(const float* __restrict__ x, int64_t N, int C, const float* __restrict__ a,
+              float* __restrict__ y) {
+  const int lane = threadIdx.x & 31;
+  float al[kCh];
+#pragma unroll
+  for (int k = 0; k < kCh; k++) al[k] = lane + 32 * k < C ? a[lane + 32 * k] : 0.f;
+  const RowWalk w;
+  for (int64_t r0 = w.first; r0 < N; r0 += w.step)
+#pragma unroll
+    for (int k = 0; k < kCh; k++) {
+      const int j = lane + 32 * k;
+      if (j >= C) break;
+      float v[kRowIlp];
+#pragma unroll
+      for (int u = 0; u < kRowIlp; u++) v[u] = r0 + u < N ? __ldg(x + (r0 + u) * C + j) : 0.f;
+#pragma unroll
+      for (int u = 0; u < kRowIlp; u++)
+        if (r0 + u < N) y[(r0 + u) * C + j] = v[u] >= 0.f ? v[u] : al[k] * v[u];
+    }
+}
+
+__global__ void __launch_bounds__(kRowThreads)
+    k_prelu_b(const float* __restrict__ x, const float* __restrict__ dy, int64_t N, int C,
+              const float* __restrict__ a, float* __restrict__ dx, float* da) {
+  __shared__ float part[32 * kCh];
+  for (int i = threadIdx.x; i < C; i += kRowThreads) part[i] = 0.f;
+  const int lane = threadIdx.x & 31;
+  float al[kCh], acc[kCh];
+#pragma unroll
+  for (int k = 0; k < kCh; k++) {
+    al[k] = lane + 32 * k < C ? a[lane + 32 * k] : 0.f;
+    acc[k] = 0.f;
+  }
+  const RowWalk w;
+  for (int64_t r0 = w.first; r0 < N; r0 += w.step)
+#pragma unroll
+    for (int k = 0; k < kCh; k++) {
+      const int j = lane + 32 * k;
+      if (j >= C) break;
+      float v[kRowIlp], g[kRowIlp];
+#pragma unroll
+      for (int u = 0; u < kRowIlp; u++) {
+        v[u] = r0 + u < N ? __ldg(x + (r0 + u) * C + j) : 0.f;
+        g[u] = r0 + u < N ? __ldg(dy + (r0 + u) * C + j) : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < kRowIlp; u++) {
+        if (r0 + u >= N) break;
+        if (dx) dx[(r0 + u) * C + j] = v[u] >= 0.f ? g[u] : al[k] * g[u];
+        if (v[u] < 0.f) acc[k] += g[u] * v[u];
+      }
+    }
   __syncthreads();
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < rows * C;
-       q += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = q / C;
-    const int j = (int)(q - r * C);
-    const int s = slice_key ? (int)(slice_key[r] & 7) : 0;
-    atomicAdd(&part[s * C + j], dy[q]);
+#pragma unroll
+  for (int k = 0; k < kCh; k++)
+    if (lane + 32 * k < C && acc[k] != 0.f) atomicAdd(&part[lane + 32 * k], acc[k]);
+  __syncthreads();
+  for (int i = threadIdx.x; i < C; i += kRowThreads)
+    if (part[i] != 0.f) atomicAdd(da + i, part[i]);
+}
+
+// db[slice(row)][j] += dy[row][j]; slice_key = nullptr: one slice (sums kept
+// in registers), else the child slot of the row's key (shared-memory sums:
+// one row per warp at a time, so the lanes' addresses differ).
+__global__ void __launch_bounds__(kRowThreads)
+    k_bias_grad(const float* __restrict__ dy, int64_t rows, int C,
+                const uint64_t* __restrict__ slice_key, float* db) {
+  __shared__ float part[8 * 32 * kCh];
+  const int ns = slice_key ? 8 : 1;
+  for (int i = threadIdx.x; i < ns * C; i += kRowThreads) part[i] = 0.f;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  float acc[kCh];
+#pragma unroll
+  for (int k = 0; k < kCh; k++) acc[k] = 0.f;
+  const RowWalk w;
+  for (int64_t r0 = w.first; r0 < rows; r0 += w.step) {
+    int s[kRowIlp];
+#pragma unroll
+    for (int u = 0; u < kRowIlp; u++)
+      s[u] = slice_key && r0 + u < rows ? (int)(slice_key[r0 + u] & 7) : 0;
+#pragma unroll
+    for (int k = 0; k < kCh; k++) {
+      const int j = lane + 32 * k;
+      if (j >= C) break;
+      float g[kRowIlp];
+#pragma unroll
+      for (int u = 0; u < kRowIlp; u++) g[u] = r0 + u < rows ? __ldg(dy + (r0 + u) * C + j) : 0.f;
+#pragma unroll
+      for (int u = 0; u < kRowIlp; u++) {
+        if (slice_key) atomicAdd(&part[s[u] * C + j], g[u]);
+        else acc[k] += g[u];
+      }
+    }
+  }
+  if (!slice_key) {
+#pragma unroll
+    for (int k = 0; k < kCh; k++)
+      if (lane + 32 * k < C && acc[k] != 0.f) atomicAdd(&part[lane + 32 * k], acc[k]);
   }
   __syncthreads();
-  const int ns = slice_key ? 8 : 1;
-  for (int i = threadIdx.x; i < ns * C; i += blockDim.x)
+  for (int i = threadIdx.x; i < ns * C; i += kRowThreads)
     if (part[i] != 0.f) atomicAdd(db + i, part[i]);
 }
 
-// ---- embedding, PReLU, fake quantisation -----------------------------------
-__global__ void k_embed_f(const uint8_t* codes, int64_t N, const float* E, int C, float* y) {
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < N * C;
-       q += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = q / C;
-    y[q] = E[codes[r] * C + (q - r * C)];
-  }
+// Elementwise kernels: four elements a thread (one 16-byte access) when
+// every pointer allows it, the tail and unaligned tensors one at a time.
+__device__ __forceinline__ float fq1(float v, float s, int z, uint8_t& m) {
+  const float r = rintf(v / s) + (float)z;
+  const float c = fminf(fmaxf(r, -128.f), 127.f);
+  m = r >= -128.f && r <= 127.f;
+  return (c - (float)z) * s;
 }
-__global__ void k_embed_b(const uint8_t* codes, int64_t N, const float* dy, int C, float* dE) {
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < N * C;
-       q += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = q / C;
-    atomicAdd(dE + codes[r] * C + (q - r * C), dy[q]);
+
+__global__ void k_fq_f(const float* __restrict__ x, int64_t n, float s, int z,
+                       float* __restrict__ y, uint8_t* __restrict__ mask, int vec) {
+  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
+                nt = (int64_t)gridDim.x * blockDim.x;
+  const int64_t n4 = vec ? n / 4 : 0;
+  for (int64_t q = t0; q < n4; q += nt) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(x) + q);
+    uchar4 m;
+    float4 o;
+    o.x = fq1(v.x, s, z, m.x);
+    o.y = fq1(v.y, s, z, m.y);
+    o.z = fq1(v.z, s, z, m.z);
+    o.w = fq1(v.w, s, z, m.w);
+    reinterpret_cast<float4*>(y)[q] = o;
+    reinterpret_cast<uchar4*>(mask)[q] = m;
   }
+  for (int64_t q = 4 * n4 + t0; q < n; q += nt) y[q] = fq1(x[q], s, z, mask[q]);
 }
-__global__ void k_prelu_f(const float* x, int64_t N, int C, const float* a, float* y) {
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < N * C;
-       q += (int64_t)gridDim.x * blockDim.x) {
-    const float v = x[q];
-    y[q] = v >= 0.f ? v : a[q % C] * v;
-  }
-}
-__global__ void k_prelu_b(const float* x, const float* dy, int64_t N, int C, const float* a,
-                          float* dx, float* da) {
-  __shared__ float part[256];
-  for (int i = threadIdx.x; i < C; i += blockDim.x) part[i] = 0.f;
-  __syncthreads();
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < N * C;
-       q += (int64_t)gridDim.x * blockDim.x) {
-    const int c = (int)(q % C);
-    const float v = x[q], g = dy[q];
-    if (dx) dx[q] = v >= 0.f ? g : a[c] * g;
-    if (v < 0.f) atomicAdd(&part[c], g * v);
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < C; i += blockDim.x)
-    if (part[i] != 0.f) atomicAdd(da + i, part[i]);
-}
-__global__ void k_fq_f(const float* x, int64_t n, float s, int z, float* y, uint8_t* mask) {
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
-       q += (int64_t)gridDim.x * blockDim.x) {
-    const float r = rintf(x[q] / s) + (float)z;
-    const float c = fminf(fmaxf(r, -128.f), 127.f);
-    y[q] = (c - (float)z) * s;
-    mask[q] = r >= -128.f && r <= 127.f;
-  }
-}
+
 // Weights: the symmetric per-tensor scale max|w| / 127 (at least 1e-12 / 127)
 // found on the device by one block, then the same rounding as k_fq_f with
 // z = 0; the scale is formed in double and rounded to float like a host-side
@@ -279,18 +412,30 @@ __global__ void __launch_bounds__(1024) k_fq_w(const float* w, int64_t n, float*
   }
   __syncthreads();
   const float s = (float)((double)fmaxf(red[0], 1e-12f) / 127.0);
-  for (int64_t q = threadIdx.x; q < n; q += blockDim.x) {
-    const float r = rintf(w[q] / s);
-    const float c = fminf(fmaxf(r, -128.f), 127.f);
-    y[q] = c * s;
-    mask[q] = r >= -128.f && r <= 127.f;
-  }
+  for (int64_t q = threadIdx.x; q < n; q += blockDim.x) y[q] = fq1(w[q], s, 0, mask[q]);
 }
 
-__global__ void k_fq_b(const float* dy, const uint8_t* mask, int64_t n, float* dx) {
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
-       q += (int64_t)gridDim.x * blockDim.x)
-    dx[q] = mask[q] ? dy[q] : 0.f;
+__global__ void k_fq_b(const float* __restrict__ dy, const uint8_t* __restrict__ mask, int64_t n,
+                       float* __restrict__ dx, int vec) {
+  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
+                nt = (int64_t)gridDim.x * blockDim.x;
+  const int64_t n4 = vec ? n / 4 : 0;
+  for (int64_t q = t0; q < n4; q += nt) {
+    const float4 g = __ldg(reinterpret_cast<const float4*>(dy) + q);
+    const uchar4 m = __ldg(reinterpret_cast<const uchar4*>(mask) + q);
+    reinterpret_cast<float4*>(dx)[q] =
+        make_float4(m.x ? g.x : 0.f, m.y ? g.y : 0.f, m.z ? g.z : 0.f, m.w ? g.w : 0.f);
+  }
+  for (int64_t q = 4 * n4 + t0; q < n; q += nt) dx[q] = mask[q] ? dy[q] : 0.f;
+}
+
+bool al16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+// blocks for the row kernels: kRowIlp rows a warp, at most 8 blocks an SM
+int rows_grid(int64_t rows, int max_blocks = 148 * 8) {
+  const int64_t warps = (rows + kRowIlp - 1) / kRowIlp;
+  return (int)std::max<int64_t>(
+      1, std::min<int64_t>((warps * 32 + kRowThreads - 1) / kRowThreads, max_blocks));
 }
 
 int grid_for(int64_t work, int threads = 256) {
@@ -334,7 +479,8 @@ int outer(Pairs p, int S, int A, int B, const float* dy, const float* x, int64_t
 int bias_grad(const float* dy, int64_t rows, int C, const uint64_t* slice_key, float* db,
               cudaStream_t st) {
   if (rows <= 0 || !db) return LPC_OK;
-  k_bias_grad<<<grid_for(rows * C), 256, 0, st>>>(dy, rows, C, slice_key, db);
+  if (C > 32 * kCh) return LPC_INVALID_ARG;
+  k_bias_grad<<<rows_grid(rows), kRowThreads, 0, st>>>(dy, rows, C, slice_key, db);
   count_launches(1);
   return cudaGetLastError() == cudaSuccess ? LPC_OK : LPC_CUDA_ERROR;
 }
@@ -363,6 +509,11 @@ int lpc_t_conv_bwd(const float* x, const float* dy, int64_t N, int cin, const in
   if (N < 0 || !ok_dims(cin, cout)) return LPC_INVALID_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   int s = LPC_OK;
+  if (bf16 && dW) {  // dW and dx from one gather of dy on the tensor cores
+    s = tconv_bwd_tc(x, dy, N, cin, nbr, W, dx, dW, st);
+    if (!s) s = bias_grad(dy, N, cout, nullptr, db, st);
+    return s;
+  }
   if (dx && bf16) s = tconv_tc(dy, N, cin, nbr, W, nullptr, dx, 1, st);
   else if (dx) s = gmv(ConvItems{nbr, 1}, W, 27, cin, cout, 1, nullptr, 0, dy, N, dx, bf16, st);
   if (!s) s = outer(ConvPairs{nbr}, 27, cout, cin, dy, x, N, dW, bf16, st);
@@ -386,6 +537,11 @@ int lpc_t_up_bwd(const float* x, const float* dy, int64_t Np, int cin, const uin
   if (Nc < 0 || Np < 0 || !ok_dims(cin, cout)) return LPC_INVALID_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   int s = LPC_OK;
+  if (bf16 && cout == 32 && dW && off) {  // dW and dx from one gather of the children's dy
+    s = tup_bwd_tc(x, dy, Np, Nc, cin, off, ckey, W, dx, dW, st);
+    if (!s) s = bias_grad(dy, Nc, cout, ckey, db, st);
+    return s;
+  }
   if (dx && bf16 && cout == 32)  // the parents' eight child slots on the tensor cores
     s = tslot_tc(dy, Np, Nc, off, ckey, W, cout, cin, nullptr, dx, 1, st);
   else if (dx)
@@ -416,7 +572,9 @@ int lpc_t_down_bwd(const float* x, const float* dy, int64_t Nc, int cin, const u
     s = texpand_tc(dy, Np, off, ckey, W, cout, cin, nullptr, dx, 1, st);
   else if (dx)
     s = gmv(UpFwdItems{par, ckey}, W, 8, cin, cout, 1, nullptr, 0, dy, Nc, dx, bf16, st);
-  if (!s) s = outer(DownPairs{par, ckey}, 8, cout, cin, dy, x, Nc, dW, bf16, st);
+  if (!s && bf16 && cin == 32 && off && dW)  // the children's x by slot against the parents' dy
+    s = tdown_dw_tc(x, dy, Np, Nc, cout, off, ckey, dW, st);
+  else if (!s) s = outer(DownPairs{par, ckey}, 8, cout, cin, dy, x, Nc, dW, bf16, st);
   if (!s) s = bias_grad(dy, Np, cout, nullptr, db, st);
   return s;
 }
@@ -425,8 +583,8 @@ int lpc_t_embed_fwd(const uint8_t* codes, int64_t N, const float* E, int C, floa
                     uint64_t stream) {
   if (N < 0 || C < 1) return LPC_INVALID_ARG;
   if (N == 0) return LPC_OK;
-  k_embed_f<<<grid_for(N * C), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(codes, N, E, C,
-                                                                                 y);
+  k_embed_f<<<rows_grid(N), kRowThreads, 0, reinterpret_cast<cudaStream_t>(stream)>>>(codes, N,
+                                                                                      E, C, y);
   count_launches(1);
   return cudaGetLastError() == cudaSuccess ? LPC_OK : LPC_CUDA_ERROR;
 }
@@ -435,8 +593,17 @@ int lpc_t_embed_bwd(const uint8_t* codes, int64_t N, const float* dy, int C, flo
                     uint64_t stream) {
   if (N < 0 || C < 1) return LPC_INVALID_ARG;
   if (N == 0) return LPC_OK;
-  k_embed_b<<<grid_for(N * C), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(codes, N, dy,
-                                                                                 C, dE);
+  // block-private tables in shared memory up to 64 channels (64 KB a block)
+  const int acc_smem = C <= 64;
+  const size_t smem = acc_smem ? sizeof(float) * 256 * C : 0;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_embed_b, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(sizeof(float) * 256 * 64));
+    attr = true;
+  }
+  k_embed_b<<<rows_grid(N, 148 * 2), kRowThreads, smem, reinterpret_cast<cudaStream_t>(stream)>>>(
+      codes, N, dy, C, dE, acc_smem);
   count_launches(1);
   return cudaGetLastError() == cudaSuccess ? LPC_OK : LPC_CUDA_ERROR;
 }
@@ -444,7 +611,8 @@ int lpc_t_embed_bwd(const uint8_t* codes, int64_t N, const float* dy, int C, flo
 int lpc_t_prelu_fwd(const float* x, int64_t N, int C, const float* a, float* y, uint64_t stream) {
   if (N < 0 || C < 1 || C > 256) return LPC_INVALID_ARG;
   if (N == 0) return LPC_OK;
-  k_prelu_f<<<grid_for(N * C), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(x, N, C, a, y);
+  k_prelu_f<<<rows_grid(N), kRowThreads, 0, reinterpret_cast<cudaStream_t>(stream)>>>(x, N, C, a,
+                                                                                      y);
   count_launches(1);
   return cudaGetLastError() == cudaSuccess ? LPC_OK : LPC_CUDA_ERROR;
 }
@@ -453,8 +621,8 @@ int lpc_t_prelu_bwd(const float* x, const float* dy, int64_t N, int C, const flo
                     float* da, uint64_t stream) {
   if (N < 0 || C < 1 || C > 256 || !da) return LPC_INVALID_ARG;
   if (N == 0) return LPC_OK;
-  k_prelu_b<<<grid_for(N * C), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(x, dy, N, C, a,
-                                                                                  dx, da);
+  k_prelu_b<<<rows_grid(N), kRowThreads, 0, reinterpret_cast<cudaStream_t>(stream)>>>(x, dy, N, C,
+                                                                                      a, dx, da);
   count_launches(1);
   return cudaGetLastError() == cudaSuccess ? LPC_OK : LPC_CUDA_ERROR;
 }
@@ -463,7 +631,9 @@ int lpc_t_fq_fwd(const float* x, int64_t n, float s, int z, float* y, uint8_t* m
                  uint64_t stream) {
   if (n < 0 || !(s > 0.f) || z < -128 || z > 127) return LPC_INVALID_ARG;
   if (n == 0) return LPC_OK;
-  k_fq_f<<<grid_for(n), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(x, n, s, z, y, mask);
+  const int vec = al16(x) && al16(y) && (reinterpret_cast<uintptr_t>(mask) & 3) == 0;
+  k_fq_f<<<grid_for(vec ? (n + 3) / 4 : n), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+      x, n, s, z, y, mask, vec);
   count_launches(1);
   return cudaGetLastError() == cudaSuccess ? LPC_OK : LPC_CUDA_ERROR;
 }
@@ -479,7 +649,9 @@ int lpc_t_fq_w(const float* w, int64_t n, float* y, uint8_t* mask, uint64_t stre
 int lpc_t_fq_bwd(const float* dy, const uint8_t* mask, int64_t n, float* dx, uint64_t stream) {
   if (n < 0) return LPC_INVALID_ARG;
   if (n == 0) return LPC_OK;
-  k_fq_b<<<grid_for(n), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(dy, mask, n, dx);
+  const int vec = al16(dy) && al16(dx) && (reinterpret_cast<uintptr_t>(mask) & 3) == 0;
+  k_fq_b<<<grid_for(vec ? (n + 3) / 4 : n), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+      dy, mask, n, dx, vec);
   count_launches(1);
   return cudaGetLastError() == cudaSuccess ? LPC_OK : LPC_CUDA_ERROR;
 }

@@ -367,6 +367,341 @@ __global__ void __launch_bounds__(kThr, 1) k_tconv_tc(TConvArgs a) {
   if (t == 0 && abort_flag) atomicExch(&g_tconv_error, 1);
 }
 
+// ---- backward: weight gradients, and input gradients from the same gather ---
+// dW[o] = sum over rows m of G_o[m]^T Y[m] for every offset o, G_o[m] the
+// gathered 32-wide bf16 row of offset o (zero where absent), Y[m] the row's
+// own NY-wide bf16 row:
+//  - conv: G_o[m] = dy[nbr[m][o]], Y = x, into dW[26 - o][co][ci] (the kernel
+//    map is symmetric: nbr[m][o] = r exactly when nbr[r][26 - o] = m);
+//  - up-step: rows are parents, G_s[p] = dy[p's child in slot s], Y = x, into
+//    dW[s][co][ci];
+//  - down-step: rows are parents, G_s[p] = x[p's child in slot s], Y = dy,
+//    into dW[s][co][ci] (the gathered channel is ci).
+// Four offsets' stages lie side by side in shared memory, so an MN-major
+// descriptor reads them as the A operand of one MMA (M = 4 offsets x 32
+// channels) per 16 rows against the MN-major Y tile (N = NY); every
+// offset's accumulator stays in tensor memory across the CTA's tiles and is
+// added into dW once at the end.  With DX the same stages also give the
+// input gradient as in k_tconv_tc (K-major A, the weight image as B), so the
+// conv's and the up-step's dx and dW share one gather.
+template <int NY, int KO, bool DX>
+struct BCfg {
+  static constexpr int RB = 64;  // gathered rows: 32 bf16, 64-byte swizzle
+  static constexpr int G = 4;    // offsets a pipeline step: one 128-row M group
+  static constexpr int kSteps = (KO + G - 1) / G;
+  static constexpr int kStageBytes = kTM * RB;
+  static constexpr int SG = (NY == 64 && KO == 27 && DX) ? 2 : 3;  // ring depth in steps
+  static constexpr int YRB = NY * 2, YSW = NY == 64 ? 128 : 64;
+  static constexpr int kYBytes = kTM * YRB;
+  static constexpr int kBBlocks = DX ? (KO * 32 + 63) / 64 : 0;
+  static constexpr int kBBlockBytes = NY * 128;
+  static constexpr int kBBytes = kBBlocks * kBBlockBytes;
+  static constexpr int kNbrBufs = (NY == 64 && KO == 27 && DX) ? 1 : 2;
+  static constexpr int kNbrBytes = kTM * KO * 4;
+  static constexpr int kDwCols = kSteps * NY;
+  static constexpr int kDxBufs = DX ? (kDwCols + 2 * NY <= 512 ? 2 : 1) : 0;
+  static constexpr int kNeed = kDwCols + kDxBufs * NY;
+  static constexpr int kTmemCols =
+      kNeed <= 64 ? 64 : (kNeed <= 128 ? 128 : (kNeed <= 256 ? 256 : 512));
+  static constexpr size_t kSmem = 1024 + kBBytes + (size_t)SG * G * kStageBytes + 2 * kYBytes +
+                                  (size_t)kNbrBufs * kNbrBytes;
+  static_assert(kNeed <= 512, "tensor memory of a backward variant exceeds 512 columns");
+  static_assert(kSmem <= 232448 - 512, "shared memory of a backward variant exceeds the limit");
+  static_assert(kTM * 4 == 2 * kProd && kTM * (YRB / 16) % kProd == 0, "copies split evenly");
+};
+
+struct TBwdArgs {
+  const __nv_bfloat16* gb;  // gathered rows [][32], bf16
+  const __nv_bfloat16* yb;  // the rows' own [n][NY], bf16
+  const int32_t* map;       // [n][KO]: the gathered row of each offset, -1 absent
+  int64_t n;
+  const uint16_t* wimg;     // DX: weight image of the input gradient
+  float* dx;                // DX: [n][NY]
+  float* dw;                // [KO][32][NY] (trans) or [KO][NY][32], accumulated into
+  int mirror;               // dW slice KO - 1 - o instead of o
+  int trans;                // the gathered channel indexes W's rows (else its columns)
+  int vec4;                 // dw is 16-byte aligned
+};
+
+template <int NY, int KO, bool DX>
+__global__ void __launch_bounds__(kThr, 1) k_tbwd_tc(TBwdArgs a) {
+  using Cfg = BCfg<NY, KO, DX>;
+  constexpr int G = Cfg::G, SG = Cfg::SG, NB = Cfg::kNbrBufs, KS = Cfg::kSteps;
+  constexpr int XB = Cfg::kDxBufs > 0 ? Cfg::kDxBufs : 1;
+  extern __shared__ unsigned char smraw[];
+  unsigned char* sm = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
+  // ring first, the Y tiles right after it, then the weight image and maps
+  unsigned char* sA = sm;
+  unsigned char* sY = sA + (size_t)SG * G * Cfg::kStageBytes;
+  unsigned char* sB = sY + 2 * Cfg::kYBytes;
+  int32_t* sNbr0 = reinterpret_cast<int32_t*>(sB + Cfg::kBBytes);
+  __shared__ uint64_t full_bar[SG], empty_bar[SG], acc_full[2], acc_empty[2], y_full[2],
+      y_empty[2], dw_bar, drain_bar, w_bar, nbr_bar[2];
+  __shared__ uint32_t tslot;
+  __shared__ int abort_flag;
+  volatile int* abort = &abort_flag;
+
+  const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+  if (w == kMmaW) tc::tmem_alloc(&tslot, Cfg::kTmemCols);
+  if (t == 0) {
+    for (int s = 0; s < SG; s++) {
+      tc::mbar_init(&full_bar[s], kProd);
+      tc::mbar_init(&empty_bar[s], 1);
+    }
+    for (int b = 0; b < 2; b++) {
+      tc::mbar_init(&acc_full[b], 1);
+      tc::mbar_init(&acc_empty[b], kEpi);
+      tc::mbar_init(&y_full[b], kProd);
+      tc::mbar_init(&y_empty[b], 1);
+      tc::mbar_init(&nbr_bar[b], 1);
+    }
+    tc::mbar_init(&dw_bar, 1);
+    tc::mbar_init(&drain_bar, 1);
+    tc::mbar_init(&w_bar, 1);
+    tc::fence_mbar_init();
+    abort_flag = 0;
+    if (DX) {
+      mbar_expect(&w_bar, Cfg::kBBytes);
+      for (int off = 0; off < Cfg::kBBytes; off += 16384)
+        bulk_g2s(sB + off, reinterpret_cast<const unsigned char*>(a.wimg) + off,
+                 (uint32_t)min(16384, Cfg::kBBytes - off), &w_bar);
+    }
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tbase = tslot;
+  const int64_t n = a.n;
+  const int64_t ntiles = (n + kTM - 1) / kTM;
+  const int my_tiles = blockIdx.x < ntiles ? (int)((ntiles - 1 - blockIdx.x) / gridDim.x + 1) : 0;
+  auto tile_r0 = [&](int lt) { return ((int64_t)blockIdx.x + (int64_t)lt * gridDim.x) * kTM; };
+
+  if (w < kPWarps) {
+    // ---------------------------------------------------------- producers --
+    int last_issued = -1, last_used = -1;
+    auto issue_nbr = [&](int lt) {
+      if (t == 0 && lt < my_tiles && tile_r0(lt) + kTM <= n) {
+        last_issued = lt;
+        tc::fence_async_smem();
+        uint64_t* bar = &nbr_bar[lt % NB];
+        mbar_expect(bar, Cfg::kNbrBytes);
+        bulk_g2s(sNbr0 + (lt % NB) * kTM * KO, a.map + tile_r0(lt) * KO, Cfg::kNbrBytes, bar);
+      }
+    };
+    issue_nbr(0);
+    constexpr int kPer = kTM * 4 / kProd;             // gathered copies a thread, per offset
+    constexpr int kYPer = kTM * (Cfg::YRB / 16) / kProd;  // Y copies a thread, per tile
+    int prow[kPer];
+    uint32_t pdst[kPer];
+    const unsigned char* psrc[kPer];
+#pragma unroll
+    for (int k = 0; k < kPer; k++) {
+      const int q = t + k * kProd;
+      prow[k] = q >> 2;
+      pdst[k] = tc::swz<64>(prow[k] * 64 + (q & 3) * 16);
+      psrc[k] = reinterpret_cast<const unsigned char*>(a.gb) + (q & 3) * 16;
+    }
+    uint32_t u = 0;
+    for (int lt = 0; lt < my_tiles; lt++) {
+      const int64_t r0 = tile_r0(lt);
+      int32_t* sNbr = sNbr0 + (lt % NB) * kTM * KO;
+      if (producer_sync_or(*abort != 0)) break;
+      // the tile's own rows (zero past the end)
+      const int yb = lt & 1;
+      if (lt < 2 || wait_or_abort(&y_empty[yb], ((lt >> 1) - 1) & 1, abort)) {
+        const uint32_t ybase = tc::smem_u32(sY + (size_t)yb * Cfg::kYBytes);
+#pragma unroll
+        for (int k = 0; k < kYPer; k++) {
+          const int q = t + k * kProd;
+          const int row = q / (Cfg::YRB / 16), c = q % (Cfg::YRB / 16);
+          const bool in = r0 + row < n;
+          tc::cp_async16(ybase + tc::swz<Cfg::YSW>(row * Cfg::YRB + c * 16),
+                         reinterpret_cast<const unsigned char*>(a.yb) +
+                             (in ? (r0 + row) * Cfg::YRB : 0) + c * 16,
+                         in);
+        }
+      }
+      asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(
+                       tc::smem_u32(&y_full[yb]))
+                   : "memory");
+      if (NB == 2) issue_nbr(lt + 1);
+      else if (lt > 0) issue_nbr(lt);
+      if (r0 + kTM <= n) {
+        if (producer_sync_or(!wait_or_abort(&nbr_bar[lt % NB], (lt / NB) & 1, abort))) break;
+        last_used = lt;
+      } else {
+        const int64_t base = r0 * KO, lim = n * KO;
+        for (int i = t; i < kTM * KO; i += kProd)
+          sNbr[i] = base + i < lim ? __ldg(a.map + base + i) : -1;
+        producer_sync_or(false);
+      }
+      for (int st = 0; st < KS; st++, u++) {
+        const int sg = (int)(u % SG);
+        if (u >= (uint32_t)SG && !wait_or_abort(&empty_bar[sg], ((u / SG) - 1) & 1, abort))
+          break;
+#pragma unroll
+        for (int i = 0; i < G; i++) {
+          const int o = st * G + i;
+          if (o >= KO) break;  // a padding offset: its M rows are never read out
+          const uint32_t sbase = tc::smem_u32(sA + (size_t)(sg * G + i) * Cfg::kStageBytes);
+#pragma unroll
+          for (int k = 0; k < kPer; k++) {
+            const int32_t nb = sNbr[prow[k] * KO + o];
+            const uint32_t r = (uint32_t)max(nb, 0);
+            tc::cp_async16(sbase + pdst[k], psrc[k] + (size_t)r * 64, nb >= 0);
+          }
+        }
+        asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(
+                         tc::smem_u32(&full_bar[sg]))
+                     : "memory");
+      }
+    }
+    if (t == 0 && last_issued > last_used)
+      tc::mbar_wait(&nbr_bar[last_issued % NB], (last_issued / NB) & 1);
+    tc::cp_async_wait<0>();
+  } else if (w == kMmaW) {
+    // ---------------------------------------------------------------- MMA --
+    if (lane == 0) {
+      constexpr uint32_t idesc_dx = tc::idesc_bf16(kTM, NY);
+      constexpr uint32_t idesc_dw = tc::idesc_bf16_mn(kTM, NY);
+      constexpr uint32_t ysbo = 8 * Cfg::YRB;  // 8 rows of Y
+      uint32_t u = 0;
+      bool ok = DX ? wait_or_abort(&w_bar, 0, abort) : true;
+      for (int lt = 0; lt < my_tiles && ok && !*abort; lt++) {
+        const int yb = lt & 1, b = DX ? lt % XB : 0;
+        if (!wait_or_abort(&y_full[yb], (lt >> 1) & 1, abort)) break;
+        if (DX && lt >= XB && !wait_or_abort(&acc_empty[b], ((lt / XB) - 1) & 1, abort)) break;
+        tc::tc_fence_after();
+        const uint32_t ya = tc::smem_u32(sY + (size_t)yb * Cfg::kYBytes);
+        const uint32_t dxacc = tbase + (uint32_t)(Cfg::kDwCols + b * NY);
+        for (int st = 0; st < KS; st++, u++) {
+          const int sg = (int)(u % SG);
+          if (!wait_or_abort(&full_bar[sg], (u / SG) & 1, abort)) {
+            ok = false;
+            break;
+          }
+          tc::fence_async_smem();
+          tc::tc_fence_after();
+          const uint32_t s0 = tc::smem_u32(sA + (size_t)sg * G * Cfg::kStageBytes);
+          if (DX) {
+#pragma unroll
+            for (int i = 0; i < G; i++) {
+              const int o = st * G + i;
+              if (o >= KO) break;
+#pragma unroll
+              for (int ks = 0; ks < 2; ks++) {
+                const int k0 = o * 32 + ks * 16;
+                const uint32_t sb =
+                    tc::smem_u32(sB) + (k0 / 64) * Cfg::kBBlockBytes + (k0 % 64) * 2;
+                tc::mma_bf16(dxacc,
+                             tc::smem_desc<64>(s0 + i * Cfg::kStageBytes + ks * 32, 8 * 64),
+                             tc::smem_desc<128>(sb, 1024), idesc_dx, (o > 0 || ks > 0) ? 1u : 0u);
+              }
+            }
+          }
+          // dW: the step's four stages (M = 4 x 32, MN-major, atoms one stage
+          // apart) against the tile's Y rows, 16 rows an MMA
+#pragma unroll
+          for (int ks = 0; ks < kTM / 16; ks++)
+            tc::mma_bf16(tbase + (uint32_t)(st * NY),
+                         tc::smem_desc_mn<64>(s0 + ks * 2 * 8 * 64, Cfg::kStageBytes, 8 * 64),
+                         tc::smem_desc_mn<Cfg::YSW>(ya + ks * 2 * ysbo, ysbo, ysbo), idesc_dw,
+                         (lt > 0 || ks > 0) ? 1u : 0u);
+          tc::mma_commit(&empty_bar[sg]);
+        }
+        if (!ok) break;
+        tc::mma_commit(&y_empty[yb]);
+        if (DX) tc::mma_commit(&acc_full[b]);
+      }
+      tc::mma_commit(&dw_bar);
+      tc::mma_commit(&drain_bar);
+      if (!tc::mbar_wait(&drain_bar, 0)) *abort = 1;
+    }
+    __syncwarp();
+  } else {
+    // ----------------------------------------------------------- epilogue --
+    const int e = t - kProd;
+    const uint32_t lane_off = (uint32_t)((w & 3) * 32) << 16;
+    bool live = true;
+    if (DX) {
+      for (int lt = 0; lt < my_tiles; lt++) {
+        const int b = lt % XB;
+        if (!__all_sync(0xffffffffu, wait_or_abort(&acc_full[b], (lt / XB) & 1, abort))) {
+          live = false;
+          break;
+        }
+        tc::tc_fence_after();
+        uint32_t raw[NY / 16][16];
+        const uint32_t dbase = tbase + lane_off + (uint32_t)(Cfg::kDwCols + b * NY);
+#pragma unroll
+        for (int g = 0; g < NY / 16; g++) tc::tmem_ld16_issue(dbase + g * 16, raw[g]);
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int g = 0; g < NY / 16; g++) tc::tmem_regs_ready(raw[g]);
+        tc::tc_fence_before();
+        mbar_arrive(&acc_empty[b]);
+        const int64_t r = tile_r0(lt) + e;
+        if (r < n) {
+          float4* dst = reinterpret_cast<float4*>(a.dx + r * NY);
+#pragma unroll
+          for (int c = 0; c < NY; c += 4)
+            dst[c / 4] = make_float4(__uint_as_float(raw[c / 16][c % 16]),
+                                     __uint_as_float(raw[c / 16][c % 16 + 1]),
+                                     __uint_as_float(raw[c / 16][c % 16 + 2]),
+                                     __uint_as_float(raw[c / 16][c % 16 + 3]));
+        }
+      }
+    }
+    // dW: the warp's 32 TMEM lanes are offset 4 g + (w & 3) of group g, one
+    // lane per gathered channel
+    if (live && my_tiles > 0 &&
+        __all_sync(0xffffffffu, wait_or_abort(&dw_bar, 0, abort)) && !*abort) {
+      tc::tc_fence_after();
+      const int q = w & 3;
+#pragma unroll 1
+      for (int g = 0; g < KS; g++) {
+        const int o = g * G + q;
+        if (o >= KO) break;
+        uint32_t raw[NY / 16][16];
+        const uint32_t dbase = tbase + lane_off + (uint32_t)(g * NY);
+#pragma unroll
+        for (int h = 0; h < NY / 16; h++) tc::tmem_ld16_issue(dbase + h * 16, raw[h]);
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int h = 0; h < NY / 16; h++) tc::tmem_regs_ready(raw[h]);
+        const int so = a.mirror ? KO - 1 - o : o;
+        if (a.trans) {
+          float* dst = a.dw + ((size_t)so * 32 + lane) * NY;
+          if (a.vec4) {
+#pragma unroll
+            for (int c = 0; c < NY; c += 4)
+              atomicAdd(reinterpret_cast<float4*>(dst + c),
+                        make_float4(__uint_as_float(raw[c / 16][c % 16]),
+                                    __uint_as_float(raw[c / 16][c % 16 + 1]),
+                                    __uint_as_float(raw[c / 16][c % 16 + 2]),
+                                    __uint_as_float(raw[c / 16][c % 16 + 3])));
+          } else {
+#pragma unroll
+            for (int c = 0; c < NY; c++) atomicAdd(dst + c, __uint_as_float(raw[c / 16][c % 16]));
+          }
+        } else {
+          float* dst = a.dw + (size_t)so * NY * 32 + lane;
+#pragma unroll
+          for (int c = 0; c < NY; c++)
+            atomicAdd(dst + (size_t)c * 32, __uint_as_float(raw[c / 16][c % 16]));
+        }
+      }
+    }
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  if (DX && t == kThr - 32) tc::mbar_wait(&w_bar, 0);
+  if (w == kMmaW) tc::tmem_dealloc(tbase, Cfg::kTmemCols);
+  if (t == 0 && abort_flag) atomicExch(&g_tconv_error, 1);
+}
+
 // float rows -> bf16 rows (round to nearest even), n x cols
 __global__ void k_f32_to_bf16(const float* __restrict__ x, int64_t count, __nv_bfloat16* out) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count / 4;
@@ -477,7 +812,108 @@ bool stage_inputs(const float* in, int64_t rows, int gw, const float* W, int cou
   return true;
 }
 
+template <int NY, int KO, bool DX>
+int launch_bwd(const TBwdArgs& a, cudaStream_t st) {
+  using Cfg = BCfg<NY, KO, DX>;
+  const int64_t ntiles = (a.n + kTM - 1) / kTM;
+  const int blocks = (int)std::min<int64_t>(ntiles, 148);
+  auto* k = k_tbwd_tc<NY, KO, DX>;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::kSmem);
+  k<<<blocks, kThr, Cfg::kSmem, st>>>(a);
+  count_launches(1);
+  return cudaGetLastError() == cudaSuccess ? LPC_OK : LPC_CUDA_ERROR;
+}
+
+Scratch g_rows_y;
+
+// cnt floats (a multiple of 4) as bf16 in scratch s, or null
+void* bf16_copy(Scratch& s, const float* in, int64_t cnt, cudaStream_t st) {
+  void* p = grow(s, (size_t)std::max<int64_t>(cnt * 2, 16));
+  if (p && cnt > 0) {
+    k_f32_to_bf16<<<(int)std::min<int64_t>((cnt / 4 + 255) / 256, 148 * 8), 256, 0, st>>>(
+        in, cnt, static_cast<__nv_bfloat16*>(p));
+    count_launches(1);
+  }
+  return p;
+}
+
+// dW (and dx when given) of one sparse op from one gather: gsrc [gn][32] the
+// gathered rows, ysrc [n][ny] the rows' own, map [n][ko]; the weight image
+// of dx from W [ko][cout][cin] in k_pack_tw's mode wmode.
+int tbwd(const float* gsrc, int64_t gn, const float* ysrc, int64_t n, int ny, const int32_t* map,
+         int ko, const float* W, int cout, int cin, int wmode, float* dx, float* dW, int mirror,
+         int trans, cudaStream_t st) {
+  if (n <= 0) return LPC_OK;
+  void* gb = bf16_copy(g_rows, gsrc, gn * 32, st);
+  void* yb = bf16_copy(g_rows_y, ysrc, n * ny, st);
+  if (!gb || !yb) return LPC_CUDA_ERROR;
+  void* img = nullptr;
+  if (dx) {
+    const size_t img_bytes = (size_t)((ko * 32 + 63) / 64) * ny * 128;
+    img = grow(g_img, img_bytes);
+    if (!img) return LPC_CUDA_ERROR;
+    cudaMemsetAsync(img, 0, img_bytes, st);
+    k_pack_tw<<<(int)std::min<int64_t>(((int64_t)ko * 32 * ny + 255) / 256, 148 * 4), 256, 0,
+                st>>>(W, cout, cin, wmode, ko, 32, ny, static_cast<unsigned char*>(img));
+    count_launches(1);
+  }
+  const TBwdArgs a{static_cast<const __nv_bfloat16*>(gb), static_cast<const __nv_bfloat16*>(yb),
+                   map, n, static_cast<const uint16_t*>(img), dx, dW, mirror, trans,
+                   (reinterpret_cast<uintptr_t>(dW) & 15) == 0};
+#define LPC_BWD(NY_, KO_)                                                 \
+  if (ny == NY_ && ko == KO_)                                             \
+    return dx ? launch_bwd<NY_, KO_, true>(a, st) : launch_bwd<NY_, KO_, false>(a, st);
+  LPC_BWD(32, 27)
+  LPC_BWD(64, 27)
+  LPC_BWD(32, 8)
+  LPC_BWD(64, 8)
+#undef LPC_BWD
+  return LPC_INVALID_ARG;
+}
+
+// the parents' slot map [np][8] in scratch, or null
+int32_t* slot_map(const uint32_t* off, const uint64_t* ckey, int64_t np, cudaStream_t st) {
+  auto* smap = static_cast<int32_t*>(grow(g_smap, (size_t)np * 8 * 4));
+  if (smap) {
+    k_slot_map<<<(int)std::min<int64_t>((np + 255) / 256, 148 * 8), 256, 0, st>>>(off, ckey, np,
+                                                                                   smap);
+    count_launches(1);
+  }
+  return smap;
+}
+
 }  // namespace
+
+// The conv's backward in bf16 mode: dW [27][32][cin] (accumulated) and, with
+// dx, dx [n][cin], from one gather of the rounded dy rows.
+int tconv_bwd_tc(const float* x, const float* dy, int64_t n, int cin, const int32_t* nbr,
+                 const float* W, float* dx, float* dW, cudaStream_t st) {
+  if (cin != 32 && cin != 64) return LPC_INVALID_ARG;
+  return tbwd(dy, n, x, n, cin, nbr, 27, W, 32, cin, 1, dx, dW, 1, 1, st);
+}
+
+// The up-step's backward in bf16 mode (cout 32): dW [8][32][cin] and, with
+// dx, the parents' dx [np][cin], from one gather of the children's dy by slot.
+int tup_bwd_tc(const float* x, const float* dy, int64_t np, int64_t nc, int cin,
+               const uint32_t* off, const uint64_t* ckey, const float* W, float* dx, float* dW,
+               cudaStream_t st) {
+  if (np <= 0) return LPC_OK;
+  if (cin != 32 && cin != 64) return LPC_INVALID_ARG;
+  int32_t* smap = slot_map(off, ckey, np, st);
+  if (!smap) return LPC_CUDA_ERROR;
+  return tbwd(dy, nc, x, np, cin, smap, 8, W, 32, cin, 2, dx, dW, 0, 1, st);
+}
+
+// The down-step's weight gradient in bf16 mode (cin 32): dW [8][cout][32]
+// from the children's x gathered by slot against the parents' dy.
+int tdown_dw_tc(const float* x, const float* dy, int64_t np, int64_t nc, int cout,
+                const uint32_t* off, const uint64_t* ckey, float* dW, cudaStream_t st) {
+  if (np <= 0) return LPC_OK;
+  if (cout != 32 && cout != 64) return LPC_INVALID_ARG;
+  int32_t* smap = slot_map(off, ckey, np, st);
+  if (!smap) return LPC_CUDA_ERROR;
+  return tbwd(x, nc, dy, np, cout, smap, 8, nullptr, cout, 32, 0, nullptr, dW, 0, 0, st);
+}
 
 // bf16-mode forward (mirror 0: x [n][cin] -> y [n][32]) or input gradient
 // (mirror 1: dy [n][32] -> dx [n][cin]) of the 3x3x3 conv on tcgen05.
