@@ -105,6 +105,16 @@ int lpc_up_prune(const uint64_t* d_pkeys, const uint8_t* d_codes, int64_t Np,
                  const uint64_t* d_ckeys, int64_t Nc, const int8_t* d_x, int cin, int z_in,
                  const int8_t* h_W, const int32_t* h_bias, const int32_t* h_mult, int shift,
                  const int16_t* h_slope, int z_out, int cout, int8_t* d_out, uint64_t stream);
+/* The same with an explicit kernel variant: 0 CUDA cores (one warp per
+ * child, dp4a; what lpc_up_prune runs), 1 tensor cores (each parent row
+ * times all eight slots' weights in bf16 MMAs with fp32 accumulators, exact
+ * for these magnitudes, then the present children's rows; LPC_TIMEOUT if a
+ * bounded wait gave up).  Both give the same bytes. */
+int lpc_up_prune_variant(const uint64_t* d_pkeys, const uint8_t* d_codes, int64_t Np,
+                         const uint64_t* d_ckeys, int64_t Nc, const int8_t* d_x, int cin,
+                         int z_in, const int8_t* h_W, const int32_t* h_bias,
+                         const int32_t* h_mult, int shift, const int16_t* h_slope, int z_out,
+                         int cout, int8_t* d_out, int variant, uint64_t stream);
 
 /* Integer softmax to cumulative table (Eq. 15): d_logits int8 [N][255],
  * h_lut u32 [256] (lut[0] = 2^16, non-increasing) -> d_cdf u16 [N][256] in

@@ -561,6 +561,7 @@ void Codec::begin_batch() {
 int Codec::check_device_error() {
   if (conv_tc_error(true)) return fail(LPC_TIMEOUT, "tensor-core conv gave up on a bounded wait");
   if (pred_tc_error(true)) return fail(LPC_TIMEOUT, "tensor-core predictor gave up on a bounded wait");
+  if (up_tc_error(true)) return fail(LPC_TIMEOUT, "tensor-core up-step gave up on a bounded wait");
   const int e = *h_err_;
   if (e == 0) return LPC_OK;
   if (e == kErrCoord) return fail(LPC_INVALID_ARG, "coordinate outside [0, 2^L)");
@@ -649,9 +650,44 @@ void Codec::embed(const DEmb& E, int h, int8_t* out, int stride, int col) {
 // rows' columns [oe_col, oe_col + 32) also get E[Y] of their codes
 void Codec::up(const DLayer& W, int h, const int8_t* x, int xs, int8_t* out, int os, EmbSrc oe,
                int oe_col) {
+  const int ci = W.cin == 64 ? 1 : 0;
+  auto go = [&](int v) {
+    if (v == 1 && W.Wtc) {
+      UpTcArgs a{W.cin,  W.z_in, W.prelu, W.shift, W.z_out, W.mult_hi != nullptr, W.Wtc, W.bias,
+                 W.mult_hi ? W.mult_hi : W.mult, W.slope, x,
+                 xs,     d_N_ + h, off_[h], code_[h], out,  os,    0,      oe,     oe_col};
+      launch_up_tc(a, gridn(h), st_);
+    } else {
+      launch_up_prune(W, key_[h - 1], par_[h - 1], d_N_ + h - 1, gridn(h - 1), x, xs, out, os, 0,
+                      st_, oe, oe_col);
+    }
+  };
+  if (up_variant_[ci] < 0 && !cap_grid_) {
+    // autotuner, as the predictor's: both variants on this launch's input
+    // (same output), warm once, best of three interleaved timed rounds
+    for (int v = 0; v < kUpVariants; v++) {
+      go(v);
+      up_tune_ms_[ci][v] = 1e30f;
+    }
+    for (int rd = 0; rd < 3; rd++)
+      for (int v = 0; v < kUpVariants; v++) {
+        cudaEventRecord(tev_[0], st_);
+        go(v);
+        cudaEventRecord(tev_[1], st_);
+        float ms = 1e30f;
+        if (cudaEventSynchronize(tev_[1]) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, tev_[0], tev_[1]) != cudaSuccess) {
+          cudaGetLastError();
+          ms = 1e30f;
+        }
+        up_tune_ms_[ci][v] = std::min(up_tune_ms_[ci][v], ms);
+      }
+    up_variant_[ci] = 0;
+    for (int v = 1; v < kUpVariants; v++)
+      if (W.Wtc && up_tune_ms_[ci][v] < up_tune_ms_[ci][up_variant_[ci]]) up_variant_[ci] = v;
+  }
   pbeg(kFamUp);
-  launch_up_prune(W, key_[h - 1], par_[h - 1], d_N_ + h - 1, gridn(h - 1), x, xs, out, os, 0,
-                  st_, oe, oe_col);
+  go(up_variant_[ci] < 0 ? 0 : up_variant_[ci]);
   pend(kFamUp, (double)W.cin * N_[h] + 32.0 * N_[h - 1] + 8.0 * N_[h - 1],
        2.0 * N_[h - 1] * W.cin * 32);
 }
@@ -672,6 +708,7 @@ void Codec::conv(const DLayer& W, int h, const int32_t* nbr, int slot, const voi
   a.wimg = W.Wtc;
   a.bias = W.bias;
   a.mult = W.mult;
+  a.mult_hi = W.mult_hi;
   a.slope = W.slope;
   a.prelu = W.prelu;
   a.shift = W.shift;
@@ -935,7 +972,8 @@ void Codec::run_level(int j, int mode, uint16_t* cdf, uint32_t* enc) {
   // its variants (it times real launches, which a capture cannot)
   // (the ablation architectures have no 64-channel conv)
   if (!gs_ || (prof.mask & ~kAsyncProfiled) || conv_variant_[0] < 0 ||
-      (M_.arch == kArchXfp && conv_variant_[1] < 0) || pred_variant_ < 0) {
+      (M_.arch == kArchXfp && conv_variant_[1] < 0) || pred_variant_ < 0 || up_variant_[0] < 0 ||
+      (M_.arch == kArchXfp && up_variant_[1] < 0)) {
     net_level(j, mode, cdf, enc, nullptr);
     return;
   }
@@ -1021,7 +1059,8 @@ bool Codec::enc_graphs_ready() const {
 // codec has lanes, else level by level.
 void Codec::run_enc_network() {
   const bool direct = !gs_ || (prof.mask & ~kAsyncProfiled) || conv_variant_[0] < 0 ||
-                      (M_.arch == kArchXfp && conv_variant_[1] < 0) || pred_variant_ < 0;
+                      (M_.arch == kArchXfp && conv_variant_[1] < 0) || pred_variant_ < 0 ||
+                      up_variant_[0] < 0 || (M_.arch == kArchXfp && up_variant_[1] < 0);
   if (!lanes_ || direct || genc_fail_) {
     for (int j = 0; j < 5; j++) run_level(j, kPredEnc, nullptr, d_enc_ + (size_t)j * P_);
     return;
@@ -2116,6 +2155,8 @@ int codec_set_tuning(codec_t* codec, const int* variants) {
   for (int c = 0; c < 2; c++)
     if (variants[c] < -1 || variants[c] >= lpc::kConvVariants) return LPC_INVALID_ARG;
   if (variants[2] < -1 || variants[2] >= lpc::kPredVariants) return LPC_INVALID_ARG;
+  for (int c = 3; c < 5; c++)
+    if (variants[c] < -1 || variants[c] >= lpc::kUpVariants) return LPC_INVALID_ARG;
   codec->c.set_tuning(variants);
   return LPC_OK;
 }
@@ -2130,6 +2171,12 @@ int codec_tuning(codec_t* codec, int* variants, float* ms) {
   if (variants) variants[2] = codec->c.pred_variant_;
   for (int v = 0; v < lpc::kPredVariants && ms; v++)
     ms[2 * lpc::kConvVariants + v] = codec->c.pred_tune_ms_[v];
+  for (int c = 0; c < 2; c++) {
+    if (variants) variants[3 + c] = codec->c.up_variant_[c];
+    for (int v = 0; v < lpc::kUpVariants && ms; v++)
+      ms[2 * lpc::kConvVariants + lpc::kPredVariants + c * lpc::kUpVariants + v] =
+          codec->c.up_tune_ms_[c][v];
+  }
   return LPC_OK;
 }
 

@@ -227,11 +227,16 @@ class Codec {
   int conv_variant_[2] = {-1, -1};
   float conv_tune_ms_[2][kConvVariants] = {};
   int pred_variant_ = -1;  // predictor: CUDA cores or tensor cores
+  // up-steps of 32- and 64-channel inputs: CUDA cores or tensor cores
+  int up_variant_[2] = {-1, -1};
+  float up_tune_ms_[2][kUpVariants] = {};
   // fix the variants (captured graphs are dropped: they hold the old ones)
   void set_tuning(const int* v) {
     conv_variant_[0] = v[0];
     conv_variant_[1] = v[1];
     pred_variant_ = v[2];
+    up_variant_[0] = v[3];
+    up_variant_[1] = v[4];
     for (auto& row : gexec_)
       for (auto& e : row)
         if (e) {

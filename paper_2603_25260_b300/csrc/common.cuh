@@ -76,6 +76,24 @@ __device__ __forceinline__ int requant(int32_t acc, int32_t m, int r, int z) {
   return (int)q;
 }
 
+// The same in the high-word form: with ms = m 2^(32 - r) (exact when r <= 32
+// and ms < 2^31), floor((acc m + 2^(r-1)) / 2^r) = floor((acc ms + 2^31) /
+// 2^32), so one wide multiply-add with K = 2^31 + z 2^32 and the high word
+// give the rounded, offset value (|acc ms| < 2^62: the high word fits int32).
+__device__ __forceinline__ int requant_hi(int32_t acc, int32_t ms, int z) {
+  const long long p = (long long)acc * ms + ((long long)z * 4294967296ll + 2147483648ll);
+  const int q = (int)(p >> 32);
+  return min(max(q, -128), 127);
+}
+
+// Whether a multiplier m with shift r admits requant_hi, and the scaled form.
+__host__ __device__ __forceinline__ bool hi_ok(int32_t m, int r) {
+  return r >= 1 && r <= 32 && m >= 0 && ((long long)m << (32 - r)) <= 0x7FFFFFFFll;
+}
+__host__ __device__ __forceinline__ int32_t hi_scale(int32_t m, int r) {
+  return (int32_t)((long long)m << (32 - r));
+}
+
 // PReLU on the INT32 accumulator with a Q15 slope, round half up.
 __device__ __forceinline__ int32_t prelu(int32_t acc, int a) {
   if (acc >= 0) return acc;

@@ -41,6 +41,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -238,9 +239,13 @@ k_conv333_tc(const __grid_constant__ ConvTcArgs a) {
       bulk_g2s(sm + off, reinterpret_cast<const unsigned char*>(a.wimg) + off,
                (uint32_t)min(16384, Cfg::kBBytes - off), &w_bar);
   }
+  // a.mult_hi: the multipliers in the high-word form (requant_hi)
+  const bool hi = a.mult_hi != nullptr;
+  const bool res_hi = hi_ok(1, a.res_shift);
+  const int32_t res_ms = res_hi ? hi_scale(1, a.res_shift) : 1;
   if (t < 32) {
     sBias[t] = a.bias[t];
-    sMult[t] = a.mult[t];
+    sMult[t] = hi ? a.mult_hi[t] : a.mult[t];
     sSlope[t] = a.prelu ? a.slope[t] : 0;
     sMa[t] = a.has_res ? a.res_mab[t] : 0;
     sMb[t] = a.has_res ? a.res_mab[32 + t] : 0;
@@ -520,27 +525,39 @@ k_conv333_tc(const __grid_constant__ ConvTcArgs a) {
       mbar_arrive(&acc_empty[b]);  // the buffer is free for tile lt + 2
       if (r < n) {
         __align__(16) int8_t q[32];
-        if (a.has_res) {
-          __align__(16) int8_t y1[32];
-          reinterpret_cast<uint4*>(y1)[0] = y1v[0];
-          reinterpret_cast<uint4*>(y1)[1] = y1v[1];
+        // the requantisation form is fixed per launch: one straight loop per
+        // form (HI: the layer's, RHI: the residual merge's)
+        auto finish = [&](auto HI, auto RHI) {
+          if (a.has_res) {
+            __align__(16) int8_t y1[32];
+            reinterpret_cast<uint4*>(y1)[0] = y1v[0];
+            reinterpret_cast<uint4*>(y1)[1] = y1v[1];
 #pragma unroll
-          for (int i = 0; i < 32; i++) {
-            int32_t v = acc[i];
-            if (a.prelu) v = prelu(v, sSlope[i]);
-            const int y2 = requant(v, sMult[i], a.shift, a.z_out);
-            int32_t m = (y1[i] - a.res_z1) * sMa[i] + (y2 - a.res_z2) * sMb[i];
-            m = prelu(m, sRsl[i]);
-            q[i] = (int8_t)requant(m, 1, a.res_shift, a.res_z_out);
-          }
-        } else {
+            for (int i = 0; i < 32; i++) {
+              int32_t v = acc[i];
+              if (a.prelu) v = prelu(v, sSlope[i]);
+              int y2;
+              if constexpr (decltype(HI)::value) y2 = requant_hi(v, sMult[i], a.z_out);
+              else y2 = requant(v, sMult[i], a.shift, a.z_out);
+              int32_t m = (y1[i] - a.res_z1) * sMa[i] + (y2 - a.res_z2) * sMb[i];
+              m = prelu(m, sRsl[i]);
+              if constexpr (decltype(RHI)::value) q[i] = (int8_t)requant_hi(m, res_ms, a.res_z_out);
+              else q[i] = (int8_t)requant(m, 1, a.res_shift, a.res_z_out);
+            }
+          } else {
 #pragma unroll
-          for (int i = 0; i < 32; i++) {
-            int32_t v = acc[i];
-            if (a.prelu) v = prelu(v, sSlope[i]);
-            q[i] = (int8_t)requant(v, sMult[i], a.shift, a.z_out);
+            for (int i = 0; i < 32; i++) {
+              int32_t v = acc[i];
+              if (a.prelu) v = prelu(v, sSlope[i]);
+              if constexpr (decltype(HI)::value) q[i] = (int8_t)requant_hi(v, sMult[i], a.z_out);
+              else q[i] = (int8_t)requant(v, sMult[i], a.shift, a.z_out);
+            }
           }
-        }
+        };
+        if (hi && res_hi) finish(std::true_type{}, std::true_type{});
+        else if (hi) finish(std::true_type{}, std::false_type{});
+        else if (res_hi) finish(std::false_type{}, std::true_type{});
+        else finish(std::false_type{}, std::false_type{});
         uint4* dst = reinterpret_cast<uint4*>(a.out + r * a.out_stride + a.out_col);
         dst[0] = reinterpret_cast<const uint4*>(q)[0];
         dst[1] = reinterpret_cast<const uint4*>(q)[1];

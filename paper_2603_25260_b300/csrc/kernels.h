@@ -196,8 +196,10 @@ struct DLayer {
   const int32_t* bias;   // [P][cout], P = S if per_slice else 1
   const int32_t* mult;   // [P][cout]
   const int16_t* slope;  // [P][cout]
-  const uint16_t* Wtc;   // 27-slice layers and the predictor's first layer: packed bf16
-                         // weights for the tensor cores
+  const uint16_t* Wtc;   // 27-slice layers, eight-slot up-steps and the predictor's first
+                         // layer: packed bf16 weights for the tensor cores
+  const int32_t* mult_hi;  // [P][cout] mult x 2^(32 - shift) when every multiplier
+                           // admits the high-word requantisation (requant_hi), else null
 };
 struct DEmb {
   int cout, z_out;
@@ -247,6 +249,36 @@ void launch_up_prune(const DLayer& W, const uint64_t* ckey, const uint32_t* cpar
                      int8_t* out, int out_stride, int out_col, cudaStream_t st, EmbSrc oe = {},
                      int oe_col = 0);
 
+// The same layer on the tensor cores, walked by parent: every parent row
+// times all eight slots' weights (the layer's Wtc image), then the present
+// children's rows.  poff [np + 1]: each parent's first child; pcode: each
+// parent's occupancy code (bit s = a child in slot s, the children in slot
+// order from poff[p]); bias, mult, slope: [8][32] per slot.
+struct UpTcArgs {
+  int cin, z_in, prelu, shift, z_out;
+  int hi;  // mult holds the high-word form
+  const uint16_t* wimg;
+  const int32_t* bias;
+  const int32_t* mult;
+  const int16_t* slope;
+  const int8_t* x;
+  int x_stride;
+  const int64_t* d_np;
+  const uint32_t* poff;
+  const uint8_t* pcode;
+  int8_t* out;
+  int out_stride, out_col;
+  EmbSrc oe;
+  int oe_col;
+};
+void launch_up_tc(const UpTcArgs& a, int64_t np_host, cudaStream_t st);
+size_t up_tc_weight_bytes();
+void pack_up_tc_weights(const int8_t* W, int cin, uint16_t* img);
+// Non-zero if a tensor-core up-step gave up on a bounded wait (optionally reset).
+int up_tc_error(bool reset);
+// up-step variants: 0 CUDA cores (dp4a, one warp per child), 1 tensor cores
+constexpr int kUpVariants = 2;
+
 // Stride-2 down conv: parent p sums slices (ckey & 7) over its children
 // off[p]..off[p+1]-1 of x (child rows).
 void launch_down(const DLayer& W, const uint64_t* ckey, const uint32_t* poff, const int64_t* d_np,
@@ -269,6 +301,7 @@ struct ConvTcArgs {
   const uint16_t* wimg;  // packed weights, conv_tc_weight_bytes(cin)
   const int32_t* bias;
   const int32_t* mult;
+  const int32_t* mult_hi;  // or null: see DLayer::mult_hi
   const int16_t* slope;
   int prelu, shift, z_out;
   const int32_t* nbr;

@@ -55,7 +55,8 @@ struct SmemLayer {
   int32_t* slope;
 };
 
-__device__ __forceinline__ SmemLayer stage_layer(const DLayer& L, int32_t* sm) {
+// hi: stage the high-word multipliers (DLayer::mult_hi, which must be set)
+__device__ __forceinline__ SmemLayer stage_layer(const DLayer& L, int32_t* sm, bool hi) {
   const int nw = L.S * (L.cin / 4) * 32;
   const int P = L.per_slice ? L.S : 1;
   SmemLayer s;
@@ -84,9 +85,10 @@ __device__ __forceinline__ SmemLayer stage_layer(const DLayer& L, int32_t* sm) {
     }
   }
   for (int i = threadIdx.x; i < L.S * 32; i += blockDim.x) s.wsum[i] = L.wsum[i];
+  const int32_t* mult = hi ? L.mult_hi : L.mult;
   for (int i = threadIdx.x; i < P * 32; i += blockDim.x) {
     s.bias[i] = L.bias[i];
-    s.mult[i] = L.mult[i];
+    s.mult[i] = mult[i];
     s.slope[i] = L.slope[i];
   }
   return s;
@@ -146,6 +148,8 @@ void launch_embed(const DEmb& E, const uint8_t* codes, const int64_t* d_n, int64
 constexpr int kUpGroup = 32;
 constexpr int kUpIlp = 4;  // children computed side by side
 
+// (the 64-bit requantisation: the high-word form's extra registers spill at
+// 64 input channels and measured no faster here)
 template <int CIN>
 __global__ void __launch_bounds__(kWarps * 32)
 k_up_prune(DLayer L, const uint64_t* __restrict__ ckey, const uint32_t* __restrict__ cpar,
@@ -177,7 +181,7 @@ k_up_prune(DLayer L, const uint64_t* __restrict__ ckey, const uint32_t* __restri
   int64_t g0 = warp_id_global() * kUpGroup;
   int b = 0;
   int c_cur = g0 < n ? issue(g0, 0) : 0;  // in flight while the layer is staged
-  const SmemLayer s = stage_layer(L, sm);
+  const SmemLayer s = stage_layer(L, sm, false);
   __syncthreads();
   for (; g0 < n; g0 += step, b ^= 1) {
     const int c_next = g0 + step < n ? issue(g0 + step, b ^ 1) : 0;
@@ -259,15 +263,13 @@ void launch_up_prune(const DLayer& W, const uint64_t* ckey, const uint32_t* cpar
   const size_t smem = smem_layer_bytes(W) + (size_t)kWarps * 2 * kUpGroup * W.cin;
   const int blocks = (int)std::min<int64_t>((nc_host + kWarps * kUpGroup - 1) / (kWarps * kUpGroup),
                                             kBlocksRow);
-  if (W.cin == 32) {
-    cudaFuncSetAttribute(k_up_prune<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_up_prune<32><<<blocks, kWarps * 32, smem, st>>>(W, ckey, cpar, d_nc, x, x_stride, out,
-                                                      out_stride, out_col, oe, oe_col);
-  } else {
-    cudaFuncSetAttribute(k_up_prune<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_up_prune<64><<<blocks, kWarps * 32, smem, st>>>(W, ckey, cpar, d_nc, x, x_stride, out,
-                                                      out_stride, out_col, oe, oe_col);
-  }
+  auto go = [&](auto k) {
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<blocks, kWarps * 32, smem, st>>>(W, ckey, cpar, d_nc, x, x_stride, out, out_stride,
+                                         out_col, oe, oe_col);
+  };
+  if (W.cin == 32) go(k_up_prune<32>);
+  else go(k_up_prune<64>);
   count_launches(1);
 }
 
@@ -281,7 +283,8 @@ void launch_up_prune(const DLayer& W, const uint64_t* ckey, const uint32_t* cpar
 constexpr int kDownGroup = 16;
 constexpr int kDownRows = 8 * kDownGroup;
 
-template <int CIN>
+// HI: the layer's multipliers in the high-word form (DLayer::mult_hi)
+template <int CIN, bool HI>
 __global__ void __launch_bounds__(kWarps * 32)
 k_down(DLayer L, const uint64_t* __restrict__ ckey, const uint32_t* __restrict__ poff,
        const int64_t* d_np, const int8_t* __restrict__ x, int x_stride, int8_t* out,
@@ -311,7 +314,7 @@ k_down(DLayer L, const uint64_t* __restrict__ ckey, const uint32_t* __restrict__
   int64_t p0 = warp_id_global() * kDownGroup;
   int b = 0;
   uint32_t o_cur = p0 < n ? issue(p0, 0) : 0;  // in flight while the layer is staged
-  const SmemLayer s = stage_layer(L, sm);
+  const SmemLayer s = stage_layer(L, sm, HI);
   __syncthreads();
   for (; p0 < n; p0 += step, b ^= 1) {
     const uint32_t o_next = p0 + step < n ? issue(p0 + step, b ^ 1) : 0;
@@ -375,7 +378,8 @@ k_down(DLayer L, const uint64_t* __restrict__ ckey, const uint32_t* __restrict__
         int32_t a = acc[u];
         if (L.prelu) a = prelu(a, s.slope[lane]);
         out[(p0 + j + u) * out_stride + out_col + lane] =
-            (int8_t)requant(a, s.mult[lane], L.shift, L.z_out);
+            (int8_t)(HI ? requant_hi(a, s.mult[lane], L.z_out)
+                    : requant(a, s.mult[lane], L.shift, L.z_out));
       }
     }
     for (; j < m; j++) {
@@ -396,7 +400,8 @@ k_down(DLayer L, const uint64_t* __restrict__ ckey, const uint32_t* __restrict__
       }
       if (L.prelu) acc = prelu(acc, s.slope[lane]);
       out[(p0 + j) * out_stride + out_col + lane] =
-          (int8_t)requant(acc, s.mult[lane], L.shift, L.z_out);
+          (int8_t)(HI ? requant_hi(acc, s.mult[lane], L.z_out)
+               : requant(acc, s.mult[lane], L.shift, L.z_out));
     }
     __syncwarp();  // buffer b is free for the group after next
     o_cur = o_next;
@@ -412,35 +417,20 @@ void launch_down(const DLayer& W, const uint64_t* ckey, const uint32_t* poff, co
       smem_layer_bytes(W) + (size_t)kWarps * 2 * ((size_t)kDownRows * W.cin + kDownRows);
   const int blocks = (int)std::min<int64_t>(
       (np_host + kWarps * kDownGroup - 1) / (kWarps * kDownGroup), kBlocksRow);
-  if (W.cin == 32) {
-    cudaFuncSetAttribute(k_down<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_down<32><<<blocks, kWarps * 32, smem, st>>>(W, ckey, poff, d_np, x, x_stride, out,
-                                                  out_stride, out_col);
-  } else {
-    cudaFuncSetAttribute(k_down<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_down<64><<<blocks, kWarps * 32, smem, st>>>(W, ckey, poff, d_np, x, x_stride, out,
-                                                  out_stride, out_col);
-  }
+  auto go = [&](auto k) {
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<blocks, kWarps * 32, smem, st>>>(W, ckey, poff, d_np, x, x_stride, out, out_stride,
+                                         out_col);
+  };
+  const bool hi = W.mult_hi != nullptr;
+  if (W.cin == 32) go(hi ? k_down<32, true> : k_down<32, false>);
+  else go(hi ? k_down<64, true> : k_down<64, false>);
   count_launches(1);
 }
 
 // Eq. 14 in a cheaper exact form when the shift r <= 32 and the multiplier
 // scaled by 2^(32 - r) stays below 2^31: floor((a m + 2^(r-1)) / 2^r) is the
 // high word of a (m 2^(32-r)) + 2^31; the zero point joins the high word.
-__device__ __forceinline__ int requant_hi(int32_t a, int32_t ms, int z) {
-  const long long p = (long long)a * ms + ((long long)z * 4294967296ll + 2147483648ll);
-  const int q = (int)(p >> 32);
-  return min(max(q, -128), 127);
-}
-
-// Whether a layer's multiplier m admits requant_hi, and the scaled form.
-__device__ __forceinline__ bool hi_ok(int32_t m, int r) {
-  return r >= 1 && r <= 32 && m >= 0 && ((long long)m << (32 - r)) <= 0x7FFFFFFFll;
-}
-__device__ __forceinline__ int32_t hi_scale(int32_t m, int r) {
-  return (int32_t)((long long)m << (32 - r));
-}
-
 __global__ void __launch_bounds__(kWarps * 32)
 k_softmax_cdf(const int8_t* __restrict__ logits, int64_t n, const uint32_t* __restrict__ lut,
               uint16_t* cdf) {

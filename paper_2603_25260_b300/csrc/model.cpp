@@ -43,7 +43,7 @@ struct Image {
 };
 
 struct LayerOffs {
-  size_t W, wsum, bias, mult, slope, tc;
+  size_t W, wsum, bias, mult, slope, tc, mhi;
 };
 
 LayerOffs pack_layer(Image& img, const BlobRecord& r) {
@@ -70,9 +70,24 @@ LayerOffs pack_layer(Image& img, const BlobRecord& r) {
   o.mult = img.add(r.mult, (size_t)P * cout * 4);
   o.slope = img.add(r.slope, (size_t)P * cout * 2);
   o.tc = 0;
+  // the multipliers in the high-word form of the requantisation, when every
+  // one of the layer admits it (the kernels then take requant_hi)
+  o.mhi = 0;
+  bool all_hi = true;
+  for (int i = 0; i < P * cout; i++) all_hi = all_hi && hi_ok(r.mult[i], r.shift);
+  if (all_hi) {
+    std::vector<int32_t> mh((size_t)P * cout);
+    for (int i = 0; i < P * cout; i++) mh[i] = hi_scale(r.mult[i], r.shift);
+    o.mhi = img.add(mh.data(), mh.size() * 4);
+  }
   if (r.S == 27 && r.kind == kSum && cout == 32 && (cin == 32 || cin == 64)) {
     std::vector<uint16_t> tcimg(conv_tc_weight_bytes(cin) / 2);
     pack_conv_tc_weights(r.W, cin, tcimg.data());
+    o.tc = img.add(tcimg.data(), tcimg.size() * 2);
+  }
+  if (r.S == 8 && r.kind == kSel && cout == 32 && (cin == 32 || cin == 64)) {  // up-steps
+    std::vector<uint16_t> tcimg(up_tc_weight_bytes() / 2);
+    pack_up_tc_weights(r.W, cin, tcimg.data());
     o.tc = img.add(tcimg.data(), tcimg.size() * 2);
   }
   if (r.S == 1 && r.kind == kSum && cout == 32 && cin == 32) {  // predictor layer 1
@@ -218,7 +233,7 @@ int model_load(const void* blob, size_t len, Model& M, std::string& err) {
   struct Fix {
     void* slot;
     int what;  // 0 emb, 1 layer, 2 res, 3 pred2
-    size_t o[6];
+    size_t o[7];
   };
   std::vector<Fix> fixes;
   size_t ri = 0;
@@ -251,7 +266,7 @@ int model_load(const void* blob, size_t len, Model& M, std::string& err) {
     d.prelu = r->prelu;
     d.per_slice = kind == kSel;
     LayerOffs o = pack_layer(img, *r);
-    fixes.push_back({&d, 1, {o.W, o.wsum, o.bias, o.mult, o.slope, o.tc}});
+    fixes.push_back({&d, 1, {o.W, o.wsum, o.bias, o.mult, o.slope, o.tc, o.mhi}});
   };
   auto resm = [&](DRes& d) {
     const BlobRecord* r = next(kRes, 2, C, C, 1);
@@ -354,6 +369,7 @@ int model_load(const void* blob, size_t len, Model& M, std::string& err) {
       d->mult = reinterpret_cast<const int32_t*>(base + f.o[3]);
       d->slope = reinterpret_cast<const int16_t*>(base + f.o[4]);
       d->Wtc = f.o[5] ? reinterpret_cast<const uint16_t*>(base + f.o[5]) : nullptr;
+      d->mult_hi = f.o[6] ? reinterpret_cast<const int32_t*>(base + f.o[6]) : nullptr;
     } else if (f.what == 2) {
       DRes* d = static_cast<DRes*>(f.slot);
       d->mab = reinterpret_cast<const int32_t*>(base + f.o[0]);
@@ -392,6 +408,7 @@ int upload_layer(const BlobRecord& r, DLayer& d, void** dmem) {
   d.mult = reinterpret_cast<const int32_t*>(base + o.mult);
   d.slope = reinterpret_cast<const int16_t*>(base + o.slope);
   d.Wtc = o.tc ? reinterpret_cast<const uint16_t*>(base + o.tc) : nullptr;
+  d.mult_hi = o.mhi ? reinterpret_cast<const int32_t*>(base + o.mhi) : nullptr;
   return LPC_OK;
 }
 

@@ -213,6 +213,7 @@ int lpc_conv333_variant(const uint64_t* d_keys, int64_t N, int depth, const int8
   a.wimg = L.Wtc;
   a.bias = L.bias;
   a.mult = L.mult;
+  a.mult_hi = L.mult_hi;
   a.slope = L.slope;
   a.prelu = L.prelu;
   a.shift = L.shift;
@@ -272,9 +273,19 @@ int lpc_up_prune(const uint64_t* d_pkeys, const uint8_t* d_codes, int64_t Np,
                  const uint64_t* d_ckeys, int64_t Nc, const int8_t* d_x, int cin, int z_in,
                  const int8_t* h_W, const int32_t* h_bias, const int32_t* h_mult, int shift,
                  const int16_t* h_slope, int z_out, int cout, int8_t* d_out, uint64_t stream) {
+  return lpc_up_prune_variant(d_pkeys, d_codes, Np, d_ckeys, Nc, d_x, cin, z_in, h_W, h_bias,
+                              h_mult, shift, h_slope, z_out, cout, d_out, 0, stream);
+}
+
+int lpc_up_prune_variant(const uint64_t* d_pkeys, const uint8_t* d_codes, int64_t Np,
+                         const uint64_t* d_ckeys, int64_t Nc, const int8_t* d_x, int cin,
+                         int z_in, const int8_t* h_W, const int32_t* h_bias,
+                         const int32_t* h_mult, int shift, const int16_t* h_slope, int z_out,
+                         int cout, int8_t* d_out, int variant, uint64_t stream) {
   (void)d_pkeys;
   (void)d_codes;
-  if (Nc < 0 || Np < 0 || bad_layer(cin, cout, shift) || !h_W || !h_bias || !h_mult)
+  if (Nc < 0 || Np < 0 || bad_layer(cin, cout, shift) || !h_W || !h_bias || !h_mult ||
+      variant < 0 || variant >= kUpVariants)
     return LPC_INVALID_ARG;
   if (Nc == 0) return LPC_OK;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -296,8 +307,18 @@ int lpc_up_prune(const uint64_t* d_pkeys, const uint8_t* d_codes, int64_t Np,
                           &mem);
   if (s) return s;
   t.ptrs.push_back(mem);
-  launch_up_prune(L, d_ckeys, cpar, d_nc, Nc, d_x, cin, d_out, cout, 0, st);
-  return finish(st, nullptr);
+  if (variant == 1) {
+    if (!L.Wtc) return LPC_CUDA_ERROR;
+    const UpTcArgs a{cin,  L.z_in, L.prelu, L.shift, L.z_out, L.mult_hi != nullptr, L.Wtc,  L.bias,
+                     L.mult_hi ? L.mult_hi : L.mult, L.slope, d_x,
+                     cin,  d_np,   poff,    pc,      d_out,   cout,   0,      EmbSrc{}, 0};
+    launch_up_tc(a, std::max<int64_t>(Np, 1), st);
+  } else {
+    launch_up_prune(L, d_ckeys, cpar, d_nc, Nc, d_x, cin, d_out, cout, 0, st);
+  }
+  const int s2 = finish(st, nullptr);
+  if (up_tc_error(true)) return LPC_TIMEOUT;
+  return s2;
 }
 
 int lpc_softmax_cdf(const int8_t* d_logits, int64_t N, const uint32_t* h_lut, uint16_t* d_cdf,

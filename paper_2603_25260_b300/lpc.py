@@ -78,6 +78,8 @@ def lib():
                                   C.c_uint64]),
             "lpc_up_prune": (I32, [P, P, I64, P, I64, P, I32, I32, P, P, P, I32, P, I32, I32, P,
                                    C.c_uint64]),
+            "lpc_up_prune_variant": (I32, [P, P, I64, P, I64, P, I32, I32, P, P, P, I32, P, I32,
+                                           I32, P, I32, C.c_uint64]),
             "lpc_softmax_cdf": (I32, [P, I64, P, P, C.c_uint64]),
         }
         for name, (res, args) in sig.items():
@@ -286,16 +288,19 @@ class Codec:
         (milliseconds; bit 0 of a variant = alternative ring shape, bit 1 =
         contiguous tile order, bit 2 = TMA gather4 loads of the neighbour rows
         instead of cp.async copies)."""
-        v = (C.c_int * 3)()
-        ms = (C.c_float * 18)()
+        v = (C.c_int * 5)()
+        ms = (C.c_float * 22)()
         self._check(self._lib.codec_tuning(self._h, v, ms))
-        return {"conv32": v[0], "conv64": v[1], "predictor": v[2],
+        return {"conv32": v[0], "conv64": v[1], "predictor": v[2], "up32": v[3], "up64": v[4],
                 "ms32": [round(x, 4) for x in ms[:8]], "ms64": [round(x, 4) for x in ms[8:16]],
-                "ms_pred": [round(x, 4) for x in ms[16:18]]}
+                "ms_pred": [round(x, 4) for x in ms[16:18]],
+                "ms_up32": [round(x, 4) for x in ms[18:20]],
+                "ms_up64": [round(x, 4) for x in ms[20:22]]}
 
-    def set_tuning(self, conv32: int = -1, conv64: int = -1, predictor: int = -1):
+    def set_tuning(self, conv32: int = -1, conv64: int = -1, predictor: int = -1, up32: int = -1,
+                   up64: int = -1):
         """Fix kernel variants instead of autotuning them (-1: tune)."""
-        v = (C.c_int * 3)(conv32, conv64, predictor)
+        v = (C.c_int * 5)(conv32, conv64, predictor, up32, up64)
         self._check(self._lib.codec_set_tuning(self._h, v))
 
     def last_phases(self) -> list[float]:
@@ -454,7 +459,7 @@ def down_s2(ckeys, pkeys, x, z_in, W, bias, mult, shift, slope, z_out):
     return out[:Np]
 
 
-def up_prune(pkeys, codes, ckeys, x, z_in, W, bias, mult, shift, slope, z_out):
+def up_prune(pkeys, codes, ckeys, x, z_in, W, bias, mult, shift, slope, z_out, variant=0):
     pkeys, ckeys = _dev(pkeys, torch.int64), _dev(ckeys, torch.int64)
     codes, x = _dev(codes, torch.uint8), _dev(x, torch.int8)
     W = _np(W, np.int8)
@@ -463,10 +468,11 @@ def up_prune(pkeys, codes, ckeys, x, z_in, W, bias, mult, shift, slope, z_out):
     out = torch.empty((max(Nc, 1), cout), dtype=torch.int8, device="cuda")
     b, m = _np(bias, np.int32), _np(mult, np.int32)
     s = None if slope is None else _np(slope, np.int16)
-    _ops_check(lib().lpc_up_prune(pkeys.data_ptr(), codes.data_ptr(), pkeys.shape[0],
-                                  ckeys.data_ptr(), Nc, x.data_ptr(), x.shape[1], z_in, _hp(W),
-                                  _hp(b), _hp(m), shift, _hp(s), z_out, cout, out.data_ptr(),
-                                  _stream()), "lpc_up_prune")
+    _ops_check(lib().lpc_up_prune_variant(pkeys.data_ptr(), codes.data_ptr(), pkeys.shape[0],
+                                          ckeys.data_ptr(), Nc, x.data_ptr(), x.shape[1], z_in,
+                                          _hp(W), _hp(b), _hp(m), shift, _hp(s), z_out, cout,
+                                          out.data_ptr(), variant, _stream()),
+               "lpc_up_prune_variant")
     return out[:Nc]
 
 

@@ -32,7 +32,7 @@ def test_headers_declare_the_boundary():
                  "lpc_t_conv_fwd", "lpc_t_conv_bwd", "lpc_t_up_fwd", "lpc_t_up_bwd",
                  "lpc_t_down_fwd", "lpc_t_down_bwd", "lpc_t_embed_fwd", "lpc_t_embed_bwd",
                  "lpc_t_prelu_fwd", "lpc_t_prelu_bwd", "lpc_t_fq_fwd", "lpc_t_fq_bwd", "lpc_t_fq_w",
-                 "lpc_t_levels", "codec_tuning", "lpc_conv333_variant",
+                 "lpc_t_levels", "codec_tuning", "lpc_conv333_variant", "lpc_up_prune_variant",
                  "codec_set_tuning"):
         assert want in names
 

@@ -183,7 +183,9 @@ def test_codec_autotuner_picks_variants(lpc, blob):
     data = cod.encode(_cuda(xyz))
     t = cod.tuning()
     assert 0 <= t["conv32"] < 8 and 0 <= t["conv64"] < 8 and 0 <= t["predictor"] < 2
-    assert all(0 < m < 1e3 for m in t["ms32"] + t["ms64"] + t["ms_pred"])
+    assert 0 <= t["up32"] < 2 and 0 <= t["up64"] < 2
+    assert all(0 < m < 1e3 for m in t["ms32"] + t["ms64"] + t["ms_pred"] + t["ms_up32"] +
+               t["ms_up64"])
     assert data == O.encode(blob, xyz, 14)  # and the next call runs the captured graphs
     assert cod.encode(_cuda(xyz)) == data
 
@@ -220,9 +222,10 @@ def test_down_s2(lpc, n, depth, seed):
     assert np.array_equal(got, want)
 
 
+@pytest.mark.parametrize("variant", [0, 1])
 @pytest.mark.parametrize("n,depth,cin,seed", [(1, 4, 32, 1), (900, 6, 64, 2), (25000, 12, 64, 3),
-                                              (5000, 9, 32, 4)])
-def test_up_prune(lpc, n, depth, cin, seed):
+                                              (5000, 9, 32, 4), (70000, 14, 64, 5)])
+def test_up_prune(lpc, n, depth, cin, seed, variant):
     xyz = synth.random_cloud(n, depth, seed)
     keys, codes = O.build_levels(xyz, depth)
     d = depth - 1
@@ -232,8 +235,29 @@ def test_up_prune(lpc, n, depth, cin, seed):
     W, bias, mult, slope = _params(8, cin, 32, seed, per_slice=True)
     want = O.up_prune(pk, cd, ck, x, 3, W, bias, mult, 21, slope, -2)
     got = lpc.up_prune(_cuda(pk.view(np.int64)), _cuda(cd), _cuda(ck.view(np.int64)), _cuda(x), 3,
-                       W, bias, mult, 21, slope, -2).cpu().numpy()
+                       W, bias, mult, 21, slope, -2, variant=variant).cpu().numpy()
     assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_up_prune_extreme_accumulator(lpc, variant):
+    """Worst-case magnitudes of the up-step: every input at -128 with
+    z_in = 127 (q - z = -255) and every weight at +-127 over 64 channels
+    (|acc| = 64 * 255 * 127), mixed signs by slot, no PReLU."""
+    xyz = synth.random_cloud(3000, 8, 9)
+    keys, codes = O.build_levels(xyz, 8)
+    pk, cd, ck = keys[7], codes[7], keys[8]
+    x = np.full((len(pk), 64), -128, np.int8)
+    W = np.full((8, 32, 64), 127, np.int8)
+    W[1::2] = -127
+    W[2, :, ::3] = -127
+    bias = np.arange(8 * 32, dtype=np.int32).reshape(8, 32) * 1001 - 90000
+    mult = np.full((8, 32), 3, np.int32)
+    want = O.up_prune(pk, cd, ck, x, 127, W, bias, mult, 15, None, 1)
+    got = lpc.up_prune(_cuda(pk.view(np.int64)), _cuda(cd), _cuda(ck.view(np.int64)), _cuda(x),
+                       127, W, bias, mult, 15, None, 1, variant=variant).cpu().numpy()
+    assert np.array_equal(got, want)
+    assert len(np.unique(want)) > 3  # the extremes do not all clip to one value
 
 
 def test_softmax_cdf(lpc):
@@ -499,11 +523,13 @@ def test_batch_into_reusable_buffer(lpc, blob):
             assert np.array_equal(O.leaf_keys(d.cpu().numpy(), L), O.leaf_keys(f, L))
 
 
-@pytest.mark.parametrize("variants", [(0, 0, 0), (3, 3, 1), (1, 2, 1), (2, 1, 0), (4, 4, 1),
-                                      (7, 5, 1), (5, 6, 0)])
+@pytest.mark.parametrize("variants", [(0, 0, 0, 0, 0), (3, 3, 1, 1, 1), (1, 2, 1, 0, 1),
+                                      (2, 1, 0, 1, 0), (4, 4, 1, 1, 1), (7, 5, 1, 0, 0),
+                                      (5, 6, 0, 1, 1)])
 def test_fixed_variants_byte_identical(lpc, blob, variants):
-    """Every fixed combination of conv and predictor variants gives the
-    oracle's stream and decodes it (graphs captured with those variants)."""
+    """Every fixed combination of conv, predictor and up-step variants gives
+    the oracle's stream and decodes it (graphs captured with those
+    variants)."""
     xyz = synth.random_cloud(15000, 13, 6)
     cod = _codec(lpc, blob, 13, 15000)
     cod.set_tuning(*variants)
@@ -513,7 +539,8 @@ def test_fixed_variants_byte_identical(lpc, blob, variants):
         assert data == want
         dec = cod.decode(data).cpu().numpy()
         assert np.array_equal(O.leaf_keys(dec, 13), O.leaf_keys(xyz, 13))
-    assert cod.tuning()["predictor"] == variants[2]
+    t = cod.tuning()
+    assert (t["predictor"], t["up32"], t["up64"]) == variants[2:]
 
 
 @pytest.mark.parametrize("threads", [1, 2, 4])
