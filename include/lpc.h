@@ -119,6 +119,7 @@ int decode_frame(codec_t* codec, const uint8_t* h_in, size_t len, int32_t* d_xyz
  * C_255 = 65536 are implicit), entries 254 and 255 are 0xFFFF.  The f_s are
  * the 16-bit integer softmax frequencies of Eq. 15 (every f_s >= 1, sum 2^16).
  * cap_nodes: rows available; *n_nodes receives N_d (LPC_CAPACITY if larger).
+ * d_cdf_out must be 16-byte aligned (LPC_INVALID_ARG otherwise).
  * Only the network runs; nothing is entropy coded. */
 int probs_level(codec_t* codec, const int32_t* d_xyz, int64_t n, int d, uint16_t* d_cdf_out,
                 int64_t cap_nodes, int64_t* n_nodes);

@@ -2037,6 +2037,8 @@ int Codec::probs(const int32_t* d_xyz, int64_t n, int d, uint16_t* d_cdf, int64_
   const int L = cfg_.L;
   if (!nn || n < 0 || (n > 0 && (!d_xyz || !d_cdf)) || d < L - cfg_.b_off || d > L - 1)
     return fail(LPC_INVALID_ARG, "probs_level: bad arguments");
+  if (reinterpret_cast<uintptr_t>(d_cdf) & 15)  // rows leave by 16-byte-aligned copies
+    return fail(LPC_INVALID_ARG, "probs_level: d_cdf_out must be 16-byte aligned");
   if (n > cfg_.max_points || n > P_) return fail(LPC_CAPACITY, "probs_level: n exceeds max_points");
   *nn = 0;
   if (n == 0) return LPC_OK;

@@ -540,9 +540,9 @@ k_predictor_dp4a(DLayer P1, DPred2 P2, const uint32_t* __restrict__ lut,
 
 // ------------------------------------------- predictor + softmax + CDF --
 // h = requant(prelu(W1 (F - z1) + b1)) (C -> C), logits = requant(W2 (h - z2)
-// + b2) (C -> 255) on the tcgen05 tensor cores, then the integer softmax one
-// warp per row.  Modes: full CDF row, the (C_s, f_s) pair of the true symbol
-// (encoder), or the logits (debug).
+// + b2) (C -> 255) on the tcgen05 tensor cores, then the integer softmax.
+// Modes: full CDF row, the (C_s, f_s) pair of the true symbol (encoder), or
+// the logits (debug).
 //
 // One persistent CTA of 16 warps per SM, as two independent groups of 8
 // warps that take alternate tiles of 128 rows (own shared-memory tiles, own
@@ -552,19 +552,28 @@ k_predictor_dp4a(DLayer P1, DPred2 P2, const uint32_t* __restrict__ lut,
 // N=32 K=32 MMA gives layer 1 in TMEM (every fp32 partial sum is an integer
 // below 2^22: 32 products of at most 255 * 127), the warps write (h - z2)
 // back as bf16 (warp: TMEM lane quadrant and half of the columns), an M=128
-// N=256 K=32 MMA gives the 255 logits, which the warps requantise into a
-// shared logits tile; then every warp runs the softmax of 16 rows, 8
-// symbols a lane.
+// N=256 K=32 MMA gives the 255 logits.  The softmax then runs one thread per
+// half row, on the half row the thread reads from TMEM (row = its TMEM lane,
+// half = its warp's column half), in four passes over its 128 symbols with
+// the two halves of a row exchanging one word through shared memory after
+// each of the first three: (1) requantise into 16-bit keys kept in the
+// shared tile, smallest key; (2) S from the bank-replicated exp table;
+// (3) the quotients by one exact 40-bit reciprocal of S, f = 1 + q stored in
+// place of the keys; (4) the cumulative row two entries per multiply-add,
+// in place, copied out coalesced.  Per-row work that a warp-per-row softmax
+// spends on reductions and scans is here a handful of scalar instructions
+// per thread.
 namespace {
 
 constexpr int kPTile = 128;
 constexpr int kPThreads = 512;
 constexpr int kPGroup = 256;     // threads of one group
-constexpr int kLogStride = 272;  // logits row stride in shared memory (conflict-free)
+constexpr int kLogStride = 528;  // key row stride in shared memory (16 B x odd: conflict-free)
 constexpr int kPredB1 = 0, kPredB2 = 2048;  // weight images
 constexpr int kPredA = 18432;               // per group: A1 (8 KB), A2 (8 KB)
-constexpr int kPredLg = kPredA + 2 * 16384; // per group: logits tile
-constexpr int kPredSmem = 1024 + kPredLg + 2 * kPTile * kLogStride;
+constexpr int kPredLg = kPredA + 2 * 16384; // per group: key tile (128 rows of 256 u16)
+constexpr int kPredTab = kPredLg + 2 * kPTile * kLogStride;  // exp table, one copy per bank
+constexpr int kPredSmem = 1024 + kPredTab + 256 * 32 * 4;
 
 __device__ int g_pred_error = 0;
 
@@ -631,9 +640,11 @@ k_predictor_tc(DLayer P1, DPred2 P2, const uint32_t* __restrict__ lut,
   __shared__ int32_t sB1[32], sM1[32], sS1[32];
   __shared__ __align__(16) int32_t sB2[256], sM2[256];
   __shared__ __align__(16) long long sK2[256];
-  __shared__ uint32_t slut[256];
   __shared__ uint64_t mbars[2];
   __shared__ uint32_t tslot;
+  // per group, half and row: the two halves of a row exchange their smallest
+  // key, then their S, then their sum of q (two arrays used alternately)
+  __shared__ uint32_t sXa[2][2][kPTile], sXb[2][2][kPTile];
   const int t = threadIdx.x, w = t >> 5, lane = t & 31;
   if (w == 0) tc::tmem_alloc(&tslot, 512);
   if (t == 0) {
@@ -650,13 +661,23 @@ k_predictor_tc(DLayer P1, DPred2 P2, const uint32_t* __restrict__ lut,
   if (t < 256) {
     const uint32_t off = kMagicBits - (uint32_t)P2.bias[t];
     sB2[t] = (int32_t)off;
-    sM2[t] = fast2 ? hi_scale(P2.mult[t], P2.shift) : P2.mult[t];
-    // high-word form with the accumulator's bits v = off + a: a ms + 2^31 +
-    // z 2^32 = v ms + K, K = 2^31 + z 2^32 - off ms (one wide multiply-add)
-    sK2[t] = fast2 ? 2147483648ll + (long long)P2.z_out * 4294967296ll -
-                         (long long)off * (long long)sM2[t]
-                   : 0ll;
-    slut[t] = lut[t];
+    sM2[t] = P2.mult[t];
+    sK2[t] = 0;
+    if (fast2) {
+      // the key's 127 - l in the high-word form: with the accumulator's bits
+      // v = off + a, a ms + 2^31 + z 2^32 = v ms + K, K = 2^31 + z 2^32 -
+      // off ms, and 127 - floor(y / 2^32) = floor((128 2^32 - 1 - y) / 2^32),
+      // so 127 - l = high word of v (-ms) + (128 2^32 - 1 - K) before the
+      // clamp (one wide multiply-add); the padding column gives 255
+      const long long ms = hi_scale(P2.mult[t], P2.shift);
+      const long long K = 2147483648ll + (long long)P2.z_out * 4294967296ll - (long long)off * ms;
+      sM2[t] = t < kNsym ? (int32_t)-ms : 0;
+      sK2[t] = t < kNsym ? 128ll * 4294967296ll - 1 - K : 255ll * 4294967296ll;
+    }
+  }
+  {  // the exp table, word 32 d + j = lut[d] for every bank j
+    uint32_t* tab = reinterpret_cast<uint32_t*>(sm + kPredTab);
+    for (int i = t; i < 256 * 32; i += kPThreads) tab[i] = __ldg(lut + (i >> 5));
   }
   if (t < 32) {
     sB1[t] = (int32_t)(kMagicBits - (uint32_t)P1.bias[t]);
@@ -678,8 +699,7 @@ k_predictor_tc(DLayer P1, DPred2 P2, const uint32_t* __restrict__ lut,
   const int g = w >> 3, wl = w & 7, tl = t & (kPGroup - 1);  // group, warp and thread in it
   const uint32_t tbase = tslot + 256 * g;
   uint64_t* mbar = &mbars[g];
-  int ck[8];
-  tie_keys(lane, ck);
+  const uint32_t tab_lane = tc::smem_u32(sm + kPredTab) + 4u * (uint32_t)lane;
   const int quad = wl & 3, cg = wl >> 2;  // TMEM lane quadrant, column half
   const int erow = quad * 32 + lane;      // tile row this thread handles in the epilogues
   const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
@@ -773,8 +793,16 @@ k_predictor_tc(DLayer P1, DPred2 P2, const uint32_t* __restrict__ lut,
       break;
     }
     tc::tc_fence_after();
-    // ---- logits: 128 columns a warp, requantised into the shared tile;
-    // the accumulator columns come in pairs of 16-column loads per wait
+    // ---- pass 1: this thread's half row (row erow, symbols 128 cg ..
+    // 128 cg + 127) of logits from TMEM, requantised into the keys
+    // (127 - l) 128 + (s & 127) (saturating packs clamp 127 - l to 0..255),
+    // stored in place in the shared tile, and their smallest key; the
+    // accumulator columns come in pairs of 16-column loads per wait
+    const int64_t r = r0 + erow;
+    unsigned char* rowp = sLg + erow * kLogStride + 256 * cg;
+    uint4* row4 = reinterpret_cast<uint4*>(rowp);
+    uint16_t* row16 = reinterpret_cast<uint16_t*>(rowp);
+    uint32_t mn = 0xFFFFFFFFu;
     uint32_t fr[2][16];
 #pragma unroll
     for (int gi = 0; gi < 8; gi++) {
@@ -783,11 +811,10 @@ k_predictor_tc(DLayer P1, DPred2 P2, const uint32_t* __restrict__ lut,
         tc::tmem_ld16_issue(tbase + lane_off + c0, fr[0]);
         tc::tmem_ld16_issue(tbase + lane_off + c0 + 16, fr[1]);
         tc::tmem_wait_ld();
+        tc::tmem_regs_ready(fr[0]);
+        tc::tmem_regs_ready(fr[1]);
       }
-      float f[16];
-#pragma unroll
-      for (int i = 0; i < 16; i++) f[i] = __uint_as_float(fr[gi & 1][i]);
-      uint32_t pk[4] = {0, 0, 0, 0};
+      int32_t u[16];
       if (fast2) {
         int32_t ms[16];
         long long kk[16];
@@ -803,66 +830,147 @@ k_predictor_tc(DLayer P1, DPred2 P2, const uint32_t* __restrict__ lut,
         }
 #pragma unroll
         for (int i = 0; i < 16; i++) {
-          const int32_t v = (int32_t)__float_as_uint(f[i] + kMagic);
-          const int q = min(max((int)(((long long)v * ms[i] + kk[i]) >> 32), -128), 127);
-          pk[i >> 2] |= (uint32_t)(uint8_t)(c0 + i >= kNsym ? 0 : q) << (8 * (i & 3));
+          const int32_t v = (int32_t)__float_as_uint(__uint_as_float(fr[gi & 1][i]) + kMagic);
+          u[i] = (int)(((long long)v * ms[i] + kk[i]) >> 32);
         }
       } else {
 #pragma unroll
         for (int i = 0; i < 16; i++) {
           const int c = c0 + i;
-          const int32_t a = acc_plus(f[i], sB2[c]);
-          const int q = c >= kNsym ? 0 : requant(a, sM2[c], P2.shift, P2.z_out);
-          pk[i >> 2] |= (uint32_t)(uint8_t)q << (8 * (i & 3));
+          const int32_t a = acc_plus(__uint_as_float(fr[gi & 1][i]), sB2[c]);
+          u[i] = c >= kNsym ? 255 : 127 - requant(a, sM2[c], P2.shift, P2.z_out);
         }
       }
-      *reinterpret_cast<uint4*>(sLg + erow * kLogStride + c0) =
-          make_uint4(pk[0], pk[1], pk[2], pk[3]);
+      if (mode == kPredLogits && r < n) {
+#pragma unroll
+        for (int i = 0; i < 16; i++)
+          if (c0 + i < kNsym) logits[r * kNsym + c0 + i] = (int8_t)(127 - min(max(u[i], 0), 255));
+      }
+      uint32_t kw[8];
+#pragma unroll
+      for (int j = 0; j < 4; j++) {
+        uint32_t p2, p4;  // saturated bytes u[4j .. 4j + 3]
+        asm("cvt.pack.sat.u8.s32.b32 %0, %1, %2, 0;" : "=r"(p2) : "r"(u[4 * j + 3]), "r"(u[4 * j + 2]));
+        asm("cvt.pack.sat.u8.s32.b32 %0, %1, %2, %3;"
+            : "=r"(p4)
+            : "r"(u[4 * j + 1]), "r"(u[4 * j]), "r"(p2));
+        const uint32_t s4 = (uint32_t)(16 * gi + 4 * j);  // s & 127 of u[4j]
+        kw[2 * j] = __byte_perm(p4, 0, 0x4140) * 128u + (s4 | ((s4 + 1) << 16));
+        kw[2 * j + 1] = __byte_perm(p4, 0, 0x4342) * 128u + ((s4 + 2) | ((s4 + 3) << 16));
+        mn = min_u16x2(mn, min_u16x2(kw[2 * j], kw[2 * j + 1]));
+      }
+      row4[2 * gi] = make_uint4(kw[0], kw[1], kw[2], kw[3]);
+      row4[2 * gi + 1] = make_uint4(kw[4], kw[5], kw[6], kw[7]);
     }
+    // the row's key (127 - l) 256 + s of its largest logit at its lowest index
+    mn = min(mn & 0xFFFFu, mn >> 16);
+    const uint32_t hkey = ((mn & kKeyOff) << 1) | (uint32_t)(128 * cg) | (mn & 127u);
+    sXa[g][cg][erow] = hkey;
     tc::tc_fence_before();
     group_sync(g);
-    // ---- integer softmax, one warp per row, 16 rows a warp, two rows at a
-    // time so that their dependent chains (reductions, table loads, the
-    // divisions) overlap; a row past the end is computed and not stored
-#pragma unroll 1
-    for (int rr = 0; rr < kPTile / 8; rr += 2) {
-      const int tr = wl * (kPTile / 8) + rr;
-      const int64_t r = r0 + tr;
-      if (r >= n) break;
-      const bool two = r + 1 < n;
-      int l[2][8];
+    if (mode == kPredLogits) continue;
+    // ---- pass 2: S = sum of e_s = lut[(127 - l_s) - u0] over the row, the
+    // table read from the copy in this thread's bank
+    const uint32_t key = min(hkey, sXa[g][cg ^ 1][erow]);
+    const int first = (int)(key & 255u);
+    const uint32_t tb = tab_lane - (key >> 8) * 128u;
+    uint32_t S = 0;
+#pragma unroll 4
+    for (int c = 0; c < 16; c++) {
+      const uint4 k4 = row4[c];
+      const uint32_t kv[4] = {k4.x, k4.y, k4.z, k4.w};
 #pragma unroll
-      for (int k = 0; k < 2; k++) {
-        const uint2 raw =
-            *reinterpret_cast<const uint2*>(sLg + (tr + k) * kLogStride + 8 * lane);
+      for (int j = 0; j < 4; j++) {
+        const uint32_t e0 = lds_u32(tb + (kv[j] & kKeyOff));
+        uint32_t e1 = lds_u32(tb + ((kv[j] >> 16) & kKeyOff));
+        if (c == 15 && j == 3) e1 = cg ? 0u : e1;  // the padding entry takes no frequency
+        S += e0 + e1;
+      }
+    }
+    sXb[g][cg][erow] = S;
+    group_sync(g);
+    S += sXb[g][cg ^ 1][erow];
+    // ---- pass 3: q_s = floor(e_s (2^16 - 255) / S) = floor(e_s A / 2^40)
+    // with A = ceil((2^16 - 255) 2^40 / S): exact for every e_s <= 2^16 as
+    // e_s S < 2^40 (the rounding up of A moves e_s A / 2^40 by less than
+    // 1 / S, less than the distance of a non-integer e_s K / S to the next
+    // integer); f_s = 1 + q_s stored in place of the keys, two to a word
+    const unsigned long long A =
+        (((unsigned long long)kQScale << 40) + S - 1) / (unsigned long long)S;
+    const uint32_t ahi = (uint32_t)(A >> 32), alo = (uint32_t)A;
+    uint32_t tot = 0;
+#pragma unroll 4
+    for (int c = 0; c < 16; c++) {
+      const uint4 k4 = row4[c];
+      const uint32_t kv[4] = {k4.x, k4.y, k4.z, k4.w};
+      uint32_t fw[4];
 #pragma unroll
-        for (int i = 0; i < 4; i++) {
-          l[k][i] = sext_byte(raw.x, i);
-          l[k][4 + i] = sext_byte(raw.y, i);
+      for (int j = 0; j < 4; j++) {
+        const uint32_t e0 = lds_u32(tb + (kv[j] & kKeyOff));
+        uint32_t e1 = lds_u32(tb + ((kv[j] >> 16) & kKeyOff));
+        if (c == 15 && j == 3) e1 = cg ? 0u : e1;
+        const uint32_t q0 = (e0 * ahi + __umulhi(e0, alo)) >> 8;
+        const uint32_t q1 = (e1 * ahi + __umulhi(e1, alo)) >> 8;
+        tot += q0 + q1;
+        fw[j] = (q0 | (q1 << 16)) + 0x00010001u;
+      }
+      row4[c] = make_uint4(fw[0], fw[1], fw[2], fw[3]);
+    }
+    sXa[g][cg][erow] = tot;
+    group_sync(g);
+    const uint32_t tot_o = sXa[g][cg ^ 1][erow];
+    const uint32_t R = kQScale - (tot + tot_o);  // the remainder, taken by the first maximum
+    {
+      const int fl = first - 128 * cg;
+      if (fl >= 0 && fl < 128) {
+        row16[fl] = (uint16_t)(row16[fl] + R);
+      }
+    }
+    // 1 + q summed over half 0 (and R once the first maximum lies there)
+    const uint32_t base = cg ? 128u + tot_o + (first < 128 ? R : 0u) : 0u;
+    if (mode == kPredCdf) {
+      // ---- pass 4: C_{s+1} = base + f_0 + ... + f_s two at a time, in
+      // place: with w = f_s | f_{s+1} << 16 and run in both halves,
+      // w 65537 + run = C_{s+1} | C_{s+2} << 16 (no carry leaves the low half
+      // below 2^16); entries 254 and 255 hold 0xFFFF
+      uint32_t runp = base * 0x10001u;
+#pragma unroll 4
+      for (int c = 0; c < 16; c++) {
+        const uint4 f4 = row4[c];
+        const uint32_t fv[4] = {f4.x, f4.y, f4.z, f4.w};
+        uint32_t cw[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+          cw[j] = fv[j] * 0x10001u + runp;
+          runp = __byte_perm(cw[j], 0, 0x3232);
         }
+        if (c == 15 && cg) cw[3] = 0xFFFFFFFFu;
+        row4[c] = make_uint4(cw[0], cw[1], cw[2], cw[3]);
       }
-      if (mode == kPredLogits) {
-#pragma unroll
-        for (int k = 0; k < 2; k++)
-#pragma unroll
-          for (int i = 0; i < 8; i++)
-            if (lane * 8 + i < kNsym && (k == 0 || two))
-              logits[(r + k) * kNsym + lane * 8 + i] = (int8_t)l[k][i];
-        continue;
+      group_sync(g);
+      // the tile's rows leave coalesced: a warp copies 16 rows, 512 B each
+#pragma unroll 4
+      for (int k = 0; k < kPTile / 8; k++) {
+        const int tr = wl * (kPTile / 8) + k;
+        if (r0 + tr < n)
+          reinterpret_cast<uint4*>(cdf + (r0 + tr) * 256)[lane] =
+              *reinterpret_cast<const uint4*>(sLg + tr * kLogStride + 16 * lane);
       }
-      SoftRow o0, o1;
-      softmax_row(l[0], ck, lane == 31, slut, o0);
-      softmax_row(l[1], ck, lane == 31, slut, o1);
-      if (mode == kPredCdf) {
-        store_cdf_row(o0, lane, cdf + r * 256);
-        if (two) store_cdf_row(o1, lane, cdf + (r + 1) * 256);
-      } else {
-        const int s0 = (int)codes[r] - 1;
-        const int s1 = two ? (int)codes[r + 1] - 1 : 0;
-        const uint32_t p0 = enc_pair(o0, lane, s0);
-        const uint32_t p1 = enc_pair(o1, lane, s1);
-        if ((s0 >> 3) == lane) enc[r] = p0;
-        if (two && (s1 >> 3) == lane) enc[r + 1] = p1;
+    } else if (r < n) {
+      // the encoder's (C_s, f_s): C_s = base + the f of this half before s;
+      // any 254 or fewer f sum below 2^16, so words add with their halves
+      // apart
+      const int sl = (int)codes[r] - 1 - 128 * cg;
+      if (sl >= 0 && sl < 128) {
+        uint32_t acc = 0;
+        for (int c = 0; c < (sl >> 3); c++) {
+          const uint4 f4 = row4[c];
+          acc += f4.x + f4.y + f4.z + f4.w;
+        }
+        uint32_t cs = base + (acc & 0xFFFFu) + (acc >> 16);
+        for (int k = sl & ~7; k < sl; k++) cs += row16[k];
+        const uint32_t fs = row16[sl];
+        enc[r] = cs | (fs << 16);
       }
     }
   }

@@ -1,5 +1,6 @@
-// The integer softmax of one row (Eq. 15), one warp per row, shared by the
-// predictor kernels and the range decoder that forms its tables itself.
+// The integer softmax of one row (Eq. 15), one warp per row, used by the
+// CUDA-core predictor and the softmax-only kernel; the tensor-core
+// predictor's per-half-row form shares its constants and helpers.
 #pragma once
 
 #include "common.cuh"
@@ -137,6 +138,29 @@ __device__ __forceinline__ uint32_t enc_pair(const SoftRow& o, int lane, int s) 
   const uint32_t fs = 1 + (rs - rp) + (s == o.first ? R : 0u);
   const uint32_t cs = (uint32_t)s + before + rp + (s > o.first ? R : 0u);
   return cs | (fs << 16);
+}
+
+
+// ---------------------------------------------- key rows (predictor) --
+// The tensor-core predictor runs the same softmax one thread per half row:
+// its epilogue writes each logit l_s as the 16-bit key (127 - l_s) 128 +
+// (s & 127), whose bits 7..14 are the byte offset of lut[127 - l_s] in a
+// copy of the exp table with one word per bank (word 32 d + lane holds
+// lut[d]); a thread reads lut[(127 - l_s) - (127 - M)] from its own bank, so
+// the 32 loads of a warp never conflict.
+constexpr uint32_t kKeyOff = 0x7F80u;  // the (127 - l) 128 bits of a key
+
+__device__ __forceinline__ uint32_t min_u16x2(uint32_t a, uint32_t b) {
+  uint32_t d;
+  asm("min.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+  return d;
+}
+
+// A read of the (read-only) bank-replicated table.
+__device__ __forceinline__ uint32_t lds_u32(uint32_t addr) {
+  uint32_t v;
+  asm("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
+  return v;
 }
 
 }  // namespace lpc
