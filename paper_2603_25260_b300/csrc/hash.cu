@@ -78,11 +78,12 @@ __device__ __forceinline__ bool step_axis(uint64_t k, uint64_t m, int d, uint64_
   return true;
 }
 
-// Count present (node, neighbour) pairs of this warp's active threads.
-__device__ __forceinline__ void count_pairs(unsigned long long* pairs, bool present) {
-  const unsigned am = __activemask();
-  const unsigned bm = __ballot_sync(am, present);
-  if ((threadIdx.x & 31) == __ffs(am) - 1) atomicAdd(pairs, (unsigned long long)__popc(bm));
+// Add the present (node, neighbour) pairs a warp counted (each thread over
+// its grid-stride loop) to the launch's count: one atomic per warp, called
+// by every thread of the warp after its loop.
+__device__ __forceinline__ void count_pairs(unsigned long long* pairs, uint32_t mine) {
+  const uint32_t w = __reduce_add_sync(0xffffffffu, mine);
+  if ((threadIdx.x & 31) == 0 && w) atomicAdd(pairs, (unsigned long long)w);
 }
 
 // OR bit 1 << o of a present (node i, offset o) pair into the present-offset
@@ -118,6 +119,7 @@ __global__ void k_kernel_map(const uint64_t* __restrict__ keys, const int64_t* d
                              const ulonglong2* __restrict__ tab, uint64_t mask, int shift,
                              int32_t* nbr, int* err, unsigned long long* pairs, uint32_t* tmask) {
   const IdxT total = (IdxT)(*d_n * 27);
+  uint32_t npair = 0;
   for (IdxT t = blockIdx.x * (IdxT)blockDim.x + threadIdx.x; t < total;
        t += (IdxT)gridDim.x * blockDim.x) {
     const IdxT i = t / 27;
@@ -148,9 +150,10 @@ __global__ void k_kernel_map(const uint64_t* __restrict__ keys, const int64_t* d
       }
     }
     nbr[t] = r;
-    if (pairs) count_pairs(pairs, r >= 0);
+    npair += r >= 0;
     if (tmask) tile_mask_or(tmask, (int64_t)i, o, r >= 0);
   }
+  if (pairs) count_pairs(pairs, npair);
 }
 
 // Child map from the parent map: children at one height, their parent rows
@@ -164,6 +167,7 @@ __global__ void k_kernel_map_child(const uint64_t* __restrict__ ckeys,
                                    const uint32_t* __restrict__ poff, int32_t* nbr,
                                    unsigned long long* pairs, uint32_t* tmask) {
   const IdxT total = (IdxT)(*d_n * 27);
+  uint32_t npair = 0;
   for (IdxT t = blockIdx.x * (IdxT)blockDim.x + threadIdx.x; t < total;
        t += (IdxT)gridDim.x * blockDim.x) {
     const IdxT i = t / 27;
@@ -184,9 +188,10 @@ __global__ void k_kernel_map_child(const uint64_t* __restrict__ ckeys,
       }
     }
     nbr[t] = r;
-    if (pairs) count_pairs(pairs, r >= 0);
+    npair += r >= 0;
     if (tmask) tile_mask_or(tmask, (int64_t)i, o, r >= 0);
   }
+  if (pairs) count_pairs(pairs, npair);
 }
 
 namespace {
