@@ -202,8 +202,9 @@ k_conv333_tc(const __grid_constant__ ConvTcArgs a) {
   constexpr int SG = S / G;        // steps in the ring
   constexpr int NB = Cfg::kNbrBufs;
   extern __shared__ unsigned char smraw[];
-  unsigned char* sm = reinterpret_cast<unsigned char*>(
-      (reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
+  // aligned to 1024 by offsetting smraw itself, so that accesses through sm
+  // stay shared-memory accesses (an integer round trip would make them generic)
+  unsigned char* sm = smraw + ((1024u - (tc::smem_u32(smraw) & 1023u)) & 1023u);
   unsigned char* sB = sm;
   unsigned char* sA = sm + Cfg::kBBytes;
   int32_t* sNbr0 = reinterpret_cast<int32_t*>(sA + (size_t)S * Cfg::kStageBytes);

@@ -635,8 +635,9 @@ k_predictor_tc(DLayer P1, DPred2 P2, const uint32_t* __restrict__ lut,
                const int8_t* __restrict__ F, int f_stride, const int64_t* d_n, int mode,
                const uint8_t* __restrict__ codes, uint16_t* cdf, uint32_t* enc, int8_t* logits) {
   extern __shared__ unsigned char smraw[];
-  unsigned char* sm = reinterpret_cast<unsigned char*>(
-      (reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
+  // aligned to 1024 by offsetting smraw itself, so that accesses through sm
+  // stay shared-memory accesses (an integer round trip would make them generic)
+  unsigned char* sm = smraw + ((1024u - (tc::smem_u32(smraw) & 1023u)) & 1023u);
   __shared__ int32_t sB1[32], sM1[32], sS1[32];
   __shared__ __align__(16) int32_t sB2[256], sM2[256];
   __shared__ __align__(16) long long sK2[256];

@@ -136,8 +136,9 @@ __global__ void __launch_bounds__(kThr, 1) k_tconv_tc(TConvArgs a) {
   using Cfg = TCfg<CIN, NOUT, KO>;
   constexpr int S = Cfg::kStages, G = Cfg::kG, SG = S / G, NB = Cfg::kNbrBufs;
   extern __shared__ unsigned char smraw[];
-  unsigned char* sm = reinterpret_cast<unsigned char*>(
-      (reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
+  // aligned to 1024 by offsetting smraw itself, so that accesses through sm
+  // stay shared-memory accesses (an integer round trip would make them generic)
+  unsigned char* sm = smraw + ((1024u - (tc::smem_u32(smraw) & 1023u)) & 1023u);
   unsigned char* sB = sm;
   unsigned char* sA = sm + Cfg::kBBytes;
   int32_t* sNbr0 = reinterpret_cast<int32_t*>(sA + (size_t)S * Cfg::kStageBytes);
@@ -429,8 +430,9 @@ __global__ void __launch_bounds__(kThr, 1) k_tbwd_tc(TBwdArgs a) {
   constexpr int G = Cfg::G, SG = Cfg::SG, NB = Cfg::kNbrBufs, KS = Cfg::kSteps;
   constexpr int XB = Cfg::kDxBufs > 0 ? Cfg::kDxBufs : 1;
   extern __shared__ unsigned char smraw[];
-  unsigned char* sm = reinterpret_cast<unsigned char*>(
-      (reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
+  // aligned to 1024 by offsetting smraw itself, so that accesses through sm
+  // stay shared-memory accesses (an integer round trip would make them generic)
+  unsigned char* sm = smraw + ((1024u - (tc::smem_u32(smraw) & 1023u)) & 1023u);
   // ring first, the Y tiles right after it, then the weight image and maps
   unsigned char* sA = sm;
   unsigned char* sY = sA + (size_t)SG * G * Cfg::kStageBytes;

@@ -92,8 +92,9 @@ template <int CIN>
 __global__ void __launch_bounds__(kUThreads, 1) k_up_tc(const UpTcArgs a) {
   using Cfg = UpCfg<CIN>;
   extern __shared__ unsigned char smraw[];
-  unsigned char* sm = reinterpret_cast<unsigned char*>(
-      (reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
+  // aligned to 1024 by offsetting smraw itself, so that accesses through sm
+  // stay shared-memory accesses (an integer round trip would make them generic)
+  unsigned char* sm = smraw + ((1024u - (tc::smem_u32(smraw) & 1023u)) & 1023u);
   unsigned char* sW = sm;  // weights: rows slot x 32 + channel, the A operand
   unsigned char* sX = sm + Cfg::kWBytes;  // parent-row stages, the B operand
   __shared__ uint64_t full_bar[kUStages], empty_bar[kUStages], acc_full[2], acc_empty[2];
