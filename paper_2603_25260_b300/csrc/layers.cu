@@ -182,6 +182,9 @@ k_up_prune(DLayer L, const uint64_t* __restrict__ ckey, const uint32_t* __restri
   int b = 0;
   int c_cur = g0 < n ? issue(g0, 0) : 0;  // in flight while the layer is staged
   const SmemLayer s = stage_layer(L, sm, false);
+  // embedding rows move as 16-byte pieces when every row start is aligned
+  const bool emb16 = ((reinterpret_cast<uintptr_t>(out) | (uintptr_t)out_stride |
+                       (uintptr_t)oe_col) & 15) == 0;
   __syncthreads();
   for (; g0 < n; g0 += step, b ^= 1) {
     const int c_next = g0 + step < n ? issue(g0 + step, b ^ 1) : 0;
@@ -191,63 +194,63 @@ k_up_prune(DLayer L, const uint64_t* __restrict__ ckey, const uint32_t* __restri
       tc::cp_async_wait<0>();
     __syncwarp();
     const int m = (int)(n - g0 < kUpGroup ? n - g0 : kUpGroup);
-    // four children at a time: independent dp4a chains overlap
-    int j = 0;
-    for (; j + kUpIlp <= m; j += kUpIlp) {
-      int c[kUpIlp];
-      int32_t acc[kUpIlp];
-      int32_t xv[kUpIlp][CIN / 4];
-      int ec[kUpIlp];  // the children's codes (with oe)
-#pragma unroll
-      for (int u = 0; u < kUpIlp; u++) {
-        const int cu = __shfl_sync(0xffffffffu, c_cur, j + u);
-        c[u] = cu & 7;
-        ec[u] = cu >> 8;
-        const int4* row = reinterpret_cast<const int4*>(stage + (b * kUpGroup + j + u) * CIN);
-#pragma unroll
-        for (int i = 0; i < CIN / 16; i++) {
-          const int4 t = row[i];
-          xv[u][4 * i] = t.x, xv[u][4 * i + 1] = t.y, xv[u][4 * i + 2] = t.z,
-          xv[u][4 * i + 3] = t.w;
-        }
-        acc[u] = s.bias[c[u] * 32 + lane] - L.z_in * s.wsum[c[u] * 32 + lane];
-      }
-      const int4* Wq = reinterpret_cast<const int4*>(s.W) + lane;
-#pragma unroll
-      for (int q = 0; q < CIN / 16; q++)
-#pragma unroll
-        for (int u = 0; u < kUpIlp; u++) {
-          const int4 t = Wq[(c[u] * (CIN / 16) + q) * 32];
-          acc[u] = __dp4a(xv[u][4 * q], t.x, acc[u]);
-          acc[u] = __dp4a(xv[u][4 * q + 1], t.y, acc[u]);
-          acc[u] = __dp4a(xv[u][4 * q + 2], t.z, acc[u]);
-          acc[u] = __dp4a(xv[u][4 * q + 3], t.w, acc[u]);
-        }
-#pragma unroll
-      for (int u = 0; u < kUpIlp; u++) {
-        int32_t a = acc[u];
-        if (L.prelu) a = prelu(a, s.slope[c[u] * 32 + lane]);
-        out[(g0 + j + u) * out_stride + out_col + lane] =
-            (int8_t)requant(a, s.mult[c[u] * 32 + lane], L.shift, L.z_out);
-        if (oe.table) out[(g0 + j + u) * out_stride + oe_col + lane] = __ldg(oe.table + ec[u] * 32 + lane);
+    // the next step's Concat(., E[Y]) half: lane j copies child j's row
+    if (oe.table && lane < m) {
+      const int8_t* es = oe.table + (c_cur >> 8) * 32;
+      int8_t* ed = out + (g0 + lane) * out_stride + oe_col;
+      if (emb16) {
+        const uint4* e4 = reinterpret_cast<const uint4*>(es);
+        uint4* d4 = reinterpret_cast<uint4*>(ed);
+        d4[0] = __ldg(e4);
+        d4[1] = __ldg(e4 + 1);
+      } else {
+        for (int i = 0; i < 32; i++) ed[i] = __ldg(es + i);
       }
     }
-    for (; j < m; j++) {
-      const int cj = __shfl_sync(0xffffffffu, c_cur, j);
-      const int c = cj & 7;
-      int32_t xv[CIN / 4];
-      const int4* row = reinterpret_cast<const int4*>(stage + (b * kUpGroup + j) * CIN);
+    // the group's children slot by slot: a slot's weight row and constants
+    // are loaded once into registers for all its children (lane = output
+    // channel), up to kUpIlp children side by side
+    const int myslot = lane < m ? (c_cur & 7) : 8;
+#pragma unroll 1
+    for (int c = 0; c < 8; c++) {
+      uint32_t mc = __ballot_sync(0xffffffffu, myslot == c);
+      if (!mc) continue;
+      const int32_t a0 = s.bias[c * 32 + lane] - L.z_in * s.wsum[c * 32 + lane];
+      const int32_t mlt = s.mult[c * 32 + lane], slp = s.slope[c * 32 + lane];
+      int4 wr[CIN / 16];
+      const int4* Wq = reinterpret_cast<const int4*>(s.W) + c * (CIN / 16) * 32 + lane;
 #pragma unroll
-      for (int i = 0; i < CIN / 16; i++) {
-        const int4 t = row[i];
-        xv[4 * i] = t.x, xv[4 * i + 1] = t.y, xv[4 * i + 2] = t.z, xv[4 * i + 3] = t.w;
+      for (int q = 0; q < CIN / 16; q++) wr[q] = Wq[q * 32];
+      while (mc) {
+        int jj[kUpIlp];  // the next children of slot c (warp-uniform; -1: none)
+#pragma unroll
+        for (int u = 0; u < kUpIlp; u++) {
+          jj[u] = mc ? __ffs(mc) - 1 : -1;
+          mc &= mc - 1;
+        }
+        int32_t acc[kUpIlp];
+#pragma unroll
+        for (int u = 0; u < kUpIlp; u++) acc[u] = a0;
+#pragma unroll
+        for (int q = 0; q < CIN / 16; q++)
+#pragma unroll
+          for (int u = 0; u < kUpIlp; u++) {
+            if (jj[u] < 0) continue;
+            const int4 x = reinterpret_cast<const int4*>(stage + (b * kUpGroup + jj[u]) * CIN)[q];
+            acc[u] = __dp4a(x.x, wr[q].x, acc[u]);
+            acc[u] = __dp4a(x.y, wr[q].y, acc[u]);
+            acc[u] = __dp4a(x.z, wr[q].z, acc[u]);
+            acc[u] = __dp4a(x.w, wr[q].w, acc[u]);
+          }
+#pragma unroll
+        for (int u = 0; u < kUpIlp; u++) {
+          if (jj[u] < 0) continue;
+          int32_t v = acc[u];
+          if (L.prelu) v = prelu(v, slp);
+          out[(g0 + jj[u]) * out_stride + out_col + lane] =
+              (int8_t)requant(v, mlt, L.shift, L.z_out);
+        }
       }
-      int32_t acc = s.bias[c * 32 + lane] - L.z_in * s.wsum[c * 32 + lane];
-      acc = dot_slice<CIN>(xv, s.W, c, lane, acc);
-      if (L.prelu) acc = prelu(acc, s.slope[c * 32 + lane]);
-      out[(g0 + j) * out_stride + out_col + lane] =
-          (int8_t)requant(acc, s.mult[c * 32 + lane], L.shift, L.z_out);
-      if (oe.table) out[(g0 + j) * out_stride + oe_col + lane] = __ldg(oe.table + (cj >> 8) * 32 + lane);
     }
     __syncwarp();  // buffer b is free for the group after next
     c_cur = c_next;
@@ -796,9 +799,10 @@ k_predictor_tc(DLayer P1, DPred2 P2, const uint32_t* __restrict__ lut,
     tc::tc_fence_after();
     // ---- pass 1: this thread's half row (row erow, symbols 128 cg ..
     // 128 cg + 127) of logits from TMEM, requantised into the keys
-    // (127 - l) 128 + (s & 127) (saturating packs clamp 127 - l to 0..255),
-    // stored in place in the shared tile, and their smallest key; the
-    // accumulator columns come in pairs of 16-column loads per wait
+    // (127 - l) 128 + (s & 127) (saturating packs clamp 127 - l to 0..255);
+    // their smallest key, and their table offsets (127 - l) 128 stored in
+    // the shared tile; the accumulator columns come in pairs of 16-column
+    // loads per wait
     const int64_t r = r0 + erow;
     unsigned char* rowp = sLg + erow * kLogStride + 256 * cg;
     uint4* row4 = reinterpret_cast<uint4*>(rowp);
@@ -860,8 +864,10 @@ k_predictor_tc(DLayer P1, DPred2 P2, const uint32_t* __restrict__ lut,
         kw[2 * j + 1] = __byte_perm(p4, 0, 0x4342) * 128u + ((s4 + 2) | ((s4 + 3) << 16));
         mn = min_u16x2(mn, min_u16x2(kw[2 * j], kw[2 * j + 1]));
       }
-      row4[2 * gi] = make_uint4(kw[0], kw[1], kw[2], kw[3]);
-      row4[2 * gi + 1] = make_uint4(kw[4], kw[5], kw[6], kw[7]);
+      // the tile keeps the table offsets (127 - l) 128 only
+      row4[2 * gi] = make_uint4(kw[0] & kKeyOff2, kw[1] & kKeyOff2, kw[2] & kKeyOff2, kw[3] & kKeyOff2);
+      row4[2 * gi + 1] =
+          make_uint4(kw[4] & kKeyOff2, kw[5] & kKeyOff2, kw[6] & kKeyOff2, kw[7] & kKeyOff2);
     }
     // the row's key (127 - l) 256 + s of its largest logit at its lowest index
     mn = min(mn & 0xFFFFu, mn >> 16);
@@ -882,8 +888,8 @@ k_predictor_tc(DLayer P1, DPred2 P2, const uint32_t* __restrict__ lut,
       const uint32_t kv[4] = {k4.x, k4.y, k4.z, k4.w};
 #pragma unroll
       for (int j = 0; j < 4; j++) {
-        const uint32_t e0 = lds_u32(tb + (kv[j] & kKeyOff));
-        uint32_t e1 = lds_u32(tb + ((kv[j] >> 16) & kKeyOff));
+        const uint32_t e0 = lds_u32(tb + (kv[j] & 0xFFFFu));
+        uint32_t e1 = lds_u32(tb + (kv[j] >> 16));
         if (c == 15 && j == 3) e1 = cg ? 0u : e1;  // the padding entry takes no frequency
         S += e0 + e1;
       }
@@ -907,8 +913,8 @@ k_predictor_tc(DLayer P1, DPred2 P2, const uint32_t* __restrict__ lut,
       uint32_t fw[4];
 #pragma unroll
       for (int j = 0; j < 4; j++) {
-        const uint32_t e0 = lds_u32(tb + (kv[j] & kKeyOff));
-        uint32_t e1 = lds_u32(tb + ((kv[j] >> 16) & kKeyOff));
+        const uint32_t e0 = lds_u32(tb + (kv[j] & 0xFFFFu));
+        uint32_t e1 = lds_u32(tb + (kv[j] >> 16));
         if (c == 15 && j == 3) e1 = cg ? 0u : e1;
         const uint32_t q0 = (e0 * ahi + __umulhi(e0, alo)) >> 8;
         const uint32_t q1 = (e1 * ahi + __umulhi(e1, alo)) >> 8;

@@ -149,6 +149,7 @@ __device__ __forceinline__ uint32_t enc_pair(const SoftRow& o, int lane, int s) 
 // lut[d]); a thread reads lut[(127 - l_s) - (127 - M)] from its own bank, so
 // the 32 loads of a warp never conflict.
 constexpr uint32_t kKeyOff = 0x7F80u;  // the (127 - l) 128 bits of a key
+constexpr uint32_t kKeyOff2 = 0x7F807F80u;  // the same in both halves of a word
 
 __device__ __forceinline__ uint32_t min_u16x2(uint32_t a, uint32_t b) {
   uint32_t d;
