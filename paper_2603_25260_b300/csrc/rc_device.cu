@@ -188,12 +188,18 @@ k_rc_encode_lanes(const RcChunk* __restrict__ ck, int n, const uint32_t* __restr
 }
 
 // Table rows reach shared memory by bulk copies (TMA, one per stage of
-// kStageRows rows, completion counted on the stage's mbarrier) kStages stages
-// ahead of use: rows do not depend on earlier symbols.
+// kStageRows rows, completion counted on the stage's mbarrier) STAGES stages
+// ahead of use: rows do not depend on earlier symbols.  A deep ring (8
+// stages, 32 KB) hides the copies of a launch with few substreams, where
+// each SM holds a few of them; a launch with many substreams (a frame
+// batch) takes the 2-stage ring (8 KB), so that about 24 instead of 7 of
+// its one-warp blocks fit on a SM and the warps hide each other's waits.
 constexpr int kStageRows = 8;
-constexpr int kStages = 8;
 constexpr int kRowBytes = 512;
-constexpr size_t kDecSmem = (size_t)kStages * kStageRows * kRowBytes + 8 * kStages;
+constexpr int kDeepStages = 8, kShallowStages = 2;
+constexpr int kDeepBlocksPerSm = 7;  // 32 KB blocks in 228 KB
+template <int STAGES>
+constexpr size_t dec_smem() { return (size_t)STAGES * kStageRows * kRowBytes + 8 * STAGES; }
 
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes,
                                          uint64_t* bar) {
@@ -204,12 +210,13 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
       : "memory");
 }
 
+template <int STAGES>
 __global__ void __launch_bounds__(32)
 k_rc_decode(const RcChunk* __restrict__ ck, int n, const int64_t* d_n,
             const uint16_t* __restrict__ cdf, const uint8_t* __restrict__ in,
             uint8_t* __restrict__ codes, int* err) {
   extern __shared__ __align__(128) uint8_t sm[];
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + (size_t)kStages * kStageRows * kRowBytes);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + (size_t)STAGES * kStageRows * kRowBytes);
   const int lane = threadIdx.x;
   const int w = blockIdx.x;
   if (d_n) n = (int)min(*d_n, (int64_t)n);
@@ -218,7 +225,7 @@ k_rc_decode(const RcChunk* __restrict__ ck, int n, const int64_t* d_n,
   const int64_t nst = (c.rows + kStageRows - 1) / kStageRows;
   const uint8_t* src = reinterpret_cast<const uint8_t*>(cdf + c.row * 256);
   auto issue = [&](int64_t st) {  // lane 0: rows of stage st into its slot
-    const int slot = (int)(st % kStages);
+    const int slot = (int)(st % STAGES);
     const int64_t r0 = st * kStageRows;
     const int64_t nr = c.rows - r0 < kStageRows ? c.rows - r0 : kStageRows;
     const uint32_t bytes = (uint32_t)(nr * kRowBytes);
@@ -226,9 +233,9 @@ k_rc_decode(const RcChunk* __restrict__ ck, int n, const int64_t* d_n,
              bar + slot);
   };
   if (lane == 0) {
-    for (int s = 0; s < kStages; s++) mbar_init(bar + s, 1);
+    for (int s = 0; s < STAGES; s++) mbar_init(bar + s, 1);
     fence_mbar_init();
-    for (int64_t st = 0; st < kStages && st < nst; st++) issue(st);
+    for (int64_t st = 0; st < STAGES && st < nst; st++) issue(st);
   }
   __syncwarp();
   const uint8_t* p = in + c.byte_off;
@@ -245,8 +252,8 @@ k_rc_decode(const RcChunk* __restrict__ ck, int n, const int64_t* d_n,
   uint8_t* dst = codes + c.row;
   int64_t st = 0;
   for (; st < nst; st++) {
-    const int slot = (int)(st % kStages);
-    const bool ok = mbar_wait(bar + slot, (uint32_t)((st / kStages) & 1));
+    const int slot = (int)(st % STAGES);
+    const bool ok = mbar_wait(bar + slot, (uint32_t)((st / STAGES) & 1));
     if (!__all_sync(0xFFFFFFFFu, ok)) {  // leave together
       lost = true;
       break;
@@ -300,17 +307,17 @@ k_rc_decode(const RcChunk* __restrict__ ck, int n, const int64_t* d_n,
       }
     }
     __syncwarp();
-    if (lane == 0 && st + kStages < nst) {
+    if (lane == 0 && st + STAGES < nst) {
       fence_async_smem();  // this stage's reads come before the copy that reuses it
-      issue(st + kStages);
+      issue(st + STAGES);
     }
   }
   if (lost) {
     // a copy never completed: report it and give the copies still counted
     // on the other stages a bounded chance to land before the block exits
     if (lane == 0) set_error(err, kErrTimeout);
-    for (int64_t q = st + 1; q < nst && q < st + kStages; q++)
-      mbar_wait(bar + (int)(q % kStages), (uint32_t)((q / kStages) & 1));
+    for (int64_t q = st + 1; q < nst && q < st + STAGES; q++)
+      mbar_wait(bar + (int)(q % STAGES), (uint32_t)((q / STAGES) & 1));
     return;
   }
   if (p > end + kRcPad) bad = true;  // read past the zero bytes a flush may leave out
@@ -330,17 +337,32 @@ void launch_rc_encode(const RcChunk* ck, int n, const uint32_t* lofreq, uint8_t*
   count_launches(1);
 }
 
+namespace {
+// the deep ring unless the launch has more than two waves of its blocks
+bool shallow_ring(int64_t nsub) { return nsub > 2 * 148 * kDeepBlocksPerSm; }
+}  // namespace
+
 void launch_rc_decode(const RcChunk* ck, int n, const uint16_t* cdf, const uint8_t* in,
                       uint8_t* codes, int* err, cudaStream_t st) {
   if (n <= 0) return;
-  k_rc_decode<<<n, 32, kDecSmem, st>>>(ck, n, nullptr, cdf, in, codes, err);
+  if (shallow_ring(n))
+    k_rc_decode<kShallowStages><<<n, 32, dec_smem<kShallowStages>(), st>>>(ck, n, nullptr, cdf,
+                                                                           in, codes, err);
+  else
+    k_rc_decode<kDeepStages><<<n, 32, dec_smem<kDeepStages>(), st>>>(ck, n, nullptr, cdf, in,
+                                                                     codes, err);
   count_launches(1);
 }
 
 void launch_rc_decode_dev(const RcChunk* ck, const int64_t* d_n, int64_t cap, const uint16_t* cdf,
                           const uint8_t* in, uint8_t* codes, int* err, cudaStream_t st) {
   if (cap <= 0) return;
-  k_rc_decode<<<(unsigned)cap, 32, kDecSmem, st>>>(ck, (int)cap, d_n, cdf, in, codes, err);
+  if (shallow_ring(cap))
+    k_rc_decode<kShallowStages><<<(unsigned)cap, 32, dec_smem<kShallowStages>(), st>>>(
+        ck, (int)cap, d_n, cdf, in, codes, err);
+  else
+    k_rc_decode<kDeepStages><<<(unsigned)cap, 32, dec_smem<kDeepStages>(), st>>>(
+        ck, (int)cap, d_n, cdf, in, codes, err);
   count_launches(1);
 }
 
