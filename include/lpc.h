@@ -165,16 +165,18 @@ int codec_profile_read(codec_t* codec, int family, double* ms, int64_t* launches
 int codec_profile_staged(codec_t* codec, int family, double* bytes);
 const char* codec_profile_name(int family);
 
-/* Autotuner state (variants[5], ms[22]): variants[0], variants[1] = the
+/* Autotuner state (variants[5], ms[26]): variants[0], variants[1] = the
  * chosen variant of the tensor-core 3x3x3 conv for 32- and 64-channel inputs
- * (-1 while untuned), ms[c * 8 + v] = the timed milliseconds of variant v
- * (bit 0: alternative ring shape, bit 1: contiguous tile order, bit 2: the
- * neighbour rows gathered by TMA gather4 loads instead of cp.async copies);
- * variants[2] = the predictor's (0 CUDA cores, 1 tensor cores), ms[16 + v]
+ * (-1 while untuned), ms[c * 10 + v] = the timed milliseconds of variant v
+ * (v < 8: 128-row tiles, bit 0: alternative ring shape, bit 1: contiguous
+ * tile order, bit 2: the neighbour rows gathered by TMA gather4 loads
+ * instead of cp.async copies; v = 8, 9: 256-row tiles in strided or
+ * contiguous order, for 64-channel inputs the 128-row variants 0 and 2);
+ * variants[2] = the predictor's (0 CUDA cores, 1 tensor cores), ms[20 + v]
  * its timings; variants[3], variants[4] = the Upsampling + Pruning step's
- * for 32- and 64-channel inputs (0 CUDA cores, one warp per child; 1 tensor
- * cores, each parent against all eight slots), ms[18 + 2 c + v] their
- * timings.
+ * for 32- and 64-channel inputs (0 CUDA cores, the children slot by slot;
+ * 1 tensor cores, each parent against all eight slots), ms[22 + 2 c + v]
+ * their timings.
  * Tuning runs on the first encode or decode; every variant gives the same
  * result. */
 int codec_tuning(codec_t* codec, int* variants, float* ms);

@@ -78,12 +78,14 @@ int lpc_conv333(const uint64_t* d_keys, int64_t N, int depth, const int8_t* d_x,
                 int z_in, const int8_t* h_W, const int32_t* h_bias, const int32_t* h_mult,
                 int shift, const int16_t* h_slope, int z_out, int cout, int8_t* d_out,
                 uint64_t stream);
-/* The same with an explicit kernel variant of the tensor-core conv (0..7:
- * bit 0 the alternative ring shape (32 channels: 18 stages in steps of nine
- * offsets), bit 1 contiguous tile order, bit 2 the neighbour rows gathered
- * by TMA gather4 loads (absent neighbours read as zeros without a memory
- * access) instead of 16-byte cp.async copies; the codec's autotuner picks
- * among them).  Every variant gives the same result. */
+/* The same with an explicit kernel variant of the tensor-core conv (0..7,
+ * 128-row tiles: bit 0 the alternative ring shape (32 channels: 18 stages
+ * in steps of nine offsets), bit 1 contiguous tile order, bit 2 the
+ * neighbour rows gathered by TMA gather4 loads (absent neighbours read as
+ * zeros without a memory access) instead of 16-byte cp.async copies; 8, 9:
+ * 256-row tiles in strided or contiguous order, 32 channels only (with 64
+ * channels they run variants 0 and 2); the codec's autotuner picks among
+ * them).  Every variant gives the same result; others: LPC_INVALID_ARG. */
 int lpc_conv333_variant(const uint64_t* d_keys, int64_t N, int depth, const int8_t* d_x, int cin,
                         int z_in, const int8_t* h_W, const int32_t* h_bias,
                         const int32_t* h_mult, int shift, const int16_t* h_slope, int z_out,

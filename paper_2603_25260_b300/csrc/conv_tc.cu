@@ -86,9 +86,18 @@ constexpr int nbr_bufs_of(int alt) {
   return CIN == 64 ? 1 : (alt ? 1 : 2);
 }
 
+// Tall tiles (256 rows, 32 channels only: two 128-row MMAs per offset into
+// the two halves of a 256-column accumulator buffer) halve the tile count
+// and with it the per-tile work (map copy, masks, barrier round trips,
+// accumulator hand-over) per row; their ring: 6 stages of 256 rows in steps
+// of three, the map a tile ahead.
+constexpr int kTallRows = 256;
+constexpr int kTallStages = 6, kTallStep = 3, kTallNbrBufs = 2;
+
 template <int CIN, int S_ = stages_of<CIN>(0), int G_ = step_of<CIN>(0),
-          int NB_ = nbr_bufs_of<CIN>(0)>
+          int NB_ = nbr_bufs_of<CIN>(0), int TM_ = kTileM>
 struct ConvCfg {
+  static constexpr int TM = TM_;                     // rows of a tile
   static constexpr int RB = CIN * 2;                 // bf16 row bytes
   static constexpr int SW = CIN == 64 ? 128 : 64;    // swizzle of the A stage
   static constexpr int kStages = S_;
@@ -99,17 +108,18 @@ struct ConvCfg {
   // one (loaded at the tile's start; leaves room for more stages)
   static constexpr int kNbrBufs = NB_;
   static_assert(kStages % kG == 0 && 27 % kG == 0, "stage groups must tile the ring and offsets");
-  static constexpr int kStageBytes = kTileM * RB;
+  static constexpr int kStageBytes = TM * RB;
   static constexpr int kPerGroup = 256 / CIN;        // offsets per fp32 accumulator
   static constexpr int kGroups = (27 + kPerGroup - 1) / kPerGroup;
   static constexpr int kBufCols = 256;               // TMEM columns per accumulator buffer
   static constexpr int kBBlocks = (27 * CIN + 63) / 64;
   static constexpr int kBBytes = kBBlocks * 4096;
   static constexpr int kChunks = RB / 16;            // 16-byte chunks per row
-  static constexpr int kNbrBytes = kTileM * 27 * 4;  // a tile's neighbour rows
+  static constexpr int kNbrBytes = TM * 27 * 4;      // a tile's neighbour rows
   static constexpr size_t kSmem =
       1024 + kBBytes + (size_t)kStages * kStageBytes + kNbrBufs * kNbrBytes;
-  static_assert(kGroups * 32 <= kBufCols, "accumulators of one tile exceed a buffer");
+  static_assert(kGroups * 32 * (TM / kTileM) <= kBufCols,
+                "accumulators of one tile exceed a buffer");
 };
 
 __device__ int g_conv_error = 0;
@@ -189,14 +199,18 @@ __device__ __forceinline__ void tma_gather4(uint32_t dst, const void* tmap, int 
       : "memory");
 }
 
-template <int CIN, int ALT, int ORDER, int GATHER>
+template <int CIN, int ALT, int ORDER, int GATHER, int TALL = 0>
 __global__ void __launch_bounds__(Roles<GATHER>::kThreads, 1)
 k_conv333_tc(const __grid_constant__ ConvTcArgs a) {
+  static_assert(!TALL || (CIN == 32 && !GATHER), "tall tiles: 32 channels, cp.async gather");
   constexpr int kProdWarps = Roles<GATHER>::kProdWarps;
   constexpr int kProducers = Roles<GATHER>::kProducers;
   constexpr int kMmaWarp = Roles<GATHER>::kMmaWarp;
   constexpr int kThreads = Roles<GATHER>::kThreads;
-  using Cfg = ConvCfg<CIN, stages_of<CIN>(ALT), step_of<CIN>(ALT), nbr_bufs_of<CIN>(ALT)>;
+  using Cfg = typename std::conditional<
+      TALL != 0, ConvCfg<CIN, kTallStages, kTallStep, kTallNbrBufs, kTallRows>,
+      ConvCfg<CIN, stages_of<CIN>(ALT), step_of<CIN>(ALT), nbr_bufs_of<CIN>(ALT)>>::type;
+  constexpr int TM = Cfg::TM;  // rows of a tile
   constexpr int S = Cfg::kStages;
   constexpr int G = Cfg::kG;       // offsets per pipeline step
   constexpr int SG = S / G;        // steps in the ring
@@ -257,7 +271,7 @@ k_conv333_tc(const __grid_constant__ ConvTcArgs a) {
   tc::tc_fence_after();
   const uint32_t tbase = tslot;
   const int64_t n = *a.d_n;
-  const int64_t ntiles = (n + kTileM - 1) / kTileM;
+  const int64_t ntiles = (n + TM - 1) / TM;
   // this CTA's tiles: t_first + lt * t_step, lt < my_tiles
   int64_t t_first, t_step;
   int my_tiles;
@@ -265,7 +279,7 @@ k_conv333_tc(const __grid_constant__ ConvTcArgs a) {
     t_first = blockIdx.x;
     t_step = gridDim.x;
     my_tiles = blockIdx.x < ntiles ? (int)((ntiles - 1 - blockIdx.x) / gridDim.x + 1) : 0;
-  } else if (a.ranges) {  // contiguous runs of about equal cost (launch_conv_ranges)
+  } else if (!TALL && a.ranges) {  // contiguous runs of about equal cost (launch_conv_ranges)
     const int2 rg = a.ranges[blockIdx.x];
     t_first = rg.x;
     t_step = 1;
@@ -276,13 +290,18 @@ k_conv333_tc(const __grid_constant__ ConvTcArgs a) {
     t_step = 1;
     my_tiles = (int)std::max<int64_t>(0, std::min<int64_t>(per, ntiles - t_first));
   }
-  auto tile_r0 = [&](int lt) { return (t_first + (int64_t)lt * t_step) * kTileM; };
+  auto tile_r0 = [&](int lt) { return (t_first + (int64_t)lt * t_step) * TM; };
   // the tile's present offsets (bit o: some node of the tile has its offset-o
   // neighbour): every role walks the same sequence, the present offsets in
   // ascending order, G to a pipeline step; absent ones are neither gathered
   // nor multiplied (their rows would all be zeros)
   auto tile_mask = [&](int lt) -> uint32_t {
-    return a.tmask ? __ldg(a.tmask + t_first + (int64_t)lt * t_step) : 0x7FFFFFFu;
+    if (!a.tmask) return 0x7FFFFFFu;
+    const int64_t tt = t_first + (int64_t)lt * t_step;
+    if (!TALL) return __ldg(a.tmask + tt);
+    // a tall tile: the masks of its two 128-row tiles
+    const int64_t m0 = 2 * tt, nm = (n + kTileM - 1) / kTileM;
+    return __ldg(a.tmask + m0) | (m0 + 1 < nm ? __ldg(a.tmask + m0 + 1) : 0u);
   };
 
   if (w < kProdWarps) {
@@ -291,12 +310,16 @@ k_conv333_tc(const __grid_constant__ ConvTcArgs a) {
     // tile ahead (a partial last tile is read with plain loads instead)
     int last_issued = -1, last_used = -1;  // thread 0's bookkeeping of nbr copies
     auto issue_nbr = [&](int lt) {
-      if (t == 0 && lt < my_tiles && tile_r0(lt) + kTileM <= n) {
+      if (t == 0 && lt < my_tiles && tile_r0(lt) + TM <= n) {
         last_issued = lt;
         tc::fence_async_smem();  // earlier reads of the buffer come first
         uint64_t* bar = &nbr_bar[lt % NB];
         mbar_expect(bar, Cfg::kNbrBytes);
-        bulk_g2s(sNbr0 + (lt % NB) * kTileM * 27, a.nbr + tile_r0(lt) * 27, Cfg::kNbrBytes, bar);
+        // in pieces of one 128-row tile's map (13,824 bytes) at most
+#pragma unroll
+        for (int pc = 0; pc < TM / kTileM; pc++)
+          bulk_g2s(sNbr0 + (lt % NB) * TM * 27 + pc * kTileM * 27,
+                   a.nbr + tile_r0(lt) * 27 + pc * kTileM * 27, Cfg::kNbrBytes / (TM / kTileM), bar);
       }
     };
     issue_nbr(0);
@@ -304,8 +327,8 @@ k_conv333_tc(const __grid_constant__ ConvTcArgs a) {
     // pairs fixed for the whole kernel, so their swizzled destinations and
     // source columns are formed once; per stage only the neighbour's row
     // changes.  TMA: lane l loads rows 4l .. 4l + 3 of every stage.
-    constexpr int kPer = GATHER ? 1 : kTileM * Cfg::kChunks / kProducers;
-    static_assert(GATHER || kPer * kProducers == kTileM * Cfg::kChunks,
+    constexpr int kPer = GATHER ? 1 : TM * Cfg::kChunks / kProducers;
+    static_assert(GATHER || kPer * kProducers == TM * Cfg::kChunks,
                   "copies must split evenly");
     int prow[kPer];
     uint32_t pdst[kPer];
@@ -325,20 +348,20 @@ k_conv333_tc(const __grid_constant__ ConvTcArgs a) {
     uint32_t tm_next = my_tiles > 0 ? tile_mask(0) : 0u;  // masks are read a tile ahead
     for (int lt = 0; lt < my_tiles; lt++) {
       const int64_t r0 = tile_r0(lt);
-      int32_t* sNbr = sNbr0 + (lt % NB) * kTileM * 27;
+      int32_t* sNbr = sNbr0 + (lt % NB) * TM * 27;
       // every producer is done issuing the previous tile's copies; all leave
       // together if any saw the abort flag
       if (producer_sync_or<kProducers>(*abort != 0)) break;
       // the next tile's map a tile ahead (two buffers; with one buffer it
       // went out at the end of the previous tile, tile 0's before the loop)
       if (NB == 2) issue_nbr(lt + 1);
-      if (r0 + kTileM <= n) {
+      if (r0 + TM <= n) {
         if (producer_sync_or<kProducers>(!wait_or_abort(&nbr_bar[lt % NB], (lt / NB) & 1, abort)))
           break;
         last_used = lt;
       } else {
         const int64_t base = r0 * 27, lim = n * 27;
-        for (int i = t; i < kTileM * 27; i += kProducers)
+        for (int i = t; i < TM * 27; i += kProducers)
           sNbr[i] = base + i < lim ? __ldg(a.nbr + base + i) : -1;
         producer_sync_or<kProducers>(false);
       }
@@ -462,6 +485,10 @@ k_conv333_tc(const __grid_constant__ ConvTcArgs a) {
               const uint32_t sb = tc::smem_u32(sB) + (k0 / 64) * 4096 + (k0 % 64) * 2;
               tc::mma_bf16(dbase + g * 32, tc::smem_desc<Cfg::SW>(sa + ks * 32, 8 * Cfg::RB),
                            tc::smem_desc<128>(sb, 1024), idesc, (acc0 || ks > 0) ? 1u : 0u);
+              if (TALL)  // rows 128..255 of the tile into the buffer's upper 128 columns
+                tc::mma_bf16(dbase + kTileM + g * 32,
+                             tc::smem_desc<Cfg::SW>(sa + kTileM * Cfg::RB + ks * 32, 8 * Cfg::RB),
+                             tc::smem_desc<128>(sb, 1024), idesc, (acc0 || ks > 0) ? 1u : 0u);
             }
           }
           tc::mma_commit(&empty_bar[sg]);
@@ -482,101 +509,115 @@ k_conv333_tc(const __grid_constant__ ConvTcArgs a) {
     uint32_t tm_next = my_tiles > 0 ? tile_mask(0) : 0u;
     for (int lt = 0; lt < my_tiles; lt++) {
       const int b = lt & 1;
-      const int64_t r = tile_r0(lt) + e;
-      // the row's inputs that do not wait for the accumulators (the
-      // residual's y1 row, the embedding row) are loaded before the wait
-      uint4 y1v[2] = {}, ev[2] = {};
-      if (r < n) {
-        if (a.has_res) {
-          const uint4* ys = reinterpret_cast<const uint4*>(a.y1 + r * a.y1_stride);
-          y1v[0] = ys[0];
-          y1v[1] = ys[1];
-        }
-        if (a.emb.table) {
-          const uint4* e4 = reinterpret_cast<const uint4*>(a.emb.table + (int)a.emb.code[r] * 32);
-          ev[0] = __ldg(e4);
-          ev[1] = __ldg(e4 + 1);
-        }
-      }
-      // the TMEM loads below are warp-collective: the warp leaves together
-      if (!__all_sync(0xffffffffu, wait_or_abort(&acc_full[b], (lt >> 1) & 1, abort))) break;
-      tc::tc_fence_after();
-      int32_t acc[32];
-#pragma unroll
-      for (int i = 0; i < 32; i++) acc[i] = sBias[i];
-      const uint32_t dbase = tbase + lane_off + (uint32_t)(b * Cfg::kBufCols);
       const uint32_t tm = tm_next;  // groups without a present offset hold nothing
       if (lt + 1 < my_tiles) tm_next = tile_mask(lt + 1);
-      // a group's 32 columns in flight per wait
+      // the tile's rows e and (tall tiles) e + 128, their accumulators in the
+      // buffer's lower and upper 128 columns
+      bool left = false;
 #pragma unroll
-      for (int g = 0; g < Cfg::kGroups; g++) {
-        if (!((tm >> (g * Cfg::kPerGroup)) & ((1u << Cfg::kPerGroup) - 1))) continue;
-        uint32_t v[2][16];
-        tc::tmem_ld16_issue(dbase + g * 32, v[0]);
-        tc::tmem_ld16_issue(dbase + g * 32 + 16, v[1]);
-        tc::tmem_wait_ld();
-#pragma unroll
-        for (int k = 0; k < 2; k++) {
-          tc::tmem_regs_ready(v[k]);
-#pragma unroll
-          for (int i = 0; i < 16; i++) acc[k * 16 + i] += __float2int_rn(__uint_as_float(v[k][i]));
-        }
-      }
-      tc::tc_fence_before();
-      mbar_arrive(&acc_empty[b]);  // the buffer is free for tile lt + 2
-      if (r < n) {
-        __align__(16) int8_t q[32];
-        // the requantisation form is fixed per launch: one straight loop per
-        // form (HI: the layer's, RHI: the residual merge's)
-        auto finish = [&](auto HI, auto RHI) {
+      for (int hf = 0; hf <= TALL; hf++) {
+        const int64_t r = tile_r0(lt) + e + hf * kTileM;
+        // the row's inputs that do not wait for the accumulators (the
+        // residual's y1 row, the embedding row) are loaded before the wait
+        uint4 y1v[2] = {}, ev[2] = {};
+        if (r < n) {
           if (a.has_res) {
-            __align__(16) int8_t y1[32];
-            reinterpret_cast<uint4*>(y1)[0] = y1v[0];
-            reinterpret_cast<uint4*>(y1)[1] = y1v[1];
-#pragma unroll
-            for (int i = 0; i < 32; i++) {
-              int32_t v = acc[i];
-              if (a.prelu) v = prelu(v, sSlope[i]);
-              int y2;
-              if constexpr (decltype(HI)::value) y2 = requant_hi(v, sMult[i], a.z_out);
-              else y2 = requant(v, sMult[i], a.shift, a.z_out);
-              int32_t m = (y1[i] - a.res_z1) * sMa[i] + (y2 - a.res_z2) * sMb[i];
-              m = prelu(m, sRsl[i]);
-              if constexpr (decltype(RHI)::value) q[i] = (int8_t)requant_hi(m, res_ms, a.res_z_out);
-              else q[i] = (int8_t)requant(m, 1, a.res_shift, a.res_z_out);
-            }
-          } else {
-#pragma unroll
-            for (int i = 0; i < 32; i++) {
-              int32_t v = acc[i];
-              if (a.prelu) v = prelu(v, sSlope[i]);
-              if constexpr (decltype(HI)::value) q[i] = (int8_t)requant_hi(v, sMult[i], a.z_out);
-              else q[i] = (int8_t)requant(v, sMult[i], a.shift, a.z_out);
-            }
+            const uint4* ys = reinterpret_cast<const uint4*>(a.y1 + r * a.y1_stride);
+            y1v[0] = ys[0];
+            y1v[1] = ys[1];
           }
-        };
-        if (hi && res_hi) finish(std::true_type{}, std::true_type{});
-        else if (hi) finish(std::true_type{}, std::false_type{});
-        else if (res_hi) finish(std::false_type{}, std::true_type{});
-        else finish(std::false_type{}, std::false_type{});
-        uint4* dst = reinterpret_cast<uint4*>(a.out + r * a.out_stride + a.out_col);
-        dst[0] = reinterpret_cast<const uint4*>(q)[0];
-        dst[1] = reinterpret_cast<const uint4*>(q)[1];
-        if (a.emb.table) {  // the next step's Concat(., E[Y]) half of the row
-          uint4* de = reinterpret_cast<uint4*>(a.out + r * a.out_stride + a.emb_col);
-          de[0] = ev[0];
-          de[1] = ev[1];
+          if (a.emb.table) {
+            const uint4* e4 = reinterpret_cast<const uint4*>(a.emb.table + (int)a.emb.code[r] * 32);
+            ev[0] = __ldg(e4);
+            ev[1] = __ldg(e4 + 1);
+          }
         }
-        if (a.outb) {
-          __align__(16) __nv_bfloat16 bq[32];
+        // the TMEM loads below are warp-collective: the warp leaves together
+        if (hf == 0) {
+          if (!__all_sync(0xffffffffu, wait_or_abort(&acc_full[b], (lt >> 1) & 1, abort))) {
+            left = true;
+            break;
+          }
+          tc::tc_fence_after();
+        }
+        int32_t acc[32];
 #pragma unroll
-          for (int i = 0; i < 32; i++) bq[i] = __int2bfloat16_rn((int)q[i] - a.outb_z);
-          uint4* db = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(a.outb) +
-                                               r * a.outb_stride);
+        for (int i = 0; i < 32; i++) acc[i] = sBias[i];
+        const uint32_t dbase = tbase + lane_off + (uint32_t)(b * Cfg::kBufCols + hf * kTileM);
+        // a group's 32 columns in flight per wait
 #pragma unroll
-          for (int k = 0; k < 4; k++) db[k] = reinterpret_cast<const uint4*>(bq)[k];
+        for (int g = 0; g < Cfg::kGroups; g++) {
+          if (!((tm >> (g * Cfg::kPerGroup)) & ((1u << Cfg::kPerGroup) - 1))) continue;
+          uint32_t v[2][16];
+          tc::tmem_ld16_issue(dbase + g * 32, v[0]);
+          tc::tmem_ld16_issue(dbase + g * 32 + 16, v[1]);
+          tc::tmem_wait_ld();
+#pragma unroll
+          for (int k = 0; k < 2; k++) {
+            tc::tmem_regs_ready(v[k]);
+#pragma unroll
+            for (int i = 0; i < 16; i++) acc[k * 16 + i] += __float2int_rn(__uint_as_float(v[k][i]));
+          }
+        }
+        if (hf == TALL) {
+          tc::tc_fence_before();
+          mbar_arrive(&acc_empty[b]);  // the buffer is free for tile lt + 2
+        }
+        if (r < n) {
+          __align__(16) int8_t q[32];
+          // the requantisation form is fixed per launch: one straight loop per
+          // form (HI: the layer's, RHI: the residual merge's)
+          auto finish = [&](auto HI, auto RHI) {
+            if (a.has_res) {
+              __align__(16) int8_t y1[32];
+              reinterpret_cast<uint4*>(y1)[0] = y1v[0];
+              reinterpret_cast<uint4*>(y1)[1] = y1v[1];
+#pragma unroll
+              for (int i = 0; i < 32; i++) {
+                int32_t v = acc[i];
+                if (a.prelu) v = prelu(v, sSlope[i]);
+                int y2;
+                if constexpr (decltype(HI)::value) y2 = requant_hi(v, sMult[i], a.z_out);
+                else y2 = requant(v, sMult[i], a.shift, a.z_out);
+                int32_t m = (y1[i] - a.res_z1) * sMa[i] + (y2 - a.res_z2) * sMb[i];
+                m = prelu(m, sRsl[i]);
+                if constexpr (decltype(RHI)::value) q[i] = (int8_t)requant_hi(m, res_ms, a.res_z_out);
+                else q[i] = (int8_t)requant(m, 1, a.res_shift, a.res_z_out);
+              }
+            } else {
+#pragma unroll
+              for (int i = 0; i < 32; i++) {
+                int32_t v = acc[i];
+                if (a.prelu) v = prelu(v, sSlope[i]);
+                if constexpr (decltype(HI)::value) q[i] = (int8_t)requant_hi(v, sMult[i], a.z_out);
+                else q[i] = (int8_t)requant(v, sMult[i], a.shift, a.z_out);
+              }
+            }
+          };
+          if (hi && res_hi) finish(std::true_type{}, std::true_type{});
+          else if (hi) finish(std::true_type{}, std::false_type{});
+          else if (res_hi) finish(std::false_type{}, std::true_type{});
+          else finish(std::false_type{}, std::false_type{});
+          uint4* dst = reinterpret_cast<uint4*>(a.out + r * a.out_stride + a.out_col);
+          dst[0] = reinterpret_cast<const uint4*>(q)[0];
+          dst[1] = reinterpret_cast<const uint4*>(q)[1];
+          if (a.emb.table) {  // the next step's Concat(., E[Y]) half of the row
+            uint4* de = reinterpret_cast<uint4*>(a.out + r * a.out_stride + a.emb_col);
+            de[0] = ev[0];
+            de[1] = ev[1];
+          }
+          if (a.outb) {
+            __align__(16) __nv_bfloat16 bq[32];
+#pragma unroll
+            for (int i = 0; i < 32; i++) bq[i] = __int2bfloat16_rn((int)q[i] - a.outb_z);
+            uint4* db = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(a.outb) +
+                                                 r * a.outb_stride);
+#pragma unroll
+            for (int k = 0; k < 4; k++) db[k] = reinterpret_cast<const uint4*>(bq)[k];
+          }
         }
       }
+      if (left) break;
     }
   }
   tc::tc_fence_before();
@@ -682,8 +723,25 @@ void launch_variant(const ConvTcArgs& a, int blocks, cudaStream_t st) {
   k<<<blocks, Roles<GATHER>::kThreads, smem, st>>>(a);
 }
 
+template <int CIN, int ORDER>
+void launch_tall(const ConvTcArgs& a, int blocks, cudaStream_t st) {
+  constexpr size_t smem = ConvCfg<CIN, kTallStages, kTallStep, kTallNbrBufs, kTallRows>::kSmem;
+  static_assert(smem <= 232448, "shared memory of a conv variant exceeds the limit");
+  auto* k = k_conv333_tc<CIN, 0, ORDER, 0, 1>;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k<<<blocks, Roles<0>::kThreads, smem, st>>>(a);
+}
+
 template <int CIN, int GATHER>
 void launch_cin(const ConvTcArgs& a, int blocks, int variant, cudaStream_t st) {
+  if (variant >= 8) {  // tall tiles (32 channels); 64 channels take 0 / 2
+    if constexpr (CIN == 32 && !GATHER) {
+      if (variant & 1) launch_tall<32, 1>(a, blocks, st);
+      else launch_tall<32, 0>(a, blocks, st);
+      return;
+    }
+    variant = (variant & 1) ? 2 : 0;
+  }
   switch (variant & 3) {
     case 1: launch_variant<CIN, 1, 0, GATHER>(a, blocks, st); break;
     case 2: launch_variant<CIN, 0, 1, GATHER>(a, blocks, st); break;

@@ -325,10 +325,13 @@ struct ConvTcArgs {
 };
 size_t conv_tc_weight_bytes(int cin);
 void pack_conv_tc_weights(const int8_t* W, int cin, uint16_t* img);
-// variant in [0, kConvVariants): ring shape (bit 0), tile order (bit 1) and
-// gather schedule (bit 2: cp.async copies, or TMA gather4 loads), chosen by
-// the codec's autotuner; every variant gives the same result.
-constexpr int kConvVariants = 8;
+// variant in [0, kConvVariants): 0..7 are 128-row tiles with ring shape
+// (bit 0), tile order (bit 1) and gather schedule (bit 2: cp.async copies,
+// or TMA gather4 loads); 8 and 9 are 256-row tiles (32 input channels; with
+// 64 the 128-row variants 0 and 2 run instead) in strided or contiguous
+// order.  Chosen by the codec's autotuner; every variant gives the same
+// result.
+constexpr int kConvVariants = 10;
 // CTAs of a conv launch over n_host nodes (its grid), and their tile runs
 // of about equal cost from the tiles' present-offset masks (ranges[ctas]),
 // which the contiguous tile order takes when given.

@@ -287,15 +287,16 @@ class Codec:
         """The conv autotuner's choice per input width and the timed variants
         (milliseconds; bit 0 of a variant = alternative ring shape, bit 1 =
         contiguous tile order, bit 2 = TMA gather4 loads of the neighbour rows
-        instead of cp.async copies)."""
+        instead of cp.async copies; 8, 9 = 256-row tiles, strided or
+        contiguous)."""
         v = (C.c_int * 5)()
-        ms = (C.c_float * 22)()
+        ms = (C.c_float * 26)()
         self._check(self._lib.codec_tuning(self._h, v, ms))
         return {"conv32": v[0], "conv64": v[1], "predictor": v[2], "up32": v[3], "up64": v[4],
-                "ms32": [round(x, 4) for x in ms[:8]], "ms64": [round(x, 4) for x in ms[8:16]],
-                "ms_pred": [round(x, 4) for x in ms[16:18]],
-                "ms_up32": [round(x, 4) for x in ms[18:20]],
-                "ms_up64": [round(x, 4) for x in ms[20:22]]}
+                "ms32": [round(x, 4) for x in ms[:10]], "ms64": [round(x, 4) for x in ms[10:20]],
+                "ms_pred": [round(x, 4) for x in ms[20:22]],
+                "ms_up32": [round(x, 4) for x in ms[22:24]],
+                "ms_up64": [round(x, 4) for x in ms[24:26]]}
 
     def set_tuning(self, conv32: int = -1, conv64: int = -1, predictor: int = -1, up32: int = -1,
                    up64: int = -1):

@@ -159,13 +159,15 @@ def test_conv333(lpc, n, depth, cin, seed):
         assert np.array_equal(got, want)
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5, 6, 7, 8, 9])
 @pytest.mark.parametrize("cin", [32, 64])
-def test_conv333_variants(lpc, cin, variant):
+@pytest.mark.parametrize("n", [40000, 40100])
+def test_conv333_variants(lpc, cin, variant, n):
     """Every kernel variant the autotuner may pick (ring shape, tile order,
-    cp.async or TMA gather4 gather) matches the oracle, over several tiles
-    and a ragged tail."""
-    n, depth, seed = 40000, 9, 21
+    cp.async or TMA gather4 gather, 128- or 256-row tiles) matches the
+    oracle, over several tiles and a ragged tail (for 256-row tiles one that
+    ends in the first or the second half of a tile)."""
+    depth, seed = 9, 21
     xyz = synth.random_cloud(n, depth, seed)
     keys = O.leaf_keys(xyz, depth)
     rng = np.random.Generator(np.random.PCG64(seed))
@@ -182,7 +184,7 @@ def test_codec_autotuner_picks_variants(lpc, blob):
     cod = _codec(lpc, blob, 14, 20000)
     data = cod.encode(_cuda(xyz))
     t = cod.tuning()
-    assert 0 <= t["conv32"] < 8 and 0 <= t["conv64"] < 8 and 0 <= t["predictor"] < 2
+    assert 0 <= t["conv32"] < 10 and 0 <= t["conv64"] < 10 and 0 <= t["predictor"] < 2
     assert 0 <= t["up32"] < 2 and 0 <= t["up64"] < 2
     assert all(0 < m < 1e3 for m in t["ms32"] + t["ms64"] + t["ms_pred"] + t["ms_up32"] +
                t["ms_up64"])
@@ -525,7 +527,7 @@ def test_batch_into_reusable_buffer(lpc, blob):
 
 @pytest.mark.parametrize("variants", [(0, 0, 0, 0, 0), (3, 3, 1, 1, 1), (1, 2, 1, 0, 1),
                                       (2, 1, 0, 1, 0), (4, 4, 1, 1, 1), (7, 5, 1, 0, 0),
-                                      (5, 6, 0, 1, 1)])
+                                      (5, 6, 0, 1, 1), (8, 8, 1, 0, 0), (9, 9, 1, 1, 1)])
 def test_fixed_variants_byte_identical(lpc, blob, variants):
     """Every fixed combination of conv, predictor and up-step variants gives
     the oracle's stream and decodes it (graphs captured with those
