@@ -266,6 +266,7 @@ Codec::~Codec() {
     if (e) cudaEventDestroy(e);
   if (gs_) cudaStreamDestroy(gs_);
   if (cs_) cudaStreamDestroy(cs_);
+  if (up_ev_) cudaEventDestroy(up_ev_);
   for (auto e : ev_) cudaEventDestroy(e);
   for (auto e : pev_) cudaEventDestroy(e);
   if (dmem_) cudaFree(dmem_);
@@ -465,6 +466,10 @@ int Codec::create(const lpc_config& cfg, const void* blob, size_t len) {
   if (cudaStreamCreateWithFlags(&cs_, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
     cs_ = nullptr;
+  }
+  if (cudaEventCreateWithFlags(&up_ev_, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    up_ev_ = nullptr;
   }
   lane_[0] = Scratch{y1_, g_[0], g_[1], gk_, hx_[0], hx_[1], fo_, xb16_, y1b16_};
   lanes_ = gs_ != nullptr && lane_[1].y1 != nullptr;
@@ -1534,13 +1539,41 @@ int Codec::decode(int nf, const uint8_t* const* in, const size_t* lens, int32_t*
     stats.phase_us[12] = now_us() - t0;
     if (dev_rc_) {
       // device range coding: the stream goes up first and the coarse levels
-      // are decoded there too (every coarse chunk of every frame at once)
-      pool_->run_indexed((int64_t)cps.size(), [&](int64_t i) {
+      // are decoded there too (every coarse chunk of every frame at once).
+      // One frame: its bytes through the coarse substreams go up first, and
+      // while the device decodes the coarse levels the pool copies the rest
+      // (the network levels' substreams), which goes up on the copy stream;
+      // the network levels wait for it
+      const Frame& F0 = fr_[0];
+      const size_t pre = nd == 1 && cs_ && up_ev_ && F0.nco > 0
+                             ? (size_t)(F0.soff[F0.nco - 1] + F0.slen[F0.nco - 1])
+                             : up_len;
+      uint8_t* const hbuf = static_cast<uint8_t*>(const_cast<void*>(up_src));
+      uint8_t* const dbuf = static_cast<uint8_t*>(up_dst);
+      size_t ncp = cps.size();
+      if (pre < up_len) {  // one frame, at byte 0 of both buffers
+        cps.clear();
+        for (size_t o = 0; o < pre; o += kCopyPart)
+          cps.push_back(HostCopy{hbuf + o, F0.in + o, std::min(kCopyPart, pre - o)});
+        ncp = cps.size();
+        for (size_t o = pre; o < F0.len; o += kCopyPart)
+          cps.push_back(HostCopy{hbuf + o, F0.in + o, std::min(kCopyPart, F0.len - o)});
+      }
+      pool_->run_indexed((int64_t)ncp, [&](int64_t i) {
         memcpy(cps[i].dst, cps[i].src, cps[i].len);
       });
-      cudaMemcpyAsync(up_dst, up_src, up_len, cudaMemcpyHostToDevice, st_);
+      cudaMemcpyAsync(up_dst, up_src, std::min(pre, up_len), cudaMemcpyHostToDevice, st_);
       stats.phase_us[13] = now_us() - t0;
       if (int s = expand_coarse_device(nd, true)) return s;
+      if (pre < up_len) {
+        pool_->run_indexed((int64_t)(cps.size() - ncp), [&](int64_t i) {
+          const HostCopy& c = cps[ncp + i];
+          memcpy(c.dst, c.src, c.len);
+        });
+        cudaMemcpyAsync(dbuf + pre, hbuf + pre, up_len - pre, cudaMemcpyHostToDevice, cs_);
+        cudaEventRecord(up_ev_, cs_);
+        cudaStreamWaitEvent(st_, up_ev_, 0);
+      }
       stats.phase_us[14] = stats.phase_us[4] = now_us() - t0;
       for (int i = 5; i < 9; i++) stats.phase_us[i] = 0;
       if (int s = decode_net_device(nd, n_out, dev, caps)) return s;

@@ -217,6 +217,7 @@ class Codec {
   bool cap_grid_ = false;
   cudaStream_t gs_ = nullptr;
   cudaStream_t cs_ = nullptr;  // copies that overlap the network (encoder's coarse codes)
+  cudaEvent_t up_ev_ = nullptr;  // decoder: the network levels' bytes are on the device
   cudaEvent_t gev_[2] = {};
   cudaGraphExec_t gexec_[3][5] = {};
   int gkern_[3][5] = {};
