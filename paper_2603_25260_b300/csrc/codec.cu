@@ -1324,86 +1324,143 @@ int Codec::encode(int nf, const int32_t* const* xyz, const int64_t* n, const int
     if (int s = check_device_error()) return s;
     prof_collect();
   }
-  // assemble every frame's stream straight into its caller buffer: headers
-  // and tables here, the substream bytes by the pool (parts of about equal
-  // size; the copies are the bulk of the work for large batches)
+  // assemble every frame's stream straight into its caller buffer.  Batches:
+  // one pool task per frame (its header, substream table and bytes), the
+  // first failing frame's status reported afterwards
   int first = LPC_OK;
-  struct Copy {
-    uint8_t* dst;
-    const uint8_t* src;
-    size_t len;
-  };
-  std::vector<Copy> copies;
-  size_t copy_bytes = 0;
-  for (int i = 0, f = 0; i < nf; i++) {
-    const bool empty = n[i] == 0;
-    const Frame* F = empty ? nullptr : &fr_[f];
-    const int L = Ls[i];
-    uint8_t head[kHdr];
-    const uint8_t hdr[10] = {'L', 'P', 'C', '1', kStreamVersion, (uint8_t)L,
-                             (uint8_t)(L - cfg_.b_off),
-                             (uint8_t)(L - cfg_.t_off), (uint8_t)M_.C, (uint8_t)(empty ? 1 : 0)};
-    memcpy(head, hdr, 10);
-    for (int k = 0; k < 8; k++) head[10 + k] = (uint8_t)(M_.hash >> (8 * k));
-    std::vector<uint8_t> table;
-    put_varint(table, (uint64_t)cfg_.chunk);
-    put_varint(table, (uint64_t)kCoarseChunk);
-    size_t b0 = 0, b1 = 0, nsub = 0;
-    if (!empty) {
-      b0 = F->sub_base;
-      b1 = f + 1 < nd ? fr_[f + 1].sub_base : tasks_.size();
-      for (int d = 1; d < F->b; d++) put_varint(table, (uint64_t)tasks_[b0 + d].count);
-      for (size_t k = b0; k < b1; k++)
-        nsub += k < b0 + (size_t)F->b ? tasks_[k].parts.size() : 1;
-    }
-    put_varint(table, nsub);
-    size_t body = 0;
-    uint64_t prev = 0;
-    for (size_t k = b0; k < b1; k++) {
-      if (k < b0 + (size_t)F->b) {
-        for (uint32_t l : tasks_[k].parts) put_len(table, l, prev);
-      } else {
-        put_len(table, tasks_[k].len, prev);
+  if (nf > 2) {
+    std::vector<int> fidx(nf), fst(nf, LPC_OK);
+    for (int i = 0, f = 0; i < nf; i++) fidx[i] = n[i] == 0 ? -1 : f++;
+    pool_->run_indexed(nf, [&](int64_t ii) {
+      const int i = (int)ii;
+      const bool empty = fidx[i] < 0;
+      const Frame* F = empty ? nullptr : &fr_[fidx[i]];
+      const int f = fidx[i];
+      const int L = Ls[i];
+      uint8_t head[kHdr];
+      const uint8_t hdr[10] = {'L', 'P', 'C', '1', kStreamVersion, (uint8_t)L,
+                               (uint8_t)(L - cfg_.b_off),
+                               (uint8_t)(L - cfg_.t_off), (uint8_t)M_.C, (uint8_t)(empty ? 1 : 0)};
+      memcpy(head, hdr, 10);
+      for (int k = 0; k < 8; k++) head[10 + k] = (uint8_t)(M_.hash >> (8 * k));
+      std::vector<uint8_t> table;
+      put_varint(table, (uint64_t)cfg_.chunk);
+      put_varint(table, (uint64_t)kCoarseChunk);
+      size_t b0 = 0, b1 = 0, nsub = 0;
+      if (!empty) {
+        b0 = F->sub_base;
+        b1 = f + 1 < nd ? fr_[f + 1].sub_base : tasks_.size();
+        for (int d = 1; d < F->b; d++) put_varint(table, (uint64_t)tasks_[b0 + d].count);
+        for (size_t k = b0; k < b1; k++)
+          nsub += k < b0 + (size_t)F->b ? tasks_[k].parts.size() : 1;
       }
-      body += tasks_[k].len;
-    }
-    const size_t total_len = kHdr + table.size() + body;
-    lens[i] = total_len;
-    if (total_len > caps[i] || !out[i]) {
-      if (!first) first = fail(LPC_CAPACITY, "encode: output buffer too small");
-    } else {
+      put_varint(table, nsub);
+      size_t body = 0;
+      uint64_t prev = 0;
+      for (size_t k = b0; k < b1; k++) {
+        if (k < b0 + (size_t)F->b) {
+          for (uint32_t l : tasks_[k].parts) put_len(table, l, prev);
+        } else {
+          put_len(table, tasks_[k].len, prev);
+        }
+        body += tasks_[k].len;
+      }
+      const size_t total_len = kHdr + table.size() + body;
+      lens[i] = total_len;
+      if (total_len > caps[i] || !out[i]) {
+        fst[i] = LPC_CAPACITY;
+        return;
+      }
       memcpy(out[i], head, kHdr);
       memcpy(out[i] + kHdr, table.data(), table.size());
       uint8_t* p = out[i] + kHdr + table.size();
       for (size_t k = b0; k < b1; k++) {
         const SubTask& T = tasks_[k];
         const uint8_t* src = T.rc >= 0 ? static_cast<const uint8_t*>(h_rcbuf_.p) : h_arena_;
-        copies.push_back(Copy{p, src + T.arena, T.len});
-        copy_bytes += T.len;
+        memcpy(p, src + T.arena, T.len);
         p += T.len;
       }
-    }
-    if (!empty) f++;
-  }
-  {
-    const int parts = (int)std::min<size_t>((size_t)pool_->size(), 1 + copy_bytes / (256 << 10));
-    const size_t per = (copy_bytes + parts - 1) / parts;
-    size_t k = 0;
-    auto run = [&copies](size_t a, size_t b) {
-      for (size_t j = a; j < b; j++) memcpy(copies[j].dst, copies[j].src, copies[j].len);
+    });
+    for (int i = 0; i < nf && !first; i++)
+      if (fst[i]) first = fail(fst[i], "encode: output buffer too small");
+  } else {
+    struct Copy {
+      uint8_t* dst;
+      const uint8_t* src;
+      size_t len;
     };
-    std::vector<std::pair<size_t, size_t>> ranges;
-    if (parts <= 1) ranges.push_back({0, copies.size()});
-    while (parts > 1 && k < copies.size()) {
-      size_t b = k, acc = 0;
-      while (b < copies.size() && (acc < per || b == k)) acc += copies[b++].len;
-      ranges.push_back({k, b});
-      k = b;
+    std::vector<Copy> copies;
+    size_t copy_bytes = 0;
+    for (int i = 0, f = 0; i < nf; i++) {
+      const bool empty = n[i] == 0;
+      const Frame* F = empty ? nullptr : &fr_[f];
+      const int L = Ls[i];
+      uint8_t head[kHdr];
+      const uint8_t hdr[10] = {'L', 'P', 'C', '1', kStreamVersion, (uint8_t)L,
+                               (uint8_t)(L - cfg_.b_off),
+                               (uint8_t)(L - cfg_.t_off), (uint8_t)M_.C, (uint8_t)(empty ? 1 : 0)};
+      memcpy(head, hdr, 10);
+      for (int k = 0; k < 8; k++) head[10 + k] = (uint8_t)(M_.hash >> (8 * k));
+      std::vector<uint8_t> table;
+      put_varint(table, (uint64_t)cfg_.chunk);
+      put_varint(table, (uint64_t)kCoarseChunk);
+      size_t b0 = 0, b1 = 0, nsub = 0;
+      if (!empty) {
+        b0 = F->sub_base;
+        b1 = f + 1 < nd ? fr_[f + 1].sub_base : tasks_.size();
+        for (int d = 1; d < F->b; d++) put_varint(table, (uint64_t)tasks_[b0 + d].count);
+        for (size_t k = b0; k < b1; k++)
+          nsub += k < b0 + (size_t)F->b ? tasks_[k].parts.size() : 1;
+      }
+      put_varint(table, nsub);
+      size_t body = 0;
+      uint64_t prev = 0;
+      for (size_t k = b0; k < b1; k++) {
+        if (k < b0 + (size_t)F->b) {
+          for (uint32_t l : tasks_[k].parts) put_len(table, l, prev);
+        } else {
+          put_len(table, tasks_[k].len, prev);
+        }
+        body += tasks_[k].len;
+      }
+      const size_t total_len = kHdr + table.size() + body;
+      lens[i] = total_len;
+      if (total_len > caps[i] || !out[i]) {
+        if (!first) first = fail(LPC_CAPACITY, "encode: output buffer too small");
+      } else {
+        memcpy(out[i], head, kHdr);
+        memcpy(out[i] + kHdr, table.data(), table.size());
+        uint8_t* p = out[i] + kHdr + table.size();
+        for (size_t k = b0; k < b1; k++) {
+          const SubTask& T = tasks_[k];
+          const uint8_t* src = T.rc >= 0 ? static_cast<const uint8_t*>(h_rcbuf_.p) : h_arena_;
+          copies.push_back(Copy{p, src + T.arena, T.len});
+          copy_bytes += T.len;
+          p += T.len;
+        }
+      }
+      if (!empty) f++;
     }
-    for (size_t r = 1; r < ranges.size(); r++)
-      pool_->submit(0, [&run, a = ranges[r].first, b = ranges[r].second] { run(a, b); });
-    if (!ranges.empty()) run(ranges[0].first, ranges[0].second);
-    pool_->wait(0);
+    {
+      const int parts = (int)std::min<size_t>((size_t)pool_->size(), 1 + copy_bytes / (256 << 10));
+      const size_t per = (copy_bytes + parts - 1) / parts;
+      size_t k = 0;
+      auto run = [&copies](size_t a, size_t b) {
+        for (size_t j = a; j < b; j++) memcpy(copies[j].dst, copies[j].src, copies[j].len);
+      };
+      std::vector<std::pair<size_t, size_t>> ranges;
+      if (parts <= 1) ranges.push_back({0, copies.size()});
+      while (parts > 1 && k < copies.size()) {
+        size_t b = k, acc = 0;
+        while (b < copies.size() && (acc < per || b == k)) acc += copies[b++].len;
+        ranges.push_back({k, b});
+        k = b;
+      }
+      for (size_t r = 1; r < ranges.size(); r++)
+        pool_->submit(0, [&run, a = ranges[r].first, b = ranges[r].second] { run(a, b); });
+      if (!ranges.empty()) run(ranges[0].first, ranges[0].second);
+      pool_->wait(0);
+    }
   }
   // statistics of the first frame
   if (nd > 0) {
