@@ -1484,45 +1484,52 @@ int Codec::decode(int nf, const uint8_t* const* in, const size_t* lens, int32_t*
   stats = Stats{};
   std::vector<int> dev;
   std::vector<Frame> all(nf);
-  for (int i = 0; i < nf; i++) {
+  // every stream's header and substream table: parsed by the pool, one
+  // task a stream, for batches; the first failing stream's status returned
+  struct PR {
+    int st;
+    const char* msg;
+    bool dev;  // a frame with points, to decode
+  };
+  auto parse = [&](int i) -> PR {
     n_out[i] = 0;
     Frame& F = all[i];
     const uint8_t* p = in[i];
     const size_t len = lens[i];
     if (!p || len < (size_t)kHdr || memcmp(p, "LPC1", 4) != 0 || p[4] != kStreamVersion)
-      return fail(LPC_CORRUPT_STREAM, "decode: not an LPC1 version 3 stream");
+      return PR{LPC_CORRUPT_STREAM, "decode: not an LPC1 version 3 stream", false};
     const int L = p[5], b = p[6], t = p[7], C = p[8], flags = p[9];
     uint64_t hash = 0;
     for (int k = 0; k < 8; k++) hash |= (uint64_t)p[10 + k] << (8 * k);
     if (L < 6 || L > kMaxDepth || b != L - cfg_.b_off)
-      return fail(LPC_CORRUPT_STREAM, "decode: bad depth fields");
+      return PR{LPC_CORRUPT_STREAM, "decode: bad depth fields", false};
     if (hash != M_.hash || C != M_.C)
-      return fail(LPC_WEIGHTS_MISMATCH, "decode: stream was written with another weight blob");
-    if (t != L - cfg_.t_off) return fail(LPC_CORRUPT_STREAM, "decode: bad threshold field");
+      return PR{LPC_WEIGHTS_MISMATCH, "decode: stream was written with another weight blob", false};
+    if (t != L - cfg_.t_off) return PR{LPC_CORRUPT_STREAM, "decode: bad threshold field", false};
     if (L > std::min(cfg_.L, kMaxL))
-      return fail(LPC_INVALID_ARG, "decode: stream depth exceeds the codec's L");
+      return PR{LPC_INVALID_ARG, "decode: stream depth exceeds the codec's L", false};
     size_t pos = kHdr;
     uint64_t chunk, kc, nsub;
     if (!get_varint(p, len, pos, chunk) || !get_varint(p, len, pos, kc) || chunk < 1 ||
         chunk > (uint64_t)ring_slots_ || kc < 1 || kc > ((uint64_t)1 << 30))
-      return fail(LPC_CORRUPT_STREAM, "decode: bad stream table");
+      return PR{LPC_CORRUPT_STREAM, "decode: bad stream table", false};
     F.kc = (int64_t)kc;
     F.cN[0] = 1;
     F.nco = 1;
     for (int d = 1; d < b && !(flags & 1); d++) {
       uint64_t v;
       if (!get_varint(p, len, pos, v) || v < 1 || v > 8 * (uint64_t)F.cN[d - 1])
-        return fail(LPC_CORRUPT_STREAM, "decode: bad coarse level size");
+        return PR{LPC_CORRUPT_STREAM, "decode: bad coarse level size", false};
       if (v > (uint64_t)cfg_.max_points)
-        return fail(LPC_CAPACITY, "decode: frame exceeds max_points");
+        return PR{LPC_CAPACITY, "decode: frame exceeds max_points", false};
       F.cN[d] = (int64_t)v;
       F.nco += (size_t)((v + kc - 1) / kc);
     }
     if (!get_varint(p, len, pos, nsub) || nsub > len)
-      return fail(LPC_CORRUPT_STREAM, "decode: bad stream table");
+      return PR{LPC_CORRUPT_STREAM, "decode: bad stream table", false};
     if (flags & 1) {
-      if (nsub != 0) return fail(LPC_CORRUPT_STREAM, "decode: empty frame with substreams");
-      continue;
+      if (nsub != 0) return PR{LPC_CORRUPT_STREAM, "decode: empty frame with substreams", false};
+      return PR{LPC_OK, nullptr, false};
     }
     F.L = L;
     F.b = b;
@@ -1535,19 +1542,28 @@ int Codec::decode(int nf, const uint8_t* const* in, const size_t* lens, int32_t*
     uint64_t prev = 0;
     for (uint64_t k = 0; k < nsub; k++) {
       uint64_t z;
-      if (!get_varint(p, len, pos, z)) return fail(LPC_CORRUPT_STREAM, "decode: bad stream table");
+      if (!get_varint(p, len, pos, z)) return PR{LPC_CORRUPT_STREAM, "decode: bad stream table", false};
       const uint64_t mag = (z + 1) >> 1;
       if ((z & 1) ? mag > prev : mag > len)
-        return fail(LPC_CORRUPT_STREAM, "decode: bad stream table");
+        return PR{LPC_CORRUPT_STREAM, "decode: bad stream table", false};
       F.slen[k] = prev = (z & 1) ? prev - mag : prev + mag;
     }
     for (uint64_t k = 0; k < nsub; k++) {
-      if (F.slen[k] > len - pos) return fail(LPC_CORRUPT_STREAM, "decode: truncated stream");
+      if (F.slen[k] > len - pos) return PR{LPC_CORRUPT_STREAM, "decode: truncated stream", false};
       F.soff[k] = pos;
       pos += F.slen[k];
     }
-    if (nsub < F.nco) return fail(LPC_CORRUPT_STREAM, "decode: missing substream");
-    dev.push_back(i);
+  if (nsub < F.nco) return PR{LPC_CORRUPT_STREAM, "decode: missing substream", false};
+  return PR{LPC_OK, nullptr, true};
+  };
+  std::vector<PR> pr(nf);
+  if (nf > 2)
+    pool_->run_indexed(nf, [&](int64_t i) { pr[i] = parse((int)i); });
+  else
+    for (int i = 0; i < nf; i++) pr[i] = parse(i);
+  for (int i = 0; i < nf; i++) {
+    if (pr[i].st != LPC_OK) return fail(pr[i].st, pr[i].msg);
+    if (pr[i].dev) dev.push_back(i);
   }
   // Decodes the frames dev (caller indices) as one batch.  coarse_ready: their
   // coarse levels were decoded by earlier pool tasks (group 3, status in
