@@ -592,3 +592,35 @@ def test_repeated_encode_graph_path(lpc, blob, host_coding):
     x = _cuda(xyz)
     for _ in range(4):
         assert cod.encode(x) == want
+
+
+def test_encode_batch_capacity_per_frame(lpc, blob):
+    """A batch (more than two frames, so the streams are assembled one frame
+    per pool task) where one frame's output buffer is too small: the call
+    returns LPC_CAPACITY with that frame's needed length, and every other
+    frame still receives the oracle's stream."""
+    import ctypes as C
+    L = 12
+    frames = [synth.random_cloud(n, L, 60 + k) for k, n in enumerate([3000, 500, 4000, 0, 2500])]
+    cod = lpc.Codec(blob, L, 4000, max_frames=len(frames))
+    xs = [_cuda(f) for f in frames]
+    want = [O.encode(blob, f, L) for f in frames]
+    nf = len(frames)
+    caps = [len(w) + 64 for w in want]
+    caps[2] = 10
+    bufs = [np.zeros(c, dtype=np.uint8) for c in caps]
+    lib = cod._lib
+    ptrs = (C.c_void_p * nf)(*[x.data_ptr() if x.shape[0] else 0 for x in xs])
+    ns = (C.c_int64 * nf)(*[x.shape[0] for x in xs])
+    ls = (C.c_int * nf)(*([L] * nf))
+    outs = (C.c_void_p * nf)(*[b.ctypes.data for b in bufs])
+    capa = (C.c_size_t * nf)(*caps)
+    lens = (C.c_size_t * nf)()
+    st = lib.encode_batch(cod._h, nf, ptrs, ns, ls, outs, capa, lens)
+    assert st == lpc.CAPACITY
+    assert lens[2] == len(want[2])
+    for i in (0, 1, 3, 4):
+        assert lens[i] == len(want[i])
+        assert bytes(bufs[i][:lens[i]]) == want[i]
+    # the codec stays usable
+    assert cod.encode_batch(xs, [L] * nf) == want
