@@ -679,9 +679,14 @@ k_predictor_tc(DLayer P1, DPred2 P2, const uint32_t* __restrict__ lut,
       sK2[t] = t < kNsym ? 128ll * 4294967296ll - 1 - K : 255ll * 4294967296ll;
     }
   }
-  {  // the exp table, word 32 d + j = lut[d] for every bank j
+  {  // the exp table, word 32 d + j = lut[d] for every bank j: the 256
+     // entries read from global memory once (one load a thread instead of
+     // sixteen), then replicated from shared memory
     uint32_t* tab = reinterpret_cast<uint32_t*>(sm + kPredTab);
-    for (int i = t; i < 256 * 32; i += kPThreads) tab[i] = __ldg(lut + (i >> 5));
+    __shared__ uint32_t slut0[256];
+    if (t < 256) slut0[t] = __ldg(lut + t);
+    __syncthreads();
+    for (int i = t; i < 256 * 32; i += kPThreads) tab[i] = slut0[i >> 5];
   }
   if (t < 32) {
     sB1[t] = (int32_t)(kMagicBits - (uint32_t)P1.bias[t]);
