@@ -195,9 +195,14 @@ __global__ void k_kernel_map_child(const uint64_t* __restrict__ ckeys,
 }
 
 namespace {
+// per_sm: blocks of 256 threads a SM; 8 is one resident wave (2048 threads)
 int grid_for(int64_t work, int per_sm) {
   return (int)std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, 148 * per_sm));
 }
+// kernel maps: one resident wave while a thread has at most 16 items (one
+// frame: ~5), two waves beyond (the 64-frame batch, ~250 items a thread,
+// measured 5 % faster with them)
+int map_blocks_per_sm(int64_t items) { return items <= (int64_t)148 * 2048 * 16 ? 8 : 16; }
 }  // namespace
 
 void launch_kernel_map(const uint64_t* keys, const int64_t* d_n, int64_t n_host, const int* Lf,
@@ -213,10 +218,10 @@ void launch_kernel_map(const uint64_t* keys, const int64_t* d_n, int64_t n_host,
   k_hash_clear<<<grid_for(slots, 8), 256, 0, st>>>(h.slots, slots);
   k_hash_insert<<<grid_for(n_host, 8), 256, 0, st>>>(keys, d_n, h.slots, mask, shift, err);
   if (n_host * 27 < ((int64_t)1 << 31))
-    k_kernel_map<uint32_t><<<grid_for(n_host * 27, 16), 256, 0, st>>>(
+    k_kernel_map<uint32_t><<<grid_for(n_host * 27, map_blocks_per_sm(n_host * 27)), 256, 0, st>>>(
         keys, d_n, Lf, depth, h.slots, mask, shift, nbr, err, pc, tmask);
   else
-    k_kernel_map<int64_t><<<grid_for(n_host * 27, 16), 256, 0, st>>>(
+    k_kernel_map<int64_t><<<grid_for(n_host * 27, map_blocks_per_sm(n_host * 27)), 256, 0, st>>>(
         keys, d_n, Lf, depth, h.slots, mask, shift, nbr, err, pc, tmask);
   count_launches(3);
 }
@@ -229,10 +234,10 @@ void launch_kernel_map_child(const uint64_t* ckeys, const uint32_t* cpar, const 
   if (tmask) cudaMemsetAsync(tmask, 0, 4 * (size_t)conv_tiles(n_host), st);
   auto pc = reinterpret_cast<unsigned long long*>(pairs);
   if (n_host * 27 < ((int64_t)1 << 31))
-    k_kernel_map_child<uint32_t><<<grid_for(n_host * 27, 16), 256, 0, st>>>(
+    k_kernel_map_child<uint32_t><<<grid_for(n_host * 27, map_blocks_per_sm(n_host * 27)), 256, 0, st>>>(
         ckeys, cpar, d_n, pnbr, pcode, poff, nbr, pc, tmask);
   else
-    k_kernel_map_child<int64_t><<<grid_for(n_host * 27, 16), 256, 0, st>>>(
+    k_kernel_map_child<int64_t><<<grid_for(n_host * 27, map_blocks_per_sm(n_host * 27)), 256, 0, st>>>(
         ckeys, cpar, d_n, pnbr, pcode, poff, nbr, pc, tmask);
   count_launches(1);
 }

@@ -418,10 +418,19 @@ void launch_down(const DLayer& W, const uint64_t* ckey, const uint32_t* poff, co
   if (np_host <= 0) return;
   const size_t smem =
       smem_layer_bytes(W) + (size_t)kWarps * 2 * ((size_t)kDownRows * W.cin + kDownRows);
-  const int blocks = (int)std::min<int64_t>(
-      (np_host + kWarps * kDownGroup - 1) / (kWarps * kDownGroup), kBlocksRow);
+  const int64_t want = (np_host + kWarps * kDownGroup - 1) / (kWarps * kDownGroup);
   auto go = [&](auto k) {
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // at most one wave of resident blocks (the warps stride over the
+    // parents): a second, partial wave cost nearly a whole one's latency
+    static int per_sm = 0;
+    if (!per_sm && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kWarps * 32, smem) !=
+                        cudaSuccess ||
+                    per_sm < 1)) {
+      cudaGetLastError();
+      per_sm = kBlocksRow / 148;
+    }
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(want, 148 * per_sm));
     k<<<blocks, kWarps * 32, smem, st>>>(W, ckey, poff, d_np, x, x_stride, out, out_stride,
                                          out_col);
   };
